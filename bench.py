@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Benchmark of the multispecies glioblastoma step on GB300.
+
+Metric: voxel-steps/s = N^3 * steps / time for steps of the operator-split model (Section 3 of
+the paper: transport, Crank-Nicolson diffusion, reactions, screened elasticity) on the 256^3
+synthetic brain, through the library's C ABI.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference ...   # the CPU oracle on the host cores, same metric
+
+With N > 1 (torchrun), every rank runs an independent replica of the workload (the workload
+has no exchange step between replicas); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxel-steps/s at 256^3 (mixed FP32 vs plain FP64, same GPU); adjoint/forward time"
+UNIT = "voxel-steps/s"
+FIELDS = ("p", "i", "n", "g", "w", "f", "o", "l", "bg", "ux", "uy", "uz", "vx", "vy", "vz")
+
+# algorithmic traffic and arithmetic of the elasticity operator kernel, per voxel and launch:
+# reads p (3 comps), face coefficients (lambda+2mu)/h^2 and mu/h^2 (3 + 3), Jacobi diagonal
+# (3), node mu and lambda (2); writes q (3): 17 FP64 arrays.
+ELAS_MATVEC_BYTES_PER_VOXEL = 17 * 8
+ELAS_MATVEC_FLOPS_PER_VOXEL = 123
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--dt", type=float, default=0.01)
+    ap.add_argument("--precision", choices=("fp64", "mixed"), default="fp64")
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=64)
+    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# GB300 FP64 peak: not in the measured-peaks file.  Derived from the FP64 issue rate of the
+# SM and the maximum SM clock ("FP64 roof").
+FP64_PEAK_TFLOPS = 1.26
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(n, steps, warm_steps=0):
+    """Time the CPU oracle (all host cores) on `steps` steps of an n^3 synthetic brain."""
+    cores = len(os.sched_getaffinity(0))
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    from oracle import Oracle
+    from synth import initial_state, workload_params
+    O = Oracle()
+    P = workload_params()
+    st = initial_state(n, seed=0)
+    O.init(n, P, st)
+    for _ in range(warm_steps):
+        O.step(n, P, 0.01, st)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        O.step(n, P, 0.01, st)
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt, cores, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    n = args.cpu_sample_n
+    value, cores, secs = oracle_sample(n, args.steps, warm_steps=args.warmup)
+    sample = (f"CPU oracle, {n}^3 synthetic brain (same generator and parameters as the "
+              f"{args.n}^3 workload), {args.warmup} untimed + {args.steps} timed steps, "
+              f"{cores} OpenMP threads; elasticity CG iterations grow with N, so the "
+              f"per-voxel rate at {args.n}^3 would be lower")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.n}^3 synthetic brain, multispecies step, dt {args.dt}",
+                   "grid": args.n, "precision": args.precision},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+    from paper_1810_05370_gb300 import Simulation
+    from synth import initial_state, workload_params
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
+    n = args.n
+    V = n ** 3
+    P = workload_params()
+    st0 = initial_state(n, seed=0)
+    sim = Simulation(n, P, st0, precision=args.precision, device=dev)
+    stream = sim.stream
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    # ---------------------------------------------------------------- device-resident timing
+    for _ in range(args.warmup):
+        sim.step(args.dt)
+    sim.set_timing(True)
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    agg = {"launches": 0, "t_mv": 0.0, "n_mv": 0, "it_elas": [], "it_diff": []}
+    for _ in range(args.steps):
+        s = sim.step(args.dt)
+        agg["launches"] += s["launches"]
+        agg["t_mv"] += s["t_elas_matvec_ms"]
+        agg["n_mv"] += s["n_elas_matvec"]
+        agg["it_elas"].append(s["it_elas"])
+        agg["it_diff"].append(s["it_diff"])
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    sim.set_timing(False)
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * V * args.steps / (ms_max * 1e-3)
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.empty(sim.shape, dtype=torch.float64, pin_memory=True) for k in FIELDS}
+        for k in FIELDS:
+            host[k].copy_(sim.state[k])
+        nbytes = sum(h.numel() * 8 for h in host.values())
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                for k in FIELDS:
+                    sim.state[k].copy_(host[k], non_blocking=True)
+            sim.step(args.dt)
+            with torch.cuda.stream(stream):
+                for k in FIELDS:
+                    host[k].copy_(sim.state[k], non_blocking=True)
+            stream.synchronize()
+        barrier()
+        secs = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([secs], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            secs = float(t.item())
+        e2e = {"value": world * V * args.steps / secs, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # ---------------------------------------------------------------- roofline of the top kernel
+    peaks, peak_src = load_peaks()
+    avg_ms = agg["t_mv"] / max(agg["n_mv"], 1)
+    mv_bytes = ELAS_MATVEC_BYTES_PER_VOXEL * V
+    mv_flops = ELAS_MATVEC_FLOPS_PER_VOXEL * V
+    gbs = mv_bytes / (avg_ms * 1e-3) / 1e9
+    tfl = mv_flops / (avg_ms * 1e-3) / 1e12
+    roof = {
+        "kernel": "k_elas_matvec (FP64 19-point Navier-Lame operator + <p, Ap>)",
+        "bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
+        "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"], "hbm_peak_source": peak_src,
+        "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"],
+        "share_of_step": agg["t_mv"] / ms if ms > 0 else None,
+    }
+
+    # ---------------------------------------------------------------- CPU baseline (rank 0)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cn = args.cpu_sample_n
+        v_cpu, cores, secs = oracle_sample(cn, args.cpu_sample_steps)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{cn}^3 synthetic brain, {args.cpu_sample_steps} steps after init "
+                         f"({secs:.1f} s); per-voxel cost grows with N, so this flatters the oracle"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{n}^3 synthetic brain (nested ellipsoids, seed 0), "
+                                   f"multispecies step dt {args.dt}, CG rtol 1e-8, "
+                                   f"{args.precision} path",
+                       "grid": n, "precision": args.precision,
+                       "l2": "inputs larger than L2 (15 state arrays + workspace, "
+                             f"{(15 * V * 8 + sim.workspace.numel()) / 1e9:.1f} GB)",
+                       "parallelism": f"replicas x{world}"},
+            "solver": {"it_elas_per_step": agg["it_elas"], "it_diff_per_step": agg["it_diff"]},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": agg["launches"],
+        }
+        print(json.dumps(out), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

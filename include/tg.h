@@ -1,0 +1,149 @@
+/* tg.h -- C ABI of the GB300 library for the operator-split multispecies glioblastoma step.
+ *
+ * Model: Subramanian, Gholami, Biros, "Simulation of glioblastoma growth using a 3D
+ * multispecies tumor model with mass effect" (arXiv:1810.05370).  Section 2 states the PDEs
+ * (Eq. e:gog for the species, Eq. e:screening / e:lame / e:forcingfunction for the mass
+ * effect, Eq. e:edema for the edema); Section 3 states the operator split that one call of
+ * tg_step advances by dt:
+ *   S0  diffusion faces and proliferation field from the step's start (Eq. e:diffusion_tensor,
+ *       e:reaction_op);
+ *   S1  semi-Lagrangian transport of p, i, n, g, w (conservative form) and f along v
+ *       (Section 3, RK2 characteristics, cubic interpolation);
+ *   S2  Crank-Nicolson diffusion of i, o and edema l, solved by Jacobi-preconditioned CG; the
+ *       increment of i is taken from g and w in proportion g/(g+w);
+ *   S3  reaction of p, i, n, g, w (Eq. e:p - e:w: logistic growth, go-or-grow switching,
+ *       hypoxic death);  S4 oxygen reaction (Eq. e:ox);  S5 edema reaction (Eq. e:edema);
+ *   S6  screened elasticity (eta I - L_h) u = -b (Eq. e:screening with Eq. e:lame and
+ *       e:forcingfunction), Jacobi-preconditioned CG;
+ *   S7  v = (u^{n+1} - u^n) / dt.
+ * Spatial operators are second-order finite differences on a periodic box (7-point
+ * variable-coefficient diffusion, 19-point variable-coefficient Navier-Lame); the paper's
+ * pseudo-spectral discretisation and spectral preconditioners are not used.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are FP64, C-contiguous, indexed [z][y][x] (x fastest), n[0]*n[1]*n[2] elements,
+ *    in DEVICE memory on the current CUDA device, and at least 16-byte aligned.
+ *  - The library never allocates device memory.  The caller owns the state arrays and one
+ *    workspace of tg_workspace_bytes() bytes; both are borrowed until tg_free.
+ *  - All GPU work goes to the stream given to tg_init (a cudaStream_t, NULL = legacy
+ *    default stream).  Calls return after the work they queued has finished (the solvers
+ *    read their convergence flags back), so buffers may be reused on return.
+ *  - Errors are returned as tg_status; nothing is printed and no global state is kept.
+ *    After any error other than TG_ERR_ARG the context refuses further work with
+ *    TG_ERR_STATE (the state arrays are then unspecified) until it is freed.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef TG_H
+#define TG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tg_ctx tg_ctx;
+
+typedef enum {
+  TG_OK = 0,
+  TG_ERR_ARG = 1,        /* invalid argument (null pointer, bad grid, dt <= 0, ...)            */
+  TG_ERR_CUDA = 2,       /* a CUDA runtime call or kernel launch failed                       */
+  TG_ERR_NOCONV = 3,     /* a CG solve reached its iteration limit                            */
+  TG_ERR_NONFINITE = 4,  /* a residual norm became NaN or Inf                                 */
+  TG_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up                                */
+  TG_ERR_STATE = 6,      /* the context is unusable after an earlier error                   */
+  TG_ERR_WORKSPACE = 7   /* workspace missing, too small or misaligned                        */
+} tg_status;
+
+typedef enum {
+  TG_FP64 = 0,   /* every operation in FP64                                                   */
+  TG_MIXED = 1   /* FP32 stencils and interpolation, FP64 reductions and outer refinement    */
+} tg_precision;
+
+/* Periodic box [0, L[0]) x [0, L[1]) x [0, L[2]) with n[d] nodes per axis, spacing
+ * h_d = L[d] / n[d] (Section 3 uses a uniform grid on a fictitious box).  n[d] >= 4. */
+typedef struct {
+  int32_t n[3];
+  double L[3];
+} tg_grid;
+
+/* Model parameters, Table t:setup.  Per-species arrays use the order
+ * (tumor = p + i + n, gray matter g, white matter w, CSF f, background bg). */
+typedef struct {
+  double k_g, k_w, k_f, k_scale;   /* K = k_scale (k_g g + k_w w + k_f f)   Eq. e:diffusion_tensor */
+  double rho_g, rho_w, rho_i_frac; /* rho = rho_g g + rho_w w; invasive rho_i = rho_i_frac rho    */
+  double alpha0, beta0, gamma, sigma_b; /* Eq. e:alpha, e:beta, e:death                            */
+  double o_hyp, o_inv, o_heal;     /* hypoxia / invasion thresholds, healthy oxygen level        */
+  double delta_s, delta_p;         /* oxygen supply and consumption, Eq. e:ox                    */
+  double eps_H;                    /* smoothed Heaviside H(x) = (1 + tanh(x / eps_H)) / 2          */
+  double E[5], nu[5], eta[5];      /* Young's modulus, Poisson ratio, screening, Eq. e:lame       */
+  double E_scale, zeta;            /* E multiplier; force b = zeta tanh(p+n) grad(p+n)           */
+  double delta_e, delta_half, delta_l; /* edema source, half-saturation, drainage, Eq. e:edema     */
+  double rtol_diff, rtol_elas;     /* CG stops at |r|_2 <= rtol |rhs|_2                          */
+  int32_t maxit_diff, maxit_elas;  /* CG iteration limits (TG_ERR_NOCONV beyond)                */
+} tg_params;
+
+/* Device pointers to the caller's state (species and materials of Section 2.3; u is the
+ * displacement of Eq. e:screening, v = u_t its velocity).  bg is read only. */
+typedef struct {
+  double *p, *i, *n, *g, *w, *f, *o, *l, *bg;
+  double *u[3], *v[3];
+} tg_state;
+
+/* Solver statistics of one call.  it_* of the last step; *_total summed over the call. */
+typedef struct {
+  int64_t steps;
+  int32_t it_diff[3];        /* CG iterations of the i, o, l solves                           */
+  int32_t it_elas;           /* CG iterations of the elasticity solve (inner, summed, in MIXED) */
+  int32_t it_elas_outer;     /* refinement sweeps of the elasticity solve (1 in FP64)        */
+  double relres_diff[3];     /* final |r| / |rhs|                                            */
+  double relres_elas;
+  int64_t it_diff_total;
+  int64_t it_elas_total;
+  int64_t launches;          /* CUDA kernels this call queued                                */
+  double t_elas_matvec_ms;   /* with timing on: summed duration of the elasticity operator   */
+  int64_t n_elas_matvec;     /*   kernel over the launches that did work, and their count    */
+} tg_stats;
+
+/* Bytes of workspace tg_init needs for this grid and precision (0 on invalid arguments). */
+size_t tg_workspace_bytes(const tg_grid* grid, tg_precision prec);
+
+/* Create a context over the caller's state and workspace and compute the initial
+ * displacement u^0 from the initial species (Eq. e:gog_elasticity at t = 0, CG from u = 0),
+ * setting v^0 = 0.  With flags & TG_INIT_KEEP_UV the given u, v are kept (resuming from a
+ * saved state).  stats may be NULL.  On success *out receives the context. */
+#define TG_INIT_KEEP_UV 1u
+tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision prec,
+                  const tg_state* state, void* workspace, size_t workspace_bytes,
+                  void* cuda_stream, uint32_t flags, tg_ctx** out, tg_stats* stats);
+
+/* Advance the state by nsteps steps of size dt (Section 3 multispecies split S0-S7).
+ * tape must be NULL (reserved).  stats may be NULL. */
+tg_status tg_step(tg_ctx* ctx, double dt, int32_t nsteps, void* tape, tg_stats* stats);
+
+/* Solve (eta I - L_h) u = rhs with Jacobi-preconditioned CG, coefficients from the current
+ * state (Eq. e:lame), starting from the given u.  rhs == NULL means rhs = -b with the force
+ * b of Eq. e:forcingfunction from the current state (the solve S6 performs); otherwise rhs
+ * holds three device arrays.  u holds three device arrays, overwritten with the solution. */
+tg_status tg_solve_elasticity(tg_ctx* ctx, double* const rhs[3], double* u[3], tg_stats* stats);
+
+/* Replace the parameters used by later calls (e.g. a parameter sweep on one context). */
+tg_status tg_set_params(tg_ctx* ctx, const tg_params* params);
+
+/* Optional kernel timing for profiling: with enable != 0 every launch of the elasticity
+ * operator kernel (the innermost loop of S6) is bracketed by CUDA events on the context's
+ * stream and stats report the summed device time of the launches that did work.  The events
+ * are created on first use (host-side objects, no device allocation). */
+tg_status tg_set_timing(tg_ctx* ctx, int32_t enable);
+
+/* Release the context (host memory only; the caller's buffers are untouched). */
+void tg_free(tg_ctx* ctx);
+
+/* Static description of a status code. */
+const char* tg_error_string(tg_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -251,6 +251,12 @@ class Oracle:
                               self._ptr(v[1]), self._ptr(v[2]), qin, qout)
         return outs
 
+    def heaviside(self, params, x):
+        self.lib.or_heaviside.restype = self.R
+        arg = self._r(x) if self.cs else C.c_double(float(np.real(x)))
+        r = self.lib.or_heaviside(C.byref(self.params(params)), arg)
+        return complex(r.re, r.im) if self.cs else float(r)
+
     def react(self, n, params, dt, rho, st, L=None):
         """In place on st['p','i','n','g','w','o','l']."""
         self.lib.or_react(C.byref(self.grid(n, L)), C.byref(self.params(params)), C.c_double(dt),

@@ -16,7 +16,7 @@
  *    both are zero), node K clamped at zero;
  *  - the unqualified "D" in the g, w equations (Eq. e:gm_wm, e:w) is D i: the Crank-Nicolson
  *    increment of i is taken from g and w in proportion g/(g+w) (zero where g+w <= 0);
- *  - smoothed Heaviside H(x) = (1 + tanh(x / eps_H)) / 2;
+ *  - smoothed Heaviside H(x) = (1 + tanh(x / eps_H)) / 2 (evaluated as a logistic);
  *  - "explicit" reaction sub-steps are one Heun (RK2) step each; p, i, n, g, w use the
  *    post-diffusion oxygen and the proliferation field of the step's start;
  *  - diffusion coefficients and rho come from the step's start; Lame, eta and the force
@@ -34,10 +34,12 @@
 #ifdef OR_COMPLEX
 #define RE(x) creal(x)
 #define TANH(x) ctanh(x)
+#define EXP(x) cexp(x)
 #define SQRT_RE(x) sqrt(creal(x))
 #else
 #define RE(x) (x)
 #define TANH(x) tanh(x)
+#define EXP(x) exp(x)
 #define SQRT_RE(x) sqrt(x)
 #endif
 
@@ -422,7 +424,10 @@ void or_sl_advect(const or_grid* G, double dt, const real_t* vx, const real_t* v
 
 /* ---------------------------------------------------------------- reactions */
 
-static real_t heaviside(const or_params* P, real_t x) { return 0.5 * (1.0 + TANH(x / P->eps_H)); }
+/* smoothed Heaviside (1 + tanh(x / eps_H)) / 2, evaluated in the equal logistic form
+ * 1 / (1 + exp(-2 x / eps_H)), which keeps full relative accuracy for x << 0 */
+real_t or_heaviside(const or_params* P, real_t x) { return 1.0 / (1.0 + EXP(-2.0 * x / P->eps_H)); }
+static real_t heaviside(const or_params* P, real_t x) { return or_heaviside(P, x); }
 
 /* oxygen factor of Eq. e:gog_reac_op / e:gog_reac_inv_op, o_mit = (o_hyp + o_inv) / 2 */
 static real_t mitosis_factor(const or_params* P, real_t o) {

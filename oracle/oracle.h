@@ -83,6 +83,7 @@ void or_divergence(const or_grid*, const real_t* vx, const real_t* vy, const rea
                    real_t* div);
 void or_sl_advect(const or_grid*, double dt, const real_t* vx, const real_t* vy, const real_t* vz,
                   real_t* const* q_in, real_t* const* q_out);
+real_t or_heaviside(const or_params*, real_t x);
 void or_react(const or_grid*, const or_params*, double dt, const real_t* rho, real_t* p,
               real_t* i, real_t* n, real_t* g, real_t* w, real_t* o, real_t* l);
 #endif

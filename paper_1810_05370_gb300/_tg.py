@@ -1,0 +1,181 @@
+"""ctypes binding of libtg.so (the C ABI declared in include/tg.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  torch supplies device memory (state arrays, workspace) and the CUDA stream.  There
+is no CPU fallback: if libtg.so cannot be loaded the import fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libtg.so")
+
+TG_OK, TG_ERR_ARG, TG_ERR_CUDA, TG_ERR_NOCONV, TG_ERR_NONFINITE, TG_ERR_TIMEOUT, \
+    TG_ERR_STATE, TG_ERR_WORKSPACE = range(8)
+TG_FP64, TG_MIXED = 0, 1
+TG_INIT_KEEP_UV = 1
+
+STATUS_NAMES = {
+    TG_OK: "TG_OK", TG_ERR_ARG: "TG_ERR_ARG", TG_ERR_CUDA: "TG_ERR_CUDA",
+    TG_ERR_NOCONV: "TG_ERR_NOCONV", TG_ERR_NONFINITE: "TG_ERR_NONFINITE",
+    TG_ERR_TIMEOUT: "TG_ERR_TIMEOUT", TG_ERR_STATE: "TG_ERR_STATE",
+    TG_ERR_WORKSPACE: "TG_ERR_WORKSPACE",
+}
+
+PARAM_SCALARS = ("k_g", "k_w", "k_f", "k_scale", "rho_g", "rho_w", "rho_i_frac",
+                 "alpha0", "beta0", "gamma", "sigma_b", "o_hyp", "o_inv", "o_heal",
+                 "delta_s", "delta_p", "eps_H")
+SPECIES = ("p", "i", "n", "g", "w", "f", "o", "l", "bg")
+
+
+class tg_grid(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("L", C.c_double * 3)]
+
+
+class tg_params(C.Structure):
+    _fields_ = [(name, C.c_double) for name in PARAM_SCALARS] + [
+        ("E", C.c_double * 5), ("nu", C.c_double * 5), ("eta", C.c_double * 5),
+        ("E_scale", C.c_double), ("zeta", C.c_double),
+        ("delta_e", C.c_double), ("delta_half", C.c_double), ("delta_l", C.c_double),
+        ("rtol_diff", C.c_double), ("rtol_elas", C.c_double),
+        ("maxit_diff", C.c_int32), ("maxit_elas", C.c_int32)]
+
+
+class tg_state(C.Structure):
+    _fields_ = [(name, C.c_void_p) for name in SPECIES] + [
+        ("u", C.c_void_p * 3), ("v", C.c_void_p * 3)]
+
+
+class tg_stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("it_diff", C.c_int32 * 3), ("it_elas", C.c_int32),
+                ("it_elas_outer", C.c_int32), ("relres_diff", C.c_double * 3),
+                ("relres_elas", C.c_double), ("it_diff_total", C.c_int64),
+                ("it_elas_total", C.c_int64), ("launches", C.c_int64),
+                ("t_elas_matvec_ms", C.c_double), ("n_elas_matvec", C.c_int64)]
+
+
+class TGError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)} ({error_string(status)})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    sig = {
+        "tg_workspace_bytes": (C.c_size_t, [P(tg_grid), C.c_int]),
+        "tg_init": (C.c_int, [P(tg_grid), P(tg_params), C.c_int, P(tg_state), C.c_void_p,
+                              C.c_size_t, C.c_void_p, C.c_uint32, P(C.c_void_p), P(tg_stats)]),
+        "tg_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, P(tg_stats)]),
+        "tg_solve_elasticity": (C.c_int, [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(tg_stats)]),
+        "tg_set_params": (C.c_int, [C.c_void_p, P(tg_params)]),
+        "tg_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+        "tg_free": (None, [C.c_void_p]),
+        "tg_error_string": (C.c_char_p, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def error_string(status: int) -> str:
+    return lib.tg_error_string(int(status)).decode()
+
+
+# ----------------------------------------------------------------------------- marshalling
+
+def make_grid(n, L=None) -> tg_grid:
+    import math
+    if isinstance(n, int):
+        n = (n, n, n)
+    L = (2 * math.pi,) * 3 if L is None else L
+    g = tg_grid()
+    for d in range(3):
+        g.n[d] = int(n[d])
+        g.L[d] = float(L[d])
+    return g
+
+
+def make_params(d: dict) -> tg_params:
+    p = tg_params()
+    for name in PARAM_SCALARS + ("E_scale", "zeta", "delta_e", "delta_half", "delta_l",
+                                 "rtol_diff", "rtol_elas"):
+        setattr(p, name, float(d[name]))
+    for name in ("E", "nu", "eta"):
+        arr = getattr(p, name)
+        for s in range(5):
+            arr[s] = float(d[name][s])
+    p.maxit_diff = int(d["maxit_diff"])
+    p.maxit_elas = int(d["maxit_elas"])
+    return p
+
+
+def stats_dict(s: tg_stats) -> dict:
+    return {"steps": int(s.steps), "it_diff": list(s.it_diff), "it_elas": int(s.it_elas),
+            "it_elas_outer": int(s.it_elas_outer), "relres_diff": list(s.relres_diff),
+            "relres_elas": float(s.relres_elas), "it_diff_total": int(s.it_diff_total),
+            "it_elas_total": int(s.it_elas_total), "launches": int(s.launches),
+            "t_elas_matvec_ms": float(s.t_elas_matvec_ms), "n_elas_matvec": int(s.n_elas_matvec)}
+
+
+# ----------------------------------------------------------------------------- same-name calls
+
+def tg_workspace_bytes(grid: tg_grid, prec: int) -> int:
+    return int(lib.tg_workspace_bytes(C.byref(grid), int(prec)))
+
+
+def tg_init(grid, params, prec, state, workspace_ptr, workspace_bytes, stream_ptr, flags=0):
+    ctx = C.c_void_p()
+    stats = tg_stats()
+    rc = lib.tg_init(C.byref(grid), C.byref(params), int(prec), C.byref(state),
+                     C.c_void_p(workspace_ptr), C.c_size_t(workspace_bytes),
+                     C.c_void_p(stream_ptr), C.c_uint32(flags), C.byref(ctx), C.byref(stats))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_init")
+    return ctx, stats_dict(stats)
+
+
+def tg_step(ctx, dt, nsteps=1):
+    stats = tg_stats()
+    rc = lib.tg_step(ctx, C.c_double(dt), C.c_int32(nsteps), None, C.byref(stats))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_step")
+    return stats_dict(stats)
+
+
+def tg_solve_elasticity(ctx, rhs_ptrs, u_ptrs):
+    stats = tg_stats()
+    rhs = (C.c_void_p * 3)(*rhs_ptrs) if rhs_ptrs is not None else None
+    u = (C.c_void_p * 3)(*u_ptrs)
+    rc = lib.tg_solve_elasticity(ctx, rhs, u, C.byref(stats))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_solve_elasticity")
+    return stats_dict(stats)
+
+
+def tg_set_params(ctx, params: tg_params):
+    rc = lib.tg_set_params(ctx, C.byref(params))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_set_params")
+
+
+def tg_set_timing(ctx, enable: bool):
+    rc = lib.tg_set_timing(ctx, 1 if enable else 0)
+    if rc != TG_OK:
+        raise TGError(rc, "tg_set_timing")
+
+
+def tg_free(ctx):
+    lib.tg_free(ctx)

@@ -1,0 +1,551 @@
+// tg_api.cu -- the C ABI of tg.h: argument checks, workspace layout, and the host-side
+// sequencing of the operator-split step (Section 3) over the kernels of this directory.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "tg_internal.cuh"
+
+using namespace tg;
+
+namespace {
+
+// ---------------------------------------------------------------------------- workspace
+// Every array holds one FP64 value per voxel and starts on a 256-byte boundary.
+enum Arr {
+  A_KF0, A_KF1, A_KF2, A_DSUM_D, A_DINV_D, A_RHO,
+  A_CR0, A_CR1, A_CR2, A_CP0, A_CP1, A_CP2, A_CQ0, A_CQ1, A_CQ2,
+  A_IDAG, A_DIV, A_SL0, A_SL1, A_SL2, A_SL3, A_SL4, A_SL5,
+  A_MU, A_LAM, A_ETA, A_F0, A_F1, A_F2, A_G0, A_G1, A_G2,
+  A_DSUM_E0, A_DSUM_E1, A_DSUM_E2, A_DINV_E0, A_DINV_E1, A_DINV_E2,
+  A_B0, A_B1, A_B2, A_DU0, A_DU1, A_DU2, A_ER0, A_ER1, A_ER2, A_EP0, A_EP1, A_EP2,
+  A_EQ0, A_EQ1, A_EQ2,
+  A_COUNT
+};
+
+constexpr size_t ALIGN = 256;
+constexpr int MAX_NV = 9;    // largest number of values reduced by one kernel
+constexpr int N_SCAL = 4;    // 3 diffusion solves + 1 elasticity solve
+
+size_t round_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+bool grid_ok(const tg_grid* g) {
+  if (!g) return false;
+  for (int d = 0; d < 3; ++d) {
+    if (g->n[d] < 4 || g->n[d] > (1 << 20)) return false;
+    if (!(g->L[d] > 0.0) || !isfinite(g->L[d])) return false;
+  }
+  return true;
+}
+
+Geo make_geo(const tg_grid* g, int sms) {
+  Geo G;
+  G.nx = g->n[0];
+  G.ny = g->n[1];
+  G.nz = g->n[2];
+  G.nxy = (long long)G.nx * G.ny;
+  G.nvox = G.nxy * G.nz;
+  for (int d = 0; d < 3; ++d) {
+    G.h[d] = g->L[d] / g->n[d];
+    G.ih2[d] = 1.0 / (G.h[d] * G.h[d]);
+    G.inv2h[d] = 1.0 / (2.0 * G.h[d]);
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) G.s_cross[a][d] = 1.0 / (4.0 * G.h[a] * G.h[d]);
+  const long long gx = (G.nx + BX - 1) / BX, gy = (G.ny + BY - 1) / BY;
+  // z chunk so that a launch has about 16 blocks per SM
+  const long long target = 16LL * std::max(sms, 1);
+  long long zc = (gx * gy * G.nz + target - 1) / target;
+  zc = std::max(1LL, std::min(zc, (long long)G.nz));
+  G.zc = (int)zc;
+  const long long gz = (G.nz + zc - 1) / zc;
+  G.grid = dim3((unsigned)gx, (unsigned)gy, (unsigned)gz);
+  G.nblocks = (int)(gx * gy * gz);
+  return G;
+}
+
+struct Layout {
+  size_t arr[A_COUNT];
+  size_t partial, counter, scal, total;
+};
+
+Layout layout(const Geo& G) {
+  Layout L;
+  size_t off = 0;
+  const size_t abytes = round_up((size_t)G.nvox * sizeof(double));
+  for (int a = 0; a < A_COUNT; ++a) {
+    L.arr[a] = off;
+    off += abytes;
+  }
+  L.partial = off;
+  off += round_up((size_t)G.nblocks * MAX_NV * sizeof(double));
+  L.counter = off;
+  off += ALIGN;
+  L.scal = off;
+  off += round_up(N_SCAL * sizeof(CgScal));
+  L.total = off;
+  return L;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+  return sms;
+}
+
+bool params_ok(const tg_params* p) {
+  if (!p) return false;
+  if (!(p->eps_H > 0.0)) return false;
+  if (!(p->o_inv > 0.5 * (p->o_hyp + p->o_inv)) && !(p->o_inv < 0.5 * (p->o_hyp + p->o_inv)))
+    return false;  // o_inv == o_mit: the ramp of Eq. e:gog_reac_op is undefined
+  if (!(p->rtol_diff >= 0.0) || !(p->rtol_elas >= 0.0)) return false;
+  if (p->maxit_diff < 0 || p->maxit_elas < 0) return false;
+  for (int s = 0; s < 5; ++s) {
+    if (p->nu[s] == 0.5 || p->nu[s] == -1.0) return false;
+    if (!isfinite(p->E[s]) || !isfinite(p->nu[s]) || !isfinite(p->eta[s])) return false;
+  }
+  return true;
+}
+
+DevParams make_dev_params(const tg_params* p) {
+  DevParams d;
+  d.k_g = p->k_g;
+  d.k_w = p->k_w;
+  d.k_f = p->k_f;
+  d.k_scale = p->k_scale;
+  d.rho_g = p->rho_g;
+  d.rho_w = p->rho_w;
+  d.rho_i_frac = p->rho_i_frac;
+  d.alpha0 = p->alpha0;
+  d.beta0 = p->beta0;
+  d.gamma = p->gamma;
+  d.sigma_b = p->sigma_b;
+  d.o_hyp = p->o_hyp;
+  d.o_inv = p->o_inv;
+  d.o_heal = p->o_heal;
+  d.o_mit = 0.5 * (p->o_hyp + p->o_inv);
+  d.delta_s = p->delta_s;
+  d.delta_p = p->delta_p;
+  d.inv_eps_H = 1.0 / p->eps_H;
+  for (int s = 0; s < 5; ++s) {
+    const double E = p->E_scale * p->E[s], nu = p->nu[s];
+    d.cmu[s] = E / (2.0 * (1.0 + nu));
+    d.clam[s] = nu * E / ((1.0 - 2.0 * nu) * (1.0 + nu));
+    d.eta[s] = p->eta[s];
+  }
+  d.zeta = p->zeta;
+  d.delta_e = p->delta_e;
+  d.delta_half = p->delta_half;
+  d.delta_l = p->delta_l;
+  return d;
+}
+
+__global__ void k_cg_reset(CgScal* S, int count, double rtol, int maxit) {
+  const int t = threadIdx.x;
+  if (t < count) {
+    CgScal s = {};
+    s.rtol = rtol;
+    s.maxit = maxit;
+    s.status = CG_RUNNING;
+    S[t] = s;
+  }
+}
+
+}  // namespace
+
+struct tg_ctx {
+  Geo G;
+  Layout L;
+  tg_params prm;
+  DevParams dp;
+  tg_precision prec;
+  tg_state st;
+  cudaStream_t stream;
+  int device;
+  char* ws;
+  double* a[A_COUNT];
+  double* partial;
+  unsigned int* counter;
+  CgScal* scal;
+  int broken;
+  int prev_it_diff;
+  int prev_it_elas;
+  // profiling: launches queued, and optional event timing of the elasticity operator kernel
+  long long launches;
+  int timing;
+  std::vector<cudaEvent_t> ev;   // pairs (start, stop) per operator launch of one solve
+  double t_matvec_ms;
+  long long n_matvec;
+};
+
+namespace {
+
+tg_status fail(tg_ctx* X, tg_status s) {
+  if (X && s != TG_OK && s != TG_ERR_ARG) X->broken = 1;
+  return s;
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    if ((call) != cudaSuccess) {                  \
+      return fail(X, TG_ERR_CUDA);                \
+    }                                             \
+  } while (0)
+
+tg_status status_of(const CgScal& s) {
+  switch (s.status) {
+    case CG_CONVERGED:
+    case CG_ZERO_RHS: return TG_OK;
+    case CG_NONFINITE: return TG_ERR_NONFINITE;
+    case CG_MAXIT: return TG_ERR_NOCONV;
+    default: return TG_ERR_CUDA;
+  }
+}
+
+// Queue iterations in chunks and read the device-side flags back between chunks.  Kernels of
+// a finished solve return at once, so overshooting a chunk only costs empty launches.
+template <class IterFn>
+tg_status drive_cg(tg_ctx* X, IterFn iter, const CgScal* dev, int nsolves, int maxit, int prev,
+                   CgScal* host) {
+  int chunk = prev > 0 ? std::max(1, prev - prev / 8) : 4;
+  long long queued = 0;
+  for (;;) {
+    for (int c = 0; c < chunk; ++c) CK(iter((int)(queued + c)));
+    queued += chunk;
+    CK(cudaMemcpyAsync(host, dev, nsolves * sizeof(CgScal), cudaMemcpyDeviceToHost, X->stream));
+    CK(cudaStreamSynchronize(X->stream));
+    bool running = false;
+    for (int r = 0; r < nsolves; ++r) running |= host[r].status == CG_RUNNING;
+    if (!running) return TG_OK;
+    if (queued > (long long)maxit + 64) return fail(X, TG_ERR_CUDA);  // flags never settled
+    chunk = (queued == chunk) ? 2 : std::min(chunk * 2, 32);
+  }
+}
+
+// grow the event pool to hold `pairs` (start, stop) pairs; false if events cannot be created
+bool ensure_events(tg_ctx* X, int pairs) {
+  while ((int)X->ev.size() < 2 * pairs) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return false;
+    X->ev.push_back(e);
+  }
+  return true;
+}
+
+Cn3 cn_view(tg_ctx* X) {
+  Cn3 C;
+  double* xs[3] = {X->st.i, X->st.o, X->st.l};
+  for (int r = 0; r < 3; ++r) {
+    C.x[r] = xs[r];
+    C.r[r] = X->a[A_CR0 + r];
+    C.p[r] = X->a[A_CP0 + r];
+    C.q[r] = X->a[A_CQ0 + r];
+    C.Kf[r] = X->a[A_KF0 + r];
+  }
+  C.dsum = X->a[A_DSUM_D];
+  C.dinv = X->a[A_DINV_D];
+  C.S = X->scal;
+  C.partial = X->partial;
+  C.counter = X->counter;
+  return C;
+}
+
+Elas elas_view(tg_ctx* X, double* const u[3], double* const b[3]) {
+  Elas E;
+  E.mu = X->a[A_MU];
+  E.lam = X->a[A_LAM];
+  E.eta = X->a[A_ETA];
+  for (int d = 0; d < 3; ++d) {
+    E.F[d] = X->a[A_F0 + d];
+    E.G[d] = X->a[A_G0 + d];
+    E.dsum[d] = X->a[A_DSUM_E0 + d];
+    E.dinv[d] = X->a[A_DINV_E0 + d];
+    E.b[d] = b ? b[d] : X->a[A_B0 + d];
+    E.du[d] = X->a[A_DU0 + d];
+    E.r[d] = X->a[A_ER0 + d];
+    E.p[d] = X->a[A_EP0 + d];
+    E.q[d] = X->a[A_EQ0 + d];
+    E.u[d] = u[d];
+    E.v[d] = X->st.v[d];
+  }
+  E.S = X->scal + 3;
+  E.partial = X->partial;
+  E.counter = X->counter;
+  return E;
+}
+
+// S2: the three Crank-Nicolson solves (i, o, l) on the faces built by S0.
+tg_status cn_solve3(tg_ctx* X, tg_stats* stats) {
+  const Cn3 C = cn_view(X);
+  k_cg_reset<<<1, 32, 0, X->stream>>>(X->scal, 3, X->prm.rtol_diff, X->prm.maxit_diff);
+  CK(cudaGetLastError());
+  CK(launch_cn_init(X->G, C, X->stream));
+  X->launches += 2;
+  CgScal host[3];
+  tg_status s = drive_cg(X, [&](int) {
+    X->launches += 3;
+    return launch_cn_iter(X->G, C, X->stream);
+  }, X->scal, 3, X->prm.maxit_diff, X->prev_it_diff, host);
+  if (s != TG_OK) return s;
+  int itmax = 0;
+  for (int r = 0; r < 3; ++r) {
+    if (host[r].status == CG_ZERO_RHS)
+      CK(cudaMemsetAsync(C.x[r], 0, (size_t)X->G.nvox * sizeof(double), X->stream));
+    itmax = std::max(itmax, host[r].it);
+    if (stats) {
+      stats->it_diff[r] = host[r].it;
+      stats->relres_diff[r] = host[r].bb > 0.0 ? sqrt(host[r].rr / host[r].bb) : 0.0;
+      stats->it_diff_total += host[r].it;
+    }
+  }
+  X->prev_it_diff = itmax;
+  for (int r = 0; r < 3; ++r) {
+    tg_status e = status_of(host[r]);
+    if (e != TG_OK) return fail(X, e);
+  }
+  return TG_OK;
+}
+
+// S6 solve on coefficients already built: (eta I - L_h) u = rhs from the given u.
+tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool minus_b,
+                     double inv_dt, tg_stats* stats) {
+  const Elas E = elas_view(X, u, b_ext);
+  k_cg_reset<<<1, 32, 0, X->stream>>>(X->scal + 3, 1, X->prm.rtol_elas, X->prm.maxit_elas);
+  CK(cudaGetLastError());
+  CK(launch_elas_init(X->G, E, minus_b, X->stream));
+  X->launches += 2;
+  CgScal host[1];
+  int recorded = 0;
+  tg_status s = drive_cg(X, [&](int q) {
+    X->launches += 3;
+    const bool timed = X->timing && ensure_events(X, q + 1);
+    if (timed) {
+      cudaEventRecord(X->ev[2 * q], X->stream);
+      recorded = q + 1;
+    }
+    cudaError_t e = launch_elas_matvec(X->G, E, X->stream);
+    if (timed) cudaEventRecord(X->ev[2 * q + 1], X->stream);
+    if (e != cudaSuccess) return e;
+    return launch_elas_update(X->G, E, X->stream);
+  }, E.S, 1, X->prm.maxit_elas, X->prev_it_elas, host);
+  if (s != TG_OK) return s;
+  X->prev_it_elas = host[0].it;
+  // launches after convergence return at once: only the first `it` did the work
+  for (int q = 0; q < std::min(recorded, host[0].it); ++q) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, X->ev[2 * q], X->ev[2 * q + 1]) == cudaSuccess) {
+      X->t_matvec_ms += ms;
+      X->n_matvec += 1;
+    }
+  }
+  if (stats) {
+    stats->it_elas = host[0].it;
+    stats->it_elas_outer = 1;
+    stats->relres_elas = host[0].bb > 0.0 ? sqrt(host[0].rr / host[0].bb) : 0.0;
+    stats->it_elas_total += host[0].it;
+  }
+  tg_status e = status_of(host[0]);
+  if (e != TG_OK) return fail(X, e);
+  CK(launch_elas_finish(X->G, E, inv_dt, host[0].status == CG_ZERO_RHS, X->stream));
+  X->launches += 1;
+  CK(cudaStreamSynchronize(X->stream));
+  return TG_OK;
+}
+
+tg_status build_elas_coef(tg_ctx* X, bool force) {
+  const tg_state& S = X->st;
+  CK(launch_lame(X->G, X->dp, S.p, S.i, S.n, S.g, S.w, S.f, S.bg, X->a[A_MU], X->a[A_LAM],
+                 X->a[A_ETA], X->stream));
+  double* const u[3] = {S.u[0], S.u[1], S.u[2]};
+  const Elas E = elas_view(X, u, nullptr);
+  CK(launch_elas_coef(X->G, X->dp, E, S.p, S.n, force, X->stream));
+  X->launches += 2;
+  return TG_OK;
+}
+
+void reset_profile(tg_ctx* X) {
+  X->launches = 0;
+  X->t_matvec_ms = 0.0;
+  X->n_matvec = 0;
+}
+
+void fill_profile(tg_ctx* X, tg_stats* stats) {
+  stats->launches = X->launches;
+  stats->t_elas_matvec_ms = X->t_matvec_ms;
+  stats->n_elas_matvec = X->n_matvec;
+}
+
+// One step of the Section 3 split.
+tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
+  const Geo& G = X->G;
+  tg_state& S = X->st;
+  cudaStream_t s = X->stream;
+  const size_t bytes = (size_t)G.nvox * sizeof(double);
+  // S0: K faces, CN diagonal and rho from the step's start
+  double* const Kf[3] = {X->a[A_KF0], X->a[A_KF1], X->a[A_KF2]};
+  CK(launch_diff_coef(G, X->dp, dt, S.g, S.w, S.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
+                      X->a[A_RHO], s));
+  // S1: semi-Lagrangian transport with v^n
+  const double* const v[3] = {S.v[0], S.v[1], S.v[2]};
+  CK(launch_divergence(G, v, X->a[A_DIV], s));
+  const double* const qin[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
+  double* const qout[6] = {X->a[A_SL0], X->a[A_SL1], X->a[A_SL2],
+                           X->a[A_SL3], X->a[A_SL4], X->a[A_SL5]};
+  CK(launch_sl_advect(G, dt, v, X->a[A_DIV], qin, qout, s));
+  X->launches += 3;
+  double* const dst[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
+  for (int q = 0; q < 6; ++q) CK(cudaMemcpyAsync(dst[q], qout[q], bytes, cudaMemcpyDeviceToDevice, s));
+  // S2: Crank-Nicolson diffusion of i, o, l (i after transport kept for the g, w fix-up)
+  CK(cudaMemcpyAsync(X->a[A_IDAG], S.i, bytes, cudaMemcpyDeviceToDevice, s));
+  tg_status e = cn_solve3(X, stats);
+  if (e != TG_OK) return e;
+  // S2 fix-up and S3-S5 reactions
+  CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l, s));
+  X->launches += 1;
+  // S6-S7: elasticity from the post-reaction state, then v = du / dt
+  e = build_elas_coef(X, true);
+  if (e != TG_OK) return e;
+  return elas_solve(X, S.u, nullptr, true, 1.0 / dt, stats);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tg_workspace_bytes(const tg_grid* grid, tg_precision prec) {
+  if (!grid_ok(grid) || (prec != TG_FP64 && prec != TG_MIXED)) return 0;
+  if (prec != TG_FP64) return 0;
+  return layout(make_geo(grid, sm_count())).total;
+}
+
+tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision prec,
+                  const tg_state* state, void* workspace, size_t workspace_bytes,
+                  void* cuda_stream, uint32_t flags, tg_ctx** out, tg_stats* stats) {
+  if (out) *out = nullptr;
+  if (!out || !grid_ok(grid) || !params_ok(params) || !state) return TG_ERR_ARG;
+  if (prec != TG_FP64) return TG_ERR_ARG;
+  const double* must[] = {state->p, state->i, state->n, state->g, state->w, state->f, state->o,
+                          state->l, state->bg, state->u[0], state->u[1], state->u[2],
+                          state->v[0], state->v[1], state->v[2]};
+  for (const double* q : must)
+    if (!q || ((uintptr_t)q & 15u)) return TG_ERR_ARG;
+  const Geo G = make_geo(grid, sm_count());
+  const Layout L = layout(G);
+  if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < L.total)
+    return TG_ERR_WORKSPACE;
+  tg_ctx* X = new (std::nothrow) tg_ctx();
+  if (!X) return TG_ERR_CUDA;
+  X->G = G;
+  X->L = L;
+  X->prm = *params;
+  X->dp = make_dev_params(params);
+  X->prec = prec;
+  X->st = *state;
+  X->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&X->device);
+  X->ws = (char*)workspace;
+  for (int a = 0; a < A_COUNT; ++a) X->a[a] = (double*)(X->ws + L.arr[a]);
+  X->partial = (double*)(X->ws + L.partial);
+  X->counter = (unsigned int*)(X->ws + L.counter);
+  X->scal = (CgScal*)(X->ws + L.scal);
+  if (cudaMemsetAsync(X->counter, 0, ALIGN, X->stream) != cudaSuccess) {
+    tg_free(X);
+    return TG_ERR_CUDA;
+  }
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!(flags & TG_INIT_KEEP_UV)) {
+    const size_t bytes = (size_t)G.nvox * sizeof(double);
+    tg_status e = TG_OK;
+    for (int d = 0; d < 3 && e == TG_OK; ++d) {
+      if (cudaMemsetAsync(X->st.u[d], 0, bytes, X->stream) != cudaSuccess ||
+          cudaMemsetAsync(X->st.v[d], 0, bytes, X->stream) != cudaSuccess)
+        e = TG_ERR_CUDA;
+    }
+    if (e == TG_OK) e = build_elas_coef(X, true);
+    if (e == TG_OK) e = elas_solve(X, X->st.u, nullptr, true, 0.0, stats);
+    if (e != TG_OK) {
+      tg_free(X);
+      return e;
+    }
+  }
+  if (cudaStreamSynchronize(X->stream) != cudaSuccess) {
+    tg_free(X);
+    return TG_ERR_CUDA;
+  }
+  if (stats) fill_profile(X, stats);
+  *out = X;
+  return TG_OK;
+}
+
+tg_status tg_step(tg_ctx* X, double dt, int32_t nsteps, void* tape, tg_stats* stats) {
+  if (!X) return TG_ERR_ARG;
+  if (X->broken) return TG_ERR_STATE;
+  if (!(dt > 0.0) || !isfinite(dt) || nsteps < 0 || tape != nullptr) return TG_ERR_ARG;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  reset_profile(X);
+  CK(cudaSetDevice(X->device));
+  for (int32_t s = 0; s < nsteps; ++s) {
+    tg_status e = do_step(X, dt, stats);
+    if (e != TG_OK) return fail(X, e);
+    if (stats) stats->steps += 1;
+  }
+  CK(cudaStreamSynchronize(X->stream));
+  if (stats) fill_profile(X, stats);
+  return TG_OK;
+}
+
+tg_status tg_solve_elasticity(tg_ctx* X, double* const rhs[3], double* u[3], tg_stats* stats) {
+  if (!X || !u || !u[0] || !u[1] || !u[2]) return TG_ERR_ARG;
+  if (rhs && (!rhs[0] || !rhs[1] || !rhs[2])) return TG_ERR_ARG;
+  if (X->broken) return TG_ERR_STATE;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  reset_profile(X);
+  CK(cudaSetDevice(X->device));
+  tg_status e = build_elas_coef(X, rhs == nullptr);
+  if (e != TG_OK) return fail(X, e);
+  double* const uu[3] = {u[0], u[1], u[2]};
+  e = elas_solve(X, uu, rhs, rhs == nullptr, 0.0, stats);
+  if (e == TG_OK && stats) fill_profile(X, stats);
+  return e;
+}
+
+tg_status tg_set_params(tg_ctx* X, const tg_params* params) {
+  if (!X || !params_ok(params)) return TG_ERR_ARG;
+  if (X->broken) return TG_ERR_STATE;
+  X->prm = *params;
+  X->dp = make_dev_params(params);
+  return TG_OK;
+}
+
+tg_status tg_set_timing(tg_ctx* X, int32_t enable) {
+  if (!X) return TG_ERR_ARG;
+  X->timing = enable != 0;
+  return TG_OK;
+}
+
+void tg_free(tg_ctx* X) {
+  if (!X) return;
+  for (cudaEvent_t e : X->ev) cudaEventDestroy(e);
+  delete X;
+}
+
+const char* tg_error_string(tg_status s) {
+  switch (s) {
+    case TG_OK: return "success";
+    case TG_ERR_ARG: return "invalid argument";
+    case TG_ERR_CUDA: return "CUDA error";
+    case TG_ERR_NOCONV: return "CG did not converge within its iteration limit";
+    case TG_ERR_NONFINITE: return "non-finite residual";
+    case TG_ERR_TIMEOUT: return "device-side wait timed out";
+    case TG_ERR_STATE: return "context unusable after an earlier error";
+    case TG_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,242 @@
+// tg_diffusion.cu -- S0 coefficients and the Crank-Nicolson diffusion solves (S2).
+//
+// Section 3: (1 - dt/2 D) c^{+} = (1 + dt/2 D) c, solved by CG, for c in {i, o, l}, with
+// D c = div(K grad c), K = k_scale (k_g g + k_w w + k_f f) (Eq. e:diffusion_op,
+// e:diffusion_tensor).  Discretely, with face coefficients a_d = dt/(2 h_d^2) K_{j+1/2 e_d}
+// (harmonic mean of the two nodes, zero when both vanish),
+//   (A c)_j = c_j + sum_d [ a_d,j (c_j - c_{j+e_d}) + a_d,j-e_d (c_j - c_{j-e_d}) ].
+// The three right-hand sides share the coefficient reads: every kernel below streams the
+// six face values of a node once and applies them to all active solves.
+#include "tg_internal.cuh"
+
+namespace tg {
+namespace {
+
+__device__ __forceinline__ double node_K(const DevParams& P, double g, double w, double f) {
+  double k = P.k_scale * (P.k_g * g + P.k_w * w + P.k_f * f);
+  return k > 0.0 ? k : 0.0;
+}
+
+__device__ __forceinline__ double harmonic(double a, double b) {
+  return (a + b) > 0.0 ? 2.0 * a * b / (a + b) : 0.0;
+}
+
+__global__ void __launch_bounds__(NT) k_diff_coef(Geo G, DevParams P, double half_dt,
+                                                  const double* __restrict__ g,
+                                                  const double* __restrict__ w,
+                                                  const double* __restrict__ f, double* Kfx,
+                                                  double* Kfy, double* Kfz, double* dsum,
+                                                  double* dinv, double* rho) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  const double sx = half_dt * G.ih2[0], sy = half_dt * G.ih2[1], sz = half_dt * G.ih2[2];
+  for (int k = k0; k < k1; ++k) {
+    const Nbr nb = make_nbr(G, i, j, k);
+    auto K = [&](long long e) { return node_K(P, g[e], w[e], f[e]); };
+    const long long c = nb.at(0, 0, 0);
+    const double kc = K(c);
+    const double fxp = harmonic(kc, K(nb.at(1, 0, 0))), fxm = harmonic(K(nb.at(-1, 0, 0)), kc);
+    const double fyp = harmonic(kc, K(nb.at(0, 1, 0))), fym = harmonic(K(nb.at(0, -1, 0)), kc);
+    const double fzp = harmonic(kc, K(nb.at(0, 0, 1))), fzm = harmonic(K(nb.at(0, 0, -1)), kc);
+    Kfx[c] = sx * fxp;
+    Kfy[c] = sy * fyp;
+    Kfz[c] = sz * fzp;
+    const double d = 1.0 + sx * (fxp + fxm) + sy * (fyp + fym) + sz * (fzp + fzm);
+    dsum[c] = d;
+    dinv[c] = 1.0 / d;
+    rho[c] = P.rho_g * g[c] + P.rho_w * w[c];
+  }
+}
+
+struct Faces {
+  double xp, xm, yp, ym, zp, zm;
+};
+
+__device__ __forceinline__ Faces load_faces(const Cn3& C, const Nbr& nb, long long c) {
+  Faces F;
+  F.xp = C.Kf[0][c];
+  F.xm = C.Kf[0][nb.at(-1, 0, 0)];
+  F.yp = C.Kf[1][c];
+  F.ym = C.Kf[1][nb.at(0, -1, 0)];
+  F.zp = C.Kf[2][c];
+  F.zm = C.Kf[2][nb.at(0, 0, -1)];
+  return F;
+}
+
+// r0 = rhs - A x0 with x0 = c and rhs = c + s, s = dt/2 D_h c, so r0 = 2 s.
+__global__ void __launch_bounds__(NT) k_cn_init(Geo G, Cn3 C) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const bool on = (i < G.nx) && (j < G.ny);
+  double acc[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) acc[q] = 0.0;
+  if (on) {
+    const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+    for (int k = k0; k < k1; ++k) {
+      const Nbr nb = make_nbr(G, i, j, k);
+      const long long c = nb.at(0, 0, 0);
+      const Faces F = load_faces(C, nb, c);
+      const double di = C.dinv[c];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const double* x = C.x[r];
+        const double xc = x[c];
+        const double s = F.xp * (x[nb.at(1, 0, 0)] - xc) - F.xm * (xc - x[nb.at(-1, 0, 0)]) +
+                         F.yp * (x[nb.at(0, 1, 0)] - xc) - F.ym * (xc - x[nb.at(0, -1, 0)]) +
+                         F.zp * (x[nb.at(0, 0, 1)] - xc) - F.zm * (xc - x[nb.at(0, 0, -1)]);
+        const double rhs = xc + s;
+        const double res = 2.0 * s;
+        const double z = di * res;
+        C.r[r][c] = res;
+        C.p[r][c] = z;
+        acc[3 * r + 0] += rhs * rhs;
+        acc[3 * r + 1] += res * res;
+        acc[3 * r + 2] += res * z;
+      }
+    }
+  }
+  double out[9];
+  if (reduce_last_block<9>(acc, C.partial, C.counter, out) && threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) cg_after_init(C.S[r], out[3 * r], out[3 * r + 1], out[3 * r + 2]);
+  }
+}
+
+// q = A p and <p, q> for every running solve; then alpha = rz / <p, q>.
+__global__ void __launch_bounds__(NT) k_cn_matvec(Geo G, Cn3 C) {
+  bool act[3];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    act[r] = C.S[r].status == CG_RUNNING;
+    any |= act[r];
+  }
+  if (!any) return;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const bool on = (i < G.nx) && (j < G.ny);
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (on) {
+    const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+    for (int k = k0; k < k1; ++k) {
+      const Nbr nb = make_nbr(G, i, j, k);
+      const long long c = nb.at(0, 0, 0);
+      const Faces F = load_faces(C, nb, c);
+      const double d = C.dsum[c];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        if (!act[r]) continue;
+        const double* p = C.p[r];
+        const double pc = p[c];
+        const double q = d * pc - (F.xp * p[nb.at(1, 0, 0)] + F.xm * p[nb.at(-1, 0, 0)] +
+                                   F.yp * p[nb.at(0, 1, 0)] + F.ym * p[nb.at(0, -1, 0)] +
+                                   F.zp * p[nb.at(0, 0, 1)] + F.zm * p[nb.at(0, 0, -1)]);
+        C.q[r][c] = q;
+        acc[r] += pc * q;
+      }
+    }
+  }
+  double out[3];
+  if (reduce_last_block<3>(acc, C.partial, C.counter, out) && threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      if (act[r]) {
+        C.S[r].pq = out[r];
+        C.S[r].alpha = C.S[r].rz / out[r];
+      }
+  }
+}
+
+// x += alpha p, r -= alpha q, then <r, D^{-1} r> and <r, r> decide convergence / beta.
+__global__ void __launch_bounds__(NT) k_cn_update(Geo G, Cn3 C) {
+  bool act[3];
+  double alpha[3];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    act[r] = C.S[r].status == CG_RUNNING;
+    alpha[r] = C.S[r].alpha;
+    any |= act[r];
+  }
+  if (!any) return;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const bool on = (i < G.nx) && (j < G.ny);
+  double acc[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) acc[q] = 0.0;
+  if (on) {
+    const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+    for (int k = k0; k < k1; ++k) {
+      const long long c = ((long long)k * G.ny + j) * G.nx + i;
+      const double di = C.dinv[c];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        if (!act[r]) continue;
+        C.x[r][c] += alpha[r] * C.p[r][c];
+        const double res = C.r[r][c] - alpha[r] * C.q[r][c];
+        C.r[r][c] = res;
+        acc[2 * r + 0] += res * (di * res);
+        acc[2 * r + 1] += res * res;
+      }
+    }
+  }
+  double out[6];
+  if (reduce_last_block<6>(acc, C.partial, C.counter, out) && threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      if (act[r]) cg_after_update(C.S[r], out[2 * r], out[2 * r + 1]);
+  }
+}
+
+// p = D^{-1} r + beta p
+__global__ void __launch_bounds__(NT) k_cn_pupdate(Geo G, Cn3 C) {
+  bool act[3];
+  double beta[3];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    act[r] = C.S[r].status == CG_RUNNING;
+    beta[r] = C.S[r].beta;
+    any |= act[r];
+  }
+  if (!any) return;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const long long c = ((long long)k * G.ny + j) * G.nx + i;
+    const double di = C.dinv[c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      if (act[r]) C.p[r][c] = di * C.r[r][c] + beta[r] * C.p[r][c];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_diff_coef(const Geo& G, const DevParams& P, double dt, const double* g,
+                             const double* w, const double* f, double* const Kf[3], double* dsum,
+                             double* dinv, double* rho, cudaStream_t st) {
+  k_diff_coef<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, 0.5 * dt, g, w, f, Kf[0], Kf[1], Kf[2], dsum,
+                                               dinv, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cn_init(const Geo& G, const Cn3& C, cudaStream_t st) {
+  k_cn_init<<<G.grid, dim3(BX, BY), 0, st>>>(G, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cn_iter(const Geo& G, const Cn3& C, cudaStream_t st) {
+  k_cn_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, C);
+  k_cn_update<<<G.grid, dim3(BX, BY), 0, st>>>(G, C);
+  k_cn_pupdate<<<G.grid, dim3(BX, BY), 0, st>>>(G, C);
+  return cudaGetLastError();
+}
+
+}  // namespace tg

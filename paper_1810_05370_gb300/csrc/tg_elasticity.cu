@@ -1,0 +1,268 @@
+// tg_elasticity.cu -- the screened Navier-Lame solve of S6 (and of tg_init / tg_solve_elasticity).
+//
+// Eq. e:screening with Eq. e:variable_elasticity: -eta u + L u = b, solved in the SPD form
+// (eta I - L_h) u = -b.  Component a of L_h u is
+//   sum_d d_d( C^{ad} d_d u_a ) + sum_{d != a} [ d_d(mu d_a u_d) + d_a(lambda d_d u_d) ]
+// with C^{aa} = lambda + 2 mu and C^{ad} = mu (d != a): compact face differences (face value
+// = mean of the two nodes) for the first sum, centred differences for the mixed terms.  The
+// stencil touches the 6 face and 12 edge neighbours of a node (19 of the 3x3x3 box).
+//
+// Per-step precomputation trades bytes for FP64 arithmetic: face coefficients already
+// divided by h_d^2 and the Jacobi diagonal are stored, so a matrix-vector product needs
+// 1 multiply and 6 fused multiply-adds per component for the face part.
+#include "tg_internal.cuh"
+
+namespace tg {
+namespace {
+
+struct ElasView {
+  const double* mu;
+  const double* lam;
+  const double* F[3];
+  const double* G[3];
+  const double* dsum[3];
+};
+
+__device__ __forceinline__ ElasView view(const Elas& E) {
+  ElasView v;
+  v.mu = E.mu;
+  v.lam = E.lam;
+  for (int d = 0; d < 3; ++d) {
+    v.F[d] = E.F[d];
+    v.G[d] = E.G[d];
+    v.dsum[d] = E.dsum[d];
+  }
+  return v;
+}
+
+// 4 h_A h_D [ d_D(mu d_A u_D) + d_A(lambda d_D u_D) ] at the centre node, centred differences.
+template <int A, int D>
+__device__ __forceinline__ double mixed(const Nbr& nb, const double* __restrict__ xd,
+                                        const double* __restrict__ mu,
+                                        const double* __restrict__ lam) {
+  const double epp = xd[at2<A, D>(nb, +1, +1)];  // c + e_A + e_D
+  const double epm = xd[at2<A, D>(nb, -1, +1)];  // c - e_A + e_D
+  const double emp = xd[at2<A, D>(nb, +1, -1)];  // c + e_A - e_D
+  const double emm = xd[at2<A, D>(nb, -1, -1)];  // c - e_A - e_D
+  return mu[at1<D>(nb, +1)] * (epp - epm) - mu[at1<D>(nb, -1)] * (emp - emm) +
+         lam[at1<A>(nb, +1)] * (epp - emp) - lam[at1<A>(nb, -1)] * (epm - emm);
+}
+
+// component A of (eta I - L_h) x at node c
+template <int A>
+__device__ __forceinline__ double elas_row(const Geo& G, const Nbr& nb, long long c,
+                                           const ElasView& E, const double* const x[3]) {
+  constexpr int D1 = (A + 1) % 3, D2 = (A + 2) % 3;
+  const double* __restrict__ xa = x[A];
+  const double* __restrict__ CA = E.F[A];
+  const double* __restrict__ C1 = E.G[D1];
+  const double* __restrict__ C2 = E.G[D2];
+  double v = E.dsum[A][c] * xa[c];
+  v -= CA[c] * xa[at1<A>(nb, 1)] + CA[at1<A>(nb, -1)] * xa[at1<A>(nb, -1)];
+  v -= C1[c] * xa[at1<D1>(nb, 1)] + C1[at1<D1>(nb, -1)] * xa[at1<D1>(nb, -1)];
+  v -= C2[c] * xa[at1<D2>(nb, 1)] + C2[at1<D2>(nb, -1)] * xa[at1<D2>(nb, -1)];
+  v -= G.s_cross[A][D1] * mixed<A, D1>(nb, x[D1], E.mu, E.lam);
+  v -= G.s_cross[A][D2] * mixed<A, D2>(nb, x[D2], E.mu, E.lam);
+  return v;
+}
+
+__global__ void __launch_bounds__(NT) k_elas_coef(Geo G, DevParams P, Elas E,
+                                                  const double* __restrict__ p,
+                                                  const double* __restrict__ n, int force) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const Nbr nb = make_nbr(G, i, j, k);
+    const long long c = nb.at(0, 0, 0);
+    const double muc = E.mu[c], lac = E.lam[c];
+    double mfp[3], mfm[3], lfp[3], lfm[3];
+    long long np[3] = {nb.at(1, 0, 0), nb.at(0, 1, 0), nb.at(0, 0, 1)};
+    long long nm[3] = {nb.at(-1, 0, 0), nb.at(0, -1, 0), nb.at(0, 0, -1)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      mfp[d] = 0.5 * (muc + E.mu[np[d]]);
+      mfm[d] = 0.5 * (E.mu[nm[d]] + muc);
+      lfp[d] = 0.5 * (lac + E.lam[np[d]]);
+      lfm[d] = 0.5 * (E.lam[nm[d]] + lac);
+      E.F[d][c] = (lfp[d] + 2.0 * mfp[d]) * G.ih2[d];
+      E.G[d][c] = mfp[d] * G.ih2[d];
+    }
+    const double et = E.eta[c];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double s = et;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double cp = (d == a) ? lfp[d] + 2.0 * mfp[d] : mfp[d];
+        const double cm = (d == a) ? lfm[d] + 2.0 * mfm[d] : mfm[d];
+        s += (cp + cm) * G.ih2[d];
+      }
+      E.dsum[a][c] = s;
+      E.dinv[a][c] = 1.0 / s;
+    }
+    if (force) {
+      const double sc = p[c] + n[c];
+      const double th = P.zeta * tanh(sc);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        E.b[d][c] = th * (((p[np[d]] + n[np[d]]) - (p[nm[d]] + n[nm[d]])) * G.inv2h[d]);
+    }
+  }
+}
+
+// r = rhs - A u, du = 0, p = D^{-1} r;  rhs = -b (force) or the caller's b.
+__global__ void __launch_bounds__(NT) k_elas_init(Geo G, Elas E, int minus_b) {
+  const ElasView V = view(E);
+  const double* const u[3] = {E.u[0], E.u[1], E.u[2]};
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const bool on = (i < G.nx) && (j < G.ny);
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (on) {
+    const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+    for (int k = k0; k < k1; ++k) {
+      const Nbr nb = make_nbr(G, i, j, k);
+      const long long c = nb.at(0, 0, 0);
+      double Au[3];
+      Au[0] = elas_row<0>(G, nb, c, V, u);
+      Au[1] = elas_row<1>(G, nb, c, V, u);
+      Au[2] = elas_row<2>(G, nb, c, V, u);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double rhs = minus_b ? -E.b[a][c] : E.b[a][c];
+        const double res = rhs - Au[a];
+        const double z = E.dinv[a][c] * res;
+        E.r[a][c] = res;
+        E.p[a][c] = z;
+        E.du[a][c] = 0.0;
+        acc[0] += rhs * rhs;
+        acc[1] += res * res;
+        acc[2] += res * z;
+      }
+    }
+  }
+  double out[3];
+  if (reduce_last_block<3>(acc, E.partial, E.counter, out) && threadIdx.x == 0 && threadIdx.y == 0)
+    cg_after_init(*E.S, out[0], out[1], out[2]);
+}
+
+__global__ void __launch_bounds__(NT) k_elas_matvec(Geo G, Elas E) {
+  if (E.S->status != CG_RUNNING) return;
+  const ElasView V = view(E);
+  const double* const p[3] = {E.p[0], E.p[1], E.p[2]};
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const bool on = (i < G.nx) && (j < G.ny);
+  double acc[1] = {0.0};
+  if (on) {
+    const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+    for (int k = k0; k < k1; ++k) {
+      const Nbr nb = make_nbr(G, i, j, k);
+      const long long c = nb.at(0, 0, 0);
+      const double q0 = elas_row<0>(G, nb, c, V, p);
+      const double q1 = elas_row<1>(G, nb, c, V, p);
+      const double q2 = elas_row<2>(G, nb, c, V, p);
+      E.q[0][c] = q0;
+      E.q[1][c] = q1;
+      E.q[2][c] = q2;
+      acc[0] += p[0][c] * q0 + p[1][c] * q1 + p[2][c] * q2;
+    }
+  }
+  double out[1];
+  if (reduce_last_block<1>(acc, E.partial, E.counter, out) && threadIdx.x == 0 && threadIdx.y == 0) {
+    E.S->pq = out[0];
+    E.S->alpha = E.S->rz / out[0];
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_elas_update(Geo G, Elas E) {
+  if (E.S->status != CG_RUNNING) return;
+  const double alpha = E.S->alpha;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const bool on = (i < G.nx) && (j < G.ny);
+  double acc[2] = {0.0, 0.0};
+  if (on) {
+    const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+    for (int k = k0; k < k1; ++k) {
+      const long long c = ((long long)k * G.ny + j) * G.nx + i;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        E.du[a][c] += alpha * E.p[a][c];
+        const double res = E.r[a][c] - alpha * E.q[a][c];
+        E.r[a][c] = res;
+        acc[0] += res * (E.dinv[a][c] * res);
+        acc[1] += res * res;
+      }
+    }
+  }
+  double out[2];
+  if (reduce_last_block<2>(acc, E.partial, E.counter, out) && threadIdx.x == 0 && threadIdx.y == 0)
+    cg_after_update(*E.S, out[0], out[1]);
+}
+
+__global__ void __launch_bounds__(NT) k_elas_pupdate(Geo G, Elas E) {
+  if (E.S->status != CG_RUNNING) return;
+  const double beta = E.S->beta;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const long long c = ((long long)k * G.ny + j) * G.nx + i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) E.p[a][c] = E.dinv[a][c] * E.r[a][c] + beta * E.p[a][c];
+  }
+}
+
+// u += du (du = -u when the right-hand side vanished, i.e. u = 0), v = du / dt
+__global__ void __launch_bounds__(NT) k_elas_finish(Geo G, Elas E, double inv_dt, int zero_rhs) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const long long c = ((long long)k * G.ny + j) * G.nx + i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double uo = E.u[a][c];
+      const double du = zero_rhs ? -uo : E.du[a][c];
+      E.u[a][c] = zero_rhs ? 0.0 : uo + du;
+      if (inv_dt > 0.0) E.v[a][c] = du * inv_dt;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_elas_coef(const Geo& G, const DevParams& P, const Elas& E, const double* p,
+                             const double* n, bool force, cudaStream_t st) {
+  k_elas_coef<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, E, p, n, force ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elas_init(const Geo& G, const Elas& E, bool minus_b, cudaStream_t st) {
+  k_elas_init<<<G.grid, dim3(BX, BY), 0, st>>>(G, E, minus_b ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elas_matvec(const Geo& G, const Elas& E, cudaStream_t st) {
+  k_elas_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elas_update(const Geo& G, const Elas& E, cudaStream_t st) {
+  k_elas_update<<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
+  k_elas_pupdate<<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elas_finish(const Geo& G, const Elas& E, double inv_dt, bool zero_rhs,
+                               cudaStream_t st) {
+  k_elas_finish<<<G.grid, dim3(BX, BY), 0, st>>>(G, E, inv_dt, zero_rhs ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace tg

@@ -1,0 +1,275 @@
+// tg_internal.cuh -- shared device helpers and host-side launch declarations of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tg.h"
+
+namespace tg {
+
+// Thread block of every grid-shaped kernel: 32 x 8 threads over (x, y), marching a chunk of
+// z planes.  x is the contiguous axis, so a warp reads 32 consecutive values of a row.
+constexpr int BX = 32;
+constexpr int BY = 8;
+constexpr int NT = BX * BY;
+constexpr int NWARP = NT / 32;
+
+struct Geo {
+  int nx, ny, nz;
+  long long nxy, nvox;
+  double h[3];
+  double ih2[3];        // 1 / h_d^2
+  double inv2h[3];      // 1 / (2 h_d)
+  double s_cross[3][3]; // 1 / (4 h_a h_d)
+  int zc;               // z planes per block
+  dim3 grid;            // (ceil(nx/BX), ceil(ny/BY), ceil(nz/zc))
+  int nblocks;
+};
+
+// Device-side state of one CG solve (one right-hand side).
+enum CgStatus : int {
+  CG_RUNNING = 0,
+  CG_CONVERGED = 1,
+  CG_NONFINITE = 2,
+  CG_MAXIT = 3,
+  CG_ZERO_RHS = 4
+};
+
+struct CgScal {
+  double rz;     // <r, D^{-1} r>
+  double rr;     // <r, r>
+  double bb;     // <rhs, rhs>
+  double pq;     // <p, A p>
+  double alpha;
+  double beta;
+  double rtol;
+  int it;
+  int maxit;
+  int status;
+  int pad;
+};
+
+// Periodic neighbour offsets of node (i, j, k): X[o+1], Y[o+1], Z[o+1] for o in {-1, 0, 1};
+// the linear index of (i + ox, j + oy, k + oz) is Z[oz+1] + Y[oy+1] + X[ox+1].
+struct Nbr {
+  long long X[3], Y[3], Z[3];
+  __device__ __forceinline__ long long at(int ox, int oy, int oz) const {
+    return Z[oz + 1] + Y[oy + 1] + X[ox + 1];
+  }
+};
+
+__device__ __forceinline__ Nbr make_nbr(const Geo& g, int i, int j, int k) {
+  Nbr n;
+  n.X[0] = (i == 0) ? g.nx - 1 : i - 1;
+  n.X[1] = i;
+  n.X[2] = (i + 1 == g.nx) ? 0 : i + 1;
+  n.Y[0] = (long long)((j == 0) ? g.ny - 1 : j - 1) * g.nx;
+  n.Y[1] = (long long)j * g.nx;
+  n.Y[2] = (long long)((j + 1 == g.ny) ? 0 : j + 1) * g.nx;
+  n.Z[0] = (long long)((k == 0) ? g.nz - 1 : k - 1) * g.nxy;
+  n.Z[1] = (long long)k * g.nxy;
+  n.Z[2] = (long long)((k + 1 == g.nz) ? 0 : k + 1) * g.nxy;
+  return n;
+}
+
+// offset vector with s_a along axis A and s_d along axis D
+template <int A, int D>
+__device__ __forceinline__ long long at2(const Nbr& n, int sa, int sd) {
+  int o[3] = {0, 0, 0};
+  o[A] += sa;
+  o[D] += sd;
+  return n.at(o[0], o[1], o[2]);
+}
+
+template <int A>
+__device__ __forceinline__ long long at1(const Nbr& n, int s) {
+  int o[3] = {0, 0, 0};
+  o[A] += s;
+  return n.at(o[0], o[1], o[2]);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int block_linear() {
+  return (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+}
+
+__device__ __forceinline__ int block_count() { return gridDim.x * gridDim.y * gridDim.z; }
+
+// Block-level sum of NV values, written to partial[block][NV]; the last block to finish sums
+// all partials in block order (deterministic) and returns true in every thread of that
+// block, with the totals in out[] valid in thread 0.  counter is reset by the last block.
+template <int NV>
+__device__ bool reduce_last_block(double (&v)[NV], double* partial, unsigned int* counter,
+                                  double (&out)[NV]) {
+  __shared__ double sh[NV][NWARP];
+  __shared__ bool am_last;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double s = warp_sum(v[q]);
+    if (lane == 0) sh[q][warp] = s;
+  }
+  __syncthreads();
+  const int nb = block_count();
+  if (tid == 0) {
+    const int b = block_linear();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < NWARP; ++w) s += sh[q][w];
+      partial[(size_t)b * NV + q] = s;
+    }
+    __threadfence();
+    unsigned int ticket = atomicAdd(counter, 1u);
+    am_last = (ticket == (unsigned int)(nb - 1));
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+  for (int b = tid; b < nb; b += NT) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] += __ldcg(partial + (size_t)b * NV + q);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double s = warp_sum(acc[q]);
+    if (lane == 0) sh[q][warp] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < NWARP; ++w) s += sh[q][w];
+      out[q] = s;
+    }
+    *counter = 0u;
+  }
+  return true;
+}
+
+// Convergence decision after an update (same order of tests as a textbook PCG loop:
+// converged, non-finite, iteration limit).
+__device__ __forceinline__ void cg_after_update(CgScal& S, double rz_new, double rr) {
+  S.it += 1;
+  S.rr = rr;
+  if (!isfinite(rr)) {
+    S.status = CG_NONFINITE;
+  } else if (sqrt(rr) <= S.rtol * sqrt(S.bb)) {
+    S.status = CG_CONVERGED;
+  } else if (S.it >= S.maxit) {
+    S.status = CG_MAXIT;
+  } else {
+    S.beta = rz_new / S.rz;
+    S.rz = rz_new;
+  }
+}
+
+__device__ __forceinline__ void cg_after_init(CgScal& S, double bb, double rr, double rz) {
+  S.bb = bb;
+  S.rr = rr;
+  S.rz = rz;
+  S.it = 0;
+  S.alpha = 0.0;
+  S.beta = 0.0;
+  if (bb == 0.0) {
+    S.status = CG_ZERO_RHS;
+  } else if (!isfinite(rr)) {
+    S.status = CG_NONFINITE;
+  } else if (sqrt(rr) <= S.rtol * sqrt(bb)) {
+    S.status = CG_CONVERGED;
+  } else if (S.maxit <= 0) {
+    S.status = CG_MAXIT;
+  } else {
+    S.status = CG_RUNNING;
+  }
+}
+
+// Parameters the kernels need, derived once per call on the host.
+struct DevParams {
+  double k_g, k_w, k_f, k_scale;
+  double rho_g, rho_w, rho_i_frac;
+  double alpha0, beta0, gamma, sigma_b, o_hyp, o_inv, o_heal, o_mit;
+  double delta_s, delta_p, inv_eps_H;
+  double cmu[5], clam[5], eta[5];   // per-species Lame and screening weights (Eq. e:lame)
+  double zeta;
+  double delta_e, delta_half, delta_l;
+};
+
+// ----------------------------------------------------------------------------- launches
+// All return cudaGetLastError() after queueing on `st`.
+
+// S0: diffusion faces (scaled by dt/(2 h_d^2)), Jacobi diagonal of the CN operator, rho.
+cudaError_t launch_diff_coef(const Geo&, const DevParams&, double dt, const double* g,
+                             const double* w, const double* f, double* const Kf[3], double* dsum,
+                             double* dinv, double* rho, cudaStream_t st);
+
+struct Cn3 {   // three simultaneous CN solves sharing one operator
+  double* x[3];
+  double* r[3];
+  double* p[3];
+  double* q[3];
+  const double* Kf[3];
+  const double* dsum;
+  const double* dinv;
+  CgScal* S;           // 3 entries
+  double* partial;
+  unsigned int* counter;
+};
+cudaError_t launch_cn_init(const Geo&, const Cn3&, cudaStream_t st);
+cudaError_t launch_cn_iter(const Geo&, const Cn3&, cudaStream_t st);
+
+// SL (S1)
+cudaError_t launch_divergence(const Geo&, const double* const v[3], double* div, cudaStream_t st);
+cudaError_t launch_sl_advect(const Geo&, double dt, const double* const v[3], const double* div,
+                             const double* const qin[6], double* const qout[6], cudaStream_t st);
+
+// S2 fix-up + S3-S5
+cudaError_t launch_react(const Geo&, const DevParams&, double dt, const double* rho,
+                         const double* i_dag, double* p, double* i, double* n, double* g,
+                         double* w, double* o, double* l, cudaStream_t st);
+
+// S6 coefficients
+cudaError_t launch_lame(const Geo&, const DevParams&, const double* p, const double* i,
+                        const double* n, const double* g, const double* w, const double* f,
+                        const double* bg, double* mu, double* lam, double* eta, cudaStream_t st);
+
+struct Elas {
+  const double* mu;
+  const double* lam;
+  const double* eta;
+  double* F[3];      // face (lambda + 2 mu) / h_d^2 between j and j + e_d
+  double* G[3];      // face mu / h_d^2
+  double* dsum[3];   // Jacobi diagonal per component
+  double* dinv[3];
+  double* b[3];      // force (or caller's rhs when b_external)
+  double* du[3];     // CG iterate: increment of u
+  double* r[3];
+  double* p[3];
+  double* q[3];
+  double* u[3];      // displacement (in: u^n, out: u^{n+1})
+  double* v[3];      // velocity (written when dt > 0)
+  CgScal* S;
+  double* partial;
+  unsigned int* counter;
+};
+cudaError_t launch_elas_coef(const Geo&, const DevParams&, const Elas&, const double* p,
+                             const double* n, bool force, cudaStream_t st);
+cudaError_t launch_elas_init(const Geo&, const Elas&, bool rhs_is_minus_b, cudaStream_t st);
+cudaError_t launch_elas_matvec(const Geo&, const Elas&, cudaStream_t st);
+cudaError_t launch_elas_update(const Geo&, const Elas&, cudaStream_t st);   // update + p-update
+cudaError_t launch_elas_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
+                               cudaStream_t st);
+
+}  // namespace tg

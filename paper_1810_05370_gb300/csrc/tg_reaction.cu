@@ -1,0 +1,139 @@
+// tg_reaction.cu -- the pointwise sub-steps: S2 fix-up of g and w, reactions S3-S5, and the
+// Lame / screening mixture of S6.
+#include "tg_internal.cuh"
+
+namespace tg {
+namespace {
+
+// smoothed Heaviside H(x) = (1 + tanh(x / eps_H)) / 2, evaluated as 1 / (1 + exp(-2 x / eps_H))
+// (the same function; this form keeps full relative accuracy where H is tiny)
+__device__ __forceinline__ double heaviside(const DevParams& P, double x) {
+  return 1.0 / (1.0 + exp(-2.0 * x * P.inv_eps_H));
+}
+
+// oxygen factor of Eq. e:gog_reac_op / e:gog_reac_inv_op
+__device__ __forceinline__ double mitosis_factor(const DevParams& P, double o) {
+  if (o > P.o_inv) return 1.0;
+  if (o >= P.o_mit) return (o - P.o_mit) / (P.o_inv - P.o_mit);
+  return 0.0;
+}
+
+// Sources of Eq. e:p, e:i, e:n, e:gm_wm, e:w at fixed oxygen (h, alpha and the mitosis
+// factor depend on o only and are passed in).
+__device__ __forceinline__ void species_rates(const DevParams& P, double rho, double o, double h,
+                                              double alpha, double mf, const double y[5],
+                                              double dy[5]) {
+  const double p = y[0], i = y[1], g = y[3], w = y[4];
+  const double beta = P.beta0 * heaviside(P, P.sigma_b - p - i) * o;   // Eq. e:beta
+  const double R = rho * p * (1.0 - p) * mf;                            // Eq. e:gog_reac_op
+  const double Rt = P.rho_i_frac * rho * i * (1.0 - i) * mf;            // Eq. e:gog_reac_inv_op
+  const double gw = g + w;
+  const double fg = gw > 0.0 ? g / gw : 0.0;
+  const double fw = gw > 0.0 ? w / gw : 0.0;
+  dy[0] = R - alpha * p + beta * i - h * p;
+  dy[1] = Rt + alpha * p - beta * i - h * i;
+  dy[2] = h * (p + i + g + w);
+  dy[3] = -fg * (R + Rt) - h * g;
+  dy[4] = -fw * (R + Rt) - h * w;
+}
+
+__global__ void __launch_bounds__(NT) k_react(Geo G, DevParams P, double dt,
+                                              const double* __restrict__ rho,
+                                              const double* __restrict__ i_dag, double* p,
+                                              double* ii, double* n, double* g, double* w,
+                                              double* o, double* l) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const long long c = ((long long)k * G.ny + j) * G.nx + i;
+    // S2 fix-up: the Crank-Nicolson increment of i comes out of g and w, in proportion
+    double y[5] = {p[c], ii[c], n[c], g[c], w[c]};
+    {
+      const double di = y[1] - i_dag[c];
+      const double gw = y[3] + y[4];
+      const double fg = gw > 0.0 ? y[3] / gw : 0.0;
+      const double fw = gw > 0.0 ? y[4] / gw : 0.0;
+      y[3] = y[3] - di * fg;
+      y[4] = y[4] - di * fw;
+    }
+    // S3: one Heun step with the post-diffusion oxygen and the step-start rho
+    const double oo = o[c], r = rho[c];
+    const double h = P.gamma * heaviside(P, P.o_hyp - oo);     // Eq. e:death
+    const double alpha = P.alpha0 * heaviside(P, P.o_inv - oo); // Eq. e:alpha
+    const double mf = mitosis_factor(P, oo);
+    double k1v[5], k2v[5], ys[5];
+    species_rates(P, r, oo, h, alpha, mf, y, k1v);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) ys[s] = y[s] + dt * k1v[s];
+    species_rates(P, r, oo, h, alpha, mf, ys, k2v);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) y[s] = y[s] + 0.5 * dt * (k1v[s] + k2v[s]);
+    p[c] = y[0];
+    ii[c] = y[1];
+    n[c] = y[2];
+    g[c] = y[3];
+    w[c] = y[4];
+    // S4: oxygen, d_t o = -delta_p p + delta_s (o_heal - o)(g + w)   (Eq. e:ox)
+    const double gwn = y[3] + y[4];
+    const double ko1 = -P.delta_p * y[0] + P.delta_s * (P.o_heal - oo) * gwn;
+    const double os = oo + dt * ko1;
+    const double ko2 = -P.delta_p * y[0] + P.delta_s * (P.o_heal - os) * gwn;
+    o[c] = oo + 0.5 * dt * (ko1 + ko2);
+    // S5: edema, d_t l = delta_e i / (i + delta_half) (1 - i) - delta_l l   (Eq. e:edema)
+    const double l0 = l[c];
+    const double src = P.delta_e * y[1] / (y[1] + P.delta_half) * (1.0 - y[1]);
+    const double kl1 = src - P.delta_l * l0;
+    const double ls = l0 + dt * kl1;
+    const double kl2 = src - P.delta_l * ls;
+    l[c] = l0 + 0.5 * dt * (kl1 + kl2);
+  }
+}
+
+// Eq. e:lame over iota = (p + i + n, g, w, f, bg); eta mixed the same way.
+__global__ void __launch_bounds__(NT) k_lame(Geo G, DevParams P, const double* __restrict__ p,
+                                             const double* __restrict__ ii,
+                                             const double* __restrict__ n,
+                                             const double* __restrict__ g,
+                                             const double* __restrict__ w,
+                                             const double* __restrict__ f,
+                                             const double* __restrict__ bg, double* mu,
+                                             double* lam, double* eta) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const long long c = ((long long)k * G.ny + j) * G.nx + i;
+    const double iota[5] = {p[c] + ii[c] + n[c], g[c], w[c], f[c], bg[c]};
+    double smu = 0.0, slam = 0.0, seta = 0.0;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+      smu += P.cmu[s] * iota[s];
+      slam += P.clam[s] * iota[s];
+      seta += P.eta[s] * iota[s];
+    }
+    mu[c] = smu;
+    lam[c] = slam;
+    eta[c] = seta;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_react(const Geo& G, const DevParams& P, double dt, const double* rho,
+                         const double* i_dag, double* p, double* i, double* n, double* g,
+                         double* w, double* o, double* l, cudaStream_t st) {
+  k_react<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, rho, i_dag, p, i, n, g, w, o, l);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lame(const Geo& G, const DevParams& P, const double* p, const double* i,
+                        const double* n, const double* g, const double* w, const double* f,
+                        const double* bg, double* mu, double* lam, double* eta, cudaStream_t st) {
+  k_lame<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, p, i, n, g, w, f, bg, mu, lam, eta);
+  return cudaGetLastError();
+}
+
+}  // namespace tg

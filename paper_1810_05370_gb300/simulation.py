@@ -1,0 +1,93 @@
+"""torch-facing wrapper around the C ABI: device buffers and streams come from torch.
+
+A `Simulation` owns the state tensors (FP64, CUDA, shape (nz, ny, nx)) and one workspace
+tensor; all arithmetic happens in libtg.so.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _tg
+
+STATE_KEYS = ("p", "i", "n", "g", "w", "f", "o", "l", "bg", "ux", "uy", "uz", "vx", "vy", "vz")
+PRECISIONS = {"fp64": _tg.TG_FP64, "mixed": _tg.TG_MIXED}
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("paper_1810_05370_gb300 needs a CUDA device; no CPU path exists")
+    return torch
+
+
+class Simulation:
+    """One simulation on one GPU: `tg_init` at construction, `tg_step` per `step` call."""
+
+    def __init__(self, n, params: dict, state: dict, precision: str = "fp64", L=None,
+                 device=None, stream=None, keep_uv: bool = False):
+        torch = _torch()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.grid = _tg.make_grid(n, L)
+        self.shape = (self.grid.n[2], self.grid.n[1], self.grid.n[0])
+        self.prec = PRECISIONS[precision]
+        self.state = {}
+        for k in STATE_KEYS:
+            v = state[k]
+            if isinstance(v, np.ndarray):
+                v = torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64))
+            v = v.to(device=self.device, dtype=torch.float64).contiguous()
+            if tuple(v.shape) != self.shape:
+                raise ValueError(f"state[{k!r}] has shape {tuple(v.shape)}, expected {self.shape}")
+            self.state[k] = v
+        nbytes = _tg.tg_workspace_bytes(self.grid, self.prec)
+        if nbytes == 0:
+            raise ValueError("invalid grid or unsupported precision")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        self.params = dict(params)
+        self._cparams = _tg.make_params(self.params)
+        self._cstate = self._state_struct()
+        with torch.cuda.device(self.device):
+            self.ctx, self.init_stats = _tg.tg_init(
+                self.grid, self._cparams, self.prec, self._cstate, self.workspace.data_ptr(),
+                nbytes, self.stream.cuda_stream, _tg.TG_INIT_KEEP_UV if keep_uv else 0)
+
+    def _state_struct(self):
+        s = _tg.tg_state()
+        for k in ("p", "i", "n", "g", "w", "f", "o", "l", "bg"):
+            setattr(s, k, self.state[k].data_ptr())
+        for a, c in enumerate("xyz"):
+            s.u[a] = self.state["u" + c].data_ptr()
+            s.v[a] = self.state["v" + c].data_ptr()
+        return s
+
+    def step(self, dt: float, nsteps: int = 1) -> dict:
+        return _tg.tg_step(self.ctx, dt, nsteps)
+
+    def solve_elasticity(self, rhs=None, u=None) -> dict:
+        """Solve (eta I - L_h) u = rhs (rhs=None: the model's -b) into u (default: the state's)."""
+        u = [self.state["ux"], self.state["uy"], self.state["uz"]] if u is None else list(u)
+        rp = None if rhs is None else [r.data_ptr() for r in rhs]
+        return _tg.tg_solve_elasticity(self.ctx, rp, [x.data_ptr() for x in u])
+
+    def set_timing(self, enable: bool = True):
+        _tg.tg_set_timing(self.ctx, enable)
+
+    def set_params(self, params: dict):
+        self.params = dict(params)
+        self._cparams = _tg.make_params(self.params)
+        _tg.tg_set_params(self.ctx, self._cparams)
+
+    def numpy(self) -> dict:
+        return {k: v.detach().cpu().numpy() for k, v in self.state.items()}
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            _tg.tg_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

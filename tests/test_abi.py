@@ -1,0 +1,70 @@
+"""Host-only checks of the C ABI library (no GPU needed): it loads, exports every function
+declared in include/tg.h, and rejects invalid arguments before touching the device."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tg():
+    from paper_1810_05370_gb300.build import build
+    build()
+    from paper_1810_05370_gb300 import _tg
+    return _tg
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "tg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(tg_[a-z_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(tg):
+    names = declared_functions()
+    assert {"tg_init", "tg_step", "tg_solve_elasticity", "tg_free", "tg_workspace_bytes",
+            "tg_error_string"} <= set(names)
+    out = subprocess.run(["nm", "-D", "--defined-only", tg.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (tg_[a-z_]+)\b", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+
+
+def test_struct_sizes_match_header_layout(tg):
+    # tg_params: 17 + 15 + 2 + 3 + 2 doubles, then two int32
+    assert C.sizeof(tg.tg_params) == (17 + 15 + 2 + 3 + 2) * 8 + 8
+    assert C.sizeof(tg.tg_grid) == 3 * 4 + 4 + 3 * 8
+    assert C.sizeof(tg.tg_state) == 15 * 8
+
+
+def test_workspace_bytes_validates_grid(tg):
+    assert tg.tg_workspace_bytes(tg.make_grid(32), tg.TG_FP64) > 0
+    assert tg.tg_workspace_bytes(tg.make_grid((3, 8, 8)), tg.TG_FP64) == 0
+    assert tg.tg_workspace_bytes(tg.make_grid((8, 8, 8), L=(1.0, -1.0, 1.0)), tg.TG_FP64) == 0
+    assert tg.tg_workspace_bytes(tg.make_grid(8), 7) == 0
+
+
+def test_init_rejects_null_arguments(tg):
+    from synth import workload_params
+    grid = tg.make_grid(8)
+    params = tg.make_params(workload_params())
+    st = tg.tg_state()          # all NULL
+    ctx = C.c_void_p()
+    rc = tg.lib.tg_init(C.byref(grid), C.byref(params), 0, C.byref(st), None, 0, None, 0,
+                        C.byref(ctx), None)
+    assert rc == tg.TG_ERR_ARG and not ctx.value
+    rc = tg.lib.tg_init(None, C.byref(params), 0, C.byref(st), None, 0, None, 0, C.byref(ctx), None)
+    assert rc == tg.TG_ERR_ARG
+    assert tg.lib.tg_step(None, C.c_double(0.01), 1, None, None) == tg.TG_ERR_ARG
+
+
+def test_error_strings(tg):
+    for s in range(8):
+        assert tg.error_string(s)
+    assert "unknown" in tg.error_string(99)

@@ -544,6 +544,20 @@ def test_oxygen_and_edema_closed_form(oracle):
         assert 2.7 < q < 3.3, errs
 
 
+def test_smoothed_heaviside_accuracy(oracle):
+    """H(x) = (1 + tanh(x / eps_H)) / 2 (Eq. e:death, e:alpha, e:beta), checked in 50-digit
+    arithmetic, including the far negative tail where the tanh form would cancel."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    P = workload_params()
+    for x in (-0.4, -0.2, -0.15, -0.05, -0.001, 0.0, 0.003, 0.05, 0.3):
+        ref = (1 + mp.tanh(mp.mpf(x) / mp.mpf(P["eps_H"]))) / 2
+        got = oracle.heaviside(P, x)
+        # relative error allowed: rounding plus the conditioning of exp at -2x/eps_H
+        cond = 2.0 * abs(x) / P["eps_H"]
+        assert abs(got - float(ref)) <= (4e-16 + cond * 2.3e-16) * float(ref) + 1e-300, (x, got, ref)
+
+
 def test_reaction_conserves_total_cell_mass_pointwise(oracle):
     """Eq. e:pw_mass_consv_gog: the sources of p, i, n, g, w sum to zero."""
     rng = np.random.default_rng(9)
