@@ -137,6 +137,33 @@ tg_status tg_set_params(tg_ctx* ctx, const tg_params* params);
  * are created on first use (host-side objects, no device allocation). */
 tg_status tg_set_timing(tg_ctx* ctx, int32_t enable);
 
+/* Elasticity solve that allocates nothing and needs no workspace or context.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that may not
+ * allocate device memory themselves, for example code running inside a host application
+ * that owns every device allocation (a fixed memory pool or budget), or a latency-critical
+ * loop that cannot afford the implicit device synchronisation of cudaMalloc.  Instead of a
+ * caller workspace it uses one scratch array compiled into the library
+ * (TG_STATIC_SCRATCH_BYTES of device memory, held on every GPU that loads the library until
+ * the process exits), so it only accepts small grids: n[0]*n[1]*n[2] <= TG_STATIC_MAX_VOXELS.
+ * Larger grids are rejected with TG_ERR_WORKSPACE before any GPU work.
+ *
+ * It computes what tg_solve_elasticity computes on a context over the same state: the Lame
+ * and screening fields from the state's species (p, i, n, g, w, f, bg are read; the other
+ * state pointers are ignored), then (eta I - L_h) u = rhs by Jacobi-preconditioned CG from the
+ * given u; rhs == NULL means rhs = -b (the force of Eq. e:forcingfunction).  All work goes to
+ * cuda_stream and the call returns after it has finished.
+ *
+ * The first call on a device looks up the scratch array's device address (with that device
+ * current) and caches it; make that first call before any stream capture.  Every call on a
+ * device shares the one scratch array and leaves its contents behind: calls whose GPU work
+ * overlaps (two host threads, or two streams) race and give wrong results, so serialise them. */
+#define TG_STATIC_MAX_VOXELS 32768
+#define TG_STATIC_SCRATCH_BYTES (16u << 20)
+tg_status tg_solve_elasticity_static(const tg_grid* grid, const tg_params* params,
+                                     const tg_state* state, double* const rhs[3], double* u[3],
+                                     void* cuda_stream, tg_stats* stats);
+
 /* Release the context (host memory only; the caller's buffers are untouched). */
 void tg_free(tg_ctx* ctx);
 

@@ -77,6 +77,9 @@ def _load():
         "tg_solve_elasticity": (C.c_int, [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(tg_stats)]),
         "tg_set_params": (C.c_int, [C.c_void_p, P(tg_params)]),
         "tg_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+        "tg_solve_elasticity_static": (C.c_int, [P(tg_grid), P(tg_params), P(tg_state),
+                                                 P(C.c_void_p), P(C.c_void_p), C.c_void_p,
+                                                 P(tg_stats)]),
         "tg_free": (None, [C.c_void_p]),
         "tg_error_string": (C.c_char_p, [C.c_int]),
     }
@@ -175,6 +178,21 @@ def tg_set_timing(ctx, enable: bool):
     rc = lib.tg_set_timing(ctx, 1 if enable else 0)
     if rc != TG_OK:
         raise TGError(rc, "tg_set_timing")
+
+
+TG_STATIC_MAX_VOXELS = 32768
+
+
+def tg_solve_elasticity_static(grid, params, state, rhs_ptrs, u_ptrs, stream_ptr):
+    """Workspace-free elasticity solve on small grids (scratch compiled into the library)."""
+    stats = tg_stats()
+    rhs = (C.c_void_p * 3)(*rhs_ptrs) if rhs_ptrs is not None else None
+    u = (C.c_void_p * 3)(*u_ptrs)
+    rc = lib.tg_solve_elasticity_static(C.byref(grid), C.byref(params), C.byref(state), rhs, u,
+                                        C.c_void_p(stream_ptr), C.byref(stats))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_solve_elasticity_static")
+    return stats_dict(stats)
 
 
 def tg_free(ctx):

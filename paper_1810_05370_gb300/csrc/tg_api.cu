@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -549,3 +550,77 @@ const char* tg_error_string(tg_status s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free elasticity solve (tg_solve_elasticity_static).  Its scratch lives in a
+// file-scope device array instead of a caller workspace.  Host code must not use the array's
+// name as an address (it is a host-side stand-in); the device address is looked up once per
+// device with cudaGetSymbolAddress and cached.
+namespace {
+
+__device__ __align__(256) unsigned char g_static_scratch[TG_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_addr[kMaxDevices] = {};
+
+// device address of g_static_scratch on the current device (set up on first use)
+tg_status static_scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return TG_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return TG_ERR_CUDA;
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return TG_OK;
+}
+
+}  // namespace
+
+extern "C" tg_status tg_solve_elasticity_static(const tg_grid* grid, const tg_params* params,
+                                                const tg_state* state, double* const rhs[3],
+                                                double* u[3], void* cuda_stream,
+                                                tg_stats* stats) {
+  if (!grid_ok(grid) || !params_ok(params) || !state || !u) return TG_ERR_ARG;
+  const double* must[] = {state->p, state->i, state->n, state->g, state->w, state->f, state->bg,
+                          u[0], u[1], u[2]};
+  for (const double* q : must)
+    if (!q || ((uintptr_t)q & 15u)) return TG_ERR_ARG;
+  if (rhs && (!rhs[0] || !rhs[1] || !rhs[2])) return TG_ERR_ARG;
+  const Geo G = make_geo(grid, sm_count());
+  const Layout L = layout(G);
+  if (G.nvox > TG_STATIC_MAX_VOXELS || L.total > (size_t)TG_STATIC_SCRATCH_BYTES)
+    return TG_ERR_WORKSPACE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TG_ERR_CUDA;
+  void* base = nullptr;
+  tg_status e = static_scratch_address(dev, &base);
+  if (e != TG_OK) return e;
+
+  // a value-initialised context on the stack over the static scratch (host memory only)
+  tg_ctx X{};
+  X.G = G;
+  X.L = L;
+  X.prm = *params;
+  X.dp = make_dev_params(params);
+  X.prec = TG_FP64;
+  X.st = *state;
+  X.stream = (cudaStream_t)cuda_stream;
+  X.device = dev;
+  X.ws = (char*)base;
+  for (int a = 0; a < A_COUNT; ++a) X.a[a] = (double*)(X.ws + L.arr[a]);
+  X.partial = (double*)(X.ws + L.partial);
+  X.counter = (unsigned int*)(X.ws + L.counter);
+  X.scal = (CgScal*)(X.ws + L.scal);
+  if (stats) memset(stats, 0, sizeof(*stats));
+  // the reduction counter must start at zero; the previous call may have left anything
+  if (cudaMemsetAsync(X.counter, 0, ALIGN, X.stream) != cudaSuccess) return TG_ERR_CUDA;
+  e = build_elas_coef(&X, rhs == nullptr);
+  if (e != TG_OK) return e;
+  double* const uu[3] = {u[0], u[1], u[2]};
+  e = elas_solve(&X, uu, rhs, rhs == nullptr, 0.0, stats);
+  if (e == TG_OK && stats) fill_profile(&X, stats);
+  return e;
+}
