@@ -30,10 +30,11 @@ METRIC = "voxel-steps/s at 256^3 (mixed FP32 vs plain FP64, same GPU); adjoint/f
 UNIT = "voxel-steps/s"
 FIELDS = ("p", "i", "n", "g", "w", "f", "o", "l", "bg", "ux", "uy", "uz", "vx", "vy", "vz")
 
-# algorithmic traffic and arithmetic of the elasticity operator kernel, per voxel and launch:
-# reads p (3 comps), face coefficients (lambda+2mu)/h^2 and mu/h^2 (3 + 3), Jacobi diagonal
-# (3), node mu and lambda (2); writes q (3): 17 FP64 arrays.
-ELAS_MATVEC_BYTES_PER_VOXEL = 17 * 8
+# Algorithmic traffic and arithmetic of the elasticity operator kernel, per voxel and launch.
+# FP64 path: reads p (3 comps), face coefficients (lambda+2mu)/h^2 and mu/h^2 (3 + 3), Jacobi
+# diagonal (3), node mu and lambda (2); writes q (3): 17 FP64 arrays; 123 FP64 flops.
+# Mixed path: reads p (3) and node mu, lambda, eta (3), writes q (3): 9 FP32 arrays.
+ELAS_MATVEC_BYTES_PER_VOXEL = {"fp64": 17 * 8, "mixed": 9 * 4}
 ELAS_MATVEC_FLOPS_PER_VOXEL = 123
 
 
@@ -44,7 +45,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--dt", type=float, default=0.01)
-    ap.add_argument("--precision", choices=("fp64", "mixed"), default="fp64")
+    ap.add_argument("--precision", choices=("fp64", "mixed"), default="mixed")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip timing the other precision on the same GPU")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -190,6 +193,7 @@ def main():
     st0 = initial_state(n, seed=0)
     sim = Simulation(n, P, st0, precision=args.precision, device=dev)
     stream = sim.stream
+    ws_bytes = sim.workspace.numel()
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -197,34 +201,70 @@ def main():
             dist.barrier()
 
     # ---------------------------------------------------------------- device-resident timing
-    for _ in range(args.warmup):
-        sim.step(args.dt)
-    sim.set_timing(True)
+    def time_steps(sim, clocks=None):
+        for _ in range(args.warmup):
+            sim.step(args.dt)
+        sim.set_timing(True)
+        barrier()
+        if clocks is not None:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        agg = {"launches": 0, "t_mv": 0.0, "n_mv": 0, "it_elas": [], "it_elas_outer": [],
+               "it_diff": []}
+        for _ in range(args.steps):
+            s = sim.step(args.dt)
+            agg["launches"] += s["launches"]
+            agg["t_mv"] += s["t_elas_matvec_ms"]
+            agg["n_mv"] += s["n_elas_matvec"]
+            agg["it_elas"].append(s["it_elas"])
+            agg["it_elas_outer"].append(s["it_elas_outer"])
+            agg["it_diff"].append(s["it_diff"])
+        e1.record(sim.stream)
+        barrier()
+        agg["clocks"] = clocks.stop() if clocks is not None else None
+        sim.set_timing(False)
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        agg["ms"] = ms
+        agg["value"] = world * V * args.steps / (ms * 1e-3)
+        return agg
+
     clocks = Clocks(local)
-    barrier()
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    agg = {"launches": 0, "t_mv": 0.0, "n_mv": 0, "it_elas": [], "it_diff": []}
-    for _ in range(args.steps):
-        s = sim.step(args.dt)
-        agg["launches"] += s["launches"]
-        agg["t_mv"] += s["t_elas_matvec_ms"]
-        agg["n_mv"] += s["n_elas_matvec"]
-        agg["it_elas"].append(s["it_elas"])
-        agg["it_diff"].append(s["it_diff"])
-    e1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    sim.set_timing(False)
-    ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * V * args.steps / (ms_max * 1e-3)
+    agg = time_steps(sim, clocks)
+    clk = agg["clocks"]
+    ms_max = agg["ms"]
+    value = agg["value"]
+
+    # ---------------------------------------------------------------- roofline of the top kernel
+    peaks, peak_src = load_peaks()
+
+    def roofline(agg, precision):
+        avg_ms = agg["t_mv"] / max(agg["n_mv"], 1)
+        mv_bytes = ELAS_MATVEC_BYTES_PER_VOXEL[precision] * V
+        gbs = mv_bytes / (avg_ms * 1e-3) / 1e9
+        share = agg["t_mv"] / agg["ms"] if agg["ms"] > 0 else None
+        if precision == "fp64":
+            tfl = ELAS_MATVEC_FLOPS_PER_VOXEL * V / (avg_ms * 1e-3) / 1e12
+            return {"kernel": "k_elas_matvec (FP64 19-point Navier-Lame operator + <p, Ap>)",
+                    "bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "derived FP64 roof (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                    "hbm_gbs": gbs, "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"],
+                    "share_of_step": share}
+        return {"kernel": "k_elas32_matvec (FP32 19-point Navier-Lame operator, faces on the fly, "
+                          "+ <p, Ap>)",
+                "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"{peak_src} HBM copy bandwidth",
+                "bytes_per_voxel": ELAS_MATVEC_BYTES_PER_VOXEL[precision],
+                "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"], "share_of_step": share}
+
+    roof = roofline(agg, args.precision)
 
     # ---------------------------------------------------------------- end to end (host buffers)
     e2e = None
@@ -253,21 +293,22 @@ def main():
         e2e = {"value": world * V * args.steps / secs, "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
-    # ---------------------------------------------------------------- roofline of the top kernel
-    peaks, peak_src = load_peaks()
-    avg_ms = agg["t_mv"] / max(agg["n_mv"], 1)
-    mv_bytes = ELAS_MATVEC_BYTES_PER_VOXEL * V
-    mv_flops = ELAS_MATVEC_FLOPS_PER_VOXEL * V
-    gbs = mv_bytes / (avg_ms * 1e-3) / 1e9
-    tfl = mv_flops / (avg_ms * 1e-3) / 1e12
-    roof = {
-        "kernel": "k_elas_matvec (FP64 19-point Navier-Lame operator + <p, Ap>)",
-        "bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
-        "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"], "hbm_peak_source": peak_src,
-        "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"],
-        "share_of_step": agg["t_mv"] / ms if ms > 0 else None,
-    }
+    # ---------------------------------------------------------------- the other precision
+    other = None
+    if not args.no_compare:
+        sim.close()
+        torch.cuda.empty_cache()
+        oprec = "fp64" if args.precision == "mixed" else "mixed"
+        sim_o = Simulation(n, P, st0, precision=oprec, device=dev)
+        ag_o = time_steps(sim_o)
+        other = {"precision": oprec, "value": ag_o["value"], "unit": UNIT,
+                 "ms_per_step": ag_o["ms"] / args.steps,
+                 "solver": {"it_elas_per_step": ag_o["it_elas"],
+                            "it_elas_outer_per_step": ag_o["it_elas_outer"],
+                            "it_diff_per_step": ag_o["it_diff"]},
+                 "roofline": roofline(ag_o, oprec), "gpu_launches": ag_o["launches"]}
+        sim_o.close()
+        sim = None
 
     # ---------------------------------------------------------------- CPU baseline (rank 0)
     cpu = None
@@ -291,17 +332,24 @@ def main():
                                    f"{args.precision} path",
                        "grid": n, "precision": args.precision,
                        "l2": "inputs larger than L2 (15 state arrays + workspace, "
-                             f"{(15 * V * 8 + sim.workspace.numel()) / 1e9:.1f} GB)",
+                             f"{(15 * V * 8 + ws_bytes) / 1e9:.1f} GB)",
                        "parallelism": f"replicas x{world}"},
-            "solver": {"it_elas_per_step": agg["it_elas"], "it_diff_per_step": agg["it_diff"]},
+            "solver": {"it_elas_per_step": agg["it_elas"],
+                       "it_elas_outer_per_step": agg["it_elas_outer"],
+                       "it_diff_per_step": agg["it_diff"]},
             "roofline": roof,
+            "compare": other,
+            "mixed_over_fp64": (None if other is None else
+                                (value / other["value"] if args.precision == "mixed"
+                                 else other["value"] / value)),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
             "gpu_launches": agg["launches"],
         }
         print(json.dumps(out), flush=True)
-    sim.close()
+    if sim is not None:
+        sim.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -28,9 +28,19 @@ enum Arr {
   A_COUNT
 };
 
+// FP32 arrays of the mixed precision (one FP32 value per voxel each)
+enum Arr32 {
+  B_MU, B_LAM, B_ETA, B_DINV0, B_DINV1, B_DINV2,
+  B_E0, B_E1, B_E2, B_R0, B_R1, B_R2, B_P0, B_P1, B_P2, B_Q0, B_Q1, B_Q2,
+  B_V0, B_V1, B_V2, B_DIV, B_SQ0, B_SQ1, B_SQ2, B_SQ3, B_SQ4, B_SQ5,
+  B_COUNT
+};
+
 constexpr size_t ALIGN = 256;
 constexpr int MAX_NV = 9;    // largest number of values reduced by one kernel
-constexpr int N_SCAL = 4;    // 3 diffusion solves + 1 elasticity solve
+constexpr int N_SCAL = 5;    // 3 diffusion solves, elasticity (outer), elasticity inner FP32
+constexpr int MAX_SWEEPS = 64;        // refinement sweeps of one mixed-precision solve
+constexpr double TAU_INNER = 1e-4;    // smallest relative reduction asked of an inner solve
 
 size_t round_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
@@ -71,16 +81,22 @@ Geo make_geo(const tg_grid* g, int sms) {
 
 struct Layout {
   size_t arr[A_COUNT];
+  size_t arr32[B_COUNT];
   size_t partial, counter, scal, total;
 };
 
-Layout layout(const Geo& G) {
+Layout layout(const Geo& G, tg_precision prec) {
   Layout L;
   size_t off = 0;
   const size_t abytes = round_up((size_t)G.nvox * sizeof(double));
   for (int a = 0; a < A_COUNT; ++a) {
     L.arr[a] = off;
     off += abytes;
+  }
+  const size_t fbytes = round_up((size_t)G.nvox * sizeof(float));
+  for (int b = 0; b < B_COUNT; ++b) {
+    L.arr32[b] = off;
+    if (prec == TG_MIXED) off += fbytes;
   }
   L.partial = off;
   off += round_up((size_t)G.nblocks * MAX_NV * sizeof(double));
@@ -170,12 +186,14 @@ struct tg_ctx {
   int device;
   char* ws;
   double* a[A_COUNT];
+  float* b32[B_COUNT];   // valid in TG_MIXED only
   double* partial;
   unsigned int* counter;
   CgScal* scal;
   int broken;
   int prev_it_diff;
   int prev_it_elas;
+  int prev_it_inner[2];   // inner FP32 iterations of the first and of later refinement sweeps
   // profiling: launches queued, and optional event timing of the elasticity operator kernel
   long long launches;
   int timing;
@@ -312,9 +330,97 @@ tg_status cn_solve3(tg_ctx* X, tg_stats* stats) {
   return TG_OK;
 }
 
+Elas32 elas32_view(tg_ctx* X) {
+  Elas32 I;
+  I.mu = X->b32[B_MU];
+  I.lam = X->b32[B_LAM];
+  I.eta = X->b32[B_ETA];
+  for (int d = 0; d < 3; ++d) {
+    I.dinv[d] = X->b32[B_DINV0 + d];
+    I.e[d] = X->b32[B_E0 + d];
+    I.r[d] = X->b32[B_R0 + d];
+    I.p[d] = X->b32[B_P0 + d];
+    I.q[d] = X->b32[B_Q0 + d];
+  }
+  I.S = X->scal + 4;
+  I.partial = X->partial;
+  I.counter = X->counter;
+  return I;
+}
+
+// add the event-timed operator launches that did work (the first `did` of `recorded`)
+void harvest_timing(tg_ctx* X, int recorded, int did) {
+  for (int q = 0; q < std::min(recorded, did); ++q) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, X->ev[2 * q], X->ev[2 * q + 1]) == cudaSuccess) {
+      X->t_matvec_ms += ms;
+      X->n_matvec += 1;
+    }
+  }
+}
+
+// TG_MIXED elasticity: iterative refinement with an FP64 residual and FP32 inner PCG.
+tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3], bool minus_b,
+                           double inv_dt, tg_stats* stats) {
+  const Elas E = elas_view(X, u, b_ext);
+  const Elas32 I = elas32_view(X);
+  CgScal* Sout = X->scal + 3;
+  const size_t bytes = (size_t)X->G.nvox * sizeof(double);
+  for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(E.du[d], 0, bytes, X->stream));
+  k_cg_reset<<<1, 32, 0, X->stream>>>(Sout, 1, X->prm.rtol_elas, X->prm.maxit_elas);
+  CK(cudaGetLastError());
+  CK(launch_elas32_coef(X->G, E, I, X->stream));
+  X->launches += 2;
+  int inner_total = 0, sweeps = 0;
+  CgScal out;
+  for (;;) {
+    CK(launch_elas_ir_residual(X->G, E, I, Sout, minus_b, TAU_INNER, X->stream));
+    X->launches += 1;
+    CK(cudaMemcpyAsync(&out, Sout, sizeof(CgScal), cudaMemcpyDeviceToHost, X->stream));
+    CK(cudaStreamSynchronize(X->stream));
+    if (out.status != CG_RUNNING) break;
+    if (sweeps >= MAX_SWEEPS || inner_total >= X->prm.maxit_elas) return fail(X, TG_ERR_NOCONV);
+    CgScal host[1];
+    int recorded = 0;
+    const int slot = sweeps == 0 ? 0 : 1;
+    tg_status s = drive_cg(X, [&](int q) {
+      X->launches += 3;
+      const bool timed = X->timing && ensure_events(X, q + 1);
+      if (timed) {
+        cudaEventRecord(X->ev[2 * q], X->stream);
+        recorded = q + 1;
+      }
+      cudaError_t e = launch_elas32_matvec(X->G, I, X->stream);
+      if (timed) cudaEventRecord(X->ev[2 * q + 1], X->stream);
+      if (e != cudaSuccess) return e;
+      return launch_elas32_update(X->G, I, X->stream);
+    }, I.S, 1, X->prm.maxit_elas, X->prev_it_inner[slot], host);
+    if (s != TG_OK) return s;
+    harvest_timing(X, recorded, host[0].it);
+    X->prev_it_inner[slot] = host[0].it;
+    inner_total += host[0].it;
+    if (host[0].status == CG_NONFINITE) return fail(X, TG_ERR_NONFINITE);
+    CK(launch_elas_ir_correct(X->G, E, I, X->stream));
+    X->launches += 1;
+    ++sweeps;
+  }
+  if (stats) {
+    stats->it_elas = inner_total;
+    stats->it_elas_outer = out.it;
+    stats->relres_elas = out.bb > 0.0 ? sqrt(out.rr / out.bb) : 0.0;
+    stats->it_elas_total += inner_total;
+  }
+  if (out.status == CG_NONFINITE) return fail(X, TG_ERR_NONFINITE);
+  CK(launch_elas_ir_finish(X->G, E, inv_dt, out.status == CG_ZERO_RHS, X->stream));
+  X->launches += 1;
+  CK(cudaStreamSynchronize(X->stream));
+  return TG_OK;
+}
+
 // S6 solve on coefficients already built: (eta I - L_h) u = rhs from the given u.
 tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool minus_b,
                      double inv_dt, tg_stats* stats) {
+  if (X->prec == TG_MIXED) return elas_solve_mixed(X, u, b_ext, minus_b, inv_dt, stats);
   const Elas E = elas_view(X, u, b_ext);
   k_cg_reset<<<1, 32, 0, X->stream>>>(X->scal + 3, 1, X->prm.rtol_elas, X->prm.maxit_elas);
   CK(cudaGetLastError());
@@ -337,13 +443,7 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
   if (s != TG_OK) return s;
   X->prev_it_elas = host[0].it;
   // launches after convergence return at once: only the first `it` did the work
-  for (int q = 0; q < std::min(recorded, host[0].it); ++q) {
-    float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, X->ev[2 * q], X->ev[2 * q + 1]) == cudaSuccess) {
-      X->t_matvec_ms += ms;
-      X->n_matvec += 1;
-    }
-  }
+  harvest_timing(X, recorded, host[0].it);
   if (stats) {
     stats->it_elas = host[0].it;
     stats->it_elas_outer = 1;
@@ -395,12 +495,36 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   const double* const v[3] = {S.v[0], S.v[1], S.v[2]};
   CK(launch_divergence(G, v, X->a[A_DIV], s));
   const double* const qin[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
-  double* const qout[6] = {X->a[A_SL0], X->a[A_SL1], X->a[A_SL2],
-                           X->a[A_SL3], X->a[A_SL4], X->a[A_SL5]};
-  CK(launch_sl_advect(G, dt, v, X->a[A_DIV], qin, qout, s));
-  X->launches += 3;
-  double* const dst[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
-  for (int q = 0; q < 6; ++q) CK(cudaMemcpyAsync(dst[q], qout[q], bytes, cudaMemcpyDeviceToDevice, s));
+  if (X->prec == TG_MIXED) {
+    // FP32 copies of everything the interpolation gathers, then FP32 transport into the state
+    F32Copy cp;
+    const double* src[10] = {S.v[0], S.v[1], S.v[2], X->a[A_DIV], S.p, S.i, S.n, S.g, S.w, S.f};
+    const int dst[10] = {B_V0, B_V1, B_V2, B_DIV, B_SQ0, B_SQ1, B_SQ2, B_SQ3, B_SQ4, B_SQ5};
+    for (int q = 0; q < 10; ++q) {
+      cp.src[q] = src[q];
+      cp.dst[q] = X->b32[dst[q]];
+    }
+    cp.count = 10;
+    CK(launch_to_f32(G.nvox, cp, s));
+    Sl32 T;
+    for (int d = 0; d < 3; ++d) T.v[d] = X->b32[B_V0 + d];
+    T.div = X->b32[B_DIV];
+    double* const outs[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
+    for (int q = 0; q < 6; ++q) {
+      T.q[q] = X->b32[B_SQ0 + q];
+      T.out[q] = outs[q];
+    }
+    CK(launch_sl32(G, dt, T, s));
+    X->launches += 3;
+  } else {
+    double* const qout[6] = {X->a[A_SL0], X->a[A_SL1], X->a[A_SL2],
+                             X->a[A_SL3], X->a[A_SL4], X->a[A_SL5]};
+    CK(launch_sl_advect(G, dt, v, X->a[A_DIV], qin, qout, s));
+    X->launches += 3;
+    double* const dst[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
+    for (int q = 0; q < 6; ++q)
+      CK(cudaMemcpyAsync(dst[q], qout[q], bytes, cudaMemcpyDeviceToDevice, s));
+  }
   // S2: Crank-Nicolson diffusion of i, o, l (i after transport kept for the g, w fix-up)
   CK(cudaMemcpyAsync(X->a[A_IDAG], S.i, bytes, cudaMemcpyDeviceToDevice, s));
   tg_status e = cn_solve3(X, stats);
@@ -420,8 +544,7 @@ extern "C" {
 
 size_t tg_workspace_bytes(const tg_grid* grid, tg_precision prec) {
   if (!grid_ok(grid) || (prec != TG_FP64 && prec != TG_MIXED)) return 0;
-  if (prec != TG_FP64) return 0;
-  return layout(make_geo(grid, sm_count())).total;
+  return layout(make_geo(grid, sm_count()), prec).total;
 }
 
 tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision prec,
@@ -429,14 +552,14 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
                   void* cuda_stream, uint32_t flags, tg_ctx** out, tg_stats* stats) {
   if (out) *out = nullptr;
   if (!out || !grid_ok(grid) || !params_ok(params) || !state) return TG_ERR_ARG;
-  if (prec != TG_FP64) return TG_ERR_ARG;
+  if (prec != TG_FP64 && prec != TG_MIXED) return TG_ERR_ARG;
   const double* must[] = {state->p, state->i, state->n, state->g, state->w, state->f, state->o,
                           state->l, state->bg, state->u[0], state->u[1], state->u[2],
                           state->v[0], state->v[1], state->v[2]};
   for (const double* q : must)
     if (!q || ((uintptr_t)q & 15u)) return TG_ERR_ARG;
   const Geo G = make_geo(grid, sm_count());
-  const Layout L = layout(G);
+  const Layout L = layout(G, prec);
   if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < L.total)
     return TG_ERR_WORKSPACE;
   tg_ctx* X = new (std::nothrow) tg_ctx();
@@ -451,6 +574,8 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
   cudaGetDevice(&X->device);
   X->ws = (char*)workspace;
   for (int a = 0; a < A_COUNT; ++a) X->a[a] = (double*)(X->ws + L.arr[a]);
+  for (int b = 0; b < B_COUNT; ++b)
+    X->b32[b] = prec == TG_MIXED ? (float*)(X->ws + L.arr32[b]) : nullptr;
   X->partial = (double*)(X->ws + L.partial);
   X->counter = (unsigned int*)(X->ws + L.counter);
   X->scal = (CgScal*)(X->ws + L.scal);
@@ -590,7 +715,7 @@ extern "C" tg_status tg_solve_elasticity_static(const tg_grid* grid, const tg_pa
     if (!q || ((uintptr_t)q & 15u)) return TG_ERR_ARG;
   if (rhs && (!rhs[0] || !rhs[1] || !rhs[2])) return TG_ERR_ARG;
   const Geo G = make_geo(grid, sm_count());
-  const Layout L = layout(G);
+  const Layout L = layout(G, TG_FP64);
   if (G.nvox > TG_STATIC_MAX_VOXELS || L.total > (size_t)TG_STATIC_SCRATCH_BYTES)
     return TG_ERR_WORKSPACE;
   int dev = 0;

@@ -15,57 +15,6 @@
 namespace tg {
 namespace {
 
-struct ElasView {
-  const double* mu;
-  const double* lam;
-  const double* F[3];
-  const double* G[3];
-  const double* dsum[3];
-};
-
-__device__ __forceinline__ ElasView view(const Elas& E) {
-  ElasView v;
-  v.mu = E.mu;
-  v.lam = E.lam;
-  for (int d = 0; d < 3; ++d) {
-    v.F[d] = E.F[d];
-    v.G[d] = E.G[d];
-    v.dsum[d] = E.dsum[d];
-  }
-  return v;
-}
-
-// 4 h_A h_D [ d_D(mu d_A u_D) + d_A(lambda d_D u_D) ] at the centre node, centred differences.
-template <int A, int D>
-__device__ __forceinline__ double mixed(const Nbr& nb, const double* __restrict__ xd,
-                                        const double* __restrict__ mu,
-                                        const double* __restrict__ lam) {
-  const double epp = xd[at2<A, D>(nb, +1, +1)];  // c + e_A + e_D
-  const double epm = xd[at2<A, D>(nb, -1, +1)];  // c - e_A + e_D
-  const double emp = xd[at2<A, D>(nb, +1, -1)];  // c + e_A - e_D
-  const double emm = xd[at2<A, D>(nb, -1, -1)];  // c - e_A - e_D
-  return mu[at1<D>(nb, +1)] * (epp - epm) - mu[at1<D>(nb, -1)] * (emp - emm) +
-         lam[at1<A>(nb, +1)] * (epp - emp) - lam[at1<A>(nb, -1)] * (epm - emm);
-}
-
-// component A of (eta I - L_h) x at node c
-template <int A>
-__device__ __forceinline__ double elas_row(const Geo& G, const Nbr& nb, long long c,
-                                           const ElasView& E, const double* const x[3]) {
-  constexpr int D1 = (A + 1) % 3, D2 = (A + 2) % 3;
-  const double* __restrict__ xa = x[A];
-  const double* __restrict__ CA = E.F[A];
-  const double* __restrict__ C1 = E.G[D1];
-  const double* __restrict__ C2 = E.G[D2];
-  double v = E.dsum[A][c] * xa[c];
-  v -= CA[c] * xa[at1<A>(nb, 1)] + CA[at1<A>(nb, -1)] * xa[at1<A>(nb, -1)];
-  v -= C1[c] * xa[at1<D1>(nb, 1)] + C1[at1<D1>(nb, -1)] * xa[at1<D1>(nb, -1)];
-  v -= C2[c] * xa[at1<D2>(nb, 1)] + C2[at1<D2>(nb, -1)] * xa[at1<D2>(nb, -1)];
-  v -= G.s_cross[A][D1] * mixed<A, D1>(nb, x[D1], E.mu, E.lam);
-  v -= G.s_cross[A][D2] * mixed<A, D2>(nb, x[D2], E.mu, E.lam);
-  return v;
-}
-
 __global__ void __launch_bounds__(NT) k_elas_coef(Geo G, DevParams P, Elas E,
                                                   const double* __restrict__ p,
                                                   const double* __restrict__ n, int force) {
@@ -114,7 +63,6 @@ __global__ void __launch_bounds__(NT) k_elas_coef(Geo G, DevParams P, Elas E,
 
 // r = rhs - A u, du = 0, p = D^{-1} r;  rhs = -b (force) or the caller's b.
 __global__ void __launch_bounds__(NT) k_elas_init(Geo G, Elas E, int minus_b) {
-  const ElasView V = view(E);
   const double* const u[3] = {E.u[0], E.u[1], E.u[2]};
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
@@ -126,9 +74,9 @@ __global__ void __launch_bounds__(NT) k_elas_init(Geo G, Elas E, int minus_b) {
       const Nbr nb = make_nbr(G, i, j, k);
       const long long c = nb.at(0, 0, 0);
       double Au[3];
-      Au[0] = elas_row<0>(G, nb, c, V, u);
-      Au[1] = elas_row<1>(G, nb, c, V, u);
-      Au[2] = elas_row<2>(G, nb, c, V, u);
+      Au[0] = elas_row64<0>(G, nb, c, E, u);
+      Au[1] = elas_row64<1>(G, nb, c, E, u);
+      Au[2] = elas_row64<2>(G, nb, c, E, u);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const double rhs = minus_b ? -E.b[a][c] : E.b[a][c];
@@ -150,7 +98,6 @@ __global__ void __launch_bounds__(NT) k_elas_init(Geo G, Elas E, int minus_b) {
 
 __global__ void __launch_bounds__(NT) k_elas_matvec(Geo G, Elas E) {
   if (E.S->status != CG_RUNNING) return;
-  const ElasView V = view(E);
   const double* const p[3] = {E.p[0], E.p[1], E.p[2]};
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
@@ -161,9 +108,9 @@ __global__ void __launch_bounds__(NT) k_elas_matvec(Geo G, Elas E) {
     for (int k = k0; k < k1; ++k) {
       const Nbr nb = make_nbr(G, i, j, k);
       const long long c = nb.at(0, 0, 0);
-      const double q0 = elas_row<0>(G, nb, c, V, p);
-      const double q1 = elas_row<1>(G, nb, c, V, p);
-      const double q2 = elas_row<2>(G, nb, c, V, p);
+      const double q0 = elas_row64<0>(G, nb, c, E, p);
+      const double q1 = elas_row64<1>(G, nb, c, E, p);
+      const double q2 = elas_row64<2>(G, nb, c, E, p);
       E.q[0][c] = q0;
       E.q[1][c] = q1;
       E.q[2][c] = q2;

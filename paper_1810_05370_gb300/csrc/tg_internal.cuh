@@ -207,6 +207,35 @@ struct DevParams {
   double delta_e, delta_half, delta_l;
 };
 
+// ----------------------------------------------------------------------------- FP32 buffers
+
+struct F32Copy {   // up to ten FP64 -> FP32 array conversions in one pass
+  const double* src[10];
+  float* dst[10];
+  int count;
+};
+
+struct Elas32 {    // inner FP32 elasticity solve of the mixed precision
+  float* mu;
+  float* lam;
+  float* eta;
+  float* dinv[3];
+  float* e[3];     // correction (CG iterate)
+  float* r[3];
+  float* p[3];
+  float* q[3];
+  CgScal* S;
+  double* partial;
+  unsigned int* counter;
+};
+
+struct Sl32 {      // FP32 transport: inputs as FP32 copies, outputs to the FP64 state
+  const float* v[3];
+  const float* div;
+  const float* q[6];
+  double* out[6];
+};
+
 // ----------------------------------------------------------------------------- launches
 // All return cudaGetLastError() after queueing on `st`.
 
@@ -264,6 +293,37 @@ struct Elas {
   double* partial;
   unsigned int* counter;
 };
+// 4 h_A h_D [ d_D(mu d_A u_D) + d_A(lambda d_D u_D) ] at the centre node (centred differences)
+template <int A, int D>
+__device__ __forceinline__ double elas_mixed64(const Nbr& nb, const double* __restrict__ xd,
+                                              const double* __restrict__ mu,
+                                              const double* __restrict__ lam) {
+  const double epp = xd[at2<A, D>(nb, +1, +1)];  // c + e_A + e_D
+  const double epm = xd[at2<A, D>(nb, -1, +1)];  // c - e_A + e_D
+  const double emp = xd[at2<A, D>(nb, +1, -1)];  // c + e_A - e_D
+  const double emm = xd[at2<A, D>(nb, -1, -1)];  // c - e_A - e_D
+  return mu[at1<D>(nb, +1)] * (epp - epm) - mu[at1<D>(nb, -1)] * (emp - emm) +
+         lam[at1<A>(nb, +1)] * (epp - emp) - lam[at1<A>(nb, -1)] * (epm - emm);
+}
+
+// component A of (eta I - L_h) x at node c, from the stored FP64 faces and diagonal
+template <int A>
+__device__ __forceinline__ double elas_row64(const Geo& G, const Nbr& nb, long long c,
+                                             const Elas& E, const double* const x[3]) {
+  constexpr int D1 = (A + 1) % 3, D2 = (A + 2) % 3;
+  const double* __restrict__ xa = x[A];
+  const double* __restrict__ CA = E.F[A];
+  const double* __restrict__ C1 = E.G[D1];
+  const double* __restrict__ C2 = E.G[D2];
+  double v = E.dsum[A][c] * xa[c];
+  v -= CA[c] * xa[at1<A>(nb, 1)] + CA[at1<A>(nb, -1)] * xa[at1<A>(nb, -1)];
+  v -= C1[c] * xa[at1<D1>(nb, 1)] + C1[at1<D1>(nb, -1)] * xa[at1<D1>(nb, -1)];
+  v -= C2[c] * xa[at1<D2>(nb, 1)] + C2[at1<D2>(nb, -1)] * xa[at1<D2>(nb, -1)];
+  v -= G.s_cross[A][D1] * elas_mixed64<A, D1>(nb, x[D1], E.mu, E.lam);
+  v -= G.s_cross[A][D2] * elas_mixed64<A, D2>(nb, x[D2], E.mu, E.lam);
+  return v;
+}
+
 cudaError_t launch_elas_coef(const Geo&, const DevParams&, const Elas&, const double* p,
                              const double* n, bool force, cudaStream_t st);
 cudaError_t launch_elas_init(const Geo&, const Elas&, bool rhs_is_minus_b, cudaStream_t st);
@@ -271,5 +331,17 @@ cudaError_t launch_elas_matvec(const Geo&, const Elas&, cudaStream_t st);
 cudaError_t launch_elas_update(const Geo&, const Elas&, cudaStream_t st);   // update + p-update
 cudaError_t launch_elas_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
                                cudaStream_t st);
+
+// mixed precision (tg_mixed.cu)
+cudaError_t launch_to_f32(long long n, const F32Copy& c, cudaStream_t st);
+cudaError_t launch_elas32_coef(const Geo&, const Elas&, const Elas32&, cudaStream_t st);
+cudaError_t launch_elas_ir_residual(const Geo&, const Elas&, const Elas32&, CgScal* Sout,
+                                    bool minus_b, double tau_min, cudaStream_t st);
+cudaError_t launch_elas32_matvec(const Geo&, const Elas32&, cudaStream_t st);
+cudaError_t launch_elas32_update(const Geo&, const Elas32&, cudaStream_t st);  // 2 kernels
+cudaError_t launch_elas_ir_correct(const Geo&, const Elas&, const Elas32&, cudaStream_t st);
+cudaError_t launch_elas_ir_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
+                                  cudaStream_t st);
+cudaError_t launch_sl32(const Geo&, double dt, const Sl32&, cudaStream_t st);
 
 }  // namespace tg

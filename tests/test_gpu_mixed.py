@@ -1,0 +1,99 @@
+"""TG_MIXED (FP32 stencils and interpolation, FP64 residuals and reductions) against the FP64
+oracle and the FP64 GPU path.  Gate: relative L2 <= 1e-5 per field."""
+import numpy as np
+import pytest
+
+from synth import initial_state, workload_params
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("p", "i", "n", "g", "w", "f", "o", "l", "ux", "uy", "uz", "vx", "vy", "vz")
+TOL_MIXED = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def errors(got, ref, fields=FIELDS):
+    return {k: rel_l2(got[k], ref[k]) for k in fields}
+
+
+def run_gpu(n, P, steps, dt, precision, seed=0):
+    from paper_1810_05370_gb300 import Simulation
+    sim = Simulation(n, P, initial_state(n, seed), precision=precision)
+    stats = [sim.step(dt) for _ in range(steps)]
+    out = sim.numpy()
+    init = sim.init_stats
+    sim.close()
+    return out, init, stats
+
+
+def run_oracle(oracle, n, P, steps, dt, seed=0):
+    st = initial_state(n, seed)
+    oracle.init(n, P, st)
+    for _ in range(steps):
+        oracle.step(n, P, dt, st)
+    return st
+
+
+def test_mixed_vs_oracle_32cubed_10_steps(torch_cuda, oracle):
+    n, steps, dt = 32, 10, 0.01
+    P = workload_params()
+    ref = run_oracle(oracle, n, P, steps, dt)
+    got, init, stats = run_gpu(n, P, steps, dt, "mixed")
+    errs = errors(got, ref)
+    print("mixed vs oracle, rel-L2:", {k: f"{v:.1e}" for k, v in errs.items()})
+    print("elasticity inner/outer:", [(s["it_elas"], s["it_elas_outer"]) for s in stats])
+    assert max(errs.values()) <= TOL_MIXED, errs
+    for s in stats:
+        assert s["relres_elas"] <= P["rtol_elas"]
+
+
+def test_mixed_vs_oracle_ragged(torch_cuda, oracle):
+    n, steps, dt = (36, 20, 12), 3, 0.01
+    P = workload_params()
+    ref = run_oracle(oracle, n, P, steps, dt, seed=5)
+    got, _, _ = run_gpu(n, P, steps, dt, "mixed", seed=5)
+    errs = errors(got, ref)
+    assert max(errs.values()) <= TOL_MIXED, errs
+
+
+def test_mixed_solve_elasticity_matches_oracle(torch_cuda, oracle):
+    import torch
+    from paper_1810_05370_gb300 import Simulation
+    n = (40, 24, 16)
+    P = workload_params(rtol_elas=1e-11)
+    st = initial_state(n, seed=2)
+    sim = Simulation(n, P, st, precision="mixed")
+    rng = np.random.default_rng(3)
+    rhs = rng.standard_normal((3, n[2], n[1], n[0]))
+    u_t = [torch.zeros(n[2], n[1], n[0], dtype=torch.float64, device="cuda") for _ in range(3)]
+    stats = sim.solve_elasticity([torch.from_numpy(rhs[a].copy()).cuda() for a in range(3)], u_t)
+    got = np.stack([u.cpu().numpy() for u in u_t])
+    mu, lam, eta = oracle.lame(n, P, st)
+    ref, _, _ = oracle.elasticity_solve(n, mu, lam, eta, rhs, rtol=1e-11)
+    assert stats["relres_elas"] <= 1e-11
+    assert stats["it_elas_outer"] >= 2
+    assert rel_l2(got, ref) <= 1e-8
+
+
+@pytest.mark.slow
+def test_mixed_vs_fp64_256cubed(torch_cuda):
+    """The 256^3 workload: mixed against the FP64 GPU path after 20 steps."""
+    n, steps, dt = 256, 20, 0.01
+    P = workload_params()
+    ref, _, _ = run_gpu(n, P, steps, dt, "fp64")
+    got, _, st = run_gpu(n, P, steps, dt, "mixed")
+    errs = errors(got, ref)
+    print("mixed vs fp64 at 256^3, rel-L2:", {k: f"{v:.1e}" for k, v in errs.items()})
+    assert max(errs.values()) <= TOL_MIXED, errs
