@@ -33,8 +33,9 @@ FIELDS = ("p", "i", "n", "g", "w", "f", "o", "l", "bg", "ux", "uy", "uz", "vx", 
 # Algorithmic traffic and arithmetic of the elasticity operator kernel, per voxel and launch.
 # FP64 path: reads p (3 comps), face coefficients (lambda+2mu)/h^2 and mu/h^2 (3 + 3), Jacobi
 # diagonal (3), node mu and lambda (2); writes q (3): 17 FP64 arrays; 123 FP64 flops.
-# Mixed path: reads p (3) and node mu, lambda, eta (3), writes q (3): 9 FP32 arrays.
-ELAS_MATVEC_BYTES_PER_VOXEL = {"fp64": 17 * 8, "mixed": 9 * 4}
+# Mixed path (the CG p-update is fused into the operator kernel): reads r, D^{-1}, p_old (3 each)
+# and node mu, lambda, eta, writes p_new and q (3 each): 18 FP32 arrays.
+ELAS_MATVEC_BYTES_PER_VOXEL = {"fp64": 17 * 8, "mixed": 18 * 4}
 ELAS_MATVEC_FLOPS_PER_VOXEL = 123
 
 
@@ -257,7 +258,7 @@ def main():
                     "hbm_gbs": gbs, "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"],
                     "share_of_step": share}
         return {"kernel": "k_elas32_matvec (FP32 19-point Navier-Lame operator, faces on the fly, "
-                          "+ <p, Ap>)",
+                          "fused p-update, + <p, Ap>)",
                 "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": gbs / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": f"{peak_src} HBM copy bandwidth",

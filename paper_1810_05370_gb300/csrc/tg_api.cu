@@ -31,7 +31,7 @@ enum Arr {
 // FP32 arrays of the mixed precision (one FP32 value per voxel each)
 enum Arr32 {
   B_MU, B_LAM, B_ETA, B_DINV0, B_DINV1, B_DINV2,
-  B_E0, B_E1, B_E2, B_R0, B_R1, B_R2, B_P0, B_P1, B_P2, B_Q0, B_Q1, B_Q2,
+  B_E0, B_E1, B_E2, B_R0, B_R1, B_R2, B_P0, B_P1, B_P2, B_PB0, B_PB1, B_PB2, B_Q0, B_Q1, B_Q2,
   B_V0, B_V1, B_V2, B_DIV, B_SQ0, B_SQ1, B_SQ2, B_SQ3, B_SQ4, B_SQ5,
   B_COUNT
 };
@@ -339,7 +339,8 @@ Elas32 elas32_view(tg_ctx* X) {
     I.dinv[d] = X->b32[B_DINV0 + d];
     I.e[d] = X->b32[B_E0 + d];
     I.r[d] = X->b32[B_R0 + d];
-    I.p[d] = X->b32[B_P0 + d];
+    I.p[0][d] = X->b32[B_P0 + d];
+    I.p[1][d] = X->b32[B_PB0 + d];
     I.q[d] = X->b32[B_Q0 + d];
   }
   I.S = X->scal + 4;
@@ -384,7 +385,7 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
     int recorded = 0;
     const int slot = sweeps == 0 ? 0 : 1;
     tg_status s = drive_cg(X, [&](int q) {
-      X->launches += 3;
+      X->launches += 2;
       const bool timed = X->timing && ensure_events(X, q + 1);
       if (timed) {
         cudaEventRecord(X->ev[2 * q], X->stream);

@@ -222,7 +222,7 @@ struct Elas32 {    // inner FP32 elasticity solve of the mixed precision
   float* dinv[3];
   float* e[3];     // correction (CG iterate)
   float* r[3];
-  float* p[3];
+  float* p[2][3];  // search direction, double-buffered: iteration k reads p[k&1], writes p[~k&1]
   float* q[3];
   CgScal* S;
   double* partial;
@@ -338,7 +338,7 @@ cudaError_t launch_elas32_coef(const Geo&, const Elas&, const Elas32&, cudaStrea
 cudaError_t launch_elas_ir_residual(const Geo&, const Elas&, const Elas32&, CgScal* Sout,
                                     bool minus_b, double tau_min, cudaStream_t st);
 cudaError_t launch_elas32_matvec(const Geo&, const Elas32&, cudaStream_t st);
-cudaError_t launch_elas32_update(const Geo&, const Elas32&, cudaStream_t st);  // 2 kernels
+cudaError_t launch_elas32_update(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_elas_ir_correct(const Geo&, const Elas&, const Elas32&, cudaStream_t st);
 cudaError_t launch_elas_ir_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
                                   cudaStream_t st);
