@@ -109,18 +109,43 @@ typedef struct {
 /* Bytes of workspace tg_init needs for this grid and precision (0 on invalid arguments). */
 size_t tg_workspace_bytes(const tg_grid* grid, tg_precision prec);
 
+/* Bytes of workspace for a context created with TG_INIT_ADJOINT (adjoint scratch included). */
+size_t tg_workspace_bytes_adjoint(const tg_grid* grid, tg_precision prec);
+
+/* Bytes of one step's tape (the forward values tg_adjoint_step needs): 26 FP64 fields. */
+size_t tg_tape_bytes(const tg_grid* grid);
+
 /* Create a context over the caller's state and workspace and compute the initial
  * displacement u^0 from the initial species (Eq. e:gog_elasticity at t = 0, CG from u = 0),
  * setting v^0 = 0.  With flags & TG_INIT_KEEP_UV the given u, v are kept (resuming from a
- * saved state).  stats may be NULL.  On success *out receives the context. */
+ * saved state).  With flags & TG_INIT_ADJOINT the workspace must hold
+ * tg_workspace_bytes_adjoint() bytes and the context can run tg_adjoint_step.  stats may be
+ * NULL.  On success *out receives the context. */
 #define TG_INIT_KEEP_UV 1u
+#define TG_INIT_ADJOINT 2u
 tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision prec,
                   const tg_state* state, void* workspace, size_t workspace_bytes,
                   void* cuda_stream, uint32_t flags, tg_ctx** out, tg_stats* stats);
 
 /* Advance the state by nsteps steps of size dt (Section 3 multispecies split S0-S7).
- * tape must be NULL (reserved).  stats may be NULL. */
+ * tape is NULL, or (with nsteps == 1) a 256-byte aligned device buffer of tg_tape_bytes()
+ * that receives the step's forward values for tg_adjoint_step.  stats may be NULL. */
 tg_status tg_step(tg_ctx* ctx, double dt, int32_t nsteps, void* tape, tg_stats* stats);
+
+/* Discrete adjoint of one step (the paper's stated next goal, adjoint-based parameter
+ * estimation, Section 5).  tape holds what tg_step recorded for this step.  lam holds the
+ * adjoint of every state field after the step (device arrays, bg ignored) and is
+ * overwritten with the adjoint before the step.  grad[5] (host) is incremented by the step's
+ * contribution to dJ/d(k_scale, rho, o_hyp, o_inv, E_scale), where rho moves rho_g and rho_w
+ * together.  Linear solves are differentiated as exact inverses.  The context must have been
+ * created with TG_INIT_ADJOINT; its state arrays are not used except bg. */
+tg_status tg_adjoint_step(tg_ctx* ctx, double dt, const void* tape, tg_state* lam,
+                          double grad[5]);
+
+/* Contribution of the initial elasticity solve u^0 = M(q^0)^{-1}(-b(q^0)) to grad (only
+ * E_scale enters it), given the adjoint lam_u of u^0.  The context's state must hold q^0 and
+ * u^0.  Needs TG_INIT_ADJOINT. */
+tg_status tg_adjoint_init(tg_ctx* ctx, double* const lam_u[3], double grad[5]);
 
 /* Solve (eta I - L_h) u = rhs with Jacobi-preconditioned CG, coefficients from the current
  * state (Eq. e:lame), starting from the given u.  rhs == NULL means rhs = -b with the force

@@ -16,6 +16,8 @@ TG_OK, TG_ERR_ARG, TG_ERR_CUDA, TG_ERR_NOCONV, TG_ERR_NONFINITE, TG_ERR_TIMEOUT,
     TG_ERR_STATE, TG_ERR_WORKSPACE = range(8)
 TG_FP64, TG_MIXED = 0, 1
 TG_INIT_KEEP_UV = 1
+TG_INIT_ADJOINT = 2
+THETA = ("k_scale", "rho", "o_hyp", "o_inv", "E_scale")
 
 STATUS_NAMES = {
     TG_OK: "TG_OK", TG_ERR_ARG: "TG_ERR_ARG", TG_ERR_CUDA: "TG_ERR_CUDA",
@@ -77,6 +79,11 @@ def _load():
         "tg_solve_elasticity": (C.c_int, [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(tg_stats)]),
         "tg_set_params": (C.c_int, [C.c_void_p, P(tg_params)]),
         "tg_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+        "tg_workspace_bytes_adjoint": (C.c_size_t, [P(tg_grid), C.c_int]),
+        "tg_tape_bytes": (C.c_size_t, [P(tg_grid)]),
+        "tg_adjoint_step": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, P(tg_state),
+                                      P(C.c_double)]),
+        "tg_adjoint_init": (C.c_int, [C.c_void_p, P(C.c_void_p), P(C.c_double)]),
         "tg_solve_elasticity_static": (C.c_int, [P(tg_grid), P(tg_params), P(tg_state),
                                                  P(C.c_void_p), P(C.c_void_p), C.c_void_p,
                                                  P(tg_stats)]),
@@ -150,9 +157,32 @@ def tg_init(grid, params, prec, state, workspace_ptr, workspace_bytes, stream_pt
     return ctx, stats_dict(stats)
 
 
-def tg_step(ctx, dt, nsteps=1):
+def tg_workspace_bytes_adjoint(grid: tg_grid, prec: int) -> int:
+    return int(lib.tg_workspace_bytes_adjoint(C.byref(grid), int(prec)))
+
+
+def tg_tape_bytes(grid: tg_grid) -> int:
+    return int(lib.tg_tape_bytes(C.byref(grid)))
+
+
+def tg_adjoint_step(ctx, dt, tape_ptr, lam: tg_state, grad):
+    """grad: a ctypes double[5] incremented in place."""
+    rc = lib.tg_adjoint_step(ctx, C.c_double(dt), C.c_void_p(tape_ptr), C.byref(lam), grad)
+    if rc != TG_OK:
+        raise TGError(rc, "tg_adjoint_step")
+
+
+def tg_adjoint_init(ctx, lam_u_ptrs, grad):
+    u = (C.c_void_p * 3)(*lam_u_ptrs)
+    rc = lib.tg_adjoint_init(ctx, u, grad)
+    if rc != TG_OK:
+        raise TGError(rc, "tg_adjoint_init")
+
+
+def tg_step(ctx, dt, nsteps=1, tape_ptr=None):
     stats = tg_stats()
-    rc = lib.tg_step(ctx, C.c_double(dt), C.c_int32(nsteps), None, C.byref(stats))
+    rc = lib.tg_step(ctx, C.c_double(dt), C.c_int32(nsteps),
+                     None if tape_ptr is None else C.c_void_p(tape_ptr), C.byref(stats))
     if rc != TG_OK:
         raise TGError(rc, "tg_step")
     return stats_dict(stats)

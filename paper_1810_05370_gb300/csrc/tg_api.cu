@@ -36,6 +36,23 @@ enum Arr32 {
   B_COUNT
 };
 
+// arrays of one step's tape (tg_step with a tape records them; tg_adjoint_step reads them)
+enum TapeArr {
+  T_P, T_I, T_N, T_G, T_W, T_F, T_O, T_L, T_U0, T_U1, T_U2, T_V0, T_V1, T_V2,
+  T_PD, T_ID, T_ND, T_GD, T_WD, T_FP, T_IDD, T_OD, T_LD, T_UP0, T_UP1, T_UP2,
+  T_COUNT
+};
+
+// FP64 scratch of the adjoint (present when the context was created with TG_INIT_ADJOINT)
+enum AdjArr {
+  C_QP0, C_QP1, C_QP2, C_QP3, C_QP4, C_QP5, C_QP6,
+  C_PSI0, C_PSI1, C_PSI2, C_RHS0, C_RHS1, C_RHS2,
+  C_LQ0, C_LQ1, C_LQ2, C_LQ3, C_LQ4, C_LQ5, C_LQ6, C_LF,
+  C_LD0, C_LD1, C_LD2, C_LD3, C_LD4, C_LCN0, C_LCN1, C_LCN2,
+  C_PHI0, C_PHI1, C_PHI2, C_LRHO, C_LDEL, C_LV0, C_LV1, C_LV2,
+  C_COUNT
+};
+
 constexpr size_t ALIGN = 256;
 constexpr int MAX_NV = 9;    // largest number of values reduced by one kernel
 constexpr int N_SCAL = 5;    // 3 diffusion solves, elasticity (outer), elasticity inner FP32
@@ -82,10 +99,11 @@ Geo make_geo(const tg_grid* g, int sms) {
 struct Layout {
   size_t arr[A_COUNT];
   size_t arr32[B_COUNT];
-  size_t partial, counter, scal, total;
+  size_t adj[C_COUNT];
+  size_t partial, counter, scal, grad, total;
 };
 
-Layout layout(const Geo& G, tg_precision prec) {
+Layout layout(const Geo& G, tg_precision prec, bool adjoint = false) {
   Layout L;
   size_t off = 0;
   const size_t abytes = round_up((size_t)G.nvox * sizeof(double));
@@ -98,12 +116,18 @@ Layout layout(const Geo& G, tg_precision prec) {
     L.arr32[b] = off;
     if (prec == TG_MIXED) off += fbytes;
   }
+  for (int c = 0; c < C_COUNT; ++c) {
+    L.adj[c] = off;
+    if (adjoint) off += abytes;
+  }
   L.partial = off;
   off += round_up((size_t)G.nblocks * MAX_NV * sizeof(double));
   L.counter = off;
   off += ALIGN;
   L.scal = off;
   off += round_up(N_SCAL * sizeof(CgScal));
+  L.grad = off;
+  off += ALIGN;
   L.total = off;
   return L;
 }
@@ -187,6 +211,10 @@ struct tg_ctx {
   char* ws;
   double* a[A_COUNT];
   float* b32[B_COUNT];   // valid in TG_MIXED only
+  double* adj[C_COUNT];  // valid with TG_INIT_ADJOINT only
+  bool has_adjoint;
+  double* grad;          // 5 device accumulators of dJ/dtheta
+  double* tape[T_COUNT]; // tape being recorded by the current step, or null
   double* partial;
   unsigned int* counter;
   CgScal* scal;
@@ -483,11 +511,29 @@ void fill_profile(tg_ctx* X, tg_stats* stats) {
 }
 
 // One step of the Section 3 split.
+tg_status record(tg_ctx* X, int slot, const double* src) {
+  if (X->tape[0] == nullptr) return TG_OK;
+  CK(cudaMemcpyAsync(X->tape[slot], src, (size_t)X->G.nvox * sizeof(double),
+                     cudaMemcpyDeviceToDevice, X->stream));
+  return TG_OK;
+}
+
+#define REC(slot, src)                          \
+  do {                                          \
+    tg_status e_ = record(X, (slot), (src));    \
+    if (e_ != TG_OK) return e_;                 \
+  } while (0)
+
 tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   const Geo& G = X->G;
   tg_state& S = X->st;
   cudaStream_t s = X->stream;
   const size_t bytes = (size_t)G.nvox * sizeof(double);
+  {
+    const double* start[14] = {S.p, S.i, S.n, S.g, S.w, S.f, S.o, S.l,
+                               S.u[0], S.u[1], S.u[2], S.v[0], S.v[1], S.v[2]};
+    for (int q = 0; q < 14; ++q) REC(T_P + q, start[q]);
+  }
   // S0: K faces, CN diagonal and rho from the step's start
   double* const Kf[3] = {X->a[A_KF0], X->a[A_KF1], X->a[A_KF2]};
   CK(launch_diff_coef(G, X->dp, dt, S.g, S.w, S.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
@@ -526,17 +572,170 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
     for (int q = 0; q < 6; ++q)
       CK(cudaMemcpyAsync(dst[q], qout[q], bytes, cudaMemcpyDeviceToDevice, s));
   }
+  {
+    const double* sl[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
+    for (int q = 0; q < 6; ++q) REC(T_PD + q, sl[q]);
+  }
   // S2: Crank-Nicolson diffusion of i, o, l (i after transport kept for the g, w fix-up)
   CK(cudaMemcpyAsync(X->a[A_IDAG], S.i, bytes, cudaMemcpyDeviceToDevice, s));
   tg_status e = cn_solve3(X, stats);
   if (e != TG_OK) return e;
+  REC(T_IDD, S.i);
+  REC(T_OD, S.o);
+  REC(T_LD, S.l);
   // S2 fix-up and S3-S5 reactions
   CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l, s));
   X->launches += 1;
   // S6-S7: elasticity from the post-reaction state, then v = du / dt
   e = build_elas_coef(X, true);
   if (e != TG_OK) return e;
-  return elas_solve(X, S.u, nullptr, true, 1.0 / dt, stats);
+  e = elas_solve(X, S.u, nullptr, true, 1.0 / dt, stats);
+  if (e != TG_OK) return e;
+  for (int d = 0; d < 3; ++d) REC(T_UP0 + d, S.u[d]);
+  return TG_OK;
+}
+
+AdjView adj_view(tg_ctx* X, const tg_state* lam) {
+  AdjView A;
+  A.lam.p = lam->p;
+  A.lam.i = lam->i;
+  A.lam.n = lam->n;
+  A.lam.g = lam->g;
+  A.lam.w = lam->w;
+  A.lam.f = lam->f;
+  A.lam.o = lam->o;
+  A.lam.l = lam->l;
+  for (int d = 0; d < 3; ++d) {
+    A.lam.u[d] = lam->u[d];
+    A.lam.v[d] = lam->v[d];
+    A.rhs[d] = X->adj[C_RHS0 + d];
+    A.psi[d] = X->adj[C_PSI0 + d];
+    A.up[d] = nullptr;
+    A.LCN[d] = X->adj[C_LCN0 + d];
+    A.phi[d] = X->adj[C_PHI0 + d];
+    A.LV[d] = X->adj[C_LV0 + d];
+  }
+  for (int q = 0; q < 7; ++q) A.LQ[q] = X->adj[C_LQ0 + q];
+  for (int q = 0; q < 5; ++q) A.LD[q] = X->adj[C_LD0 + q];
+  A.LF = X->adj[C_LF];
+  A.LRHO = X->adj[C_LRHO];
+  A.LDEL = X->adj[C_LDEL];
+  A.grad = X->grad;
+  A.partial = X->partial;
+  A.counter = X->counter;
+  return A;
+}
+
+TapeView tape_view(tg_ctx* X, const void* tape) {
+  const char* base = (const char*)tape;
+  const size_t stride = round_up((size_t)X->G.nvox * sizeof(double));
+  auto at = [&](int q) { return (const double*)(base + (size_t)q * stride); };
+  TapeView T;
+  T.p = at(T_P);
+  T.i = at(T_I);
+  T.n = at(T_N);
+  T.g = at(T_G);
+  T.w = at(T_W);
+  T.f = at(T_F);
+  T.o = at(T_O);
+  T.l = at(T_L);
+  for (int d = 0; d < 3; ++d) {
+    T.u[d] = at(T_U0 + d);
+    T.v[d] = at(T_V0 + d);
+    T.up[d] = at(T_UP0 + d);
+  }
+  T.pdag = at(T_PD);
+  T.idag = at(T_ID);
+  T.ndag = at(T_ND);
+  T.gdag = at(T_GD);
+  T.wdag = at(T_WD);
+  T.fplus = at(T_FP);
+  T.iddag = at(T_IDD);
+  T.odag = at(T_OD);
+  T.ldag = at(T_LD);
+  return T;
+}
+
+tg_status read_grad(tg_ctx* X, double grad[5]) {
+  double g[5];
+  CK(cudaMemcpyAsync(g, X->grad, sizeof(g), cudaMemcpyDeviceToHost, X->stream));
+  CK(cudaStreamSynchronize(X->stream));
+  for (int k = 0; k < 5; ++k) grad[k] += g[k];
+  return TG_OK;
+}
+
+// Adjoint of one step (see tg_adjoint.cu for the order and the formulas).
+tg_status do_adjoint_step(tg_ctx* X, double dt, const void* tape, const tg_state* lam,
+                          double grad[5]) {
+  const Geo& G = X->G;
+  cudaStream_t s = X->stream;
+  const size_t bytes = (size_t)G.nvox * sizeof(double);
+  AdjView A = adj_view(X, lam);
+  const TapeView T = tape_view(X, tape);
+  for (int d = 0; d < 3; ++d) A.up[d] = T.up[d];
+  CK(cudaMemsetAsync(X->grad, 0, 5 * sizeof(double), s));
+  // S7^T and copies of the incoming lambdas
+  CK(launch_adj_prep(G, A, 1.0 / dt, s));
+  // recompute the reacted species q+ from the tape (S0 faces and rho come along)
+  double* qp[7];
+  for (int q = 0; q < 7; ++q) qp[q] = X->adj[C_QP0 + q];
+  const double* src[7] = {T.pdag, T.iddag, T.ndag, T.gdag, T.wdag, T.odag, T.ldag};
+  for (int q = 0; q < 7; ++q) CK(cudaMemcpyAsync(qp[q], src[q], bytes, cudaMemcpyDeviceToDevice, s));
+  double* const Kf[3] = {X->a[A_KF0], X->a[A_KF1], X->a[A_KF2]};
+  CK(launch_diff_coef(G, X->dp, dt, T.g, T.w, T.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
+                      X->a[A_RHO], s));
+  CK(launch_react(G, X->dp, dt, X->a[A_RHO], T.idag, qp[0], qp[1], qp[2], qp[3], qp[4], qp[5],
+                  qp[6], s));
+  // S6^T: coefficients at q+, adjoint solve, sensitivities
+  CK(launch_lame(G, X->dp, qp[0], qp[1], qp[2], qp[3], qp[4], T.fplus, X->st.bg, X->a[A_MU],
+                 X->a[A_LAM], X->a[A_ETA], s));
+  {
+    double* const psi[3] = {A.psi[0], A.psi[1], A.psi[2]};
+    const Elas E = elas_view(X, psi, nullptr);
+    CK(launch_elas_coef(G, X->dp, E, qp[0], qp[2], false, s));
+  }
+  X->launches += 6;
+  for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(A.psi[d], 0, bytes, s));
+  {
+    double* const psi[3] = {A.psi[0], A.psi[1], A.psi[2]};
+    double* const rhs[3] = {A.rhs[0], A.rhs[1], A.rhs[2]};
+    tg_status e = elas_solve(X, psi, rhs, false, 0.0, nullptr);
+    if (e != TG_OK) return e;
+  }
+  const double invE = X->prm.E_scale != 0.0 ? 1.0 / X->prm.E_scale : 0.0;
+  CK(launch_adj_elas_coef(G, X->dp, A, X->a[A_MU], X->a[A_LAM], qp[0], qp[2], invE, true, s));
+  // S5^T, S4^T, S3^T and the fix-up
+  CK(launch_adj_react(G, X->dp, dt, A, T, X->a[A_RHO], s));
+  X->launches += 2;
+  // S2^T: three adjoint Crank-Nicolson solves on the step-start faces
+  {
+    Cn3 C = cn_view(X);
+    for (int r = 0; r < 3; ++r) C.x[r] = A.phi[r];
+    k_cg_reset<<<1, 32, 0, s>>>(X->scal, 3, X->prm.rtol_diff, X->prm.maxit_diff);
+    CK(cudaGetLastError());
+    CK(launch_cn_init_rhs(G, C, A, s));
+    X->launches += 2;
+    CgScal host[3];
+    tg_status e = drive_cg(X, [&](int) {
+      X->launches += 3;
+      return launch_cn_iter(G, C, s);
+    }, X->scal, 3, X->prm.maxit_diff, X->prev_it_diff, host);
+    if (e != TG_OK) return e;
+    for (int r = 0; r < 3; ++r) {
+      tg_status e2 = status_of(host[r]);
+      if (e2 != TG_OK) return fail(X, e2);
+    }
+  }
+  CK(launch_adj_cn_post(G, X->dp, dt, A, T, s));
+  // S1^T: transport transpose (scatter), then div_h^T
+  CK(cudaMemsetAsync(A.LDEL, 0, bytes, s));
+  for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(A.LV[d], 0, bytes, s));
+  const double* const v[3] = {T.v[0], T.v[1], T.v[2]};
+  CK(launch_divergence(G, v, X->a[A_DIV], s));
+  CK(launch_adj_sl(G, dt, A, T, X->a[A_DIV], s));
+  CK(launch_adj_div(G, A, s));
+  X->launches += 4;
+  return read_grad(X, grad);
 }
 
 }  // namespace
@@ -546,6 +745,17 @@ extern "C" {
 size_t tg_workspace_bytes(const tg_grid* grid, tg_precision prec) {
   if (!grid_ok(grid) || (prec != TG_FP64 && prec != TG_MIXED)) return 0;
   return layout(make_geo(grid, sm_count()), prec).total;
+}
+
+size_t tg_workspace_bytes_adjoint(const tg_grid* grid, tg_precision prec) {
+  if (!grid_ok(grid) || (prec != TG_FP64 && prec != TG_MIXED)) return 0;
+  return layout(make_geo(grid, sm_count()), prec, true).total;
+}
+
+size_t tg_tape_bytes(const tg_grid* grid) {
+  if (!grid_ok(grid)) return 0;
+  const size_t v = (size_t)grid->n[0] * grid->n[1] * grid->n[2];
+  return (size_t)T_COUNT * round_up(v * sizeof(double));
 }
 
 tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision prec,
@@ -560,7 +770,8 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
   for (const double* q : must)
     if (!q || ((uintptr_t)q & 15u)) return TG_ERR_ARG;
   const Geo G = make_geo(grid, sm_count());
-  const Layout L = layout(G, prec);
+  const bool adjoint = (flags & TG_INIT_ADJOINT) != 0;
+  const Layout L = layout(G, prec, adjoint);
   if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < L.total)
     return TG_ERR_WORKSPACE;
   tg_ctx* X = new (std::nothrow) tg_ctx();
@@ -577,6 +788,9 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
   for (int a = 0; a < A_COUNT; ++a) X->a[a] = (double*)(X->ws + L.arr[a]);
   for (int b = 0; b < B_COUNT; ++b)
     X->b32[b] = prec == TG_MIXED ? (float*)(X->ws + L.arr32[b]) : nullptr;
+  X->has_adjoint = adjoint;
+  for (int c = 0; c < C_COUNT; ++c) X->adj[c] = adjoint ? (double*)(X->ws + L.adj[c]) : nullptr;
+  X->grad = (double*)(X->ws + L.grad);
   X->partial = (double*)(X->ws + L.partial);
   X->counter = (unsigned int*)(X->ws + L.counter);
   X->scal = (CgScal*)(X->ws + L.scal);
@@ -612,15 +826,23 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
 tg_status tg_step(tg_ctx* X, double dt, int32_t nsteps, void* tape, tg_stats* stats) {
   if (!X) return TG_ERR_ARG;
   if (X->broken) return TG_ERR_STATE;
-  if (!(dt > 0.0) || !isfinite(dt) || nsteps < 0 || tape != nullptr) return TG_ERR_ARG;
+  if (!(dt > 0.0) || !isfinite(dt) || nsteps < 0) return TG_ERR_ARG;
+  if (tape && (nsteps != 1 || ((uintptr_t)tape % ALIGN) != 0)) return TG_ERR_ARG;
   if (stats) memset(stats, 0, sizeof(*stats));
   reset_profile(X);
   CK(cudaSetDevice(X->device));
+  const size_t stride = round_up((size_t)X->G.nvox * sizeof(double));
+  for (int q = 0; q < T_COUNT; ++q)
+    X->tape[q] = tape ? (double*)((char*)tape + (size_t)q * stride) : nullptr;
   for (int32_t s = 0; s < nsteps; ++s) {
     tg_status e = do_step(X, dt, stats);
-    if (e != TG_OK) return fail(X, e);
+    if (e != TG_OK) {
+      X->tape[0] = nullptr;
+      return fail(X, e);
+    }
     if (stats) stats->steps += 1;
   }
+  X->tape[0] = nullptr;
   CK(cudaStreamSynchronize(X->stream));
   if (stats) fill_profile(X, stats);
   return TG_OK;
@@ -639,6 +861,45 @@ tg_status tg_solve_elasticity(tg_ctx* X, double* const rhs[3], double* u[3], tg_
   e = elas_solve(X, uu, rhs, rhs == nullptr, 0.0, stats);
   if (e == TG_OK && stats) fill_profile(X, stats);
   return e;
+}
+
+tg_status tg_adjoint_step(tg_ctx* X, double dt, const void* tape, tg_state* lam, double grad[5]) {
+  if (!X || !tape || !lam || !grad) return TG_ERR_ARG;
+  if (X->broken) return TG_ERR_STATE;
+  if (!X->has_adjoint) return TG_ERR_WORKSPACE;
+  if (!(dt > 0.0) || !isfinite(dt) || ((uintptr_t)tape % ALIGN) != 0) return TG_ERR_ARG;
+  const double* must[] = {lam->p, lam->i, lam->n, lam->g, lam->w, lam->f, lam->o, lam->l,
+                          lam->u[0], lam->u[1], lam->u[2], lam->v[0], lam->v[1], lam->v[2]};
+  for (const double* q : must)
+    if (!q) return TG_ERR_ARG;
+  reset_profile(X);
+  CK(cudaSetDevice(X->device));
+  tg_status e = do_adjoint_step(X, dt, tape, lam, grad);
+  return e == TG_OK ? TG_OK : fail(X, e);
+}
+
+tg_status tg_adjoint_init(tg_ctx* X, double* const lam_u[3], double grad[5]) {
+  if (!X || !lam_u || !lam_u[0] || !lam_u[1] || !lam_u[2] || !grad) return TG_ERR_ARG;
+  if (X->broken) return TG_ERR_STATE;
+  if (!X->has_adjoint) return TG_ERR_WORKSPACE;
+  CK(cudaSetDevice(X->device));
+  const Geo& G = X->G;
+  cudaStream_t s = X->stream;
+  tg_state dummy = X->st;
+  AdjView A = adj_view(X, &dummy);
+  for (int d = 0; d < 3; ++d) A.up[d] = X->st.u[d];
+  CK(cudaMemsetAsync(X->grad, 0, 5 * sizeof(double), s));
+  tg_status e = build_elas_coef(X, false);
+  if (e != TG_OK) return fail(X, e);
+  const size_t bytes = (size_t)G.nvox * sizeof(double);
+  for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(A.psi[d], 0, bytes, s));
+  double* const psi[3] = {A.psi[0], A.psi[1], A.psi[2]};
+  e = elas_solve(X, psi, lam_u, false, 0.0, nullptr);
+  if (e != TG_OK) return fail(X, e);
+  const double invE = X->prm.E_scale != 0.0 ? 1.0 / X->prm.E_scale : 0.0;
+  CK(launch_adj_elas_coef(G, X->dp, A, X->a[A_MU], X->a[A_LAM], X->st.p, X->st.n, invE, false, s));
+  e = read_grad(X, grad);
+  return e == TG_OK ? TG_OK : fail(X, e);
 }
 
 tg_status tg_set_params(tg_ctx* X, const tg_params* params) {

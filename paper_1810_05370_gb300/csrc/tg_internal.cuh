@@ -344,4 +344,52 @@ cudaError_t launch_elas_ir_finish(const Geo&, const Elas&, double inv_dt, bool z
                                   cudaStream_t st);
 cudaError_t launch_sl32(const Geo&, double dt, const Sl32&, cudaStream_t st);
 
+// ----------------------------------------------------------------------------- adjoint
+
+struct LamState {   // the caller's adjoint fields (one per state field; bg has none)
+  double *p, *i, *n, *g, *w, *f, *o, *l;
+  double* u[3];
+  double* v[3];
+};
+
+struct TapeView {   // forward values of one step, recorded by tg_step
+  const double *p, *i, *n, *g, *w, *f, *o, *l;   // state at the step's start
+  const double* u[3];
+  const double* v[3];
+  const double *pdag, *idag, *ndag, *gdag, *wdag, *fplus;   // after transport (S1)
+  const double *iddag, *odag, *ldag;                         // after diffusion (S2)
+  const double* up[3];                                       // u after the elasticity solve
+};
+
+struct AdjView {
+  LamState lam;
+  double* rhs[3];     // right-hand side of the adjoint elasticity solve
+  double* psi[3];     // its solution
+  const double* up[3];
+  double* LQ[7];      // lambda of the reacted p, i, n, g, w, o, l
+  double* LF;         // lambda of f after transport
+  double* LD[5];      // lambda of p, i, n, g, w after transport
+  double* LCN[3];     // lambda of the CN outputs i, o, l
+  double* phi[3];     // adjoint CN solutions
+  double* LRHO;       // lambda of the proliferation field
+  double* LDEL;       // lambda of div v
+  double* LV[3];      // scattered part of lambda_v
+  double* grad;       // dJ/dtheta accumulators (5, device)
+  double* partial;
+  unsigned int* counter;
+};
+
+cudaError_t launch_adj_prep(const Geo&, const AdjView&, double inv_dt, cudaStream_t st);
+cudaError_t launch_adj_elas_coef(const Geo&, const DevParams&, const AdjView&, const double* mu,
+                                 const double* lam, const double* p, const double* n,
+                                 double inv_Escale, bool species, cudaStream_t st);
+cudaError_t launch_adj_react(const Geo&, const DevParams&, double dt, const AdjView&,
+                             const TapeView&, const double* rho, cudaStream_t st);
+cudaError_t launch_cn_init_rhs(const Geo&, const Cn3&, const AdjView&, cudaStream_t st);
+cudaError_t launch_adj_cn_post(const Geo&, const DevParams&, double dt, const AdjView&,
+                               const TapeView&, cudaStream_t st);
+cudaError_t launch_adj_sl(const Geo&, double dt, const AdjView&, const TapeView&,
+                          const double* div, cudaStream_t st);
+cudaError_t launch_adj_div(const Geo&, const AdjView&, cudaStream_t st);
+
 }  // namespace tg

@@ -24,7 +24,7 @@ class Simulation:
     """One simulation on one GPU: `tg_init` at construction, `tg_step` per `step` call."""
 
     def __init__(self, n, params: dict, state: dict, precision: str = "fp64", L=None,
-                 device=None, stream=None, keep_uv: bool = False):
+                 device=None, stream=None, keep_uv: bool = False, adjoint: bool = False):
         torch = _torch()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.grid = _tg.make_grid(n, L)
@@ -39,7 +39,9 @@ class Simulation:
             if tuple(v.shape) != self.shape:
                 raise ValueError(f"state[{k!r}] has shape {tuple(v.shape)}, expected {self.shape}")
             self.state[k] = v
-        nbytes = _tg.tg_workspace_bytes(self.grid, self.prec)
+        self.adjoint = adjoint
+        nbytes = (_tg.tg_workspace_bytes_adjoint if adjoint else _tg.tg_workspace_bytes)(
+            self.grid, self.prec)
         if nbytes == 0:
             raise ValueError("invalid grid or unsupported precision")
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
@@ -50,7 +52,8 @@ class Simulation:
         with torch.cuda.device(self.device):
             self.ctx, self.init_stats = _tg.tg_init(
                 self.grid, self._cparams, self.prec, self._cstate, self.workspace.data_ptr(),
-                nbytes, self.stream.cuda_stream, _tg.TG_INIT_KEEP_UV if keep_uv else 0)
+                nbytes, self.stream.cuda_stream,
+                (_tg.TG_INIT_KEEP_UV if keep_uv else 0) | (_tg.TG_INIT_ADJOINT if adjoint else 0))
 
     def _state_struct(self):
         s = _tg.tg_state()
@@ -61,8 +64,33 @@ class Simulation:
             s.v[a] = self.state["v" + c].data_ptr()
         return s
 
-    def step(self, dt: float, nsteps: int = 1) -> dict:
-        return _tg.tg_step(self.ctx, dt, nsteps)
+    def step(self, dt: float, nsteps: int = 1, tape=None) -> dict:
+        """nsteps steps; with a tape (uint8 CUDA tensor of tape_bytes()), record one step."""
+        return _tg.tg_step(self.ctx, dt, nsteps, None if tape is None else tape.data_ptr())
+
+    def tape_bytes(self) -> int:
+        return _tg.tg_tape_bytes(self.grid)
+
+    def new_tape(self):
+        torch = _torch()
+        return torch.empty(self.tape_bytes(), dtype=torch.uint8, device=self.device)
+
+    def adjoint_step(self, dt: float, tape, lam: dict, grad):
+        """lam: dict of adjoint tensors keyed like the state (bg not needed), in place."""
+        _tg.tg_adjoint_step(self.ctx, dt, tape.data_ptr(), self._lam_struct(lam), grad)
+
+    def adjoint_init(self, lam: dict, grad):
+        _tg.tg_adjoint_init(self.ctx, [lam[k].data_ptr() for k in ("ux", "uy", "uz")], grad)
+
+    @staticmethod
+    def _lam_struct(lam):
+        s = _tg.tg_state()
+        for k in ("p", "i", "n", "g", "w", "f", "o", "l"):
+            setattr(s, k, lam[k].data_ptr())
+        for a, c in enumerate("xyz"):
+            s.u[a] = lam["u" + c].data_ptr()
+            s.v[a] = lam["v" + c].data_ptr()
+        return s
 
     def solve_elasticity(self, rhs=None, u=None) -> dict:
         """Solve (eta I - L_h) u = rhs (rhs=None: the model's -b) into u (default: the state's)."""
