@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-n", type=int, default=128)
+    ap.add_argument("--adjoint-steps", type=int, default=50)
+    ap.add_argument("--adjoint-checkpoint", type=int, default=10)
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     return ap.parse_args()
@@ -311,6 +315,35 @@ def main():
         sim_o.close()
         sim = None
 
+    # ---------------------------------------------------------------- gradient cost (rank 0)
+    adjoint = None
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        from paper_1810_05370_gb300.rollout import Rollout
+        an, asteps = args.adjoint_n, args.adjoint_steps
+        ast0 = initial_state(an, seed=0)
+        sim_f = Simulation(an, P, ast0, precision="fp64", device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sim_f.step(args.dt, nsteps=asteps)
+        torch.cuda.synchronize(dev)
+        t_fwd = time.perf_counter() - t0
+        sim_f.close()
+        t0 = time.perf_counter()
+        ro = Rollout(an, P, ast0, asteps, args.dt, checkpoint_every=args.adjoint_checkpoint)
+        p_final = ro.forward()
+        vol = (2 * np.pi / an) ** 3
+        g = ro.gradient(vol * (p_final - 1.05 * p_final))
+        torch.cuda.synchronize(dev)
+        t_grad = time.perf_counter() - t0
+        ro.close()
+        adjoint = {"grid": an, "steps": asteps, "checkpoint_every": args.adjoint_checkpoint,
+                   "precision": "fp64", "forward_s": t_fwd,
+                   "forward_recompute_adjoint_s": t_grad,
+                   "adjoint_over_forward": t_grad / t_fwd,
+                   "gradient": [float(x) for x in g],
+                   "note": "init (u^0 solve) included in both; misfit against 1.05 p_N"}
+        torch.cuda.empty_cache()
+
     # ---------------------------------------------------------------- CPU baseline (rank 0)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -340,6 +373,7 @@ def main():
                        "it_diff_per_step": agg["it_diff"]},
             "roofline": roof,
             "compare": other,
+            "adjoint": adjoint,
             "mixed_over_fp64": (None if other is None else
                                 (value / other["value"] if args.precision == "mixed"
                                  else other["value"] / value)),

@@ -137,8 +137,10 @@ tg_status tg_step(tg_ctx* ctx, double dt, int32_t nsteps, void* tape, tg_stats* 
  * adjoint of every state field after the step (device arrays, bg ignored) and is
  * overwritten with the adjoint before the step.  grad[5] (host) is incremented by the step's
  * contribution to dJ/d(k_scale, rho, o_hyp, o_inv, E_scale), where rho moves rho_g and rho_w
- * together.  Linear solves are differentiated as exact inverses.  The context must have been
- * created with TG_INIT_ADJOINT; its state arrays are not used except bg. */
+ * together.  Linear solves are differentiated as exact inverses; the adjoint elasticity
+ * solve iterates in FP32 inside FP64 residual refinement and stops at the FP64 tolerance
+ * rtol_elas, like the forward solve of TG_MIXED.  The context must have been created with
+ * TG_INIT_ADJOINT; its state arrays are not used except bg. */
 tg_status tg_adjoint_step(tg_ctx* ctx, double dt, const void* tape, tg_state* lam,
                           double grad[5]);
 

@@ -112,9 +112,10 @@ Layout layout(const Geo& G, tg_precision prec, bool adjoint = false) {
     off += abytes;
   }
   const size_t fbytes = round_up((size_t)G.nvox * sizeof(float));
+  // FP32 arrays: the mixed precision, and the adjoint's refined elasticity solves
   for (int b = 0; b < B_COUNT; ++b) {
     L.arr32[b] = off;
-    if (prec == TG_MIXED) off += fbytes;
+    if (prec == TG_MIXED || adjoint) off += fbytes;
   }
   for (int c = 0; c < C_COUNT; ++c) {
     L.adj[c] = off;
@@ -213,6 +214,7 @@ struct tg_ctx {
   float* b32[B_COUNT];   // valid in TG_MIXED only
   double* adj[C_COUNT];  // valid with TG_INIT_ADJOINT only
   bool has_adjoint;
+  bool psi_valid;        // the adjoint scratch holds the previous adjoint solution (warm start)
   double* grad;          // 5 device accumulators of dJ/dtheta
   double* tape[T_COUNT]; // tape being recorded by the current step, or null
   double* partial;
@@ -695,12 +697,17 @@ tg_status do_adjoint_step(tg_ctx* X, double dt, const void* tape, const tg_state
     CK(launch_elas_coef(G, X->dp, E, qp[0], qp[2], false, s));
   }
   X->launches += 6;
-  for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(A.psi[d], 0, bytes, s));
+  // the previous step's adjoint solution is the starting guess (the solve is differentiated
+  // as an exact inverse, so the guess only changes the iteration count)
+  if (!X->psi_valid)
+    for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(A.psi[d], 0, bytes, s));
   {
     double* const psi[3] = {A.psi[0], A.psi[1], A.psi[2]};
     double* const rhs[3] = {A.rhs[0], A.rhs[1], A.rhs[2]};
-    tg_status e = elas_solve(X, psi, rhs, false, 0.0, nullptr);
+    X->psi_valid = false;
+    tg_status e = elas_solve_mixed(X, psi, rhs, false, 0.0, nullptr);
     if (e != TG_OK) return e;
+    X->psi_valid = true;
   }
   const double invE = X->prm.E_scale != 0.0 ? 1.0 / X->prm.E_scale : 0.0;
   CK(launch_adj_elas_coef(G, X->dp, A, X->a[A_MU], X->a[A_LAM], qp[0], qp[2], invE, true, s));
@@ -787,7 +794,7 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
   X->ws = (char*)workspace;
   for (int a = 0; a < A_COUNT; ++a) X->a[a] = (double*)(X->ws + L.arr[a]);
   for (int b = 0; b < B_COUNT; ++b)
-    X->b32[b] = prec == TG_MIXED ? (float*)(X->ws + L.arr32[b]) : nullptr;
+    X->b32[b] = (prec == TG_MIXED || adjoint) ? (float*)(X->ws + L.arr32[b]) : nullptr;
   X->has_adjoint = adjoint;
   for (int c = 0; c < C_COUNT; ++c) X->adj[c] = adjoint ? (double*)(X->ws + L.adj[c]) : nullptr;
   X->grad = (double*)(X->ws + L.grad);
@@ -892,10 +899,13 @@ tg_status tg_adjoint_init(tg_ctx* X, double* const lam_u[3], double grad[5]) {
   tg_status e = build_elas_coef(X, false);
   if (e != TG_OK) return fail(X, e);
   const size_t bytes = (size_t)G.nvox * sizeof(double);
-  for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(A.psi[d], 0, bytes, s));
+  if (!X->psi_valid)
+    for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(A.psi[d], 0, bytes, s));
   double* const psi[3] = {A.psi[0], A.psi[1], A.psi[2]};
-  e = elas_solve(X, psi, lam_u, false, 0.0, nullptr);
+  X->psi_valid = false;
+  e = elas_solve_mixed(X, psi, lam_u, false, 0.0, nullptr);
   if (e != TG_OK) return fail(X, e);
+  X->psi_valid = true;
   const double invE = X->prm.E_scale != 0.0 ? 1.0 / X->prm.E_scale : 0.0;
   CK(launch_adj_elas_coef(G, X->dp, A, X->a[A_MU], X->a[A_LAM], X->st.p, X->st.n, invE, false, s));
   e = read_grad(X, grad);

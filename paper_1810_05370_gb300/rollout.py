@@ -38,6 +38,25 @@ def theta_of(params: dict):
                      params["E_scale"]], dtype=np.float64)
 
 
+def forward_final_p(n, params: dict, state0: dict, steps: int, dt: float, precision="fp64"):
+    """Final tumor density of a plain forward run (numpy array)."""
+    sim = Simulation(n, params, state0, precision=precision)
+    sim.step(dt, nsteps=steps)
+    p = sim.state["p"].cpu().numpy()
+    sim.close()
+    return p
+
+
+def make_target(n, params: dict, state0: dict, steps: int, dt: float,
+                factors=(1.2, 1.1, 1.02, 1.02, 0.9), noise=0.01, seed=7):
+    """Synthetic observation: the final p of a run at theta_true = theta * factors, plus
+    additive Gaussian noise of standard deviation noise * max(p) (numpy PCG64 seed)."""
+    th = theta_of(params) * np.asarray(factors, dtype=np.float64)
+    p = forward_final_p(n, apply_theta(params, th), state0, steps, dt)
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    return p + noise * float(np.max(p)) * rng.standard_normal(p.shape)
+
+
 class Rollout:
     def __init__(self, n, params: dict, state0: dict, steps: int, dt: float,
                  checkpoint_every: int = 10, precision: str = "fp64", L=None):
@@ -52,12 +71,19 @@ class Rollout:
         for k, v in self.checkpoints[s].items():
             self.sim.state[k].copy_(v)
 
+    def _last_segment(self):
+        return ((self.steps - 1) // self.every) * self.every
+
     def forward(self):
-        """Run the steps; returns the final tumor density p (a CUDA tensor, copied)."""
+        """Run the steps; returns the final tumor density p (a CUDA tensor, copied).  The
+        steps of the last segment record their tapes directly, so the gradient does not
+        replay that segment."""
+        last = self._last_segment()
+        self.tapes = [self.sim.new_tape() for _ in range(min(self.every, self.steps))]
         for s in range(self.steps):
             if s % self.every == 0:
                 self._save(s)
-            self.sim.step(self.dt)
+            self.sim.step(self.dt, tape=self.tapes[s - last] if s >= last else None)
         return self.sim.state["p"].clone()
 
     def gradient(self, lam_p):
@@ -67,12 +93,14 @@ class Rollout:
         lam = {k: torch.zeros_like(sim.state["p"]) for k in ADJ_KEYS}
         lam["p"].copy_(lam_p)
         grad = (C.c_double * 5)()
-        tapes = [sim.new_tape() for _ in range(min(self.every, self.steps))]
+        tapes = self.tapes
+        last = self._last_segment()
         for c0 in reversed(range(0, self.steps, self.every)):
             c1 = min(c0 + self.every, self.steps)
-            self._restore(c0)
-            for s in range(c0, c1):
-                sim.step(self.dt, tape=tapes[s - c0])
+            if c0 != last:                       # the forward pass recorded the last one
+                self._restore(c0)
+                for s in range(c0, c1):
+                    sim.step(self.dt, tape=tapes[s - c0])
             for s in reversed(range(c0, c1)):
                 sim.adjoint_step(self.dt, tapes[s - c0], lam, grad)
         self._restore(0)

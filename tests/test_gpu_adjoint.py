@@ -130,3 +130,44 @@ def test_gradient_matches_oracle_complex_step(torch_cuda):
     gr = np.array([ref[k] for k in THETA])
     print("adjoint:", g, "\ncomplex step:", gr)
     assert np.all(np.abs(g - gr) <= 1e-4 * np.abs(gr) + 1e-9 * np.abs(gr).max()), (g, gr)
+
+
+@pytest.mark.slow
+def test_gradient_128cubed_50_steps_vs_central_differences(torch_cuda):
+    """The adjoint workload: 128^3, 50 steps, checkpoint every 10 steps with recompute; misfit
+    of the final p against a run at perturbed theta plus 1% noise; gradient against central
+    differences at eps = 1e-6 (relative) of FP64 forward runs with rtol 1e-12."""
+    import time
+    import torch
+    from paper_1810_05370_gb300.rollout import (Rollout, apply_theta, forward_final_p,
+                                                make_target, theta_of)
+    n, steps, dt = 128, 50, 0.01
+    P = workload_params(rtol_diff=1e-12, rtol_elas=1e-12, maxit_elas=50000)
+    st0 = initial_state(n, seed=0)
+    target = make_target(n, P, st0, steps, dt)
+    vol = (2 * np.pi / n) ** 3
+    J = lambda p: 0.5 * vol * float(np.sum((p - target) ** 2))  # noqa: E731
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    forward_final_p(n, P, st0, steps, dt)
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ro = Rollout(n, P, st0, steps, dt, checkpoint_every=10)
+    pN = ro.forward()
+    g = ro.gradient(vol * (pN - torch.from_numpy(target).cuda()))
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    ro.close()
+    th0 = theta_of(P)
+    fd = np.zeros(5)
+    for q in range(5):
+        h = 1e-6 * abs(th0[q])
+        tp, tm = th0.copy(), th0.copy()
+        tp[q] += h
+        tm[q] -= h
+        fd[q] = (J(forward_final_p(n, apply_theta(P, tp), st0, steps, dt))
+                 - J(forward_final_p(n, apply_theta(P, tm), st0, steps, dt))) / (2 * h)
+    print("adjoint:", g, "\ncentral differences:", fd,
+          f"\n(forward + recompute + adjoint) / forward = {t_grad / t_plain:.2f}")
+    assert np.all(np.abs(g - fd) <= 1e-4 * np.abs(fd) + 1e-9 * np.abs(fd).max()), (g, fd)

@@ -613,3 +613,24 @@ def test_init_displacement_points_away_from_tumor(oracle):
     mag = np.sqrt((u * u).sum(0))
     sel = mag > 0.3 * mag.max()
     assert np.mean((r * u).sum(0)[sel] > 0) > 0.9
+
+
+# ----------------------------------------------------------------------------- gradients
+
+def test_complex_step_oracle_matches_real_differences():
+    """The complex-step build of the oracle differentiates the same step the real build
+    computes: its gradient of J = 1/2 h^3 |p_N - target|^2 agrees with central differences of
+    the real oracle (hypoxic parameters, so that o_hyp and o_inv matter)."""
+    from oracle import Oracle
+    from oracle.gradient import THETA, central_difference_gradient, complex_step_gradient, run
+    n, steps, dt = (12, 10, 8), 4, 0.02
+    P = workload_params(delta_s=5.0, delta_p=20.0, rtol_diff=1e-14, rtol_elas=1e-14,
+                        maxit_diff=5000, maxit_elas=50000)
+    Pt = dict(P, k_scale=1.2, rho_g=11.0, rho_w=11.0, E_scale=0.9)
+    target = run(Oracle(), n, Pt, steps, dt)["p"]
+    cs = complex_step_gradient(n, P, steps, dt, target)
+    fd = central_difference_gradient(n, P, steps, dt, target, eps=1e-5)
+    scale = max(abs(v) for v in cs.values())
+    for k in THETA:
+        assert abs(cs[k]) > 1e-6 * scale, (k, cs)
+        assert abs(cs[k] - fd[k]) <= 1e-5 * abs(cs[k]) + 1e-9 * scale, (k, cs[k], fd[k])
