@@ -191,6 +191,60 @@ tg_status tg_solve_elasticity_static(const tg_grid* grid, const tg_params* param
                                      const tg_state* state, double* const rhs[3], double* u[3],
                                      void* cuda_stream, tg_stats* stats);
 
+/* ---------------------------------------------------------------------------------------
+ * Batches: many simulations (different grids and parameters) stepped together in TG_MIXED
+ * precision.  Each simulation has its own state (caller-owned, as for tg_init); the batch
+ * runs the Crank-Nicolson and elasticity solves of all simulations in persistent cooperative
+ * kernels that walk one list of (simulation, tile) work items, with per-simulation CG state,
+ * and replays one captured CUDA graph per step (a stream other than the legacy default
+ * stream is needed for the graph; otherwise the same work is launched directly).  Grid-wide
+ * waits inside the persistent kernels are bounded in time (TG_ERR_TIMEOUT). */
+typedef struct tg_batch tg_batch;
+
+typedef struct {
+  int64_t steps;
+  int64_t it_elas_total;    /* inner FP32 elasticity iterations, summed over simulations */
+  int64_t it_elas_max;      /* largest per-simulation count of one step                   */
+  int64_t sweeps_total;     /* refinement sweeps (residual evaluations), summed             */
+  int64_t it_diff_total;    /* CN iterations (three solves), summed                          */
+  double relres_elas_max;   /* largest final |r|/|rhs| of an elasticity solve               */
+  int64_t launches;         /* kernels launched (the graph's count per replay)              */
+  int32_t graph;            /* 1 when the step ran as a replayed CUDA graph                 */
+  int32_t tile_depth;       /* z depth of the work tiles                                    */
+  int32_t coop_blocks;      /* blocks of the persistent elasticity solver                   */
+  int32_t pad;
+} tg_batch_stats;
+
+typedef struct {            /* what tg_batch_autotune measured */
+  int32_t count;
+  int32_t best_zc, best_blocks;
+  int32_t zc[32], blocks[32];
+  float ms[32];
+} tg_batch_tune;
+
+/* Workspace bytes for a batch (per-simulation workspaces plus the batch lists); 0 if invalid.
+ * Only TG_MIXED is supported. */
+size_t tg_batch_workspace_bytes(int32_t nsims, const tg_grid* grids, tg_precision prec);
+
+/* Create the batch: nsims simulations with their own grid, parameters and state; computes
+ * each u^0 (as tg_init).  All work goes to cuda_stream. */
+tg_status tg_batch_init(int32_t nsims, const tg_grid* grids, const tg_params* params,
+                        const tg_state* states, tg_precision prec, void* workspace,
+                        size_t workspace_bytes, void* cuda_stream, tg_batch** out);
+
+/* Choose the work-tile depth and the persistent grid size by timing a short run of the
+ * elasticity inner solver on the current states (which it does not change).  result may be
+ * NULL. */
+tg_status tg_batch_autotune(tg_batch* batch, double dt, tg_batch_tune* result);
+
+/* Advance every simulation by nsteps steps of dt (the split of tg_step). */
+tg_status tg_batch_step(tg_batch* batch, double dt, int32_t nsteps, tg_batch_stats* stats);
+
+/* Time limit of one grid-wide wait in the persistent kernels (default 20 s). */
+tg_status tg_batch_set_timeout(tg_batch* batch, uint64_t timeout_ns);
+
+void tg_batch_free(tg_batch* batch);
+
 /* Release the context (host memory only; the caller's buffers are untouched). */
 void tg_free(tg_ctx* ctx);
 

@@ -58,6 +58,18 @@ class tg_stats(C.Structure):
                 ("t_elas_matvec_ms", C.c_double), ("n_elas_matvec", C.c_int64)]
 
 
+class tg_batch_stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("it_elas_total", C.c_int64), ("it_elas_max", C.c_int64),
+                ("sweeps_total", C.c_int64), ("it_diff_total", C.c_int64),
+                ("relres_elas_max", C.c_double), ("launches", C.c_int64), ("graph", C.c_int32),
+                ("tile_depth", C.c_int32), ("coop_blocks", C.c_int32), ("pad", C.c_int32)]
+
+
+class tg_batch_tune(C.Structure):
+    _fields_ = [("count", C.c_int32), ("best_zc", C.c_int32), ("best_blocks", C.c_int32),
+                ("zc", C.c_int32 * 32), ("blocks", C.c_int32 * 32), ("ms", C.c_float * 32)]
+
+
 class TGError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -87,6 +99,13 @@ def _load():
         "tg_solve_elasticity_static": (C.c_int, [P(tg_grid), P(tg_params), P(tg_state),
                                                  P(C.c_void_p), P(C.c_void_p), C.c_void_p,
                                                  P(tg_stats)]),
+        "tg_batch_workspace_bytes": (C.c_size_t, [C.c_int32, P(tg_grid), C.c_int]),
+        "tg_batch_init": (C.c_int, [C.c_int32, P(tg_grid), P(tg_params), P(tg_state), C.c_int,
+                                    C.c_void_p, C.c_size_t, C.c_void_p, P(C.c_void_p)]),
+        "tg_batch_autotune": (C.c_int, [C.c_void_p, C.c_double, P(tg_batch_tune)]),
+        "tg_batch_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, P(tg_batch_stats)]),
+        "tg_batch_set_timeout": (C.c_int, [C.c_void_p, C.c_uint64]),
+        "tg_batch_free": (None, [C.c_void_p]),
         "tg_free": (None, [C.c_void_p]),
         "tg_error_string": (C.c_char_p, [C.c_int]),
     }
@@ -227,3 +246,48 @@ def tg_solve_elasticity_static(grid, params, state, rhs_ptrs, u_ptrs, stream_ptr
 
 def tg_free(ctx):
     lib.tg_free(ctx)
+
+
+# ----------------------------------------------------------------------------- batches
+
+def tg_batch_workspace_bytes(grids, prec) -> int:
+    arr = (tg_grid * len(grids))(*grids)
+    return int(lib.tg_batch_workspace_bytes(len(grids), arr, int(prec)))
+
+
+def tg_batch_init(grids, params, states, prec, workspace_ptr, workspace_bytes, stream_ptr):
+    n = len(grids)
+    ga, pa, sa = (tg_grid * n)(*grids), (tg_params * n)(*params), (tg_state * n)(*states)
+    out = C.c_void_p()
+    rc = lib.tg_batch_init(n, ga, pa, sa, int(prec), C.c_void_p(workspace_ptr),
+                           C.c_size_t(workspace_bytes), C.c_void_p(stream_ptr), C.byref(out))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_batch_init")
+    return out
+
+
+def tg_batch_autotune(batch, dt):
+    t = tg_batch_tune()
+    rc = lib.tg_batch_autotune(batch, C.c_double(dt), C.byref(t))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_batch_autotune")
+    return {"best_zc": t.best_zc, "best_blocks": t.best_blocks,
+            "candidates": [(t.zc[k], t.blocks[k], float(t.ms[k])) for k in range(t.count)]}
+
+
+def tg_batch_step(batch, dt, nsteps=1):
+    s = tg_batch_stats()
+    rc = lib.tg_batch_step(batch, C.c_double(dt), C.c_int32(nsteps), C.byref(s))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_batch_step")
+    return {f: getattr(s, f) for f, _ in tg_batch_stats._fields_ if f != "pad"}
+
+
+def tg_batch_set_timeout(batch, ns):
+    rc = lib.tg_batch_set_timeout(batch, C.c_uint64(int(ns)))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_batch_set_timeout")
+
+
+def tg_batch_free(batch):
+    lib.tg_batch_free(batch)

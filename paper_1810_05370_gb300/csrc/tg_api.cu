@@ -442,6 +442,7 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
     stats->it_elas_total += inner_total;
   }
   if (out.status == CG_NONFINITE) return fail(X, TG_ERR_NONFINITE);
+  if (out.status == CG_MAXIT) return fail(X, TG_ERR_NOCONV);
   CK(launch_elas_ir_finish(X->G, E, inv_dt, out.status == CG_ZERO_RHS, X->stream));
   X->launches += 1;
   CK(cudaStreamSynchronize(X->stream));
@@ -1021,3 +1022,529 @@ extern "C" tg_status tg_solve_elasticity_static(const tg_grid* grid, const tg_pa
   if (e == TG_OK && stats) fill_profile(&X, stats);
   return e;
 }
+
+// =============================================================================================
+// Batches: many simulations of different grids stepped together.  Each simulation keeps its own
+// context (state, workspace); the batch adds the tile and flat-range lists that let one launch
+// cover all simulations, and runs the solvers as persistent cooperative kernels.  One step is
+// captured once in a CUDA graph and replayed.
+namespace {
+
+constexpr int BATCH_GRAPH_SWEEPS = 6;   // refinement sweeps inside the step graph
+constexpr int BATCH_MAX_SWEEPS = 64;    // total, including sweeps run after the graph
+const int kZcCandidates[] = {4, 8, 16, 32};
+constexpr unsigned long long kDefaultTimeoutNs = 20ULL * 1000 * 1000 * 1000;   // 20 s
+
+struct BatchArea {
+  size_t sims, tile_sim, item_sim, partial, counters, bar, stat, total;
+  size_t partial_per_sim;   // doubles
+};
+
+Geo geo_with_depth(const Geo& G0, int zc) {
+  Geo G = G0;
+  G.zc = std::max(1, std::min(zc, G.nz));
+  const unsigned gz = (unsigned)((G.nz + G.zc - 1) / G.zc);
+  G.grid = dim3(G0.grid.x, G0.grid.y, gz);
+  G.nblocks = (int)(G.grid.x * G.grid.y * gz);
+  return G;
+}
+
+long long flat_items(long long n) {
+  const long long g = n / 4;
+  return std::max(1LL, (g + FLAT_GROUPS - 1) / FLAT_GROUPS);
+}
+
+BatchArea batch_area(int nsims, const tg_grid* grids) {
+  BatchArea A;
+  long long max_tiles_total = 0, items_total = 0, per_sim = 0;
+  for (int s = 0; s < nsims; ++s) {
+    const Geo G = make_geo(&grids[s], sm_count());
+    const Geo Gmin = geo_with_depth(G, kZcCandidates[0]);
+    max_tiles_total += Gmin.nblocks;
+    const long long it = flat_items(G.nvox);
+    items_total += it;
+    per_sim = std::max(per_sim, std::max((long long)Gmin.nblocks, it) * MAX_NV);
+  }
+  size_t off = 0;
+  A.sims = off;
+  off += round_up((size_t)nsims * sizeof(BSim));
+  A.tile_sim = off;
+  off += round_up((size_t)max_tiles_total * sizeof(int));
+  A.item_sim = off;
+  off += round_up((size_t)items_total * sizeof(int));
+  A.partial_per_sim = (size_t)per_sim;
+  A.partial = off;
+  off += round_up((size_t)nsims * per_sim * sizeof(double));
+  A.counters = off;
+  off += round_up((size_t)nsims * 64);
+  A.bar = off;
+  off += ALIGN;
+  A.stat = off;
+  off += round_up((size_t)nsims * sizeof(BatchStat));
+  A.total = off;
+  return A;
+}
+
+// Enqueue S0, S1 and the copy of i before diffusion for one simulation (mixed precision).
+tg_status queue_pre_diffusion(tg_ctx* X, double dt) {
+  const Geo& G = X->G;
+  tg_state& S = X->st;
+  cudaStream_t s = X->stream;
+  const size_t bytes = (size_t)G.nvox * sizeof(double);
+  double* const Kf[3] = {X->a[A_KF0], X->a[A_KF1], X->a[A_KF2]};
+  CK(launch_diff_coef(G, X->dp, dt, S.g, S.w, S.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
+                      X->a[A_RHO], s));
+  const double* const v[3] = {S.v[0], S.v[1], S.v[2]};
+  CK(launch_divergence(G, v, X->a[A_DIV], s));
+  F32Copy cp;
+  const double* src[10] = {S.v[0], S.v[1], S.v[2], X->a[A_DIV], S.p, S.i, S.n, S.g, S.w, S.f};
+  const int dst[10] = {B_V0, B_V1, B_V2, B_DIV, B_SQ0, B_SQ1, B_SQ2, B_SQ3, B_SQ4, B_SQ5};
+  for (int q = 0; q < 10; ++q) {
+    cp.src[q] = src[q];
+    cp.dst[q] = X->b32[dst[q]];
+  }
+  cp.count = 10;
+  CK(launch_to_f32(G.nvox, cp, s));
+  Sl32 T;
+  for (int d = 0; d < 3; ++d) T.v[d] = X->b32[B_V0 + d];
+  T.div = X->b32[B_DIV];
+  double* const outs[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
+  for (int q = 0; q < 6; ++q) {
+    T.q[q] = X->b32[B_SQ0 + q];
+    T.out[q] = outs[q];
+  }
+  CK(launch_sl32(G, dt, T, s));
+  CK(cudaMemcpyAsync(X->a[A_IDAG], S.i, bytes, cudaMemcpyDeviceToDevice, s));
+  return TG_OK;
+}
+
+// Enqueue the fix-up and reactions (S2-S5) and the elasticity coefficients for one simulation.
+tg_status queue_post_diffusion(tg_ctx* X, double dt) {
+  const Geo& G = X->G;
+  tg_state& S = X->st;
+  cudaStream_t s = X->stream;
+  const size_t bytes = (size_t)G.nvox * sizeof(double);
+  CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l, s));
+  tg_status e = build_elas_coef(X, true);
+  if (e != TG_OK) return e;
+  double* const u[3] = {S.u[0], S.u[1], S.u[2]};
+  const Elas E = elas_view(X, u, nullptr);
+  CK(launch_elas32_coef(G, E, elas32_view(X), s));
+  for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(X->a[A_DU0 + d], 0, bytes, s));
+  return TG_OK;
+}
+
+}  // namespace
+
+struct tg_batch {
+  int nsims;
+  cudaStream_t stream;
+  int device;
+  std::vector<tg_ctx*> ctx;
+  char* ws;
+  BatchArea area;
+  std::vector<BSim> h_sims;
+  BSim* d_sims;
+  int* d_tile_sim;
+  int* d_item_sim;
+  double* d_partial;
+  unsigned int* d_counters;
+  unsigned int* d_bar;
+  int* d_err;
+  BatchStat* d_stat;
+  int zc;
+  int coop_cn, coop_el;
+  int ntiles, nitems;
+  unsigned long long timeout_ns;
+  cudaGraphExec_t graph;
+  bool graph_ready;
+  double graph_dt;
+  bool use_graph;
+  int broken;
+  long long launches;
+};
+
+namespace {
+
+tg_status bfail(tg_batch* B, tg_status s) {
+  if (B && s != TG_OK && s != TG_ERR_ARG) B->broken = 1;
+  return s;
+}
+
+#define BCK(call)                          \
+  do {                                     \
+    if ((call) != cudaSuccess) {           \
+      return bfail(B, TG_ERR_CUDA);        \
+    }                                      \
+  } while (0)
+
+BatchDev batch_dev(const tg_batch* B, int maxit) {
+  BatchDev D;
+  D.sims = B->d_sims;
+  D.nsims = B->nsims;
+  D.tile_sim = B->d_tile_sim;
+  D.item_sim = B->d_item_sim;
+  D.ntiles = B->ntiles;
+  D.nitems = B->nitems;
+  D.bar = B->d_bar;
+  D.err = B->d_err;
+  D.timeout_ns = B->timeout_ns;
+  D.maxit = maxit;
+  D.tau_min = TAU_INNER;
+  D.max_sweeps = BATCH_MAX_SWEEPS;
+  return D;
+}
+
+int batch_maxit(const tg_batch* B) {
+  int m = 0;
+  for (const BSim& S : B->h_sims) m = std::max(m, std::max(S.maxit_elas, S.maxit_diff));
+  return m;
+}
+
+// lay the simulations out as tiles of depth zc; upload the descriptors and lists
+tg_status build_tiling(tg_batch* B, int zc) {
+  std::vector<int> tile_sim, item_sim;
+  B->h_sims.resize(B->nsims);
+  for (int s = 0; s < B->nsims; ++s) {
+    tg_ctx* X = B->ctx[s];
+    BSim& S = B->h_sims[s];
+    S.G = geo_with_depth(X->G, zc);
+    S.K = make_consts32(S.G);
+    double* const u[3] = {X->st.u[0], X->st.u[1], X->st.u[2]};
+    S.E = elas_view(X, u, nullptr);
+    S.I = elas32_view(X);
+    S.C = cn_view(X);
+    double* part = B->d_partial + (size_t)s * B->area.partial_per_sim;
+    unsigned int* cnt = B->d_counters + (size_t)s * 16;
+    S.E.partial = S.I.partial = S.C.partial = part;
+    S.E.counter = S.I.counter = S.C.counter = cnt;
+    S.Sout = X->scal + 3;
+    S.tile0 = (int)tile_sim.size();
+    S.ntiles = S.G.nblocks;
+    for (int t = 0; t < S.ntiles; ++t) tile_sim.push_back(s);
+    S.item0 = (int)item_sim.size();
+    S.nitems = (int)flat_items(S.G.nvox);
+    for (int t = 0; t < S.nitems; ++t) item_sim.push_back(s);
+    S.n = S.G.nvox;
+    S.rtol_elas = X->prm.rtol_elas;
+    S.rtol_diff = X->prm.rtol_diff;
+    S.maxit_elas = X->prm.maxit_elas;
+    S.maxit_diff = X->prm.maxit_diff;
+  }
+  B->zc = zc;
+  B->ntiles = (int)tile_sim.size();
+  B->nitems = (int)item_sim.size();
+  BCK(cudaMemcpyAsync(B->d_sims, B->h_sims.data(), B->h_sims.size() * sizeof(BSim),
+                      cudaMemcpyHostToDevice, B->stream));
+  BCK(cudaMemcpyAsync(B->d_tile_sim, tile_sim.data(), tile_sim.size() * sizeof(int),
+                      cudaMemcpyHostToDevice, B->stream));
+  BCK(cudaMemcpyAsync(B->d_item_sim, item_sim.data(), item_sim.size() * sizeof(int),
+                      cudaMemcpyHostToDevice, B->stream));
+  BCK(cudaMemsetAsync(B->d_counters, 0, (size_t)B->nsims * 64, B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  B->graph_ready = false;
+  return TG_OK;
+}
+
+// everything one step queues before the refinement sweeps that run after the graph
+tg_status queue_step(tg_batch* B, double dt) {
+  const BatchDev D = batch_dev(B, batch_maxit(B));
+  BCK(cudaMemsetAsync(B->d_bar, 0, ALIGN, B->stream));
+  BCK(launch_batch_reset(D, B->stream));
+  for (tg_ctx* X : B->ctx) {
+    tg_status e = queue_pre_diffusion(X, dt);
+    if (e != TG_OK) return bfail(B, e);
+  }
+  BCK(launch_batch_cn(D, B->coop_cn, B->stream));
+  for (tg_ctx* X : B->ctx) {
+    tg_status e = queue_post_diffusion(X, dt);
+    if (e != TG_OK) return bfail(B, e);
+  }
+  for (int k = 0; k < BATCH_GRAPH_SWEEPS; ++k) BCK(launch_batch_sweep(D, B->coop_el, B->stream));
+  BCK(launch_batch_status(D, B->d_stat, B->stream));
+  B->launches += 2 + 1 + (long long)B->ctx.size() * 11 + 3LL * BATCH_GRAPH_SWEEPS + 1;
+  return TG_OK;
+}
+
+tg_status capture_step(tg_batch* B, double dt) {
+  if (B->graph_ready) {
+    cudaGraphExecDestroy(B->graph);
+    B->graph_ready = false;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return TG_ERR_CUDA;
+  const long long before = B->launches;
+  const int broken = B->broken;
+  std::vector<int> ctx_broken;
+  for (tg_ctx* X : B->ctx) ctx_broken.push_back(X->broken);
+  tg_status e = queue_step(B, dt);
+  B->launches = before;
+  B->broken = broken;                   // a capture that fails only disables the graph
+  for (size_t k = 0; k < B->ctx.size(); ++k) B->ctx[k]->broken = ctx_broken[k];
+  cudaError_t ce = cudaStreamEndCapture(B->stream, &g);
+  if (e != TG_OK || ce != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return e != TG_OK ? e : TG_ERR_CUDA;
+  }
+  ce = cudaGraphInstantiate(&B->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return TG_ERR_CUDA;
+  }
+  B->graph_ready = true;
+  B->graph_dt = dt;
+  return TG_OK;
+}
+
+tg_status batch_read_status(tg_batch* B, std::vector<BatchStat>& st) {
+  st.resize(B->nsims);
+  BCK(cudaMemcpyAsync(st.data(), B->d_stat, B->nsims * sizeof(BatchStat), cudaMemcpyDeviceToHost,
+                      B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  return TG_OK;
+}
+
+tg_status batch_check_timeout(tg_batch* B) {
+  int err = 0;
+  BCK(cudaMemcpyAsync(&err, B->d_err, sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  return err ? bfail(B, TG_ERR_TIMEOUT) : TG_OK;
+}
+
+tg_status batch_one_step(tg_batch* B, double dt, tg_batch_stats* stats) {
+  if (B->use_graph) {
+    if (!B->graph_ready || B->graph_dt != dt) {
+      tg_status e = capture_step(B, dt);
+      if (e != TG_OK) B->use_graph = false;     // fall back to direct launches
+    }
+  }
+  if (B->use_graph && B->graph_ready) {
+    BCK(cudaGraphLaunch(B->graph, B->stream));
+    B->launches += 2 + 1 + (long long)B->ctx.size() * 11 + 3LL * BATCH_GRAPH_SWEEPS + 1;
+  } else {
+    tg_status e = queue_step(B, dt);
+    if (e != TG_OK) return e;
+  }
+  tg_status e = batch_check_timeout(B);
+  if (e != TG_OK) return e;
+  std::vector<BatchStat> st;
+  e = batch_read_status(B, st);
+  if (e != TG_OK) return e;
+  // refinement sweeps beyond the ones in the graph (rare)
+  const BatchDev D = batch_dev(B, batch_maxit(B));
+  for (int extra = 0; extra < BATCH_MAX_SWEEPS; ++extra) {
+    bool running = false;
+    for (const BatchStat& b : st) running |= b.elas_status == CG_RUNNING;
+    if (!running) break;
+    BCK(cudaMemsetAsync(B->d_bar, 0, ALIGN, B->stream));
+    BCK(launch_batch_sweep(D, B->coop_el, B->stream));
+    BCK(launch_batch_status(D, B->d_stat, B->stream));
+    B->launches += 4;
+    e = batch_check_timeout(B);
+    if (e != TG_OK) return e;
+    e = batch_read_status(B, st);
+    if (e != TG_OK) return e;
+  }
+  for (const BatchStat& b : st) {
+    for (int r = 0; r < 3; ++r) {
+      if (b.cn_status[r] == CG_NONFINITE) return bfail(B, TG_ERR_NONFINITE);
+      if (b.cn_status[r] != CG_CONVERGED && b.cn_status[r] != CG_ZERO_RHS)
+        return bfail(B, TG_ERR_NOCONV);
+    }
+    if (b.elas_status == CG_NONFINITE) return bfail(B, TG_ERR_NONFINITE);
+    if (b.elas_status != CG_CONVERGED && b.elas_status != CG_ZERO_RHS)
+      return bfail(B, TG_ERR_NOCONV);
+  }
+  BCK(launch_batch_finish(D, 1.0 / dt, B->stream));
+  B->launches += 1;
+  BCK(cudaStreamSynchronize(B->stream));
+  if (stats) {
+    stats->steps += 1;
+    for (const BatchStat& b : st) {
+      stats->it_elas_total += b.elas_inner;
+      stats->sweeps_total += b.elas_sweeps;
+      stats->it_diff_total += b.cn_it[0] + b.cn_it[1] + b.cn_it[2];
+      stats->it_elas_max = std::max<int64_t>(stats->it_elas_max, b.elas_inner);
+      stats->relres_elas_max = std::max(stats->relres_elas_max, b.elas_relres);
+    }
+  }
+  return TG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tg_batch_workspace_bytes(int32_t nsims, const tg_grid* grids, tg_precision prec) {
+  if (nsims <= 0 || !grids || prec != TG_MIXED) return 0;
+  size_t total = 0;
+  for (int s = 0; s < nsims; ++s) {
+    const size_t b = tg_workspace_bytes(&grids[s], prec);
+    if (b == 0) return 0;
+    total += round_up(b);
+  }
+  return total + batch_area(nsims, grids).total;
+}
+
+tg_status tg_batch_init(int32_t nsims, const tg_grid* grids, const tg_params* params,
+                        const tg_state* states, tg_precision prec, void* workspace,
+                        size_t workspace_bytes, void* cuda_stream, tg_batch** out) {
+  if (out) *out = nullptr;
+  if (!out || nsims <= 0 || !grids || !params || !states || prec != TG_MIXED) return TG_ERR_ARG;
+  const size_t need = tg_batch_workspace_bytes(nsims, grids, prec);
+  if (need == 0) return TG_ERR_ARG;
+  if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < need)
+    return TG_ERR_WORKSPACE;
+  tg_batch* B = new (std::nothrow) tg_batch();
+  if (!B) return TG_ERR_CUDA;
+  B->nsims = nsims;
+  B->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&B->device);
+  B->timeout_ns = kDefaultTimeoutNs;
+  B->use_graph = true;
+  char* base = (char*)workspace;
+  size_t off = 0;
+  for (int s = 0; s < nsims; ++s) {
+    const size_t b = tg_workspace_bytes(&grids[s], prec);
+    tg_ctx* X = nullptr;
+    tg_status e = tg_init(&grids[s], &params[s], prec, &states[s], base + off, b, cuda_stream, 0,
+                          &X, nullptr);
+    if (e != TG_OK) {
+      for (tg_ctx* c : B->ctx) tg_free(c);
+      delete B;
+      return e;
+    }
+    B->ctx.push_back(X);
+    off += round_up(b);
+  }
+  B->ws = base + off;
+  B->area = batch_area(nsims, grids);
+  B->d_sims = (BSim*)(B->ws + B->area.sims);
+  B->d_tile_sim = (int*)(B->ws + B->area.tile_sim);
+  B->d_item_sim = (int*)(B->ws + B->area.item_sim);
+  B->d_partial = (double*)(B->ws + B->area.partial);
+  B->d_counters = (unsigned int*)(B->ws + B->area.counters);
+  B->d_bar = (unsigned int*)(B->ws + B->area.bar);
+  B->d_err = (int*)(B->ws + B->area.bar + 64);
+  B->d_stat = (BatchStat*)(B->ws + B->area.stat);
+  const int sms = sm_count();
+  B->coop_cn = std::max(1, batch_coop_blocks_per_sm(0)) * sms;
+  B->coop_el = std::max(1, batch_coop_blocks_per_sm(1)) * sms;
+  tg_status e = build_tiling(B, 8);
+  if (e != TG_OK) {
+    tg_batch_free(B);
+    return e;
+  }
+  *out = B;
+  return TG_OK;
+}
+
+tg_status tg_batch_step(tg_batch* B, double dt, int32_t nsteps, tg_batch_stats* stats) {
+  if (!B) return TG_ERR_ARG;
+  if (B->broken) return TG_ERR_STATE;
+  if (!(dt > 0.0) || !isfinite(dt) || nsteps < 0) return TG_ERR_ARG;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  BCK(cudaSetDevice(B->device));
+  B->launches = 0;
+  for (int32_t s = 0; s < nsteps; ++s) {
+    tg_status e = batch_one_step(B, dt, stats);
+    if (e != TG_OK) return bfail(B, e);
+  }
+  if (stats) {
+    stats->launches = B->launches;
+    stats->graph = B->use_graph && B->graph_ready ? 1 : 0;
+    stats->tile_depth = B->zc;
+    stats->coop_blocks = B->coop_el;
+  }
+  return TG_OK;
+}
+
+// Pick the tile depth and the persistent grid size of the elasticity inner solver by timing
+// a bounded number of inner iterations on the current state (only scratch arrays change).
+tg_status tg_batch_autotune(tg_batch* B, double dt, tg_batch_tune* result) {
+  if (!B) return TG_ERR_ARG;
+  if (B->broken) return TG_ERR_STATE;
+  if (!(dt > 0.0)) return TG_ERR_ARG;
+  BCK(cudaSetDevice(B->device));
+  for (tg_ctx* X : B->ctx) {
+    tg_status e = build_elas_coef(X, true);
+    if (e != TG_OK) return bfail(B, e);
+    double* const u[3] = {X->st.u[0], X->st.u[1], X->st.u[2]};
+    BCK(launch_elas32_coef(X->G, elas_view(X, u, nullptr), elas32_view(X), B->stream));
+  }
+  const int sms = sm_count();
+  const int max_bps = std::max(1, batch_coop_blocks_per_sm(1));
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  float best = -1.0f;
+  int best_zc = B->zc, best_blocks = B->coop_el, n = 0;
+  for (int zc : kZcCandidates) {
+    tg_status e = build_tiling(B, zc);
+    if (e != TG_OK) return e;
+    for (int bps = 1; bps <= max_bps; ++bps) {
+      const int blocks = bps * sms;
+      float ms_best = -1.0f;
+      for (int rep = 0; rep < 2; ++rep) {
+        BatchDev D = batch_dev(B, batch_maxit(B));
+        BCK(cudaMemsetAsync(B->d_bar, 0, ALIGN, B->stream));
+        BCK(launch_batch_reset(D, B->stream));
+        BCK(launch_batch_residual(D, B->stream));
+        D.maxit = 16;                                   // a fixed, short inner run
+        BCK(cudaEventRecord(e0, B->stream));
+        BCK(launch_batch_elas_inner(D, blocks, B->stream));
+        BCK(cudaEventRecord(e1, B->stream));
+        BCK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        BCK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms_best < 0.0f || ms < ms_best) ms_best = ms;
+      }
+      if (result && n < 32) {
+        result->zc[n] = zc;
+        result->blocks[n] = blocks;
+        result->ms[n] = ms_best;
+      }
+      ++n;
+      if (best < 0.0f || ms_best < best) {
+        best = ms_best;
+        best_zc = zc;
+        best_blocks = blocks;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tg_status e = batch_check_timeout(B);
+  if (e != TG_OK) return e;
+  e = build_tiling(B, best_zc);
+  if (e != TG_OK) return e;
+  B->coop_el = best_blocks;
+  if (result) {
+    result->count = std::min(n, 32);
+    result->best_zc = best_zc;
+    result->best_blocks = best_blocks;
+  }
+  return TG_OK;
+}
+
+tg_status tg_batch_set_timeout(tg_batch* B, uint64_t timeout_ns) {
+  if (!B || timeout_ns == 0) return TG_ERR_ARG;
+  B->timeout_ns = timeout_ns;
+  if (B->graph_ready) {
+    cudaGraphExecDestroy(B->graph);
+    B->graph_ready = false;
+  }
+  return TG_OK;
+}
+
+void tg_batch_free(tg_batch* B) {
+  if (!B) return;
+  if (B->graph_ready) cudaGraphExecDestroy(B->graph);
+  for (tg_ctx* X : B->ctx) tg_free(X);
+  delete B;
+}
+
+}  // extern "C"

@@ -7,7 +7,7 @@
 //   (A c)_j = c_j + sum_d [ a_d,j (c_j - c_{j+e_d}) + a_d,j-e_d (c_j - c_{j-e_d}) ].
 // The three right-hand sides share the coefficient reads: every kernel below streams the
 // six face values of a node once and applies them to all active solves.
-#include "tg_internal.cuh"
+#include "tg_tiles.cuh"
 
 namespace tg {
 namespace {
@@ -50,54 +50,11 @@ __global__ void __launch_bounds__(NT) k_diff_coef(Geo G, DevParams P, double hal
   }
 }
 
-struct Faces {
-  double xp, xm, yp, ym, zp, zm;
-};
-
-__device__ __forceinline__ Faces load_faces(const Cn3& C, const Nbr& nb, long long c) {
-  Faces F;
-  F.xp = C.Kf[0][c];
-  F.xm = C.Kf[0][nb.at(-1, 0, 0)];
-  F.yp = C.Kf[1][c];
-  F.ym = C.Kf[1][nb.at(0, -1, 0)];
-  F.zp = C.Kf[2][c];
-  F.zm = C.Kf[2][nb.at(0, 0, -1)];
-  return F;
-}
-
-// r0 = rhs - A x0 with x0 = c and rhs = c + s, s = dt/2 D_h c, so r0 = 2 s.
 __global__ void __launch_bounds__(NT) k_cn_init(Geo G, Cn3 C) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const bool on = (i < G.nx) && (j < G.ny);
   double acc[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) acc[q] = 0.0;
-  if (on) {
-    const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
-    for (int k = k0; k < k1; ++k) {
-      const Nbr nb = make_nbr(G, i, j, k);
-      const long long c = nb.at(0, 0, 0);
-      const Faces F = load_faces(C, nb, c);
-      const double di = C.dinv[c];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const double* x = C.x[r];
-        const double xc = x[c];
-        const double s = F.xp * (x[nb.at(1, 0, 0)] - xc) - F.xm * (xc - x[nb.at(-1, 0, 0)]) +
-                         F.yp * (x[nb.at(0, 1, 0)] - xc) - F.ym * (xc - x[nb.at(0, -1, 0)]) +
-                         F.zp * (x[nb.at(0, 0, 1)] - xc) - F.zm * (xc - x[nb.at(0, 0, -1)]);
-        const double rhs = xc + s;
-        const double res = 2.0 * s;
-        const double z = di * res;
-        C.r[r][c] = res;
-        C.p[r][c] = z;
-        acc[3 * r + 0] += rhs * rhs;
-        acc[3 * r + 1] += res * res;
-        acc[3 * r + 2] += res * z;
-      }
-    }
-  }
+  cn_init_tile(G, C, blockIdx.x, blockIdx.y, blockIdx.z, acc);
   double out[9];
   if (reduce_last_block<9>(acc, C.partial, C.counter, out) && threadIdx.x == 0 && threadIdx.y == 0) {
 #pragma unroll
@@ -105,7 +62,6 @@ __global__ void __launch_bounds__(NT) k_cn_init(Geo G, Cn3 C) {
   }
 }
 
-// q = A p and <p, q> for every running solve; then alpha = rz / <p, q>.
 __global__ void __launch_bounds__(NT) k_cn_matvec(Geo G, Cn3 C) {
   bool act[3];
   bool any = false;
@@ -115,30 +71,8 @@ __global__ void __launch_bounds__(NT) k_cn_matvec(Geo G, Cn3 C) {
     any |= act[r];
   }
   if (!any) return;
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const bool on = (i < G.nx) && (j < G.ny);
   double acc[3] = {0.0, 0.0, 0.0};
-  if (on) {
-    const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
-    for (int k = k0; k < k1; ++k) {
-      const Nbr nb = make_nbr(G, i, j, k);
-      const long long c = nb.at(0, 0, 0);
-      const Faces F = load_faces(C, nb, c);
-      const double d = C.dsum[c];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        if (!act[r]) continue;
-        const double* p = C.p[r];
-        const double pc = p[c];
-        const double q = d * pc - (F.xp * p[nb.at(1, 0, 0)] + F.xm * p[nb.at(-1, 0, 0)] +
-                                   F.yp * p[nb.at(0, 1, 0)] + F.ym * p[nb.at(0, -1, 0)] +
-                                   F.zp * p[nb.at(0, 0, 1)] + F.zm * p[nb.at(0, 0, -1)]);
-        C.q[r][c] = q;
-        acc[r] += pc * q;
-      }
-    }
-  }
+  cn_matvec_tile<false>(G, C, act, blockIdx.x, blockIdx.y, blockIdx.z, acc);
   double out[3];
   if (reduce_last_block<3>(acc, C.partial, C.counter, out) && threadIdx.x == 0 && threadIdx.y == 0) {
 #pragma unroll
@@ -150,7 +84,6 @@ __global__ void __launch_bounds__(NT) k_cn_matvec(Geo G, Cn3 C) {
   }
 }
 
-// x += alpha p, r -= alpha q, then <r, D^{-1} r> and <r, r> decide convergence / beta.
 __global__ void __launch_bounds__(NT) k_cn_update(Geo G, Cn3 C) {
   bool act[3];
   double alpha[3];
@@ -162,28 +95,10 @@ __global__ void __launch_bounds__(NT) k_cn_update(Geo G, Cn3 C) {
     any |= act[r];
   }
   if (!any) return;
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const bool on = (i < G.nx) && (j < G.ny);
   double acc[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) acc[q] = 0.0;
-  if (on) {
-    const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
-    for (int k = k0; k < k1; ++k) {
-      const long long c = ((long long)k * G.ny + j) * G.nx + i;
-      const double di = C.dinv[c];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        if (!act[r]) continue;
-        C.x[r][c] += alpha[r] * C.p[r][c];
-        const double res = C.r[r][c] - alpha[r] * C.q[r][c];
-        C.r[r][c] = res;
-        acc[2 * r + 0] += res * (di * res);
-        acc[2 * r + 1] += res * res;
-      }
-    }
-  }
+  cn_update_tile(G, C, act, alpha, blockIdx.x, blockIdx.y, blockIdx.z, acc);
   double out[6];
   if (reduce_last_block<6>(acc, C.partial, C.counter, out) && threadIdx.x == 0 && threadIdx.y == 0) {
 #pragma unroll
@@ -192,7 +107,6 @@ __global__ void __launch_bounds__(NT) k_cn_update(Geo G, Cn3 C) {
   }
 }
 
-// p = D^{-1} r + beta p
 __global__ void __launch_bounds__(NT) k_cn_pupdate(Geo G, Cn3 C) {
   bool act[3];
   double beta[3];
@@ -204,17 +118,7 @@ __global__ void __launch_bounds__(NT) k_cn_pupdate(Geo G, Cn3 C) {
     any |= act[r];
   }
   if (!any) return;
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  if (i >= G.nx || j >= G.ny) return;
-  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
-  for (int k = k0; k < k1; ++k) {
-    const long long c = ((long long)k * G.ny + j) * G.nx + i;
-    const double di = C.dinv[c];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-      if (act[r]) C.p[r][c] = di * C.r[r][c] + beta[r] * C.p[r][c];
-  }
+  cn_pupdate_tile(G, C, act, beta, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace

@@ -101,12 +101,12 @@ __device__ __forceinline__ int block_linear() {
 
 __device__ __forceinline__ int block_count() { return gridDim.x * gridDim.y * gridDim.z; }
 
-// Block-level sum of NV values, written to partial[block][NV]; the last block to finish sums
-// all partials in block order (deterministic) and returns true in every thread of that
-// block, with the totals in out[] valid in thread 0.  counter is reset by the last block.
+// Block-level sum of NV values, written to partial[b][NV] for work item b of nb; the last item
+// to finish sums all partials in item order (deterministic) and returns true in every thread
+// of that block, with the totals in out[] valid in thread 0.  counter is reset by the last.
 template <int NV>
-__device__ bool reduce_last_block(double (&v)[NV], double* partial, unsigned int* counter,
-                                  double (&out)[NV]) {
+__device__ bool reduce_indexed(double (&v)[NV], double* partial, unsigned int* counter, int b,
+                               int nb, double (&out)[NV]) {
   __shared__ double sh[NV][NWARP];
   __shared__ bool am_last;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -117,9 +117,7 @@ __device__ bool reduce_last_block(double (&v)[NV], double* partial, unsigned int
     if (lane == 0) sh[q][warp] = s;
   }
   __syncthreads();
-  const int nb = block_count();
   if (tid == 0) {
-    const int b = block_linear();
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       double s = 0.0;
@@ -136,9 +134,9 @@ __device__ bool reduce_last_block(double (&v)[NV], double* partial, unsigned int
   double acc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-  for (int b = tid; b < nb; b += NT) {
+  for (int k = tid; k < nb; k += NT) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) acc[q] += __ldcg(partial + (size_t)b * NV + q);
+    for (int q = 0; q < NV; ++q) acc[q] += __ldcg(partial + (size_t)k * NV + q);
   }
   __syncthreads();
 #pragma unroll
@@ -156,7 +154,15 @@ __device__ bool reduce_last_block(double (&v)[NV], double* partial, unsigned int
     }
     *counter = 0u;
   }
+  __syncthreads();
   return true;
+}
+
+// the same over the blocks of a launch
+template <int NV>
+__device__ bool reduce_last_block(double (&v)[NV], double* partial, unsigned int* counter,
+                                  double (&out)[NV]) {
+  return reduce_indexed<NV>(v, partial, counter, block_linear(), block_count(), out);
 }
 
 // Convergence decision after an update (same order of tests as a textbook PCG loop:
@@ -343,6 +349,67 @@ cudaError_t launch_elas_ir_correct(const Geo&, const Elas&, const Elas32&, cudaS
 cudaError_t launch_elas_ir_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
                                   cudaStream_t st);
 cudaError_t launch_sl32(const Geo&, double dt, const Sl32&, cudaStream_t st);
+
+// ----------------------------------------------------------------------------- batches
+
+struct Consts32 {   // FP32 copies of the grid constants the FP32 operator needs
+  float ih2[3];
+  float sc[3][3];
+};
+
+inline Consts32 make_consts32(const Geo& G) {
+  Consts32 K;
+  for (int d = 0; d < 3; ++d) K.ih2[d] = (float)G.ih2[d];
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) K.sc[a][d] = (float)G.s_cross[a][d];
+  return K;
+}
+
+constexpr long long FLAT_GROUPS = 8LL * NT;   // float4 groups per flat work item
+
+struct BSim {       // one simulation of a batch, as the batched kernels see it
+  Geo G;            // its grid, with the batch's tile depth
+  Consts32 K;
+  Elas E;           // FP64 elasticity view (faces, u, force, du)
+  Elas32 I;         // FP32 inner solve (I.S: inner CG scalars)
+  Cn3 C;            // the three diffusion solves
+  CgScal* Sout;     // outer (refinement) scalars of the elasticity solve
+  int tile0, ntiles;   // its grid tiles in the batch's tile list
+  int item0, nitems;   // its flat ranges in the batch's flat list
+  long long n;
+  double rtol_elas, rtol_diff;
+  int maxit_elas, maxit_diff;
+};
+
+struct BatchDev {
+  const BSim* sims;
+  int nsims;
+  const int* tile_sim;   // tile list -> simulation
+  const int* item_sim;   // flat list -> simulation
+  int ntiles, nitems;
+  unsigned int* bar;     // [0] arrivals, [1] generation
+  int* err;              // set by a barrier wait that ran out of time
+  unsigned long long timeout_ns;
+  int maxit;             // bound on the iterations of one persistent solve
+  double tau_min;
+  int max_sweeps;
+};
+
+struct BatchStat {
+  int elas_status, elas_sweeps, elas_inner, pad;
+  double elas_relres;
+  int cn_status[3], cn_it[3];
+  double cn_relres[3];
+};
+
+int batch_coop_blocks_per_sm(int which);   // 0: diffusion solver, 1: elasticity inner solver
+cudaError_t launch_batch_reset(const BatchDev&, cudaStream_t st);
+cudaError_t launch_batch_status(const BatchDev&, BatchStat* out, cudaStream_t st);
+cudaError_t launch_batch_cn(const BatchDev&, int coop_blocks, cudaStream_t st);
+cudaError_t launch_batch_sweep(const BatchDev&, int coop_blocks, cudaStream_t st);
+cudaError_t launch_batch_elas_inner(const BatchDev&, int coop_blocks, cudaStream_t st);
+cudaError_t launch_batch_residual(const BatchDev&, cudaStream_t st);
+cudaError_t launch_batch_finish(const BatchDev&, double inv_dt, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- adjoint
 

@@ -1,0 +1,520 @@
+// tg_tiles.cuh -- per-tile building blocks of the iterative solvers (Crank-Nicolson diffusion
+// CG, FP32 elasticity CG, FP64 refinement) shared by the per-simulation kernels
+// (tg_diffusion.cu, tg_mixed.cu) and the batched persistent solvers (tg_batch.cu).
+#pragma once
+
+#include "tg_internal.cuh"
+
+namespace tg {
+
+// The operator kernel is tiled: a block owns a 32 x 8 column of nodes and marches it through
+// its z range, keeping three planes (k-1, k, k+1) of the search direction and of the node
+// mu, lambda in shared memory with a one-node halo (34 x 10 per plane).  The search direction
+// is formed while the plane is staged, p_new = D^{-1} r + beta p_old (the CG p-update of the
+// previous iteration), written once per node and double-buffered so that neighbouring blocks
+// still read p_old.  Each node is then read from global memory about 1.4 times (halo and
+// z-overlap) instead of about 60 times.
+constexpr int HX = BX + 2;
+constexpr int HY = BY + 2;
+constexpr int HXY = HX * HY;
+
+struct Tile32 {
+  float p[3][3][HXY];  // [plane slot][component][node]
+  float mu[3][HXY];
+  float la[3][HXY];
+};
+
+
+__device__ __forceinline__ bool running(const CgScal* S) { return S->status == CG_RUNNING; }
+
+// Loads of data that other blocks of the same (persistent) kernel may have written go to L2
+// (COH = true); otherwise they may use the read-only path.
+template <bool COH>
+__device__ __forceinline__ float ldf(const float* p) {
+  return COH ? __ldcg(p) : __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ float4 ldf4(const float4* p) {
+  return COH ? __ldcg(p) : __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ double ldd(const double* p) {
+  return COH ? __ldcg(p) : *p;
+}
+
+// CG scalars shared between blocks of a persistent kernel: copy in and out through volatile
+// accesses (never from a possibly stale L1 line)
+__device__ __forceinline__ CgScal ld_cg(const CgScal* p) {
+  const volatile CgScal* v = p;
+  CgScal s;
+  s.rz = v->rz;
+  s.rr = v->rr;
+  s.bb = v->bb;
+  s.pq = v->pq;
+  s.alpha = v->alpha;
+  s.beta = v->beta;
+  s.rtol = v->rtol;
+  s.it = v->it;
+  s.maxit = v->maxit;
+  s.status = v->status;
+  s.pad = v->pad;
+  return s;
+}
+__device__ __forceinline__ void st_cg(CgScal* p, const CgScal& s) {
+  volatile CgScal* v = p;
+  v->rz = s.rz;
+  v->rr = s.rr;
+  v->bb = s.bb;
+  v->pq = s.pq;
+  v->alpha = s.alpha;
+  v->beta = s.beta;
+  v->rtol = s.rtol;
+  v->it = s.it;
+  v->maxit = s.maxit;
+  v->status = s.status;
+  v->pad = s.pad;
+}
+
+
+// Pointers to the centre node of one thread in each staged plane: p (3 components), mu and
+// lambda of planes k-1, k, k+1; neighbours are then constant offsets (+-1, +-HX).
+struct Cell {
+  const float* p[3][3];   // [plane -1, 0, +1][component]
+  const float* mu[3];
+  const float* la[3];
+};
+
+__device__ __forceinline__ float tp(const Tile32&, const Cell& t, int a, int ox, int oy, int oz) {
+  return t.p[oz + 1][a][ox + oy * HX];
+}
+__device__ __forceinline__ float tmu(const Tile32&, const Cell& t, int ox, int oy, int oz) {
+  return t.mu[oz + 1][ox + oy * HX];
+}
+__device__ __forceinline__ float tla(const Tile32&, const Cell& t, int ox, int oy, int oz) {
+  return t.la[oz + 1][ox + oy * HX];
+}
+
+struct Fac32 {
+  float Fp[3], Fm[3];   // (lambda + 2 mu) faces / h_d^2 at +e_d and -e_d
+  float Gp[3], Gm[3];   // mu faces / h_d^2
+  float mup[3], mum[3]; // node mu at c +/- e_d
+  float lap[3], lam[3]; // node lambda at c +/- e_d
+  float eta;
+};
+
+__device__ __forceinline__ void tile_fac(const Tile32& T, const Cell& t, const float ih2[3],
+                                         float eta, Fac32& f) {
+  const float muc = tmu(T, t, 0, 0, 0), lac = tla(T, t, 0, 0, 0);
+  f.eta = eta;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int ox = d == 0, oy = d == 1, oz = d == 2;
+    f.mup[d] = tmu(T, t, ox, oy, oz);
+    f.mum[d] = tmu(T, t, -ox, -oy, -oz);
+    f.lap[d] = tla(T, t, ox, oy, oz);
+    f.lam[d] = tla(T, t, -ox, -oy, -oz);
+    const float gp = 0.5f * (muc + f.mup[d]), gm = 0.5f * (f.mum[d] + muc);
+    const float lp = 0.5f * (lac + f.lap[d]), lm = 0.5f * (f.lam[d] + lac);
+    f.Gp[d] = gp * ih2[d];
+    f.Gm[d] = gm * ih2[d];
+    f.Fp[d] = (lp + 2.0f * gp) * ih2[d];
+    f.Fm[d] = (lm + 2.0f * gm) * ih2[d];
+  }
+}
+
+// component A of (eta I - L_h) p at the centre node, all operands from the tile
+template <int A>
+__device__ __forceinline__ float row_tile(const Tile32& T, const Cell& t, const Fac32& f,
+                                          const float sc[3][3]) {
+  constexpr int D1 = (A + 1) % 3, D2 = (A + 2) % 3;
+  float diag = f.eta, off = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int ox = d == 0, oy = d == 1, oz = d == 2;
+    const float cp = (d == A) ? f.Fp[d] : f.Gp[d];
+    const float cm = (d == A) ? f.Fm[d] : f.Gm[d];
+    diag += cp + cm;
+    off += cp * tp(T, t, A, ox, oy, oz) + cm * tp(T, t, A, -ox, -oy, -oz);
+  }
+  float v = diag * tp(T, t, A, 0, 0, 0) - off;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int D = k == 0 ? D1 : D2;
+    // offsets of c + sa e_A + sd e_D
+    const int ax = A == 0, ay = A == 1, az = A == 2;
+    const int dx = D == 0, dy = D == 1, dz = D == 2;
+    const float epp = tp(T, t, D, ax + dx, ay + dy, az + dz);
+    const float epm = tp(T, t, D, -ax + dx, -ay + dy, -az + dz);
+    const float emp = tp(T, t, D, ax - dx, ay - dy, az - dz);
+    const float emm = tp(T, t, D, -ax - dx, -ay - dy, -az - dz);
+    const float mixed = f.mup[D] * (epp - epm) - f.mum[D] * (emp - emm) +
+                        f.lap[A] * (epp - emp) - f.lam[A] * (epm - emm);
+    v -= sc[A][D] * mixed;
+  }
+  return v;
+}
+
+// One tile (bx, by, bz) of the FP32 operator with the fused p-update, for CG iteration `it`
+// with coefficient beta; returns this thread's FP32 part of <p_new, A p_new>.  T is the
+// block's shared staging area.
+template <bool COH>
+__device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32& K,
+                                                    const Elas32& I, int it, double beta_d,
+                                                    int bx, int by, int bz, Tile32& T) {
+  const bool first = it == 0;                 // p = D^{-1} r (the old p is undefined)
+  const float beta = first ? 0.0f : (float)beta_d;
+  const float* __restrict__ po[3] = {I.p[it & 1][0], I.p[it & 1][1], I.p[it & 1][2]};
+  float* pn[3] = {I.p[(it & 1) ^ 1][0], I.p[(it & 1) ^ 1][1], I.p[(it & 1) ^ 1][2]};
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int i0 = bx * BX, j0 = by * BY;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool on = (i < G.nx) && (j < G.ny);
+  const int k0 = bz * G.zc, k1 = min(G.nz, k0 + G.zc);
+
+  // the (at most two) halo-tile nodes this thread stages: tile slot tid and tid + NT; their
+  // wrapped (x, y) offsets (full modulo: a tile may be wider than the grid)
+  auto wrapped = [&](int s) {
+    int gi = (i0 - 1 + s % HX) % G.nx, gj = (j0 - 1 + s / HX) % G.ny;
+    gi = gi < 0 ? gi + G.nx : gi;
+    gj = gj < 0 ? gj + G.ny : gj;
+    return (long long)gj * G.nx + gi;
+  };
+  const int hs1 = tid + NT;
+  const bool two = hs1 < HXY;
+  const long long ho0 = wrapped(tid);
+  const long long ho1 = two ? wrapped(hs1) : 0;
+
+  // a staged node: the three components of p_new and the node mu, lambda
+  struct Staged {
+    float p[3], mu, la;
+  };
+  auto fetch = [&](long long g, Staged& v) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float z = __ldg(I.dinv[a] + g) * ldf<COH>(I.r[a] + g);
+      v.p[a] = first ? z : z + beta * ldf<COH>(po[a] + g);
+    }
+    v.mu = __ldg(I.mu + g);
+    v.la = __ldg(I.lam + g);
+  };
+  auto put = [&](const Staged& v, int slot, int s) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) T.p[slot][a][s] = v.p[a];
+    T.mu[slot][s] = v.mu;
+    T.la[slot][s] = v.la;
+  };
+  auto plane_offset = [&](int kk) {
+    const int kw = kk < 0 ? kk + G.nz : (kk >= G.nz ? kk - G.nz : kk);
+    return (long long)kw * G.nxy;
+  };
+  // registers carry plane k+2 while plane k is computed (loads overlap the arithmetic)
+  Staged r0, r1;
+  {
+    long long zo = plane_offset(k0 - 1);
+    fetch(zo + ho0, r0);
+    if (two) fetch(zo + ho1, r1);
+    put(r0, 0, tid);
+    if (two) put(r1, 0, hs1);
+    zo = plane_offset(k0);
+    fetch(zo + ho0, r0);
+    if (two) fetch(zo + ho1, r1);
+    put(r0, 1, tid);
+    if (two) put(r1, 1, hs1);
+    zo = plane_offset(k0 + 1);
+    fetch(zo + ho0, r0);
+    if (two) fetch(zo + ho1, r1);
+    put(r0, 2, tid);
+    if (two) put(r1, 2, hs1);
+  }
+
+  float part = 0.0f;
+  const int ci = (ty + 1) * HX + (tx + 1);
+  int s0 = 0, s1 = 1, s2 = 2;            // slots of planes k-1, k, k+1
+  for (int k = k0; k < k1; ++k) {
+    Cell t;
+    const int sl[3] = {s0, s1, s2};
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) t.p[o][a] = &T.p[sl[o]][a][ci];
+      t.mu[o] = &T.mu[sl[o]][ci];
+      t.la[o] = &T.la[sl[o]][ci];
+    }
+    const bool more = k + 1 < k1;
+    if (more) {                         // issue the loads of plane k+2
+      const long long zo = plane_offset(k + 2);
+      fetch(zo + ho0, r0);
+      if (two) fetch(zo + ho1, r1);
+    }
+    __syncthreads();
+    if (on) {
+      const long long c = (long long)k * G.nxy + (long long)j * G.nx + i;
+      Fac32 f;
+      tile_fac(T, t, K.ih2, __ldg(I.eta + c), f);
+      const float q0 = row_tile<0>(T, t, f, K.sc);
+      const float q1 = row_tile<1>(T, t, f, K.sc);
+      const float q2 = row_tile<2>(T, t, f, K.sc);
+      const float p0 = tp(T, t, 0, 0, 0, 0), p1 = tp(T, t, 1, 0, 0, 0), p2 = tp(T, t, 2, 0, 0, 0);
+      pn[0][c] = p0;
+      pn[1][c] = p1;
+      pn[2][c] = p2;
+      I.q[0][c] = q0;
+      I.q[1][c] = q1;
+      I.q[2][c] = q2;
+      part += p0 * q0 + p1 * q1 + p2 * q2;
+    }
+    __syncthreads();
+    if (more) {                         // plane k-1 is free: it becomes plane k+2
+      put(r0, s0, tid);
+      if (two) put(r1, s0, hs1);
+    }
+    const int sf = s0;                  // rotate: (k-1, k, k+1) <- (k, k+1, k+2)
+    s0 = s1;
+    s1 = s2;
+    s2 = sf;
+  }
+  return part;
+}
+
+// e += alpha p, r -= alpha q (p as written by this iteration's operator kernel, buffer pb),
+// over float4 groups g = g0, g0 + gs, ... < g1 of an n-voxel system, plus the scalar tail
+// n - n % 4 .. n when `tail` is set; accumulates <r, D^{-1} r> and <r, r>: the twelve products
+// of one group summed in FP32, the groups in FP64.
+template <bool COH>
+__device__ __forceinline__ void elas32_update_range(const Elas32& I, long long n, long long g0,
+                                                    long long g1, long long gs, float alpha,
+                                                    int pb, bool tail, double& drz,
+                                                    double& drr) {
+  for (long long v = g0; v < g1; v += gs) {
+    float prz = 0.0f, prr = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float4* e4 = reinterpret_cast<float4*>(I.e[a]) + v;
+      float4* r4 = reinterpret_cast<float4*>(I.r[a]) + v;
+      const float4 p = ldf4<COH>(reinterpret_cast<const float4*>(I.p[pb][a]) + v);
+      const float4 q = ldf4<COH>(reinterpret_cast<const float4*>(I.q[a]) + v);
+      const float4 d = __ldg(reinterpret_cast<const float4*>(I.dinv[a]) + v);
+      float4 e = *e4, r = *r4;
+      e.x += alpha * p.x; e.y += alpha * p.y; e.z += alpha * p.z; e.w += alpha * p.w;
+      r.x -= alpha * q.x; r.y -= alpha * q.y; r.z -= alpha * q.z; r.w -= alpha * q.w;
+      *e4 = e;
+      *r4 = r;
+      prz += r.x * (d.x * r.x) + r.y * (d.y * r.y) + r.z * (d.z * r.z) + r.w * (d.w * r.w);
+      prr += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+    }
+    drz += (double)prz;
+    drr += (double)prr;
+  }
+  if (tail) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    for (long long c = 4 * (n / 4) + tid; c < n; c += nth) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        I.e[a][c] += alpha * ldf<COH>(I.p[pb][a] + c);
+        const float res = I.r[a][c] - alpha * ldf<COH>(I.q[a] + c);
+        I.r[a][c] = res;
+        drz += (double)(res * (I.dinv[a][c] * res));
+        drr += (double)(res * res);
+      }
+    }
+  }
+}
+
+
+// FP64 residual r = rhs - A u over one tile; writes the FP32 inner right-hand side r and
+// zeroes the FP32 correction e; accumulates (|rhs|^2, |r|^2, <r, D^{-1} r>).
+__device__ __forceinline__ void elas_ir_residual_tile(const Geo& G, const Elas& E, const Elas32& I,
+                                                      int minus_b, int bx, int by, int bz,
+                                                      double (&acc)[3]) {
+  const double* const u[3] = {E.u[0], E.u[1], E.u[2]};
+  const int i = bx * BX + threadIdx.x;
+  const int j = by * BY + threadIdx.y;
+  if (i < G.nx && j < G.ny) {
+    const int k0 = bz * G.zc, k1 = min(G.nz, k0 + G.zc);
+    for (int k = k0; k < k1; ++k) {
+      const Nbr nb = make_nbr(G, i, j, k);
+      const long long c = nb.at(0, 0, 0);
+      double Au[3];
+      Au[0] = elas_row64<0>(G, nb, c, E, u);
+      Au[1] = elas_row64<1>(G, nb, c, E, u);
+      Au[2] = elas_row64<2>(G, nb, c, E, u);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double rhs = minus_b ? -E.b[a][c] : E.b[a][c];
+        const double res = rhs - Au[a];
+        const float r32 = (float)res;
+        const float z32 = I.dinv[a][c] * r32;
+        I.r[a][c] = r32;
+        I.e[a][c] = 0.0f;
+        acc[0] += rhs * rhs;
+        acc[1] += res * res;
+        acc[2] += (double)r32 * (double)z32;
+      }
+    }
+  }
+}
+
+// Outer decision after a residual (the same test as the FP64 solve: |r| <= rtol |rhs|) and the
+// start of the inner FP32 solve A e = r with relative target max(tau_min, half of what the
+// outer still needs).  O.pad counts the inner iterations spent so far; a solve that exceeds
+// max_sweeps residuals or maxit inner iterations stops with CG_MAXIT.
+__device__ __forceinline__ void elas_ir_residual_finalize(CgScal& O, CgScal& S, double bb,
+                                                          double rr, double rz, double tau_min,
+                                                          int max_sweeps) {
+  if (O.it > 0) O.pad += S.it;
+  O.bb = bb;
+  O.rr = rr;
+  O.it += 1;
+  if (bb == 0.0) {
+    O.status = CG_ZERO_RHS;
+  } else if (!isfinite(rr)) {
+    O.status = CG_NONFINITE;
+  } else if (sqrt(rr) <= O.rtol * sqrt(bb)) {
+    O.status = CG_CONVERGED;
+  } else if (O.it > max_sweeps || O.pad >= O.maxit) {
+    O.status = CG_MAXIT;
+  } else {
+    O.status = CG_RUNNING;
+  }
+  S.bb = rr;
+  S.rr = rr;
+  S.rz = rz;
+  S.it = 0;
+  S.maxit = O.maxit;
+  S.alpha = 0.0;
+  S.beta = 0.0;
+  S.rtol = (rr > 0.0) ? fmax(tau_min, 0.5 * O.rtol * sqrt(bb / rr)) : 1.0;
+  S.status = (O.status == CG_RUNNING) ? CG_RUNNING : CG_CONVERGED;
+}
+
+// u += e, du += e over voxels c = c0, c0 + cs, ... < c1
+__device__ __forceinline__ void elas_ir_correct_range(const Elas& E, const Elas32& I, long long c0,
+                                                      long long c1, long long cs) {
+  for (long long c = c0; c < c1; c += cs) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double e = (double)I.e[a][c];
+      E.u[a][c] += e;
+      E.du[a][c] += e;
+    }
+  }
+}
+
+
+// ------------------------------------------------------------------------------ CN tiles
+
+struct Faces {
+  double xp, xm, yp, ym, zp, zm;
+};
+
+__device__ __forceinline__ Faces load_faces(const Cn3& C, const Nbr& nb, long long c) {
+  Faces F;
+  F.xp = C.Kf[0][c];
+  F.xm = C.Kf[0][nb.at(-1, 0, 0)];
+  F.yp = C.Kf[1][c];
+  F.ym = C.Kf[1][nb.at(0, -1, 0)];
+  F.zp = C.Kf[2][c];
+  F.zm = C.Kf[2][nb.at(0, 0, -1)];
+  return F;
+}
+
+// CN start on one tile: x0 = c, rhs = c + s, r0 = 2 s with s = dt/2 D_h c; accumulates
+// (|rhs|^2, |r|^2, <r, D^{-1} r>) per right-hand side.
+__device__ __forceinline__ void cn_init_tile(const Geo& G, const Cn3& C, int bx, int by, int bz,
+                                             double (&acc)[9]) {
+  const int i = bx * BX + threadIdx.x;
+  const int j = by * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = bz * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const Nbr nb = make_nbr(G, i, j, k);
+    const long long c = nb.at(0, 0, 0);
+    const Faces F = load_faces(C, nb, c);
+    const double di = C.dinv[c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const double* x = C.x[r];
+      const double xc = x[c];
+      const double s = F.xp * (x[nb.at(1, 0, 0)] - xc) - F.xm * (xc - x[nb.at(-1, 0, 0)]) +
+                       F.yp * (x[nb.at(0, 1, 0)] - xc) - F.ym * (xc - x[nb.at(0, -1, 0)]) +
+                       F.zp * (x[nb.at(0, 0, 1)] - xc) - F.zm * (xc - x[nb.at(0, 0, -1)]);
+      const double rhs = xc + s;
+      const double res = 2.0 * s;
+      const double z = di * res;
+      C.r[r][c] = res;
+      C.p[r][c] = z;
+      acc[3 * r + 0] += rhs * rhs;
+      acc[3 * r + 1] += res * res;
+      acc[3 * r + 2] += res * z;
+    }
+  }
+}
+
+// q = A p and <p, q> for the running solves act[] on one tile
+template <bool COH>
+__device__ __forceinline__ void cn_matvec_tile(const Geo& G, const Cn3& C, const bool (&act)[3],
+                                               int bx, int by, int bz, double (&acc)[3]) {
+  const int i = bx * BX + threadIdx.x;
+  const int j = by * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = bz * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const Nbr nb = make_nbr(G, i, j, k);
+    const long long c = nb.at(0, 0, 0);
+    const Faces F = load_faces(C, nb, c);
+    const double d = C.dsum[c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (!act[r]) continue;
+      const double* p = C.p[r];
+      const double pc = ldd<COH>(p + c);
+      const double q = d * pc - (F.xp * ldd<COH>(p + nb.at(1, 0, 0)) + F.xm * ldd<COH>(p + nb.at(-1, 0, 0)) +
+                                 F.yp * ldd<COH>(p + nb.at(0, 1, 0)) + F.ym * ldd<COH>(p + nb.at(0, -1, 0)) +
+                                 F.zp * ldd<COH>(p + nb.at(0, 0, 1)) + F.zm * ldd<COH>(p + nb.at(0, 0, -1)));
+      C.q[r][c] = q;
+      acc[r] += pc * q;
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q; accumulates <r, D^{-1} r>, <r, r> per running solve
+__device__ __forceinline__ void cn_update_tile(const Geo& G, const Cn3& C, const bool (&act)[3],
+                                               const double (&alpha)[3], int bx, int by, int bz,
+                                               double (&acc)[6]) {
+  const int i = bx * BX + threadIdx.x;
+  const int j = by * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = bz * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const long long c = ((long long)k * G.ny + j) * G.nx + i;
+    const double di = C.dinv[c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (!act[r]) continue;
+      C.x[r][c] += alpha[r] * C.p[r][c];
+      const double res = C.r[r][c] - alpha[r] * C.q[r][c];
+      C.r[r][c] = res;
+      acc[2 * r + 0] += res * (di * res);
+      acc[2 * r + 1] += res * res;
+    }
+  }
+}
+
+// p = D^{-1} r + beta p for the running solves
+__device__ __forceinline__ void cn_pupdate_tile(const Geo& G, const Cn3& C, const bool (&act)[3],
+                                                const double (&beta)[3], int bx, int by, int bz) {
+  const int i = bx * BX + threadIdx.x;
+  const int j = by * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = bz * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const long long c = ((long long)k * G.ny + j) * G.nx + i;
+    const double di = C.dinv[c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      if (act[r]) C.p[r][c] = di * C.r[r][c] + beta[r] * C.p[r][c];
+  }
+}
+
+}  // namespace tg

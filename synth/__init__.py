@@ -6,7 +6,7 @@ time-step arithmetic (no operators, solvers, interpolation or reaction terms), s
 oracle and the GPU path can consume its output without sharing any of the method.
 """
 from .brain import synthetic_brain, initial_state, grf_terms, evaluate_grf
-from .params import table_setup_params, workload_params, WORKLOADS
+from .params import table_setup_params, workload_params, batch_workload, WORKLOADS
 
 __all__ = [
     "synthetic_brain",
@@ -16,4 +16,5 @@ __all__ = [
     "table_setup_params",
     "workload_params",
     "WORKLOADS",
+    "batch_workload",
 ]

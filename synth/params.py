@@ -78,3 +78,18 @@ def workload_params(**overrides):
             raise KeyError(f"unknown parameter {k!r}")
         p[k] = v
     return p
+
+
+def batch_workload(nsims: int = 64, sizes=(64, 96, 128), seed: int = 1000):
+    """The batched workload: per simulation a grid drawn uniformly from `sizes`, rho ~ U[5, 15]
+    (rho_g = rho_w) and k_scale ~ U[0.5, 2], and the brain seed 1000 + s.  Returns a list of
+    (n, params, brain_seed)."""
+    import numpy as np
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    out = []
+    for s in range(nsims):
+        n = int(rng.choice(sizes))
+        rho = float(rng.uniform(5.0, 15.0))
+        ks = float(rng.uniform(0.5, 2.0))
+        out.append((n, workload_params(rho_g=rho, rho_w=rho, k_scale=ks), seed + s))
+    return out

@@ -1,0 +1,91 @@
+"""Batched simulations (persistent cooperative solvers, captured step graph) against the oracle
+and the single-simulation path; bounded grid-wide waits; the autotuner."""
+import numpy as np
+import pytest
+
+from synth import initial_state, workload_params
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("p", "i", "n", "g", "w", "f", "o", "l", "ux", "uy", "uz", "vx", "vy", "vz")
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def small_batch():
+    return [((24, 24, 24), workload_params(rho_g=6.0, rho_w=6.0, k_scale=0.7), 1001),
+            ((36, 20, 12), workload_params(rho_g=14.0, rho_w=14.0, k_scale=1.8), 1002),
+            ((32, 32, 16), workload_params(rho_g=10.0, rho_w=10.0, k_scale=1.0), 1003)]
+
+
+def test_batch_matches_oracle_and_single_runs(torch_cuda, oracle):
+    from paper_1810_05370_gb300 import Simulation
+    from paper_1810_05370_gb300.batch import Batch
+    steps, dt = 4, 0.01
+    spec = small_batch()
+    batch = Batch([(n, P, initial_state(n, seed)) for n, P, seed in spec])
+    stats = batch.step(dt, nsteps=steps)
+    assert stats["steps"] == steps
+    for s, (n, P, seed) in enumerate(spec):
+        got = batch.numpy(s)
+        ref = initial_state(n, seed)
+        oracle.init(n, P, ref)
+        for _ in range(steps):
+            oracle.step(n, P, dt, ref)
+        errs = {k: rel_l2(got[k], ref[k]) for k in FIELDS}
+        assert max(errs.values()) <= 1e-5, (s, errs)
+        sim = Simulation(n, P, initial_state(n, seed), precision="mixed")
+        sim.step(dt, nsteps=steps)
+        single = sim.numpy()
+        sim.close()
+        errs1 = {k: rel_l2(got[k], single[k]) for k in FIELDS}
+        assert max(errs1.values()) <= 1e-5, (s, errs1)
+    print("batch stats:", stats)
+    batch.close()
+
+
+def test_batch_autotune_keeps_results(torch_cuda, oracle):
+    from paper_1810_05370_gb300.batch import Batch
+    steps, dt = 2, 0.01
+    spec = small_batch()
+    batch = Batch([(n, P, initial_state(n, seed)) for n, P, seed in spec])
+    tune = batch.autotune(dt)
+    assert tune["candidates"] and tune["best_zc"] in (4, 8, 16, 32)
+    stats = batch.step(dt, nsteps=steps)
+    assert stats["tile_depth"] == tune["best_zc"]
+    n, P, seed = spec[1]
+    ref = initial_state(n, seed)
+    oracle.init(n, P, ref)
+    for _ in range(steps):
+        oracle.step(n, P, dt, ref)
+    got = batch.numpy(1)
+    assert max(rel_l2(got[k], ref[k]) for k in FIELDS) <= 1e-5
+    batch.close()
+
+
+def test_batch_wait_limit_reports_timeout(torch_cuda):
+    """A grid-wide wait that runs out of time returns TG_ERR_TIMEOUT; the batch then refuses
+    further steps."""
+    from paper_1810_05370_gb300 import _tg
+    from paper_1810_05370_gb300.batch import Batch
+    spec = small_batch()
+    batch = Batch([(n, P, initial_state(n, seed)) for n, P, seed in spec])
+    batch.set_timeout(1)                  # 1 ns: every wait gives up at once
+    with pytest.raises(_tg.TGError) as e:
+        batch.step(0.01)
+    assert e.value.status == _tg.TG_ERR_TIMEOUT
+    with pytest.raises(_tg.TGError) as e:
+        batch.step(0.01)
+    assert e.value.status == _tg.TG_ERR_STATE
+    batch.close()
