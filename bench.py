@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--adjoint-n", type=int, default=128)
     ap.add_argument("--adjoint-steps", type=int, default=50)
     ap.add_argument("--adjoint-checkpoint", type=int, default=10)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-sims", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     return ap.parse_args()
@@ -173,6 +176,49 @@ def run_reference(args, world, rank):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
+
+
+def run_batch(args, dev):
+    """64 simulations of uneven grids (64/96/128^3, rho ~ U[5,15], k_scale ~ U[0.5,2]) stepped
+    as one batch (persistent solvers, replayed step graph, autotuned tiles) against the same
+    simulations run one after another through the single-simulation path, both mixed."""
+    import torch
+    from paper_1810_05370_gb300 import Simulation
+    from paper_1810_05370_gb300.batch import Batch
+    from synth import batch_workload, initial_state
+    spec = batch_workload(args.batch_sims)
+    states = [initial_state(n, seed) for n, _, seed in spec]
+    bt = Batch([(n, P, st) for (n, P, _), st in zip(spec, states)], device=dev)
+    tune = bt.autotune(args.dt)
+    bt.step(args.dt, 1)                                   # warm-up (captures the step graph)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    stats = bt.step(args.dt, args.batch_steps)
+    torch.cuda.synchronize(dev)
+    t_batch = time.perf_counter() - t0
+    voxels = bt.voxels
+    bt.close()
+    del bt
+    torch.cuda.empty_cache()
+    t_seq = 0.0
+    for (n, P, _), st in zip(spec, states):
+        sim = Simulation(n, P, st, precision="mixed", device=dev)
+        sim.step(args.dt)                                 # warm-up, as for the batch
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sim.step(args.dt, args.batch_steps)
+        torch.cuda.synchronize(dev)
+        t_seq += time.perf_counter() - t0
+        sim.close()
+    vs = voxels * args.batch_steps
+    return {"sims": len(spec), "voxels": voxels, "steps": args.batch_steps, "precision": "mixed",
+            "voxel_steps_per_s": vs / t_batch, "sequential_voxel_steps_per_s": vs / t_seq,
+            "speedup_over_sequential": t_seq / t_batch, "seconds": t_batch,
+            "sequential_seconds": t_seq, "graph": stats["graph"],
+            "tile_depth": stats["tile_depth"], "coop_blocks": stats["coop_blocks"],
+            "inner_iterations": stats["it_elas_total"], "launches": stats["launches"],
+            "autotune": {"best_zc": tune["best_zc"], "best_blocks": tune["best_blocks"],
+                         "candidates": tune["candidates"]}}
 
 
 def main():
@@ -344,6 +390,12 @@ def main():
                    "note": "init (u^0 solve) included in both; misfit against 1.05 p_N"}
         torch.cuda.empty_cache()
 
+    # ---------------------------------------------------------------- batched workload (rank 0)
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batch = run_batch(args, dev)
+        torch.cuda.empty_cache()
+
     # ---------------------------------------------------------------- CPU baseline (rank 0)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -374,6 +426,7 @@ def main():
             "roofline": roof,
             "compare": other,
             "adjoint": adjoint,
+            "batch": batch,
             "mixed_over_fp64": (None if other is None else
                                 (value / other["value"] if args.precision == "mixed"
                                  else other["value"] / value)),

@@ -1493,6 +1493,7 @@ tg_status tg_batch_autotune(tg_batch* B, double dt, tg_batch_tune* result) {
         BCK(cudaMemsetAsync(B->d_bar, 0, ALIGN, B->stream));
         BCK(launch_batch_reset(D, B->stream));
         BCK(launch_batch_residual(D, B->stream));
+        BCK(launch_batch_force_inner(D, B->stream));    // u^0 may already solve the system
         D.maxit = 16;                                   // a fixed, short inner run
         BCK(cudaEventRecord(e0, B->stream));
         BCK(launch_batch_elas_inner(D, blocks, B->stream));

@@ -91,6 +91,16 @@ __global__ void k_batch_reset(BatchDev B) {
   *S.C.counter = 0u;
 }
 
+// for timing only: make every inner solve run (tolerance 0) whatever its residual is
+__global__ void k_batch_force_inner(BatchDev B) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B.nsims) return;
+  CgScal* S = B.sims[s].I.S;
+  S->status = CG_RUNNING;
+  S->rtol = 0.0;
+  S->maxit = 1 << 30;
+}
+
 // per simulation: outer elasticity status, residual count, inner iterations, CN statuses and
 // iterations, relative residuals
 __global__ void k_batch_status(BatchDev B, BatchStat* out) {
@@ -378,6 +388,11 @@ cudaError_t launch_batch_elas_inner(const BatchDev& B, int coop_blocks, cudaStre
 
 cudaError_t launch_batch_residual(const BatchDev& B, cudaStream_t st) {
   k_batch_ir_residual<<<B.ntiles, dim3(BX, BY), 0, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_force_inner(const BatchDev& B, cudaStream_t st) {
+  k_batch_force_inner<<<(B.nsims + 63) / 64, 64, 0, st>>>(B);
   return cudaGetLastError();
 }
 

@@ -409,6 +409,7 @@ cudaError_t launch_batch_cn(const BatchDev&, int coop_blocks, cudaStream_t st);
 cudaError_t launch_batch_sweep(const BatchDev&, int coop_blocks, cudaStream_t st);
 cudaError_t launch_batch_elas_inner(const BatchDev&, int coop_blocks, cudaStream_t st);
 cudaError_t launch_batch_residual(const BatchDev&, cudaStream_t st);
+cudaError_t launch_batch_force_inner(const BatchDev&, cudaStream_t st);
 cudaError_t launch_batch_finish(const BatchDev&, double inv_dt, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- adjoint
