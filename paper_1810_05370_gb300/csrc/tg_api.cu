@@ -1032,7 +1032,7 @@ namespace {
 
 constexpr int BATCH_GRAPH_SWEEPS = 6;   // refinement sweeps inside the step graph
 constexpr int BATCH_MAX_SWEEPS = 64;    // total, including sweeps run after the graph
-const int kZcCandidates[] = {4, 8, 16, 32};
+const int kZcCandidates[] = {8, 16, 32, 64};
 constexpr unsigned long long kDefaultTimeoutNs = 20ULL * 1000 * 1000 * 1000;   // 20 s
 
 struct BatchArea {

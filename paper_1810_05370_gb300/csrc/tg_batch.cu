@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(NT) k_batch_ir_residual(BatchDev B) {
     elas_ir_residual_finalize(*S.Sout, *S.I.S, out[0], out[1], out[2], B.tau_min, B.max_sweeps);
 }
 
-__global__ void __launch_bounds__(NT, 3) k_batch_elas_inner(BatchDev B) {
+__global__ void __launch_bounds__(NT, 4) k_batch_elas_inner(BatchDev B) {
   __shared__ Tile32 T;
   for (int iter = 0; iter <= B.maxit; ++iter) {
     bool any = false;

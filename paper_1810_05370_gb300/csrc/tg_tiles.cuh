@@ -18,10 +18,13 @@ constexpr int HX = BX + 2;
 constexpr int HY = BY + 2;
 constexpr int HXY = HX * HY;
 
+// Four plane slots: while planes k-1, k, k+1 are read, plane k+2 is written into the fourth,
+// so one barrier per plane suffices.
+constexpr int NSLOT = 4;
 struct Tile32 {
-  float p[3][3][HXY];  // [plane slot][component][node]
-  float mu[3][HXY];
-  float la[3][HXY];
+  float p[NSLOT][3][HXY];  // [plane slot][component][node]
+  float mu[NSLOT][HXY];
+  float la[NSLOT][HXY];
 };
 
 
@@ -210,27 +213,18 @@ __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32
   };
   // registers carry plane k+2 while plane k is computed (loads overlap the arithmetic)
   Staged r0, r1;
-  {
-    long long zo = plane_offset(k0 - 1);
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    const long long zo = plane_offset(k0 - 1 + o);
     fetch(zo + ho0, r0);
     if (two) fetch(zo + ho1, r1);
-    put(r0, 0, tid);
-    if (two) put(r1, 0, hs1);
-    zo = plane_offset(k0);
-    fetch(zo + ho0, r0);
-    if (two) fetch(zo + ho1, r1);
-    put(r0, 1, tid);
-    if (two) put(r1, 1, hs1);
-    zo = plane_offset(k0 + 1);
-    fetch(zo + ho0, r0);
-    if (two) fetch(zo + ho1, r1);
-    put(r0, 2, tid);
-    if (two) put(r1, 2, hs1);
+    put(r0, o, tid);
+    if (two) put(r1, o, hs1);
   }
 
   float part = 0.0f;
   const int ci = (ty + 1) * HX + (tx + 1);
-  int s0 = 0, s1 = 1, s2 = 2;            // slots of planes k-1, k, k+1
+  int s0 = 0, s1 = 1, s2 = 2, s3 = 3;    // slots of planes k-1, k, k+1 and the free one
   for (int k = k0; k < k1; ++k) {
     Cell t;
     const int sl[3] = {s0, s1, s2};
@@ -247,7 +241,7 @@ __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32
       fetch(zo + ho0, r0);
       if (two) fetch(zo + ho1, r1);
     }
-    __syncthreads();
+    __syncthreads();                    // plane k+1 (written last iteration) is visible
     if (on) {
       const long long c = (long long)k * G.nxy + (long long)j * G.nx + i;
       Fac32 f;
@@ -264,16 +258,17 @@ __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32
       I.q[2][c] = q2;
       part += p0 * q0 + p1 * q1 + p2 * q2;
     }
-    __syncthreads();
-    if (more) {                         // plane k-1 is free: it becomes plane k+2
-      put(r0, s0, tid);
-      if (two) put(r1, s0, hs1);
+    if (more) {                         // plane k+2 goes to the free slot
+      put(r0, s3, tid);
+      if (two) put(r1, s3, hs1);
     }
-    const int sf = s0;                  // rotate: (k-1, k, k+1) <- (k, k+1, k+2)
+    const int sf = s0;                  // rotate: (k-1, k, k+1, free) <- (k, k+1, k+2, k-1)
     s0 = s1;
     s1 = s2;
-    s2 = sf;
+    s2 = s3;
+    s3 = sf;
   }
+  __syncthreads();                      // the tile may be restaged by the caller's next item
   return part;
 }
 
