@@ -67,7 +67,8 @@ def _make_types(cs):
             ("E_scale", R), ("zeta", R),
             ("delta_e", R), ("delta_half", R), ("delta_l", R),
             ("rtol_diff", C.c_double), ("rtol_elas", C.c_double),
-            ("maxit_diff", C.c_int32), ("maxit_elas", C.c_int32)]
+            ("maxit_diff", C.c_int32), ("maxit_elas", C.c_int32),
+            ("precond_elas", C.c_int32)]
 
     P = C.POINTER(R)
 
@@ -119,6 +120,8 @@ class Oracle:
                     arr[s] = self._r(d[name][s])
             elif name in ("maxit_diff", "maxit_elas"):
                 setattr(p, name, int(d[name]))
+            elif name == "precond_elas":
+                setattr(p, name, int(d.get(name, 0)))
             elif name in ("rtol_diff", "rtol_elas"):
                 setattr(p, name, float(d[name]))
             else:
@@ -217,17 +220,37 @@ class Oracle:
                                      self._ptr(eta), self._ptr(u3), self._ptr(out))
         return out
 
-    def elasticity_solve(self, n, mu, lam, eta, rhs3, u3=None, rtol=1e-8, maxit=10000, L=None):
+    def elasticity_solve(self, n, mu, lam, eta, rhs3, u3=None, rtol=1e-8, maxit=10000, L=None,
+                         precond=0):
         rhs3 = np.ascontiguousarray(rhs3, dtype=self.dtype)
         u3 = np.zeros_like(rhs3) if u3 is None else np.array(u3, dtype=self.dtype, order="C")
         it = C.c_int32(0)
         rr = C.c_double(0)
         rc = self.lib.or_elasticity_solve(C.byref(self.grid(n, L)), self._ptr(mu), self._ptr(lam),
                                           self._ptr(eta), self._ptr(rhs3), self._ptr(u3),
-                                          C.c_double(rtol), C.c_int32(maxit), C.byref(it),
-                                          C.byref(rr))
+                                          C.c_double(rtol), C.c_int32(maxit),
+                                          C.c_int32(int(precond)), C.byref(it), C.byref(rr))
         self._check(rc, "elasticity_solve")
         return u3, it.value, rr.value
+
+    def dft3(self, n, x, inverse=False, L=None):
+        """Unnormalised 3-D DFT of a complex array (sign -1 forward, +1 inverse)."""
+        re = np.ascontiguousarray(np.real(x), dtype=np.float64).copy()
+        im = np.ascontiguousarray(np.imag(x), dtype=np.float64).copy()
+        dp = C.POINTER(C.c_double)
+        self.lib.or_dft3(C.byref(self.grid(n, L)), re.ctypes.data_as(dp), im.ctypes.data_as(dp),
+                         C.c_int(1 if inverse else -1))
+        return re + 1j * im
+
+    def elasticity_spectral(self, n, mu0, lam0, eta0, r3, L=None):
+        """z = A0^{-1} r for the constant-coefficient operator (three real components)."""
+        r3 = np.ascontiguousarray(np.real(r3), dtype=np.float64)
+        z3 = np.zeros_like(r3)
+        dp = C.POINTER(C.c_double)
+        self.lib.or_elasticity_spectral(C.byref(self.grid(n, L)), C.c_double(mu0),
+                                        C.c_double(lam0), C.c_double(eta0),
+                                        r3.ctypes.data_as(dp), z3.ctypes.data_as(dp))
+        return z3
 
     def interp(self, n, q, X, Y, Z, L=None):
         self.lib.or_interp.restype = self.R

@@ -10,8 +10,11 @@
  *    paper's pseudo-spectral ones (Section 3);
  *  - the split is the sequence of Section 3 applied once per step (first-order Lie);
  *  - the elasticity solve is (eta I - L_h) u = -b, i.e. Eq. e:screening moved to SPD form;
- *    it is symmetric, so CG replaces the paper's GMRES; Jacobi preconditioning for both
- *    elliptic solves replaces the paper's spectral preconditioners;
+ *    it is symmetric, so CG replaces the paper's GMRES; it is preconditioned either by
+ *    Jacobi or, as in Section 3, by the exact inverse of the constant-coefficient operator
+ *    with the domain means of mu, lambda and eta -- for the finite-difference operator that
+ *    inverse is diagonal in the discrete Fourier basis (one 3x3 system per wave vector);
+ *    the diffusion solves use Jacobi;
  *  - the diffusion face coefficient is the harmonic mean of the two node values (zero when
  *    both are zero), node K clamped at zero;
  *  - the unqualified "D" in the g, w equations (Eq. e:gm_wm, e:w) is D i: the Crank-Nicolson
@@ -86,13 +89,22 @@ static real_t dot(int64_t m, const real_t* x, const real_t* y) {
   return s;
 }
 
-/* ---------------------------------------------------------------- Jacobi PCG
- * Solves A x = b from the given x; stops when |r|_2 <= rtol |b|_2 (Section 3: CG for the
- * diffusion solve, a Krylov method for the elasticity solve). */
+/* ---------------------------------------------------------------- PCG
+ * Solves A x = b from the given x with preconditioner z = M(r); stops when
+ * |r|_2 <= rtol |b|_2 (Section 3: CG for the diffusion solve, a Krylov method for the
+ * elasticity solve). */
 typedef void (*apply_fn)(const void* ctx, const real_t* x, real_t* y);
+typedef void (*prec_fn)(const void* ctx, int64_t m, const real_t* r, real_t* z);
 
-static int pcg(int64_t m, apply_fn A, const void* ctx, const real_t* dinv, const real_t* b,
-               real_t* x, double rtol, int32_t maxit, int32_t* iters, double* relres) {
+/* Jacobi: z = D^{-1} r, ctx the array of inverse diagonal entries */
+static void jacobi_prec(const void* ctx, int64_t m, const real_t* r, real_t* z) {
+  const real_t* dinv = (const real_t*)ctx;
+  for (int64_t e = 0; e < m; ++e) z[e] = dinv[e] * r[e];
+}
+
+static int pcg(int64_t m, apply_fn A, const void* ctx, prec_fn M, const void* mctx,
+               const real_t* b, real_t* x, double rtol, int32_t maxit, int32_t* iters,
+               double* relres) {
   real_t* r = (real_t*)malloc((size_t)m * sizeof(real_t));
   real_t* z = (real_t*)malloc((size_t)m * sizeof(real_t));
   real_t* p = (real_t*)malloc((size_t)m * sizeof(real_t));
@@ -107,7 +119,7 @@ static int pcg(int64_t m, apply_fn A, const void* ctx, const real_t* dinv, const
   }
   A(ctx, x, q);
   for (int64_t e = 0; e < m; ++e) r[e] = b[e] - q[e];
-  for (int64_t e = 0; e < m; ++e) z[e] = dinv[e] * r[e];
+  M(mctx, m, r, z);
   for (int64_t e = 0; e < m; ++e) p[e] = z[e];
   real_t rz = dot(m, r, z);
   rnorm = SQRT_RE(dot(m, r, r));
@@ -118,7 +130,7 @@ static int pcg(int64_t m, apply_fn A, const void* ctx, const real_t* dinv, const
     real_t alpha = rz / dot(m, p, q);
     for (int64_t e = 0; e < m; ++e) x[e] += alpha * p[e];
     for (int64_t e = 0; e < m; ++e) r[e] -= alpha * q[e];
-    for (int64_t e = 0; e < m; ++e) z[e] = dinv[e] * r[e];
+    M(mctx, m, r, z);
     real_t rz_new = dot(m, r, z);
     rnorm = SQRT_RE(dot(m, r, r));
     real_t beta = rz_new / rz;
@@ -214,7 +226,7 @@ int or_cn_solve(const or_grid* G, const real_t* Kf0, const real_t* Kf1, const re
   }
   if (c_out != c_in) memcpy(c_out, c_in, (size_t)m * sizeof(real_t));
   cn_ctx C = {G, {Kf0, Kf1, Kf2}, dt, tmp};
-  int st = pcg(m, cn_apply, &C, dinv, rhs, c_out, rtol, maxit, iters, relres);
+  int st = pcg(m, cn_apply, &C, jacobi_prec, dinv, rhs, c_out, rtol, maxit, iters, relres);
   free(rhs); free(dinv); free(tmp);
   return st;
 }
@@ -315,11 +327,206 @@ static void el_apply(const void* vctx, const real_t* x, real_t* y) {
   or_elasticity_apply(C->G, C->mu, C->lam, C->eta, x, y);
 }
 
-/* (eta I - L_h) u = rhs by Jacobi PCG from the given u (Section 3, elasticity sub-step) */
+/* ---------------------------------------------------------------- discrete Fourier transform
+ * Unnormalised DFT of one line, X[k] = sum_j x[j] exp(sgn 2 pi i j k / n), sgn = -1 forward,
+ * +1 inverse.  Lengths that are powers of two use the textbook radix-2 Cooley-Tukey scheme
+ * in its iterative form (bit-reversed reordering, then rounds of butterflies on blocks of
+ * length 2, 4, ..., n); other lengths evaluate the definition term by term. */
+static int is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+/* wr[k] + i wi[k] = exp(sgn 2 pi i k / n), k = 0 .. n-1 */
+static void dft_roots(int n, int sgn, double* wr, double* wi) {
+  for (int k = 0; k < n; ++k) {
+    double a = sgn * 2.0 * M_PI * (double)k / (double)n;
+    wr[k] = cos(a);
+    wi[k] = sin(a);
+  }
+}
+
+static void dft_line(int n, double* re, double* im, const double* wr, const double* wi,
+                     double* tr, double* ti) {
+  if (is_pow2(n)) {
+    for (int a = 1, b = 0; a < n; ++a) {       /* bit-reversal permutation */
+      int bit = n >> 1;
+      for (; b & bit; bit >>= 1) b ^= bit;
+      b ^= bit;
+      if (a < b) {
+        double t = re[a]; re[a] = re[b]; re[b] = t;
+        t = im[a]; im[a] = im[b]; im[b] = t;
+      }
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+      int half = len / 2, step = n / len;
+      for (int s0 = 0; s0 < n; s0 += len)
+        for (int k = 0; k < half; ++k) {
+          double c = wr[k * step], sn = wi[k * step];
+          int lo = s0 + k, hi = s0 + k + half;
+          double vr = re[hi] * c - im[hi] * sn;
+          double vi = re[hi] * sn + im[hi] * c;
+          re[hi] = re[lo] - vr;
+          im[hi] = im[lo] - vi;
+          re[lo] += vr;
+          im[lo] += vi;
+        }
+    }
+  } else {
+    for (int k = 0; k < n; ++k) {
+      double sr = 0.0, si = 0.0;
+      for (int j = 0; j < n; ++j) {
+        int q = (int)(((int64_t)j * k) % n);
+        sr += re[j] * wr[q] - im[j] * wi[q];
+        si += re[j] * wi[q] + im[j] * wr[q];
+      }
+      tr[k] = sr;
+      ti[k] = si;
+    }
+    memcpy(re, tr, (size_t)n * sizeof(double));
+    memcpy(im, ti, (size_t)n * sizeof(double));
+  }
+}
+
+/* 3-D DFT of re + i im over the grid (x fastest), axis by axis; sgn as in dft_line */
+void or_dft3(const or_grid* G, double* re, double* im, int sgn) {
+  int64_t m = nvox(G);
+  for (int d = 0; d < 3; ++d) {
+    int n = G->n[d];
+    int64_t stride = d == 0 ? 1 : (d == 1 ? G->n[0] : (int64_t)G->n[0] * G->n[1]);
+    double* wr = (double*)malloc((size_t)n * sizeof(double));
+    double* wi = (double*)malloc((size_t)n * sizeof(double));
+    dft_roots(n, sgn, wr, wi);
+    int64_t nlines = m / n;
+#pragma omp parallel
+    {
+      double* buf = (double*)malloc((size_t)(4 * n) * sizeof(double));
+#pragma omp for schedule(static)
+      for (int64_t l = 0; l < nlines; ++l) {
+        /* first node of line l: all coordinates but axis d enumerate the lines */
+        int64_t base = (l / stride) * stride * n + (l % stride);
+        for (int j = 0; j < n; ++j) {
+          buf[j] = re[base + j * stride];
+          buf[n + j] = im[base + j * stride];
+        }
+        dft_line(n, buf, buf + n, wr, wi, buf + 2 * n, buf + 3 * n);
+        for (int j = 0; j < n; ++j) {
+          re[base + j * stride] = buf[j];
+          im[base + j * stride] = buf[n + j];
+        }
+      }
+      free(buf);
+    }
+    free(wr);
+    free(wi);
+  }
+}
+
+/* Section 3 elasticity preconditioner: z = A0^{-1} r, A0 = eta0 I - L_h with constant
+ * mu0, lam0, eta0.  On a grid mode exp(i theta . j), theta_d = 2 pi k_d / n_d, the compact
+ * second difference gives -S_d, S_d = (2 - 2 cos theta_d) / h_d^2, and the centred first
+ * difference gives i T_d, T_d = sin theta_d / h_d.  A0 therefore maps the mode's amplitude
+ * vector by the real symmetric matrix
+ *   M_aa = eta0 + mu0 (S_0 + S_1 + S_2) + (lam0 + mu0) S_a,
+ *   M_ab = (lam0 + mu0) T_a T_b   (a != b),
+ * solved here by Cramer's rule for every mode.  A singular M (only the mean mode when
+ * eta0 = 0) maps to zero.  r3, z3: three real components, one after another. */
+void or_elasticity_spectral(const or_grid* G, double mu0, double lam0, double eta0,
+                            const double* r3, double* z3) {
+  int64_t m = nvox(G);
+  double* re = (double*)malloc((size_t)(3 * m) * sizeof(double));
+  double* im = (double*)calloc((size_t)(3 * m), sizeof(double));
+  memcpy(re, r3, (size_t)(3 * m) * sizeof(double));
+  for (int a = 0; a < 3; ++a) or_dft3(G, re + a * m, im + a * m, -1);
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < m; ++e) {
+    int64_t c[3];
+    coords(G, e, c);
+    double S[3], T[3];
+    for (int d = 0; d < 3; ++d) {
+      double th = 2.0 * M_PI * (double)c[d] / (double)G->n[d];
+      double h = hd(G, d);
+      S[d] = (2.0 - 2.0 * cos(th)) / (h * h);
+      T[d] = sin(th) / h;
+    }
+    double M[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        M[a][b] = (a == b) ? eta0 + mu0 * (S[0] + S[1] + S[2]) + (lam0 + mu0) * S[a]
+                           : (lam0 + mu0) * T[a] * T[b];
+    double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1])
+               - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0])
+               + M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    double xr[3], xi[3];
+    for (int a = 0; a < 3; ++a) {
+      /* Cramer: replace column a of M by the right-hand side */
+      double Mr[3][3], Mi[3][3];
+      for (int q = 0; q < 3; ++q)
+        for (int b = 0; b < 3; ++b) {
+          Mr[q][b] = (b == a) ? re[q * m + e] : M[q][b];
+          Mi[q][b] = (b == a) ? im[q * m + e] : M[q][b];
+        }
+      double dr = Mr[0][0] * (Mr[1][1] * Mr[2][2] - Mr[1][2] * Mr[2][1])
+                - Mr[0][1] * (Mr[1][0] * Mr[2][2] - Mr[1][2] * Mr[2][0])
+                + Mr[0][2] * (Mr[1][0] * Mr[2][1] - Mr[1][1] * Mr[2][0]);
+      double di = Mi[0][0] * (Mi[1][1] * Mi[2][2] - Mi[1][2] * Mi[2][1])
+                - Mi[0][1] * (Mi[1][0] * Mi[2][2] - Mi[1][2] * Mi[2][0])
+                + Mi[0][2] * (Mi[1][0] * Mi[2][1] - Mi[1][1] * Mi[2][0]);
+      xr[a] = det != 0.0 ? dr / det : 0.0;
+      xi[a] = det != 0.0 ? di / det : 0.0;
+    }
+    for (int a = 0; a < 3; ++a) {
+      re[a * m + e] = xr[a];
+      im[a * m + e] = xi[a];
+    }
+  }
+  for (int a = 0; a < 3; ++a) or_dft3(G, re + a * m, im + a * m, +1);
+  for (int64_t e = 0; e < 3 * m; ++e) z3[e] = re[e] / (double)m;
+  free(re);
+  free(im);
+}
+
+typedef struct { const or_grid* G; double mu0, lam0, eta0; } sp_ctx;
+
+/* the spectral preconditioner on the real and (complex-step) imaginary parts separately:
+ * it is a fixed real linear map, independent of the perturbation */
+static void spectral_prec(const void* vctx, int64_t m3, const real_t* r, real_t* z) {
+  const sp_ctx* C = (const sp_ctx*)vctx;
+  double* a = (double*)malloc((size_t)m3 * sizeof(double));
+  double* b = (double*)malloc((size_t)m3 * sizeof(double));
+  for (int64_t e = 0; e < m3; ++e) a[e] = RE(r[e]);
+  or_elasticity_spectral(C->G, C->mu0, C->lam0, C->eta0, a, b);
+#ifdef OR_COMPLEX
+  double* c = (double*)malloc((size_t)m3 * sizeof(double));
+  for (int64_t e = 0; e < m3; ++e) a[e] = cimag(r[e]);
+  or_elasticity_spectral(C->G, C->mu0, C->lam0, C->eta0, a, c);
+  for (int64_t e = 0; e < m3; ++e) z[e] = b[e] + I * c[e];
+  free(c);
+#else
+  for (int64_t e = 0; e < m3; ++e) z[e] = b[e];
+#endif
+  free(a);
+  free(b);
+}
+
+/* (eta I - L_h) u = rhs by PCG from the given u (Section 3, elasticity sub-step);
+ * precond 0: Jacobi, 1: the constant-coefficient spectral inverse with the domain means of
+ * mu, lambda, eta (real parts in complex-step mode) */
 int or_elasticity_solve(const or_grid* G, const real_t* mu, const real_t* lam, const real_t* eta,
                         const real_t* rhs3, real_t* u3, double rtol, int32_t maxit,
-                        int32_t* iters, double* relres) {
+                        int32_t precond, int32_t* iters, double* relres) {
   int64_t m = nvox(G);
+  el_ctx C = {G, mu, lam, eta};
+  if (precond == 1) {
+    sp_ctx S = {G, 0.0, 0.0, 0.0};
+    for (int64_t e = 0; e < m; ++e) {
+      S.mu0 += RE(mu[e]);
+      S.lam0 += RE(lam[e]);
+      S.eta0 += RE(eta[e]);
+    }
+    S.mu0 /= (double)m;
+    S.lam0 /= (double)m;
+    S.eta0 /= (double)m;
+    return pcg(3 * m, el_apply, &C, spectral_prec, &S, rhs3, u3, rtol, maxit, iters, relres);
+  }
+  if (precond != 0) return OR_ERR_ARG;
   real_t* dinv = (real_t*)malloc((size_t)(3 * m) * sizeof(real_t));
   for (int a = 0; a < 3; ++a) {
     for (int64_t e = 0; e < m; ++e) {
@@ -334,8 +541,7 @@ int or_elasticity_solve(const or_grid* G, const real_t* mu, const real_t* lam, c
       dinv[a * m + e] = 1.0 / diag;
     }
   }
-  el_ctx C = {G, mu, lam, eta};
-  int st = pcg(3 * m, el_apply, &C, dinv, rhs3, u3, rtol, maxit, iters, relres);
+  int st = pcg(3 * m, el_apply, &C, jacobi_prec, dinv, rhs3, u3, rtol, maxit, iters, relres);
   free(dinv);
   return st;
 }
@@ -513,7 +719,8 @@ static int elasticity_substep(const or_grid* G, const or_params* P, or_state* S,
   or_force(G, P, S->p, S->n, rhs, rhs + m, rhs + 2 * m);
   for (int64_t e = 0; e < 3 * m; ++e) rhs[e] = -rhs[e];
   for (int a = 0; a < 3; ++a) memcpy(u3 + a * m, S->u[a], (size_t)m * sizeof(real_t));
-  int st = or_elasticity_solve(G, mu, lam, eta, rhs, u3, P->rtol_elas, P->maxit_elas, iters, relres);
+  int st = or_elasticity_solve(G, mu, lam, eta, rhs, u3, P->rtol_elas, P->maxit_elas,
+                               P->precond_elas, iters, relres);
   for (int a = 0; a < 3; ++a) memcpy(S->u[a], u3 + a * m, (size_t)m * sizeof(real_t));
   free(mu); free(lam); free(eta); free(rhs); free(u3);
   return st;

@@ -38,6 +38,7 @@ typedef struct {
   real_t delta_e, delta_half, delta_l;    /* Eq. e:edema                                  */
   double rtol_diff, rtol_elas;            /* Krylov stopping: |r| <= rtol |rhs|           */
   int32_t maxit_diff, maxit_elas;
+  int32_t precond_elas;                   /* 0 Jacobi, 1 spectral (Section 3)             */
 } or_params;
 
 typedef struct {
@@ -77,7 +78,10 @@ void or_elasticity_apply(const or_grid*, const real_t* mu, const real_t* lam, co
                          const real_t* u3, real_t* out3);
 int or_elasticity_solve(const or_grid*, const real_t* mu, const real_t* lam, const real_t* eta,
                         const real_t* rhs3, real_t* u3, double rtol, int32_t maxit,
-                        int32_t* iters, double* relres);
+                        int32_t precond, int32_t* iters, double* relres);
+void or_dft3(const or_grid*, double* re, double* im, int sgn);
+void or_elasticity_spectral(const or_grid*, double mu0, double lam0, double eta0,
+                            const double* r3, double* z3);
 real_t or_interp(const or_grid*, const real_t* q, real_t X, real_t Y, real_t Z);
 void or_divergence(const or_grid*, const real_t* vx, const real_t* vy, const real_t* vz,
                    real_t* div);

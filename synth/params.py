@@ -44,6 +44,9 @@ def table_setup_params():
         # solver controls (Table t:numparams gives tau = 1e-3; the workloads use 1e-8)
         "rtol_diff": 1.0e-8, "rtol_elas": 1.0e-8,
         "maxit_diff": 1000, "maxit_elas": 10000,
+        # elasticity preconditioner: 0 Jacobi, 1 the constant-coefficient spectral inverse
+        # with domain-mean Lame coefficients (Section 3)
+        "precond_elas": 0,
     }
 
 
