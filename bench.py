@@ -28,6 +28,7 @@ if ROOT not in sys.path:
 
 METRIC = "voxel-steps/s at 256^3 (mixed FP32 vs plain FP64, same GPU); adjoint/forward time"
 UNIT = "voxel-steps/s"
+PRECONDS = {"jacobi": 0, "spectral": 1}
 FIELDS = ("p", "i", "n", "g", "w", "f", "o", "l", "bg", "ux", "uy", "uz", "vx", "vy", "vz")
 
 # Algorithmic traffic and arithmetic of the elasticity operator kernel, per voxel and launch.
@@ -47,6 +48,8 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--dt", type=float, default=0.01)
     ap.add_argument("--precision", choices=("fp64", "mixed"), default="mixed")
+    ap.add_argument("--precond", choices=("spectral", "jacobi"), default="spectral",
+                    help="elasticity preconditioner (Section 3 uses the spectral one)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other precision on the same GPU")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
@@ -240,7 +243,7 @@ def main():
     dev = torch.device("cuda", local)
     n = args.n
     V = n ** 3
-    P = workload_params()
+    P = workload_params(precond_elas=PRECONDS[args.precond])
     st0 = initial_state(n, seed=0)
     sim = Simulation(n, P, st0, precision=args.precision, device=dev)
     stream = sim.stream
@@ -417,6 +420,7 @@ def main():
                                    f"multispecies step dt {args.dt}, CG rtol 1e-8, "
                                    f"{args.precision} path",
                        "grid": n, "precision": args.precision,
+                       "elasticity_preconditioner": args.precond,
                        "l2": "inputs larger than L2 (15 state arrays + workspace, "
                              f"{(15 * V * 8 + ws_bytes) / 1e9:.1f} GB)",
                        "parallelism": f"replicas x{world}"},

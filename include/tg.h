@@ -14,11 +14,14 @@
  *   S3  reaction of p, i, n, g, w (Eq. e:p - e:w: logistic growth, go-or-grow switching,
  *       hypoxic death);  S4 oxygen reaction (Eq. e:ox);  S5 edema reaction (Eq. e:edema);
  *   S6  screened elasticity (eta I - L_h) u = -b (Eq. e:screening with Eq. e:lame and
- *       e:forcingfunction), Jacobi-preconditioned CG;
+ *       e:forcingfunction), CG preconditioned by Jacobi or (Section 3) by the exact inverse
+ *       of the constant-coefficient operator with the domain means of mu, lambda, eta;
  *   S7  v = (u^{n+1} - u^n) / dt.
  * Spatial operators are second-order finite differences on a periodic box (7-point
  * variable-coefficient diffusion, 19-point variable-coefficient Navier-Lame); the paper's
- * pseudo-spectral discretisation and spectral preconditioners are not used.
+ * pseudo-spectral discretisation is not used.  The spectral elasticity preconditioner
+ * (TG_PRECOND_SPECTRAL) inverts the finite-difference operator's own discrete symbol with
+ * FFTs and needs every grid size to be a power of two between 4 and 2048.
  *
  * Conventions for every entry point:
  *  - Arrays are FP64, C-contiguous, indexed [z][y][x] (x fastest), n[0]*n[1]*n[2] elements,
@@ -82,7 +85,13 @@ typedef struct {
   double delta_e, delta_half, delta_l; /* edema source, half-saturation, drainage, Eq. e:edema     */
   double rtol_diff, rtol_elas;     /* CG stops at |r|_2 <= rtol |rhs|_2                          */
   int32_t maxit_diff, maxit_elas;  /* CG iteration limits (TG_ERR_NOCONV beyond)                */
+  int32_t precond_elas;            /* elasticity preconditioner: TG_PRECOND_JACOBI or
+                                      TG_PRECOND_SPECTRAL (Section 3: constant coefficients
+                                      averaged over the domain, inverted by FFT)             */
 } tg_params;
+
+#define TG_PRECOND_JACOBI 0
+#define TG_PRECOND_SPECTRAL 1
 
 /* Device pointers to the caller's state (species and materials of Section 2.3; u is the
  * displacement of Eq. e:screening, v = u_t its velocity).  bg is read only. */
@@ -106,11 +115,14 @@ typedef struct {
   int64_t n_elas_matvec;     /*   kernel over the launches that did work, and their count    */
 } tg_stats;
 
-/* Bytes of workspace tg_init needs for this grid and precision (0 on invalid arguments). */
-size_t tg_workspace_bytes(const tg_grid* grid, tg_precision prec);
+/* Bytes of workspace tg_init needs for this grid, parameters and precision (0 on invalid
+ * arguments, including TG_PRECOND_SPECTRAL on a grid it does not support).  params may be
+ * NULL: Jacobi preconditioning.  Only params->precond_elas changes the size. */
+size_t tg_workspace_bytes(const tg_grid* grid, const tg_params* params, tg_precision prec);
 
 /* Bytes of workspace for a context created with TG_INIT_ADJOINT (adjoint scratch included). */
-size_t tg_workspace_bytes_adjoint(const tg_grid* grid, tg_precision prec);
+size_t tg_workspace_bytes_adjoint(const tg_grid* grid, const tg_params* params,
+                                  tg_precision prec);
 
 /* Bytes of one step's tape (the forward values tg_adjoint_step needs): 26 FP64 fields. */
 size_t tg_tape_bytes(const tg_grid* grid);
@@ -149,13 +161,15 @@ tg_status tg_adjoint_step(tg_ctx* ctx, double dt, const void* tape, tg_state* la
  * u^0.  Needs TG_INIT_ADJOINT. */
 tg_status tg_adjoint_init(tg_ctx* ctx, double* const lam_u[3], double grad[5]);
 
-/* Solve (eta I - L_h) u = rhs with Jacobi-preconditioned CG, coefficients from the current
+/* Solve (eta I - L_h) u = rhs with preconditioned CG, coefficients from the current
  * state (Eq. e:lame), starting from the given u.  rhs == NULL means rhs = -b with the force
  * b of Eq. e:forcingfunction from the current state (the solve S6 performs); otherwise rhs
  * holds three device arrays.  u holds three device arrays, overwritten with the solution. */
 tg_status tg_solve_elasticity(tg_ctx* ctx, double* const rhs[3], double* u[3], tg_stats* stats);
 
-/* Replace the parameters used by later calls (e.g. a parameter sweep on one context). */
+/* Replace the parameters used by later calls (e.g. a parameter sweep on one context).
+ * Switching to TG_PRECOND_SPECTRAL needs a context whose workspace was sized for it
+ * (TG_ERR_WORKSPACE otherwise). */
 tg_status tg_set_params(tg_ctx* ctx, const tg_params* params);
 
 /* Optional kernel timing for profiling: with enable != 0 every launch of the elasticity
@@ -178,7 +192,7 @@ tg_status tg_set_timing(tg_ctx* ctx, int32_t enable);
  * It computes what tg_solve_elasticity computes on a context over the same state: the Lame
  * and screening fields from the state's species (p, i, n, g, w, f, bg are read; the other
  * state pointers are ignored), then (eta I - L_h) u = rhs by Jacobi-preconditioned CG from the
- * given u; rhs == NULL means rhs = -b (the force of Eq. e:forcingfunction).  All work goes to
+ * given u (params->precond_elas is ignored here); rhs == NULL means rhs = -b (the force of Eq. e:forcingfunction).  All work goes to
  * cuda_stream and the call returns after it has finished.
  *
  * The first call on a device looks up the scratch array's device address (with that device

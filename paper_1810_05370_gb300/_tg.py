@@ -17,6 +17,7 @@ TG_OK, TG_ERR_ARG, TG_ERR_CUDA, TG_ERR_NOCONV, TG_ERR_NONFINITE, TG_ERR_TIMEOUT,
 TG_FP64, TG_MIXED = 0, 1
 TG_INIT_KEEP_UV = 1
 TG_INIT_ADJOINT = 2
+TG_PRECOND_JACOBI, TG_PRECOND_SPECTRAL = 0, 1
 THETA = ("k_scale", "rho", "o_hyp", "o_inv", "E_scale")
 
 STATUS_NAMES = {
@@ -42,7 +43,7 @@ class tg_params(C.Structure):
         ("E_scale", C.c_double), ("zeta", C.c_double),
         ("delta_e", C.c_double), ("delta_half", C.c_double), ("delta_l", C.c_double),
         ("rtol_diff", C.c_double), ("rtol_elas", C.c_double),
-        ("maxit_diff", C.c_int32), ("maxit_elas", C.c_int32)]
+        ("maxit_diff", C.c_int32), ("maxit_elas", C.c_int32), ("precond_elas", C.c_int32)]
 
 
 class tg_state(C.Structure):
@@ -84,14 +85,14 @@ def _load():
     lib = C.CDLL(LIB_PATH)
     P = C.POINTER
     sig = {
-        "tg_workspace_bytes": (C.c_size_t, [P(tg_grid), C.c_int]),
+        "tg_workspace_bytes": (C.c_size_t, [P(tg_grid), P(tg_params), C.c_int]),
         "tg_init": (C.c_int, [P(tg_grid), P(tg_params), C.c_int, P(tg_state), C.c_void_p,
                               C.c_size_t, C.c_void_p, C.c_uint32, P(C.c_void_p), P(tg_stats)]),
         "tg_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, P(tg_stats)]),
         "tg_solve_elasticity": (C.c_int, [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(tg_stats)]),
         "tg_set_params": (C.c_int, [C.c_void_p, P(tg_params)]),
         "tg_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
-        "tg_workspace_bytes_adjoint": (C.c_size_t, [P(tg_grid), C.c_int]),
+        "tg_workspace_bytes_adjoint": (C.c_size_t, [P(tg_grid), P(tg_params), C.c_int]),
         "tg_tape_bytes": (C.c_size_t, [P(tg_grid)]),
         "tg_adjoint_step": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, P(tg_state),
                                       P(C.c_double)]),
@@ -148,6 +149,7 @@ def make_params(d: dict) -> tg_params:
             arr[s] = float(d[name][s])
     p.maxit_diff = int(d["maxit_diff"])
     p.maxit_elas = int(d["maxit_elas"])
+    p.precond_elas = int(d.get("precond_elas", TG_PRECOND_JACOBI))
     return p
 
 
@@ -161,8 +163,10 @@ def stats_dict(s: tg_stats) -> dict:
 
 # ----------------------------------------------------------------------------- same-name calls
 
-def tg_workspace_bytes(grid: tg_grid, prec: int) -> int:
-    return int(lib.tg_workspace_bytes(C.byref(grid), int(prec)))
+def tg_workspace_bytes(grid: tg_grid, params, prec: int) -> int:
+    """params: a tg_params, or None (Jacobi preconditioning)."""
+    return int(lib.tg_workspace_bytes(C.byref(grid), None if params is None else C.byref(params),
+                                      int(prec)))
 
 
 def tg_init(grid, params, prec, state, workspace_ptr, workspace_bytes, stream_ptr, flags=0):
@@ -176,8 +180,10 @@ def tg_init(grid, params, prec, state, workspace_ptr, workspace_bytes, stream_pt
     return ctx, stats_dict(stats)
 
 
-def tg_workspace_bytes_adjoint(grid: tg_grid, prec: int) -> int:
-    return int(lib.tg_workspace_bytes_adjoint(C.byref(grid), int(prec)))
+def tg_workspace_bytes_adjoint(grid: tg_grid, params, prec: int) -> int:
+    return int(lib.tg_workspace_bytes_adjoint(C.byref(grid),
+                                              None if params is None else C.byref(params),
+                                              int(prec)))
 
 
 def tg_tape_bytes(grid: tg_grid) -> int:

@@ -96,14 +96,63 @@ Geo make_geo(const tg_grid* g, int sms) {
   return G;
 }
 
+// ---------------------------------------------------------------- spectral preconditioner
+// Every axis a power of two in [4, 2048]: the FFT passes stage whole lines in shared memory.
+bool spectral_grid_ok(const Geo& G) {
+  for (int n : {G.nx, G.ny, G.nz})
+    if (n < 4 || n > 2048 || (n & (n - 1)) != 0) return false;
+  return true;
+}
+
+int floor_pow2(long long v) {
+  int p = 1;
+  while ((long long)p * 2 <= v) p *= 2;
+  return p;
+}
+
+// Line batch sizes of the passes: about 32 KB of shared memory per x block, 64 KB per y
+// block and 96 KB per z block (two ping-pong buffers each).
+template <typename R>
+void spec_shape(const Geo& G, Spec<R>& V) {
+  const long long cs = sizeof(typename CxOf<R>::T);
+  V.nx = G.nx;
+  V.ny = G.ny;
+  V.nz = G.nz;
+  V.nxh = G.nx / 2 + 1;
+  V.nxp = (V.nxh + 15) / 16 * 16;
+  V.pb = std::max(1, std::min(G.ny / 2, floor_pow2(32768 / (2 * G.nx * cs))));
+  V.tx = std::max(1, std::min(16, floor_pow2(65536 / (2 * G.ny * cs))));
+  V.tz = std::max(1, std::min(16, floor_pow2(98304 / (6 * G.nz * cs))));
+}
+
+// partial sums: one per x-pass block (the larger count of the FP32 and FP64 shapes), and the
+// 1024 x 3 of the mean reduction
+int spec_partial_count(const Geo& G) {
+  Spec<float> a;
+  Spec<double> b;
+  spec_shape(G, a);
+  spec_shape(G, b);
+  const long long na = 3LL * G.nz * (G.ny / (2 * a.pb));
+  const long long nb = 3LL * G.nz * (G.ny / (2 * b.pb));
+  return (int)std::max<long long>(std::max(na, nb), 3 * 1024);
+}
+
+size_t spec_table_bytes(const Geo& G, size_t real_bytes) {
+  const size_t n = (size_t)G.nx + G.ny + G.nz;
+  return round_up(n * 2 * real_bytes) + round_up(n * 2 * real_bytes);  // roots; S and T
+}
+
 struct Layout {
   size_t arr[A_COUNT];
   size_t arr32[B_COUNT];
   size_t adj[C_COUNT];
-  size_t partial, counter, scal, grad, total;
+  size_t partial, counter, scal, grad;
+  bool spectral;
+  size_t sp_w, sp_z32[3], sp_z64[3], sp_tab32, sp_tab64, sp_mean, sp_partial, sp_counter;
+  size_t total;
 };
 
-Layout layout(const Geo& G, tg_precision prec, bool adjoint = false) {
+Layout layout(const Geo& G, tg_precision prec, bool adjoint = false, bool spectral = false) {
   Layout L;
   size_t off = 0;
   const size_t abytes = round_up((size_t)G.nvox * sizeof(double));
@@ -129,8 +178,63 @@ Layout layout(const Geo& G, tg_precision prec, bool adjoint = false) {
   off += round_up(N_SCAL * sizeof(CgScal));
   L.grad = off;
   off += ALIGN;
+  // spectral preconditioner: the FP32 form serves the mixed precision and the adjoint's
+  // refined solves, the FP64 form the FP64 solves; one half-spectrum buffer serves both
+  L.spectral = spectral;
+  const bool need32 = spectral && (prec == TG_MIXED || adjoint);
+  const bool need64 = spectral && prec == TG_FP64;
+  Spec<float> s32;
+  spec_shape(G, s32);
+  const size_t wmodes = (size_t)3 * G.nz * G.ny * s32.nxp;
+  L.sp_w = off;
+  if (spectral) off += round_up(wmodes * (need64 ? sizeof(double2) : sizeof(float2)));
+  for (int d = 0; d < 3; ++d) {
+    L.sp_z32[d] = off;
+    if (need32) off += fbytes;
+  }
+  for (int d = 0; d < 3; ++d) {
+    L.sp_z64[d] = off;
+    if (need64) off += abytes;
+  }
+  L.sp_tab32 = off;
+  if (need32) off += spec_table_bytes(G, sizeof(float));
+  L.sp_tab64 = off;
+  if (need64) off += spec_table_bytes(G, sizeof(double));
+  L.sp_mean = off;
+  if (spectral) off += ALIGN;
+  L.sp_partial = off;
+  if (spectral) off += round_up((size_t)spec_partial_count(G) * sizeof(double));
+  L.sp_counter = off;
+  if (spectral) off += ALIGN;
   L.total = off;
   return L;
+}
+
+template <typename R>
+Spec<R> spec_view(const Geo& G, const Layout& L, char* ws, size_t tab_off) {
+  using C = typename CxOf<R>::T;
+  Spec<R> V;
+  spec_shape(G, V);
+  V.W = (C*)(ws + L.sp_w);
+  const int n[3] = {G.nx, G.ny, G.nz};
+  const size_t ntot = (size_t)G.nx + G.ny + G.nz;
+  C* tw = (C*)(ws + tab_off);
+  R* st = (R*)(ws + tab_off + round_up(ntot * sizeof(C)));
+  for (int d = 0; d < 3; ++d) {
+    V.tw[d] = tw;
+    tw += n[d];
+    V.S[d] = st;
+    st += n[d];
+  }
+  for (int d = 0; d < 3; ++d) {
+    V.T[d] = st;
+    st += n[d];
+  }
+  V.mean = (double*)(ws + L.sp_mean);
+  V.partial = (double*)(ws + L.sp_partial);
+  V.counter = (unsigned int*)(ws + L.sp_counter);
+  V.nb_partial = spec_partial_count(G);
+  return V;
 }
 
 int sm_count() {
@@ -142,6 +246,7 @@ int sm_count() {
 
 bool params_ok(const tg_params* p) {
   if (!p) return false;
+  if (p->precond_elas != TG_PRECOND_JACOBI && p->precond_elas != TG_PRECOND_SPECTRAL) return false;
   if (!(p->eps_H > 0.0)) return false;
   if (!(p->o_inv > 0.5 * (p->o_hyp + p->o_inv)) && !(p->o_inv < 0.5 * (p->o_hyp + p->o_inv)))
     return false;  // o_inv == o_mit: the ramp of Eq. e:gog_reac_op is undefined
@@ -230,6 +335,11 @@ struct tg_ctx {
   std::vector<cudaEvent_t> ev;   // pairs (start, stop) per operator launch of one solve
   double t_matvec_ms;
   long long n_matvec;
+  // spectral elasticity preconditioner (workspace sized for it when L.spectral)
+  Spec<float> sp32;      // FP32 form: mixed precision, adjoint refined solves
+  Spec<double> sp64;     // FP64 form: FP64 solves
+  float* z32[3];
+  double* z64[3];
 };
 
 namespace {
@@ -321,6 +431,7 @@ Elas elas_view(tg_ctx* X, double* const u[3], double* const b[3]) {
     E.q[d] = X->a[A_EQ0 + d];
     E.u[d] = u[d];
     E.v[d] = X->st.v[d];
+    E.z[d] = X->z64[d];
   }
   E.S = X->scal + 3;
   E.partial = X->partial;
@@ -360,6 +471,11 @@ tg_status cn_solve3(tg_ctx* X, tg_stats* stats) {
   return TG_OK;
 }
 
+// the spectral preconditioner is in use (requested and the workspace holds its buffers)
+bool spectral_on(const tg_ctx* X) {
+  return X->L.spectral && X->prm.precond_elas == TG_PRECOND_SPECTRAL;
+}
+
 Elas32 elas32_view(tg_ctx* X) {
   Elas32 I;
   I.mu = X->b32[B_MU];
@@ -372,6 +488,7 @@ Elas32 elas32_view(tg_ctx* X) {
     I.p[0][d] = X->b32[B_P0 + d];
     I.p[1][d] = X->b32[B_PB0 + d];
     I.q[d] = X->b32[B_Q0 + d];
+    I.z[d] = X->z32[d];
   }
   I.S = X->scal + 4;
   I.partial = X->partial;
@@ -402,6 +519,13 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
   CK(cudaGetLastError());
   CK(launch_elas32_coef(X->G, E, I, X->stream));
   X->launches += 2;
+  const bool spec = spectral_on(X);
+  if (spec) {
+    CK(launch_spec_mean(X->G.nvox, E.mu, E.lam, E.eta, X->sp32.mean, X->sp32.partial,
+                        X->sp32.counter, X->stream));
+    X->launches += 1;
+  }
+  const float* const r32[3] = {I.r[0], I.r[1], I.r[2]};
   int inner_total = 0, sweeps = 0;
   CgScal out;
   for (;;) {
@@ -411,20 +535,28 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
     CK(cudaStreamSynchronize(X->stream));
     if (out.status != CG_RUNNING) break;
     if (sweeps >= MAX_SWEEPS || inner_total >= X->prm.maxit_elas) return fail(X, TG_ERR_NOCONV);
+    if (spec) {   // z = P r and <r, z> for the inner solve's first direction
+      CK(launch_spectral(X->sp32, r32, X->z32, I.S, X->stream));
+      X->launches += 5;
+    }
     CgScal host[1];
     int recorded = 0;
     const int slot = sweeps == 0 ? 0 : 1;
     tg_status s = drive_cg(X, [&](int q) {
-      X->launches += 2;
+      X->launches += spec ? 7 : 2;
       const bool timed = X->timing && ensure_events(X, q + 1);
       if (timed) {
         cudaEventRecord(X->ev[2 * q], X->stream);
         recorded = q + 1;
       }
-      cudaError_t e = launch_elas32_matvec(X->G, I, X->stream);
+      cudaError_t e = spec ? launch_elas32_matvec_spec(X->G, I, X->stream)
+                           : launch_elas32_matvec(X->G, I, X->stream);
       if (timed) cudaEventRecord(X->ev[2 * q + 1], X->stream);
       if (e != cudaSuccess) return e;
-      return launch_elas32_update(X->G, I, X->stream);
+      if (!spec) return launch_elas32_update(X->G, I, X->stream);
+      e = launch_elas32_update_spec(X->G, I, X->stream);
+      if (e != cudaSuccess) return e;
+      return launch_spectral(X->sp32, r32, X->z32, I.S, X->stream);
     }, I.S, 1, X->prm.maxit_elas, X->prev_it_inner[slot], host);
     if (s != TG_OK) return s;
     harvest_timing(X, recorded, host[0].it);
@@ -454,14 +586,25 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
                      double inv_dt, tg_stats* stats) {
   if (X->prec == TG_MIXED) return elas_solve_mixed(X, u, b_ext, minus_b, inv_dt, stats);
   const Elas E = elas_view(X, u, b_ext);
+  const bool spec = spectral_on(X);
   k_cg_reset<<<1, 32, 0, X->stream>>>(X->scal + 3, 1, X->prm.rtol_elas, X->prm.maxit_elas);
   CK(cudaGetLastError());
-  CK(launch_elas_init(X->G, E, minus_b, X->stream));
-  X->launches += 2;
+  const double* const r64[3] = {E.r[0], E.r[1], E.r[2]};
+  if (spec) {
+    CK(launch_spec_mean(X->G.nvox, E.mu, E.lam, E.eta, X->sp64.mean, X->sp64.partial,
+                        X->sp64.counter, X->stream));
+    CK(launch_elas_init_spec(X->G, E, minus_b, X->stream));
+    CK(launch_spectral(X->sp64, r64, X->z64, E.S, X->stream));
+    CK(launch_elas_pupdate_spec(X->G, E, X->stream));
+    X->launches += 9;
+  } else {
+    CK(launch_elas_init(X->G, E, minus_b, X->stream));
+    X->launches += 2;
+  }
   CgScal host[1];
   int recorded = 0;
   tg_status s = drive_cg(X, [&](int q) {
-    X->launches += 3;
+    X->launches += spec ? 8 : 3;
     const bool timed = X->timing && ensure_events(X, q + 1);
     if (timed) {
       cudaEventRecord(X->ev[2 * q], X->stream);
@@ -470,7 +613,11 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
     cudaError_t e = launch_elas_matvec(X->G, E, X->stream);
     if (timed) cudaEventRecord(X->ev[2 * q + 1], X->stream);
     if (e != cudaSuccess) return e;
-    return launch_elas_update(X->G, E, X->stream);
+    if (!spec) return launch_elas_update(X->G, E, X->stream);
+    e = launch_elas_update_spec(X->G, E, X->stream);
+    if (e == cudaSuccess) e = launch_spectral(X->sp64, r64, X->z64, E.S, X->stream);
+    if (e == cudaSuccess) e = launch_elas_pupdate_spec(X->G, E, X->stream);
+    return e;
   }, E.S, 1, X->prm.maxit_elas, X->prev_it_elas, host);
   if (s != TG_OK) return s;
   X->prev_it_elas = host[0].it;
@@ -746,18 +893,53 @@ tg_status do_adjoint_step(tg_ctx* X, double dt, const void* tape, const tg_state
   return read_grad(X, grad);
 }
 
+// Views of the spectral buffers and their one-time tables (twiddles, symbol factors).
+tg_status spectral_setup(tg_ctx* X) {
+  const Layout& L = X->L;
+  for (int d = 0; d < 3; ++d) {
+    X->z32[d] = nullptr;
+    X->z64[d] = nullptr;
+  }
+  if (!L.spectral) return TG_OK;
+  const bool need32 = X->prec == TG_MIXED || X->has_adjoint;
+  const bool need64 = X->prec == TG_FP64;
+  if (cudaMemsetAsync(X->ws + L.sp_counter, 0, ALIGN, X->stream) != cudaSuccess) return TG_ERR_CUDA;
+  if (need32) {
+    X->sp32 = spec_view<float>(X->G, L, X->ws, L.sp_tab32);
+    for (int d = 0; d < 3; ++d) X->z32[d] = (float*)(X->ws + L.sp_z32[d]);
+    if (spec_prepare(X->sp32) != cudaSuccess) return TG_ERR_CUDA;
+    if (launch_spec_tables(X->sp32, X->G.h, X->stream) != cudaSuccess) return TG_ERR_CUDA;
+  }
+  if (need64) {
+    X->sp64 = spec_view<double>(X->G, L, X->ws, L.sp_tab64);
+    for (int d = 0; d < 3; ++d) X->z64[d] = (double*)(X->ws + L.sp_z64[d]);
+    if (spec_prepare(X->sp64) != cudaSuccess) return TG_ERR_CUDA;
+    if (launch_spec_tables(X->sp64, X->G.h, X->stream) != cudaSuccess) return TG_ERR_CUDA;
+  }
+  return TG_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
-size_t tg_workspace_bytes(const tg_grid* grid, tg_precision prec) {
+size_t tg_workspace_bytes(const tg_grid* grid, const tg_params* params, tg_precision prec) {
   if (!grid_ok(grid) || (prec != TG_FP64 && prec != TG_MIXED)) return 0;
-  return layout(make_geo(grid, sm_count()), prec).total;
+  if (params && !params_ok(params)) return 0;
+  const Geo G = make_geo(grid, sm_count());
+  const bool spectral = params && params->precond_elas == TG_PRECOND_SPECTRAL;
+  if (spectral && !spectral_grid_ok(G)) return 0;
+  return layout(G, prec, false, spectral).total;
 }
 
-size_t tg_workspace_bytes_adjoint(const tg_grid* grid, tg_precision prec) {
+size_t tg_workspace_bytes_adjoint(const tg_grid* grid, const tg_params* params,
+                                  tg_precision prec) {
   if (!grid_ok(grid) || (prec != TG_FP64 && prec != TG_MIXED)) return 0;
-  return layout(make_geo(grid, sm_count()), prec, true).total;
+  if (params && !params_ok(params)) return 0;
+  const Geo G = make_geo(grid, sm_count());
+  const bool spectral = params && params->precond_elas == TG_PRECOND_SPECTRAL;
+  if (spectral && !spectral_grid_ok(G)) return 0;
+  return layout(G, prec, true, spectral).total;
 }
 
 size_t tg_tape_bytes(const tg_grid* grid) {
@@ -779,7 +961,9 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
     if (!q || ((uintptr_t)q & 15u)) return TG_ERR_ARG;
   const Geo G = make_geo(grid, sm_count());
   const bool adjoint = (flags & TG_INIT_ADJOINT) != 0;
-  const Layout L = layout(G, prec, adjoint);
+  const bool spectral = params->precond_elas == TG_PRECOND_SPECTRAL;
+  if (spectral && !spectral_grid_ok(G)) return TG_ERR_ARG;
+  const Layout L = layout(G, prec, adjoint, spectral);
   if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < L.total)
     return TG_ERR_WORKSPACE;
   tg_ctx* X = new (std::nothrow) tg_ctx();
@@ -803,6 +987,10 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
   X->counter = (unsigned int*)(X->ws + L.counter);
   X->scal = (CgScal*)(X->ws + L.scal);
   if (cudaMemsetAsync(X->counter, 0, ALIGN, X->stream) != cudaSuccess) {
+    tg_free(X);
+    return TG_ERR_CUDA;
+  }
+  if (spectral_setup(X) != TG_OK) {
     tg_free(X);
     return TG_ERR_CUDA;
   }
@@ -916,6 +1104,7 @@ tg_status tg_adjoint_init(tg_ctx* X, double* const lam_u[3], double grad[5]) {
 tg_status tg_set_params(tg_ctx* X, const tg_params* params) {
   if (!X || !params_ok(params)) return TG_ERR_ARG;
   if (X->broken) return TG_ERR_STATE;
+  if (params->precond_elas == TG_PRECOND_SPECTRAL && !X->L.spectral) return TG_ERR_WORKSPACE;
   X->prm = *params;
   X->dp = make_dev_params(params);
   return TG_OK;
@@ -1382,7 +1571,7 @@ size_t tg_batch_workspace_bytes(int32_t nsims, const tg_grid* grids, tg_precisio
   if (nsims <= 0 || !grids || prec != TG_MIXED) return 0;
   size_t total = 0;
   for (int s = 0; s < nsims; ++s) {
-    const size_t b = tg_workspace_bytes(&grids[s], prec);
+    const size_t b = tg_workspace_bytes(&grids[s], nullptr, prec);
     if (b == 0) return 0;
     total += round_up(b);
   }
@@ -1408,10 +1597,12 @@ tg_status tg_batch_init(int32_t nsims, const tg_grid* grids, const tg_params* pa
   char* base = (char*)workspace;
   size_t off = 0;
   for (int s = 0; s < nsims; ++s) {
-    const size_t b = tg_workspace_bytes(&grids[s], prec);
+    const size_t b = tg_workspace_bytes(&grids[s], nullptr, prec);
+    tg_params ps = params[s];
+    ps.precond_elas = TG_PRECOND_JACOBI;   // the persistent batch solvers are Jacobi-PCG
     tg_ctx* X = nullptr;
-    tg_status e = tg_init(&grids[s], &params[s], prec, &states[s], base + off, b, cuda_stream, 0,
-                          &X, nullptr);
+    tg_status e = tg_init(&grids[s], &ps, prec, &states[s], base + off, b, cuda_stream, 0, &X,
+                          nullptr);
     if (e != TG_OK) {
       for (tg_ctx* c : B->ctx) tg_free(c);
       delete B;

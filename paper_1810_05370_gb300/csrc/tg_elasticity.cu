@@ -61,7 +61,9 @@ __global__ void __launch_bounds__(NT) k_elas_coef(Geo G, DevParams P, Elas E,
   }
 }
 
-// r = rhs - A u, du = 0, p = D^{-1} r;  rhs = -b (force) or the caller's b.
+// r = rhs - A u, du = 0, p = D^{-1} r;  rhs = -b (force) or the caller's b.  With SPEC the
+// preconditioner runs in separate kernels afterwards: only r, du and the norms here.
+template <bool SPEC>
 __global__ void __launch_bounds__(NT) k_elas_init(Geo G, Elas E, int minus_b) {
   const double* const u[3] = {E.u[0], E.u[1], E.u[2]};
   const int i = blockIdx.x * BX + threadIdx.x;
@@ -81,13 +83,15 @@ __global__ void __launch_bounds__(NT) k_elas_init(Geo G, Elas E, int minus_b) {
       for (int a = 0; a < 3; ++a) {
         const double rhs = minus_b ? -E.b[a][c] : E.b[a][c];
         const double res = rhs - Au[a];
-        const double z = E.dinv[a][c] * res;
         E.r[a][c] = res;
-        E.p[a][c] = z;
         E.du[a][c] = 0.0;
         acc[0] += rhs * rhs;
         acc[1] += res * res;
-        acc[2] += res * z;
+        if (!SPEC) {
+          const double z = E.dinv[a][c] * res;
+          E.p[a][c] = z;
+          acc[2] += res * z;
+        }
       }
     }
   }
@@ -124,6 +128,7 @@ __global__ void __launch_bounds__(NT) k_elas_matvec(Geo G, Elas E) {
   }
 }
 
+template <bool SPEC>
 __global__ void __launch_bounds__(NT) k_elas_update(Geo G, Elas E) {
   if (E.S->status != CG_RUNNING) return;
   const double alpha = E.S->alpha;
@@ -140,14 +145,19 @@ __global__ void __launch_bounds__(NT) k_elas_update(Geo G, Elas E) {
         E.du[a][c] += alpha * E.p[a][c];
         const double res = E.r[a][c] - alpha * E.q[a][c];
         E.r[a][c] = res;
-        acc[0] += res * (E.dinv[a][c] * res);
+        if (!SPEC) acc[0] += res * (E.dinv[a][c] * res);
         acc[1] += res * res;
       }
     }
   }
   double out[2];
-  if (reduce_last_block<2>(acc, E.partial, E.counter, out) && threadIdx.x == 0 && threadIdx.y == 0)
-    cg_after_update(*E.S, out[0], out[1]);
+  if (reduce_last_block<2>(acc, E.partial, E.counter, out) && threadIdx.x == 0 &&
+      threadIdx.y == 0) {
+    if (SPEC)
+      cg_after_update_rr(*E.S, out[1]);
+    else
+      cg_after_update(*E.S, out[0], out[1]);
+  }
 }
 
 __global__ void __launch_bounds__(NT) k_elas_pupdate(Geo G, Elas E) {
@@ -161,6 +171,22 @@ __global__ void __launch_bounds__(NT) k_elas_pupdate(Geo G, Elas E) {
     const long long c = ((long long)k * G.ny + j) * G.nx + i;
 #pragma unroll
     for (int a = 0; a < 3; ++a) E.p[a][c] = E.dinv[a][c] * E.r[a][c] + beta * E.p[a][c];
+  }
+}
+
+// p = z + beta p with z from the spectral preconditioner (p = z on the first iteration)
+__global__ void __launch_bounds__(NT) k_elas_pupdate_spec(Geo G, Elas E) {
+  if (E.S->status != CG_RUNNING) return;
+  const double beta = E.S->beta;
+  const bool first = E.S->it == 0;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const long long c = ((long long)k * G.ny + j) * G.nx + i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) E.p[a][c] = first ? E.z[a][c] : E.z[a][c] + beta * E.p[a][c];
   }
 }
 
@@ -191,7 +217,12 @@ cudaError_t launch_elas_coef(const Geo& G, const DevParams& P, const Elas& E, co
 }
 
 cudaError_t launch_elas_init(const Geo& G, const Elas& E, bool minus_b, cudaStream_t st) {
-  k_elas_init<<<G.grid, dim3(BX, BY), 0, st>>>(G, E, minus_b ? 1 : 0);
+  k_elas_init<false><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, minus_b ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elas_init_spec(const Geo& G, const Elas& E, bool minus_b, cudaStream_t st) {
+  k_elas_init<true><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, minus_b ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -201,8 +232,18 @@ cudaError_t launch_elas_matvec(const Geo& G, const Elas& E, cudaStream_t st) {
 }
 
 cudaError_t launch_elas_update(const Geo& G, const Elas& E, cudaStream_t st) {
-  k_elas_update<<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
+  k_elas_update<false><<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
   k_elas_pupdate<<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elas_update_spec(const Geo& G, const Elas& E, cudaStream_t st) {
+  k_elas_update<true><<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elas_pupdate_spec(const Geo& G, const Elas& E, cudaStream_t st) {
+  k_elas_pupdate_spec<<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
   return cudaGetLastError();
 }
 

@@ -182,6 +182,29 @@ __device__ __forceinline__ void cg_after_update(CgScal& S, double rz_new, double
   }
 }
 
+// With a preconditioner applied in separate kernels the update decides convergence from
+// <r, r> alone and the preconditioner's last kernel supplies <r, z> and beta.
+__device__ __forceinline__ void cg_after_update_rr(CgScal& S, double rr) {
+  S.it += 1;
+  S.rr = rr;
+  if (!isfinite(rr)) {
+    S.status = CG_NONFINITE;
+  } else if (sqrt(rr) <= S.rtol * sqrt(S.bb)) {
+    S.status = CG_CONVERGED;
+  } else if (S.it >= S.maxit) {
+    S.status = CG_MAXIT;
+  }
+}
+
+__device__ __forceinline__ void cg_after_precond(CgScal& S, double rz_new) {
+  if (!isfinite(rz_new)) {
+    S.status = CG_NONFINITE;
+    return;
+  }
+  S.beta = (S.it == 0) ? 0.0 : rz_new / S.rz;
+  S.rz = rz_new;
+}
+
 __device__ __forceinline__ void cg_after_init(CgScal& S, double bb, double rr, double rz) {
   S.bb = bb;
   S.rr = rr;
@@ -230,6 +253,7 @@ struct Elas32 {    // inner FP32 elasticity solve of the mixed precision
   float* r[3];
   float* p[2][3];  // search direction, double-buffered: iteration k reads p[k&1], writes p[~k&1]
   float* q[3];
+  const float* z[3];  // preconditioned residual when the spectral preconditioner is on
   CgScal* S;
   double* partial;
   unsigned int* counter;
@@ -241,6 +265,43 @@ struct Sl32 {      // FP32 transport: inputs as FP32 copies, outputs to the FP64
   const float* q[6];
   double* out[6];
 };
+
+// ---------------------------------------------------------------- spectral preconditioner
+// Section 3: the elasticity solve is preconditioned by the exact inverse of the operator with
+// constant coefficients (the domain means of mu, lambda, eta).  For the finite-difference
+// operator on the periodic grid that inverse is diagonal in the discrete Fourier basis: one
+// 3x3 real symmetric system per wave vector, diagonal plus rank one (Sherman-Morrison).
+// Grid sizes are powers of two.  W holds the half spectrum (kx = 0 .. nx/2) of the three
+// components after the x transform, rows padded to nxp modes.
+template <typename R> struct CxOf;
+template <> struct CxOf<float> { using T = float2; };
+template <> struct CxOf<double> { using T = double2; };
+
+template <typename R>
+struct Spec {
+  using C = typename CxOf<R>::T;
+  int nx, ny, nz, nxh, nxp;   // grid; x modes kept (nx/2 + 1); row pitch of W in modes
+  int pb, tx, tz;             // row pairs per x-pass block; mode columns per y / z block
+  C* W;                       // 3 components x nz x ny x nxp
+  C* tw[3];                   // exp(-2 pi i k / n_d), k < n_d
+  R* S[3];                    // 4 sin^2(theta_k / 2) / h_d^2, theta_k = 2 pi k / n_d
+  R* T[3];                    // sin(theta_k) / h_d
+  double* mean;               // mu0, lambda0, eta0 (device)
+  double* partial;            // per-block partial sums (x inverse pass, means)
+  unsigned int* counter;
+  int nb_partial;             // capacity of partial, in doubles
+};
+
+// shared memory of each pass (bytes) and the block counts of its grid
+template <typename R> size_t spec_smem_x(const Spec<R>& V) {
+  return 2 * (size_t)V.pb * V.nx * sizeof(typename CxOf<R>::T);
+}
+template <typename R> size_t spec_smem_y(const Spec<R>& V) {
+  return 2 * (size_t)V.tx * V.ny * sizeof(typename CxOf<R>::T);
+}
+template <typename R> size_t spec_smem_z(const Spec<R>& V) {
+  return 2 * (size_t)3 * V.tz * V.nz * sizeof(typename CxOf<R>::T);
+}
 
 // ----------------------------------------------------------------------------- launches
 // All return cudaGetLastError() after queueing on `st`.
@@ -295,6 +356,7 @@ struct Elas {
   double* q[3];
   double* u[3];      // displacement (in: u^n, out: u^{n+1})
   double* v[3];      // velocity (written when dt > 0)
+  double* z[3];      // spectral preconditioner output (null with Jacobi)
   CgScal* S;
   double* partial;
   unsigned int* counter;
@@ -335,6 +397,9 @@ cudaError_t launch_elas_coef(const Geo&, const DevParams&, const Elas&, const do
 cudaError_t launch_elas_init(const Geo&, const Elas&, bool rhs_is_minus_b, cudaStream_t st);
 cudaError_t launch_elas_matvec(const Geo&, const Elas&, cudaStream_t st);
 cudaError_t launch_elas_update(const Geo&, const Elas&, cudaStream_t st);   // update + p-update
+cudaError_t launch_elas_init_spec(const Geo&, const Elas&, bool rhs_is_minus_b, cudaStream_t st);
+cudaError_t launch_elas_update_spec(const Geo&, const Elas&, cudaStream_t st);
+cudaError_t launch_elas_pupdate_spec(const Geo&, const Elas&, cudaStream_t st);
 cudaError_t launch_elas_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
                                cudaStream_t st);
 
@@ -349,6 +414,21 @@ cudaError_t launch_elas_ir_correct(const Geo&, const Elas&, const Elas32&, cudaS
 cudaError_t launch_elas_ir_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
                                   cudaStream_t st);
 cudaError_t launch_sl32(const Geo&, double dt, const Sl32&, cudaStream_t st);
+
+// spectral preconditioner: one-time tables, per-solve means, z = A0^{-1} r with <r, z>
+// finishing the CG scalars in S (S may be null: plain application)
+template <typename R>
+cudaError_t launch_spec_tables(const Spec<R>&, const double h[3], cudaStream_t st);
+template <typename R>
+cudaError_t spec_prepare(const Spec<R>&);   // shared-memory limits of the pass kernels
+cudaError_t launch_spec_mean(long long n, const double* mu, const double* lam,
+                             const double* eta, double* mean, double* partial,
+                             unsigned int* counter, cudaStream_t st);
+template <typename R>
+cudaError_t launch_spectral(const Spec<R>&, const R* const r[3], R* const z[3], CgScal* S,
+                            cudaStream_t st);
+cudaError_t launch_elas32_matvec_spec(const Geo&, const Elas32&, cudaStream_t st);
+cudaError_t launch_elas32_update_spec(const Geo&, const Elas32&, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- batches
 

@@ -77,6 +77,36 @@ __global__ void __launch_bounds__(NT) k_elas32_update(long long n, Elas32 I) {
     cg_after_update(*I.S, out[0], out[1]);
 }
 
+// the same with the spectral preconditioner: the operator stages p = z + beta p, the update
+// decides convergence from <r, r> and the preconditioner's last pass supplies beta
+__global__ void __launch_bounds__(NT) k_elas32_matvec_spec(Geo G, Consts32 K, Elas32 I) {
+  if (!running(I.S)) return;
+  __shared__ Tile32 T;
+  const float part = elas32_matvec_tile<false, true>(G, K, I, I.S->it, I.S->beta, blockIdx.x,
+                                                     blockIdx.y, blockIdx.z, T);
+  double acc[1] = {(double)part};
+  double out[1];
+  if (reduce_last_block<1>(acc, I.partial, I.counter, out) && threadIdx.x == 0 && threadIdx.y == 0) {
+    I.S->pq = out[0];
+    I.S->alpha = I.S->rz / out[0];
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_elas32_update_spec(long long n, Elas32 I) {
+  if (!running(I.S)) return;
+  const float alpha = (float)I.S->alpha;
+  const int pb = (I.S->it & 1) ^ 1;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double drz = 0.0, drr = 0.0;
+  elas32_update_range<false, true>(I, n, t0, n / 4, stride, alpha, pb, blockIdx.x == 0, drz,
+                                   drr);
+  double acc[1] = {drr};
+  double out[1];
+  if (reduce_last_block<1>(acc, I.partial, I.counter, out) && threadIdx.x == 0 && threadIdx.y == 0)
+    cg_after_update_rr(*I.S, out[0]);
+}
+
 // ------------------------------------------------------------------------------ refinement
 
 // FP64 residual of the current iterate, outer stopping test and start of the inner solve
@@ -231,6 +261,16 @@ static int reduce_blocks(const Geo& G, long long items) {
 
 cudaError_t launch_elas32_update(const Geo& G, const Elas32& I, cudaStream_t st) {
   k_elas32_update<<<reduce_blocks(G, (G.nvox + 3) / 4), NT, 0, st>>>(G.nvox, I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elas32_matvec_spec(const Geo& G, const Elas32& I, cudaStream_t st) {
+  k_elas32_matvec_spec<<<G.grid, dim3(BX, BY), 0, st>>>(G, make_consts32(G), I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elas32_update_spec(const Geo& G, const Elas32& I, cudaStream_t st) {
+  k_elas32_update_spec<<<reduce_blocks(G, (G.nvox + 3) / 4), NT, 0, st>>>(G.nvox, I);
   return cudaGetLastError();
 }
 

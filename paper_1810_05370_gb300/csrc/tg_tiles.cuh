@@ -159,8 +159,9 @@ __device__ __forceinline__ float row_tile(const Tile32& T, const Cell& t, const 
 
 // One tile (bx, by, bz) of the FP32 operator with the fused p-update, for CG iteration `it`
 // with coefficient beta; returns this thread's FP32 part of <p_new, A p_new>.  T is the
-// block's shared staging area.
-template <bool COH>
+// block's shared staging area.  The preconditioned residual is D^{-1} r (Jacobi) or, with
+// SPEC, the array z the spectral preconditioner wrote.
+template <bool COH, bool SPEC = false>
 __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32& K,
                                                     const Elas32& I, int it, double beta_d,
                                                     int bx, int by, int bz, Tile32& T) {
@@ -195,7 +196,7 @@ __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32
   auto fetch = [&](long long g, Staged& v) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float z = __ldg(I.dinv[a] + g) * ldf<COH>(I.r[a] + g);
+      const float z = SPEC ? ldf<COH>(I.z[a] + g) : __ldg(I.dinv[a] + g) * ldf<COH>(I.r[a] + g);
       v.p[a] = first ? z : z + beta * ldf<COH>(po[a] + g);
     }
     v.mu = __ldg(I.mu + g);
@@ -276,7 +277,7 @@ __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32
 // over float4 groups g = g0, g0 + gs, ... < g1 of an n-voxel system, plus the scalar tail
 // n - n % 4 .. n when `tail` is set; accumulates <r, D^{-1} r> and <r, r>: the twelve products
 // of one group summed in FP32, the groups in FP64.
-template <bool COH>
+template <bool COH, bool SPEC = false>
 __device__ __forceinline__ void elas32_update_range(const Elas32& I, long long n, long long g0,
                                                     long long g1, long long gs, float alpha,
                                                     int pb, bool tail, double& drz,
@@ -289,13 +290,15 @@ __device__ __forceinline__ void elas32_update_range(const Elas32& I, long long n
       float4* r4 = reinterpret_cast<float4*>(I.r[a]) + v;
       const float4 p = ldf4<COH>(reinterpret_cast<const float4*>(I.p[pb][a]) + v);
       const float4 q = ldf4<COH>(reinterpret_cast<const float4*>(I.q[a]) + v);
-      const float4 d = __ldg(reinterpret_cast<const float4*>(I.dinv[a]) + v);
       float4 e = *e4, r = *r4;
       e.x += alpha * p.x; e.y += alpha * p.y; e.z += alpha * p.z; e.w += alpha * p.w;
       r.x -= alpha * q.x; r.y -= alpha * q.y; r.z -= alpha * q.z; r.w -= alpha * q.w;
       *e4 = e;
       *r4 = r;
-      prz += r.x * (d.x * r.x) + r.y * (d.y * r.y) + r.z * (d.z * r.z) + r.w * (d.w * r.w);
+      if (!SPEC) {
+        const float4 d = __ldg(reinterpret_cast<const float4*>(I.dinv[a]) + v);
+        prz += r.x * (d.x * r.x) + r.y * (d.y * r.y) + r.z * (d.z * r.z) + r.w * (d.w * r.w);
+      }
       prr += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
     }
     drz += (double)prz;
@@ -309,7 +312,7 @@ __device__ __forceinline__ void elas32_update_range(const Elas32& I, long long n
         I.e[a][c] += alpha * ldf<COH>(I.p[pb][a] + c);
         const float res = I.r[a][c] - alpha * ldf<COH>(I.q[a] + c);
         I.r[a][c] = res;
-        drz += (double)(res * (I.dinv[a][c] * res));
+        if (!SPEC) drz += (double)(res * (I.dinv[a][c] * res));
         drr += (double)(res * res);
       }
     }

@@ -40,14 +40,15 @@ class Simulation:
                 raise ValueError(f"state[{k!r}] has shape {tuple(v.shape)}, expected {self.shape}")
             self.state[k] = v
         self.adjoint = adjoint
-        nbytes = (_tg.tg_workspace_bytes_adjoint if adjoint else _tg.tg_workspace_bytes)(
-            self.grid, self.prec)
-        if nbytes == 0:
-            raise ValueError("invalid grid or unsupported precision")
-        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
-        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
         self.params = dict(params)
         self._cparams = _tg.make_params(self.params)
+        nbytes = (_tg.tg_workspace_bytes_adjoint if adjoint else _tg.tg_workspace_bytes)(
+            self.grid, self._cparams, self.prec)
+        if nbytes == 0:
+            raise ValueError("invalid grid, unsupported precision, or a preconditioner the "
+                             "grid does not support")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
         self._cstate = self._state_struct()
         with torch.cuda.device(self.device):
             self.ctx, self.init_stats = _tg.tg_init(

@@ -37,17 +37,17 @@ def test_every_declared_symbol_is_exported(tg):
 
 
 def test_struct_sizes_match_header_layout(tg):
-    # tg_params: 17 + 15 + 2 + 3 + 2 doubles, then two int32
-    assert C.sizeof(tg.tg_params) == (17 + 15 + 2 + 3 + 2) * 8 + 8
+    # tg_params: 17 + 15 + 2 + 3 + 2 doubles, then three int32 (maxit x2, precond_elas)
+    assert C.sizeof(tg.tg_params) == (17 + 15 + 2 + 3 + 2) * 8 + 3 * 4 + 4   # 3 int32 + padding
     assert C.sizeof(tg.tg_grid) == 3 * 4 + 4 + 3 * 8
     assert C.sizeof(tg.tg_state) == 15 * 8
 
 
 def test_workspace_bytes_validates_grid(tg):
-    assert tg.tg_workspace_bytes(tg.make_grid(32), tg.TG_FP64) > 0
-    assert tg.tg_workspace_bytes(tg.make_grid((3, 8, 8)), tg.TG_FP64) == 0
-    assert tg.tg_workspace_bytes(tg.make_grid((8, 8, 8), L=(1.0, -1.0, 1.0)), tg.TG_FP64) == 0
-    assert tg.tg_workspace_bytes(tg.make_grid(8), 7) == 0
+    assert tg.tg_workspace_bytes(tg.make_grid(32), None, tg.TG_FP64) > 0
+    assert tg.tg_workspace_bytes(tg.make_grid((3, 8, 8)), None, tg.TG_FP64) == 0
+    assert tg.tg_workspace_bytes(tg.make_grid((8, 8, 8), L=(1.0, -1.0, 1.0)), None, tg.TG_FP64) == 0
+    assert tg.tg_workspace_bytes(tg.make_grid(8), None, 7) == 0
 
 
 def test_init_rejects_null_arguments(tg):
@@ -68,3 +68,18 @@ def test_error_strings(tg):
     for s in range(8):
         assert tg.error_string(s)
     assert "unknown" in tg.error_string(99)
+
+
+def test_spectral_preconditioner_grid_rules(tg):
+    """TG_PRECOND_SPECTRAL needs power-of-two axes in [4, 2048]; it enlarges the workspace."""
+    from synth import workload_params
+    Pj = tg.make_params(workload_params())
+    Ps = tg.make_params(workload_params(precond_elas=tg.TG_PRECOND_SPECTRAL))
+    g = tg.make_grid((32, 16, 8))
+    for prec in (tg.TG_FP64, tg.TG_MIXED):
+        assert tg.tg_workspace_bytes(g, Ps, prec) > tg.tg_workspace_bytes(g, Pj, prec) > 0
+        assert tg.tg_workspace_bytes(g, None, prec) == tg.tg_workspace_bytes(g, Pj, prec)
+    assert tg.tg_workspace_bytes(tg.make_grid((36, 20, 12)), Ps, tg.TG_FP64) == 0
+    assert tg.tg_workspace_bytes(tg.make_grid((36, 20, 12)), Pj, tg.TG_FP64) > 0
+    Pbad = tg.make_params(workload_params(precond_elas=7))
+    assert tg.tg_workspace_bytes(g, Pbad, tg.TG_FP64) == 0

@@ -188,7 +188,7 @@ def test_status_codes(torch_cuda):
     sim.close()
     # workspace too small
     grid = _tg.make_grid(n)
-    need = _tg.tg_workspace_bytes(grid, _tg.TG_FP64)
+    need = _tg.tg_workspace_bytes(grid, None, _tg.TG_FP64)
     ws = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
     s = Simulation(n, P, st)
     with pytest.raises(_tg.TGError) as e:
