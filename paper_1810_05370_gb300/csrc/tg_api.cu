@@ -110,8 +110,9 @@ int floor_pow2(long long v) {
   return p;
 }
 
-// Line batch sizes of the passes: about 32 KB of shared memory per x block, 64 KB per y
-// block and 96 KB per z block (two ping-pong buffers each).
+// Line batch sizes of the passes: up to 64 KB of line buffers per block (two ping-pong
+// buffers), at most 16 lines (so a radix-16 stage gives 256 threads n/16 butterflies of 16
+// lines).  A z block has one thread per radix-16 butterfly of its 3 tz lines.
 template <typename R>
 void spec_shape(const Geo& G, Spec<R>& V) {
   const long long cs = sizeof(typename CxOf<R>::T);
@@ -120,9 +121,11 @@ void spec_shape(const Geo& G, Spec<R>& V) {
   V.nz = G.nz;
   V.nxh = G.nx / 2 + 1;
   V.nxp = (V.nxh + 15) / 16 * 16;
-  V.pb = std::max(1, std::min(G.ny / 2, floor_pow2(32768 / (2 * G.nx * cs))));
+  V.pb = std::max(1, std::min(std::min(G.ny / 2, 16), floor_pow2(65536 / (2 * G.nx * cs))));
   V.tx = std::max(1, std::min(16, floor_pow2(65536 / (2 * G.ny * cs))));
-  V.tz = std::max(1, std::min(16, floor_pow2(98304 / (6 * G.nz * cs))));
+  V.tz = std::max(1, std::min(16, floor_pow2(65536 / (6 * G.nz * cs))));
+  const int items = 3 * V.tz * std::max(1, G.nz / 16);
+  V.nt_z = std::max(64, std::min(NT, (items + 31) / 32 * 32));
 }
 
 // partial sums: one per x-pass block (the larger count of the FP32 and FP64 shapes), and the

@@ -282,6 +282,7 @@ struct Spec {
   using C = typename CxOf<R>::T;
   int nx, ny, nz, nxh, nxp;   // grid; x modes kept (nx/2 + 1); row pitch of W in modes
   int pb, tx, tz;             // row pairs per x-pass block; mode columns per y / z block
+  int nt_z;                   // threads of a z-pass block
   C* W;                       // 3 components x nz x ny x nxp
   C* tw[3];                   // exp(-2 pi i k / n_d), k < n_d
   R* S[3];                    // 4 sin^2(theta_k / 2) / h_d^2, theta_k = 2 pi k / n_d
@@ -292,15 +293,15 @@ struct Spec {
   int nb_partial;             // capacity of partial, in doubles
 };
 
-// shared memory of each pass (bytes) and the block counts of its grid
-template <typename R> size_t spec_smem_x(const Spec<R>& V) {
-  return 2 * (size_t)V.pb * V.nx * sizeof(typename CxOf<R>::T);
+// shared memory of each pass (bytes): the line length's twiddles and two line buffers
+template <typename R> size_t spec_smem_x(const Spec<R>& V) {   // lines padded to pb + 1
+  return (1 + 2 * ((size_t)V.pb + 1)) * V.nx * sizeof(typename CxOf<R>::T);
 }
 template <typename R> size_t spec_smem_y(const Spec<R>& V) {
-  return 2 * (size_t)V.tx * V.ny * sizeof(typename CxOf<R>::T);
+  return (1 + 2 * (size_t)V.tx) * V.ny * sizeof(typename CxOf<R>::T);
 }
 template <typename R> size_t spec_smem_z(const Spec<R>& V) {
-  return 2 * (size_t)3 * V.tz * V.nz * sizeof(typename CxOf<R>::T);
+  return (1 + 2 * (size_t)3 * V.tz) * V.nz * sizeof(typename CxOf<R>::T);
 }
 
 // ----------------------------------------------------------------------------- launches

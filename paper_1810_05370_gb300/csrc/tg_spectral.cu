@@ -44,60 +44,153 @@ template <int SGN, typename C> __device__ __forceinline__ C root(const C* tw, in
   return SGN < 0 ? w : C{w.x, -w.y};
 }
 
-// Transforms nl lines of length n (a power of two).  Element e of line l sits at
-// a[l * ls + e * es]; b has the same shape and is scratch.  line_fast: consecutive threads
-// take consecutive lines (lines interleaved in memory), else consecutive butterflies of one
-// line.  Entry: a loaded and visible to the block.  Returns the buffer holding the result
-// (visible to the block).
-template <int SGN, typename C>
-__device__ C* fft_lines(C* a, C* b, int n, int nl, int ls, int es, bool line_fast,
-                        const C* __restrict__ tw) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int Ns = 1; Ns < n;) {
-    const int R = ((n / Ns) & 3) == 0 ? 4 : 2;
-    const int nb = n / R;               // butterflies per line
-    const int ts = n / (Ns * R);        // twiddle table stride of this stage
-    const int total = nl * nb;
-    for (int it = tid; it < total; it += nthr) {
-      int l, j;
-      if (line_fast) {
-        l = it % nl;
-        j = it / nl;
-      } else {
-        j = it % nb;
-        l = it / nb;
-      }
-      const int k = j % Ns;             // position inside the current sub-transform
-      const int d = (j / Ns) * Ns * R + k;
-      const C* src = a + (size_t)l * ls;
-      C* dst = b + (size_t)l * ls;
-      C v0 = src[(size_t)j * es], v1 = src[(size_t)(j + nb) * es];
-      if (R == 4) {
-        C v2 = src[(size_t)(j + 2 * nb) * es], v3 = src[(size_t)(j + 3 * nb) * es];
-        if (k > 0) {
-          v1 = cmul(v1, root<SGN>(tw, k * ts));
-          v2 = cmul(v2, root<SGN>(tw, 2 * k * ts));
-          v3 = cmul(v3, root<SGN>(tw, 3 * k * ts));
-        }
-        const C a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3);
-        const C a3 = rot<SGN>(csub(v1, v3));
-        dst[(size_t)d * es] = cadd(a0, a2);
-        dst[(size_t)(d + Ns) * es] = cadd(a1, a3);
-        dst[(size_t)(d + 2 * Ns) * es] = csub(a0, a2);
-        dst[(size_t)(d + 3 * Ns) * es] = csub(a1, a3);
-      } else {
-        if (k > 0) v1 = cmul(v1, root<SGN>(tw, k * ts));
-        dst[(size_t)d * es] = cadd(v0, v1);
-        dst[(size_t)(d + Ns) * es] = csub(v0, v1);
-      }
+// --------------------------------------------------------------- small DFTs in registers
+// v[0..R) in, X[0..R) out in natural order, X[k] = sum_m v[m] exp(SGN 2 pi i m k / R).
+template <int SGN, typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+  const C a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), a3 = rot<SGN>(csub(v1, v3));
+  v0 = cadd(a0, a2);
+  v1 = cadd(a1, a3);
+  v2 = csub(a0, a2);
+  v3 = csub(a1, a3);
+}
+
+// v * exp(SGN 2 pi i m / 16) for the constant m; cos and sin of m pi / 8 written out
+template <int SGN, int M, typename C> __device__ __forceinline__ C w16(C v) {
+  using R = decltype(v.x);
+  constexpr double c1 = 0.92387953251128674, s1 = 0.38268343236508977, h = 0.70710678118654752;
+  constexpr double cs = M == 1 ? c1 : M == 2 ? h : M == 3 ? s1 : M == 6 ? -h : M == 9 ? -c1 : 1.0;
+  constexpr double sn = M == 1 ? s1 : M == 2 ? h : M == 3 ? c1 : M == 6 ? h : M == 9 ? -s1 : 0.0;
+  if constexpr (M == 0) {
+    return v;
+  } else if constexpr (M == 4) {
+    return rot<SGN>(v);                 // exp(SGN i pi / 2) = SGN i
+  } else {
+    const R c = (R)cs, w = (R)(SGN < 0 ? -sn : sn);
+    return C{v.x * c - v.y * w, v.x * w + v.y * c};
+  }
+}
+
+template <int LR, int SGN, typename C> __device__ __forceinline__ void dft(C (&v)[1 << LR]) {
+  if constexpr (LR == 1) {
+    const C t = v[0];
+    v[0] = cadd(t, v[1]);
+    v[1] = csub(t, v[1]);
+  } else if constexpr (LR == 2) {
+    dft4<SGN>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (LR == 3) {
+    // even and odd halves, then X[k] = E[k] + W8^k O[k], X[k + 4] = E[k] - W8^k O[k]
+    dft4<SGN>(v[0], v[2], v[4], v[6]);
+    dft4<SGN>(v[1], v[3], v[5], v[7]);
+    const C o1 = w16<SGN, 2>(v[3]), o2 = w16<SGN, 4>(v[5]), o3 = w16<SGN, 6>(v[7]);
+    const C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+  } else {
+    // 16 = 4 x 4: Y_q = DFT4 of v[q + 4m] (lands at v[q + 4k]), Z_q[k] = W16^{qk} Y_q[k],
+    // X[k + 4t] = DFT4 over q of Z_q[k]
+    dft4<SGN>(v[0], v[4], v[8], v[12]);
+    dft4<SGN>(v[1], v[5], v[9], v[13]);
+    dft4<SGN>(v[2], v[6], v[10], v[14]);
+    dft4<SGN>(v[3], v[7], v[11], v[15]);
+    v[5] = w16<SGN, 1>(v[5]);
+    v[6] = w16<SGN, 2>(v[6]);
+    v[7] = w16<SGN, 3>(v[7]);
+    v[9] = w16<SGN, 2>(v[9]);
+    v[10] = w16<SGN, 4>(v[10]);
+    v[11] = w16<SGN, 6>(v[11]);
+    v[13] = w16<SGN, 3>(v[13]);
+    v[14] = w16<SGN, 6>(v[14]);
+    v[15] = w16<SGN, 9>(v[15]);
+    dft4<SGN>(v[0], v[1], v[2], v[3]);
+    dft4<SGN>(v[4], v[5], v[6], v[7]);
+    dft4<SGN>(v[8], v[9], v[10], v[11]);
+    dft4<SGN>(v[12], v[13], v[14], v[15]);
+    // X[k + 4t] sits at v[4k + t]: transpose the 4 x 4 block
+    C t[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) t[q] = v[q];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = t[4 * (q & 3) + (q >> 2)];
+  }
+}
+
+// One Stockham stage of radix 2^LR over lo * hi lines of length n = 2^ln: sub-transforms of
+// length Ns = 2^lNs are merged into ones of length Ns * R.  Line l = lh * lo + ll (ll < lo,
+// lh < hi, lo a power of two) has element e at a[l * ls + e * es].  Work item `it` is
+// (ll, j, lh) with ll fastest, so consecutive threads take consecutive interleaved lines
+// (es > 1) or consecutive butterflies of one line (lo = 1, es = 1).  tw[k] =
+// exp(-2 pi i k / n) (the inverse transform conjugates it).
+template <int LR, int SGN, typename C>
+__device__ __forceinline__ void fft_stage(const C* a, C* b, int ln, int lNs, int llo, int hi,
+                                          int ls, int es, const C* tw) {
+  constexpr int R = 1 << LR;
+  const int lnb = ln - LR, nb = 1 << lnb, Ns = 1 << lNs, lts = ln - lNs - LR;
+  const int lo_mask = (1 << llo) - 1;
+  const int total = hi << (llo + lnb);
+  for (int it = threadIdx.x; it < total; it += blockDim.x) {
+    const int ll = it & lo_mask;
+    const int rest = it >> llo;
+    const int j = rest & (nb - 1);
+    const int l = ((rest >> lnb) << llo) + ll;
+    const int k = j & (Ns - 1);           // position inside the current sub-transform
+    const int d = ((j >> lNs) << (lNs + LR)) + k;
+    const C* src = a + l * ls;
+    C* dst = b + l * ls;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * es];
+    if (k > 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], root<SGN>(tw, (r * k) << lts));
     }
+    dft<LR, SGN>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(d + r * Ns) * es] = v[r];
+  }
+}
+
+// Transforms the lines (layout as in fft_stage) of length n = 2^ln, n >= 2: one stage of
+// radix 2, 4 or 8 for the remainder of ln mod 4, then radix-16 stages, one barrier after
+// each.  Entry: a and tw loaded and visible to the block.  Returns the buffer holding the
+// result (visible to the block).
+template <int SGN, typename C>
+__device__ C* fft_lines(C* a, C* b, int ln, int llo, int hi, int ls, int es, const C* tw) {
+  int lNs = ln & 3;
+  if (lNs == 1) fft_stage<1, SGN>(a, b, ln, 0, llo, hi, ls, es, tw);
+  if (lNs == 2) fft_stage<2, SGN>(a, b, ln, 0, llo, hi, ls, es, tw);
+  if (lNs == 3) fft_stage<3, SGN>(a, b, ln, 0, llo, hi, ls, es, tw);
+  if (lNs != 0) {
     __syncthreads();
     C* t = a;
     a = b;
     b = t;
-    Ns *= R;
+  }
+  for (; lNs < ln; lNs += 4) {
+    fft_stage<4, SGN>(a, b, ln, lNs, llo, hi, ls, es, tw);
+    __syncthreads();
+    C* t = a;
+    a = b;
+    b = t;
   }
   return a;
+}
+
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
+// Global -> shared staging in batches of LB elements per thread: all loads of a batch are
+// issued before any result is stored, so each thread keeps LB loads in flight.
+constexpr int LB = 8;
+
+// the n twiddles of one line length into shared memory
+template <typename C>
+__device__ __forceinline__ void load_roots(C* dst, const C* __restrict__ src, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
 template <typename C> __device__ __forceinline__ C* smem_cx() {
@@ -118,23 +211,40 @@ __global__ void __launch_bounds__(NT) k_spec_x_fwd(Spec<R> V, const R* __restric
                                                    const R* __restrict__ r2, const CgScal* S) {
   using C = typename CxOf<R>::T;
   if (spec_skip<R>(S)) return;
-  C* a = smem_cx<C>();
-  C* b = a + (size_t)V.pb * V.nx;
-  const int comp = blockIdx.z, z = blockIdx.y, y0 = 2 * V.pb * blockIdx.x;
+  // lines interleaved, element e of line l at e * es + l; es = pb + 1 keeps the row-wise
+  // staging accesses (consecutive e) free of bank conflicts
+  const int n = V.nx, ln = ilog2(n), pb = V.pb, es = pb + 1;
+  C* tw = smem_cx<C>();
+  C* a = tw + n;
+  C* b = a + (size_t)es * n;
+  load_roots(tw, V.tw[0], n);
+  const int comp = blockIdx.z, z = blockIdx.y, y0 = 2 * pb * blockIdx.x;
   const R* src = comp == 0 ? r0 : (comp == 1 ? r1 : r2);
-  const size_t row0 = ((size_t)z * V.ny + y0) * V.nx;
-  const int n = V.nx;
-  for (int idx = threadIdx.x; idx < V.pb * n; idx += blockDim.x) {
-    const int l = idx / n, x = idx - l * n;
-    const size_t o = row0 + (size_t)(2 * l) * n + x;
-    a[idx] = C{src[o], src[o + n]};
+  const size_t row0 = ((size_t)z * V.ny + y0) * n;
+  const int total = pb * n;
+  for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {
+    R va[LB], vb[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) {
+        const size_t o = row0 + (size_t)(2 * (idx >> ln)) * n + (idx & (n - 1));
+        va[u] = __ldg(src + o);
+        vb[u] = __ldg(src + o + n);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) a[(idx & (n - 1)) * es + (idx >> ln)] = C{va[u], vb[u]};
+    }
   }
   __syncthreads();
-  const C* F = fft_lines<-1>(a, b, n, V.pb, n, 1, false, V.tw[0]);
+  const C* F = fft_lines<-1>(a, b, ln, ilog2(pb), 1, 1, es, tw);
   C* W = V.W + (((size_t)comp * V.nz + z) * V.ny + y0) * V.nxp;
-  for (int idx = threadIdx.x; idx < V.pb * V.nxh; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < pb * V.nxh; idx += blockDim.x) {
     const int l = idx / V.nxh, k = idx - l * V.nxh;
-    const C f = F[(size_t)l * n + k], g = F[(size_t)l * n + ((n - k) & (n - 1))];
+    const C f = F[k * es + l], g = F[((n - k) & (n - 1)) * es + l];
     // row 2l: (f + conj g) / 2;  row 2l+1: (f - conj g) / (2i)
     W[(size_t)(2 * l) * V.nxp + k] = C{(R)0.5 * (f.x + g.x), (R)0.5 * (f.y - g.y)};
     W[(size_t)(2 * l + 1) * V.nxp + k] = C{(R)0.5 * (f.y + g.y), (R)-0.5 * (f.x - g.x)};
@@ -147,20 +257,32 @@ template <typename R, int SGN>
 __global__ void __launch_bounds__(NT) k_spec_y(Spec<R> V, const CgScal* S) {
   using C = typename CxOf<R>::T;
   if (spec_skip<R>(S)) return;
-  C* a = smem_cx<C>();
-  C* b = a + (size_t)V.tx * V.ny;
-  const int kx0 = blockIdx.x * V.tx, z = blockIdx.y, comp = blockIdx.z;
-  const int ncol = min(V.tx, V.nxh - kx0);
+  const int tx = V.tx, ltx = ilog2(tx);
+  C* tw = smem_cx<C>();
+  C* a = tw + V.ny;
+  C* b = a + (size_t)tx * V.ny;
+  load_roots(tw, V.tw[1], V.ny);
+  const int kx0 = blockIdx.x * tx, z = blockIdx.y, comp = blockIdx.z;
+  const int ncol = min(tx, V.nxh - kx0);
   C* W = V.W + ((size_t)comp * V.nz + z) * V.ny * V.nxp + kx0;
-  const int tx = V.tx;
-  for (int idx = threadIdx.x; idx < tx * V.ny; idx += blockDim.x) {
-    const int y = idx / tx, col = idx - y * tx;
-    a[idx] = col < ncol ? W[(size_t)y * V.nxp + col] : C{(R)0, (R)0};
+  const int total = tx * V.ny;
+  for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {
+    C v[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x, col = idx & (tx - 1);
+      v[u] = (idx < total && col < ncol) ? W[(size_t)(idx >> ltx) * V.nxp + col] : C{(R)0, (R)0};
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) a[idx] = v[u];
+    }
   }
   __syncthreads();
-  const C* F = fft_lines<SGN>(a, b, V.ny, tx, 1, tx, true, V.tw[1]);
+  const C* F = fft_lines<SGN>(a, b, ilog2(V.ny), ltx, 1, 1, tx, tw);
   for (int idx = threadIdx.x; idx < tx * V.ny; idx += blockDim.x) {
-    const int y = idx / tx, col = idx - y * tx;
+    const int y = idx >> ltx, col = idx & (tx - 1);
     if (col < ncol) W[(size_t)y * V.nxp + col] = F[idx];
   }
 }
@@ -172,26 +294,40 @@ template <typename R>
 __global__ void __launch_bounds__(NT) k_spec_z(Spec<R> V, const CgScal* S) {
   using C = typename CxOf<R>::T;
   if (spec_skip<R>(S)) return;
-  C* a = smem_cx<C>();
-  C* b = a + (size_t)3 * V.tz * V.nz;
-  const int kx0 = blockIdx.x * V.tz, ky = blockIdx.y;
-  const int tz = V.tz, lw = 3 * tz;          // lines: (component, column), interleaved
+  const int tz = V.tz, ltz = ilog2(tz), lw = 3 * tz;   // lines: (component, column)
+  C* tw = smem_cx<C>();
+  C* a = tw + V.nz;
+  C* b = a + (size_t)lw * V.nz;
+  load_roots(tw, V.tw[2], V.nz);
+  const int kx0 = blockIdx.x * tz, ky = blockIdx.y;
   const int ncol = min(tz, V.nxh - kx0);
   const size_t plane = (size_t)V.ny * V.nxp, comp_stride = (size_t)V.nz * plane;
   C* W = V.W + (size_t)ky * V.nxp + kx0;
-  for (int idx = threadIdx.x; idx < lw * V.nz; idx += blockDim.x) {
-    const int kz = idx / lw, rem = idx - kz * lw, comp = rem / tz, col = rem - comp * tz;
-    a[idx] = col < ncol ? W[comp * comp_stride + (size_t)kz * plane + col] : C{(R)0, (R)0};
+  const int total = lw * V.nz;
+  for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {
+    C v[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      const int col = idx & (tz - 1), rest = idx >> ltz, kz = rest / 3, comp = rest - 3 * kz;
+      v[u] = (idx < total && col < ncol) ? W[comp * comp_stride + (size_t)kz * plane + col]
+                                         : C{(R)0, (R)0};
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) a[idx] = v[u];
+    }
   }
   __syncthreads();
-  C* F = fft_lines<-1>(a, b, V.nz, lw, 1, lw, true, V.tw[2]);
+  C* F = fft_lines<-1>(a, b, ilog2(V.nz), ltz, 3, 1, lw, tw);
   C* other = F == a ? b : a;
   const R mu0 = (R)V.mean[0], lam0 = (R)V.mean[1], eta0 = (R)V.mean[2];
   const R c = lam0 + mu0;
   const R inv_vol = (R)(1.0 / ((double)V.nx * V.ny * V.nz));
   const R Sy = V.S[1][ky], Ty = V.T[1][ky];
   for (int idx = threadIdx.x; idx < tz * V.nz; idx += blockDim.x) {
-    const int kz = idx / tz, col = idx - kz * tz;
+    const int kz = idx >> ltz, col = idx & (tz - 1);
     if (col >= ncol) continue;
     const int kx = kx0 + col;
     const R Sv[3] = {V.S[0][kx], Sy, V.S[2][kz]};
@@ -220,9 +356,9 @@ __global__ void __launch_bounds__(NT) k_spec_z(Spec<R> V, const CgScal* S) {
     }
   }
   __syncthreads();
-  const C* G = fft_lines<+1>(F, other, V.nz, lw, 1, lw, true, V.tw[2]);
+  const C* G = fft_lines<+1>(F, other, ilog2(V.nz), ltz, 3, 1, lw, tw);
   for (int idx = threadIdx.x; idx < lw * V.nz; idx += blockDim.x) {
-    const int kz = idx / lw, rem = idx - kz * lw, comp = rem / tz, col = rem - comp * tz;
+    const int col = idx & (tz - 1), rest = idx >> ltz, kz = rest / 3, comp = rest - 3 * kz;
     if (col < ncol) W[comp * comp_stride + (size_t)kz * plane + col] = G[idx];
   }
 }
@@ -238,39 +374,73 @@ __global__ void __launch_bounds__(NT) k_spec_x_inv(Spec<R> V, const R* __restric
                                                    R* z2, CgScal* S) {
   using C = typename CxOf<R>::T;
   if (spec_skip<R>(S)) return;
-  C* a = smem_cx<C>();
-  C* b = a + (size_t)V.pb * V.nx;
+  const int n = V.nx, ln = ilog2(n), half = n / 2, pb = V.pb, es = pb + 1;
+  C* tw = smem_cx<C>();
+  C* a = tw + n;
+  C* b = a + (size_t)es * n;
+  load_roots(tw, V.tw[0], n);
   const int comp = blockIdx.z, z = blockIdx.y, y0 = 2 * V.pb * blockIdx.x;
-  const int n = V.nx, half = n / 2;
   const C* W = V.W + (((size_t)comp * V.nz + z) * V.ny + y0) * V.nxp;
-  for (int idx = threadIdx.x; idx < V.pb * n; idx += blockDim.x) {
-    const int l = idx / n, k = idx - l * n;
-    const bool lower = k <= half;
-    const int kk = lower ? k : n - k;
-    C A = W[(size_t)(2 * l) * V.nxp + kk], B = W[(size_t)(2 * l + 1) * V.nxp + kk];
-    if (k == 0 || k == half) {
-      A.y = (R)0;
-      B.y = (R)0;
-    } else if (!lower) {
-      A.y = -A.y;
-      B.y = -B.y;
+  const int total = pb * n;
+  for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {
+    C A[LB], B[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) {
+        const int l = idx >> ln, k = idx & (n - 1);
+        const int kk = k <= half ? k : n - k;
+        A[u] = __ldg(W + (size_t)(2 * l) * V.nxp + kk);
+        B[u] = __ldg(W + (size_t)(2 * l + 1) * V.nxp + kk);
+      }
     }
-    a[idx] = C{A.x - B.y, A.y + B.x};
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) {
+        const int l = idx >> ln, k = idx & (n - 1);
+        C a_ = A[u], b_ = B[u];
+        if (k == 0 || k == half) {
+          a_.y = (R)0;
+          b_.y = (R)0;
+        } else if (k > half) {
+          a_.y = -a_.y;
+          b_.y = -b_.y;
+        }
+        a[k * es + l] = C{a_.x - b_.y, a_.y + b_.x};
+      }
+    }
   }
   __syncthreads();
-  const C* F = fft_lines<+1>(a, b, n, V.pb, n, 1, false, V.tw[0]);
+  const C* F = fft_lines<+1>(a, b, ln, ilog2(pb), 1, 1, es, tw);
   const R* rs = comp == 0 ? r0 : (comp == 1 ? r1 : r2);
   R* zs = comp == 0 ? z0 : (comp == 1 ? z1 : z2);
   const size_t row0 = ((size_t)z * V.ny + y0) * n;
   double acc[1] = {0.0};
   R part = (R)0;
-  for (int idx = threadIdx.x; idx < V.pb * n; idx += blockDim.x) {
-    const int l = idx / n, x = idx - l * n;
-    const size_t o = row0 + (size_t)(2 * l) * n + x;
-    const C f = F[idx];
-    zs[o] = f.x;
-    zs[o + n] = f.y;
-    part += rs[o] * f.x + rs[o + n] * f.y;
+  for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {
+    R ra[LB], rb[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) {
+        const size_t o = row0 + (size_t)(2 * (idx >> ln)) * n + (idx & (n - 1));
+        ra[u] = __ldg(rs + o);
+        rb[u] = __ldg(rs + o + n);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) {
+        const int l = idx >> ln, x = idx & (n - 1);
+        const size_t o = row0 + (size_t)(2 * l) * n + x;
+        const C f = F[x * es + l];
+        zs[o] = f.x;
+        zs[o + n] = f.y;
+        part += ra[u] * f.x + rb[u] * f.y;
+      }
+    }
   }
   acc[0] = (double)part;
   if (S == nullptr) return;
@@ -365,7 +535,7 @@ cudaError_t launch_spectral(const Spec<R>& V, const R* const r[3], R* const z[3]
   const dim3 gz((V.nxh + V.tz - 1) / V.tz, V.ny);
   k_spec_x_fwd<R><<<gx, NT, spec_smem_x(V), st>>>(V, r[0], r[1], r[2], S);
   k_spec_y<R, -1><<<gy, NT, spec_smem_y(V), st>>>(V, S);
-  k_spec_z<R><<<gz, NT, spec_smem_z(V), st>>>(V, S);
+  k_spec_z<R><<<gz, V.nt_z, spec_smem_z(V), st>>>(V, S);
   k_spec_y<R, +1><<<gy, NT, spec_smem_y(V), st>>>(V, S);
   k_spec_x_inv<R><<<gx, NT, spec_smem_x(V), st>>>(V, r[0], r[1], r[2], z[0], z[1], z[2], S);
   return cudaGetLastError();
