@@ -737,7 +737,8 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   REC(T_OD, S.o);
   REC(T_LD, S.l);
   // S2 fix-up and S3-S5 reactions
-  CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l, s));
+  CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l,
+                  X->prec == TG_MIXED, s));
   X->launches += 1;
   // S6-S7: elasticity from the post-reaction state, then v = du / dt
   e = build_elas_coef(X, true);
@@ -838,7 +839,7 @@ tg_status do_adjoint_step(tg_ctx* X, double dt, const void* tape, const tg_state
   CK(launch_diff_coef(G, X->dp, dt, T.g, T.w, T.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
                       X->a[A_RHO], s));
   CK(launch_react(G, X->dp, dt, X->a[A_RHO], T.idag, qp[0], qp[1], qp[2], qp[3], qp[4], qp[5],
-                  qp[6], s));
+                  qp[6], X->prec == TG_MIXED, s));
   // S6^T: coefficients at q+, adjoint solve, sensitivities
   CK(launch_lame(G, X->dp, qp[0], qp[1], qp[2], qp[3], qp[4], T.fplus, X->st.bg, X->a[A_MU],
                  X->a[A_LAM], X->a[A_ETA], s));
@@ -1316,7 +1317,8 @@ tg_status queue_post_diffusion(tg_ctx* X, double dt) {
   tg_state& S = X->st;
   cudaStream_t s = X->stream;
   const size_t bytes = (size_t)G.nvox * sizeof(double);
-  CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l, s));
+  CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l,
+                  X->prec == TG_MIXED, s));
   tg_status e = build_elas_coef(X, true);
   if (e != TG_OK) return e;
   double* const u[3] = {S.u[0], S.u[1], S.u[2]};

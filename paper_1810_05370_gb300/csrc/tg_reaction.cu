@@ -5,31 +5,40 @@
 namespace tg {
 namespace {
 
+// The rates are evaluated in T: FP64, or FP32 in the mixed precision (the state and its
+// Heun update stay FP64; only the rate arithmetic, dominated by exp and divisions, drops to
+// FP32, whose relative error ~1e-7 in an increment dt * rate is far below the mixed
+// precision's tolerance).
+__device__ __forceinline__ double exp_t(double x) { return exp(x); }
+__device__ __forceinline__ float exp_t(float x) { return expf(x); }
+
 // smoothed Heaviside H(x) = (1 + tanh(x / eps_H)) / 2, evaluated as 1 / (1 + exp(-2 x / eps_H))
 // (the same function; this form keeps full relative accuracy where H is tiny)
-__device__ __forceinline__ double heaviside(const DevParams& P, double x) {
-  return 1.0 / (1.0 + exp(-2.0 * x * P.inv_eps_H));
+template <typename T>
+__device__ __forceinline__ T heaviside(const DevParams& P, T x) {
+  return (T)1 / ((T)1 + exp_t((T)-2 * x * (T)P.inv_eps_H));
 }
 
 // oxygen factor of Eq. e:gog_reac_op / e:gog_reac_inv_op
-__device__ __forceinline__ double mitosis_factor(const DevParams& P, double o) {
-  if (o > P.o_inv) return 1.0;
-  if (o >= P.o_mit) return (o - P.o_mit) / (P.o_inv - P.o_mit);
-  return 0.0;
+template <typename T>
+__device__ __forceinline__ T mitosis_factor(const DevParams& P, T o) {
+  if (o > (T)P.o_inv) return (T)1;
+  if (o >= (T)P.o_mit) return (o - (T)P.o_mit) / (T)(P.o_inv - P.o_mit);
+  return (T)0;
 }
 
 // Sources of Eq. e:p, e:i, e:n, e:gm_wm, e:w at fixed oxygen (h, alpha and the mitosis
 // factor depend on o only and are passed in).
-__device__ __forceinline__ void species_rates(const DevParams& P, double rho, double o, double h,
-                                              double alpha, double mf, const double y[5],
-                                              double dy[5]) {
-  const double p = y[0], i = y[1], g = y[3], w = y[4];
-  const double beta = P.beta0 * heaviside(P, P.sigma_b - p - i) * o;   // Eq. e:beta
-  const double R = rho * p * (1.0 - p) * mf;                            // Eq. e:gog_reac_op
-  const double Rt = P.rho_i_frac * rho * i * (1.0 - i) * mf;            // Eq. e:gog_reac_inv_op
-  const double gw = g + w;
-  const double fg = gw > 0.0 ? g / gw : 0.0;
-  const double fw = gw > 0.0 ? w / gw : 0.0;
+template <typename T>
+__device__ __forceinline__ void species_rates(const DevParams& P, T rho, T o, T h, T alpha, T mf,
+                                              const T y[5], T dy[5]) {
+  const T p = y[0], i = y[1], g = y[3], w = y[4];
+  const T beta = (T)P.beta0 * heaviside<T>(P, (T)P.sigma_b - p - i) * o;   // Eq. e:beta
+  const T R = rho * p * ((T)1 - p) * mf;                                   // Eq. e:gog_reac_op
+  const T Rt = (T)P.rho_i_frac * rho * i * ((T)1 - i) * mf;                // Eq. e:gog_reac_inv_op
+  const T gw = g + w;
+  const T fg = gw > (T)0 ? g / gw : (T)0;
+  const T fw = gw > (T)0 ? w / gw : (T)0;
   dy[0] = R - alpha * p + beta * i - h * p;
   dy[1] = Rt + alpha * p - beta * i - h * i;
   dy[2] = h * (p + i + g + w);
@@ -37,6 +46,7 @@ __device__ __forceinline__ void species_rates(const DevParams& P, double rho, do
   dy[4] = -fw * (R + Rt) - h * w;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(NT) k_react(Geo G, DevParams P, double dt,
                                               const double* __restrict__ rho,
                                               const double* __restrict__ i_dag, double* p,
@@ -59,17 +69,20 @@ __global__ void __launch_bounds__(NT) k_react(Geo G, DevParams P, double dt,
       y[4] = y[4] - di * fw;
     }
     // S3: one Heun step with the post-diffusion oxygen and the step-start rho
-    const double oo = o[c], r = rho[c];
-    const double h = P.gamma * heaviside(P, P.o_hyp - oo);     // Eq. e:death
-    const double alpha = P.alpha0 * heaviside(P, P.o_inv - oo); // Eq. e:alpha
-    const double mf = mitosis_factor(P, oo);
-    double k1v[5], k2v[5], ys[5];
-    species_rates(P, r, oo, h, alpha, mf, y, k1v);
+    const double oo = o[c];
+    const T ot = (T)oo, r = (T)rho[c], dtt = (T)dt;
+    const T h = (T)P.gamma * heaviside<T>(P, (T)P.o_hyp - ot);     // Eq. e:death
+    const T alpha = (T)P.alpha0 * heaviside<T>(P, (T)P.o_inv - ot); // Eq. e:alpha
+    const T mf = mitosis_factor<T>(P, ot);
+    T yt[5], k1v[5], k2v[5], ys[5];
 #pragma unroll
-    for (int s = 0; s < 5; ++s) ys[s] = y[s] + dt * k1v[s];
-    species_rates(P, r, oo, h, alpha, mf, ys, k2v);
+    for (int s = 0; s < 5; ++s) yt[s] = (T)y[s];
+    species_rates<T>(P, r, ot, h, alpha, mf, yt, k1v);
 #pragma unroll
-    for (int s = 0; s < 5; ++s) y[s] = y[s] + 0.5 * dt * (k1v[s] + k2v[s]);
+    for (int s = 0; s < 5; ++s) ys[s] = yt[s] + dtt * k1v[s];
+    species_rates<T>(P, r, ot, h, alpha, mf, ys, k2v);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) y[s] = y[s] + 0.5 * dt * (double)(k1v[s] + k2v[s]);
     p[c] = y[0];
     ii[c] = y[1];
     n[c] = y[2];
@@ -124,8 +137,11 @@ __global__ void __launch_bounds__(NT) k_lame(Geo G, DevParams P, const double* _
 
 cudaError_t launch_react(const Geo& G, const DevParams& P, double dt, const double* rho,
                          const double* i_dag, double* p, double* i, double* n, double* g,
-                         double* w, double* o, double* l, cudaStream_t st) {
-  k_react<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, rho, i_dag, p, i, n, g, w, o, l);
+                         double* w, double* o, double* l, bool fp32_rates, cudaStream_t st) {
+  if (fp32_rates)
+    k_react<float><<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, rho, i_dag, p, i, n, g, w, o, l);
+  else
+    k_react<double><<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, rho, i_dag, p, i, n, g, w, o, l);
   return cudaGetLastError();
 }
 
