@@ -33,6 +33,7 @@ enum Arr32 {
   B_MU, B_LAM, B_ETA, B_DINV0, B_DINV1, B_DINV2,
   B_E0, B_E1, B_E2, B_R0, B_R1, B_R2, B_P0, B_P1, B_P2, B_PB0, B_PB1, B_PB2, B_Q0, B_Q1, B_Q2,
   B_V0, B_V1, B_V2, B_DIV, B_SQ0, B_SQ1, B_SQ2, B_SQ3, B_SQ4, B_SQ5,
+  B_CKF0, B_CKF1, B_CKF2, B_CDINV,   // FP32 CN faces and Jacobi inverse diagonal
   B_COUNT
 };
 
@@ -55,9 +56,18 @@ enum AdjArr {
 
 constexpr size_t ALIGN = 256;
 constexpr int MAX_NV = 9;    // largest number of values reduced by one kernel
-constexpr int N_SCAL = 5;    // 3 diffusion solves, elasticity (outer), elasticity inner FP32
+// 3 diffusion solves (outer in the mixed precision), elasticity (outer), elasticity inner
+// FP32, 3 inner FP32 diffusion solves
+constexpr int N_SCAL = 8;
 constexpr int MAX_SWEEPS = 64;        // refinement sweeps of one mixed-precision solve
 constexpr double TAU_INNER = 1e-4;    // smallest relative reduction asked of an inner solve
+// Which of the diffusion solves (bits: i, o, l) the mixed precision refines around FP32.
+// Oxygen stays FP64: a converged CN solve is fixed only to within its tolerance, and the
+// necrotic source h(o) (p + i + g + w) turns an oxygen difference do into a relative
+// difference of about (2 / eps_H) do = 200 do in n -- two solvers stopping at different
+// points of the same tolerance then differ by ~5e-5 in n (64^3 brain, rtol 1e-8), more than
+// the mixed precision's 1e-5.  i and l enter the other fields without such a gain.
+constexpr int CN_MIXED_MASK = 0b101;
 
 size_t round_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
@@ -332,6 +342,7 @@ struct tg_ctx {
   int prev_it_diff;
   int prev_it_elas;
   int prev_it_inner[2];   // inner FP32 iterations of the first and of later refinement sweeps
+  int prev_it_cn_inner[2];  // the same for the mixed precision's diffusion solves
   // profiling: launches queued, and optional event timing of the elasticity operator kernel
   long long launches;
   int timing;
@@ -443,11 +454,12 @@ Elas elas_view(tg_ctx* X, double* const u[3], double* const b[3]) {
 }
 
 // S2: the three Crank-Nicolson solves (i, o, l) on the faces built by S0.
-tg_status cn_solve3(tg_ctx* X, tg_stats* stats) {
+// mask: bit r set for the fields this call solves (the others are left untouched)
+tg_status cn_solve3(tg_ctx* X, tg_stats* stats, int mask = 7) {
   const Cn3 C = cn_view(X);
   k_cg_reset<<<1, 32, 0, X->stream>>>(X->scal, 3, X->prm.rtol_diff, X->prm.maxit_diff);
   CK(cudaGetLastError());
-  CK(launch_cn_init(X->G, C, X->stream));
+  CK(launch_cn_init(X->G, C, X->stream, mask));
   X->launches += 2;
   CgScal host[3];
   tg_status s = drive_cg(X, [&](int) {
@@ -457,6 +469,7 @@ tg_status cn_solve3(tg_ctx* X, tg_stats* stats) {
   if (s != TG_OK) return s;
   int itmax = 0;
   for (int r = 0; r < 3; ++r) {
+    if (!((mask >> r) & 1)) continue;
     if (host[r].status == CG_ZERO_RHS)
       CK(cudaMemsetAsync(C.x[r], 0, (size_t)X->G.nvox * sizeof(double), X->stream));
     itmax = std::max(itmax, host[r].it);
@@ -469,6 +482,77 @@ tg_status cn_solve3(tg_ctx* X, tg_stats* stats) {
   X->prev_it_diff = itmax;
   for (int r = 0; r < 3; ++r) {
     tg_status e = status_of(host[r]);
+    if (e != TG_OK) return fail(X, e);
+  }
+  return TG_OK;
+}
+
+Cn32 cn32_view(tg_ctx* X) {
+  Cn32 I;
+  for (int r = 0; r < 3; ++r) {   // the elasticity's FP32 CG vectors are free during S2
+    I.e[r] = X->b32[B_E0 + r];
+    I.r[r] = X->b32[B_R0 + r];
+    I.p[r] = X->b32[B_P0 + r];
+    I.q[r] = X->b32[B_Q0 + r];
+    I.Kf[r] = X->b32[B_CKF0 + r];
+  }
+  I.dinv = X->b32[B_CDINV];
+  I.S = X->scal + 5;
+  I.partial = X->partial;
+  I.counter = X->counter;
+  return I;
+}
+
+// S2 in the mixed precision: FP64 residuals around FP32 inner solves (the FP32 faces and
+// diagonal were written in S0).  Statistics count inner iterations.
+tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
+  const Cn3 C = cn_view(X);
+  const Cn32 I = cn32_view(X);
+  k_cg_reset<<<1, 32, 0, X->stream>>>(X->scal, 3, X->prm.rtol_diff, X->prm.maxit_diff);
+  CK(cudaGetLastError());
+  X->launches += 1;
+  int inner_total[3] = {0, 0, 0};
+  int sweeps = 0;
+  CgScal out[3];
+  for (;;) {
+    CK(launch_cn_ir_residual(X->G, C, I, X->scal, sweeps == 0, TAU_INNER, MAX_SWEEPS, mask,
+                             X->stream));
+    X->launches += 1;
+    CK(cudaMemcpyAsync(out, X->scal, 3 * sizeof(CgScal), cudaMemcpyDeviceToHost, X->stream));
+    CK(cudaStreamSynchronize(X->stream));
+    bool any = false;
+    for (int r = 0; r < 3; ++r) any |= out[r].status == CG_RUNNING;
+    if (!any) break;
+    CgScal host[3];
+    const int slot = sweeps == 0 ? 0 : 1;
+    tg_status st = drive_cg(X, [&](int) {
+      X->launches += 3;
+      return launch_cn32_iter(X->G, I, X->stream);
+    }, I.S, 3, X->prm.maxit_diff, X->prev_it_cn_inner[slot], host);
+    if (st != TG_OK) return st;
+    int itmax = 0;
+    for (int r = 0; r < 3; ++r) {
+      if (out[r].status == CG_RUNNING) inner_total[r] += host[r].it;
+      itmax = std::max(itmax, host[r].it);
+      if (host[r].status == CG_NONFINITE) return fail(X, TG_ERR_NONFINITE);
+    }
+    X->prev_it_cn_inner[slot] = itmax;
+    CK(launch_cn_ir_correct(X->G, C, I, mask, X->stream));
+    X->launches += 1;
+    ++sweeps;
+  }
+  for (int r = 0; r < 3; ++r) {
+    if (!((mask >> r) & 1)) continue;
+    if (out[r].status == CG_ZERO_RHS)
+      CK(cudaMemsetAsync(C.x[r], 0, (size_t)X->G.nvox * sizeof(double), X->stream));
+    if (stats) {
+      stats->it_diff[r] = inner_total[r];
+      stats->relres_diff[r] = out[r].bb > 0.0 ? sqrt(out[r].rr / out[r].bb) : 0.0;
+      stats->it_diff_total += inner_total[r];
+    }
+  }
+  for (int r = 0; r < 3; ++r) {
+    tg_status e = status_of(out[r]);
     if (e != TG_OK) return fail(X, e);
   }
   return TG_OK;
@@ -691,6 +775,17 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   double* const Kf[3] = {X->a[A_KF0], X->a[A_KF1], X->a[A_KF2]};
   CK(launch_diff_coef(G, X->dp, dt, S.g, S.w, S.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
                       X->a[A_RHO], s));
+  if (X->prec == TG_MIXED) {   // FP32 faces and diagonal of the inner diffusion solves
+    F32Copy cp;
+    const double* src[4] = {Kf[0], Kf[1], Kf[2], X->a[A_DINV_D]};
+    for (int q = 0; q < 4; ++q) {
+      cp.src[q] = src[q];
+      cp.dst[q] = X->b32[B_CKF0 + q];
+    }
+    cp.count = 4;
+    CK(launch_to_f32(G.nvox, cp, s));
+    X->launches += 1;
+  }
   // S1: semi-Lagrangian transport with v^n
   const double* const v[3] = {S.v[0], S.v[1], S.v[2]};
   CK(launch_divergence(G, v, X->a[A_DIV], s));
@@ -731,7 +826,13 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   }
   // S2: Crank-Nicolson diffusion of i, o, l (i after transport kept for the g, w fix-up)
   CK(cudaMemcpyAsync(X->a[A_IDAG], S.i, bytes, cudaMemcpyDeviceToDevice, s));
-  tg_status e = cn_solve3(X, stats);
+  tg_status e = TG_OK;
+  if (X->prec == TG_MIXED) {
+    e = cn_solve3(X, stats, 7 & ~CN_MIXED_MASK);
+    if (e == TG_OK) e = cn_solve3_mixed(X, stats, CN_MIXED_MASK);
+  } else {
+    e = cn_solve3(X, stats);
+  }
   if (e != TG_OK) return e;
   REC(T_IDD, S.i);
   REC(T_OD, S.o);

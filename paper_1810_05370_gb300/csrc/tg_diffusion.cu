@@ -50,15 +50,21 @@ __global__ void __launch_bounds__(NT) k_diff_coef(Geo G, DevParams P, double hal
   }
 }
 
-__global__ void __launch_bounds__(NT) k_cn_init(Geo G, Cn3 C) {
+// mask: bit r set for the solves to start; the others are marked finished
+__global__ void __launch_bounds__(NT) k_cn_init(Geo G, Cn3 C, int mask) {
   double acc[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) acc[q] = 0.0;
-  cn_init_tile(G, C, blockIdx.x, blockIdx.y, blockIdx.z, acc);
+  cn_init_tile(G, C, blockIdx.x, blockIdx.y, blockIdx.z, acc, mask);
   double out[9];
   if (reduce_last_block<9>(acc, C.partial, C.counter, out) && threadIdx.x == 0 && threadIdx.y == 0) {
 #pragma unroll
-    for (int r = 0; r < 3; ++r) cg_after_init(C.S[r], out[3 * r], out[3 * r + 1], out[3 * r + 2]);
+    for (int r = 0; r < 3; ++r) {
+      if ((mask >> r) & 1)
+        cg_after_init(C.S[r], out[3 * r], out[3 * r + 1], out[3 * r + 2]);
+      else
+        cg_skip(C.S[r]);
+    }
   }
 }
 
@@ -131,8 +137,8 @@ cudaError_t launch_diff_coef(const Geo& G, const DevParams& P, double dt, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_cn_init(const Geo& G, const Cn3& C, cudaStream_t st) {
-  k_cn_init<<<G.grid, dim3(BX, BY), 0, st>>>(G, C);
+cudaError_t launch_cn_init(const Geo& G, const Cn3& C, cudaStream_t st, int mask) {
+  k_cn_init<<<G.grid, dim3(BX, BY), 0, st>>>(G, C, mask);
   return cudaGetLastError();
 }
 

@@ -205,6 +205,14 @@ __device__ __forceinline__ void cg_after_precond(CgScal& S, double rz_new) {
   S.rz = rz_new;
 }
 
+// a solve left out of a masked launch: finished, with nothing done
+__device__ __forceinline__ void cg_skip(CgScal& S) {
+  S.it = 0;
+  S.bb = 0.0;
+  S.rr = 0.0;
+  S.status = CG_CONVERGED;
+}
+
 __device__ __forceinline__ void cg_after_init(CgScal& S, double bb, double rr, double rz) {
   S.bb = bb;
   S.rr = rr;
@@ -324,8 +332,29 @@ struct Cn3 {   // three simultaneous CN solves sharing one operator
   double* partial;
   unsigned int* counter;
 };
-cudaError_t launch_cn_init(const Geo&, const Cn3&, cudaStream_t st);
+cudaError_t launch_cn_init(const Geo&, const Cn3&, cudaStream_t st, int mask = 7);
 cudaError_t launch_cn_iter(const Geo&, const Cn3&, cudaStream_t st);
+
+// Mixed precision S2: iterative refinement around three FP32 CN solves.  The FP64 side keeps
+// the fields (Cn3::x), the right-hand sides (stored in Cn3::p) and the residuals; the FP32
+// side solves A e = r with Jacobi PCG on FP32 faces, the diagonal rebuilt from the faces.
+struct Cn32 {
+  float* e[3];
+  float* r[3];
+  float* p[3];
+  float* q[3];
+  const float* Kf[3];
+  const float* dinv;
+  CgScal* S;           // 3 inner solves
+  double* partial;
+  unsigned int* counter;
+};
+// FP64 residual r = rhs - A x (init: rhs = x + dt/2 D_h x is formed and stored first), its
+// FP32 copy, e = 0, and the outer test / inner start per right-hand side (Sout: 3 entries)
+cudaError_t launch_cn_ir_residual(const Geo&, const Cn3&, const Cn32&, CgScal* Sout, bool init,
+                                  double tau_min, int max_sweeps, int mask, cudaStream_t st);
+cudaError_t launch_cn32_iter(const Geo&, const Cn32&, cudaStream_t st);
+cudaError_t launch_cn_ir_correct(const Geo&, const Cn3&, const Cn32&, int mask, cudaStream_t st);
 
 // SL (S1)
 cudaError_t launch_divergence(const Geo&, const double* const v[3], double* div, cudaStream_t st);

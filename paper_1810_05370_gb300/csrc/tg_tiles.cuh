@@ -418,9 +418,9 @@ __device__ __forceinline__ Faces load_faces(const Cn3& C, const Nbr& nb, long lo
 }
 
 // CN start on one tile: x0 = c, rhs = c + s, r0 = 2 s with s = dt/2 D_h c; accumulates
-// (|rhs|^2, |r|^2, <r, D^{-1} r>) per right-hand side.
+// (|rhs|^2, |r|^2, <r, D^{-1} r>) per right-hand side in the bit mask (bit r: solve r).
 __device__ __forceinline__ void cn_init_tile(const Geo& G, const Cn3& C, int bx, int by, int bz,
-                                             double (&acc)[9]) {
+                                             double (&acc)[9], int mask = 7) {
   const int i = bx * BX + threadIdx.x;
   const int j = by * BY + threadIdx.y;
   if (i >= G.nx || j >= G.ny) return;
@@ -432,6 +432,7 @@ __device__ __forceinline__ void cn_init_tile(const Geo& G, const Cn3& C, int bx,
     const double di = C.dinv[c];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
+      if (!((mask >> r) & 1)) continue;
       const double* x = C.x[r];
       const double xc = x[c];
       const double s = F.xp * (x[nb.at(1, 0, 0)] - xc) - F.xm * (xc - x[nb.at(-1, 0, 0)]) +
