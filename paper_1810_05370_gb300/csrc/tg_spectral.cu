@@ -22,8 +22,10 @@
 //   y inverse  in place;
 //   x inverse  the Hermitian half spectra of two rows form one complex line whose inverse
 //              transform carries both real rows; writes z and reduces <r, z>.
-// The 1-D transforms are Stockham autosort FFTs (radix 4, one radix-2 stage when log2 n is
-// odd) ping-ponging between two shared-memory buffers, one barrier per stage.
+// The 1-D transforms are Stockham autosort FFTs whose butterflies are radix-16 DFTs held in
+// registers (one radix-2, 4 or 8 stage takes the remainder of log2 n), ping-ponging between
+// two shared-memory buffers with one barrier per stage; each block keeps its line length's
+// twiddles in shared memory and issues its global loads in batches of eight per thread.
 #include "tg_tiles.cuh"
 
 namespace tg {
