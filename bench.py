@@ -34,9 +34,12 @@ FIELDS = ("p", "i", "n", "g", "w", "f", "o", "l", "bg", "ux", "uy", "uz", "vx", 
 # Algorithmic traffic and arithmetic of the elasticity operator kernel, per voxel and launch.
 # FP64 path: reads p (3 comps), face coefficients (lambda+2mu)/h^2 and mu/h^2 (3 + 3), Jacobi
 # diagonal (3), node mu and lambda (2); writes q (3): 17 FP64 arrays; 123 FP64 flops.
-# Mixed path (the CG p-update is fused into the operator kernel): reads r, D^{-1}, p_old (3 each)
-# and node mu, lambda, eta, writes p_new and q (3 each): 18 FP32 arrays.
-ELAS_MATVEC_BYTES_PER_VOXEL = {"fp64": 17 * 8, "mixed": 18 * 4}
+# Mixed path (the CG p-update is fused into the operator kernel): with Jacobi it reads r,
+# D^{-1}, p_old (3 each) and node mu, lambda, eta and writes p_new and q (3 each): 18 FP32
+# arrays; with the spectral preconditioner the preconditioned residual z (3) replaces r and
+# D^{-1} (6): 15 FP32 arrays.
+ELAS_MATVEC_BYTES_PER_VOXEL = {("fp64", "jacobi"): 17 * 8, ("fp64", "spectral"): 17 * 8,
+                               ("mixed", "jacobi"): 18 * 4, ("mixed", "spectral"): 15 * 4}
 ELAS_MATVEC_FLOPS_PER_VOXEL = 123
 
 
@@ -299,7 +302,7 @@ def main():
 
     def roofline(agg, precision):
         avg_ms = agg["t_mv"] / max(agg["n_mv"], 1)
-        mv_bytes = ELAS_MATVEC_BYTES_PER_VOXEL[precision] * V
+        mv_bytes = ELAS_MATVEC_BYTES_PER_VOXEL[(precision, args.precond)] * V
         gbs = mv_bytes / (avg_ms * 1e-3) / 1e9
         share = agg["t_mv"] / agg["ms"] if agg["ms"] > 0 else None
         if precision == "fp64":
@@ -310,12 +313,13 @@ def main():
                     "peak_source": "derived FP64 roof (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                     "hbm_gbs": gbs, "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"],
                     "share_of_step": share}
-        return {"kernel": "k_elas32_matvec (FP32 19-point Navier-Lame operator, faces on the fly, "
+        kname = "k_elas32_matvec_spec" if args.precond == "spectral" else "k_elas32_matvec"
+        return {"kernel": f"{kname} (FP32 19-point Navier-Lame operator, faces on the fly, "
                           "fused p-update, + <p, Ap>)",
                 "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": gbs / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": f"{peak_src} HBM copy bandwidth",
-                "bytes_per_voxel": ELAS_MATVEC_BYTES_PER_VOXEL[precision],
+                "bytes_per_voxel": ELAS_MATVEC_BYTES_PER_VOXEL[(precision, args.precond)],
                 "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"], "share_of_step": share}
 
     roof = roofline(agg, args.precision)

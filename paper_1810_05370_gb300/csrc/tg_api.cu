@@ -622,6 +622,8 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
     CK(cudaStreamSynchronize(X->stream));
     if (out.status != CG_RUNNING) break;
     if (sweeps >= MAX_SWEEPS || inner_total >= X->prm.maxit_elas) return fail(X, TG_ERR_NOCONV);
+    CK(launch_elas32_scale_r(X->G, I, X->stream));
+    X->launches += 1;
     if (spec) {   // z = P r and <r, z> for the inner solve's first direction
       CK(launch_spectral(X->sp32, r32, X->z32, I.S, X->stream));
       X->launches += 5;

@@ -44,6 +44,7 @@ struct CgScal {
   double alpha;
   double beta;
   double rtol;
+  double scale;  // inner solves of a refinement: the right-hand side was multiplied by it
   int it;
   int maxit;
   int status;
@@ -458,6 +459,7 @@ template <typename R>
 cudaError_t launch_spectral(const Spec<R>&, const R* const r[3], R* const z[3], CgScal* S,
                             cudaStream_t st);
 cudaError_t launch_elas32_matvec_spec(const Geo&, const Elas32&, cudaStream_t st);
+cudaError_t launch_elas32_scale_r(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_elas32_update_spec(const Geo&, const Elas32&, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- batches

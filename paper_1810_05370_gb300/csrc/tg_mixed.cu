@@ -117,13 +117,26 @@ __global__ void __launch_bounds__(NT) k_elas_ir_residual(Geo G, Elas E, Elas32 I
   elas_ir_residual_tile(G, E, I, minus_b, blockIdx.x, blockIdx.y, blockIdx.z, acc);
   double out[3];
   if (reduce_last_block<3>(acc, E.partial, E.counter, out) && threadIdx.x == 0 && threadIdx.y == 0)
-    elas_ir_residual_finalize(*Sout, *I.S, out[0], out[1], out[2], tau_min, max_sweeps);
+    elas_ir_residual_finalize(*Sout, *I.S, out[0], out[1], out[2], tau_min, max_sweeps, true);
+}
+
+// r *= scale (the inner solve's right-hand side normalisation, a power of two: exact)
+__global__ void __launch_bounds__(NT) k_elas32_scale_r(long long n, Elas32 I) {
+  if (!running(I.S)) return;
+  const float s = (float)I.S->scale;
+  if (s == 1.0f) return;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) I.r[a][c] *= s;
+  }
 }
 
 // u += e, du += e (FP64 accumulation of the FP32 correction)
 __global__ void __launch_bounds__(NT) k_elas_ir_correct(long long n, Elas E, Elas32 I) {
   const long long stride = (long long)gridDim.x * blockDim.x;
-  elas_ir_correct_range(E, I, (long long)blockIdx.x * blockDim.x + threadIdx.x, n, stride);
+  elas_ir_correct_range(E, I, (long long)blockIdx.x * blockDim.x + threadIdx.x, n, stride,
+                        1.0 / I.S->scale);
 }
 
 // v = du / dt; a vanishing right-hand side means u = 0
@@ -261,6 +274,11 @@ static int reduce_blocks(const Geo& G, long long items) {
 
 cudaError_t launch_elas32_update(const Geo& G, const Elas32& I, cudaStream_t st) {
   k_elas32_update<<<reduce_blocks(G, (G.nvox + 3) / 4), NT, 0, st>>>(G.nvox, I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elas32_scale_r(const Geo& G, const Elas32& I, cudaStream_t st) {
+  k_elas32_scale_r<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, I);
   return cudaGetLastError();
 }
 

@@ -57,6 +57,7 @@ __device__ __forceinline__ CgScal ld_cg(const CgScal* p) {
   s.alpha = v->alpha;
   s.beta = v->beta;
   s.rtol = v->rtol;
+  s.scale = v->scale;
   s.it = v->it;
   s.maxit = v->maxit;
   s.status = v->status;
@@ -72,6 +73,7 @@ __device__ __forceinline__ void st_cg(CgScal* p, const CgScal& s) {
   v->alpha = s.alpha;
   v->beta = s.beta;
   v->rtol = s.rtol;
+  v->scale = s.scale;
   v->it = s.it;
   v->maxit = s.maxit;
   v->status = s.status;
@@ -356,10 +358,15 @@ __device__ __forceinline__ void elas_ir_residual_tile(const Geo& G, const Elas& 
 // Outer decision after a residual (the same test as the FP64 solve: |r| <= rtol |rhs|) and the
 // start of the inner FP32 solve A e = r with relative target max(tau_min, half of what the
 // outer still needs).  O.pad counts the inner iterations spent so far; a solve that exceeds
-// max_sweeps residuals or maxit inner iterations stops with CG_MAXIT.
+// max_sweeps residuals or maxit inner iterations stops with CG_MAXIT.  With normalize the
+// inner right-hand side is to be multiplied by S.scale, the power of two nearest 1 / |r|, so
+// that the FP32 iteration sees values of order one whatever the residual's size (deep
+// tolerances or small adjoint sources would otherwise underflow FP32 products); the inner
+// scalars are set for the scaled system and the correction divides by S.scale.
 __device__ __forceinline__ void elas_ir_residual_finalize(CgScal& O, CgScal& S, double bb,
                                                           double rr, double rz, double tau_min,
-                                                          int max_sweeps) {
+                                                          int max_sweeps,
+                                                          bool normalize = false) {
   if (O.it > 0) O.pad += S.it;
   O.bb = bb;
   O.rr = rr;
@@ -375,9 +382,12 @@ __device__ __forceinline__ void elas_ir_residual_finalize(CgScal& O, CgScal& S, 
   } else {
     O.status = CG_RUNNING;
   }
-  S.bb = rr;
-  S.rr = rr;
-  S.rz = rz;
+  const double s =
+      (normalize && rr > 0.0 && isfinite(rr)) ? exp2(-rint(0.5 * log2(rr))) : 1.0;
+  S.scale = s;
+  S.bb = rr * s * s;
+  S.rr = rr * s * s;
+  S.rz = rz * s * s;
   S.it = 0;
   S.maxit = O.maxit;
   S.alpha = 0.0;
@@ -386,13 +396,15 @@ __device__ __forceinline__ void elas_ir_residual_finalize(CgScal& O, CgScal& S, 
   S.status = (O.status == CG_RUNNING) ? CG_RUNNING : CG_CONVERGED;
 }
 
-// u += e, du += e over voxels c = c0, c0 + cs, ... < c1
+// u += e / scale, du += e / scale over voxels c = c0, c0 + cs, ... < c1 (scale: the inner
+// right-hand side's factor, a power of two)
 __device__ __forceinline__ void elas_ir_correct_range(const Elas& E, const Elas32& I, long long c0,
-                                                      long long c1, long long cs) {
+                                                      long long c1, long long cs,
+                                                      double inv_scale = 1.0) {
   for (long long c = c0; c < c1; c += cs) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double e = (double)I.e[a][c];
+      const double e = (double)I.e[a][c] * inv_scale;
       E.u[a][c] += e;
       E.du[a][c] += e;
     }
