@@ -68,7 +68,7 @@ def _make_types(cs):
             ("delta_e", R), ("delta_half", R), ("delta_l", R),
             ("rtol_diff", C.c_double), ("rtol_elas", C.c_double),
             ("maxit_diff", C.c_int32), ("maxit_elas", C.c_int32),
-            ("precond_elas", C.c_int32)]
+            ("precond_elas", C.c_int32), ("model", C.c_int32)]
 
     P = C.POINTER(R)
 
@@ -120,7 +120,7 @@ class Oracle:
                     arr[s] = self._r(d[name][s])
             elif name in ("maxit_diff", "maxit_elas"):
                 setattr(p, name, int(d[name]))
-            elif name == "precond_elas":
+            elif name in ("precond_elas", "model"):
                 setattr(p, name, int(d.get(name, 0)))
             elif name in ("rtol_diff", "rtol_elas"):
                 setattr(p, name, float(d[name]))
@@ -279,6 +279,11 @@ class Oracle:
         arg = self._r(x) if self.cs else C.c_double(float(np.real(x)))
         r = self.lib.or_heaviside(C.byref(self.params(params)), arg)
         return complex(r.re, r.im) if self.cs else float(r)
+
+    def react_single(self, n, dt, rho, st, L=None):
+        """Single-species reaction, in place on st['p'] (c), st['g'], st['w']."""
+        self.lib.or_react_single(C.byref(self.grid(n, L)), C.c_double(dt), self._ptr(rho),
+                                 *[self._ptr(st[k]) for k in ("p", "g", "w")])
 
     def react(self, n, params, dt, rho, st, L=None):
         """In place on st['p','i','n','g','w','o','l']."""

@@ -695,6 +695,34 @@ void or_react(const or_grid* G, const or_params* P, double dt, const real_t* rho
   }
 }
 
+/* Single-species model (Eq. e:rd): one Heun step of the reaction part,
+ *   d_t c = R,  d_t g = -g/(g+w) R,  d_t w = -w/(g+w) R,  R = rho c (1 - c)  (Eq. e:reac_op),
+ * rho frozen at the step's start (reading 10); the ratio is 0 where g + w <= 0. */
+static void single_rates(real_t rho, const real_t y[3], real_t dy[3]) {
+  real_t R = rho * y[0] * (1.0 - y[0]);
+  real_t gw = y[1] + y[2];
+  real_t fg = RE(gw) > 0.0 ? y[1] / gw : 0.0;
+  real_t fw = RE(gw) > 0.0 ? y[2] / gw : 0.0;
+  dy[0] = R;
+  dy[1] = -fg * R;
+  dy[2] = -fw * R;
+}
+
+void or_react_single(const or_grid* G, double dt, const real_t* rho, real_t* c, real_t* g,
+                     real_t* w) {
+  int64_t m = nvox(G);
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < m; ++e) {
+    real_t y[3] = {c[e], g[e], w[e]};
+    real_t k1[3], k2[3], ys[3];
+    single_rates(rho[e], y, k1);
+    for (int s = 0; s < 3; ++s) ys[s] = y[s] + dt * k1[s];
+    single_rates(rho[e], ys, k2);
+    for (int s = 0; s < 3; ++s) y[s] = y[s] + 0.5 * dt * (k1[s] + k2[s]);
+    c[e] = y[0]; g[e] = y[1]; w[e] = y[2];
+  }
+}
+
 /* ---------------------------------------------------------------- step */
 
 static real_t* alloc_field(int64_t m) { return (real_t*)calloc((size_t)m, sizeof(real_t)); }
@@ -745,7 +773,10 @@ int or_init(const or_grid* G, const or_params* P, or_state* S, or_stats* stats) 
   return st;
 }
 
-/* One step of the multispecies splitting (Section 3):
+/* One step of the multispecies splitting (Section 3), or of the single-species one for
+ * P->model == 1 (Section 3's list for Eq. e:rd: c in p; S2 diffuses c alone and S3 is the
+ * logistic reaction of c with its loss from g and w; i and n, zero for that model, are only
+ * advected; o and l are left alone):
  *  S0  K (faces) and rho from the state at the step's start;
  *  S1  semi-Lagrangian advection of p, i, n, g, w (conservative) and f with v^n;
  *  S2  Crank-Nicolson diffusion of i, o and edema l; the increment of i leaves g and w;
@@ -773,24 +804,30 @@ int or_step(const or_grid* G, const or_params* P, double dt, or_state* S, or_sta
   or_sl_advect(G, dt, S->v[0], S->v[1], S->v[2], qin, qout);
   for (int s = 0; s < 6; ++s) memcpy(qin[s], qout[s], (size_t)m * sizeof(real_t));
 
-  /* S2 */
-  real_t* i_old = qout[0];            /* reuse as scratch: i after advection */
-  memcpy(i_old, S->i, (size_t)m * sizeof(real_t));
-  real_t* fields[3] = {S->i, S->o, S->l};
-  for (int c = 0; c < 3 && st == OR_OK; ++c)
+  /* S2: the diffusing fields are i, o, l (multispecies) or c, kept in p (single species,
+   * Section 3's list for Eq. e:rd); the increment of the first leaves g and w */
+  const int single = P->model == 1;
+  real_t* dif = single ? S->p : S->i;
+  real_t* i_old = qout[0];            /* reuse as scratch: the field after advection */
+  memcpy(i_old, dif, (size_t)m * sizeof(real_t));
+  real_t* fields[3] = {dif, S->o, S->l};
+  for (int c = 0; c < (single ? 1 : 3) && st == OR_OK; ++c)
     st = or_cn_solve(G, Kf[0], Kf[1], Kf[2], dt, fields[c], fields[c], P->rtol_diff,
                      P->maxit_diff, &local.it_diff[c], &local.relres_diff[c]);
   if (st == OR_OK) {
     for (int64_t e = 0; e < m; ++e) {
-      real_t di = S->i[e] - i_old[e];
+      real_t di = dif[e] - i_old[e];
       real_t g = S->g[e], w = S->w[e], gw = g + w;
       real_t fg = RE(gw) > 0.0 ? g / gw : 0.0;
       real_t fw = RE(gw) > 0.0 ? w / gw : 0.0;
       S->g[e] = g - di * fg;
       S->w[e] = w - di * fw;
     }
-    /* S3 - S5 */
-    or_react(G, P, dt, rho, S->p, S->i, S->n, S->g, S->w, S->o, S->l);
+    /* S3 - S5 (single species: the logistic reaction of c with the g, w losses) */
+    if (single)
+      or_react_single(G, dt, rho, S->p, S->g, S->w);
+    else
+      or_react(G, P, dt, rho, S->p, S->i, S->n, S->g, S->w, S->o, S->l);
     /* S6 - S7 */
     real_t* u_old[3] = {qout[1], qout[2], qout[3]};
     for (int a = 0; a < 3; ++a) memcpy(u_old[a], S->u[a], (size_t)m * sizeof(real_t));

@@ -39,6 +39,7 @@ typedef struct {
   double rtol_diff, rtol_elas;            /* Krylov stopping: |r| <= rtol |rhs|           */
   int32_t maxit_diff, maxit_elas;
   int32_t precond_elas;                   /* 0 Jacobi, 1 spectral (Section 3)             */
+  int32_t model;                          /* 0 multispecies, 1 single species (Eq. e:rd)  */
 } or_params;
 
 typedef struct {
@@ -90,4 +91,6 @@ void or_sl_advect(const or_grid*, double dt, const real_t* vx, const real_t* vy,
 real_t or_heaviside(const or_params*, real_t x);
 void or_react(const or_grid*, const or_params*, double dt, const real_t* rho, real_t* p,
               real_t* i, real_t* n, real_t* g, real_t* w, real_t* o, real_t* l);
+void or_react_single(const or_grid*, double dt, const real_t* rho, real_t* c, real_t* g,
+                     real_t* w);
 #endif

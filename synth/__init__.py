@@ -5,12 +5,13 @@ parameter sets of the benchmark workloads and seeded random draws.  It contains 
 time-step arithmetic (no operators, solvers, interpolation or reaction terms), so both the
 oracle and the GPU path can consume its output without sharing any of the method.
 """
-from .brain import synthetic_brain, initial_state, grf_terms, evaluate_grf
+from .brain import synthetic_brain, initial_state, initial_state_single, grf_terms, evaluate_grf
 from .params import table_setup_params, workload_params, batch_workload, WORKLOADS
 
 __all__ = [
     "synthetic_brain",
     "initial_state",
+    "initial_state_single",
     "grf_terms",
     "evaluate_grf",
     "table_setup_params",

@@ -151,3 +151,14 @@ def initial_state(n, seed: int = 0, o_heal: float = 1.0):
     for c in ("ux", "uy", "uz", "vx", "vy", "vz"):
         st[c] = np.zeros_like(p)
     return {k2: np.ascontiguousarray(v) for k2, v in st.items()}
+
+
+def initial_state_single(n, seed: int = 0, o_heal: float = 1.0):
+    """Initial state of the single-species model (tumor density c stored in "p"): the same
+    tumor shape with c0 = 0.88 G_t (g + w), the mass the healthy tissue gives up, so that
+    c + g + w equals the healthy tissue; i = n = l = 0 and o = o_heal (unused by the model)."""
+    st = initial_state(n, seed, o_heal)
+    b = synthetic_brain(n, seed)
+    st["p"] = np.ascontiguousarray(0.88 * b["tumor"] * (b["g"] + b["w"]))
+    st["i"] = np.zeros_like(st["p"])
+    return st

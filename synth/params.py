@@ -47,6 +47,9 @@ def table_setup_params():
         # elasticity preconditioner: 0 Jacobi, 1 the constant-coefficient spectral inverse
         # with domain-mean Lame coefficients (Section 3)
         "precond_elas": 0,
+        # 0: the multispecies model (Eq. e:gog); 1: the single-species model (Eq. e:rd),
+        # whose tumor density c lives in p
+        "model": 0,
     }
 
 

@@ -719,3 +719,56 @@ def test_spectral_pcg_matches_jacobi_on_brain(oracle):
     assert rs <= 1e-10
     assert np.abs(us - uj).max() <= 1e-7 * np.abs(uj).max()
     assert its < 0.6 * itj
+
+
+# ----------------------------------------------------------------- single-species model
+
+def test_single_species_reaction_logistic_third_order_and_mass(oracle):
+    """Eq. e:reac_op: c' = rho c (1 - c) has the exact flow c e^{rho t} / (1 - c + c e^{rho t});
+    one Heun step errs by O(dt^3); g and w lose what c gains, in proportion g : w."""
+    n = (4, 4, 4)
+    errs = []
+    for dt in (0.02, 0.01, 0.005):
+        st = {"p": np.full((4, 4, 4), 0.3), "g": np.full((4, 4, 4), 0.4),
+              "w": np.full((4, 4, 4), 0.25)}
+        oracle.react_single(n, dt, np.full((4, 4, 4), 10.0), st)
+        e = np.exp(10.0 * dt)
+        errs.append(abs(st["p"][0, 0, 0] - 0.3 * e / (1 - 0.3 + 0.3 * e)))
+        gain = st["p"][0, 0, 0] - 0.3
+        assert abs((0.4 - st["g"][0, 0, 0]) - gain * 0.4 / 0.65) < 1e-14
+        assert abs((0.25 - st["w"][0, 0, 0]) - gain * 0.25 / 0.65) < 1e-14
+    for q in order(errs):
+        assert 2.7 < q < 3.3, errs
+
+
+def test_single_species_step_diffuses_c_and_conserves_mass(oracle):
+    """Single-species split (Section 3, Eq. e:rd): with v = 0 the step keeps c + g + w per
+    voxel; c diffuses (its CN solve runs), o, l and i = 0 stay as they were."""
+    from synth import initial_state_single
+    n = (16, 16, 16)
+    st = initial_state_single(n, seed=3)
+    P = workload_params(model=1)
+    o0, l0 = st["o"].copy(), st["l"].copy()
+    m0 = st["p"] + st["g"] + st["w"]
+    oracle.init(n, P, st)
+    s = oracle.step(n, P, 0.01, st)
+    m1 = st["p"] + st["g"] + st["w"]
+    assert np.max(np.abs(m1 - m0)) <= 1e-14 * max(1.0, m0.max())
+    assert s["it_diff"][0] > 0 and s["it_diff"][1] == 0 and s["it_diff"][2] == 0
+    assert np.array_equal(st["o"], o0) and np.array_equal(st["l"], l0)
+    assert np.max(np.abs(st["i"])) == 0.0 and np.max(np.abs(st["n"])) == 0.0
+    assert np.max(np.abs(st["vx"])) > 0
+
+
+def test_single_species_diffusion_spreads_the_tumor(oracle):
+    """Without growth (rho = 0) the tumor mass sum c is conserved by the step up to the CN
+    residual and its peak falls (Eq. e:diffusion_op)."""
+    from synth import initial_state_single
+    n = (16, 16, 16)
+    st = initial_state_single(n, seed=4)
+    P = workload_params(model=1, rho_g=0.0, rho_w=0.0, rtol_diff=1e-13)
+    c0 = st["p"].copy()
+    oracle.init(n, P, st)
+    oracle.step(n, P, 0.05, st)
+    assert abs(st["p"].sum() - c0.sum()) <= 1e-9 * c0.sum()
+    assert st["p"].max() < c0.max()
