@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=50)
     ap.add_argument("--adjoint-checkpoint", type=int, default=10)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-single", action="store_true",
+                    help="skip the single-species model (Eq. e:rd) line")
     ap.add_argument("--batch-sims", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--cpu-sample-n", type=int, default=64)
@@ -398,6 +400,22 @@ def main():
         torch.cuda.empty_cache()
 
     # ---------------------------------------------------------------- batched workload (rank 0)
+    # ---------------------------------------------------------------- single-species model
+    single = None
+    if rank == 0 and world == 1 and not args.no_single:
+        from synth import initial_state_single
+        Ps = workload_params(precond_elas=PRECONDS[args.precond], model=1)
+        sim_s = Simulation(n, Ps, initial_state_single(n, seed=0), precision=args.precision,
+                           device=dev)
+        ag_s = time_steps(sim_s)
+        single = {"model": "single species (Eq. e:rd)", "precision": args.precision,
+                  "value": ag_s["value"], "unit": UNIT, "ms_per_step": ag_s["ms"] / args.steps,
+                  "solver": {"it_elas_per_step": ag_s["it_elas"],
+                             "it_diff_per_step": ag_s["it_diff"]},
+                  "gpu_launches": ag_s["launches"]}
+        sim_s.close()
+        torch.cuda.empty_cache()
+
     batch = None
     if rank == 0 and world == 1 and not args.no_batch:
         batch = run_batch(args, dev)
@@ -434,6 +452,7 @@ def main():
             "roofline": roof,
             "compare": other,
             "adjoint": adjoint,
+            "single_species": single,
             "batch": batch,
             "mixed_over_fp64": (None if other is None else
                                 (value / other["value"] if args.precision == "mixed"

@@ -88,10 +88,22 @@ typedef struct {
   int32_t precond_elas;            /* elasticity preconditioner: TG_PRECOND_JACOBI or
                                       TG_PRECOND_SPECTRAL (Section 3: constant coefficients
                                       averaged over the domain, inverted by FFT)             */
+  int32_t model;                   /* TG_MODEL_MULTISPECIES (Eq. e:gog) or TG_MODEL_SINGLE   */
 } tg_params;
 
 #define TG_PRECOND_JACOBI 0
 #define TG_PRECOND_SPECTRAL 1
+
+/* TG_MODEL_SINGLE: the single-species model of Eq. e:rd with its split from Section 3 --
+ * semi-Lagrangian transport of (c, g, w) and f, Crank-Nicolson diffusion of c whose increment
+ * leaves g and w in proportion g/(g+w), one Heun step of the logistic reaction
+ * R = rho c (1 - c) (Eq. e:reac_op) with g and w losing R in the same proportion, then the
+ * elasticity solve with b = zeta tanh(c) grad c (Eq. e:force) and Lame coefficients with c as
+ * the tumor species.  The tumor density c is carried in tg_state.p; i and n must be zero
+ * (they are transported but nothing creates them); o and l are left untouched.  Contexts
+ * with TG_INIT_ADJOINT, tapes and batches support the multispecies model only. */
+#define TG_MODEL_MULTISPECIES 0
+#define TG_MODEL_SINGLE 1
 
 /* Device pointers to the caller's state (species and materials of Section 2.3; u is the
  * displacement of Eq. e:screening, v = u_t its velocity).  bg is read only. */

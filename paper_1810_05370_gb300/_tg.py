@@ -18,6 +18,7 @@ TG_FP64, TG_MIXED = 0, 1
 TG_INIT_KEEP_UV = 1
 TG_INIT_ADJOINT = 2
 TG_PRECOND_JACOBI, TG_PRECOND_SPECTRAL = 0, 1
+TG_MODEL_MULTISPECIES, TG_MODEL_SINGLE = 0, 1
 THETA = ("k_scale", "rho", "o_hyp", "o_inv", "E_scale")
 
 STATUS_NAMES = {
@@ -43,7 +44,8 @@ class tg_params(C.Structure):
         ("E_scale", C.c_double), ("zeta", C.c_double),
         ("delta_e", C.c_double), ("delta_half", C.c_double), ("delta_l", C.c_double),
         ("rtol_diff", C.c_double), ("rtol_elas", C.c_double),
-        ("maxit_diff", C.c_int32), ("maxit_elas", C.c_int32), ("precond_elas", C.c_int32)]
+        ("maxit_diff", C.c_int32), ("maxit_elas", C.c_int32), ("precond_elas", C.c_int32),
+        ("model", C.c_int32)]
 
 
 class tg_state(C.Structure):
@@ -150,6 +152,7 @@ def make_params(d: dict) -> tg_params:
     p.maxit_diff = int(d["maxit_diff"])
     p.maxit_elas = int(d["maxit_elas"])
     p.precond_elas = int(d.get("precond_elas", TG_PRECOND_JACOBI))
+    p.model = int(d.get("model", TG_MODEL_MULTISPECIES))
     return p
 
 

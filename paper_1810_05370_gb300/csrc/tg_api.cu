@@ -259,6 +259,7 @@ int sm_count() {
 
 bool params_ok(const tg_params* p) {
   if (!p) return false;
+  if (p->model != TG_MODEL_MULTISPECIES && p->model != TG_MODEL_SINGLE) return false;
   if (p->precond_elas != TG_PRECOND_JACOBI && p->precond_elas != TG_PRECOND_SPECTRAL) return false;
   if (!(p->eps_H > 0.0)) return false;
   if (!(p->o_inv > 0.5 * (p->o_hyp + p->o_inv)) && !(p->o_inv < 0.5 * (p->o_hyp + p->o_inv)))
@@ -410,9 +411,13 @@ bool ensure_events(tg_ctx* X, int pairs) {
   return true;
 }
 
+// the single-species model (Eq. e:rd): c is carried in p, only it diffuses
+bool single_species(const tg_ctx* X) { return X->prm.model == TG_MODEL_SINGLE; }
+
 Cn3 cn_view(tg_ctx* X) {
   Cn3 C;
-  double* xs[3] = {X->st.i, X->st.o, X->st.l};
+  // the diffusing fields: i, o, l (multispecies) or c in the first slot (single species)
+  double* xs[3] = {single_species(X) ? X->st.p : X->st.i, X->st.o, X->st.l};
   for (int r = 0; r < 3; ++r) {
     C.x[r] = xs[r];
     C.r[r] = X->a[A_CR0 + r];
@@ -826,10 +831,14 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
     const double* sl[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
     for (int q = 0; q < 6; ++q) REC(T_PD + q, sl[q]);
   }
-  // S2: Crank-Nicolson diffusion of i, o, l (i after transport kept for the g, w fix-up)
-  CK(cudaMemcpyAsync(X->a[A_IDAG], S.i, bytes, cudaMemcpyDeviceToDevice, s));
+  // S2: Crank-Nicolson diffusion of i, o, l (i after transport kept for the g, w fix-up);
+  // single species: of c alone
+  const bool single = single_species(X);
+  CK(cudaMemcpyAsync(X->a[A_IDAG], single ? S.p : S.i, bytes, cudaMemcpyDeviceToDevice, s));
   tg_status e = TG_OK;
-  if (X->prec == TG_MIXED) {
+  if (single) {
+    e = X->prec == TG_MIXED ? cn_solve3_mixed(X, stats, 1) : cn_solve3(X, stats, 1);
+  } else if (X->prec == TG_MIXED) {
     e = cn_solve3(X, stats, 7 & ~CN_MIXED_MASK);
     if (e == TG_OK) e = cn_solve3_mixed(X, stats, CN_MIXED_MASK);
   } else {
@@ -841,7 +850,7 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   REC(T_LD, S.l);
   // S2 fix-up and S3-S5 reactions
   CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l,
-                  X->prec == TG_MIXED, s));
+                  X->prec == TG_MIXED, single_species(X), s));
   X->launches += 1;
   // S6-S7: elasticity from the post-reaction state, then v = du / dt
   e = build_elas_coef(X, true);
@@ -942,7 +951,7 @@ tg_status do_adjoint_step(tg_ctx* X, double dt, const void* tape, const tg_state
   CK(launch_diff_coef(G, X->dp, dt, T.g, T.w, T.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
                       X->a[A_RHO], s));
   CK(launch_react(G, X->dp, dt, X->a[A_RHO], T.idag, qp[0], qp[1], qp[2], qp[3], qp[4], qp[5],
-                  qp[6], X->prec == TG_MIXED, s));
+                  qp[6], X->prec == TG_MIXED, false, s));
   // S6^T: coefficients at q+, adjoint solve, sensitivities
   CK(launch_lame(G, X->dp, qp[0], qp[1], qp[2], qp[3], qp[4], T.fplus, X->st.bg, X->a[A_MU],
                  X->a[A_LAM], X->a[A_ETA], s));
@@ -1061,6 +1070,8 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
   if (out) *out = nullptr;
   if (!out || !grid_ok(grid) || !params_ok(params) || !state) return TG_ERR_ARG;
   if (prec != TG_FP64 && prec != TG_MIXED) return TG_ERR_ARG;
+  // the adjoint differentiates the multispecies step only
+  if ((flags & TG_INIT_ADJOINT) && params->model != TG_MODEL_MULTISPECIES) return TG_ERR_ARG;
   const double* must[] = {state->p, state->i, state->n, state->g, state->w, state->f, state->o,
                           state->l, state->bg, state->u[0], state->u[1], state->u[2],
                           state->v[0], state->v[1], state->v[2]};
@@ -1131,6 +1142,7 @@ tg_status tg_step(tg_ctx* X, double dt, int32_t nsteps, void* tape, tg_stats* st
   if (X->broken) return TG_ERR_STATE;
   if (!(dt > 0.0) || !isfinite(dt) || nsteps < 0) return TG_ERR_ARG;
   if (tape && (nsteps != 1 || ((uintptr_t)tape % ALIGN) != 0)) return TG_ERR_ARG;
+  if (tape && single_species(X)) return TG_ERR_ARG;
   if (stats) memset(stats, 0, sizeof(*stats));
   reset_profile(X);
   CK(cudaSetDevice(X->device));
@@ -1212,6 +1224,7 @@ tg_status tg_set_params(tg_ctx* X, const tg_params* params) {
   if (!X || !params_ok(params)) return TG_ERR_ARG;
   if (X->broken) return TG_ERR_STATE;
   if (params->precond_elas == TG_PRECOND_SPECTRAL && !X->L.spectral) return TG_ERR_WORKSPACE;
+  if (X->has_adjoint && params->model != TG_MODEL_MULTISPECIES) return TG_ERR_ARG;
   X->prm = *params;
   X->dp = make_dev_params(params);
   return TG_OK;
@@ -1421,7 +1434,7 @@ tg_status queue_post_diffusion(tg_ctx* X, double dt) {
   cudaStream_t s = X->stream;
   const size_t bytes = (size_t)G.nvox * sizeof(double);
   CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l,
-                  X->prec == TG_MIXED, s));
+                  X->prec == TG_MIXED, single_species(X), s));
   tg_status e = build_elas_coef(X, true);
   if (e != TG_OK) return e;
   double* const u[3] = {S.u[0], S.u[1], S.u[2]};
@@ -1691,6 +1704,8 @@ tg_status tg_batch_init(int32_t nsims, const tg_grid* grids, const tg_params* pa
                         size_t workspace_bytes, void* cuda_stream, tg_batch** out) {
   if (out) *out = nullptr;
   if (!out || nsims <= 0 || !grids || !params || !states || prec != TG_MIXED) return TG_ERR_ARG;
+  for (int s = 0; s < nsims; ++s)   // the persistent solvers step the multispecies model
+    if (params[s].model != TG_MODEL_MULTISPECIES) return TG_ERR_ARG;
   const size_t need = tg_batch_workspace_bytes(nsims, grids, prec);
   if (need == 0) return TG_ERR_ARG;
   if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < need)

@@ -362,10 +362,12 @@ cudaError_t launch_divergence(const Geo&, const double* const v[3], double* div,
 cudaError_t launch_sl_advect(const Geo&, double dt, const double* const v[3], const double* div,
                              const double* const qin[6], double* const qout[6], cudaStream_t st);
 
-// S2 fix-up + S3-S5 (fp32_rates: the mixed precision's FP32 rate arithmetic)
+// S2 fix-up + S3-S5 (fp32_rates: the mixed precision's FP32 rate arithmetic; single: the
+// single-species model, c in p)
 cudaError_t launch_react(const Geo&, const DevParams&, double dt, const double* rho,
                          const double* i_dag, double* p, double* i, double* n, double* g,
-                         double* w, double* o, double* l, bool fp32_rates, cudaStream_t st);
+                         double* w, double* o, double* l, bool fp32_rates, bool single,
+                         cudaStream_t st);
 
 // S6 coefficients
 cudaError_t launch_lame(const Geo&, const DevParams&, const double* p, const double* i,

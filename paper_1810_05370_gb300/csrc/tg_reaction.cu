@@ -46,8 +46,26 @@ __device__ __forceinline__ void species_rates(const DevParams& P, T rho, T o, T 
   dy[4] = -fw * (R + Rt) - h * w;
 }
 
+// Single-species model (Eq. e:rd, Eq. e:reac_op): d_t c = rho c (1 - c), and g, w lose
+// what c gains in proportion g : w; c is carried in y[0].
 template <typename T>
-__global__ void __launch_bounds__(NT) k_react(Geo G, DevParams P, double dt,
+__device__ __forceinline__ void single_rates(T rho, const T y[5], T dy[5]) {
+  const T c = y[0], g = y[3], w = y[4];
+  const T R = rho * c * ((T)1 - c);
+  const T gw = g + w;
+  const T fg = gw > (T)0 ? g / gw : (T)0;
+  const T fw = gw > (T)0 ? w / gw : (T)0;
+  dy[0] = R;
+  dy[1] = (T)0;
+  dy[2] = (T)0;
+  dy[3] = -fg * R;
+  dy[4] = -fw * R;
+}
+
+// single: the single-species model -- the CN increment of c (in p) leaves g and w, the
+// reaction is the logistic one above, and oxygen and edema are not touched
+template <typename T>
+__global__ void __launch_bounds__(NT) k_react(Geo G, DevParams P, double dt, int single,
                                               const double* __restrict__ rho,
                                               const double* __restrict__ i_dag, double* p,
                                               double* ii, double* n, double* g, double* w,
@@ -61,7 +79,7 @@ __global__ void __launch_bounds__(NT) k_react(Geo G, DevParams P, double dt,
     // S2 fix-up: the Crank-Nicolson increment of i comes out of g and w, in proportion
     double y[5] = {p[c], ii[c], n[c], g[c], w[c]};
     {
-      const double di = y[1] - i_dag[c];
+      const double di = y[single ? 0 : 1] - i_dag[c];
       const double gw = y[3] + y[4];
       const double fg = gw > 0.0 ? y[3] / gw : 0.0;
       const double fw = gw > 0.0 ? y[4] / gw : 0.0;
@@ -77,10 +95,16 @@ __global__ void __launch_bounds__(NT) k_react(Geo G, DevParams P, double dt,
     T yt[5], k1v[5], k2v[5], ys[5];
 #pragma unroll
     for (int s = 0; s < 5; ++s) yt[s] = (T)y[s];
-    species_rates<T>(P, r, ot, h, alpha, mf, yt, k1v);
+    if (single)
+      single_rates<T>(r, yt, k1v);
+    else
+      species_rates<T>(P, r, ot, h, alpha, mf, yt, k1v);
 #pragma unroll
     for (int s = 0; s < 5; ++s) ys[s] = yt[s] + dtt * k1v[s];
-    species_rates<T>(P, r, ot, h, alpha, mf, ys, k2v);
+    if (single)
+      single_rates<T>(r, ys, k2v);
+    else
+      species_rates<T>(P, r, ot, h, alpha, mf, ys, k2v);
 #pragma unroll
     for (int s = 0; s < 5; ++s) y[s] = y[s] + 0.5 * dt * (double)(k1v[s] + k2v[s]);
     p[c] = y[0];
@@ -88,6 +112,7 @@ __global__ void __launch_bounds__(NT) k_react(Geo G, DevParams P, double dt,
     n[c] = y[2];
     g[c] = y[3];
     w[c] = y[4];
+    if (single) continue;
     // S4: oxygen, d_t o = -delta_p p + delta_s (o_heal - o)(g + w)   (Eq. e:ox)
     const double gwn = y[3] + y[4];
     const double ko1 = -P.delta_p * y[0] + P.delta_s * (P.o_heal - oo) * gwn;
@@ -137,11 +162,15 @@ __global__ void __launch_bounds__(NT) k_lame(Geo G, DevParams P, const double* _
 
 cudaError_t launch_react(const Geo& G, const DevParams& P, double dt, const double* rho,
                          const double* i_dag, double* p, double* i, double* n, double* g,
-                         double* w, double* o, double* l, bool fp32_rates, cudaStream_t st) {
+                         double* w, double* o, double* l, bool fp32_rates, bool single,
+                         cudaStream_t st) {
+  const int sg = single ? 1 : 0;
   if (fp32_rates)
-    k_react<float><<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, rho, i_dag, p, i, n, g, w, o, l);
+    k_react<float><<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, sg, rho, i_dag, p, i, n, g, w, o,
+                                                     l);
   else
-    k_react<double><<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, rho, i_dag, p, i, n, g, w, o, l);
+    k_react<double><<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, sg, rho, i_dag, p, i, n, g, w, o,
+                                                      l);
   return cudaGetLastError();
 }
 

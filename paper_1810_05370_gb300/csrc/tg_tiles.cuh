@@ -228,7 +228,12 @@ __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32
   float part = 0.0f;
   const int ci = (ty + 1) * HX + (tx + 1);
   int s0 = 0, s1 = 1, s2 = 2, s3 = 3;    // slots of planes k-1, k, k+1 and the free one
+  // eta of the thread's own node, loaded one plane ahead
+  const long long col = (long long)j * G.nx + i;
+  float eta_next = (on && k0 < k1) ? __ldg(I.eta + (long long)k0 * G.nxy + col) : 0.0f;
   for (int k = k0; k < k1; ++k) {
+    const float eta_k = eta_next;
+    if (on && k + 1 < k1) eta_next = __ldg(I.eta + (long long)(k + 1) * G.nxy + col);
     Cell t;
     const int sl[3] = {s0, s1, s2};
 #pragma unroll
@@ -246,9 +251,9 @@ __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32
     }
     __syncthreads();                    // plane k+1 (written last iteration) is visible
     if (on) {
-      const long long c = (long long)k * G.nxy + (long long)j * G.nx + i;
+      const long long c = (long long)k * G.nxy + col;
       Fac32 f;
-      tile_fac(T, t, K.ih2, __ldg(I.eta + c), f);
+      tile_fac(T, t, K.ih2, eta_k, f);
       const float q0 = row_tile<0>(T, t, f, K.sc);
       const float q1 = row_tile<1>(T, t, f, K.sc);
       const float q2 = row_tile<2>(T, t, f, K.sc);

@@ -37,8 +37,8 @@ def test_every_declared_symbol_is_exported(tg):
 
 
 def test_struct_sizes_match_header_layout(tg):
-    # tg_params: 17 + 15 + 2 + 3 + 2 doubles, then three int32 (maxit x2, precond_elas)
-    assert C.sizeof(tg.tg_params) == (17 + 15 + 2 + 3 + 2) * 8 + 3 * 4 + 4   # 3 int32 + padding
+    # tg_params: 17 + 15 + 2 + 3 + 2 doubles, then four int32 (maxit x2, precond_elas, model)
+    assert C.sizeof(tg.tg_params) == (17 + 15 + 2 + 3 + 2) * 8 + 4 * 4
     assert C.sizeof(tg.tg_grid) == 3 * 4 + 4 + 3 * 8
     assert C.sizeof(tg.tg_state) == 15 * 8
 
