@@ -280,6 +280,21 @@ class Oracle:
         r = self.lib.or_heaviside(C.byref(self.params(params)), arg)
         return complex(r.re, r.im) if self.cs else float(r)
 
+    def diagnostics(self, n, mu, lam, u3, L=None):
+        """(trace T, in-plane max shear, det(I + grad u)) per node."""
+        u3 = np.ascontiguousarray(u3, dtype=self.dtype)
+        tr, tau, jac = (self._new(mu) for _ in range(3))
+        self.lib.or_diagnostics(C.byref(self.grid(n, L)), self._ptr(mu), self._ptr(lam),
+                                self._ptr(u3), self._ptr(tr), self._ptr(tau), self._ptr(jac))
+        return tr, tau, jac
+
+    def displacement_extent(self, n, u3, seed, thr, L=None):
+        u3 = np.ascontiguousarray(u3, dtype=self.dtype)
+        self.lib.or_displacement_extent.restype = C.c_double
+        sd = (C.c_double * 3)(*[float(v) for v in seed])
+        return float(self.lib.or_displacement_extent(C.byref(self.grid(n, L)), self._ptr(u3), sd,
+                                                     C.c_double(thr)))
+
     def react_single(self, n, dt, rho, st, L=None):
         """Single-species reaction, in place on st['p'] (c), st['g'], st['w']."""
         self.lib.or_react_single(C.byref(self.grid(n, L)), C.c_double(dt), self._ptr(rho),

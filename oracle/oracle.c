@@ -723,6 +723,59 @@ void or_react_single(const or_grid* G, double dt, const real_t* rho, real_t* c, 
   }
 }
 
+/* ---------------------------------------------------------------- diagnostics */
+
+void or_diagnostics(const or_grid* G, const real_t* mu, const real_t* lam, const real_t* u3,
+                    real_t* trace, real_t* tau, real_t* jac) {
+  int64_t m = nvox(G);
+  const real_t* u[3] = {u3, u3 + m, u3 + 2 * m};
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < m; ++e) {
+    int64_t c[3];
+    coords(G, e, c);
+    real_t D[3][3];                       /* D[a][d] = d u_a / d x_d, centred */
+    for (int a = 0; a < 3; ++a)
+      for (int d = 0; d < 3; ++d)
+        D[a][d] = (u[a][at(G, c, d, +1, -1, 0)] - u[a][at(G, c, d, -1, -1, 0)]) / (2.0 * hd(G, d));
+    real_t E[3][3], T[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) E[a][b] = 0.5 * (D[a][b] + D[b][a]);
+    real_t trE = E[0][0] + E[1][1] + E[2][2];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) T[a][b] = (a == b ? lam[e] * trE : 0.0) + 2.0 * mu[e] * E[a][b];
+    trace[e] = T[0][0] + T[1][1] + T[2][2];
+    real_t hx = 0.5 * (T[0][0] - T[1][1]);
+    tau[e] = SQRT_RE(hx * hx + T[0][1] * T[0][1]);
+    real_t F[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) F[a][b] = (a == b ? 1.0 : 0.0) + D[a][b];
+    jac[e] = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1])
+           - F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0])
+           + F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+  }
+}
+
+double or_displacement_extent(const or_grid* G, const real_t* u3, const double seed[3],
+                              double thr) {
+  int64_t m = nvox(G);
+  double best = 0.0;
+  for (int64_t e = 0; e < m; ++e) {
+    double uu = 0.0;
+    for (int a = 0; a < 3; ++a) uu += RE(u3[a * m + e]) * RE(u3[a * m + e]);
+    if (sqrt(uu) < thr) continue;
+    int64_t c[3];
+    coords(G, e, c);
+    double r2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double x = c[d] * hd(G, d) - seed[d];
+      x -= G->L[d] * floor(x / G->L[d] + 0.5);   /* nearest periodic image */
+      r2 += x * x;
+    }
+    if (sqrt(r2) > best) best = sqrt(r2);
+  }
+  return best;
+}
+
 /* ---------------------------------------------------------------- step */
 
 static real_t* alloc_field(int64_t m) { return (real_t*)calloc((size_t)m, sizeof(real_t)); }

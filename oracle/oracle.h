@@ -93,4 +93,12 @@ void or_react(const or_grid*, const or_params*, double dt, const real_t* rho, re
               real_t* i, real_t* n, real_t* g, real_t* w, real_t* o, real_t* l);
 void or_react_single(const or_grid*, double dt, const real_t* rho, real_t* c, real_t* g,
                      real_t* w);
+/* Mass-effect diagnostics (Section 3): trace of the stress T = lambda tr(E) I + 2 mu E
+ * (Eq. e:hook), the in-plane maximum shear stress of Eq. e:princ_stress and
+ * J = det(I + grad u) (Eq. e:jacobian), with centred differences for grad u. */
+void or_diagnostics(const or_grid*, const real_t* mu, const real_t* lam, const real_t* u3,
+                    real_t* trace, real_t* tau, real_t* jac);
+/* largest periodic distance from the point seed of a node with |u| >= thr (0 if none) */
+double or_displacement_extent(const or_grid*, const real_t* u3, const double seed[3],
+                              double thr);
 #endif

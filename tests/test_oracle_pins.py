@@ -772,3 +772,65 @@ def test_single_species_diffusion_spreads_the_tumor(oracle):
     oracle.step(n, P, 0.05, st)
     assert abs(st["p"].sum() - c0.sum()) <= 1e-9 * c0.sum()
     assert st["p"].max() < c0.max()
+
+
+# ----------------------------------------------------------------- mass-effect diagnostics
+
+def _centred_factor(h):
+    """d/dx sin(x) by centred differences on spacing h: cos(x) sin(h) / h (exact)."""
+    return np.sin(h) / h
+
+
+def test_diagnostics_uniaxial_and_shear_closed_forms(oracle):
+    """Eq. e:hook, e:princ_stress, e:jacobian on fields whose centred gradient is known in
+    closed form: uniaxial u = (eps sin x, 0, 0) gives J = 1 + g, tr T = (3 lambda + 2 mu) g and
+    tau = mu |g|; simple shear u = (eps sin y, 0, 0) gives J = 1, tr T = 0, tau = mu |s|."""
+    n = (16, 12, 10)
+    L = (TWO_PI, TWO_PI, TWO_PI)
+    X, Y, Z = mesh(n, L)
+    h = spacing(n, L)
+    mu0, lam0, eps = 1.7, 5.0, 0.01
+    mu, lam = mu0 * np.ones(X.shape), lam0 * np.ones(X.shape)
+    zero = np.zeros(X.shape)
+    tr, tau, jac = oracle.diagnostics(n, mu, lam, np.stack([eps * np.sin(X), zero, zero]), L)
+    g = eps * np.cos(X) * _centred_factor(h[0])
+    assert np.allclose(jac, 1 + g, atol=1e-14)
+    assert np.allclose(tr, (3 * lam0 + 2 * mu0) * g, atol=1e-13)
+    assert np.allclose(tau, mu0 * np.abs(g), atol=1e-13)
+    tr, tau, jac = oracle.diagnostics(n, mu, lam, np.stack([eps * np.sin(Y), zero, zero]), L)
+    s = eps * np.cos(Y) * _centred_factor(h[1])
+    assert np.allclose(jac, 1.0, atol=1e-15)
+    assert np.allclose(tr, 0.0, atol=1e-14)
+    assert np.allclose(tau, mu0 * np.abs(s), atol=1e-13)
+
+
+def test_diagnostics_jacobian_cross_terms(oracle):
+    """u = (a sin y, b sin x, c sin z): F = [[1, a', 0], [b', 1, 0], [0, 0, 1 + c']] so
+    det F = (1 + c')(1 - a' b') -- a dropped cofactor or a wrong sign fails it."""
+    n = (12, 14, 10)
+    L = (TWO_PI, 3.0, 5.0)
+    X, Y, Z = mesh(n, L)
+    h = spacing(n, L)
+    a, b, c = 0.2, -0.3, 0.1
+    ky, kx, kz = TWO_PI / L[1], TWO_PI / L[0], TWO_PI / L[2]
+    u3 = np.stack([a * np.sin(ky * Y), b * np.sin(kx * X), c * np.sin(kz * Z)])
+    ones = np.ones(X.shape)
+    _, _, jac = oracle.diagnostics(n, ones, ones, u3, L)
+    ap = a * ky * np.cos(ky * Y) * np.sin(ky * h[1]) / (ky * h[1])
+    bp = b * kx * np.cos(kx * X) * np.sin(kx * h[0]) / (kx * h[0])
+    cp = c * kz * np.cos(kz * Z) * np.sin(kz * h[2]) / (kz * h[2])
+    assert np.allclose(jac, (1 + cp) * (1 - ap * bp), atol=1e-13)
+
+
+def test_displacement_extent_brute_force(oracle):
+    """d_max: the largest periodic distance from the seed of a node with |u| >= threshold."""
+    n = (16, 16, 16)
+    X, Y, Z = mesh(n)
+    seed = np.array([0.3, 6.0, 3.1])
+    d = [np.abs(Q - s) for Q, s in zip((X, Y, Z), seed)]
+    d = [np.minimum(q, TWO_PI - q) for q in d]
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    u = np.stack([np.where(r < 1.3, 0.5, 0.01), np.zeros(X.shape), np.zeros(X.shape)])
+    got = oracle.displacement_extent(n, u, seed, 0.1)
+    assert abs(got - r[r < 1.3].max()) < 1e-12
+    assert oracle.displacement_extent(n, u, seed, 1.0) == 0.0
