@@ -179,6 +179,24 @@ tg_status tg_adjoint_init(tg_ctx* ctx, double* const lam_u[3], double grad[5]);
  * holds three device arrays.  u holds three device arrays, overwritten with the solution. */
 tg_status tg_solve_elasticity(tg_ctx* ctx, double* const rhs[3], double* u[3], tg_stats* stats);
 
+/* Mass-effect diagnostics of the current state (Section 3): per node, the trace of the stress
+ * T = lambda tr(E) I + 2 mu E (Eq. e:hook, Lame coefficients of Eq. e:lame from the state),
+ * the in-plane maximum shear stress sqrt(((T_xx - T_yy)/2)^2 + T_xy^2) (Eq. e:princ_stress)
+ * and J = det(I + grad u) (Eq. e:jacobian), grad u by centred differences; and summaries.
+ * fields: NULL, or three device arrays (any of them NULL) receiving tr T, the shear and J.
+ * seed (host, physical coordinates in the box) and u_threshold define d_max.  out (host,
+ * required) receives the summaries. */
+typedef struct {
+  double jac_min, jac_max;   /* extremes of J                                               */
+  double jac_dev_l2;         /* (h_x h_y h_z sum (J - 1)^2)^(1/2)                             */
+  double trace_min, trace_max;
+  double shear_max;          /* largest in-plane maximum shear stress                       */
+  double d_max;              /* largest periodic distance from seed of a node with
+                                |u| >= u_threshold (0 if there is none)                     */
+} tg_diag;
+tg_status tg_diagnostics(tg_ctx* ctx, const double seed[3], double u_threshold,
+                         double* const fields[3], tg_diag* out);
+
 /* Replace the parameters used by later calls (e.g. a parameter sweep on one context).
  * Switching to TG_PRECOND_SPECTRAL needs a context whose workspace was sized for it
  * (TG_ERR_WORKSPACE otherwise). */

@@ -73,6 +73,11 @@ class tg_batch_tune(C.Structure):
                 ("zc", C.c_int32 * 32), ("blocks", C.c_int32 * 32), ("ms", C.c_float * 32)]
 
 
+class tg_diag(C.Structure):
+    _fields_ = [(name, C.c_double) for name in ("jac_min", "jac_max", "jac_dev_l2", "trace_min",
+                                                "trace_max", "shear_max", "d_max")]
+
+
 class TGError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -94,6 +99,8 @@ def _load():
         "tg_solve_elasticity": (C.c_int, [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(tg_stats)]),
         "tg_set_params": (C.c_int, [C.c_void_p, P(tg_params)]),
         "tg_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+        "tg_diagnostics": (C.c_int, [C.c_void_p, P(C.c_double), C.c_double, P(C.c_void_p),
+                                     P(tg_diag)]),
         "tg_workspace_bytes_adjoint": (C.c_size_t, [P(tg_grid), P(tg_params), C.c_int]),
         "tg_tape_bytes": (C.c_size_t, [P(tg_grid)]),
         "tg_adjoint_step": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, P(tg_state),
@@ -181,6 +188,17 @@ def tg_init(grid, params, prec, state, workspace_ptr, workspace_bytes, stream_pt
     if rc != TG_OK:
         raise TGError(rc, "tg_init")
     return ctx, stats_dict(stats)
+
+
+def tg_diagnostics(ctx, seed, u_threshold, field_ptrs=None) -> dict:
+    """field_ptrs: None or three device pointers (None entries allowed)."""
+    sd = (C.c_double * 3)(*[float(v) for v in seed])
+    fp = None if field_ptrs is None else (C.c_void_p * 3)(*[p or None for p in field_ptrs])
+    out = tg_diag()
+    rc = lib.tg_diagnostics(ctx, sd, C.c_double(u_threshold), fp, C.byref(out))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_diagnostics")
+    return {f: getattr(out, f) for f, _ in tg_diag._fields_}
 
 
 def tg_workspace_bytes_adjoint(grid: tg_grid, params, prec: int) -> int:

@@ -1230,6 +1230,43 @@ tg_status tg_set_params(tg_ctx* X, const tg_params* params) {
   return TG_OK;
 }
 
+tg_status tg_diagnostics(tg_ctx* X, const double seed[3], double u_threshold,
+                         double* const fields[3], tg_diag* out) {
+  if (!X || !seed || !out || !(u_threshold >= 0.0)) return TG_ERR_ARG;
+  if (X->broken) return TG_ERR_STATE;
+  CK(cudaSetDevice(X->device));
+  const Geo& G = X->G;
+  tg_state& S = X->st;
+  CK(launch_lame(G, X->dp, S.p, S.i, S.n, S.g, S.w, S.f, S.bg, X->a[A_MU], X->a[A_LAM],
+                 X->a[A_ETA], X->stream));
+  DiagArgs A;
+  for (int d = 0; d < 3; ++d) {
+    A.u[d] = S.u[d];
+    A.out[d] = fields ? fields[d] : nullptr;
+    A.seed[d] = seed[d];
+    A.L[d] = G.h[d] * (d == 0 ? G.nx : (d == 1 ? G.ny : G.nz));
+  }
+  A.mu = X->a[A_MU];
+  A.lam = X->a[A_LAM];
+  A.threshold = u_threshold;
+  A.partial = X->partial;
+  A.counter = X->counter;
+  A.result = X->grad + 8;   // 7 spare doubles of the reduction area, after the gradient's 5
+  CK(launch_diagnostics(G, A, X->stream));
+  X->launches += 2;
+  double r[7];
+  CK(cudaMemcpyAsync(r, A.result, sizeof(r), cudaMemcpyDeviceToHost, X->stream));
+  CK(cudaStreamSynchronize(X->stream));
+  out->jac_min = r[0];
+  out->jac_max = r[1];
+  out->jac_dev_l2 = r[2];
+  out->trace_min = r[3];
+  out->trace_max = r[4];
+  out->shear_max = r[5];
+  out->d_max = r[6];
+  return TG_OK;
+}
+
 tg_status tg_set_timing(tg_ctx* X, int32_t enable) {
   if (!X) return TG_ERR_ARG;
   X->timing = enable != 0;

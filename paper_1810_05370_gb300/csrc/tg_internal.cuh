@@ -275,6 +275,21 @@ struct Sl32 {      // FP32 transport: inputs as FP32 copies, outputs to the FP64
   double* out[6];
 };
 
+// ---------------------------------------------------------------- diagnostics (Section 3)
+struct DiagArgs {
+  const double* u[3];
+  const double* mu;
+  const double* lam;
+  double* out[3];          // tr T, max shear, det(I + grad u); entries may be null
+  double seed[3];          // tumor seed (physical coordinates)
+  double L[3];             // box lengths (periodic distances)
+  double threshold;        // |u| reaching it counts for d_max
+  double* partial;         // 7 per block
+  unsigned int* counter;
+  double* result;          // 7 doubles (device)
+};
+cudaError_t launch_diagnostics(const Geo&, const DiagArgs&, cudaStream_t st);
+
 // ---------------------------------------------------------------- spectral preconditioner
 // Section 3: the elasticity solve is preconditioned by the exact inverse of the operator with
 // constant coefficients (the domain means of mu, lambda, eta).  For the finite-difference

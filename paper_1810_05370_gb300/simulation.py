@@ -102,6 +102,21 @@ class Simulation:
     def set_timing(self, enable: bool = True):
         _tg.tg_set_timing(self.ctx, enable)
 
+    def diagnostics(self, seed, u_threshold: float = 0.0, fields: bool = False) -> dict:
+        """Mass-effect diagnostics of the current state (tg_diagnostics): summaries, plus the
+        per-node tr T, max shear and det(I + grad u) tensors when fields is True."""
+        import torch
+        out = None
+        if fields:
+            out = [torch.empty(self.shape, dtype=torch.float64, device=self.device)
+                   for _ in range(3)]
+        with torch.cuda.device(self.device):
+            d = _tg.tg_diagnostics(self.ctx, seed, u_threshold,
+                                   None if out is None else [t.data_ptr() for t in out])
+        if out is not None:
+            d["trace"], d["shear"], d["jacobian"] = out
+        return d
+
     def set_params(self, params: dict):
         self.params = dict(params)
         self._cparams = _tg.make_params(self.params)
