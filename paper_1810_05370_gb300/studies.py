@@ -110,3 +110,34 @@ def sensitivity_adjoint(n, params: dict, state0: dict, steps: int, dt: float,
     ro.close()
     th = theta_of(params)
     return {name: float(th[k] * g[k] / norm) for k, name in enumerate(THETA)}
+
+
+def main(argv=None):
+    """python -m paper_1810_05370_gb300.studies [--n N] [--steps K]: runs both studies on the
+    synthetic brain and prints one JSON object per study."""
+    import argparse
+    import json
+
+    from synth import initial_state, workload_params
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--dt", type=float, default=0.01)
+    ap.add_argument("--what", choices=("grid", "sensitivity", "all"), default="all")
+    args = ap.parse_args(argv)
+    P = workload_params(precond_elas=1)
+    st0 = initial_state(args.n, 0)
+    if args.what in ("grid", "all"):
+        rows = mass_effect_grid(args.n, P, st0, [1e3, 3e3, 1e4, 3e4, 1e5],
+                                [3.5e3, 7e3, 1.4e4, 2.8e4, 5.6e4], args.steps, args.dt)
+        print(json.dumps({"study": "mass_effect_grid", "n": args.n, "steps": args.steps,
+                          "rows": rows}), flush=True)
+    if args.what in ("sensitivity", "all"):
+        fd = sensitivity_fd(args.n, P, st0, args.steps, args.dt, eps=0.05, precision="mixed")
+        adj = sensitivity_adjoint(args.n, workload_params(), st0, args.steps, args.dt)
+        print(json.dumps({"study": "sensitivity", "n": args.n, "steps": args.steps,
+                          "one_factor_eps_0.05": fd, "adjoint_limit_p": adj}), flush=True)
+
+
+if __name__ == "__main__":
+    main()
