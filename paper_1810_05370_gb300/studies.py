@@ -10,6 +10,8 @@ sensitivity_fd        one-factor-at-a-time sensitivities g = (|q| - |q*|) / (eps
 sensitivity_adjoint   the eps -> 0 limit of the same quantity for q = p and the parameters
                       the adjoint differentiates, theta d|p|/dtheta / |p|, from one adjoint
                       pass (tg_adjoint_step) instead of one forward run per parameter.
+mesh_convergence      the mesh-convergence study: relative L2 errors of p, i, n, g, w on
+                      coarser grids (space and time refined together) against a fine grid.
 
 These are host-side orchestrations of library calls; every step and diagnostic runs in the
 library's kernels.
@@ -112,6 +114,44 @@ def sensitivity_adjoint(n, params: dict, state0: dict, steps: int, dt: float,
     return {name: float(th[k] * g[k] / norm) for k, name in enumerate(THETA)}
 
 
+def mesh_convergence(sizes=(64, 128, 256), ref: int = 512, T: float = 0.16,
+                     dt_coarse: float = 0.02, params: dict = None, precision: str = "mixed",
+                     seed: int = 0):
+    """Section 4's mesh-convergence study: the same continuous synthetic brain (interface and
+    tumor widths fixed by the coarsest grid) run to time T on each grid with dt refined with h
+    (dt = dt_coarse * sizes[0] / N), against the run on the ref^3 grid.  e_q =
+    |q_h - q_ref|_2 / |q_ref|_2 over the coarse nodes (node j of an N grid is node
+    j * ref / N of the reference grid).  Returns {"errors": {N: {q: e_q}}, "rates": ...}."""
+    from synth import initial_state, workload_params
+    P = workload_params(precond_elas=1) if params is None else params
+    hw = 2 * np.pi / sizes[0]
+    fields = ("p", "i", "n", "g", "w")
+
+    def run(N):
+        dt = dt_coarse * sizes[0] / N
+        steps = int(round(T / dt))
+        sim = Simulation(N, P, initial_state(N, seed, h_widths=hw), precision=precision)
+        sim.step(dt, nsteps=steps)
+        out = {q: sim.state[q].cpu().numpy() for q in fields}
+        sim.close()
+        return out
+
+    reference = run(ref)
+    errors = {}
+    for N in sizes:
+        got = run(N)
+        r = ref // N
+        errors[N] = {}
+        for q in fields:
+            rq = reference[q][::r, ::r, ::r]
+            errors[N][q] = float(np.linalg.norm(got[q] - rq) / np.linalg.norm(rq))
+    rates = {}
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        rates[f"{a}->{b}"] = {q: float(np.log2(errors[a][q] / errors[b][q])) for q in fields}
+    return {"T": T, "dt_coarse": dt_coarse, "sizes": list(sizes), "ref": ref,
+            "errors": {str(k): v for k, v in errors.items()}, "rates": rates}
+
+
 def main(argv=None):
     """python -m paper_1810_05370_gb300.studies [--n N] [--steps K]: runs both studies on the
     synthetic brain and prints one JSON object per study."""
@@ -123,7 +163,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--dt", type=float, default=0.01)
-    ap.add_argument("--what", choices=("grid", "sensitivity", "all"), default="all")
+    ap.add_argument("--what", choices=("grid", "sensitivity", "mesh", "all"), default="all")
     args = ap.parse_args(argv)
     P = workload_params(precond_elas=1)
     st0 = initial_state(args.n, 0)
@@ -137,6 +177,8 @@ def main(argv=None):
         adj = sensitivity_adjoint(args.n, workload_params(), st0, args.steps, args.dt)
         print(json.dumps({"study": "sensitivity", "n": args.n, "steps": args.steps,
                           "one_factor_eps_0.05": fd, "adjoint_limit_p": adj}), flush=True)
+    if args.what == "mesh":   # not in "all": the 512^3 reference takes minutes
+        print(json.dumps({"study": "mesh_convergence", **mesh_convergence()}), flush=True)
 
 
 if __name__ == "__main__":

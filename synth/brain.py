@@ -79,11 +79,13 @@ def _smooth_indicator(phi, width):
     return 0.5 * (1.0 - np.tanh(phi / width))
 
 
-def synthetic_brain(n, seed: int = 0):
-    """Material fractions (g, w, f, bg) and the tumor shape G_t for an n^3 (or (nx,ny,nz)) grid."""
+def synthetic_brain(n, seed: int = 0, h_widths=None):
+    """Material fractions (g, w, f, bg) and the tumor shape G_t for an n^3 (or (nx,ny,nz)) grid.
+    The interface and tumor widths scale with the grid spacing, or with h_widths when given
+    (the same continuous brain sampled on every grid, as a mesh-convergence study needs)."""
     nx, ny, nz = _grid_shape(n)
     h = np.array([TWO_PI / nx, TWO_PI / ny, TWO_PI / nz])
-    hmean = float(np.mean(h))
+    hmean = float(np.mean(h)) if h_widths is None else float(h_widths)
     rng = np.random.default_rng(np.random.PCG64(seed))
     x = TWO_PI * np.arange(nx) / nx
     y = TWO_PI * np.arange(ny) / ny
@@ -125,7 +127,7 @@ def synthetic_brain(n, seed: int = 0):
     return {k2: np.ascontiguousarray(v, dtype=np.float64) for k2, v in out.items()}
 
 
-def initial_state(n, seed: int = 0, o_heal: float = 1.0):
+def initial_state(n, seed: int = 0, o_heal: float = 1.0, h_widths=None):
     """The state the first step starts from (u and v are zero; u^0 is computed by the solver).
 
     Tumor amplitude (not fixed by the paper): p0 = 0.8 G_t (g + w), i0 = 0.1 p0 (Section 4
@@ -133,7 +135,7 @@ def initial_state(n, seed: int = 0, o_heal: float = 1.0):
     o0 = o_heal, edema l0 = 0, and the healthy tissue gives up exactly the mass the tumor
     takes: g0 = g (1 - 0.88 G_t), w0 = w (1 - 0.88 G_t).
     """
-    b = synthetic_brain(n, seed)
+    b = synthetic_brain(n, seed, h_widths)
     gt = b["tumor"]
     gw = b["g"] + b["w"]
     p = 0.8 * gt * gw

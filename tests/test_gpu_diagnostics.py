@@ -105,3 +105,13 @@ def test_adjoint_sensitivity_matches_one_factor_differences(torch_cuda):
     for name in ("rho", "o_hyp", "k_scale"):
         central = 0.5 * (plus[name]["p"] + minus[name]["p"])
         assert ga[name] == pytest.approx(central, rel=1e-3, abs=1e-7), (name, ga, central)
+
+
+def test_mesh_convergence_small(torch_cuda):
+    """Section 4's mesh-convergence study at small sizes: errors against the finest grid fall
+    as space and time are refined together (the paper observes about first order)."""
+    from paper_1810_05370_gb300.studies import mesh_convergence
+    r = mesh_convergence(sizes=(16, 32), ref=64, T=0.08, dt_coarse=0.02)
+    for q in ("p", "i", "g", "w"):
+        assert r["errors"]["32"][q] < r["errors"]["16"][q], r
+        assert r["rates"]["16->32"][q] > 0.5, r
