@@ -185,6 +185,167 @@ __device__ C* fft_lines(C* a, C* b, int ln, int llo, int hi, int ls, int es, con
 
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 
+// --------------------------------------------------- stages that read or write global memory
+// The y and z passes keep their lines interleaved both in global memory (consecutive mode
+// columns are contiguous) and in shared memory, so the first stage of a transform can gather
+// its radix-16 inputs straight from global memory into registers (16 loads in flight per
+// thread) and the last stage can scatter its outputs straight back: two shared-memory round
+// trips and a barrier fewer per transform.  Accessors: element e of line l.
+template <typename C> struct SmemIO {
+  C* p;
+  int ls, es;
+  __device__ __forceinline__ C ld(int l, int e) const { return p[l * ls + e * es]; }
+  __device__ __forceinline__ void st(int l, int e, C v) const { p[l * ls + e * es] = v; }
+};
+
+// y pass: line l = mode column kx0 + l of one (component, z) plane; element e = row y
+template <typename C> struct ColIO {
+  C* W;     // &W[comp][z][0][kx0]
+  int nxp, ncol;
+  __device__ __forceinline__ C ld(int l, int e) const {
+    return l < ncol ? W[(size_t)e * nxp + l] : C{0, 0};
+  }
+  __device__ __forceinline__ void st(int l, int e, C v) const {
+    if (l < ncol) W[(size_t)e * nxp + l] = v;
+  }
+};
+
+// z pass: line l = (component l >> ltz, column l & (tz - 1)); element e = plane kz
+template <typename C> struct ZIO {
+  C* W;     // &W[0][0][ky][kx0]
+  size_t plane, comp_stride;
+  int tz, ltz, ncol;
+  __device__ __forceinline__ size_t at(int l, int e) const {
+    return (size_t)(l >> ltz) * comp_stride + (size_t)e * plane + (l & (tz - 1));
+  }
+  __device__ __forceinline__ C ld(int l, int e) const {
+    return (l & (tz - 1)) < ncol ? W[at(l, e)] : C{0, 0};
+  }
+  __device__ __forceinline__ void st(int l, int e, C v) const {
+    if ((l & (tz - 1)) < ncol) W[at(l, e)] = v;
+  }
+};
+
+// fft_stage with accessors for its source and destination (same work mapping)
+template <int LR, int SGN, typename C, class SRC, class DST>
+__device__ __forceinline__ void fft_stage_io(const SRC& src, const DST& dst, int ln, int lNs,
+                                             int llo, int hi, const C* tw) {
+  constexpr int R = 1 << LR;
+  const int lnb = ln - LR, nb = 1 << lnb, Ns = 1 << lNs, lts = ln - lNs - LR;
+  const int lo_mask = (1 << llo) - 1;
+  const int total = hi << (llo + lnb);
+  for (int it = threadIdx.x; it < total; it += blockDim.x) {
+    const int ll = it & lo_mask;
+    const int rest = it >> llo;
+    const int j = rest & (nb - 1);
+    const int l = ((rest >> lnb) << llo) + ll;
+    const int k = j & (Ns - 1);
+    const int d = ((j >> lNs) << (lNs + LR)) + k;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src.ld(l, j + r * nb);
+    if (k > 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], root<SGN>(tw, (r * k) << lts));
+    }
+    dft<LR, SGN>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst.st(l, d + r * Ns, v[r]);
+  }
+}
+
+template <int SGN, typename C, class SRC, class DST>
+__device__ __forceinline__ void stage_any(int LR, const SRC& src, const DST& dst, int ln, int lNs,
+                                          int llo, int hi, const C* tw) {
+  if (LR == 1) fft_stage_io<1, SGN>(src, dst, ln, lNs, llo, hi, tw);
+  else if (LR == 2) fft_stage_io<2, SGN>(src, dst, ln, lNs, llo, hi, tw);
+  else if (LR == 3) fft_stage_io<3, SGN>(src, dst, ln, lNs, llo, hi, tw);
+  else fft_stage_io<4, SGN>(src, dst, ln, lNs, llo, hi, tw);
+}
+
+// Transforms of length 2^ln (plan as in fft_lines) whose first stage reads global memory
+// through an accessor and/or whose last stage writes it; a and b are the shared ping-pong
+// buffers (layout ls, es).  The first stage never uses twiddles (Ns = 1), so tw only has to be
+// visible by the second stage: a barrier follows every stage but the last.
+template <int SGN, typename C, class SRC>
+__device__ C* fft_from_global(const SRC& first, C* a, C* b, int ls, int es, int ln, int llo,
+                              int hi, const C* tw) {
+  const int rem = ln & 3, nst = (rem ? 1 : 0) + (ln >> 2);
+  int lNs = 0;
+  C* cur = b;
+  C* oth = a;
+  for (int s = 0; s < nst; ++s) {
+    const int LR = (s == 0 && rem) ? rem : 4;
+    if (s == 0)
+      stage_any<SGN>(LR, first, SmemIO<C>{cur, ls, es}, ln, lNs, llo, hi, tw);
+    else
+      stage_any<SGN>(LR, SmemIO<C>{oth, ls, es}, SmemIO<C>{cur, ls, es}, ln, lNs, llo, hi, tw);
+    __syncthreads();
+    lNs += LR;
+    C* t = cur;   // the result of this stage becomes the next input
+    cur = oth;
+    oth = t;
+  }
+  return oth;     // holds the last stage's output
+}
+
+// input in `in` (visible to the block), scratch `oth`; the last stage writes through `last`
+template <int SGN, typename C, class DST>
+__device__ void fft_to_global(C* in, C* oth, const DST& last, int ls, int es, int ln, int llo,
+                              int hi, const C* tw) {
+  const int rem = ln & 3, nst = (rem ? 1 : 0) + (ln >> 2);
+  int lNs = 0;
+  for (int s = 0; s < nst; ++s) {
+    const int LR = (s == 0 && rem) ? rem : 4;
+    if (s == nst - 1) {
+      stage_any<SGN>(LR, SmemIO<C>{in, ls, es}, last, ln, lNs, llo, hi, tw);
+    } else {
+      stage_any<SGN>(LR, SmemIO<C>{in, ls, es}, SmemIO<C>{oth, ls, es}, ln, lNs, llo, hi, tw);
+      __syncthreads();
+      C* t = in;
+      in = oth;
+      oth = t;
+    }
+    lNs += LR;
+  }
+}
+
+// global lines in place: through shared memory, both ends direct
+template <int SGN, typename C, class IO>
+__device__ void fft_global_inplace(const IO& io, C* a, C* b, int ls, int es, int ln, int llo,
+                                   int hi, const C* tw) {
+  const int rem = ln & 3, nst = (rem ? 1 : 0) + (ln >> 2);
+  if (nst == 1) {   // one stage: stage into shared memory first (its reads and writes overlap)
+    C* r = fft_from_global<SGN>(io, a, b, ls, es, ln, llo, hi, tw);
+    const int nl = hi << llo, n = 1 << ln;
+    for (int q = threadIdx.x; q < nl * n; q += blockDim.x) {
+      const int l = q % nl, e = q / nl;
+      io.st(l, e, r[l * ls + e * es]);
+    }
+    return;
+  }
+  // first stage: global -> b; middle stages ping-pong; last stage -> global
+  const int LR0 = rem ? rem : 4;
+  stage_any<SGN>(LR0, io, SmemIO<C>{b, ls, es}, ln, 0, llo, hi, tw);
+  __syncthreads();
+  const int rest_ln = ln;   // the remaining stages continue from Ns = 2^LR0
+  int lNs = LR0;
+  C* in = b;
+  C* oth = a;
+  for (int s = 1; s < nst; ++s) {
+    if (s == nst - 1) {
+      stage_any<SGN>(4, SmemIO<C>{in, ls, es}, io, rest_ln, lNs, llo, hi, tw);
+    } else {
+      stage_any<SGN>(4, SmemIO<C>{in, ls, es}, SmemIO<C>{oth, ls, es}, rest_ln, lNs, llo, hi, tw);
+      __syncthreads();
+      C* t = in;
+      in = oth;
+      oth = t;
+    }
+    lNs += 4;
+  }
+}
+
 // Global -> shared staging in batches of LB elements per thread: all loads of a batch are
 // issued before any result is stored, so each thread keeps LB loads in flight.
 constexpr int LB = 8;
@@ -265,28 +426,9 @@ __global__ void __launch_bounds__(NT) k_spec_y(Spec<R> V, const CgScal* S) {
   C* b = a + (size_t)tx * V.ny;
   load_roots(tw, V.tw[1], V.ny);
   const int kx0 = blockIdx.x * tx, z = blockIdx.y, comp = blockIdx.z;
-  const int ncol = min(tx, V.nxh - kx0);
-  C* W = V.W + ((size_t)comp * V.nz + z) * V.ny * V.nxp + kx0;
-  const int total = tx * V.ny;
-  for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {
-    C v[LB];
-#pragma unroll
-    for (int u = 0; u < LB; ++u) {
-      const int idx = i0 + u * blockDim.x, col = idx & (tx - 1);
-      v[u] = (idx < total && col < ncol) ? W[(size_t)(idx >> ltx) * V.nxp + col] : C{(R)0, (R)0};
-    }
-#pragma unroll
-    for (int u = 0; u < LB; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      if (idx < total) a[idx] = v[u];
-    }
-  }
-  __syncthreads();
-  const C* F = fft_lines<SGN>(a, b, ilog2(V.ny), ltx, 1, 1, tx, tw);
-  for (int idx = threadIdx.x; idx < tx * V.ny; idx += blockDim.x) {
-    const int y = idx >> ltx, col = idx & (tx - 1);
-    if (col < ncol) W[(size_t)y * V.nxp + col] = F[idx];
-  }
+  const ColIO<C> io{V.W + ((size_t)comp * V.nz + z) * V.ny * V.nxp + kx0, V.nxp,
+                    min(tx, V.nxh - kx0)};
+  fft_global_inplace<SGN>(io, a, b, 1, tx, ilog2(V.ny), ltx, 1, tw);
 }
 
 // ---------------------------------------------------------------------------- z pass
@@ -304,25 +446,8 @@ __global__ void __launch_bounds__(NT) k_spec_z(Spec<R> V, const CgScal* S) {
   const int kx0 = blockIdx.x * tz, ky = blockIdx.y;
   const int ncol = min(tz, V.nxh - kx0);
   const size_t plane = (size_t)V.ny * V.nxp, comp_stride = (size_t)V.nz * plane;
-  C* W = V.W + (size_t)ky * V.nxp + kx0;
-  const int total = lw * V.nz;
-  for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {
-    C v[LB];
-#pragma unroll
-    for (int u = 0; u < LB; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      const int col = idx & (tz - 1), rest = idx >> ltz, kz = rest / 3, comp = rest - 3 * kz;
-      v[u] = (idx < total && col < ncol) ? W[comp * comp_stride + (size_t)kz * plane + col]
-                                         : C{(R)0, (R)0};
-    }
-#pragma unroll
-    for (int u = 0; u < LB; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      if (idx < total) a[idx] = v[u];
-    }
-  }
-  __syncthreads();
-  C* F = fft_lines<-1>(a, b, ilog2(V.nz), ltz, 3, 1, lw, tw);
+  const ZIO<C> io{V.W + (size_t)ky * V.nxp + kx0, plane, comp_stride, tz, ltz, ncol};
+  C* F = fft_from_global<-1>(io, a, b, 1, lw, ilog2(V.nz), ltz, 3, tw);
   C* other = F == a ? b : a;
   const R mu0 = (R)V.mean[0], lam0 = (R)V.mean[1], eta0 = (R)V.mean[2];
   const R c = lam0 + mu0;
@@ -358,11 +483,7 @@ __global__ void __launch_bounds__(NT) k_spec_z(Spec<R> V, const CgScal* S) {
     }
   }
   __syncthreads();
-  const C* G = fft_lines<+1>(F, other, ilog2(V.nz), ltz, 3, 1, lw, tw);
-  for (int idx = threadIdx.x; idx < lw * V.nz; idx += blockDim.x) {
-    const int col = idx & (tz - 1), rest = idx >> ltz, kz = rest / 3, comp = rest - 3 * kz;
-    if (col < ncol) W[comp * comp_stride + (size_t)kz * plane + col] = G[idx];
-  }
+  fft_to_global<+1>(F, other, io, 1, lw, ilog2(V.nz), ltz, 3, tw);
 }
 
 // ---------------------------------------------------------------------------- x inverse
