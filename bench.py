@@ -271,7 +271,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(sim.stream)
         agg = {"launches": 0, "t_mv": 0.0, "n_mv": 0, "it_elas": [], "it_elas_outer": [],
-               "it_diff": []}
+               "it_diff": [], "phase_ms": [0.0, 0.0, 0.0, 0.0]}
         for _ in range(args.steps):
             s = sim.step(args.dt)
             agg["launches"] += s["launches"]
@@ -280,6 +280,8 @@ def main():
             agg["it_elas"].append(s["it_elas"])
             agg["it_elas_outer"].append(s["it_elas_outer"])
             agg["it_diff"].append(s["it_diff"])
+            for q in range(4):
+                agg["phase_ms"][q] += s["t_phase_ms"][q] / args.steps
         e1.record(sim.stream)
         barrier()
         agg["clocks"] = clocks.stop() if clocks is not None else None
@@ -362,7 +364,7 @@ def main():
         sim_o = Simulation(n, P, st0, precision=oprec, device=dev)
         ag_o = time_steps(sim_o)
         other = {"precision": oprec, "value": ag_o["value"], "unit": UNIT,
-                 "ms_per_step": ag_o["ms"] / args.steps,
+                 "ms_per_step": ag_o["ms"] / args.steps, "phase_ms_per_step": ag_o["phase_ms"],
                  "solver": {"it_elas_per_step": ag_o["it_elas"],
                             "it_elas_outer_per_step": ag_o["it_elas_outer"],
                             "it_diff_per_step": ag_o["it_diff"]},
@@ -446,6 +448,8 @@ def main():
                        "l2": "inputs larger than L2 (15 state arrays + workspace, "
                              f"{(15 * V * 8 + ws_bytes) / 1e9:.1f} GB)",
                        "parallelism": f"replicas x{world}"},
+            "phase_ms_per_step": dict(zip(("S0-S1 transport", "S2 diffusion", "S3-S5 reactions",
+                                           "S6-S7 elasticity"), agg["phase_ms"])),
             "solver": {"it_elas_per_step": agg["it_elas"],
                        "it_elas_outer_per_step": agg["it_elas_outer"],
                        "it_diff_per_step": agg["it_diff"]},

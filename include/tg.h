@@ -125,6 +125,8 @@ typedef struct {
   int64_t launches;          /* CUDA kernels this call queued                                */
   double t_elas_matvec_ms;   /* with timing on: summed duration of the elasticity operator   */
   int64_t n_elas_matvec;     /*   kernel over the launches that did work, and their count    */
+  double t_phase_ms[4];      /* with timing on: device time of S0-S1, S2, S3-S5 and S6-S7     */
+                             /*   (event to event on the stream), summed over the call's steps */
 } tg_stats;
 
 /* Bytes of workspace tg_init needs for this grid, parameters and precision (0 on invalid

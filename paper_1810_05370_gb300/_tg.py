@@ -58,7 +58,8 @@ class tg_stats(C.Structure):
                 ("it_elas_outer", C.c_int32), ("relres_diff", C.c_double * 3),
                 ("relres_elas", C.c_double), ("it_diff_total", C.c_int64),
                 ("it_elas_total", C.c_int64), ("launches", C.c_int64),
-                ("t_elas_matvec_ms", C.c_double), ("n_elas_matvec", C.c_int64)]
+                ("t_elas_matvec_ms", C.c_double), ("n_elas_matvec", C.c_int64),
+                ("t_phase_ms", C.c_double * 4)]
 
 
 class tg_batch_stats(C.Structure):
@@ -168,7 +169,8 @@ def stats_dict(s: tg_stats) -> dict:
             "it_elas_outer": int(s.it_elas_outer), "relres_diff": list(s.relres_diff),
             "relres_elas": float(s.relres_elas), "it_diff_total": int(s.it_diff_total),
             "it_elas_total": int(s.it_elas_total), "launches": int(s.launches),
-            "t_elas_matvec_ms": float(s.t_elas_matvec_ms), "n_elas_matvec": int(s.n_elas_matvec)}
+            "t_elas_matvec_ms": float(s.t_elas_matvec_ms), "n_elas_matvec": int(s.n_elas_matvec),
+            "t_phase_ms": [float(x) for x in s.t_phase_ms]}
 
 
 # ----------------------------------------------------------------------------- same-name calls

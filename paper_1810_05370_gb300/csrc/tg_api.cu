@@ -350,6 +350,9 @@ struct tg_ctx {
   std::vector<cudaEvent_t> ev;   // pairs (start, stop) per operator launch of one solve
   double t_matvec_ms;
   long long n_matvec;
+  cudaEvent_t pev[5];    // phase boundaries of a step (created on first use)
+  bool pev_ok;
+  double t_phase[4];
   // spectral elasticity preconditioner (workspace sized for it when L.spectral)
   Spec<float> sp32;      // FP32 form: mixed precision, adjoint refined solves
   Spec<double> sp64;     // FP64 form: FP64 solves
@@ -746,12 +749,39 @@ void reset_profile(tg_ctx* X) {
   X->launches = 0;
   X->t_matvec_ms = 0.0;
   X->n_matvec = 0;
+  for (int q = 0; q < 4; ++q) X->t_phase[q] = 0.0;
 }
 
 void fill_profile(tg_ctx* X, tg_stats* stats) {
   stats->launches = X->launches;
   stats->t_elas_matvec_ms = X->t_matvec_ms;
   stats->n_elas_matvec = X->n_matvec;
+  for (int q = 0; q < 4; ++q) stats->t_phase_ms[q] = X->t_phase[q];
+}
+
+// phase boundary q (0..4) of a step, with timing on
+void phase_mark(tg_ctx* X, int q) {
+  if (!X->timing) return;
+  if (!X->pev_ok) {
+    for (int e = 0; e < 5; ++e) {
+      if (cudaEventCreate(&X->pev[e]) != cudaSuccess) {
+        while (e-- > 0) cudaEventDestroy(X->pev[e]);
+        return;
+      }
+    }
+    X->pev_ok = true;
+  }
+  cudaEventRecord(X->pev[q], X->stream);
+}
+
+// after a step with timing on (the stream has been synchronised): add the phase durations
+void phase_harvest(tg_ctx* X) {
+  if (!X->timing || !X->pev_ok) return;
+  if (cudaEventSynchronize(X->pev[4]) != cudaSuccess) return;
+  for (int q = 0; q < 4; ++q) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, X->pev[q], X->pev[q + 1]) == cudaSuccess) X->t_phase[q] += ms;
+  }
 }
 
 // One step of the Section 3 split.
@@ -779,6 +809,7 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
     for (int q = 0; q < 14; ++q) REC(T_P + q, start[q]);
   }
   // S0: K faces, CN diagonal and rho from the step's start
+  phase_mark(X, 0);
   double* const Kf[3] = {X->a[A_KF0], X->a[A_KF1], X->a[A_KF2]};
   CK(launch_diff_coef(G, X->dp, dt, S.g, S.w, S.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
                       X->a[A_RHO], s));
@@ -833,6 +864,7 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   }
   // S2: Crank-Nicolson diffusion of i, o, l (i after transport kept for the g, w fix-up);
   // single species: of c alone
+  phase_mark(X, 1);
   const bool single = single_species(X);
   CK(cudaMemcpyAsync(X->a[A_IDAG], single ? S.p : S.i, bytes, cudaMemcpyDeviceToDevice, s));
   tg_status e = TG_OK;
@@ -849,15 +881,19 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   REC(T_OD, S.o);
   REC(T_LD, S.l);
   // S2 fix-up and S3-S5 reactions
+  phase_mark(X, 2);
   CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l,
                   X->prec == TG_MIXED, single_species(X), s));
   X->launches += 1;
   // S6-S7: elasticity from the post-reaction state, then v = du / dt
+  phase_mark(X, 3);
   e = build_elas_coef(X, true);
   if (e != TG_OK) return e;
   e = elas_solve(X, S.u, nullptr, true, 1.0 / dt, stats);
   if (e != TG_OK) return e;
+  phase_mark(X, 4);
   for (int d = 0; d < 3; ++d) REC(T_UP0 + d, S.u[d]);
+  phase_harvest(X);
   return TG_OK;
 }
 
@@ -1276,6 +1312,8 @@ tg_status tg_set_timing(tg_ctx* X, int32_t enable) {
 void tg_free(tg_ctx* X) {
   if (!X) return;
   for (cudaEvent_t e : X->ev) cudaEventDestroy(e);
+  if (X->pev_ok)
+    for (cudaEvent_t e : X->pev) cudaEventDestroy(e);
   delete X;
 }
 
