@@ -25,6 +25,8 @@ enum Arr {
   A_DSUM_E0, A_DSUM_E1, A_DSUM_E2, A_DINV_E0, A_DINV_E1, A_DINV_E2,
   A_B0, A_B1, A_B2, A_DU0, A_DU1, A_DU2, A_ER0, A_ER1, A_ER2, A_EP0, A_EP1, A_EP2,
   A_EQ0, A_EQ1, A_EQ2,
+  // (hi, lo) FP32 pairs of u, mu, lambda for the double-FP32 residual (TG_MIXED only)
+  A_UDF0, A_UDF1, A_UDF2, A_MUDF, A_LAMDF,
   A_COUNT
 };
 
@@ -171,7 +173,7 @@ Layout layout(const Geo& G, tg_precision prec, bool adjoint = false, bool spectr
   const size_t abytes = round_up((size_t)G.nvox * sizeof(double));
   for (int a = 0; a < A_COUNT; ++a) {
     L.arr[a] = off;
-    off += abytes;
+    if (a < A_UDF0 || prec == TG_MIXED) off += abytes;
   }
   const size_t fbytes = round_up((size_t)G.nvox * sizeof(float));
   // FP32 arrays: the mixed precision, and the adjoint's refined elasticity solves
@@ -350,6 +352,8 @@ struct tg_ctx {
   std::vector<cudaEvent_t> ev;   // pairs (start, stop) per operator launch of one solve
   double t_matvec_ms;
   long long n_matvec;
+  bool df_res;           // the mixed precision's residual in double-FP32 (df_residual_ok)
+  bool in_batch;         // owned by a batch (its persistent solvers read FP64 faces)
   cudaEvent_t pev[5];    // phase boundaries of a step (created on first use)
   bool pev_ok;
   double t_phase[4];
@@ -454,11 +458,24 @@ Elas elas_view(tg_ctx* X, double* const u[3], double* const b[3]) {
     E.u[d] = u[d];
     E.v[d] = X->st.v[d];
     E.z[d] = X->z64[d];
+    E.udf[d] = reinterpret_cast<float2*>(X->a[A_UDF0 + d]);
   }
+  E.df = X->df_res ? 1 : 0;
+  E.mudf = reinterpret_cast<float2*>(X->a[A_MUDF]);
+  E.lamdf = reinterpret_cast<float2*>(X->a[A_LAMDF]);
   E.S = X->scal + 3;
   E.partial = X->partial;
   E.counter = X->counter;
   return E;
+}
+
+// The mixed precision's FP64 residual runs in double-FP32 arithmetic when the tolerance allows
+// it: its ~48-bit significand resolves residuals down to about 1e-13 of |A||u|, ample for
+// rtol_elas >= 1e-10; deeper tolerances, adjoint contexts and batches keep FP64.
+constexpr double DF_RTOL_MIN = 1e-10;
+bool df_residual_ok(const tg_ctx* X) {
+  return X->prec == TG_MIXED && !X->has_adjoint && !X->in_batch &&
+         X->prm.rtol_elas >= DF_RTOL_MIN;
 }
 
 // S2: the three Crank-Nicolson solves (i, o, l) on the faces built by S0.
@@ -605,6 +622,12 @@ void harvest_timing(tg_ctx* X, int recorded, int did) {
 // TG_MIXED elasticity: iterative refinement with an FP64 residual and FP32 inner PCG.
 tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3], bool minus_b,
                            double inv_dt, tg_stats* stats) {
+  if (X->df_res && b_ext) {   // the double-FP32 residual reads (hi, lo) pairs of the rhs
+    double* const packed[3] = {X->a[A_B0], X->a[A_B1], X->a[A_B2]};
+    CK(launch_df_pack3(X->G, b_ext, packed, X->stream));
+    X->launches += 1;
+    b_ext = nullptr;
+  }
   const Elas E = elas_view(X, u, b_ext);
   const Elas32 I = elas32_view(X);
   CgScal* Sout = X->scal + 3;
@@ -1135,6 +1158,7 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
   for (int b = 0; b < B_COUNT; ++b)
     X->b32[b] = (prec == TG_MIXED || adjoint) ? (float*)(X->ws + L.arr32[b]) : nullptr;
   X->has_adjoint = adjoint;
+  X->df_res = df_residual_ok(X);
   for (int c = 0; c < C_COUNT; ++c) X->adj[c] = adjoint ? (double*)(X->ws + L.adj[c]) : nullptr;
   X->grad = (double*)(X->ws + L.grad);
   X->partial = (double*)(X->ws + L.partial);
@@ -1262,6 +1286,7 @@ tg_status tg_set_params(tg_ctx* X, const tg_params* params) {
   if (params->precond_elas == TG_PRECOND_SPECTRAL && !X->L.spectral) return TG_ERR_WORKSPACE;
   if (X->has_adjoint && params->model != TG_MODEL_MULTISPECIES) return TG_ERR_ARG;
   X->prm = *params;
+  X->df_res = df_residual_ok(X);
   X->dp = make_dev_params(params);
   return TG_OK;
 }
@@ -1806,6 +1831,8 @@ tg_status tg_batch_init(int32_t nsims, const tg_grid* grids, const tg_params* pa
       delete B;
       return e;
     }
+    X->in_batch = true;      // the batch's persistent residual kernel reads FP64 faces
+    X->df_res = false;
     B->ctx.push_back(X);
     off += round_up(b);
   }

@@ -122,7 +122,9 @@ __global__ void __launch_bounds__(NT) k_cn32_matvec(Geo G, Cn32 I) {
   }
 }
 
-// e += alpha p, r -= alpha q; <r, D^{-1} r>, <r, r>
+// e += alpha p, r -= alpha q; <r, D^{-1} r>, <r, r>.  float4 groups g = g0, g0 + gs, ... of an
+// n-voxel system plus the scalar tail n - n % 4 .. n (block 0); a group's products are summed
+// in FP32, groups in FP64.
 __global__ void __launch_bounds__(NT) k_cn32_update(long long n, Cn32 I) {
   bool act[3];
   if (!active3(I, act)) return;
@@ -130,17 +132,39 @@ __global__ void __launch_bounds__(NT) k_cn32_update(long long n, Cn32 I) {
 #pragma unroll
   for (int r = 0; r < 3; ++r) alpha[r] = (float)I.S[r].alpha;
   double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
-    const float di = __ldg(I.dinv + c);
+  const long long gs = (long long)gridDim.x * blockDim.x, ng = n / 4;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < ng; v += gs) {
+    const float4 d = __ldg(reinterpret_cast<const float4*>(I.dinv) + v);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       if (!act[r]) continue;
-      I.e[r][c] += alpha[r] * I.p[r][c];
-      const float res = I.r[r][c] - alpha[r] * I.q[r][c];
-      I.r[r][c] = res;
-      acc[2 * r] += (double)(res * (di * res));
-      acc[2 * r + 1] += (double)(res * res);
+      float4* e4 = reinterpret_cast<float4*>(I.e[r]) + v;
+      float4* r4 = reinterpret_cast<float4*>(I.r[r]) + v;
+      const float4 p = reinterpret_cast<const float4*>(I.p[r])[v];
+      const float4 q = reinterpret_cast<const float4*>(I.q[r])[v];
+      float4 e = *e4, x = *r4;
+      const float a = alpha[r];
+      e.x += a * p.x; e.y += a * p.y; e.z += a * p.z; e.w += a * p.w;
+      x.x -= a * q.x; x.y -= a * q.y; x.z -= a * q.z; x.w -= a * q.w;
+      *e4 = e;
+      *r4 = x;
+      acc[2 * r] += (double)(x.x * (d.x * x.x) + x.y * (d.y * x.y) + x.z * (d.z * x.z) +
+                             x.w * (d.w * x.w));
+      acc[2 * r + 1] += (double)(x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w);
+    }
+  }
+  if (blockIdx.x == 0) {
+    for (long long c = 4 * ng + threadIdx.x; c < n; c += blockDim.x) {
+      const float di = I.dinv[c];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        if (!act[r]) continue;
+        I.e[r][c] += alpha[r] * I.p[r][c];
+        const float res = I.r[r][c] - alpha[r] * I.q[r][c];
+        I.r[r][c] = res;
+        acc[2 * r] += (double)(res * (di * res));
+        acc[2 * r + 1] += (double)(res * res);
+      }
     }
   }
   double out[6];
@@ -151,7 +175,7 @@ __global__ void __launch_bounds__(NT) k_cn32_update(long long n, Cn32 I) {
   }
 }
 
-// p = D^{-1} r + beta p (p = D^{-1} r on an inner solve's first iteration)
+// p = D^{-1} r + beta p (p = D^{-1} r on an inner solve's first iteration), float4 groups
 __global__ void __launch_bounds__(NT) k_cn32_pupdate(long long n, Cn32 I) {
   bool act[3];
   if (!active3(I, act)) return;
@@ -162,14 +186,33 @@ __global__ void __launch_bounds__(NT) k_cn32_pupdate(long long n, Cn32 I) {
     beta[r] = (float)I.S[r].beta;
     first[r] = I.S[r].it == 0;
   }
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
-    const float di = __ldg(I.dinv + c);
+  const long long gs = (long long)gridDim.x * blockDim.x, ng = n / 4;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < ng; v += gs) {
+    const float4 d = __ldg(reinterpret_cast<const float4*>(I.dinv) + v);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       if (!act[r]) continue;
-      const float z = di * I.r[r][c];
-      I.p[r][c] = first[r] ? z : z + beta[r] * I.p[r][c];
+      const float4 x = reinterpret_cast<const float4*>(I.r[r])[v];
+      float4* p4 = reinterpret_cast<float4*>(I.p[r]) + v;
+      const float4 z = {d.x * x.x, d.y * x.y, d.z * x.z, d.w * x.w};
+      if (first[r]) {
+        *p4 = z;
+      } else {
+        const float4 p = *p4;
+        const float b = beta[r];
+        *p4 = float4{z.x + b * p.x, z.y + b * p.y, z.z + b * p.z, z.w + b * p.w};
+      }
+    }
+  }
+  if (blockIdx.x == 0) {
+    for (long long c = 4 * ng + threadIdx.x; c < n; c += blockDim.x) {
+      const float di = I.dinv[c];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        if (!act[r]) continue;
+        const float z = di * I.r[r][c];
+        I.p[r][c] = first[r] ? z : z + beta[r] * I.p[r][c];
+      }
     }
   }
 }
@@ -185,7 +228,7 @@ __global__ void __launch_bounds__(NT) k_cn_ir_correct(long long n, Cn3 C, Cn32 I
 }
 
 int flat_blocks(const Geo& G) {   // never more blocks than the partial-sum buffer holds
-  long long b = (G.nvox + NT - 1) / NT;
+  long long b = (G.nvox / 4 + NT - 1) / NT;
   b = b < 8LL * 152 ? b : 8LL * 152;
   b = b < G.nblocks ? b : G.nblocks;
   return (int)(b > 0 ? b : 1);

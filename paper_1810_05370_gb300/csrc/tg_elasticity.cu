@@ -35,8 +35,14 @@ __global__ void __launch_bounds__(NT) k_elas_coef(Geo G, DevParams P, Elas E,
       mfm[d] = 0.5 * (E.mu[nm[d]] + muc);
       lfp[d] = 0.5 * (lac + E.lam[np[d]]);
       lfm[d] = 0.5 * (E.lam[nm[d]] + lac);
-      E.F[d][c] = (lfp[d] + 2.0 * mfp[d]) * G.ih2[d];
-      E.G[d][c] = mfp[d] * G.ih2[d];
+      const double fv = (lfp[d] + 2.0 * mfp[d]) * G.ih2[d], gv = mfp[d] * G.ih2[d];
+      if (E.df) {   // (hi, lo) pairs for the double-FP32 residual
+        reinterpret_cast<float2*>(E.F[d])[c] = df_pack(fv);
+        reinterpret_cast<float2*>(E.G[d])[c] = df_pack(gv);
+      } else {
+        E.F[d][c] = fv;
+        E.G[d][c] = gv;
+      }
     }
     const double et = E.eta[c];
 #pragma unroll
@@ -48,15 +54,23 @@ __global__ void __launch_bounds__(NT) k_elas_coef(Geo G, DevParams P, Elas E,
         const double cm = (d == a) ? lfm[d] + 2.0 * mfm[d] : mfm[d];
         s += (cp + cm) * G.ih2[d];
       }
-      E.dsum[a][c] = s;
+      if (E.df)
+        reinterpret_cast<float2*>(E.dsum[a])[c] = df_pack(s);
+      else
+        E.dsum[a][c] = s;
       E.dinv[a][c] = 1.0 / s;
     }
     if (force) {
       const double sc = p[c] + n[c];
       const double th = P.zeta * tanh(sc);
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
-        E.b[d][c] = th * (((p[np[d]] + n[np[d]]) - (p[nm[d]] + n[nm[d]])) * G.inv2h[d]);
+      for (int d = 0; d < 3; ++d) {
+        const double bv = th * (((p[np[d]] + n[np[d]]) - (p[nm[d]] + n[nm[d]])) * G.inv2h[d]);
+        if (E.df)
+          reinterpret_cast<float2*>(E.b[d])[c] = df_pack(bv);
+        else
+          E.b[d][c] = bv;
+      }
     }
   }
 }

@@ -405,10 +405,60 @@ struct Elas {
   double* u[3];      // displacement (in: u^n, out: u^{n+1})
   double* v[3];      // velocity (written when dt > 0)
   double* z[3];      // spectral preconditioner output (null with Jacobi)
+  // double-FP32 residual of the mixed precision (df != 0): F, G and dsum then hold (hi, lo)
+  // FP32 pairs instead of FP64 values, and udf, mudf, lamdf the pairs of u, mu and lambda
+  int df;
+  float2* udf[3];
+  float2* mudf;
+  float2* lamdf;
   CgScal* S;
   double* partial;
   unsigned int* counter;
 };
+
+// A double-FP32 ("double-float") number hi + lo, |lo| <= ulp(hi) / 2: about 48 bits of
+// significand from FP32 arithmetic, which GB300 executes 64 times faster than FP64.  The
+// operations are the classical error-free transformations: Knuth's two-sum for a + b, and
+// the fused multiply-add remainder a * b - fl(a * b) for products; __fadd_rn / __fmul_rn keep
+// the compiler from contracting them.
+struct Df {
+  float hi, lo;
+};
+__device__ __forceinline__ Df df_split(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - (double)hi)};
+}
+__device__ __forceinline__ Df df_of(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ float2 df_pack(double x) {
+  const Df d = df_split(x);
+  return make_float2(d.hi, d.lo);
+}
+__device__ __forceinline__ Df df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ Df df_fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ Df df_add(Df x, Df y) {
+  Df s = df_two_sum(x.hi, y.hi);
+  const Df t = df_two_sum(x.lo, y.lo);
+  s = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ Df df_sub(Df x, Df y) { return df_add(x, Df{-y.hi, -y.lo}); }
+__device__ __forceinline__ Df df_mul(Df x, Df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ double df_value(Df x) { return (double)x.hi + (double)x.lo; }
+
 // 4 h_A h_D [ d_D(mu d_A u_D) + d_A(lambda d_D u_D) ] at the centre node (centred differences)
 template <int A, int D>
 __device__ __forceinline__ double elas_mixed64(const Nbr& nb, const double* __restrict__ xd,
@@ -454,6 +504,8 @@ cudaError_t launch_elas_finish(const Geo&, const Elas&, double inv_dt, bool zero
 // mixed precision (tg_mixed.cu)
 cudaError_t launch_to_f32(long long n, const F32Copy& c, cudaStream_t st);
 cudaError_t launch_elas32_coef(const Geo&, const Elas&, const Elas32&, cudaStream_t st);
+cudaError_t launch_df_pack3(const Geo&, const double* const b[3], double* const out[3],
+                            cudaStream_t st);
 cudaError_t launch_elas_ir_residual(const Geo&, const Elas&, const Elas32&, CgScal* Sout,
                                     bool minus_b, double tau_min, cudaStream_t st);
 cudaError_t launch_elas32_matvec(const Geo&, const Elas32&, cudaStream_t st);

@@ -28,21 +28,36 @@ __global__ void __launch_bounds__(NT) k_to_f32(long long n, F32Copy c) {
   }
 }
 
-// FP32 node coefficients and Jacobi inverse diagonal from the FP64 ones
-__global__ void __launch_bounds__(NT) k_elas32_coef(long long n, const double* __restrict__ mu,
-                                                    const double* __restrict__ lam,
-                                                    const double* __restrict__ eta,
-                                                    const double* __restrict__ d0,
-                                                    const double* __restrict__ d1,
-                                                    const double* __restrict__ d2, Elas32 I) {
+// FP32 node coefficients and Jacobi inverse diagonal from the FP64 ones; with the double-FP32
+// residual also the (hi, lo) pairs of mu, lambda and the starting u
+__global__ void __launch_bounds__(NT) k_elas32_coef(long long n, Elas E, Elas32 I) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-    I.mu[e] = (float)mu[e];
-    I.lam[e] = (float)lam[e];
-    I.eta[e] = (float)eta[e];
-    I.dinv[0][e] = (float)d0[e];
-    I.dinv[1][e] = (float)d1[e];
-    I.dinv[2][e] = (float)d2[e];
+    const double mu = E.mu[e], lam = E.lam[e];
+    I.mu[e] = (float)mu;
+    I.lam[e] = (float)lam;
+    I.eta[e] = (float)E.eta[e];
+    I.dinv[0][e] = (float)E.dinv[0][e];
+    I.dinv[1][e] = (float)E.dinv[1][e];
+    I.dinv[2][e] = (float)E.dinv[2][e];
+    if (E.df) {
+      E.mudf[e] = df_pack(mu);
+      E.lamdf[e] = df_pack(lam);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) E.udf[a][e] = df_pack(E.u[a][e]);
+    }
+  }
+}
+
+// an external right-hand side into the (hi, lo) pairs the double-FP32 residual reads
+__global__ void __launch_bounds__(NT) k_df_pack3(long long n, const double* b0, const double* b1,
+                                                 const double* b2, double* o0, double* o1,
+                                                 double* o2) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    reinterpret_cast<float2*>(o0)[e] = df_pack(b0[e]);
+    reinterpret_cast<float2*>(o1)[e] = df_pack(b1[e]);
+    reinterpret_cast<float2*>(o2)[e] = df_pack(b2[e]);
   }
 }
 
@@ -110,11 +125,15 @@ __global__ void __launch_bounds__(NT) k_elas32_update_spec(long long n, Elas32 I
 // ------------------------------------------------------------------------------ refinement
 
 // FP64 residual of the current iterate, outer stopping test and start of the inner solve
+template <bool DF>
 __global__ void __launch_bounds__(NT) k_elas_ir_residual(Geo G, Elas E, Elas32 I, CgScal* Sout,
                                                          int minus_b, double tau_min,
                                                          int max_sweeps) {
   double acc[3] = {0.0, 0.0, 0.0};
-  elas_ir_residual_tile(G, E, I, minus_b, blockIdx.x, blockIdx.y, blockIdx.z, acc);
+  if (DF)
+    elas_ir_residual_tile_df(G, E, I, minus_b, blockIdx.x, blockIdx.y, blockIdx.z, acc);
+  else
+    elas_ir_residual_tile(G, E, I, minus_b, blockIdx.x, blockIdx.y, blockIdx.z, acc);
   double out[3];
   if (reduce_last_block<3>(acc, E.partial, E.counter, out) && threadIdx.x == 0 && threadIdx.y == 0)
     elas_ir_residual_finalize(*Sout, *I.S, out[0], out[1], out[2], tau_min, max_sweeps, true);
@@ -245,8 +264,14 @@ cudaError_t launch_to_f32(long long n, const F32Copy& c, cudaStream_t st) {
 }
 
 cudaError_t launch_elas32_coef(const Geo& G, const Elas& E, const Elas32& I, cudaStream_t st) {
-  k_elas32_coef<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E.mu, E.lam, E.eta, E.dinv[0],
-                                                      E.dinv[1], E.dinv[2], I);
+  k_elas32_coef<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_pack3(const Geo& G, const double* const b[3], double* const out[3],
+                            cudaStream_t st) {
+  k_df_pack3<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, b[0], b[1], b[2], out[0], out[1],
+                                                   out[2]);
   return cudaGetLastError();
 }
 
@@ -254,8 +279,12 @@ cudaError_t launch_elas32_coef(const Geo& G, const Elas& E, const Elas32& I, cud
 
 cudaError_t launch_elas_ir_residual(const Geo& G, const Elas& E, const Elas32& I, CgScal* Sout,
                                     bool minus_b, double tau_min, cudaStream_t st) {
-  k_elas_ir_residual<<<G.grid, dim3(BX, BY), 0, st>>>(G, E, I, Sout, minus_b ? 1 : 0, tau_min,
-                                                      1 << 30);
+  if (E.df)
+    k_elas_ir_residual<true><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, I, Sout, minus_b ? 1 : 0,
+                                                              tau_min, 1 << 30);
+  else
+    k_elas_ir_residual<false><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, I, Sout, minus_b ? 1 : 0,
+                                                               tau_min, 1 << 30);
   return cudaGetLastError();
 }
 

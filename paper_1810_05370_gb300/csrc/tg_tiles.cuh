@@ -360,6 +360,87 @@ __device__ __forceinline__ void elas_ir_residual_tile(const Geo& G, const Elas& 
   }
 }
 
+// The same residual in double-FP32 arithmetic (Elas::df): the operator's faces, diagonal, u,
+// mu, lambda and b are (hi, lo) FP32 pairs and every product and sum is an error-free
+// double-FP32 operation, so the FP64 units only convert the per-thread sums.  Sums of squares
+// are formed in FP32 per thread (a few dozen terms of one sign) and in FP64 across threads.
+template <int A, int D>
+__device__ __forceinline__ Df elas_mixed_df(const Nbr& nb, const float2* __restrict__ xd,
+                                            const float2* __restrict__ mu,
+                                            const float2* __restrict__ lam) {
+  const Df epp = df_of(xd[at2<A, D>(nb, +1, +1)]);
+  const Df epm = df_of(xd[at2<A, D>(nb, -1, +1)]);
+  const Df emp = df_of(xd[at2<A, D>(nb, +1, -1)]);
+  const Df emm = df_of(xd[at2<A, D>(nb, -1, -1)]);
+  const Df t1 = df_mul(df_of(mu[at1<D>(nb, +1)]), df_sub(epp, epm));
+  const Df t2 = df_mul(df_of(mu[at1<D>(nb, -1)]), df_sub(emp, emm));
+  const Df t3 = df_mul(df_of(lam[at1<A>(nb, +1)]), df_sub(epp, emp));
+  const Df t4 = df_mul(df_of(lam[at1<A>(nb, -1)]), df_sub(epm, emm));
+  return df_sub(df_add(df_sub(t1, t2), t3), t4);
+}
+
+template <int A>
+__device__ __forceinline__ Df elas_row_df(const Nbr& nb, long long c, const Elas& E,
+                                          const Df (&sc)[3][3]) {
+  constexpr int D1 = (A + 1) % 3, D2 = (A + 2) % 3;
+  const float2* __restrict__ xa = E.udf[A];
+  const float2* __restrict__ CA = reinterpret_cast<const float2*>(E.F[A]);
+  const float2* __restrict__ C1 = reinterpret_cast<const float2*>(E.G[D1]);
+  const float2* __restrict__ C2 = reinterpret_cast<const float2*>(E.G[D2]);
+  const float2* __restrict__ DS = reinterpret_cast<const float2*>(E.dsum[A]);
+  Df v = df_mul(df_of(DS[c]), df_of(xa[c]));
+  v = df_sub(v, df_mul(df_of(CA[c]), df_of(xa[at1<A>(nb, 1)])));
+  v = df_sub(v, df_mul(df_of(CA[at1<A>(nb, -1)]), df_of(xa[at1<A>(nb, -1)])));
+  v = df_sub(v, df_mul(df_of(C1[c]), df_of(xa[at1<D1>(nb, 1)])));
+  v = df_sub(v, df_mul(df_of(C1[at1<D1>(nb, -1)]), df_of(xa[at1<D1>(nb, -1)])));
+  v = df_sub(v, df_mul(df_of(C2[c]), df_of(xa[at1<D2>(nb, 1)])));
+  v = df_sub(v, df_mul(df_of(C2[at1<D2>(nb, -1)]), df_of(xa[at1<D2>(nb, -1)])));
+  v = df_sub(v, df_mul(sc[A][D1], elas_mixed_df<A, D1>(nb, E.udf[D1], E.mudf, E.lamdf)));
+  v = df_sub(v, df_mul(sc[A][D2], elas_mixed_df<A, D2>(nb, E.udf[D2], E.mudf, E.lamdf)));
+  return v;
+}
+
+// b holds (hi, lo) pairs as well: E.b[a] reinterpreted
+__device__ __forceinline__ void elas_ir_residual_tile_df(const Geo& G, const Elas& E,
+                                                         const Elas32& I, int minus_b, int bx,
+                                                         int by, int bz, double (&acc)[3]) {
+  Df sc[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sc[a][d] = df_split(G.s_cross[a][d]);
+  float sbb = 0.0f, srr = 0.0f, srz = 0.0f;
+  const int i = bx * BX + threadIdx.x;
+  const int j = by * BY + threadIdx.y;
+  if (i < G.nx && j < G.ny) {
+    const int k0 = bz * G.zc, k1 = min(G.nz, k0 + G.zc);
+    for (int k = k0; k < k1; ++k) {
+      const Nbr nb = make_nbr(G, i, j, k);
+      const long long c = nb.at(0, 0, 0);
+      Df Au[3];
+      Au[0] = elas_row_df<0>(nb, c, E, sc);
+      Au[1] = elas_row_df<1>(nb, c, E, sc);
+      Au[2] = elas_row_df<2>(nb, c, E, sc);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float2 bv = reinterpret_cast<const float2*>(E.b[a])[c];
+        const Df rhs = minus_b ? Df{-bv.x, -bv.y} : Df{bv.x, bv.y};
+        const Df res = df_sub(rhs, Au[a]);
+        const float r32 = __fadd_rn(res.hi, res.lo);
+        const float z32 = I.dinv[a][c] * r32;
+        I.r[a][c] = r32;
+        I.e[a][c] = 0.0f;
+        sbb += rhs.hi * rhs.hi;
+        srr += r32 * r32;
+        srz += r32 * z32;
+      }
+    }
+  }
+  acc[0] += (double)sbb;
+  acc[1] += (double)srr;
+  acc[2] += (double)srz;
+}
+
 // Outer decision after a residual (the same test as the FP64 solve: |r| <= rtol |rhs|) and the
 // start of the inner FP32 solve A e = r with relative target max(tau_min, half of what the
 // outer still needs).  O.pad counts the inner iterations spent so far; a solve that exceeds
@@ -410,8 +491,10 @@ __device__ __forceinline__ void elas_ir_correct_range(const Elas& E, const Elas3
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const double e = (double)I.e[a][c] * inv_scale;
-      E.u[a][c] += e;
+      const double un = E.u[a][c] + e;
+      E.u[a][c] = un;
       E.du[a][c] += e;
+      if (E.df) E.udf[a][c] = df_pack(un);
     }
   }
 }

@@ -97,3 +97,26 @@ def test_mixed_vs_fp64_256cubed(torch_cuda):
     errs = errors(got, ref)
     print("mixed vs fp64 at 256^3, rel-L2:", {k: f"{v:.1e}" for k, v in errs.items()})
     assert max(errs.values()) <= TOL_MIXED, errs
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_mixed_double_fp32_residual_reaches_1e10(torch_cuda, oracle, precond):
+    """At rtol_elas = 1e-10 the mixed refinement uses the double-FP32 residual; the solve must
+    still reach the tolerance (an FP32-grade residual would stall near 1e-7) and agree with
+    the oracle's tightly converged solution."""
+    import torch
+    from paper_1810_05370_gb300 import Simulation
+    n = (32, 32, 16)
+    P = workload_params(rtol_elas=1e-10, precond_elas=precond)
+    st = initial_state(n, seed=4)
+    sim = Simulation(n, P, st, precision="mixed")
+    rng = np.random.default_rng(9)
+    rhs = rng.standard_normal((3, n[2], n[1], n[0]))
+    u_t = [torch.zeros(n[2], n[1], n[0], dtype=torch.float64, device="cuda") for _ in range(3)]
+    stats = sim.solve_elasticity([torch.from_numpy(rhs[a].copy()).cuda() for a in range(3)], u_t)
+    got = np.stack([u.cpu().numpy() for u in u_t])
+    sim.close()
+    mu, lam, eta = oracle.lame(n, P, st)
+    ref, _, _ = oracle.elasticity_solve(n, mu, lam, eta, rhs, rtol=1e-13)
+    assert stats["relres_elas"] <= 1e-10
+    assert rel_l2(got, ref) <= 1e-7
