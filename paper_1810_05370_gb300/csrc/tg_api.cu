@@ -140,8 +140,8 @@ void spec_shape(const Geo& G, Spec<R>& V) {
   V.nt_z = std::max(64, std::min(NT, (items + 31) / 32 * 32));
 }
 
-// partial sums: one per x-pass block (the larger count of the FP32 and FP64 shapes), and the
-// 1024 x 3 of the mean reduction
+// partial sums: one per z-pass block (the <r, z> reduction) and the 1024 x 3 of the mean
+// reduction, for the larger of the FP32 and FP64 shapes (the x-pass count is kept as a floor)
 int spec_partial_count(const Geo& G) {
   Spec<float> a;
   Spec<double> b;
@@ -149,7 +149,10 @@ int spec_partial_count(const Geo& G) {
   spec_shape(G, b);
   const long long na = 3LL * G.nz * (G.ny / (2 * a.pb));
   const long long nb = 3LL * G.nz * (G.ny / (2 * b.pb));
-  return (int)std::max<long long>(std::max(na, nb), 3 * 1024);
+  // the z pass reduces <r, z>: one partial per block
+  const long long za = (long long)((a.nxh + a.tz - 1) / a.tz) * G.ny;
+  const long long zb = (long long)((b.nxh + b.tz - 1) / b.tz) * G.ny;
+  return (int)std::max<long long>(std::max(std::max(na, nb), std::max(za, zb)), 3 * 1024);
 }
 
 size_t spec_table_bytes(const Geo& G, size_t real_bytes) {

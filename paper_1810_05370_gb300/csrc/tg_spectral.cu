@@ -18,10 +18,11 @@
 //              is split off the line's transform and written to W;
 //   y forward  columns of W, in place;
 //   z          columns of all three components together: forward transform, the 3x3
-//              inverse per mode (with the 1/V normalisation), inverse transform, in place;
+//              inverse per mode (with the 1/V normalisation) and <r, z> by Parseval's
+//              identity (a sum of non-negative terms r^* M^{-1} r^), inverse transform, in place;
 //   y inverse  in place;
 //   x inverse  the Hermitian half spectra of two rows form one complex line whose inverse
-//              transform carries both real rows; writes z and reduces <r, z>.
+//              transform carries both real rows; writes z.
 // The 1-D transforms are Stockham autosort FFTs whose butterflies are radix-16 DFTs held in
 // registers (one radix-2, 4 or 8 stage takes the remainder of log2 n), ping-ponging between
 // two shared-memory buffers with one barrier per stage; each block keeps its line length's
@@ -366,6 +367,42 @@ __device__ __forceinline__ bool spec_skip(const CgScal* S) {
   return S != nullptr && S->status != CG_RUNNING;
 }
 
+// Sum of one value per thread over a launch of any block size (a multiple of 32): warps,
+// then the block's warps in order into partial[b]; the last block to finish sums the
+// partials (each thread a fixed stride, then its warps in order: deterministic) and returns
+// true in thread 0 with the total.
+__device__ bool block_sum_last(double v, double* partial, unsigned int* counter, int b, int nb,
+                               double& total) {
+  __shared__ double sh[32];
+  __shared__ bool am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sh[w];
+    partial[b] = s;
+    __threadfence();
+    am_last = atomicAdd(counter, 1u) == (unsigned int)(nb - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double s = 0.0;   // every thread a fixed stride of the partials, then warps in order
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) s += __ldcg(partial + k);
+  s = warp_sum(s);
+  __syncthreads();
+  if (lane == 0) sh[warp] = s;
+  __syncthreads();
+  if (threadIdx.x != 0) return false;
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += sh[w];
+  total = t;
+  *counter = 0u;
+  return true;
+}
+
 // ---------------------------------------------------------------------------- x forward
 // block (pair tile, z, component): rows y0 .. y0 + 2 pb - 1 of plane z
 template <typename R>
@@ -435,7 +472,7 @@ __global__ void __launch_bounds__(NT) k_spec_y(Spec<R> V, const CgScal* S) {
 // block (mode-column tile, ky): the three components' z columns; forward transform, the
 // constant-coefficient inverse per mode, inverse transform; in place
 template <typename R>
-__global__ void __launch_bounds__(NT) k_spec_z(Spec<R> V, const CgScal* S) {
+__global__ void __launch_bounds__(NT) k_spec_z(Spec<R> V, CgScal* S) {
   using C = typename CxOf<R>::T;
   if (spec_skip<R>(S)) return;
   const int tz = V.tz, ltz = ilog2(tz), lw = 3 * tz;   // lines: (component, column)
@@ -453,6 +490,9 @@ __global__ void __launch_bounds__(NT) k_spec_z(Spec<R> V, const CgScal* S) {
   const R c = lam0 + mu0;
   const R inv_vol = (R)(1.0 / ((double)V.nx * V.ny * V.nz));
   const R Sy = V.S[1][ky], Ty = V.T[1][ky];
+  // <r, z> by Parseval: sum over modes of conj(r^) z^ (z^ already carries 1/V), each stored
+  // mode with 0 < kx < nx/2 standing for its conjugate as well; every term is >= 0
+  R rz_part = (R)0;
   for (int idx = threadIdx.x; idx < tz * V.nz; idx += blockDim.x) {
     const int kz = idx >> ltz, col = idx & (tz - 1);
     if (col >= ncol) continue;
@@ -475,15 +515,23 @@ __global__ void __launch_bounds__(NT) k_spec_z(Spec<R> V, const CgScal* S) {
       s.y += Tv[q] * y[q].y;
     }
     const R f = c / ((R)1 + c * tdt);
+    const R wgt = (kx == 0 || kx == V.nx / 2) ? (R)1 : (R)2;   // conjugate modes not stored
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const R g = f * Tv[q] * dinv[q];
-      F[(size_t)kz * lw + q * tz + col] =
-          C{(y[q].x - g * s.x) * inv_vol, (y[q].y - g * s.y) * inv_vol};
+      const C rq = F[(size_t)kz * lw + q * tz + col];
+      const C zq = C{(y[q].x - g * s.x) * inv_vol, (y[q].y - g * s.y) * inv_vol};
+      rz_part += wgt * (rq.x * zq.x + rq.y * zq.y);
+      F[(size_t)kz * lw + q * tz + col] = zq;
     }
   }
   __syncthreads();
   fft_to_global<+1>(F, other, io, 1, lw, ilog2(V.nz), ltz, 3, tw);
+  if (S == nullptr) return;
+  double out;
+  if (block_sum_last((double)rz_part, V.partial, V.counter, blockIdx.y * gridDim.x + blockIdx.x,
+                     gridDim.x * gridDim.y, out))
+    cg_after_precond(*S, out);
 }
 
 // ---------------------------------------------------------------------------- x inverse
@@ -491,10 +539,8 @@ __global__ void __launch_bounds__(NT) k_spec_z(Spec<R> V, const CgScal* S) {
 // C[k] = A[k] + i B[k] over all k (Hermitian extension); the inverse transform is
 // a + i b.  Writes z and accumulates <r, z>; the last block finishes the CG scalars.
 template <typename R>
-__global__ void __launch_bounds__(NT) k_spec_x_inv(Spec<R> V, const R* __restrict__ r0,
-                                                   const R* __restrict__ r1,
-                                                   const R* __restrict__ r2, R* z0, R* z1,
-                                                   R* z2, CgScal* S) {
+__global__ void __launch_bounds__(NT) k_spec_x_inv(Spec<R> V, R* z0, R* z1, R* z2,
+                                                   const CgScal* S) {
   using C = typename CxOf<R>::T;
   if (spec_skip<R>(S)) return;
   const int n = V.nx, ln = ilog2(n), half = n / 2, pb = V.pb, es = pb + 1;
@@ -536,42 +582,15 @@ __global__ void __launch_bounds__(NT) k_spec_x_inv(Spec<R> V, const R* __restric
   }
   __syncthreads();
   const C* F = fft_lines<+1>(a, b, ln, ilog2(pb), 1, 1, es, tw);
-  const R* rs = comp == 0 ? r0 : (comp == 1 ? r1 : r2);
   R* zs = comp == 0 ? z0 : (comp == 1 ? z1 : z2);
   const size_t row0 = ((size_t)z * V.ny + y0) * n;
-  double acc[1] = {0.0};
-  R part = (R)0;
-  for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {
-    R ra[LB], rb[LB];
-#pragma unroll
-    for (int u = 0; u < LB; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      if (idx < total) {
-        const size_t o = row0 + (size_t)(2 * (idx >> ln)) * n + (idx & (n - 1));
-        ra[u] = __ldg(rs + o);
-        rb[u] = __ldg(rs + o + n);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < LB; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      if (idx < total) {
-        const int l = idx >> ln, x = idx & (n - 1);
-        const size_t o = row0 + (size_t)(2 * l) * n + x;
-        const C f = F[x * es + l];
-        zs[o] = f.x;
-        zs[o + n] = f.y;
-        part += ra[u] * f.x + rb[u] * f.y;
-      }
-    }
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int l = idx >> ln, x = idx & (n - 1);
+    const size_t o = row0 + (size_t)(2 * l) * n + x;
+    const C f = F[x * es + l];
+    zs[o] = f.x;
+    zs[o + n] = f.y;
   }
-  acc[0] = (double)part;
-  if (S == nullptr) return;
-  const int nb = gridDim.x * gridDim.y * gridDim.z;
-  const int bl = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  double out[1];
-  if (reduce_indexed<1>(acc, V.partial, V.counter, bl, nb, out) && threadIdx.x == 0)
-    cg_after_precond(*S, out[0]);
 }
 
 // ---------------------------------------------------------------------------- tables, means
@@ -660,7 +679,7 @@ cudaError_t launch_spectral(const Spec<R>& V, const R* const r[3], R* const z[3]
   k_spec_y<R, -1><<<gy, NT, spec_smem_y(V), st>>>(V, S);
   k_spec_z<R><<<gz, V.nt_z, spec_smem_z(V), st>>>(V, S);
   k_spec_y<R, +1><<<gy, NT, spec_smem_y(V), st>>>(V, S);
-  k_spec_x_inv<R><<<gx, NT, spec_smem_x(V), st>>>(V, r[0], r[1], r[2], z[0], z[1], z[2], S);
+  k_spec_x_inv<R><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S);
   return cudaGetLastError();
 }
 
