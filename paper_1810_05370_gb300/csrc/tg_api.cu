@@ -666,7 +666,7 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
     int recorded = 0;
     const int slot = sweeps == 0 ? 0 : 1;
     tg_status s = drive_cg(X, [&](int q) {
-      X->launches += spec ? 7 : 2;
+      X->launches += spec ? 6 : 2;
       const bool timed = X->timing && ensure_events(X, q + 1);
       if (timed) {
         cudaEventRecord(X->ev[2 * q], X->stream);
@@ -677,9 +677,7 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
       if (timed) cudaEventRecord(X->ev[2 * q + 1], X->stream);
       if (e != cudaSuccess) return e;
       if (!spec) return launch_elas32_update(X->G, I, X->stream);
-      e = launch_elas32_update_spec(X->G, I, X->stream);
-      if (e != cudaSuccess) return e;
-      return launch_spectral(X->sp32, r32, X->z32, I.S, X->stream);
+      return launch_spectral_update(X->sp32, I, X->z32, X->stream);
     }, I.S, 1, X->prm.maxit_elas, X->prev_it_inner[slot], host);
     if (s != TG_OK) return s;
     harvest_timing(X, recorded, host[0].it);

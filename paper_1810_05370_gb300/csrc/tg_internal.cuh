@@ -528,6 +528,8 @@ template <typename R>
 cudaError_t launch_spectral(const Spec<R>&, const R* const r[3], R* const z[3], CgScal* S,
                             cudaStream_t st);
 cudaError_t launch_elas32_matvec_spec(const Geo&, const Elas32&, cudaStream_t st);
+cudaError_t launch_spectral_update(const Spec<float>&, const Elas32&, float* const z[3],
+                                   cudaStream_t st);
 cudaError_t launch_elas32_scale_r(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_elas32_update_spec(const Geo&, const Elas32&, cudaStream_t st);
 

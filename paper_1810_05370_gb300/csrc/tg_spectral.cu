@@ -404,31 +404,69 @@ __device__ bool block_sum_last(double v, double* partial, unsigned int* counter,
 }
 
 // ---------------------------------------------------------------------------- x forward
-// block (pair tile, z, component): rows y0 .. y0 + 2 pb - 1 of plane z
+// block (pair tile, z, component): rows y0 .. y0 + 2 pb - 1 of plane z.  The staged lines
+// are interleaved, element e of line l at e * es + l; es = pb + 1 keeps the row-wise staging
+// accesses (consecutive e) free of bank conflicts.
+template <typename R>
+struct XTile {
+  using C = typename CxOf<R>::T;
+  int n, ln, pb, es, comp, z, y0;
+  size_t row0;   // first voxel of the block's rows in a component array
+};
+
+template <typename R>
+__device__ __forceinline__ XTile<R> x_tile(const Spec<R>& V) {
+  XTile<R> t;
+  t.n = V.nx;
+  t.ln = ilog2(V.nx);
+  t.pb = V.pb;
+  t.es = V.pb + 1;
+  t.comp = blockIdx.z;
+  t.z = blockIdx.y;
+  t.y0 = 2 * V.pb * blockIdx.x;
+  t.row0 = ((size_t)t.z * V.ny + t.y0) * V.nx;
+  return t;
+}
+
+// transform the staged rows (in a) and write both half spectra to W
+template <typename R>
+__device__ __forceinline__ void x_fwd_finish(const Spec<R>& V, const XTile<R>& t,
+                                             typename CxOf<R>::T* a, typename CxOf<R>::T* b,
+                                             const typename CxOf<R>::T* tw) {
+  using C = typename CxOf<R>::T;
+  const int n = t.n, es = t.es;
+  const C* F = fft_lines<-1>(a, b, t.ln, ilog2(t.pb), 1, 1, es, tw);
+  C* W = V.W + (((size_t)t.comp * V.nz + t.z) * V.ny + t.y0) * V.nxp;
+  for (int idx = threadIdx.x; idx < t.pb * V.nxh; idx += blockDim.x) {
+    const int l = idx / V.nxh, k = idx - l * V.nxh;
+    const C f = F[k * es + l], g = F[((n - k) & (n - 1)) * es + l];
+    // row 2l: (f + conj g) / 2;  row 2l+1: (f - conj g) / (2i)
+    W[(size_t)(2 * l) * V.nxp + k] = C{(R)0.5 * (f.x + g.x), (R)0.5 * (f.y - g.y)};
+    W[(size_t)(2 * l + 1) * V.nxp + k] = C{(R)0.5 * (f.y + g.y), (R)-0.5 * (f.x - g.x)};
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(NT) k_spec_x_fwd(Spec<R> V, const R* __restrict__ r0,
                                                    const R* __restrict__ r1,
                                                    const R* __restrict__ r2, const CgScal* S) {
   using C = typename CxOf<R>::T;
   if (spec_skip<R>(S)) return;
-  // lines interleaved, element e of line l at e * es + l; es = pb + 1 keeps the row-wise
-  // staging accesses (consecutive e) free of bank conflicts
-  const int n = V.nx, ln = ilog2(n), pb = V.pb, es = pb + 1;
+  const XTile<R> t = x_tile(V);
+  const int n = t.n, ln = t.ln, es = t.es;
   C* tw = smem_cx<C>();
   C* a = tw + n;
   C* b = a + (size_t)es * n;
   load_roots(tw, V.tw[0], n);
-  const int comp = blockIdx.z, z = blockIdx.y, y0 = 2 * pb * blockIdx.x;
-  const R* src = comp == 0 ? r0 : (comp == 1 ? r1 : r2);
-  const size_t row0 = ((size_t)z * V.ny + y0) * n;
-  const int total = pb * n;
+  const R* src = t.comp == 0 ? r0 : (t.comp == 1 ? r1 : r2);
+  const int total = t.pb * n;
   for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {
     R va[LB], vb[LB];
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
       const int idx = i0 + u * blockDim.x;
       if (idx < total) {
-        const size_t o = row0 + (size_t)(2 * (idx >> ln)) * n + (idx & (n - 1));
+        const size_t o = t.row0 + (size_t)(2 * (idx >> ln)) * n + (idx & (n - 1));
         va[u] = __ldg(src + o);
         vb[u] = __ldg(src + o + n);
       }
@@ -440,15 +478,71 @@ __global__ void __launch_bounds__(NT) k_spec_x_fwd(Spec<R> V, const R* __restric
     }
   }
   __syncthreads();
-  const C* F = fft_lines<-1>(a, b, ln, ilog2(pb), 1, 1, es, tw);
-  C* W = V.W + (((size_t)comp * V.nz + z) * V.ny + y0) * V.nxp;
-  for (int idx = threadIdx.x; idx < pb * V.nxh; idx += blockDim.x) {
-    const int l = idx / V.nxh, k = idx - l * V.nxh;
-    const C f = F[k * es + l], g = F[((n - k) & (n - 1)) * es + l];
-    // row 2l: (f + conj g) / 2;  row 2l+1: (f - conj g) / (2i)
-    W[(size_t)(2 * l) * V.nxp + k] = C{(R)0.5 * (f.x + g.x), (R)0.5 * (f.y - g.y)};
-    W[(size_t)(2 * l + 1) * V.nxp + k] = C{(R)0.5 * (f.y + g.y), (R)-0.5 * (f.x - g.x)};
+  x_fwd_finish(V, t, a, b, tw);
+}
+
+// The mixed precision's CG update fused into the x forward pass: for the block's rows
+// e += alpha p, r -= alpha q (p as written by this iteration's operator kernel), the new r
+// staged straight into the transform, and <r, r> reduced over the launch; the last block
+// takes the convergence decision.  Saves the pass that re-read r.
+__global__ void __launch_bounds__(NT) k_spec_update_xfwd(Spec<float> V, Elas32 I) {
+  using C = float2;
+  if (!running(I.S)) return;
+  const float alpha = (float)I.S->alpha;
+  const int pbuf = (I.S->it & 1) ^ 1;
+  const XTile<float> t = x_tile(V);
+  const int n = t.n, ln = t.ln, es = t.es;
+  C* tw = smem_cx<C>();
+  C* a = tw + n;
+  C* b = a + (size_t)es * n;
+  load_roots(tw, V.tw[0], n);
+  float* e = I.e[t.comp];
+  float* r = I.r[t.comp];
+  const float* p = I.p[pbuf][t.comp];
+  const float* q = I.q[t.comp];
+  constexpr int UB = 4;
+  float rr = 0.0f;
+  const int total = t.pb * n;
+  for (int i0 = threadIdx.x; i0 < total; i0 += UB * blockDim.x) {
+    float ea[UB], eb[UB], ra[UB], rb[UB], pa[UB], pbv[UB], qa[UB], qb[UB];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) {
+        const size_t o = t.row0 + (size_t)(2 * (idx >> ln)) * n + (idx & (n - 1));
+        ea[u] = e[o];
+        eb[u] = e[o + n];
+        ra[u] = r[o];
+        rb[u] = r[o + n];
+        pa[u] = p[o];
+        pbv[u] = p[o + n];
+        qa[u] = q[o];
+        qb[u] = q[o + n];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) {
+        const size_t o = t.row0 + (size_t)(2 * (idx >> ln)) * n + (idx & (n - 1));
+        const float xa = ra[u] - alpha * qa[u], xb = rb[u] - alpha * qb[u];
+        e[o] = ea[u] + alpha * pa[u];
+        e[o + n] = eb[u] + alpha * pbv[u];
+        r[o] = xa;
+        r[o + n] = xb;
+        rr += xa * xa + xb * xb;
+        a[(idx & (n - 1)) * es + (idx >> ln)] = C{xa, xb};
+      }
+    }
   }
+  double acc[1] = {(double)rr};
+  double out[1];
+  const int nb = gridDim.x * gridDim.y * gridDim.z;
+  const int bl = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  if (reduce_indexed<1>(acc, V.partial, V.counter, bl, nb, out) && threadIdx.x == 0)
+    cg_after_update_rr(*I.S, out[0]);   // reduce_indexed's barriers also publish the staging
+  __syncthreads();
+  x_fwd_finish(V, t, a, b, tw);
 }
 
 // ---------------------------------------------------------------------------- y pass
@@ -646,6 +740,7 @@ cudaError_t spec_prepare(const Spec<R>& V) {
     return cudaErrorInvalidValue;
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   e = cudaFuncSetAttribute(k_spec_x_fwd<R>, A, optin);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_update_xfwd, A, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_x_inv<R>, A, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_y<R, -1>, A, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_y<R, +1>, A, optin);
@@ -680,6 +775,21 @@ cudaError_t launch_spectral(const Spec<R>& V, const R* const r[3], R* const z[3]
   k_spec_z<R><<<gz, V.nt_z, spec_smem_z(V), st>>>(V, S);
   k_spec_y<R, +1><<<gy, NT, spec_smem_y(V), st>>>(V, S);
   k_spec_x_inv<R><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S);
+  return cudaGetLastError();
+}
+
+// one preconditioned CG iteration's update and preconditioner (mixed precision): the fused
+// update + x forward pass, then the remaining four passes
+cudaError_t launch_spectral_update(const Spec<float>& V, const Elas32& I, float* const z[3],
+                                   cudaStream_t st) {
+  const dim3 gx(V.ny / (2 * V.pb), V.nz, 3);
+  const dim3 gy((V.nxh + V.tx - 1) / V.tx, V.nz, 3);
+  const dim3 gz((V.nxh + V.tz - 1) / V.tz, V.ny);
+  k_spec_update_xfwd<<<gx, NT, spec_smem_x(V), st>>>(V, I);
+  k_spec_y<float, -1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S);
+  k_spec_z<float><<<gz, V.nt_z, spec_smem_z(V), st>>>(V, I.S);
+  k_spec_y<float, +1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S);
+  k_spec_x_inv<float><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], I.S);
   return cudaGetLastError();
 }
 
