@@ -635,7 +635,12 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
   const Elas32 I = elas32_view(X);
   CgScal* Sout = X->scal + 3;
   const size_t bytes = (size_t)X->G.nvox * sizeof(double);
-  for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(E.du[d], 0, bytes, X->stream));
+  if (inv_dt > 0.0) {   // a step's solve: start from the extrapolated u^n + dt v^n
+    CK(launch_elas_extrapolate(X->G, E, 1.0 / inv_dt, X->stream));
+    X->launches += 1;
+  } else {
+    for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(E.du[d], 0, bytes, X->stream));
+  }
   k_cg_reset<<<1, 32, 0, X->stream>>>(Sout, 1, X->prm.rtol_elas, X->prm.maxit_elas);
   CK(cudaGetLastError());
   CK(launch_elas32_coef(X->G, E, I, X->stream));

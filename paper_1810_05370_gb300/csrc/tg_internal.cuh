@@ -511,6 +511,7 @@ cudaError_t launch_elas_ir_residual(const Geo&, const Elas&, const Elas32&, CgSc
 cudaError_t launch_elas32_matvec(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_elas32_update(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_elas_ir_correct(const Geo&, const Elas&, const Elas32&, cudaStream_t st);
+cudaError_t launch_elas_extrapolate(const Geo&, const Elas&, double dt, cudaStream_t st);
 cudaError_t launch_elas_ir_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
                                   cudaStream_t st);
 cudaError_t launch_sl32(const Geo&, double dt, const Sl32&, cudaStream_t st);

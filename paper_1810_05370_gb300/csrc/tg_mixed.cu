@@ -158,6 +158,20 @@ __global__ void __launch_bounds__(NT) k_elas_ir_correct(long long n, Elas E, Ela
                         1.0 / I.S->scale);
 }
 
+// Starting guess of a step's solve, linear extrapolation in time: u = u^n + dt v^n
+// (= 2 u^n - u^{n-1}), du = dt v^n so that v^{n+1} = du / dt still measures u^{n+1} - u^n
+__global__ void __launch_bounds__(NT) k_elas_extrapolate(long long n, Elas E, double dt) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double d = dt * E.v[a][c];
+      E.u[a][c] += d;
+      E.du[a][c] = d;
+    }
+  }
+}
+
 // v = du / dt; a vanishing right-hand side means u = 0
 __global__ void __launch_bounds__(NT) k_elas_ir_finish(long long n, Elas E, double inv_dt,
                                                        int zero_rhs) {
@@ -323,6 +337,11 @@ cudaError_t launch_elas32_update_spec(const Geo& G, const Elas32& I, cudaStream_
 
 cudaError_t launch_elas_ir_correct(const Geo& G, const Elas& E, const Elas32& I, cudaStream_t st) {
   k_elas_ir_correct<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elas_extrapolate(const Geo& G, const Elas& E, double dt, cudaStream_t st) {
+  k_elas_extrapolate<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, dt);
   return cudaGetLastError();
 }
 
