@@ -14,8 +14,9 @@
  *   S3  reaction of p, i, n, g, w (Eq. e:p - e:w: logistic growth, go-or-grow switching,
  *       hypoxic death);  S4 oxygen reaction (Eq. e:ox);  S5 edema reaction (Eq. e:edema);
  *   S6  screened elasticity (eta I - L_h) u = -b (Eq. e:screening with Eq. e:lame and
- *       e:forcingfunction), CG preconditioned by Jacobi or (Section 3) by the exact inverse
- *       of the constant-coefficient operator with the domain means of mu, lambda, eta;
+ *       e:forcingfunction), CG from the extrapolated u^n + dt v^n, preconditioned by Jacobi
+ *       or (Section 3) by the exact inverse of the constant-coefficient operator with the
+ *       domain means of mu, lambda, eta;
  *   S7  v = (u^{n+1} - u^n) / dt.
  * Spatial operators are second-order finite differences on a periodic box (7-point
  * variable-coefficient diffusion, 19-point variable-coefficient Navier-Lame); the paper's

@@ -834,7 +834,8 @@ int or_init(const or_grid* G, const or_params* P, or_state* S, or_stats* stats) 
  *  S1  semi-Lagrangian advection of p, i, n, g, w (conservative) and f with v^n;
  *  S2  Crank-Nicolson diffusion of i, o and edema l; the increment of i leaves g and w;
  *  S3  reaction of p, i, n, g, w;  S4 oxygen reaction;  S5 edema reaction;
- *  S6  elasticity solve for u^{n+1};  S7 v^{n+1} = (u^{n+1} - u^n) / dt. */
+ *  S6  elasticity solve for u^{n+1}, started from u^n + dt v^n;
+ *  S7  v^{n+1} = (u^{n+1} - u^n) / dt. */
 int or_step(const or_grid* G, const or_params* P, double dt, or_state* S, or_stats* stats) {
   if (!valid_grid(G) || !(dt > 0.0)) return OR_ERR_ARG;
   int64_t m = nvox(G);
@@ -884,6 +885,9 @@ int or_step(const or_grid* G, const or_params* P, double dt, or_state* S, or_sta
     /* S6 - S7 */
     real_t* u_old[3] = {qout[1], qout[2], qout[3]};
     for (int a = 0; a < 3; ++a) memcpy(u_old[a], S->u[a], (size_t)m * sizeof(real_t));
+    /* the solve starts from the linear extrapolation u^n + dt v^n (= 2 u^n - u^{n-1}) */
+    for (int a = 0; a < 3; ++a)
+      for (int64_t e = 0; e < m; ++e) S->u[a][e] = S->u[a][e] + dt * S->v[a][e];
     st = elasticity_substep(G, P, S, &local.it_elas, &local.relres_elas);
     for (int a = 0; a < 3; ++a)
       for (int64_t e = 0; e < m; ++e) S->v[a][e] = (S->u[a][e] - u_old[a][e]) / dt;

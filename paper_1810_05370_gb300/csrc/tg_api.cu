@@ -716,6 +716,10 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
   k_cg_reset<<<1, 32, 0, X->stream>>>(X->scal + 3, 1, X->prm.rtol_elas, X->prm.maxit_elas);
   CK(cudaGetLastError());
   const double* const r64[3] = {E.r[0], E.r[1], E.r[2]};
+  if (inv_dt > 0.0) {   // a step's solve: start from the extrapolated u^n + dt v^n
+    CK(launch_elas_extrapolate(X->G, E, 1.0 / inv_dt, X->stream));
+    X->launches += 1;
+  }
   if (spec) {
     CK(launch_spec_mean(X->G.nvox, E.mu, E.lam, E.eta, X->sp64.mean, X->sp64.partial,
                         X->sp64.counter, X->stream));
@@ -757,7 +761,8 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
   }
   tg_status e = status_of(host[0]);
   if (e != TG_OK) return fail(X, e);
-  CK(launch_elas_finish(X->G, E, inv_dt, host[0].status == CG_ZERO_RHS, X->stream));
+  CK(launch_elas_finish(X->G, E, inv_dt, host[0].status == CG_ZERO_RHS, inv_dt > 0.0,
+                        X->stream));
   X->launches += 1;
   CK(cudaStreamSynchronize(X->stream));
   return TG_OK;
@@ -1538,7 +1543,6 @@ tg_status queue_post_diffusion(tg_ctx* X, double dt) {
   const Geo& G = X->G;
   tg_state& S = X->st;
   cudaStream_t s = X->stream;
-  const size_t bytes = (size_t)G.nvox * sizeof(double);
   CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l,
                   X->prec == TG_MIXED, single_species(X), s));
   tg_status e = build_elas_coef(X, true);
@@ -1546,7 +1550,7 @@ tg_status queue_post_diffusion(tg_ctx* X, double dt) {
   double* const u[3] = {S.u[0], S.u[1], S.u[2]};
   const Elas E = elas_view(X, u, nullptr);
   CK(launch_elas32_coef(G, E, elas32_view(X), s));
-  for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(X->a[A_DU0 + d], 0, bytes, s));
+  CK(launch_elas_extrapolate(G, E, dt, s));   // u^n + dt v^n; du = dt v^n
   return TG_OK;
 }
 

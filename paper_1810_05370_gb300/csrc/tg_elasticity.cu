@@ -204,8 +204,10 @@ __global__ void __launch_bounds__(NT) k_elas_pupdate_spec(Geo G, Elas E) {
   }
 }
 
-// u += du (du = -u when the right-hand side vanished, i.e. u = 0), v = du / dt
-__global__ void __launch_bounds__(NT) k_elas_finish(Geo G, Elas E, double inv_dt, int zero_rhs) {
+// u += du (du = -u when the right-hand side vanished, i.e. u = 0), v = vo + du / dt with
+// vo = v^n when the solve started from the extrapolated u^n + dt v^n (extrap), else 0
+__global__ void __launch_bounds__(NT) k_elas_finish(Geo G, Elas E, double inv_dt, int zero_rhs,
+                                                    int extrap) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= G.nx || j >= G.ny) return;
@@ -217,7 +219,10 @@ __global__ void __launch_bounds__(NT) k_elas_finish(Geo G, Elas E, double inv_dt
       const double uo = E.u[a][c];
       const double du = zero_rhs ? -uo : E.du[a][c];
       E.u[a][c] = zero_rhs ? 0.0 : uo + du;
-      if (inv_dt > 0.0) E.v[a][c] = du * inv_dt;
+      if (inv_dt > 0.0) {
+        const double vo = extrap ? E.v[a][c] : 0.0;
+        E.v[a][c] = vo + du * inv_dt;
+      }
     }
   }
 }
@@ -262,8 +267,9 @@ cudaError_t launch_elas_pupdate_spec(const Geo& G, const Elas& E, cudaStream_t s
 }
 
 cudaError_t launch_elas_finish(const Geo& G, const Elas& E, double inv_dt, bool zero_rhs,
-                               cudaStream_t st) {
-  k_elas_finish<<<G.grid, dim3(BX, BY), 0, st>>>(G, E, inv_dt, zero_rhs ? 1 : 0);
+                               bool extrap, cudaStream_t st) {
+  k_elas_finish<<<G.grid, dim3(BX, BY), 0, st>>>(G, E, inv_dt, zero_rhs ? 1 : 0,
+                                                 extrap ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -499,7 +499,7 @@ cudaError_t launch_elas_init_spec(const Geo&, const Elas&, bool rhs_is_minus_b, 
 cudaError_t launch_elas_update_spec(const Geo&, const Elas&, cudaStream_t st);
 cudaError_t launch_elas_pupdate_spec(const Geo&, const Elas&, cudaStream_t st);
 cudaError_t launch_elas_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
-                               cudaStream_t st);
+                               bool extrap, cudaStream_t st);
 
 // mixed precision (tg_mixed.cu)
 cudaError_t launch_to_f32(long long n, const F32Copy& c, cudaStream_t st);

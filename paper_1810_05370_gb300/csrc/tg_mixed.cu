@@ -165,8 +165,8 @@ __global__ void __launch_bounds__(NT) k_elas_extrapolate(long long n, Elas E, do
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double d = dt * E.v[a][c];
-      E.u[a][c] += d;
+      const double d = __dmul_rn(dt, E.v[a][c]);   // rounded as u + dt v is, no contraction
+      E.u[a][c] = __dadd_rn(E.u[a][c], d);
       E.du[a][c] = d;
     }
   }
