@@ -1376,7 +1376,7 @@ const char* tg_error_string(tg_status s) {
 // device with cudaGetSymbolAddress and cached.
 namespace {
 
-__device__ __align__(256) unsigned char g_static_scratch[TG_STATIC_SCRATCH_BYTES];
+static __device__ __align__(256) unsigned char g_static_scratch[TG_STATIC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mutex;
