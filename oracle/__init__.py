@@ -252,6 +252,17 @@ class Oracle:
                                         r3.ctypes.data_as(dp), z3.ctypes.data_as(dp))
         return z3
 
+    def elasticity_scaled_spectral(self, n, mu, lam, eta, r3, L=None):
+        """z = s * A0^{-1} (s * r) with s = (D0 / D)^{1/2} (preconditioner 2; real build)."""
+        r3 = np.ascontiguousarray(np.real(r3), dtype=np.float64)
+        z3 = np.zeros_like(r3)
+        dp = C.POINTER(C.c_double)
+        arrs = [np.ascontiguousarray(np.real(a), dtype=np.float64) for a in (mu, lam, eta)]
+        self.lib.or_elasticity_scaled_spectral(C.byref(self.grid(n, L)),
+                                               *[a.ctypes.data_as(dp) for a in arrs],
+                                               r3.ctypes.data_as(dp), z3.ctypes.data_as(dp))
+        return z3
+
     def interp(self, n, q, X, Y, Z, L=None):
         self.lib.or_interp.restype = self.R
         arg = (lambda v: self._r(v)) if self.cs else (lambda v: C.c_double(float(np.real(v))))

@@ -506,28 +506,11 @@ static void spectral_prec(const void* vctx, int64_t m3, const real_t* r, real_t*
   free(b);
 }
 
-/* (eta I - L_h) u = rhs by PCG from the given u (Section 3, elasticity sub-step);
- * precond 0: Jacobi, 1: the constant-coefficient spectral inverse with the domain means of
- * mu, lambda, eta (real parts in complex-step mode) */
-int or_elasticity_solve(const or_grid* G, const real_t* mu, const real_t* lam, const real_t* eta,
-                        const real_t* rhs3, real_t* u3, double rtol, int32_t maxit,
-                        int32_t precond, int32_t* iters, double* relres) {
+/* Diagonal of A = eta I - L_h for component a at every node: eta plus the two faces of the
+ * second difference in each direction (the centred mixed terms do not touch the diagonal). */
+static void elas_diag(const or_grid* G, const real_t* mu, const real_t* lam, const real_t* eta,
+                      real_t* diag3) {
   int64_t m = nvox(G);
-  el_ctx C = {G, mu, lam, eta};
-  if (precond == 1) {
-    sp_ctx S = {G, 0.0, 0.0, 0.0};
-    for (int64_t e = 0; e < m; ++e) {
-      S.mu0 += RE(mu[e]);
-      S.lam0 += RE(lam[e]);
-      S.eta0 += RE(eta[e]);
-    }
-    S.mu0 /= (double)m;
-    S.lam0 /= (double)m;
-    S.eta0 /= (double)m;
-    return pcg(3 * m, el_apply, &C, spectral_prec, &S, rhs3, u3, rtol, maxit, iters, relres);
-  }
-  if (precond != 0) return OR_ERR_ARG;
-  real_t* dinv = (real_t*)malloc((size_t)(3 * m) * sizeof(real_t));
   for (int a = 0; a < 3; ++a) {
     for (int64_t e = 0; e < m; ++e) {
       int64_t c[3];
@@ -538,9 +521,102 @@ int or_elasticity_solve(const or_grid* G, const real_t* mu, const real_t* lam, c
         double h = hd(G, d);
         diag += (elas_face(a, d, mu, lam, e, jp) + elas_face(a, d, mu, lam, jm, e)) / (h * h);
       }
-      dinv[a * m + e] = 1.0 / diag;
+      diag3[a * m + e] = diag;
     }
   }
+}
+
+/* Preconditioner 2 (this library's, not the paper's): the spectral inverse between two
+ * diagonal scalings, z = s * A0^{-1} (s * r) with s = (D0 / D)^{1/2} per component and node,
+ * D the diagonal of A and D0 that of A0 (D0_a = eta0 + sum_d 2 c_ad / h_d^2 with
+ * c_aa = lam0 + 2 mu0 and c_ad = mu0 otherwise).  It is symmetric positive definite, equals
+ * A0^{-1} where the coefficients are the means, and equals A^{-1} when A is diagonal
+ * (mu = lambda = 0).  Real parts of the coefficients in complex-step mode. */
+static void scaled_spectral_scale(const or_grid* G, const real_t* mu, const real_t* lam,
+                                  const real_t* eta, double mu0, double lam0, double eta0,
+                                  double* s3) {
+  int64_t m = nvox(G);
+  real_t* diag3 = (real_t*)malloc((size_t)(3 * m) * sizeof(real_t));
+  elas_diag(G, mu, lam, eta, diag3);
+  for (int a = 0; a < 3; ++a) {
+    double d0 = eta0;
+    for (int d = 0; d < 3; ++d) {
+      double h = hd(G, d);
+      d0 += 2.0 * (d == a ? lam0 + 2.0 * mu0 : mu0) / (h * h);
+    }
+    for (int64_t e = 0; e < m; ++e) s3[a * m + e] = sqrt(d0 / RE(diag3[a * m + e]));
+  }
+  free(diag3);
+}
+
+static void domain_means(int64_t m, const real_t* mu, const real_t* lam, const real_t* eta,
+                         double* mu0, double* lam0, double* eta0) {
+  *mu0 = *lam0 = *eta0 = 0.0;
+  for (int64_t e = 0; e < m; ++e) {
+    *mu0 += RE(mu[e]);
+    *lam0 += RE(lam[e]);
+    *eta0 += RE(eta[e]);
+  }
+  *mu0 /= (double)m;
+  *lam0 /= (double)m;
+  *eta0 /= (double)m;
+}
+
+#ifndef OR_COMPLEX
+/* z = s * A0^{-1} (s * r) for the given coefficients (the map preconditioner 2 applies) */
+void or_elasticity_scaled_spectral(const or_grid* G, const double* mu, const double* lam,
+                                   const double* eta, const double* r3, double* z3) {
+  int64_t m = nvox(G);
+  double mu0, lam0, eta0;
+  domain_means(m, mu, lam, eta, &mu0, &lam0, &eta0);
+  double* s3 = (double*)malloc((size_t)(3 * m) * sizeof(double));
+  double* a = (double*)malloc((size_t)(3 * m) * sizeof(double));
+  scaled_spectral_scale(G, mu, lam, eta, mu0, lam0, eta0, s3);
+  for (int64_t e = 0; e < 3 * m; ++e) a[e] = s3[e] * r3[e];
+  or_elasticity_spectral(G, mu0, lam0, eta0, a, z3);
+  for (int64_t e = 0; e < 3 * m; ++e) z3[e] = s3[e] * z3[e];
+  free(s3);
+  free(a);
+}
+#endif
+
+typedef struct { sp_ctx sp; const double* s3; } ssp_ctx;
+
+static void scaled_spectral_prec(const void* vctx, int64_t m3, const real_t* r, real_t* z) {
+  const ssp_ctx* C = (const ssp_ctx*)vctx;
+  real_t* t = (real_t*)malloc((size_t)m3 * sizeof(real_t));
+  for (int64_t e = 0; e < m3; ++e) t[e] = C->s3[e] * r[e];
+  spectral_prec(&C->sp, m3, t, z);
+  for (int64_t e = 0; e < m3; ++e) z[e] = C->s3[e] * z[e];
+  free(t);
+}
+
+/* (eta I - L_h) u = rhs by PCG from the given u (Section 3, elasticity sub-step);
+ * precond 0: Jacobi, 1: the constant-coefficient spectral inverse with the domain means of
+ * mu, lambda, eta (real parts in complex-step mode), 2: that inverse between the diagonal
+ * scalings above */
+int or_elasticity_solve(const or_grid* G, const real_t* mu, const real_t* lam, const real_t* eta,
+                        const real_t* rhs3, real_t* u3, double rtol, int32_t maxit,
+                        int32_t precond, int32_t* iters, double* relres) {
+  int64_t m = nvox(G);
+  el_ctx C = {G, mu, lam, eta};
+  if (precond == 1 || precond == 2) {
+    sp_ctx S = {G, 0.0, 0.0, 0.0};
+    domain_means(m, mu, lam, eta, &S.mu0, &S.lam0, &S.eta0);
+    if (precond == 1)
+      return pcg(3 * m, el_apply, &C, spectral_prec, &S, rhs3, u3, rtol, maxit, iters, relres);
+    double* s3 = (double*)malloc((size_t)(3 * m) * sizeof(double));
+    scaled_spectral_scale(G, mu, lam, eta, S.mu0, S.lam0, S.eta0, s3);
+    ssp_ctx SS = {S, s3};
+    int st = pcg(3 * m, el_apply, &C, scaled_spectral_prec, &SS, rhs3, u3, rtol, maxit, iters,
+                 relres);
+    free(s3);
+    return st;
+  }
+  if (precond != 0) return OR_ERR_ARG;
+  real_t* dinv = (real_t*)malloc((size_t)(3 * m) * sizeof(real_t));
+  elas_diag(G, mu, lam, eta, dinv);
+  for (int64_t e = 0; e < 3 * m; ++e) dinv[e] = 1.0 / dinv[e];
   int st = pcg(3 * m, el_apply, &C, jacobi_prec, dinv, rhs3, u3, rtol, maxit, iters, relres);
   free(dinv);
   return st;

@@ -83,6 +83,10 @@ int or_elasticity_solve(const or_grid*, const real_t* mu, const real_t* lam, con
 void or_dft3(const or_grid*, double* re, double* im, int sgn);
 void or_elasticity_spectral(const or_grid*, double mu0, double lam0, double eta0,
                             const double* r3, double* z3);
+/* Preconditioner 2: z = s * A0^{-1} (s * r), s = (D0 / D)^{1/2} (diagonals of A0 and A);
+ * real build only */
+void or_elasticity_scaled_spectral(const or_grid*, const double* mu, const double* lam,
+                                   const double* eta, const double* r3, double* z3);
 real_t or_interp(const or_grid*, const real_t* q, real_t X, real_t Y, real_t Z);
 void or_divergence(const or_grid*, const real_t* vx, const real_t* vy, const real_t* vz,
                    real_t* div);

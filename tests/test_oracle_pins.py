@@ -721,6 +721,69 @@ def test_spectral_pcg_matches_jacobi_on_brain(oracle):
     assert its < 0.6 * itj
 
 
+# ------------------------------------------------- diagonally scaled spectral preconditioner
+
+def test_scaled_spectral_equals_spectral_for_constant_coefficients(oracle):
+    """s = (D0 / D)^{1/2} is 1 when the coefficients equal their means: preconditioner 2 is then
+    preconditioner 1 (a wrong D0 -- a dropped face, lambda in place of lambda + 2 mu -- makes
+    s differ from 1 on a grid with unequal spacings)."""
+    n = (16, 8, 8)
+    L = (TWO_PI, 5.0, 3.0)
+    rng = np.random.default_rng(21)
+    r = rng.standard_normal((3, n[2], n[1], n[0]))
+    ones = np.ones(r.shape[1:])
+    z1 = oracle.elasticity_spectral(n, 1.7, 5.2, 0.8, r, L)
+    z2 = oracle.elasticity_scaled_spectral(n, 1.7 * ones, 5.2 * ones, 0.8 * ones, r, L)
+    assert np.abs(z2 - z1).max() <= 1e-13 * np.abs(z1).max()
+
+
+def test_scaled_spectral_inverts_a_diagonal_operator(oracle):
+    """mu = lambda = 0: A = diag(eta) and A0 = mean(eta) I, so s A0^{-1} s = diag(1 / eta)
+    exactly (an inverted ratio or a missing square root in s breaks it); PCG then converges in
+    one iteration."""
+    n = (8, 8, 8)
+    rng = np.random.default_rng(22)
+    eta = rng.uniform(0.5, 40.0, (8, 8, 8))
+    zeros = np.zeros_like(eta)
+    r = rng.standard_normal((3, 8, 8, 8))
+    z = oracle.elasticity_scaled_spectral(n, zeros, zeros, eta, r)
+    assert np.abs(z - r / eta).max() <= 1e-13 * np.abs(r / eta).max()
+    u, it, rr = oracle.elasticity_solve(n, zeros, zeros, eta, r, rtol=1e-12, precond=2)
+    assert it == 1 and rr <= 1e-12
+
+
+def test_scaled_spectral_symmetric_positive(oracle):
+    """Variable coefficients: <P x, y> = <x, P y> and <P x, x> > 0 (PCG needs an SPD map)."""
+    n = (8, 8, 8)
+    rng = np.random.default_rng(23)
+    mu = rng.uniform(0.5, 3.0, (8, 8, 8))
+    lam = rng.uniform(1.0, 20.0, (8, 8, 8))
+    eta = rng.uniform(0.1, 50.0, (8, 8, 8))
+    x = rng.standard_normal((3, 8, 8, 8))
+    y = rng.standard_normal((3, 8, 8, 8))
+    Px = oracle.elasticity_scaled_spectral(n, mu, lam, eta, x)
+    Py = oracle.elasticity_scaled_spectral(n, mu, lam, eta, y)
+    assert abs(np.sum(Px * y) - np.sum(x * Py)) <= 1e-13 * np.sqrt(np.sum(Px**2) * np.sum(y**2))
+    assert np.sum(Px * x) > 0
+
+
+def test_scaled_spectral_pcg_on_brain(oracle):
+    """Brain coefficients (eta spans 1e3 in tissue to 1e6 outside): the same solution as
+    Jacobi, in well under the plain spectral preconditioner's iterations (the domain-mean eta
+    is the background's, so A0 alone misjudges the tissue's diagonal by orders of magnitude)."""
+    n = 48
+    P = workload_params()
+    st = initial_state(n, 0)
+    mu, lam, eta = oracle.lame(n, P, st)
+    rhs = -np.stack(oracle.force(n, P, st["p"], st["n"]))
+    uj, itj, _ = oracle.elasticity_solve(n, mu, lam, eta, rhs, rtol=1e-10, precond=0)
+    u1, it1, _ = oracle.elasticity_solve(n, mu, lam, eta, rhs, rtol=1e-10, precond=1)
+    u2, it2, r2 = oracle.elasticity_solve(n, mu, lam, eta, rhs, rtol=1e-10, precond=2)
+    assert r2 <= 1e-10
+    assert np.abs(u2 - uj).max() <= 1e-7 * np.abs(uj).max()
+    assert it2 < 0.6 * it1, (itj, it1, it2)
+
+
 # ----------------------------------------------------------------- single-species model
 
 def test_single_species_reaction_logistic_third_order_and_mass(oracle):
