@@ -28,7 +28,7 @@ if ROOT not in sys.path:
 
 METRIC = "voxel-steps/s at 256^3 (mixed FP32 vs plain FP64, same GPU); adjoint/forward time"
 UNIT = "voxel-steps/s"
-PRECONDS = {"jacobi": 0, "spectral": 1}
+PRECONDS = {"jacobi": 0, "spectral": 1, "scaled": 2}
 FIELDS = ("p", "i", "n", "g", "w", "f", "o", "l", "bg", "ux", "uy", "uz", "vx", "vy", "vz")
 
 # Algorithmic traffic and arithmetic of the elasticity operator kernel, per voxel and launch.
@@ -39,7 +39,9 @@ FIELDS = ("p", "i", "n", "g", "w", "f", "o", "l", "bg", "ux", "uy", "uz", "vx", 
 # arrays; with the spectral preconditioner the preconditioned residual z (3) replaces r and
 # D^{-1} (6): 15 FP32 arrays.
 ELAS_MATVEC_BYTES_PER_VOXEL = {("fp64", "jacobi"): 17 * 8, ("fp64", "spectral"): 17 * 8,
-                               ("mixed", "jacobi"): 18 * 4, ("mixed", "spectral"): 15 * 4}
+                               ("fp64", "scaled"): 17 * 8,
+                               ("mixed", "jacobi"): 18 * 4, ("mixed", "spectral"): 15 * 4,
+                               ("mixed", "scaled"): 15 * 4}
 ELAS_MATVEC_FLOPS_PER_VOXEL = 123
 
 
@@ -51,8 +53,9 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--dt", type=float, default=0.01)
     ap.add_argument("--precision", choices=("fp64", "mixed"), default="mixed")
-    ap.add_argument("--precond", choices=("spectral", "jacobi"), default="spectral",
-                    help="elasticity preconditioner (Section 3 uses the spectral one)")
+    ap.add_argument("--precond", choices=("scaled", "spectral", "jacobi"), default="scaled",
+                    help="elasticity preconditioner: Section 3's spectral one, that one between "
+                         "diagonal scalings (scaled), or Jacobi")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other precision on the same GPU")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
@@ -144,14 +147,15 @@ def dist_setup(args):
     return world, rank, local
 
 
-def oracle_sample(n, steps, warm_steps=0):
-    """Time the CPU oracle (all host cores) on `steps` steps of an n^3 synthetic brain."""
+def oracle_sample(n, steps, warm_steps=0, precond=0):
+    """Time the CPU oracle (all host cores) on `steps` steps of an n^3 synthetic brain, with
+    the given elasticity preconditioner (the GPU line's)."""
     cores = len(os.sched_getaffinity(0))
     os.environ["OMP_NUM_THREADS"] = str(cores)
     from oracle import Oracle
     from synth import initial_state, workload_params
     O = Oracle()
-    P = workload_params()
+    P = workload_params(precond_elas=precond)
     st = initial_state(n, seed=0)
     O.init(n, P, st)
     for _ in range(warm_steps):
@@ -167,9 +171,11 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     n = args.cpu_sample_n
-    value, cores, secs = oracle_sample(n, args.steps, warm_steps=args.warmup)
+    value, cores, secs = oracle_sample(n, args.steps, warm_steps=args.warmup,
+                                       precond=PRECONDS[args.precond])
     sample = (f"CPU oracle, {n}^3 synthetic brain (same generator and parameters as the "
-              f"{args.n}^3 workload), {args.warmup} untimed + {args.steps} timed steps, "
+              f"{args.n}^3 workload, {args.precond} elasticity preconditioner), "
+              f"{args.warmup} untimed + {args.steps} timed steps, "
               f"{cores} OpenMP threads; elasticity CG iterations grow with N, so the "
               f"per-voxel rate at {args.n}^3 would be lower")
     out = {
@@ -178,7 +184,8 @@ def run_reference(args, world, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"{args.n}^3 synthetic brain, multispecies step, dt {args.dt}",
-                   "grid": args.n, "precision": args.precision},
+                   "grid": args.n, "precision": args.precision,
+                   "elasticity_preconditioner": args.precond},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -317,7 +324,7 @@ def main():
                     "peak_source": "derived FP64 roof (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                     "hbm_gbs": gbs, "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"],
                     "share_of_step": share}
-        kname = "k_elas32_matvec_spec" if args.precond == "spectral" else "k_elas32_matvec"
+        kname = "k_elas32_matvec" if args.precond == "jacobi" else "k_elas32_matvec_spec"
         return {"kernel": f"{kname} (FP32 19-point Navier-Lame operator, faces on the fly, "
                           "fused p-update, + <p, Ap>)",
                 "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -427,9 +434,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cn = args.cpu_sample_n
-        v_cpu, cores, secs = oracle_sample(cn, args.cpu_sample_steps)
+        v_cpu, cores, secs = oracle_sample(cn, args.cpu_sample_steps,
+                                           precond=PRECONDS[args.precond])
         cpu = {"value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{cn}^3 synthetic brain, {args.cpu_sample_steps} steps after init "
+               "sample": f"{cn}^3 synthetic brain, {args.precond} elasticity preconditioner, "
+                         f"{args.cpu_sample_steps} steps after init "
                          f"({secs:.1f} s); per-voxel cost grows with N, so this flatters the oracle"}
 
     if rank == 0:

@@ -17,7 +17,7 @@ TG_OK, TG_ERR_ARG, TG_ERR_CUDA, TG_ERR_NOCONV, TG_ERR_NONFINITE, TG_ERR_TIMEOUT,
 TG_FP64, TG_MIXED = 0, 1
 TG_INIT_KEEP_UV = 1
 TG_INIT_ADJOINT = 2
-TG_PRECOND_JACOBI, TG_PRECOND_SPECTRAL = 0, 1
+TG_PRECOND_JACOBI, TG_PRECOND_SPECTRAL, TG_PRECOND_SPECTRAL_SCALED = 0, 1, 2
 TG_MODEL_MULTISPECIES, TG_MODEL_SINGLE = 0, 1
 THETA = ("k_scale", "rho", "o_hyp", "o_inv", "E_scale")
 

@@ -63,6 +63,9 @@ constexpr int MAX_NV = 9;    // largest number of values reduced by one kernel
 constexpr int N_SCAL = 8;
 constexpr int MAX_SWEEPS = 64;        // refinement sweeps of one mixed-precision solve
 constexpr double TAU_INNER = 1e-4;    // smallest relative reduction asked of an inner solve
+// ... of a spectrally preconditioned inner elasticity solve: its few, well-conditioned FP32
+// iterations reach 1e-6 without stagnating, so one sweep usually meets the FP64 tolerance
+constexpr double TAU_INNER_SPECTRAL = 1e-6;
 // Which of the diffusion solves (bits: i, o, l) the mixed precision refines around FP32.
 // Oxygen stays FP64: a converged CN solve is fixed only to within its tolerance, and the
 // necrotic source h(o) (p + i + g + w) turns an oxygen difference do into a relative
@@ -110,6 +113,10 @@ Geo make_geo(const tg_grid* g, int sms) {
 
 // ---------------------------------------------------------------- spectral preconditioner
 // Every axis a power of two in [4, 2048]: the FFT passes stage whole lines in shared memory.
+bool spectral_precond(int pc) {
+  return pc == TG_PRECOND_SPECTRAL || pc == TG_PRECOND_SPECTRAL_SCALED;
+}
+
 bool spectral_grid_ok(const Geo& G) {
   for (int n : {G.nx, G.ny, G.nz})
     if (n < 4 || n > 2048 || (n & (n - 1)) != 0) return false;
@@ -166,7 +173,8 @@ struct Layout {
   size_t adj[C_COUNT];
   size_t partial, counter, scal, grad;
   bool spectral;
-  size_t sp_w, sp_z32[3], sp_z64[3], sp_tab32, sp_tab64, sp_mean, sp_partial, sp_counter;
+  size_t sp_w, sp_z32[3], sp_z64[3], sp_s32[3], sp_s64[3], sp_tab32, sp_tab64, sp_mean,
+      sp_partial, sp_counter;
   size_t total;
 };
 
@@ -214,6 +222,15 @@ Layout layout(const Geo& G, tg_precision prec, bool adjoint = false, bool spectr
     L.sp_z64[d] = off;
     if (need64) off += abytes;
   }
+  // the diagonal scaling of TG_PRECOND_SPECTRAL_SCALED (any spectral context may switch to it)
+  for (int d = 0; d < 3; ++d) {
+    L.sp_s32[d] = off;
+    if (need32) off += fbytes;
+  }
+  for (int d = 0; d < 3; ++d) {
+    L.sp_s64[d] = off;
+    if (need64) off += abytes;
+  }
   L.sp_tab32 = off;
   if (need32) off += spec_table_bytes(G, sizeof(float));
   L.sp_tab64 = off;
@@ -248,6 +265,7 @@ Spec<R> spec_view(const Geo& G, const Layout& L, char* ws, size_t tab_off) {
     V.T[d] = st;
     st += n[d];
   }
+  for (int d = 0; d < 3; ++d) V.s[d] = nullptr;
   V.mean = (double*)(ws + L.sp_mean);
   V.partial = (double*)(ws + L.sp_partial);
   V.counter = (unsigned int*)(ws + L.sp_counter);
@@ -265,7 +283,9 @@ int sm_count() {
 bool params_ok(const tg_params* p) {
   if (!p) return false;
   if (p->model != TG_MODEL_MULTISPECIES && p->model != TG_MODEL_SINGLE) return false;
-  if (p->precond_elas != TG_PRECOND_JACOBI && p->precond_elas != TG_PRECOND_SPECTRAL) return false;
+  if (p->precond_elas != TG_PRECOND_JACOBI && p->precond_elas != TG_PRECOND_SPECTRAL &&
+      p->precond_elas != TG_PRECOND_SPECTRAL_SCALED)
+    return false;
   if (!(p->eps_H > 0.0)) return false;
   if (!(p->o_inv > 0.5 * (p->o_hyp + p->o_inv)) && !(p->o_inv < 0.5 * (p->o_hyp + p->o_inv)))
     return false;  // o_inv == o_mit: the ramp of Eq. e:gog_reac_op is undefined
@@ -365,6 +385,8 @@ struct tg_ctx {
   Spec<double> sp64;     // FP64 form: FP64 solves
   float* z32[3];
   double* z64[3];
+  float* s32[3];         // diagonal scaling of TG_PRECOND_SPECTRAL_SCALED
+  double* s64[3];
 };
 
 namespace {
@@ -443,6 +465,11 @@ Cn3 cn_view(tg_ctx* X) {
   return C;
 }
 
+// the context's elasticity solves use a spectral preconditioner (its workspace has the buffers)
+bool spectral_on(const tg_ctx* X) {
+  return X->L.spectral && spectral_precond(X->prm.precond_elas);
+}
+
 Elas elas_view(tg_ctx* X, double* const u[3], double* const b[3]) {
   Elas E;
   E.mu = X->a[A_MU];
@@ -464,6 +491,7 @@ Elas elas_view(tg_ctx* X, double* const u[3], double* const b[3]) {
     E.udf[d] = reinterpret_cast<float2*>(X->a[A_UDF0 + d]);
   }
   E.df = X->df_res ? 1 : 0;
+  E.jacobi = spectral_on(X) ? 0 : 1;
   E.mudf = reinterpret_cast<float2*>(X->a[A_MUDF]);
   E.lamdf = reinterpret_cast<float2*>(X->a[A_LAMDF]);
   E.S = X->scal + 3;
@@ -587,9 +615,6 @@ tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
 }
 
 // the spectral preconditioner is in use (requested and the workspace holds its buffers)
-bool spectral_on(const tg_ctx* X) {
-  return X->L.spectral && X->prm.precond_elas == TG_PRECOND_SPECTRAL;
-}
 
 Elas32 elas32_view(tg_ctx* X) {
   Elas32 I;
@@ -646,16 +671,23 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
   CK(launch_elas32_coef(X->G, E, I, X->stream));
   X->launches += 2;
   const bool spec = spectral_on(X);
+  Spec<float> V = X->sp32;   // the scaled preconditioner's view carries s
   if (spec) {
-    CK(launch_spec_mean(X->G.nvox, E.mu, E.lam, E.eta, X->sp32.mean, X->sp32.partial,
-                        X->sp32.counter, X->stream));
+    CK(launch_spec_mean(X->G.nvox, E.mu, E.lam, E.eta, V.mean, V.partial, V.counter,
+                        X->stream));
     X->launches += 1;
+    if (X->prm.precond_elas == TG_PRECOND_SPECTRAL_SCALED) {
+      for (int d = 0; d < 3; ++d) V.s[d] = X->s32[d];
+      CK(launch_spec_scale(X->G, V, E, X->stream));
+      X->launches += 1;
+    }
   }
   const float* const r32[3] = {I.r[0], I.r[1], I.r[2]};
   int inner_total = 0, sweeps = 0;
   CgScal out;
   for (;;) {
-    CK(launch_elas_ir_residual(X->G, E, I, Sout, minus_b, TAU_INNER, X->stream));
+    CK(launch_elas_ir_residual(X->G, E, I, Sout, minus_b, spec ? TAU_INNER_SPECTRAL : TAU_INNER,
+                               X->stream));
     X->launches += 1;
     CK(cudaMemcpyAsync(&out, Sout, sizeof(CgScal), cudaMemcpyDeviceToHost, X->stream));
     CK(cudaStreamSynchronize(X->stream));
@@ -664,7 +696,7 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
     CK(launch_elas32_scale_r(X->G, I, X->stream));
     X->launches += 1;
     if (spec) {   // z = P r and <r, z> for the inner solve's first direction
-      CK(launch_spectral(X->sp32, r32, X->z32, I.S, X->stream));
+      CK(launch_spectral(V, r32, X->z32, I.S, X->stream));
       X->launches += 5;
     }
     CgScal host[1];
@@ -682,7 +714,7 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
       if (timed) cudaEventRecord(X->ev[2 * q + 1], X->stream);
       if (e != cudaSuccess) return e;
       if (!spec) return launch_elas32_update(X->G, I, X->stream);
-      return launch_spectral_update(X->sp32, I, X->z32, X->stream);
+      return launch_spectral_update(V, I, X->z32, X->stream);
     }, I.S, 1, X->prm.maxit_elas, X->prev_it_inner[slot], host);
     if (s != TG_OK) return s;
     harvest_timing(X, recorded, host[0].it);
@@ -720,11 +752,17 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
     CK(launch_elas_extrapolate(X->G, E, 1.0 / inv_dt, X->stream));
     X->launches += 1;
   }
+  Spec<double> V = X->sp64;   // the scaled preconditioner's view carries s
   if (spec) {
-    CK(launch_spec_mean(X->G.nvox, E.mu, E.lam, E.eta, X->sp64.mean, X->sp64.partial,
-                        X->sp64.counter, X->stream));
+    CK(launch_spec_mean(X->G.nvox, E.mu, E.lam, E.eta, V.mean, V.partial, V.counter,
+                        X->stream));
+    if (X->prm.precond_elas == TG_PRECOND_SPECTRAL_SCALED) {
+      for (int d = 0; d < 3; ++d) V.s[d] = X->s64[d];
+      CK(launch_spec_scale(X->G, V, E, X->stream));
+      X->launches += 1;
+    }
     CK(launch_elas_init_spec(X->G, E, minus_b, X->stream));
-    CK(launch_spectral(X->sp64, r64, X->z64, E.S, X->stream));
+    CK(launch_spectral(V, r64, X->z64, E.S, X->stream));
     CK(launch_elas_pupdate_spec(X->G, E, X->stream));
     X->launches += 9;
   } else {
@@ -745,7 +783,7 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
     if (e != cudaSuccess) return e;
     if (!spec) return launch_elas_update(X->G, E, X->stream);
     e = launch_elas_update_spec(X->G, E, X->stream);
-    if (e == cudaSuccess) e = launch_spectral(X->sp64, r64, X->z64, E.S, X->stream);
+    if (e == cudaSuccess) e = launch_spectral(V, r64, X->z64, E.S, X->stream);
     if (e == cudaSuccess) e = launch_elas_pupdate_spec(X->G, E, X->stream);
     return e;
   }, E.S, 1, X->prm.maxit_elas, X->prev_it_elas, host);
@@ -847,6 +885,7 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   double* const Kf[3] = {X->a[A_KF0], X->a[A_KF1], X->a[A_KF2]};
   CK(launch_diff_coef(G, X->dp, dt, S.g, S.w, S.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
                       X->a[A_RHO], s));
+  X->launches += 1;   // S0 is two kernels (faces, diagonal)
   if (X->prec == TG_MIXED) {   // FP32 faces and diagonal of the inner diffusion solves
     F32Copy cp;
     const double* src[4] = {Kf[0], Kf[1], Kf[2], X->a[A_DINV_D]};
@@ -1030,7 +1069,7 @@ tg_status do_adjoint_step(tg_ctx* X, double dt, const void* tape, const tg_state
     const Elas E = elas_view(X, psi, nullptr);
     CK(launch_elas_coef(G, X->dp, E, qp[0], qp[2], false, s));
   }
-  X->launches += 6;
+  X->launches += 7;
   // the previous step's adjoint solution is the starting guess (the solve is differentiated
   // as an exact inverse, so the guess only changes the iteration count)
   if (!X->psi_valid)
@@ -1085,6 +1124,8 @@ tg_status spectral_setup(tg_ctx* X) {
   for (int d = 0; d < 3; ++d) {
     X->z32[d] = nullptr;
     X->z64[d] = nullptr;
+    X->s32[d] = nullptr;
+    X->s64[d] = nullptr;
   }
   if (!L.spectral) return TG_OK;
   const bool need32 = X->prec == TG_MIXED || X->has_adjoint;
@@ -1092,13 +1133,19 @@ tg_status spectral_setup(tg_ctx* X) {
   if (cudaMemsetAsync(X->ws + L.sp_counter, 0, ALIGN, X->stream) != cudaSuccess) return TG_ERR_CUDA;
   if (need32) {
     X->sp32 = spec_view<float>(X->G, L, X->ws, L.sp_tab32);
-    for (int d = 0; d < 3; ++d) X->z32[d] = (float*)(X->ws + L.sp_z32[d]);
+    for (int d = 0; d < 3; ++d) {
+      X->z32[d] = (float*)(X->ws + L.sp_z32[d]);
+      X->s32[d] = (float*)(X->ws + L.sp_s32[d]);
+    }
     if (spec_prepare(X->sp32) != cudaSuccess) return TG_ERR_CUDA;
     if (launch_spec_tables(X->sp32, X->G.h, X->stream) != cudaSuccess) return TG_ERR_CUDA;
   }
   if (need64) {
     X->sp64 = spec_view<double>(X->G, L, X->ws, L.sp_tab64);
-    for (int d = 0; d < 3; ++d) X->z64[d] = (double*)(X->ws + L.sp_z64[d]);
+    for (int d = 0; d < 3; ++d) {
+      X->z64[d] = (double*)(X->ws + L.sp_z64[d]);
+      X->s64[d] = (double*)(X->ws + L.sp_s64[d]);
+    }
     if (spec_prepare(X->sp64) != cudaSuccess) return TG_ERR_CUDA;
     if (launch_spec_tables(X->sp64, X->G.h, X->stream) != cudaSuccess) return TG_ERR_CUDA;
   }
@@ -1113,7 +1160,7 @@ size_t tg_workspace_bytes(const tg_grid* grid, const tg_params* params, tg_preci
   if (!grid_ok(grid) || (prec != TG_FP64 && prec != TG_MIXED)) return 0;
   if (params && !params_ok(params)) return 0;
   const Geo G = make_geo(grid, sm_count());
-  const bool spectral = params && params->precond_elas == TG_PRECOND_SPECTRAL;
+  const bool spectral = params && spectral_precond(params->precond_elas);
   if (spectral && !spectral_grid_ok(G)) return 0;
   return layout(G, prec, false, spectral).total;
 }
@@ -1123,7 +1170,7 @@ size_t tg_workspace_bytes_adjoint(const tg_grid* grid, const tg_params* params,
   if (!grid_ok(grid) || (prec != TG_FP64 && prec != TG_MIXED)) return 0;
   if (params && !params_ok(params)) return 0;
   const Geo G = make_geo(grid, sm_count());
-  const bool spectral = params && params->precond_elas == TG_PRECOND_SPECTRAL;
+  const bool spectral = params && spectral_precond(params->precond_elas);
   if (spectral && !spectral_grid_ok(G)) return 0;
   return layout(G, prec, true, spectral).total;
 }
@@ -1149,7 +1196,7 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
     if (!q || ((uintptr_t)q & 15u)) return TG_ERR_ARG;
   const Geo G = make_geo(grid, sm_count());
   const bool adjoint = (flags & TG_INIT_ADJOINT) != 0;
-  const bool spectral = params->precond_elas == TG_PRECOND_SPECTRAL;
+  const bool spectral = spectral_precond(params->precond_elas);
   if (spectral && !spectral_grid_ok(G)) return TG_ERR_ARG;
   const Layout L = layout(G, prec, adjoint, spectral);
   if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < L.total)
@@ -1294,7 +1341,7 @@ tg_status tg_adjoint_init(tg_ctx* X, double* const lam_u[3], double grad[5]) {
 tg_status tg_set_params(tg_ctx* X, const tg_params* params) {
   if (!X || !params_ok(params)) return TG_ERR_ARG;
   if (X->broken) return TG_ERR_STATE;
-  if (params->precond_elas == TG_PRECOND_SPECTRAL && !X->L.spectral) return TG_ERR_WORKSPACE;
+  if (spectral_precond(params->precond_elas) && !X->L.spectral) return TG_ERR_WORKSPACE;
   if (X->has_adjoint && params->model != TG_MODEL_MULTISPECIES) return TG_ERR_ARG;
   X->prm = *params;
   X->df_res = df_residual_ok(X);
@@ -1682,7 +1729,9 @@ tg_status queue_step(tg_batch* B, double dt) {
   }
   for (int k = 0; k < BATCH_GRAPH_SWEEPS; ++k) BCK(launch_batch_sweep(D, B->coop_el, B->stream));
   BCK(launch_batch_status(D, B->d_stat, B->stream));
-  B->launches += 2 + 1 + (long long)B->ctx.size() * 11 + 3LL * BATCH_GRAPH_SWEEPS + 1;
+  // per simulation: S0 faces and diagonal, divergence, FP32 copies, transport; reactions,
+  // Lame, elasticity coefficients, their FP32 copies, the extrapolated start
+  B->launches += 2 + 1 + (long long)B->ctx.size() * 10 + 3LL * BATCH_GRAPH_SWEEPS + 1;
   return TG_OK;
 }
 
@@ -1743,7 +1792,7 @@ tg_status batch_one_step(tg_batch* B, double dt, tg_batch_stats* stats) {
   }
   if (B->use_graph && B->graph_ready) {
     BCK(cudaGraphLaunch(B->graph, B->stream));
-    B->launches += 2 + 1 + (long long)B->ctx.size() * 11 + 3LL * BATCH_GRAPH_SWEEPS + 1;
+    B->launches += 2 + 1 + (long long)B->ctx.size() * 10 + 3LL * BATCH_GRAPH_SWEEPS + 1;
   } else {
     tg_status e = queue_step(B, dt);
     if (e != TG_OK) return e;

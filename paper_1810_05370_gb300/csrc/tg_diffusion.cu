@@ -21,12 +21,15 @@ __device__ __forceinline__ double harmonic(double a, double b) {
   return (a + b) > 0.0 ? 2.0 * a * b / (a + b) : 0.0;
 }
 
-__global__ void __launch_bounds__(NT) k_diff_coef(Geo G, DevParams P, double half_dt,
-                                                  const double* __restrict__ g,
-                                                  const double* __restrict__ w,
-                                                  const double* __restrict__ f, double* Kfx,
-                                                  double* Kfy, double* Kfz, double* dsum,
-                                                  double* dinv, double* rho) {
+// S0 in two passes.  FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU, so each face
+// (one division) is formed once, by the node below it, instead of by both of its nodes:
+// k_diff_faces writes a_d,j for the faces j + e_d/2 and rho; k_diff_diag then adds the faces
+// below each node from the neighbours' entries.
+__global__ void __launch_bounds__(NT) k_diff_faces(Geo G, DevParams P, double half_dt,
+                                                   const double* __restrict__ g,
+                                                   const double* __restrict__ w,
+                                                   const double* __restrict__ f, double* Kfx,
+                                                   double* Kfy, double* Kfz, double* rho) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= G.nx || j >= G.ny) return;
@@ -37,16 +40,29 @@ __global__ void __launch_bounds__(NT) k_diff_coef(Geo G, DevParams P, double hal
     auto K = [&](long long e) { return node_K(P, g[e], w[e], f[e]); };
     const long long c = nb.at(0, 0, 0);
     const double kc = K(c);
-    const double fxp = harmonic(kc, K(nb.at(1, 0, 0))), fxm = harmonic(K(nb.at(-1, 0, 0)), kc);
-    const double fyp = harmonic(kc, K(nb.at(0, 1, 0))), fym = harmonic(K(nb.at(0, -1, 0)), kc);
-    const double fzp = harmonic(kc, K(nb.at(0, 0, 1))), fzm = harmonic(K(nb.at(0, 0, -1)), kc);
-    Kfx[c] = sx * fxp;
-    Kfy[c] = sy * fyp;
-    Kfz[c] = sz * fzp;
-    const double d = 1.0 + sx * (fxp + fxm) + sy * (fyp + fym) + sz * (fzp + fzm);
+    Kfx[c] = sx * harmonic(kc, K(nb.at(1, 0, 0)));
+    Kfy[c] = sy * harmonic(kc, K(nb.at(0, 1, 0)));
+    Kfz[c] = sz * harmonic(kc, K(nb.at(0, 0, 1)));
+    rho[c] = P.rho_g * g[c] + P.rho_w * w[c];
+  }
+}
+
+// CN diagonal 1 + sum of the six faces of each node, and its inverse
+__global__ void __launch_bounds__(NT) k_diff_diag(Geo G, const double* __restrict__ Kfx,
+                                                  const double* __restrict__ Kfy,
+                                                  const double* __restrict__ Kfz, double* dsum,
+                                                  double* dinv) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const Nbr nb = make_nbr(G, i, j, k);
+    const long long c = nb.at(0, 0, 0);
+    const double d = 1.0 + (Kfx[c] + Kfx[nb.at(-1, 0, 0)]) + (Kfy[c] + Kfy[nb.at(0, -1, 0)]) +
+                     (Kfz[c] + Kfz[nb.at(0, 0, -1)]);
     dsum[c] = d;
     dinv[c] = 1.0 / d;
-    rho[c] = P.rho_g * g[c] + P.rho_w * w[c];
   }
 }
 
@@ -132,8 +148,9 @@ __global__ void __launch_bounds__(NT) k_cn_pupdate(Geo G, Cn3 C) {
 cudaError_t launch_diff_coef(const Geo& G, const DevParams& P, double dt, const double* g,
                              const double* w, const double* f, double* const Kf[3], double* dsum,
                              double* dinv, double* rho, cudaStream_t st) {
-  k_diff_coef<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, 0.5 * dt, g, w, f, Kf[0], Kf[1], Kf[2], dsum,
-                                               dinv, rho);
+  k_diff_faces<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, 0.5 * dt, g, w, f, Kf[0], Kf[1], Kf[2],
+                                                rho);
+  k_diff_diag<<<G.grid, dim3(BX, BY), 0, st>>>(G, Kf[0], Kf[1], Kf[2], dsum, dinv);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(NT) k_elas_coef(Geo G, DevParams P, Elas E,
         reinterpret_cast<float2*>(E.dsum[a])[c] = df_pack(s);
       else
         E.dsum[a][c] = s;
-      E.dinv[a][c] = 1.0 / s;
+      if (E.jacobi) E.dinv[a][c] = 1.0 / s;
     }
     if (force) {
       const double sc = p[c] + n[c];

@@ -311,6 +311,8 @@ struct Spec {
   C* tw[3];                   // exp(-2 pi i k / n_d), k < n_d
   R* S[3];                    // 4 sin^2(theta_k / 2) / h_d^2, theta_k = 2 pi k / n_d
   R* T[3];                    // sin(theta_k) / h_d
+  R* s[3];                    // diagonal scaling s = (D0 / D)^{1/2} per component (null:
+                              // the unscaled preconditioner)
   double* mean;               // mu0, lambda0, eta0 (device)
   double* partial;            // per-block partial sums (x inverse pass, means)
   unsigned int* counter;
@@ -396,7 +398,7 @@ struct Elas {
   double* F[3];      // face (lambda + 2 mu) / h_d^2 between j and j + e_d
   double* G[3];      // face mu / h_d^2
   double* dsum[3];   // Jacobi diagonal per component
-  double* dinv[3];
+  double* dinv[3];   // its inverse, formed only with Jacobi preconditioning (jacobi != 0)
   double* b[3];      // force (or caller's rhs when b_external)
   double* du[3];     // CG iterate: increment of u
   double* r[3];
@@ -408,6 +410,7 @@ struct Elas {
   // double-FP32 residual of the mixed precision (df != 0): F, G and dsum then hold (hi, lo)
   // FP32 pairs instead of FP64 values, and udf, mudf, lamdf the pairs of u, mu and lambda
   int df;
+  int jacobi;        // 0 with the spectral preconditioner: dinv (FP64 and FP32) is not used
   float2* udf[3];
   float2* mudf;
   float2* lamdf;
@@ -522,6 +525,9 @@ template <typename R>
 cudaError_t launch_spec_tables(const Spec<R>&, const double h[3], cudaStream_t st);
 template <typename R>
 cudaError_t spec_prepare(const Spec<R>&);   // shared-memory limits of the pass kernels
+// V.s = (D0 / D)^{1/2} from E.dsum and the means (TG_PRECOND_SPECTRAL_SCALED)
+template <typename R>
+cudaError_t launch_spec_scale(const Geo&, const Spec<R>& V, const Elas& E, cudaStream_t st);
 cudaError_t launch_spec_mean(long long n, const double* mu, const double* lam,
                              const double* eta, double* mean, double* partial,
                              unsigned int* counter, cudaStream_t st);

@@ -37,9 +37,11 @@ __global__ void __launch_bounds__(NT) k_elas32_coef(long long n, Elas E, Elas32 
     I.mu[e] = (float)mu;
     I.lam[e] = (float)lam;
     I.eta[e] = (float)E.eta[e];
-    I.dinv[0][e] = (float)E.dinv[0][e];
-    I.dinv[1][e] = (float)E.dinv[1][e];
-    I.dinv[2][e] = (float)E.dinv[2][e];
+    if (E.jacobi) {
+      I.dinv[0][e] = (float)E.dinv[0][e];
+      I.dinv[1][e] = (float)E.dinv[1][e];
+      I.dinv[2][e] = (float)E.dinv[2][e];
+    }
     if (E.df) {
       E.mudf[e] = df_pack(mu);
       E.lamdf[e] = df_pack(lam);

@@ -459,6 +459,7 @@ __global__ void __launch_bounds__(NT) k_spec_x_fwd(Spec<R> V, const R* __restric
   C* b = a + (size_t)es * n;
   load_roots(tw, V.tw[0], n);
   const R* src = t.comp == 0 ? r0 : (t.comp == 1 ? r1 : r2);
+  const R* sc = V.s[t.comp];   // the transform takes s r with the scaled preconditioner
   const int total = t.pb * n;
   for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {
     R va[LB], vb[LB];
@@ -469,6 +470,10 @@ __global__ void __launch_bounds__(NT) k_spec_x_fwd(Spec<R> V, const R* __restric
         const size_t o = t.row0 + (size_t)(2 * (idx >> ln)) * n + (idx & (n - 1));
         va[u] = __ldg(src + o);
         vb[u] = __ldg(src + o + n);
+        if (sc) {
+          va[u] *= __ldg(sc + o);
+          vb[u] *= __ldg(sc + o + n);
+        }
       }
     }
 #pragma unroll
@@ -500,6 +505,7 @@ __global__ void __launch_bounds__(NT) k_spec_update_xfwd(Spec<float> V, Elas32 I
   float* r = I.r[t.comp];
   const float* p = I.p[pbuf][t.comp];
   const float* q = I.q[t.comp];
+  const float* sc = V.s[t.comp];   // the transform takes s r with the scaled preconditioner
   constexpr int UB = 4;
   float rr = 0.0f;
   const int total = t.pb * n;
@@ -531,7 +537,8 @@ __global__ void __launch_bounds__(NT) k_spec_update_xfwd(Spec<float> V, Elas32 I
         r[o] = xa;
         r[o + n] = xb;
         rr += xa * xa + xb * xb;
-        a[(idx & (n - 1)) * es + (idx >> ln)] = C{xa, xb};
+        a[(idx & (n - 1)) * es + (idx >> ln)] =
+            sc ? C{xa * __ldg(sc + o), xb * __ldg(sc + o + n)} : C{xa, xb};
       }
     }
   }
@@ -628,6 +635,162 @@ __global__ void __launch_bounds__(NT) k_spec_z(Spec<R> V, CgScal* S) {
     cg_after_precond(*S, out);
 }
 
+// ------------------------------------------------------------- z pass, in registers (FP32)
+// For nz = 16 P (P = 8 or 16) each column's transforms run in registers.  A block takes
+// ZR_COLS mode columns kx at one ky with P threads per column; thread t of a column loads the
+// elements kz = t + P m (m < 16) of a component.  Forward transform, four-step with
+// nz = 16 x P:
+//   A[t][k2] = sum_m x[t + P m] exp(-2 pi i m k2 / 16)        DFT16 in registers
+//   B[t][k2] = A[t][k2] exp(-2 pi i t k2 / nz)                 twiddle
+//   X[k2 + 16 k1] = sum_t B[t][k2] exp(-2 pi i t k1 / P)       DFT_P after an exchange
+// The exchange goes through shared memory: thread t then owns the J = 16 / P columns
+// k2 = t + P j and holds the modes kz = k2 + 16 k1.  The inverse transform retraces the steps
+// (inverse DFT_P, exchange back, conjugate twiddle, inverse DFT16), so every element crosses
+// shared memory twice per component instead of four times.  A thread holds one component in
+// registers at a time: the spectra of components 0 and 1 wait in thread-private shared-memory
+// slots while component 2 is transformed, the 3x3 inverse reads them back mode by mode, and
+// component 2 stays in registers from its forward to its inverse transform.  Consecutive
+// threads take consecutive columns, so a warp's loads and stores of one plane are rows of W.
+constexpr int ZR_COLS = 8;
+
+// exchange buffer: 16 rows k2 of P x ZR_COLS elements, padded by ZR_COLS so that the column
+// groups t and t + 1 of a half-warp fall in different banks
+template <int P>
+__host__ __device__ constexpr int zr_row() { return (P + 1) * ZR_COLS; }
+template <int P>
+constexpr size_t spec_smem_zr() {   // twiddles, the exchange buffer, two components' spectra
+  return (size_t)(16 * P + 16 * zr_row<P>() + 2 * 16 * ZR_COLS * P) * sizeof(float2);
+}
+
+template <int P>
+__global__ void __launch_bounds__(ZR_COLS * P, 512 / (ZR_COLS * P))
+    k_spec_zr(Spec<float> V, CgScal* S) {
+  using C = float2;
+  constexpr int N = 16 * P, J = 16 / P, LP = P == 16 ? 4 : (P == 8 ? 3 : 2);
+  constexpr int NTH = ZR_COLS * P;
+  static_assert(P == 4 || P == 8 || P == 16, "nz = 64, 128 or 256");
+  if (spec_skip<float>(S)) return;
+  C* tw = smem_cx<C>();
+  C* xb = tw + N;                       // exchange buffer
+  C* held = xb + 16 * zr_row<P>();      // spectra of components 0 and 1: [q][i][thread]
+  load_roots(tw, V.tw[2], N);
+  const int c = threadIdx.x % ZR_COLS, t = threadIdx.x / ZR_COLS;
+  const int kx = blockIdx.x * ZR_COLS + c, ky = blockIdx.y;
+  const bool valid = kx < V.nxh;
+  // element offsets stay below 3 nz ny nxp < 2^31 for nz <= 256
+  const int plane = V.ny * V.nxp, comp_stride = N * plane;
+  C* col = V.W + ky * V.nxp + (valid ? kx : 0) + t * plane;
+  auto slot = [&](int k2, int tt) { return k2 * zr_row<P>() + tt * ZR_COLS + c; };
+  auto hslot = [&](int q, int i) { return (q * 16 + i) * NTH + (int)threadIdx.x; };
+  C v[16];
+
+  // forward transform of component q: modes kz = t + P j + 16 k1 end at v[j P + k1]
+  auto forward = [&](int q) {
+    const C* src = col + q * comp_stride;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = valid ? src[P * m * plane] : C{0.0f, 0.0f};
+    if (q == 0) __syncthreads();   // twiddles visible
+    dft<4, -1>(v);
+#pragma unroll
+    for (int k2 = 1; k2 < 16; ++k2) v[k2] = cmul(v[k2], tw[t * k2]);
+    if (q > 0) __syncthreads();    // the previous exchange has been read
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) xb[slot(k2, t)] = v[k2];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int u = 0; u < P; ++u) v[j * P + u] = xb[slot(t + P * j, u)];
+#pragma unroll
+    for (int j = 0; j < J; ++j) dft<LP, -1>(*reinterpret_cast<C(*)[P]>(&v[j * P]));
+  };
+  // inverse transform of the modes in v (component q) and the store of its elements
+  auto inverse = [&](int q) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) dft<LP, +1>(*reinterpret_cast<C(*)[P]>(&v[j * P]));
+    __syncthreads();               // the previous exchange has been read
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int u = 0; u < P; ++u) xb[slot(t + P * j, u)] = v[j * P + u];
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) v[k2] = xb[slot(k2, t)];
+#pragma unroll
+    for (int k2 = 1; k2 < 16; ++k2) v[k2] = cmul(v[k2], root<+1>(tw, t * k2));
+    dft<4, +1>(v);
+    if (valid) {
+      C* dst = col + q * comp_stride;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) dst[P * m * plane] = v[m];
+    }
+  };
+
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    forward(q);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) held[hslot(q, i)] = v[i];
+  }
+  forward(2);
+
+  // the 3x3 inverse per mode (as in k_spec_z; reciprocals to FP32 accuracy suffice for a
+  // preconditioner) and the Parseval term of <r, z>
+  const float mu0 = (float)V.mean[0], lam0 = (float)V.mean[1], eta0 = (float)V.mean[2];
+  const float cc = lam0 + mu0;
+  const float inv_vol = (float)(1.0 / ((double)V.nx * V.ny * V.nz));
+  const float Sx = V.S[0][valid ? kx : 0], Tx = V.T[0][valid ? kx : 0];
+  const float Sy = V.S[1][ky], Ty = V.T[1][ky];
+  const float wgt = !valid ? 0.0f : ((kx == 0 || kx == V.nx / 2) ? 1.0f : 2.0f);
+  float rz_part = 0.0f;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      const int i = j * P + k1, kz = t + P * j + 16 * k1;
+      const float Sv[3] = {Sx, Sy, __ldg(V.S[2] + kz)};
+      const float Tv[3] = {Tx, Ty, __ldg(V.T[2] + kz)};
+      const float base = eta0 + mu0 * (Sv[0] + Sv[1] + Sv[2]);
+      const C rv[3] = {held[hslot(0, i)], held[hslot(1, i)], v[i]};
+      float tdt = 0.0f, dinv[3];
+      C y[3], s = {0.0f, 0.0f};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float D = base + cc * (Sv[q] - Tv[q] * Tv[q]);
+        dinv[q] = D > 0.0f ? __fdividef(1.0f, D) : 0.0f;
+        y[q] = C{rv[q].x * dinv[q], rv[q].y * dinv[q]};
+        tdt += Tv[q] * Tv[q] * dinv[q];
+        s.x += Tv[q] * y[q].x;
+        s.y += Tv[q] * y[q].y;
+      }
+      const float f = __fdividef(cc, 1.0f + cc * tdt);
+      C zv[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float g = f * Tv[q] * dinv[q];
+        zv[q] = C{(y[q].x - g * s.x) * inv_vol, (y[q].y - g * s.y) * inv_vol};
+        rz_part += wgt * (rv[q].x * zv[q].x + rv[q].y * zv[q].y);
+      }
+      held[hslot(0, i)] = zv[0];
+      held[hslot(1, i)] = zv[1];
+      v[i] = zv[2];
+    }
+  }
+
+  inverse(2);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = held[hslot(q, i)];
+    inverse(q);
+  }
+  if (S == nullptr) return;
+  double out;
+  if (block_sum_last((double)rz_part, V.partial, V.counter, blockIdx.y * gridDim.x + blockIdx.x,
+                     gridDim.x * gridDim.y, out))
+    cg_after_precond(*S, out);
+}
+
 // ---------------------------------------------------------------------------- x inverse
 // block (pair tile, z, component): the half spectra of rows y0 + 2l, y0 + 2l + 1 form
 // C[k] = A[k] + i B[k] over all k (Hermitian extension); the inverse transform is
@@ -677,13 +840,14 @@ __global__ void __launch_bounds__(NT) k_spec_x_inv(Spec<R> V, R* z0, R* z1, R* z
   __syncthreads();
   const C* F = fft_lines<+1>(a, b, ln, ilog2(pb), 1, 1, es, tw);
   R* zs = comp == 0 ? z0 : (comp == 1 ? z1 : z2);
+  const R* sc = V.s[comp];   // z = s A0^{-1} (s r) with the scaled preconditioner
   const size_t row0 = ((size_t)z * V.ny + y0) * n;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int l = idx >> ln, x = idx & (n - 1);
     const size_t o = row0 + (size_t)(2 * l) * n + x;
     const C f = F[x * es + l];
-    zs[o] = f.x;
-    zs[o + n] = f.y;
+    zs[o] = sc ? f.x * __ldg(sc + o) : f.x;
+    zs[o + n] = sc ? f.y * __ldg(sc + o + n) : f.y;
   }
 }
 
@@ -723,6 +887,39 @@ __global__ void __launch_bounds__(NT) k_spec_mean(long long n, const double* __r
   }
 }
 
+// Diagonal scaling of TG_PRECOND_SPECTRAL_SCALED: s_a = (D0_a / D_a)^{1/2} per node, D_a the
+// Jacobi diagonal of the variable-coefficient operator (FP64, or (hi, lo) pairs with the
+// double-FP32 residual) and D0_a = eta0 + 2 (lambda0 + 2 mu0) / h_a^2 + 2 mu0 sum_{d != a}
+// 1 / h_d^2 that of the constant-coefficient operator.  The FP32 form is evaluated in FP32.
+template <typename R>
+__global__ void __launch_bounds__(NT) k_spec_scale(long long n, Spec<R> V, Elas E, double ih20,
+                                                   double ih21, double ih22) {
+  const double mu0 = V.mean[0], lam0 = V.mean[1], eta0 = V.mean[2];
+  const double ih2[3] = {ih20, ih21, ih22};
+  R d0[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double v = eta0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v += 2.0 * (d == a ? lam0 + 2.0 * mu0 : mu0) * ih2[d];
+    d0[a] = (R)v;
+  }
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R D;
+      if (E.df) {
+        const float2 h = reinterpret_cast<const float2*>(E.dsum[a])[e];
+        D = sizeof(R) == 4 ? (R)h.x : (R)((double)h.x + (double)h.y);
+      } else {
+        D = (R)E.dsum[a][e];
+      }
+      V.s[a][e] = sqrt(d0[a] / D);
+    }
+  }
+}
+
 }  // namespace
 
 // Every pass kernel may use up to the device's opt-in shared memory per block, less 1 KB for
@@ -745,7 +942,19 @@ cudaError_t spec_prepare(const Spec<R>& V) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_y<R, -1>, A, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_y<R, +1>, A, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_z<R>, A, optin);
+  if constexpr (sizeof(R) == 4) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_zr<16>, A, optin);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_zr<8>, A, optin);
+  }
   return e;
+}
+
+template <typename R>
+cudaError_t launch_spec_scale(const Geo& G, const Spec<R>& V, const Elas& E, cudaStream_t st) {
+  const long long want = (G.nvox + NT - 1) / NT;
+  const int blocks = (int)(want < 4096 ? (want > 0 ? want : 1) : 4096);
+  k_spec_scale<R><<<blocks, NT, 0, st>>>(G.nvox, V, E, G.ih2[0], G.ih2[1], G.ih2[2]);
+  return cudaGetLastError();
 }
 
 template <typename R>
@@ -764,15 +973,32 @@ cudaError_t launch_spec_mean(long long n, const double* mu, const double* lam,
   return cudaGetLastError();
 }
 
+// the z pass: in registers for FP32 and nz = 128 or 256, staged through shared memory otherwise
+template <typename R>
+void launch_spec_z(const Spec<R>& V, CgScal* S, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {
+    const dim3 g((V.nxh + ZR_COLS - 1) / ZR_COLS, V.ny);
+    if (V.nz == 256) {
+      k_spec_zr<16><<<g, 16 * ZR_COLS, spec_smem_zr<16>(), st>>>(V, S);
+      return;
+    }
+    if (V.nz == 128) {
+      k_spec_zr<8><<<g, 8 * ZR_COLS, spec_smem_zr<8>(), st>>>(V, S);
+      return;
+    }
+  }
+  const dim3 gz((V.nxh + V.tz - 1) / V.tz, V.ny);
+  k_spec_z<R><<<gz, V.nt_z, spec_smem_z(V), st>>>(V, S);
+}
+
 template <typename R>
 cudaError_t launch_spectral(const Spec<R>& V, const R* const r[3], R* const z[3], CgScal* S,
                             cudaStream_t st) {
   const dim3 gx(V.ny / (2 * V.pb), V.nz, 3);
   const dim3 gy((V.nxh + V.tx - 1) / V.tx, V.nz, 3);
-  const dim3 gz((V.nxh + V.tz - 1) / V.tz, V.ny);
   k_spec_x_fwd<R><<<gx, NT, spec_smem_x(V), st>>>(V, r[0], r[1], r[2], S);
   k_spec_y<R, -1><<<gy, NT, spec_smem_y(V), st>>>(V, S);
-  k_spec_z<R><<<gz, V.nt_z, spec_smem_z(V), st>>>(V, S);
+  launch_spec_z(V, S, st);
   k_spec_y<R, +1><<<gy, NT, spec_smem_y(V), st>>>(V, S);
   k_spec_x_inv<R><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S);
   return cudaGetLastError();
@@ -784,10 +1010,9 @@ cudaError_t launch_spectral_update(const Spec<float>& V, const Elas32& I, float*
                                    cudaStream_t st) {
   const dim3 gx(V.ny / (2 * V.pb), V.nz, 3);
   const dim3 gy((V.nxh + V.tx - 1) / V.tx, V.nz, 3);
-  const dim3 gz((V.nxh + V.tz - 1) / V.tz, V.ny);
   k_spec_update_xfwd<<<gx, NT, spec_smem_x(V), st>>>(V, I);
   k_spec_y<float, -1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S);
-  k_spec_z<float><<<gz, V.nt_z, spec_smem_z(V), st>>>(V, I.S);
+  launch_spec_z(V, I.S, st);
   k_spec_y<float, +1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S);
   k_spec_x_inv<float><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], I.S);
   return cudaGetLastError();
@@ -795,6 +1020,10 @@ cudaError_t launch_spectral_update(const Spec<float>& V, const Elas32& I, float*
 
 template cudaError_t spec_prepare<float>(const Spec<float>&);
 template cudaError_t spec_prepare<double>(const Spec<double>&);
+template cudaError_t launch_spec_scale<float>(const Geo&, const Spec<float>&, const Elas&,
+                                              cudaStream_t);
+template cudaError_t launch_spec_scale<double>(const Geo&, const Spec<double>&, const Elas&,
+                                               cudaStream_t);
 template cudaError_t launch_spec_tables<float>(const Spec<float>&, const double[3], cudaStream_t);
 template cudaError_t launch_spec_tables<double>(const Spec<double>&, const double[3], cudaStream_t);
 template cudaError_t launch_spectral<float>(const Spec<float>&, const float* const[3],

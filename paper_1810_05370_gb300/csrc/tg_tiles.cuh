@@ -349,7 +349,7 @@ __device__ __forceinline__ void elas_ir_residual_tile(const Geo& G, const Elas& 
         const double rhs = minus_b ? -E.b[a][c] : E.b[a][c];
         const double res = rhs - Au[a];
         const float r32 = (float)res;
-        const float z32 = I.dinv[a][c] * r32;
+        const float z32 = E.jacobi ? I.dinv[a][c] * r32 : 0.0f;
         I.r[a][c] = r32;
         I.e[a][c] = 0.0f;
         acc[0] += rhs * rhs;
@@ -427,7 +427,7 @@ __device__ __forceinline__ void elas_ir_residual_tile_df(const Geo& G, const Ela
         const Df rhs = minus_b ? Df{-bv.x, -bv.y} : Df{bv.x, bv.y};
         const Df res = df_sub(rhs, Au[a]);
         const float r32 = __fadd_rn(res.hi, res.lo);
-        const float z32 = I.dinv[a][c] * r32;
+        const float z32 = E.jacobi ? I.dinv[a][c] * r32 : 0.0f;
         I.r[a][c] = r32;
         I.e[a][c] = 0.0f;
         sbb += rhs.hi * rhs.hi;

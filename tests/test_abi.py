@@ -83,3 +83,8 @@ def test_spectral_preconditioner_grid_rules(tg):
     assert tg.tg_workspace_bytes(tg.make_grid((36, 20, 12)), Pj, tg.TG_FP64) > 0
     Pbad = tg.make_params(workload_params(precond_elas=7))
     assert tg.tg_workspace_bytes(g, Pbad, tg.TG_FP64) == 0
+    # the scaled form shares the spectral workspace (a context may switch between the two)
+    Pc = tg.make_params(workload_params(precond_elas=tg.TG_PRECOND_SPECTRAL_SCALED))
+    for prec in (tg.TG_FP64, tg.TG_MIXED):
+        assert tg.tg_workspace_bytes(g, Pc, prec) == tg.tg_workspace_bytes(g, Ps, prec)
+    assert tg.tg_workspace_bytes(tg.make_grid((36, 20, 12)), Pc, tg.TG_FP64) == 0
