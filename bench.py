@@ -43,6 +43,10 @@ ELAS_MATVEC_BYTES_PER_VOXEL = {("fp64", "jacobi"): 17 * 8, ("fp64", "spectral"):
                                ("mixed", "jacobi"): 18 * 4, ("mixed", "spectral"): 15 * 4,
                                ("mixed", "scaled"): 15 * 4}
 ELAS_MATVEC_FLOPS_PER_VOXEL = 123
+# DRAM traffic of one k_elas32_matvec_spec launch at 256^3 (dram__bytes_read.sum +
+# dram__bytes_write.sum from an ncu capture of that kernel, mean of two launches: 637.0 MB
+# read + 368.0 MB written; profiles/elas32_matvec_spec_256.md).  Only for that kernel and size.
+MATVEC_SPEC_DRAM_BYTES_256 = 1.005e9
 
 
 def parse():
@@ -325,10 +329,13 @@ def main():
                     "hbm_gbs": gbs, "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"],
                     "share_of_step": share}
         kname = "k_elas32_matvec" if args.precond == "jacobi" else "k_elas32_matvec_spec"
+        traffic = (MATVEC_SPEC_DRAM_BYTES_256
+                   if kname == "k_elas32_matvec_spec" and args.n == 256 else None)
         return {"kernel": f"{kname} (FP32 19-point Navier-Lame operator, faces on the fly, "
                           "fused p-update, + <p, Ap>)",
                 "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
+                "traffic_per_voxel": traffic / V if traffic else None,
                 "peak_source": f"{peak_src} HBM copy bandwidth",
                 "bytes_per_voxel": ELAS_MATVEC_BYTES_PER_VOXEL[(precision, args.precond)],
                 "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"], "share_of_step": share}

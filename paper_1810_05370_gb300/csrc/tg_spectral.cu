@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(NT) k_spec_x_fwd(Spec<R> V, const R* __restric
 // e += alpha p, r -= alpha q (p as written by this iteration's operator kernel), the new r
 // staged straight into the transform, and <r, r> reduced over the launch; the last block
 // takes the convergence decision.  Saves the pass that re-read r.
-__global__ void __launch_bounds__(NT) k_spec_update_xfwd(Spec<float> V, Elas32 I) {
+__global__ void __launch_bounds__(NT, 4) k_spec_update_xfwd(Spec<float> V, Elas32 I) {
   using C = float2;
   if (!running(I.S)) return;
   const float alpha = (float)I.S->alpha;
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(NT) k_spec_update_xfwd(Spec<float> V, Elas32 I
   float rr = 0.0f;
   const int total = t.pb * n;
   for (int i0 = threadIdx.x; i0 < total; i0 += UB * blockDim.x) {
-    float ea[UB], eb[UB], ra[UB], rb[UB], pa[UB], pbv[UB], qa[UB], qb[UB];
+    float ea[UB], eb[UB], ra[UB], rb[UB], pa[UB], pbv[UB], qa[UB], qb[UB], sa[UB], sb[UB];
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
       const int idx = i0 + u * blockDim.x;
@@ -524,6 +524,8 @@ __global__ void __launch_bounds__(NT) k_spec_update_xfwd(Spec<float> V, Elas32 I
         pbv[u] = p[o + n];
         qa[u] = q[o];
         qb[u] = q[o + n];
+        sa[u] = sc ? __ldg(sc + o) : 1.0f;
+        sb[u] = sc ? __ldg(sc + o + n) : 1.0f;
       }
     }
 #pragma unroll
@@ -537,8 +539,7 @@ __global__ void __launch_bounds__(NT) k_spec_update_xfwd(Spec<float> V, Elas32 I
         r[o] = xa;
         r[o + n] = xb;
         rr += xa * xa + xb * xb;
-        a[(idx & (n - 1)) * es + (idx >> ln)] =
-            sc ? C{xa * __ldg(sc + o), xb * __ldg(sc + o + n)} : C{xa, xb};
+        a[(idx & (n - 1)) * es + (idx >> ln)] = C{xa * sa[u], xb * sb[u]};
       }
     }
   }
@@ -842,12 +843,38 @@ __global__ void __launch_bounds__(NT) k_spec_x_inv(Spec<R> V, R* z0, R* z1, R* z
   R* zs = comp == 0 ? z0 : (comp == 1 ? z1 : z2);
   const R* sc = V.s[comp];   // z = s A0^{-1} (s r) with the scaled preconditioner
   const size_t row0 = ((size_t)z * V.ny + y0) * n;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int l = idx >> ln, x = idx & (n - 1);
-    const size_t o = row0 + (size_t)(2 * l) * n + x;
-    const C f = F[x * es + l];
-    zs[o] = sc ? f.x * __ldg(sc + o) : f.x;
-    zs[o + n] = sc ? f.y * __ldg(sc + o + n) : f.y;
+  if (sc == nullptr) {
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int l = idx >> ln, x = idx & (n - 1);
+      const size_t o = row0 + (size_t)(2 * l) * n + x;
+      const C f = F[x * es + l];
+      zs[o] = f.x;
+      zs[o + n] = f.y;
+    }
+    return;
+  }
+  for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {   // LB scalings in flight
+    R sa[LB], sb[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) {
+        const size_t o = row0 + (size_t)(2 * (idx >> ln)) * n + (idx & (n - 1));
+        sa[u] = __ldg(sc + o);
+        sb[u] = __ldg(sc + o + n);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) {
+        const int l = idx >> ln, x = idx & (n - 1);
+        const size_t o = row0 + (size_t)(2 * l) * n + x;
+        const C f = F[x * es + l];
+        zs[o] = f.x * sa[u];
+        zs[o + n] = f.y * sb[u];
+      }
+    }
   }
 }
 
