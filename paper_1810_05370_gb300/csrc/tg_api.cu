@@ -25,8 +25,10 @@ enum Arr {
   A_DSUM_E0, A_DSUM_E1, A_DSUM_E2, A_DINV_E0, A_DINV_E1, A_DINV_E2,
   A_B0, A_B1, A_B2, A_DU0, A_DU1, A_DU2, A_ER0, A_ER1, A_ER2, A_EP0, A_EP1, A_EP2,
   A_EQ0, A_EQ1, A_EQ2,
-  // (hi, lo) FP32 pairs of u, mu, lambda for the double-FP32 residual (TG_MIXED only)
+  // (hi, lo) FP32 pairs of u, mu, lambda for the double-FP32 residual (TG_MIXED only), and of
+  // the diffusion faces and fields for the diffusion solves' double-FP32 residual
   A_UDF0, A_UDF1, A_UDF2, A_MUDF, A_LAMDF,
+  A_KFDF0, A_KFDF1, A_KFDF2, A_XDF0, A_XDF1, A_XDF2,
   A_COUNT
 };
 
@@ -376,6 +378,7 @@ struct tg_ctx {
   double t_matvec_ms;
   long long n_matvec;
   bool df_res;           // the mixed precision's residual in double-FP32 (df_residual_ok)
+  bool cn_df;            // ... and that of its diffusion solves (cn_df_ok)
   bool in_batch;         // owned by a batch (its persistent solvers read FP64 faces)
   cudaEvent_t pev[5];    // phase boundaries of a step (created on first use)
   bool pev_ok;
@@ -462,6 +465,11 @@ Cn3 cn_view(tg_ctx* X) {
   C.S = X->scal;
   C.partial = X->partial;
   C.counter = X->counter;
+  C.df = X->cn_df ? 1 : 0;
+  for (int r = 0; r < 3; ++r) {
+    C.xdf[r] = X->cn_df ? reinterpret_cast<float2*>(X->a[A_XDF0 + r]) : nullptr;
+    C.Kfdf[r] = X->cn_df ? reinterpret_cast<const float2*>(X->a[A_KFDF0 + r]) : nullptr;
+  }
   return C;
 }
 
@@ -507,6 +515,10 @@ constexpr double DF_RTOL_MIN = 1e-10;
 bool df_residual_ok(const tg_ctx* X) {
   return X->prec == TG_MIXED && !X->has_adjoint && !X->in_batch &&
          X->prm.rtol_elas >= DF_RTOL_MIN;
+}
+bool cn_df_ok(const tg_ctx* X) {
+  return X->prec == TG_MIXED && !X->has_adjoint && !X->in_batch &&
+         X->prm.rtol_diff >= DF_RTOL_MIN;
 }
 
 // S2: the three Crank-Nicolson solves (i, o, l) on the faces built by S0.
@@ -570,6 +582,12 @@ tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
   int inner_total[3] = {0, 0, 0};
   int sweeps = 0;
   CgScal out[3];
+  if (C.df) {   // (hi, lo) pairs of the fields for the first double-FP32 residual
+    double* const pk[3] = {reinterpret_cast<double*>(C.xdf[0]), reinterpret_cast<double*>(C.xdf[1]),
+                           reinterpret_cast<double*>(C.xdf[2])};
+    CK(launch_df_pack3(X->G, C.x, pk, X->stream));
+    X->launches += 1;
+  }
   for (;;) {
     CK(launch_cn_ir_residual(X->G, C, I, X->scal, sweeps == 0, TAU_INNER, MAX_SWEEPS, mask,
                              X->stream));
@@ -613,8 +631,6 @@ tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
   }
   return TG_OK;
 }
-
-// the spectral preconditioner is in use (requested and the workspace holds its buffers)
 
 Elas32 elas32_view(tg_ctx* X) {
   Elas32 I;
@@ -668,7 +684,10 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
   }
   k_cg_reset<<<1, 32, 0, X->stream>>>(Sout, 1, X->prm.rtol_elas, X->prm.maxit_elas);
   CK(cudaGetLastError());
-  CK(launch_elas32_coef(X->G, E, I, X->stream));
+  // with the double-FP32 residual the node coefficients came with the faces; only the
+  // (extrapolated) starting u is packed here
+  CK(launch_elas32_coef(X->G, E, I, X->stream,
+                        X->df_res ? ELAS32_U : ELAS32_NODES | ELAS32_DINV | ELAS32_U));
   X->launches += 2;
   const bool spec = spectral_on(X);
   Spec<float> V = X->sp32;   // the scaled preconditioner's view carries s
@@ -812,6 +831,13 @@ tg_status build_elas_coef(tg_ctx* X, bool force) {
                  X->a[A_ETA], X->stream));
   double* const u[3] = {S.u[0], S.u[1], S.u[2]};
   const Elas E = elas_view(X, u, nullptr);
+  if (X->df_res) {   // FP32 nodes and node pairs first, then the faces in double-FP32
+    const Elas32 I = elas32_view(X);
+    CK(launch_elas32_coef(X->G, E, I, X->stream, ELAS32_NODES));
+    CK(launch_elas_coef_df(X->G, X->dp, E, I, S.p, S.n, force, X->stream));
+    X->launches += 3;
+    return TG_OK;
+  }
   CK(launch_elas_coef(X->G, X->dp, E, S.p, S.n, force, X->stream));
   X->launches += 2;
   return TG_OK;
@@ -883,8 +909,9 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   // S0: K faces, CN diagonal and rho from the step's start
   phase_mark(X, 0);
   double* const Kf[3] = {X->a[A_KF0], X->a[A_KF1], X->a[A_KF2]};
+  double* const Kfdf[3] = {X->a[A_KFDF0], X->a[A_KFDF1], X->a[A_KFDF2]};
   CK(launch_diff_coef(G, X->dp, dt, S.g, S.w, S.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
-                      X->a[A_RHO], s));
+                      X->a[A_RHO], s, X->cn_df ? Kfdf : nullptr));
   X->launches += 1;   // S0 is two kernels (faces, diagonal)
   if (X->prec == TG_MIXED) {   // FP32 faces and diagonal of the inner diffusion solves
     F32Copy cp;
@@ -1217,6 +1244,7 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
     X->b32[b] = (prec == TG_MIXED || adjoint) ? (float*)(X->ws + L.arr32[b]) : nullptr;
   X->has_adjoint = adjoint;
   X->df_res = df_residual_ok(X);
+  X->cn_df = cn_df_ok(X);
   for (int c = 0; c < C_COUNT; ++c) X->adj[c] = adjoint ? (double*)(X->ws + L.adj[c]) : nullptr;
   X->grad = (double*)(X->ws + L.grad);
   X->partial = (double*)(X->ws + L.partial);
@@ -1345,6 +1373,7 @@ tg_status tg_set_params(tg_ctx* X, const tg_params* params) {
   if (X->has_adjoint && params->model != TG_MODEL_MULTISPECIES) return TG_ERR_ARG;
   X->prm = *params;
   X->df_res = df_residual_ok(X);
+  X->cn_df = cn_df_ok(X);
   X->dp = make_dev_params(params);
   return TG_OK;
 }
@@ -1892,6 +1921,7 @@ tg_status tg_batch_init(int32_t nsims, const tg_grid* grids, const tg_params* pa
     }
     X->in_batch = true;      // the batch's persistent residual kernel reads FP64 faces
     X->df_res = false;
+    X->cn_df = false;
     B->ctx.push_back(X);
     off += round_up(b);
   }

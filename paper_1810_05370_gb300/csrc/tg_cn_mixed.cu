@@ -69,6 +69,74 @@ __global__ void __launch_bounds__(NT) k_cn_ir_residual(Geo G, Cn3 C, Cn32 I, CgS
   }
 }
 
+// The same in double-FP32 arithmetic (C.df): fields, faces and right-hand sides as (hi, lo)
+// pairs, s = sum over the six faces of a (x_n - x_c) with error-free sums and products on the
+// FP32 units; the norms of a thread's voxels are summed in FP32, threads and blocks in FP64.
+__global__ void __launch_bounds__(NT) k_cn_ir_residual_df(Geo G, Cn3 C, Cn32 I, CgScal* Sout,
+                                                          int init, double tau_min,
+                                                          int max_sweeps, int mask) {
+  float sbb[3] = {0.0f, 0.0f, 0.0f}, srr[3] = {0.0f, 0.0f, 0.0f}, srz[3] = {0.0f, 0.0f, 0.0f};
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i < G.nx && j < G.ny) {
+    const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+    for (int k = k0; k < k1; ++k) {
+      const Nbr nb = make_nbr(G, i, j, k);
+      const long long c = nb.at(0, 0, 0);
+      const long long nbr[6] = {nb.at(1, 0, 0), nb.at(-1, 0, 0), nb.at(0, 1, 0),
+                                nb.at(0, -1, 0), nb.at(0, 0, 1), nb.at(0, 0, -1)};
+      const Df f[6] = {df_of(C.Kfdf[0][c]), df_of(C.Kfdf[0][nbr[1]]), df_of(C.Kfdf[1][c]),
+                       df_of(C.Kfdf[1][nbr[3]]), df_of(C.Kfdf[2][c]), df_of(C.Kfdf[2][nbr[5]])};
+      const float di = I.dinv[c];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        if (!((mask >> r) & 1)) continue;
+        const float2* x = C.xdf[r];
+        const Df xc = df_of(x[c]);
+        Df s = df_mul(f[0], df_sub(df_of(x[nbr[0]]), xc));
+#pragma unroll
+        for (int q = 1; q < 6; ++q) s = df_add(s, df_mul(f[q], df_sub(df_of(x[nbr[q]]), xc)));
+        float2* rhs2 = reinterpret_cast<float2*>(C.p[r]);
+        Df rhs;
+        if (init) {
+          rhs = df_add(xc, s);
+          rhs2[c] = make_float2(rhs.hi, rhs.lo);
+        } else {
+          rhs = df_of(rhs2[c]);
+        }
+        const Df res = df_add(df_sub(rhs, xc), s);
+        const float r32 = __fadd_rn(res.hi, res.lo);
+        I.r[r][c] = r32;
+        I.e[r][c] = 0.0f;
+        sbb[r] += rhs.hi * rhs.hi;
+        srr[r] += r32 * r32;
+        srz[r] += r32 * (di * r32);
+      }
+    }
+  }
+  double acc[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    acc[3 * r + 0] = (double)sbb[r];
+    acc[3 * r + 1] = (double)srr[r];
+    acc[3 * r + 2] = (double)srz[r];
+  }
+  double out[9];
+  if (reduce_last_block<9>(acc, C.partial, C.counter, out) && threadIdx.x == 0 &&
+      threadIdx.y == 0) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if ((mask >> r) & 1) {
+        elas_ir_residual_finalize(Sout[r], I.S[r], out[3 * r], out[3 * r + 1], out[3 * r + 2],
+                                  tau_min, max_sweeps);
+      } else {
+        cg_skip(Sout[r]);
+        cg_skip(I.S[r]);
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ bool active3(const Cn32& I, bool (&act)[3]) {
   bool any = false;
 #pragma unroll
@@ -222,8 +290,12 @@ __global__ void __launch_bounds__(NT) k_cn_ir_correct(long long n, Cn3 C, Cn32 I
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-      if ((mask >> r) & 1) C.x[r][c] += (double)I.e[r][c];
+    for (int r = 0; r < 3; ++r) {
+      if (!((mask >> r) & 1)) continue;
+      const double x = C.x[r][c] + (double)I.e[r][c];
+      C.x[r][c] = x;
+      if (C.df) C.xdf[r][c] = df_pack(x);   // the next residual's pairs
+    }
   }
 }
 
@@ -239,8 +311,12 @@ int flat_blocks(const Geo& G) {   // never more blocks than the partial-sum buff
 cudaError_t launch_cn_ir_residual(const Geo& G, const Cn3& C, const Cn32& I, CgScal* Sout,
                                   bool init, double tau_min, int max_sweeps, int mask,
                                   cudaStream_t st) {
-  k_cn_ir_residual<<<G.grid, dim3(BX, BY), 0, st>>>(G, C, I, Sout, init ? 1 : 0, tau_min,
-                                                    max_sweeps, mask);
+  if (C.df)
+    k_cn_ir_residual_df<<<G.grid, dim3(BX, BY), 0, st>>>(G, C, I, Sout, init ? 1 : 0, tau_min,
+                                                         max_sweeps, mask);
+  else
+    k_cn_ir_residual<<<G.grid, dim3(BX, BY), 0, st>>>(G, C, I, Sout, init ? 1 : 0, tau_min,
+                                                      max_sweeps, mask);
   return cudaGetLastError();
 }
 

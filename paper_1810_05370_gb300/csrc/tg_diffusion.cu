@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(NT) k_diff_faces(Geo G, DevParams P, double ha
                                                    const double* __restrict__ g,
                                                    const double* __restrict__ w,
                                                    const double* __restrict__ f, double* Kfx,
-                                                   double* Kfy, double* Kfz, double* rho) {
+                                                   double* Kfy, double* Kfz, double* rho,
+                                                   float2* dfx, float2* dfy, float2* dfz) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= G.nx || j >= G.ny) return;
@@ -40,9 +41,17 @@ __global__ void __launch_bounds__(NT) k_diff_faces(Geo G, DevParams P, double ha
     auto K = [&](long long e) { return node_K(P, g[e], w[e], f[e]); };
     const long long c = nb.at(0, 0, 0);
     const double kc = K(c);
-    Kfx[c] = sx * harmonic(kc, K(nb.at(1, 0, 0)));
-    Kfy[c] = sy * harmonic(kc, K(nb.at(0, 1, 0)));
-    Kfz[c] = sz * harmonic(kc, K(nb.at(0, 0, 1)));
+    const double fx = sx * harmonic(kc, K(nb.at(1, 0, 0)));
+    const double fy = sy * harmonic(kc, K(nb.at(0, 1, 0)));
+    const double fz = sz * harmonic(kc, K(nb.at(0, 0, 1)));
+    Kfx[c] = fx;
+    Kfy[c] = fy;
+    Kfz[c] = fz;
+    if (dfx) {   // (hi, lo) pairs for the mixed precision's double-FP32 residual
+      dfx[c] = df_pack(fx);
+      dfy[c] = df_pack(fy);
+      dfz[c] = df_pack(fz);
+    }
     rho[c] = P.rho_g * g[c] + P.rho_w * w[c];
   }
 }
@@ -147,9 +156,13 @@ __global__ void __launch_bounds__(NT) k_cn_pupdate(Geo G, Cn3 C) {
 
 cudaError_t launch_diff_coef(const Geo& G, const DevParams& P, double dt, const double* g,
                              const double* w, const double* f, double* const Kf[3], double* dsum,
-                             double* dinv, double* rho, cudaStream_t st) {
+                             double* dinv, double* rho, cudaStream_t st,
+                             double* const Kfdf[3]) {
+  float2* df[3] = {nullptr, nullptr, nullptr};
+  if (Kfdf)
+    for (int d = 0; d < 3; ++d) df[d] = reinterpret_cast<float2*>(Kfdf[d]);
   k_diff_faces<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, 0.5 * dt, g, w, f, Kf[0], Kf[1], Kf[2],
-                                                rho);
+                                                rho, df[0], df[1], df[2]);
   k_diff_diag<<<G.grid, dim3(BX, BY), 0, st>>>(G, Kf[0], Kf[1], Kf[2], dsum, dinv);
   return cudaGetLastError();
 }

@@ -336,7 +336,8 @@ template <typename R> size_t spec_smem_z(const Spec<R>& V) {
 // S0: diffusion faces (scaled by dt/(2 h_d^2)), Jacobi diagonal of the CN operator, rho.
 cudaError_t launch_diff_coef(const Geo&, const DevParams&, double dt, const double* g,
                              const double* w, const double* f, double* const Kf[3], double* dsum,
-                             double* dinv, double* rho, cudaStream_t st);
+                             double* dinv, double* rho, cudaStream_t st,
+                             double* const Kfdf[3] = nullptr);   // (hi, lo) pairs, optional
 
 struct Cn3 {   // three simultaneous CN solves sharing one operator
   double* x[3];
@@ -349,6 +350,11 @@ struct Cn3 {   // three simultaneous CN solves sharing one operator
   CgScal* S;           // 3 entries
   double* partial;
   unsigned int* counter;
+  // double-FP32 residual of the mixed precision (df != 0): (hi, lo) pairs of the fields and
+  // of the faces; the right-hand sides in p are then pairs as well
+  int df;
+  float2* xdf[3];
+  const float2* Kfdf[3];
 };
 cudaError_t launch_cn_init(const Geo&, const Cn3&, cudaStream_t st, int mask = 7);
 cudaError_t launch_cn_iter(const Geo&, const Cn3&, cudaStream_t st);
@@ -495,6 +501,9 @@ __device__ __forceinline__ double elas_row64(const Geo& G, const Nbr& nb, long l
 
 cudaError_t launch_elas_coef(const Geo&, const DevParams&, const Elas&, const double* p,
                              const double* n, bool force, cudaStream_t st);
+// the same as (hi, lo) pairs from the node pairs E.mudf, E.lamdf (E.df); I.dinv if E.jacobi
+cudaError_t launch_elas_coef_df(const Geo&, const DevParams&, const Elas&, const Elas32& I,
+                                const double* p, const double* n, bool force, cudaStream_t st);
 cudaError_t launch_elas_init(const Geo&, const Elas&, bool rhs_is_minus_b, cudaStream_t st);
 cudaError_t launch_elas_matvec(const Geo&, const Elas&, cudaStream_t st);
 cudaError_t launch_elas_update(const Geo&, const Elas&, cudaStream_t st);   // update + p-update
@@ -506,7 +515,9 @@ cudaError_t launch_elas_finish(const Geo&, const Elas&, double inv_dt, bool zero
 
 // mixed precision (tg_mixed.cu)
 cudaError_t launch_to_f32(long long n, const F32Copy& c, cudaStream_t st);
-cudaError_t launch_elas32_coef(const Geo&, const Elas&, const Elas32&, cudaStream_t st);
+constexpr int ELAS32_NODES = 1, ELAS32_DINV = 2, ELAS32_U = 4;
+cudaError_t launch_elas32_coef(const Geo&, const Elas&, const Elas32&, cudaStream_t st,
+                              int parts = ELAS32_NODES | ELAS32_DINV | ELAS32_U);
 cudaError_t launch_df_pack3(const Geo&, const double* const b[3], double* const out[3],
                             cudaStream_t st);
 cudaError_t launch_elas_ir_residual(const Geo&, const Elas&, const Elas32&, CgScal* Sout,

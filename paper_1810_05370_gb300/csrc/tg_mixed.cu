@@ -29,22 +29,27 @@ __global__ void __launch_bounds__(NT) k_to_f32(long long n, F32Copy c) {
 }
 
 // FP32 node coefficients and Jacobi inverse diagonal from the FP64 ones; with the double-FP32
-// residual also the (hi, lo) pairs of mu, lambda and the starting u
-__global__ void __launch_bounds__(NT) k_elas32_coef(long long n, Elas E, Elas32 I) {
+// residual also the (hi, lo) pairs of mu, lambda and the starting u.  parts selects
+// ELAS32_NODES (mu, lambda, eta and their pairs), ELAS32_DINV, ELAS32_U.
+__global__ void __launch_bounds__(NT) k_elas32_coef(long long n, Elas E, Elas32 I, int parts) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-    const double mu = E.mu[e], lam = E.lam[e];
-    I.mu[e] = (float)mu;
-    I.lam[e] = (float)lam;
-    I.eta[e] = (float)E.eta[e];
-    if (E.jacobi) {
+    if (parts & ELAS32_NODES) {
+      const double mu = E.mu[e], lam = E.lam[e];
+      I.mu[e] = (float)mu;
+      I.lam[e] = (float)lam;
+      I.eta[e] = (float)E.eta[e];
+      if (E.df) {
+        E.mudf[e] = df_pack(mu);
+        E.lamdf[e] = df_pack(lam);
+      }
+    }
+    if ((parts & ELAS32_DINV) && E.jacobi) {
       I.dinv[0][e] = (float)E.dinv[0][e];
       I.dinv[1][e] = (float)E.dinv[1][e];
       I.dinv[2][e] = (float)E.dinv[2][e];
     }
-    if (E.df) {
-      E.mudf[e] = df_pack(mu);
-      E.lamdf[e] = df_pack(lam);
+    if ((parts & ELAS32_U) && E.df) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) E.udf[a][e] = df_pack(E.u[a][e]);
     }
@@ -279,8 +284,9 @@ cudaError_t launch_to_f32(long long n, const F32Copy& c, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_elas32_coef(const Geo& G, const Elas& E, const Elas32& I, cudaStream_t st) {
-  k_elas32_coef<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, I);
+cudaError_t launch_elas32_coef(const Geo& G, const Elas& E, const Elas32& I, cudaStream_t st,
+                              int parts) {
+  k_elas32_coef<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, I, parts);
   return cudaGetLastError();
 }
 
