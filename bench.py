@@ -34,19 +34,19 @@ FIELDS = ("p", "i", "n", "g", "w", "f", "o", "l", "bg", "ux", "uy", "uz", "vx", 
 # Algorithmic traffic and arithmetic of the elasticity operator kernel, per voxel and launch.
 # FP64 path: reads p (3 comps), face coefficients (lambda+2mu)/h^2 and mu/h^2 (3 + 3), Jacobi
 # diagonal (3), node mu and lambda (2); writes q (3): 17 FP64 arrays; 123 FP64 flops.
-# Mixed path (the CG p-update is fused into the operator kernel): with Jacobi it reads r,
-# D^{-1}, p_old (3 each) and node mu, lambda, eta and writes p_new and q (3 each): 18 FP32
-# arrays; with the spectral preconditioner the preconditioned residual z (3) replaces r and
-# D^{-1} (6): 15 FP32 arrays.
+# Mixed path with Jacobi (the CG p-update fused into the operator kernel): reads r, D^{-1},
+# p_old (3 each) and node mu, lambda, eta and writes p_new and q (3 each): 18 FP32 arrays.
+# With a spectral preconditioner the p-update is fused into the preconditioner's last pass,
+# so the operator kernel reads p (3) and mu, lambda, eta and writes q (3): 9 FP32 arrays.
 ELAS_MATVEC_BYTES_PER_VOXEL = {("fp64", "jacobi"): 17 * 8, ("fp64", "spectral"): 17 * 8,
                                ("fp64", "scaled"): 17 * 8,
-                               ("mixed", "jacobi"): 18 * 4, ("mixed", "spectral"): 15 * 4,
-                               ("mixed", "scaled"): 15 * 4}
+                               ("mixed", "jacobi"): 18 * 4, ("mixed", "spectral"): 9 * 4,
+                               ("mixed", "scaled"): 9 * 4}
 ELAS_MATVEC_FLOPS_PER_VOXEL = 123
 # DRAM traffic of one k_elas32_matvec_spec launch at 256^3 (dram__bytes_read.sum +
-# dram__bytes_write.sum from an ncu capture of that kernel, mean of two launches: 637.0 MB
-# read + 368.0 MB written; profiles/elas32_matvec_spec_256.md).  Only for that kernel and size.
-MATVEC_SPEC_DRAM_BYTES_256 = 1.005e9
+# dram__bytes_write.sum from an ncu capture of that kernel; profiles/elas32_matvec_spec_256.md).
+# None until the current form of the kernel has been captured.
+MATVEC_SPEC_DRAM_BYTES_256 = None
 
 
 def parse():

@@ -714,8 +714,11 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
     if (sweeps >= MAX_SWEEPS || inner_total >= X->prm.maxit_elas) return fail(X, TG_ERR_NOCONV);
     CK(launch_elas32_scale_r(X->G, I, X->stream));
     X->launches += 1;
-    if (spec) {   // z = P r and <r, z> for the inner solve's first direction
-      CK(launch_spectral(V, r32, X->z32, I.S, X->stream));
+    if (spec) {   // p = P r and <r, P r> for the inner solve's first direction
+      PUpd<float> pu;
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 3; ++a) pu.p[b][a] = I.p[b][a];
+      CK(launch_spectral(V, r32, X->z32, I.S, X->stream, &pu));
       X->launches += 5;
     }
     CgScal host[1];

@@ -319,6 +319,14 @@ struct Spec {
   int nb_partial;             // capacity of partial, in doubles
 };
 
+// The CG p-update fused into the x inverse pass (mixed precision): the pass writes the new
+// search direction p = z + beta p_old instead of z, into the buffer of the two that the
+// iteration's operator kernel reads (they alternate with the iteration count S->it).
+template <typename R>
+struct PUpd {
+  R* p[2][3];
+};
+
 // shared memory of each pass (bytes): the line length's twiddles and two line buffers
 template <typename R> size_t spec_smem_x(const Spec<R>& V) {   // lines padded to pb + 1
   return (1 + 2 * ((size_t)V.pb + 1)) * V.nx * sizeof(typename CxOf<R>::T);
@@ -544,7 +552,7 @@ cudaError_t launch_spec_mean(long long n, const double* mu, const double* lam,
                              unsigned int* counter, cudaStream_t st);
 template <typename R>
 cudaError_t launch_spectral(const Spec<R>&, const R* const r[3], R* const z[3], CgScal* S,
-                            cudaStream_t st);
+                            cudaStream_t st, const PUpd<R>* pu = nullptr);
 cudaError_t launch_elas32_matvec_spec(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_spectral_update(const Spec<float>&, const Elas32&, float* const z[3],
                                    cudaStream_t st);

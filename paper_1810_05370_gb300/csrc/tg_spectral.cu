@@ -795,10 +795,11 @@ __global__ void __launch_bounds__(ZR_COLS * P, 512 / (ZR_COLS * P))
 // ---------------------------------------------------------------------------- x inverse
 // block (pair tile, z, component): the half spectra of rows y0 + 2l, y0 + 2l + 1 form
 // C[k] = A[k] + i B[k] over all k (Hermitian extension); the inverse transform is
-// a + i b.  Writes z and accumulates <r, z>; the last block finishes the CG scalars.
-template <typename R>
-__global__ void __launch_bounds__(NT) k_spec_x_inv(Spec<R> V, R* z0, R* z1, R* z2,
-                                                   const CgScal* S) {
+// a + i b.  Writes z = s (inverse transform) (s = 1 unscaled), or with PU the new search
+// direction p = z + beta p_old (beta = 0 on a solve's first iteration).
+template <typename R, bool PUP>
+__global__ void __launch_bounds__(NT, PUP ? 4 : 2) k_spec_x_inv(Spec<R> V, R* z0, R* z1, R* z2,
+                                                                const CgScal* S, PUpd<R> PU) {
   using C = typename CxOf<R>::T;
   if (spec_skip<R>(S)) return;
   const int n = V.nx, ln = ilog2(n), half = n / 2, pb = V.pb, es = pb + 1;
@@ -840,28 +841,32 @@ __global__ void __launch_bounds__(NT) k_spec_x_inv(Spec<R> V, R* z0, R* z1, R* z
   }
   __syncthreads();
   const C* F = fft_lines<+1>(a, b, ln, ilog2(pb), 1, 1, es, tw);
-  R* zs = comp == 0 ? z0 : (comp == 1 ? z1 : z2);
+  R* out = comp == 0 ? z0 : (comp == 1 ? z1 : z2);
+  const R* pold = nullptr;
+  R beta = (R)0;
+  if (PUP) {   // selects written out: no indexed copy of the parameter arrays
+    const int it = S->it;
+    R* const p0 = comp == 0 ? PU.p[0][0] : (comp == 1 ? PU.p[0][1] : PU.p[0][2]);
+    R* const p1 = comp == 0 ? PU.p[1][0] : (comp == 1 ? PU.p[1][1] : PU.p[1][2]);
+    out = (it & 1) ? p0 : p1;
+    if (it > 0) {
+      pold = (it & 1) ? p1 : p0;
+      beta = (R)S->beta;
+    }
+  }
   const R* sc = V.s[comp];   // z = s A0^{-1} (s r) with the scaled preconditioner
   const size_t row0 = ((size_t)z * V.ny + y0) * n;
-  if (sc == nullptr) {
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int l = idx >> ln, x = idx & (n - 1);
-      const size_t o = row0 + (size_t)(2 * l) * n + x;
-      const C f = F[x * es + l];
-      zs[o] = f.x;
-      zs[o + n] = f.y;
-    }
-    return;
-  }
-  for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {   // LB scalings in flight
-    R sa[LB], sb[LB];
+  for (int i0 = threadIdx.x; i0 < total; i0 += LB * blockDim.x) {   // LB loads in flight
+    R sa[LB], sb[LB], pa[LB], pbv[LB];
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
       const int idx = i0 + u * blockDim.x;
       if (idx < total) {
         const size_t o = row0 + (size_t)(2 * (idx >> ln)) * n + (idx & (n - 1));
-        sa[u] = __ldg(sc + o);
-        sb[u] = __ldg(sc + o + n);
+        sa[u] = sc ? __ldg(sc + o) : (R)1;
+        sb[u] = sc ? __ldg(sc + o + n) : (R)1;
+        pa[u] = (PUP && pold) ? pold[o] : (R)0;
+        pbv[u] = (PUP && pold) ? pold[o + n] : (R)0;
       }
     }
 #pragma unroll
@@ -871,8 +876,8 @@ __global__ void __launch_bounds__(NT) k_spec_x_inv(Spec<R> V, R* z0, R* z1, R* z
         const int l = idx >> ln, x = idx & (n - 1);
         const size_t o = row0 + (size_t)(2 * l) * n + x;
         const C f = F[x * es + l];
-        zs[o] = f.x * sa[u];
-        zs[o + n] = f.y * sb[u];
+        out[o] = PUP ? f.x * sa[u] + beta * pa[u] : f.x * sa[u];
+        out[o + n] = PUP ? f.y * sb[u] + beta * pbv[u] : f.y * sb[u];
       }
     }
   }
@@ -965,7 +970,10 @@ cudaError_t spec_prepare(const Spec<R>& V) {
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   e = cudaFuncSetAttribute(k_spec_x_fwd<R>, A, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_update_xfwd, A, optin);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_x_inv<R>, A, optin);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_x_inv<R, false>, A, optin);
+  if constexpr (sizeof(R) == 4) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_x_inv<R, true>, A, optin);
+  }
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_y<R, -1>, A, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_y<R, +1>, A, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_z<R>, A, optin);
@@ -1020,14 +1028,22 @@ void launch_spec_z(const Spec<R>& V, CgScal* S, cudaStream_t st) {
 
 template <typename R>
 cudaError_t launch_spectral(const Spec<R>& V, const R* const r[3], R* const z[3], CgScal* S,
-                            cudaStream_t st) {
+                            cudaStream_t st, const PUpd<R>* pu) {
   const dim3 gx(V.ny / (2 * V.pb), V.nz, 3);
   const dim3 gy((V.nxh + V.tx - 1) / V.tx, V.nz, 3);
   k_spec_x_fwd<R><<<gx, NT, spec_smem_x(V), st>>>(V, r[0], r[1], r[2], S);
   k_spec_y<R, -1><<<gy, NT, spec_smem_y(V), st>>>(V, S);
   launch_spec_z(V, S, st);
   k_spec_y<R, +1><<<gy, NT, spec_smem_y(V), st>>>(V, S);
-  k_spec_x_inv<R><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S);
+  PUpd<R> P = {};
+  if constexpr (sizeof(R) == 4) {
+    if (pu) {
+      P = *pu;
+      k_spec_x_inv<R, true><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S, P);
+      return cudaGetLastError();
+    }
+  }
+  k_spec_x_inv<R, false><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S, P);
   return cudaGetLastError();
 }
 
@@ -1041,7 +1057,10 @@ cudaError_t launch_spectral_update(const Spec<float>& V, const Elas32& I, float*
   k_spec_y<float, -1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S);
   launch_spec_z(V, I.S, st);
   k_spec_y<float, +1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S);
-  k_spec_x_inv<float><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], I.S);
+  PUpd<float> P;   // p = z + beta p_old straight from the last pass
+  for (int b = 0; b < 2; ++b)
+    for (int a = 0; a < 3; ++a) P.p[b][a] = I.p[b][a];
+  k_spec_x_inv<float, true><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], I.S, P);
   return cudaGetLastError();
 }
 
@@ -1054,8 +1073,10 @@ template cudaError_t launch_spec_scale<double>(const Geo&, const Spec<double>&, 
 template cudaError_t launch_spec_tables<float>(const Spec<float>&, const double[3], cudaStream_t);
 template cudaError_t launch_spec_tables<double>(const Spec<double>&, const double[3], cudaStream_t);
 template cudaError_t launch_spectral<float>(const Spec<float>&, const float* const[3],
-                                            float* const[3], CgScal*, cudaStream_t);
+                                            float* const[3], CgScal*, cudaStream_t,
+                                            const PUpd<float>*);
 template cudaError_t launch_spectral<double>(const Spec<double>&, const double* const[3],
-                                             double* const[3], CgScal*, cudaStream_t);
+                                             double* const[3], CgScal*, cudaStream_t,
+                                             const PUpd<double>*);
 
 }  // namespace tg

@@ -161,8 +161,9 @@ __device__ __forceinline__ float row_tile(const Tile32& T, const Cell& t, const 
 
 // One tile (bx, by, bz) of the FP32 operator with the fused p-update, for CG iteration `it`
 // with coefficient beta; returns this thread's FP32 part of <p_new, A p_new>.  T is the
-// block's shared staging area.  The preconditioned residual is D^{-1} r (Jacobi) or, with
-// SPEC, the array z the spectral preconditioner wrote.
+// block's shared staging area.  With Jacobi the tile forms p_new = D^{-1} r + beta p_old
+// while staging and writes it; with SPEC the spectral preconditioner's last pass already
+// wrote p_new (into the buffer p[(it & 1) ^ 1]), which the tile only reads.
 template <bool COH, bool SPEC = false>
 __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32& K,
                                                     const Elas32& I, int it, double beta_d,
@@ -198,8 +199,12 @@ __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32
   auto fetch = [&](long long g, Staged& v) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float z = SPEC ? ldf<COH>(I.z[a] + g) : __ldg(I.dinv[a] + g) * ldf<COH>(I.r[a] + g);
-      v.p[a] = first ? z : z + beta * ldf<COH>(po[a] + g);
+      if (SPEC) {   // the preconditioner's last pass wrote p_new = z + beta p_old
+        v.p[a] = ldf<COH>(pn[a] + g);
+      } else {
+        const float z = __ldg(I.dinv[a] + g) * ldf<COH>(I.r[a] + g);
+        v.p[a] = first ? z : z + beta * ldf<COH>(po[a] + g);
+      }
     }
     v.mu = __ldg(I.mu + g);
     v.la = __ldg(I.lam + g);
@@ -258,9 +263,11 @@ __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32
       const float q1 = row_tile<1>(T, t, f, K.sc);
       const float q2 = row_tile<2>(T, t, f, K.sc);
       const float p0 = tp(T, t, 0, 0, 0, 0), p1 = tp(T, t, 1, 0, 0, 0), p2 = tp(T, t, 2, 0, 0, 0);
-      pn[0][c] = p0;
-      pn[1][c] = p1;
-      pn[2][c] = p2;
+      if (!SPEC) {
+        pn[0][c] = p0;
+        pn[1][c] = p1;
+        pn[2][c] = p2;
+      }
       I.q[0][c] = q0;
       I.q[1][c] = q1;
       I.q[2][c] = q2;
