@@ -43,10 +43,12 @@ ELAS_MATVEC_BYTES_PER_VOXEL = {("fp64", "jacobi"): 17 * 8, ("fp64", "spectral"):
                                ("mixed", "jacobi"): 18 * 4, ("mixed", "spectral"): 9 * 4,
                                ("mixed", "scaled"): 9 * 4}
 ELAS_MATVEC_FLOPS_PER_VOXEL = 123
-# DRAM traffic of one k_elas32_matvec_spec launch at 256^3 (dram__bytes_read.sum +
-# dram__bytes_write.sum from an ncu capture of that kernel; profiles/elas32_matvec_spec_256.md).
-# None until the current form of the kernel has been captured.
-MATVEC_SPEC_DRAM_BYTES_256 = None
+# DRAM traffic per launch at 256^3 with the scaled spectral preconditioner
+# (dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture, mean of two launches;
+# profiles/elas32_matvec_spec_256.md): the operator kernel 415.7 + 174.9 MB, the fused update
+# + x forward pass 1012.4 + 558.6 MB.  Only for these kernels in this configuration.
+MATVEC_SPEC_DRAM_BYTES_256 = 590.55e6
+UPDATE_XFWD_DRAM_BYTES_256 = 1570.92e6
 
 
 def parse():
@@ -88,7 +90,8 @@ def load_peaks():
 
 
 # GB300 FP64 peak: not in the measured-peaks file.  Derived from the FP64 issue rate of the
-# SM and the maximum SM clock ("FP64 roof").
+# SM (2 DFMA per clock) and the maximum SM clock; a probe of independent FMA chains reaches
+# 95 % of it.
 FP64_PEAK_TFLOPS = 1.26
 
 
@@ -281,13 +284,15 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(sim.stream)
-        agg = {"launches": 0, "t_mv": 0.0, "n_mv": 0, "it_elas": [], "it_elas_outer": [],
-               "it_diff": [], "phase_ms": [0.0, 0.0, 0.0, 0.0]}
+        agg = {"launches": 0, "t_mv": 0.0, "n_mv": 0, "t_up": 0.0, "n_up": 0, "it_elas": [],
+               "it_elas_outer": [], "it_diff": [], "phase_ms": [0.0, 0.0, 0.0, 0.0]}
         for _ in range(args.steps):
             s = sim.step(args.dt)
             agg["launches"] += s["launches"]
             agg["t_mv"] += s["t_elas_matvec_ms"]
             agg["n_mv"] += s["n_elas_matvec"]
+            agg["t_up"] += s["t_spec_update_ms"]
+            agg["n_up"] += s["n_spec_update"]
             agg["it_elas"].append(s["it_elas"])
             agg["it_elas_outer"].append(s["it_elas_outer"])
             agg["it_diff"].append(s["it_diff"])
@@ -322,25 +327,47 @@ def main():
         share = agg["t_mv"] / agg["ms"] if agg["ms"] > 0 else None
         if precision == "fp64":
             tfl = ELAS_MATVEC_FLOPS_PER_VOXEL * V / (avg_ms * 1e-3) / 1e12
-            return {"kernel": "k_elas_matvec (FP64 19-point Navier-Lame operator + <p, Ap>)",
-                    "bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "derived FP64 roof (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                    "hbm_gbs": gbs, "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"],
-                    "share_of_step": share}
+            r64 = {"kernel": "k_elas_matvec (FP64 19-point Navier-Lame operator + <p, Ap>)",
+                   "bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS,
+                   "unit": "TFLOP/s", "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
+                   "peak_source": "derived FP64 roof (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                   "hbm_gbs": gbs, "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"],
+                   "share_of_step": share}
+            return r64, [r64]
         kname = "k_elas32_matvec" if args.precond == "jacobi" else "k_elas32_matvec_spec"
-        traffic = (MATVEC_SPEC_DRAM_BYTES_256
-                   if kname == "k_elas32_matvec_spec" and args.n == 256 else None)
-        return {"kernel": f"{kname} (FP32 19-point Navier-Lame operator, faces on the fly, "
-                          "fused p-update, + <p, Ap>)",
-                "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
-                "traffic_per_voxel": traffic / V if traffic else None,
-                "peak_source": f"{peak_src} HBM copy bandwidth",
-                "bytes_per_voxel": ELAS_MATVEC_BYTES_PER_VOXEL[(precision, args.precond)],
-                "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"], "share_of_step": share}
+        captured = args.n == 256 and args.precond == "scaled"
+        traffic = MATVEC_SPEC_DRAM_BYTES_256 if kname == "k_elas32_matvec_spec" and captured else None
+        mv = {"kernel": f"{kname} (FP32 19-point Navier-Lame operator, faces on the fly, "
+                        "+ <p, Ap>)",
+              "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+              "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
+              "traffic_per_voxel": traffic / V if traffic else None,
+              "peak_source": f"{peak_src} HBM copy bandwidth",
+              "bytes_per_voxel": ELAS_MATVEC_BYTES_PER_VOXEL[(precision, args.precond)],
+              "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"], "share_of_step": share}
+        if agg["n_up"] == 0:
+            return mv, [mv]
+        # the spectral CG's update fused with the first FFT pass: e, p, r, q read and e, r
+        # written (3 components each, FP32), the half spectrum written (nx/2 + 1 complex FP32
+        # modes per row and component), and with the scaled preconditioner s read
+        n = args.n
+        up_bpv = 6 * 12 + 3 * 8 * (n // 2 + 1) / n + (12 if args.precond == "scaled" else 0)
+        up_ms = agg["t_up"] / agg["n_up"]
+        up_gbs = up_bpv * V / (up_ms * 1e-3) / 1e9
+        up = {"kernel": "k_spec_update_xfwd (CG update e += alpha p, r -= alpha q, <r, r>, fused "
+                        "with the x forward FFT pass of the preconditioner)",
+              "bound": "hbm", "achieved": up_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+              "frac": up_gbs / peaks["hbm_gbs"],
+              "traffic": UPDATE_XFWD_DRAM_BYTES_256 if captured else None,
+              "traffic_per_voxel": UPDATE_XFWD_DRAM_BYTES_256 / V if captured else None,
+              "peak_source": f"{peak_src} HBM copy bandwidth", "bytes_per_voxel": up_bpv,
+              "avg_launch_ms": up_ms, "launches_timed": agg["n_up"],
+              "share_of_step": agg["t_up"] / agg["ms"] if agg["ms"] > 0 else None}
+        # the dominant kernel is the one with the larger share of the step
+        top = up if agg["t_up"] > agg["t_mv"] else mv
+        return top, [mv, up]
 
-    roof = roofline(agg, args.precision)
+    roof, roof_all = roofline(agg, args.precision)
 
     # ---------------------------------------------------------------- end to end (host buffers)
     e2e = None
@@ -382,7 +409,7 @@ def main():
                  "solver": {"it_elas_per_step": ag_o["it_elas"],
                             "it_elas_outer_per_step": ag_o["it_elas_outer"],
                             "it_diff_per_step": ag_o["it_diff"]},
-                 "roofline": roofline(ag_o, oprec), "gpu_launches": ag_o["launches"]}
+                 "roofline": roofline(ag_o, oprec)[0], "gpu_launches": ag_o["launches"]}
         sim_o.close()
         sim = None
 
@@ -470,6 +497,7 @@ def main():
                        "it_elas_outer_per_step": agg["it_elas_outer"],
                        "it_diff_per_step": agg["it_diff"]},
             "roofline": roof,
+            "roofline_kernels": roof_all,
             "compare": other,
             "adjoint": adjoint,
             "single_species": single,

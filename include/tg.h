@@ -137,6 +137,9 @@ typedef struct {
   int64_t n_elas_matvec;     /*   kernel over the launches that did work, and their count    */
   double t_phase_ms[4];      /* with timing on: device time of S0-S1, S2, S3-S5 and S6-S7     */
                              /*   (event to event on the stream), summed over the call's steps */
+  double t_spec_update_ms;   /* with timing on, TG_MIXED with a spectral preconditioner: summed */
+  int64_t n_spec_update;     /*   duration of the CG update fused with the first FFT pass and  */
+                             /*   its count (the launches that did work)                       */
 } tg_stats;
 
 /* Bytes of workspace tg_init needs for this grid, parameters and precision (0 on invalid

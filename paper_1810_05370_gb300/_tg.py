@@ -59,7 +59,8 @@ class tg_stats(C.Structure):
                 ("relres_elas", C.c_double), ("it_diff_total", C.c_int64),
                 ("it_elas_total", C.c_int64), ("launches", C.c_int64),
                 ("t_elas_matvec_ms", C.c_double), ("n_elas_matvec", C.c_int64),
-                ("t_phase_ms", C.c_double * 4)]
+                ("t_phase_ms", C.c_double * 4),
+                ("t_spec_update_ms", C.c_double), ("n_spec_update", C.c_int64)]
 
 
 class tg_batch_stats(C.Structure):
@@ -170,7 +171,9 @@ def stats_dict(s: tg_stats) -> dict:
             "relres_elas": float(s.relres_elas), "it_diff_total": int(s.it_diff_total),
             "it_elas_total": int(s.it_elas_total), "launches": int(s.launches),
             "t_elas_matvec_ms": float(s.t_elas_matvec_ms), "n_elas_matvec": int(s.n_elas_matvec),
-            "t_phase_ms": [float(x) for x in s.t_phase_ms]}
+            "t_phase_ms": [float(x) for x in s.t_phase_ms],
+            "t_spec_update_ms": float(s.t_spec_update_ms),
+            "n_spec_update": int(s.n_spec_update)}
 
 
 # ----------------------------------------------------------------------------- same-name calls

@@ -377,6 +377,8 @@ struct tg_ctx {
   std::vector<cudaEvent_t> ev;   // pairs (start, stop) per operator launch of one solve
   double t_matvec_ms;
   long long n_matvec;
+  double t_update_ms;    // the mixed spectral CG's fused update + x forward pass
+  long long n_update;
   bool df_res;           // the mixed precision's residual in double-FP32 (df_residual_ok)
   bool cn_df;            // ... and that of its diffusion solves (cn_df_ok)
   bool in_batch;         // owned by a batch (its persistent solvers read FP64 faces)
@@ -436,9 +438,10 @@ tg_status drive_cg(tg_ctx* X, IterFn iter, const CgScal* dev, int nsolves, int m
   }
 }
 
-// grow the event pool to hold `pairs` (start, stop) pairs; false if events cannot be created
-bool ensure_events(tg_ctx* X, int pairs) {
-  while ((int)X->ev.size() < 2 * pairs) {
+// grow the event pool to hold the events of `iters` timed iterations (three each: before and
+// after the operator kernel, after the update pass); false if events cannot be created
+bool ensure_events(tg_ctx* X, int iters) {
+  while ((int)X->ev.size() < 3 * iters) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return false;
     X->ev.push_back(e);
@@ -653,12 +656,16 @@ Elas32 elas32_view(tg_ctx* X) {
 }
 
 // add the event-timed operator launches that did work (the first `did` of `recorded`)
-void harvest_timing(tg_ctx* X, int recorded, int did) {
+void harvest_timing(tg_ctx* X, int recorded, int did, bool update = false) {
   for (int q = 0; q < std::min(recorded, did); ++q) {
     float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, X->ev[2 * q], X->ev[2 * q + 1]) == cudaSuccess) {
+    if (cudaEventElapsedTime(&ms, X->ev[3 * q], X->ev[3 * q + 1]) == cudaSuccess) {
       X->t_matvec_ms += ms;
       X->n_matvec += 1;
+    }
+    if (update && cudaEventElapsedTime(&ms, X->ev[3 * q + 1], X->ev[3 * q + 2]) == cudaSuccess) {
+      X->t_update_ms += ms;
+      X->n_update += 1;
     }
   }
 }
@@ -728,18 +735,18 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
       X->launches += spec ? 6 : 2;
       const bool timed = X->timing && ensure_events(X, q + 1);
       if (timed) {
-        cudaEventRecord(X->ev[2 * q], X->stream);
+        cudaEventRecord(X->ev[3 * q], X->stream);
         recorded = q + 1;
       }
       cudaError_t e = spec ? launch_elas32_matvec_spec(X->G, I, X->stream)
                            : launch_elas32_matvec(X->G, I, X->stream);
-      if (timed) cudaEventRecord(X->ev[2 * q + 1], X->stream);
+      if (timed) cudaEventRecord(X->ev[3 * q + 1], X->stream);
       if (e != cudaSuccess) return e;
       if (!spec) return launch_elas32_update(X->G, I, X->stream);
-      return launch_spectral_update(V, I, X->z32, X->stream);
+      return launch_spectral_update(V, I, X->z32, X->stream, timed ? X->ev[3 * q + 2] : nullptr);
     }, I.S, 1, X->prm.maxit_elas, X->prev_it_inner[slot], host);
     if (s != TG_OK) return s;
-    harvest_timing(X, recorded, host[0].it);
+    harvest_timing(X, recorded, host[0].it, spec);
     X->prev_it_inner[slot] = host[0].it;
     inner_total += host[0].it;
     if (host[0].status == CG_NONFINITE) return fail(X, TG_ERR_NONFINITE);
@@ -797,11 +804,11 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
     X->launches += spec ? 8 : 3;
     const bool timed = X->timing && ensure_events(X, q + 1);
     if (timed) {
-      cudaEventRecord(X->ev[2 * q], X->stream);
+      cudaEventRecord(X->ev[3 * q], X->stream);
       recorded = q + 1;
     }
     cudaError_t e = launch_elas_matvec(X->G, E, X->stream);
-    if (timed) cudaEventRecord(X->ev[2 * q + 1], X->stream);
+    if (timed) cudaEventRecord(X->ev[3 * q + 1], X->stream);
     if (e != cudaSuccess) return e;
     if (!spec) return launch_elas_update(X->G, E, X->stream);
     e = launch_elas_update_spec(X->G, E, X->stream);
@@ -850,6 +857,8 @@ void reset_profile(tg_ctx* X) {
   X->launches = 0;
   X->t_matvec_ms = 0.0;
   X->n_matvec = 0;
+  X->t_update_ms = 0.0;
+  X->n_update = 0;
   for (int q = 0; q < 4; ++q) X->t_phase[q] = 0.0;
 }
 
@@ -857,6 +866,8 @@ void fill_profile(tg_ctx* X, tg_stats* stats) {
   stats->launches = X->launches;
   stats->t_elas_matvec_ms = X->t_matvec_ms;
   stats->n_elas_matvec = X->n_matvec;
+  stats->t_spec_update_ms = X->t_update_ms;
+  stats->n_spec_update = X->n_update;
   for (int q = 0; q < 4; ++q) stats->t_phase_ms[q] = X->t_phase[q];
 }
 

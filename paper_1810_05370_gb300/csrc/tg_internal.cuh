@@ -555,7 +555,7 @@ cudaError_t launch_spectral(const Spec<R>&, const R* const r[3], R* const z[3], 
                             cudaStream_t st, const PUpd<R>* pu = nullptr);
 cudaError_t launch_elas32_matvec_spec(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_spectral_update(const Spec<float>&, const Elas32&, float* const z[3],
-                                   cudaStream_t st);
+                                   cudaStream_t st, cudaEvent_t after_update = nullptr);
 cudaError_t launch_elas32_scale_r(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_elas32_update_spec(const Geo&, const Elas32&, cudaStream_t st);
 

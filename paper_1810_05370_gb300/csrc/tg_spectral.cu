@@ -1050,10 +1050,11 @@ cudaError_t launch_spectral(const Spec<R>& V, const R* const r[3], R* const z[3]
 // one preconditioned CG iteration's update and preconditioner (mixed precision): the fused
 // update + x forward pass, then the remaining four passes
 cudaError_t launch_spectral_update(const Spec<float>& V, const Elas32& I, float* const z[3],
-                                   cudaStream_t st) {
+                                   cudaStream_t st, cudaEvent_t after_update) {
   const dim3 gx(V.ny / (2 * V.pb), V.nz, 3);
   const dim3 gy((V.nxh + V.tx - 1) / V.tx, V.nz, 3);
   k_spec_update_xfwd<<<gx, NT, spec_smem_x(V), st>>>(V, I);
+  if (after_update) cudaEventRecord(after_update, st);
   k_spec_y<float, -1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S);
   launch_spec_z(V, I.S, st);
   k_spec_y<float, +1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S);
