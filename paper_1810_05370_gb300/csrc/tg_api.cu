@@ -62,7 +62,7 @@ constexpr size_t ALIGN = 256;
 constexpr int MAX_NV = 9;    // largest number of values reduced by one kernel
 // 3 diffusion solves (outer in the mixed precision), elasticity (outer), elasticity inner
 // FP32, 3 inner FP32 diffusion solves
-constexpr int N_SCAL = 8;
+constexpr int N_SCAL = 11;   // 3 CN, 2 elasticity, 3 inner CN, 3 concurrent CN
 constexpr int MAX_SWEEPS = 64;        // refinement sweeps of one mixed-precision solve
 constexpr double TAU_INNER = 1e-4;    // smallest relative reduction asked of an inner solve
 // ... of a spectrally preconditioned inner elasticity solve: its few, well-conditioned FP32
@@ -174,6 +174,7 @@ struct Layout {
   size_t arr32[B_COUNT];
   size_t adj[C_COUNT];
   size_t partial, counter, scal, grad;
+  size_t partial2, counter2;   // reductions of the oxygen solve running on the side stream
   bool spectral;
   size_t sp_w, sp_z32[3], sp_z64[3], sp_s32[3], sp_s64[3], sp_tab32, sp_tab64, sp_mean,
       sp_partial, sp_counter;
@@ -206,6 +207,10 @@ Layout layout(const Geo& G, tg_precision prec, bool adjoint = false, bool spectr
   off += round_up(N_SCAL * sizeof(CgScal));
   L.grad = off;
   off += ALIGN;
+  L.partial2 = off;
+  if (prec == TG_MIXED) off += round_up((size_t)G.nblocks * MAX_NV * sizeof(double));
+  L.counter2 = off;
+  if (prec == TG_MIXED) off += ALIGN;
   // spectral preconditioner: the FP32 form serves the mixed precision and the adjoint's
   // refined solves, the FP64 form the FP64 solves; one half-spectrum buffer serves both
   L.spectral = spectral;
@@ -366,6 +371,12 @@ struct tg_ctx {
   double* partial;
   unsigned int* counter;
   CgScal* scal;
+  // TG_MIXED: the FP64 oxygen solve of S2 runs on a side stream (created on first use),
+  // forked from and joined to the context's stream by events, with its own reductions
+  double* partial2;
+  unsigned int* counter2;
+  cudaStream_t side;
+  cudaEvent_t fork_ev, join_ev;
   int broken;
   int prev_it_diff;
   int prev_it_elas;
@@ -420,22 +431,32 @@ tg_status status_of(const CgScal& s) {
 
 // Queue iterations in chunks and read the device-side flags back between chunks.  Kernels of
 // a finished solve return at once, so overshooting a chunk only costs empty launches.
+// On stream st; `queued` iterations may already be in flight (then the loop reads the flags
+// first).
+int first_chunk(int prev) { return prev > 0 ? std::max(1, prev - prev / 8) : 4; }
+
 template <class IterFn>
-tg_status drive_cg(tg_ctx* X, IterFn iter, const CgScal* dev, int nsolves, int maxit, int prev,
-                   CgScal* host) {
-  int chunk = prev > 0 ? std::max(1, prev - prev / 8) : 4;
-  long long queued = 0;
+tg_status drive_cg_on(tg_ctx* X, cudaStream_t st, IterFn iter, const CgScal* dev, int nsolves,
+                      int maxit, int prev, CgScal* host, long long queued = 0) {
+  int chunk = queued > 0 ? 0 : first_chunk(prev);
+  const long long first = queued > 0 ? queued : chunk;
   for (;;) {
     for (int c = 0; c < chunk; ++c) CK(iter((int)(queued + c)));
     queued += chunk;
-    CK(cudaMemcpyAsync(host, dev, nsolves * sizeof(CgScal), cudaMemcpyDeviceToHost, X->stream));
-    CK(cudaStreamSynchronize(X->stream));
+    CK(cudaMemcpyAsync(host, dev, nsolves * sizeof(CgScal), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     bool running = false;
     for (int r = 0; r < nsolves; ++r) running |= host[r].status == CG_RUNNING;
     if (!running) return TG_OK;
     if (queued > (long long)maxit + 64) return fail(X, TG_ERR_CUDA);  // flags never settled
-    chunk = (queued == chunk) ? 2 : std::min(chunk * 2, 32);
+    chunk = (queued == first) ? 2 : std::min(chunk * 2, 32);
   }
+}
+
+template <class IterFn>
+tg_status drive_cg(tg_ctx* X, IterFn iter, const CgScal* dev, int nsolves, int maxit, int prev,
+                   CgScal* host) {
+  return drive_cg_on(X, X->stream, iter, dev, nsolves, maxit, prev, host);
 }
 
 // grow the event pool to hold the events of `iters` timed iterations (three each: before and
@@ -588,7 +609,11 @@ tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
   if (C.df) {   // (hi, lo) pairs of the fields for the first double-FP32 residual
     double* const pk[3] = {reinterpret_cast<double*>(C.xdf[0]), reinterpret_cast<double*>(C.xdf[1]),
                            reinterpret_cast<double*>(C.xdf[2])};
-    CK(launch_df_pack3(X->G, C.x, pk, X->stream));
+    // only the solved fields are read (oxygen may be in its own solve on the side stream)
+    const int f0 = (mask & 1) ? 0 : ((mask & 4) ? 2 : 1);
+    const double* const src[3] = {C.x[(mask & 1) ? 0 : f0], C.x[(mask & 2) ? 1 : f0],
+                                  C.x[(mask & 4) ? 2 : f0]};
+    CK(launch_df_pack3(X->G, src, pk, X->stream));
     X->launches += 1;
   }
   for (;;) {
@@ -633,6 +658,61 @@ tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
     if (e != TG_OK) return fail(X, e);
   }
   return TG_OK;
+}
+
+// S2 of the mixed multispecies step: the FP64 oxygen solve on the side stream, concurrently with
+// the FP32-refined i and l solves on the context's stream.  The FP64 CG is limited by the FP64
+// units and the refined solves by memory, so the two overlap.  The oxygen solve has its own CG
+// scalars (scal + 8) and reduction buffers; the first chunk of its iterations is queued before
+// the i, l solve starts and the rest is driven after it; events fork and join the streams.
+tg_status cn_solve_mixed_concurrent(tg_ctx* X, tg_stats* stats) {
+  constexpr int MASK_O = 7 & ~CN_MIXED_MASK;
+  if (!X->side) {
+    CK(cudaStreamCreateWithFlags(&X->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&X->fork_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&X->join_ev, cudaEventDisableTiming));
+  }
+  cudaStream_t so = X->side;
+  Cn3 C = cn_view(X);
+  C.S = X->scal + 8;
+  C.partial = X->partial2;
+  C.counter = X->counter2;
+  C.df = 0;
+  CK(cudaEventRecord(X->fork_ev, X->stream));
+  CK(cudaStreamWaitEvent(so, X->fork_ev, 0));
+  k_cg_reset<<<1, 32, 0, so>>>(C.S, 3, X->prm.rtol_diff, X->prm.maxit_diff);
+  CK(cudaGetLastError());
+  CK(launch_cn_init(X->G, C, so, MASK_O));
+  const int chunk = first_chunk(X->prev_it_diff);
+  for (int c = 0; c < chunk; ++c) CK(launch_cn_iter(X->G, C, so));
+  X->launches += 2 + 3LL * chunk;
+  // i and l on the context's stream meanwhile
+  tg_status e = cn_solve3_mixed(X, stats, CN_MIXED_MASK);
+  if (e != TG_OK) {
+    cudaStreamSynchronize(so);   // nothing of the side stream outlives the call
+    return e;
+  }
+  CgScal host[3];
+  e = drive_cg_on(X, so, [&](int) {
+    X->launches += 3;
+    return launch_cn_iter(X->G, C, so);
+  }, C.S, 3, X->prm.maxit_diff, X->prev_it_diff, host, chunk);
+  if (e != TG_OK) {
+    cudaStreamSynchronize(so);
+    return e;
+  }
+  if (host[1].status == CG_ZERO_RHS)
+    CK(cudaMemsetAsync(C.x[1], 0, (size_t)X->G.nvox * sizeof(double), so));
+  CK(cudaEventRecord(X->join_ev, so));
+  CK(cudaStreamWaitEvent(X->stream, X->join_ev, 0));
+  X->prev_it_diff = host[1].it;
+  if (stats) {
+    stats->it_diff[1] = host[1].it;
+    stats->relres_diff[1] = host[1].bb > 0.0 ? sqrt(host[1].rr / host[1].bb) : 0.0;
+    stats->it_diff_total += host[1].it;
+  }
+  e = status_of(host[1]);
+  return e == TG_OK ? TG_OK : fail(X, e);
 }
 
 Elas32 elas32_view(tg_ctx* X) {
@@ -985,8 +1065,7 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   if (single) {
     e = X->prec == TG_MIXED ? cn_solve3_mixed(X, stats, 1) : cn_solve3(X, stats, 1);
   } else if (X->prec == TG_MIXED) {
-    e = cn_solve3(X, stats, 7 & ~CN_MIXED_MASK);
-    if (e == TG_OK) e = cn_solve3_mixed(X, stats, CN_MIXED_MASK);
+    e = cn_solve_mixed_concurrent(X, stats);
   } else {
     e = cn_solve3(X, stats);
   }
@@ -1264,7 +1343,10 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
   X->partial = (double*)(X->ws + L.partial);
   X->counter = (unsigned int*)(X->ws + L.counter);
   X->scal = (CgScal*)(X->ws + L.scal);
-  if (cudaMemsetAsync(X->counter, 0, ALIGN, X->stream) != cudaSuccess) {
+  X->partial2 = (double*)(X->ws + L.partial2);
+  X->counter2 = (unsigned int*)(X->ws + L.counter2);
+  if (cudaMemsetAsync(X->counter, 0, ALIGN, X->stream) != cudaSuccess ||
+      (prec == TG_MIXED && cudaMemsetAsync(X->counter2, 0, ALIGN, X->stream) != cudaSuccess)) {
     tg_free(X);
     return TG_ERR_CUDA;
   }
@@ -1437,6 +1519,12 @@ tg_status tg_set_timing(tg_ctx* X, int32_t enable) {
 
 void tg_free(tg_ctx* X) {
   if (!X) return;
+  if (X->side) {
+    cudaStreamSynchronize(X->side);
+    cudaStreamDestroy(X->side);
+  }
+  if (X->fork_ev) cudaEventDestroy(X->fork_ev);
+  if (X->join_ev) cudaEventDestroy(X->join_ev);
   for (cudaEvent_t e : X->ev) cudaEventDestroy(e);
   if (X->pev_ok)
     for (cudaEvent_t e : X->pev) cudaEventDestroy(e);
