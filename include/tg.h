@@ -29,9 +29,12 @@
  *    in DEVICE memory on the current CUDA device, and at least 16-byte aligned.
  *  - The library never allocates device memory.  The caller owns the state arrays and one
  *    workspace of tg_workspace_bytes() bytes; both are borrowed until tg_free.
- *  - All GPU work goes to the stream given to tg_init (a cudaStream_t, NULL = legacy
- *    default stream).  Calls return after the work they queued has finished (the solvers
- *    read their convergence flags back), so buffers may be reused on return.
+ *  - All GPU work is ordered on the stream given to tg_init (a cudaStream_t, NULL = legacy
+ *    default stream).  In TG_MIXED the oxygen solve of S2 runs on a second stream that the
+ *    context creates on first use; it starts after and ends before the given stream's work
+ *    around it (events), so callers see one stream.  Calls return after the work they queued
+ *    has finished (the solvers read their convergence flags back), so buffers may be reused
+ *    on return.
  *  - Errors are returned as tg_status; nothing is printed and no global state is kept.
  *    After any error other than TG_ERR_ARG the context refuses further work with
  *    TG_ERR_STATE (the state arrays are then unspecified) until it is freed.

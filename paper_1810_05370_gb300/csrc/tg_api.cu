@@ -667,7 +667,7 @@ tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
 // the i, l solve starts and the rest is driven after it; events fork and join the streams.
 tg_status cn_solve_mixed_concurrent(tg_ctx* X, tg_stats* stats) {
   constexpr int MASK_O = 7 & ~CN_MIXED_MASK;
-  if (!X->side) {
+  if (!X->side) {   // default priority (the highest measured no better)
     CK(cudaStreamCreateWithFlags(&X->side, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&X->fork_ev, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&X->join_ev, cudaEventDisableTiming));
