@@ -419,27 +419,40 @@ def main():
         from paper_1810_05370_gb300.rollout import Rollout
         an, asteps = args.adjoint_n, args.adjoint_steps
         ast0 = initial_state(an, seed=0)
-        sim_f = Simulation(an, P, ast0, precision="fp64", device=dev)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        sim_f.step(args.dt, nsteps=asteps)
-        torch.cuda.synchronize(dev)
-        t_fwd = time.perf_counter() - t0
-        sim_f.close()
-        t0 = time.perf_counter()
-        ro = Rollout(an, P, ast0, asteps, args.dt, checkpoint_every=args.adjoint_checkpoint)
-        p_final = ro.forward()
-        vol = (2 * np.pi / an) ** 3
-        g = ro.gradient(vol * (p_final - 1.05 * p_final))
-        torch.cuda.synchronize(dev)
-        t_grad = time.perf_counter() - t0
-        ro.close()
+        ce = args.adjoint_checkpoint
+        # untimed: a rollout of one checkpoint segment loads the adjoint's kernels (first use)
+        wu = Rollout(an, P, ast0, ce, args.dt, checkpoint_every=ce)
+        wu.gradient(wu.forward())
+        wu.close()
+        del wu
+        # two rounds, the second kept: the first on a freshly started GPU has measured up to
+        # 25 % slower for the gradient pass; simulations and rollouts are created (u^0 solve,
+        # workspace) before each clock starts
+        for _ in range(2):
+            sim_f = Simulation(an, P, ast0, precision="fp64", device=dev)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            sim_f.step(args.dt, nsteps=asteps)
+            torch.cuda.synchronize(dev)
+            t_fwd = time.perf_counter() - t0
+            sim_f.close()
+            ro = Rollout(an, P, ast0, asteps, args.dt, checkpoint_every=ce)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            p_final = ro.forward()
+            vol = (2 * np.pi / an) ** 3
+            g = ro.gradient(vol * (p_final - 1.05 * p_final))
+            torch.cuda.synchronize(dev)
+            t_grad = time.perf_counter() - t0
+            ro.close()
+            del ro
         adjoint = {"grid": an, "steps": asteps, "checkpoint_every": args.adjoint_checkpoint,
                    "precision": "fp64", "forward_s": t_fwd,
                    "forward_recompute_adjoint_s": t_grad,
                    "adjoint_over_forward": t_grad / t_fwd,
                    "gradient": [float(x) for x in g],
-                   "note": "init (u^0 solve) included in both; misfit against 1.05 p_N"}
+                   "note": "init (u^0 solve) outside both clocks; kernels loaded by an untimed "
+                           "rollout first; second of two rounds; misfit against 1.05 p_N"}
         torch.cuda.empty_cache()
 
     # ---------------------------------------------------------------- batched workload (rank 0)
