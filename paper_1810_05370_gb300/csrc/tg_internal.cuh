@@ -262,7 +262,8 @@ struct Elas32 {    // inner FP32 elasticity solve of the mixed precision
   float* r[3];
   float* p[2][3];  // search direction, double-buffered: iteration k reads p[k&1], writes p[~k&1]
   float* q[3];
-  const float* z[3];  // preconditioned residual when the spectral preconditioner is on
+  const float* z[3];  // z = P r of a plain preconditioner application (the spectral CG itself
+                      // takes p from the preconditioner's last pass)
   CgScal* S;
   double* partial;
   unsigned int* counter;

@@ -99,8 +99,9 @@ __global__ void __launch_bounds__(NT) k_elas32_update(long long n, Elas32 I) {
     cg_after_update(*I.S, out[0], out[1]);
 }
 
-// the same with the spectral preconditioner: the operator stages p = z + beta p, the update
-// decides convergence from <r, r> and the preconditioner's last pass supplies beta
+// the same with the spectral preconditioner: the preconditioner's last pass already wrote
+// p = z + beta p_old, so the operator only stages p; the update decides convergence from
+// <r, r>
 __global__ void __launch_bounds__(NT) k_elas32_matvec_spec(Geo G, Consts32 K, Elas32 I) {
   if (!running(I.S)) return;
   __shared__ Tile32 T;
