@@ -88,6 +88,102 @@ def test_diffusion_node_K_mixture_and_clamp(oracle):
     assert np.allclose(K, np.maximum(ref, 0.0), rtol=1e-15, atol=0)
 
 
+def _layered_K(nx, rng, lo=0.01, hi=1.0):
+    """Node conductivities that vary along x only (a periodic stack of slabs), log-uniform."""
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), nx))
+
+
+def test_diffusion_faces_layered_medium_series_resistance(oracle):
+    """A periodic stack of slabs, one node (cell of width h) each, conductivity K_j: with a
+    source in slab 0 and a sink in slab m, the steady flux between them is constant, and the
+    potential drops by F (h/2)(1/K_j + 1/K_{j+1}) from node j to node j+1: the series
+    resistance of two half cells (the zero-flux interface condition of Section 2.2 between
+    tissues of different diffusivity).  The potential built from that physical law alone must
+    make D_h c vanish everywhere except at the source and sink planes, and there D_h c must
+    equal the net flux divided by h.  An arithmetic face mean violates it in every slab."""
+    n = (16, 4, 3)
+    nx = n[0]
+    h = TWO_PI / nx
+    rng = np.random.default_rng(21)
+    Kx = _layered_K(nx, rng)
+    m = 6                                    # sink slab
+    # link resistances of the series law, link j between node j and node j + 1 (periodic)
+    res = [(h / 2) * (1 / Kx[j] + 1 / Kx[(j + 1) % nx]) for j in range(nx)]
+    R1 = sum(res[j] for j in range(m))      # path 0 -> m going right
+    R2 = sum(res[j] for j in range(m, nx))  # path m -> 0 going right (i.e. 0 -> m going left)
+    F1 = 1.0                                # flux to the right on the links 0..m-1
+    F2 = F1 * R1 / R2                       # flux to the left from node 0 round to node m
+    c1 = np.zeros(nx)
+    for j in range(m):
+        c1[j + 1] = c1[j] - F1 * res[j]
+    for j in range(nx - 1, m, -1):          # walking left from node 0 (= node nx) down to m+1
+        c1[j] = c1[(j + 1) % nx] - F2 * res[j]
+    assert abs(c1[m] - (c1[m + 1] - F2 * res[m])) <= 1e-12 * R1  # both paths meet at the sink
+    K = np.ascontiguousarray(np.broadcast_to(Kx, (n[2], n[1], nx)))
+    c = np.ascontiguousarray(np.broadcast_to(c1, (n[2], n[1], nx)))
+    Kf = oracle.diffusion_faces(n, K)
+    out = oracle.diffusion_apply(n, Kf, c)[0, 0]
+    # net outflow F1 + F2 at the source, inflow F1 + F2 at the sink, nothing elsewhere
+    expect = np.zeros(nx)
+    expect[0] = -(F1 + F2) / h
+    expect[m] = (F1 + F2) / h
+    assert np.max(np.abs(out - expect)) <= 1e-11 * (F1 + F2) / h, out - expect
+    # the same test with arithmetic face means fails by far more than the tolerance
+    Kf_arith = [0.5 * (K + np.roll(K, -1, axis=2 - d)) for d in range(3)]
+    bad = oracle.diffusion_apply(n, Kf_arith, c)[0, 0]
+    assert np.max(np.abs(bad - expect)) > 1e-2 * (F1 + F2) / h
+
+
+def test_diffusion_faces_two_node_values_and_zero_pair(oracle):
+    """Each x face equals the conductance of two half cells in series, 2 K_a K_b / (K_a + K_b),
+    i.e. 1 / (mean of 1/K_a and 1/K_b); equal nodes give K itself; a pair of K = 0 nodes gives
+    0 (not NaN); one K = 0 node gives 0."""
+    n = (8, 4, 4)
+    rng = np.random.default_rng(5)
+    Kx = _layered_K(8, rng)
+    Kx[5] = Kx[6] = 0.0                      # the faces 4|5 and 6|7 touch one zero, 5|6 two
+    Kx[2] = Kx[3] = 0.37                     # equal pair: face 2|3 must be 0.37
+    K = np.ascontiguousarray(np.broadcast_to(Kx, (4, 4, 8)))
+    fx = oracle.diffusion_faces(n, K)[0][0, 0]
+    for j in range(8):
+        a, b = Kx[j], Kx[(j + 1) % 8]
+        want = 0.0 if a == 0.0 or b == 0.0 else 1.0 / (0.5 / a + 0.5 / b)
+        assert np.isfinite(fx[j]) and abs(fx[j] - want) <= 1e-15 * max(want, 1e-300), (j, fx[j])
+    assert fx[2] == pytest.approx(0.37, rel=1e-15)
+    assert fx[4] == 0.0 and fx[5] == 0.0 and fx[6] == 0.0
+
+
+def test_diffusion_zero_K_slab_is_insulated(oracle):
+    """A slab of K = 0 nodes (CSF/background, k_CSF = 0) inside tissue: the harmonic faces give
+    zero flux across its boundary (the zero-flux condition of Section 2.2).  Changing c inside
+    the slab changes D_h c nowhere, D_h c is 0 inside it, a Crank-Nicolson step leaves the slab
+    untouched and conserves the tissue's mass.  Arithmetic face means leak through the
+    slab's boundary and fail the first check."""
+    n = (12, 6, 5)
+    rng = np.random.default_rng(8)
+    K = rng.uniform(0.2, 1.0, (n[2], n[1], n[0]))
+    slab = np.zeros(n[0], bool)
+    slab[4:7] = True
+    K[:, :, slab] = 0.0
+    K = np.ascontiguousarray(K)
+    c = rng.standard_normal(K.shape)
+    c2 = c.copy()
+    c2[:, :, slab] += rng.standard_normal(c2[:, :, slab].shape)
+    Kf = oracle.diffusion_faces(n, K)
+    d1 = oracle.diffusion_apply(n, Kf, c)
+    d2 = oracle.diffusion_apply(n, Kf, c2)
+    assert np.array_equal(d1, d2)
+    assert np.all(d1[:, :, slab] == 0.0)
+    c_out, it, _ = oracle.cn_solve(n, Kf, 0.05, c2, rtol=1e-13)
+    assert np.max(np.abs(c_out[:, :, slab] - c2[:, :, slab])) <= 1e-13
+    tissue = ~slab
+    assert abs(c_out[:, :, tissue].sum() - c2[:, :, tissue].sum()) <= 1e-10 * np.abs(c2).sum()
+    Kf_arith = [np.ascontiguousarray(0.5 * (K + np.roll(K, -1, axis=2 - d))) for d in range(3)]
+    a1 = oracle.diffusion_apply(n, Kf_arith, c)
+    a2 = oracle.diffusion_apply(n, Kf_arith, c2)
+    assert np.max(np.abs(a1[:, :, ~slab] - a2[:, :, ~slab])) > 1e-3
+
+
 # ----------------------------------------------------------------------------- elasticity
 
 def elasticity_symbol(w, h, mu, lam, eta):
