@@ -132,6 +132,35 @@ def test_gradient_matches_oracle_complex_step(torch_cuda):
     assert np.all(np.abs(g - gr) <= 1e-4 * np.abs(gr) + 1e-9 * np.abs(gr).max()), (g, gr)
 
 
+def test_tumor_rollout_autograd_matches_oracle_complex_step(torch_cuda):
+    """The torch.autograd.Function interface: p_N = TumorRollout.apply(theta, ...), the misfit
+    J = 1/2 h^3 sum (p_N - target)^2 formed in torch, and torch.autograd.grad(J, theta) against
+    the oracle's complex-step gradient (the parameter-estimation use of Section 5)."""
+    import torch
+    from oracle import Oracle
+    from oracle.gradient import THETA, complex_step_gradient, run
+    from paper_1810_05370_gb300.rollout import TumorRollout, theta_of
+    n, steps, dt = (20, 16, 12), 6, 0.02
+    P = workload_params(**HYPOXIC, **TIGHT)
+    Pt = workload_params(**HYPOXIC, **TIGHT, k_scale=1.2, rho_g=11.0, rho_w=11.0, E_scale=0.9)
+    target = run(Oracle(), n, Pt, steps, dt)["p"]
+    ref = complex_step_gradient(n, P, steps, dt, target)
+    gr = np.array([ref[k] for k in THETA])
+    theta = torch.tensor(theta_of(P), dtype=torch.float64, device="cuda", requires_grad=True)
+    pN = TumorRollout.apply(theta, n, P, initial_state(n, seed=0), steps, dt, 4)
+    assert pN.requires_grad and pN.shape == (n[2], n[1], n[0])
+    vol = (2 * np.pi) ** 3 / (n[0] * n[1] * n[2])
+    J = 0.5 * vol * torch.sum((pN - torch.from_numpy(target).cuda()) ** 2)
+    (g,) = torch.autograd.grad(J, theta)
+    assert g.dtype == torch.float64 and g.device == theta.device
+    g = g.cpu().numpy()
+    print("autograd:", g, "\ncomplex step:", gr)
+    assert np.all(np.abs(g - gr) <= 1e-4 * np.abs(gr) + 1e-9 * np.abs(gr).max()), (g, gr)
+    # the forward value is the plain rollout's final p
+    p_plain = run(Oracle(), n, P, steps, dt)["p"]
+    assert np.linalg.norm(pN.detach().cpu().numpy() - p_plain) <= 1e-10 * np.linalg.norm(p_plain)
+
+
 @pytest.mark.slow
 def test_gradient_128cubed_50_steps_vs_central_differences(torch_cuda):
     """The adjoint workload: 128^3, 50 steps, checkpoint every 10 steps with recompute; misfit

@@ -1,0 +1,182 @@
+"""Parity of the benchmark's own configuration: the scaled spectral elasticity preconditioner
+(TG_PRECOND_SPECTRAL_SCALED) on grids whose axes take the FFT plans of the 128^3 and 256^3
+workloads, element by element against the CPU oracle through the C ABI.
+
+* 256 x 256 x 8 and 128 x 128 x 16: the x and y passes of the n = 256 plan (two radix-16
+  stages, no remainder) and of the n = 128 plan (radix 16 and a radix-8 remainder), FP64 gate
+  1e-10 with elasticity iteration counts within one, mixed gate 1e-5.
+* 128^3 x 100 steps (the plain forward workload): the FP64 path compared with the oracle's
+  stored trajectory after every 10 steps (tests/golden/make_config2_128.py wrote it), on a
+  fixed sample of voxels and on whole-field norms, sums and maxima, with the same CG iteration
+  counts in every step; the mixed path on the same trajectory within the mixed gate.
+* 256^3 x 100 steps (the mixed-precision workload): the mixed path against the FP64 path per
+  field (1e-5), and the initial displacement of the mixed path against the oracle's discrete
+  elasticity equation.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from synth import initial_state, workload_params
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+TOL_MIXED = 1e-5
+SCALED = 2
+FIELDS = ("p", "i", "n", "g", "w", "f", "o", "l", "ux", "uy", "uz", "vx", "vy", "vz")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "config2_128_fp64.npz")
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def oracle_run(oracle, n, P, steps, dt, seed=0):
+    st = initial_state(n, seed)
+    s0 = oracle.init(n, P, st)
+    stats = [oracle.step(n, P, dt, st) for _ in range(steps)]
+    return st, s0, stats
+
+
+def gpu_run(n, P, steps, dt, precision, seed=0):
+    from paper_1810_05370_gb300 import Simulation
+    sim = Simulation(n, P, initial_state(n, seed), precision=precision)
+    s0 = sim.init_stats
+    stats = [sim.step(dt) for _ in range(steps)]
+    out = sim.numpy()
+    sim.close()
+    return out, s0, stats
+
+
+@pytest.mark.parametrize("n", [(256, 256, 8), (128, 128, 16)])
+def test_fp64_scaled_spectral_long_xy_axes_match_oracle(torch_cuda, oracle, n):
+    steps, dt = 3, 0.01
+    P = workload_params(precond_elas=SCALED)
+    ref, r0, rst = oracle_run(oracle, n, P, steps, dt)
+    got, g0, gst = gpu_run(n, P, steps, dt, "fp64")
+    errs = {k: rel_l2(got[k], ref[k]) for k in FIELDS}
+    print(n, "fp64 vs oracle:", {k: f"{v:.1e}" for k, v in errs.items()})
+    assert max(errs.values()) <= TOL, errs
+    assert abs(g0["it_elas"] - r0["it_elas"]) <= 1
+    for a, b in zip(gst, rst):
+        assert abs(a["it_elas"] - b["it_elas"]) <= 1
+        assert a["it_diff"] == b["it_diff"]
+
+
+@pytest.mark.parametrize("n", [(256, 256, 8), (128, 128, 16)])
+def test_mixed_scaled_spectral_long_xy_axes_match_oracle(torch_cuda, oracle, n):
+    steps, dt = 3, 0.01
+    P = workload_params(precond_elas=SCALED)
+    ref, _, _ = oracle_run(oracle, n, P, steps, dt)
+    got, _, gst = gpu_run(n, P, steps, dt, "mixed")
+    errs = {k: rel_l2(got[k], ref[k]) for k in FIELDS}
+    print(n, "mixed vs oracle:", {k: f"{v:.1e}" for k, v in errs.items()})
+    assert max(errs.values()) <= TOL_MIXED, errs
+    for s in gst:
+        assert s["relres_elas"] <= P["rtol_elas"]
+
+
+def _golden():
+    if not os.path.exists(GOLDEN):
+        pytest.fail(f"missing {GOLDEN}: run tests/golden/make_config2_128.py")
+    return np.load(GOLDEN)
+
+
+def _check_snapshot(g, j, got, tol, what):
+    idx = g["index"]
+    names = [str(x) for x in g["fields"]]
+    bad = {}
+    for f, name in enumerate(names):
+        x = got[name].ravel()
+        e = rel_l2(x[idx], g["values"][j, f])
+        ref_norm = g["norms"][j, f]
+        e_norm = abs(np.linalg.norm(x) - ref_norm) / ref_norm if ref_norm > 0 else np.linalg.norm(x)
+        scale = max(g["maxabs"][j, f], 1e-300)
+        e_sum = abs(x.sum() - g["sums"][j, f]) / (scale * x.size)
+        e_max = abs(np.abs(x).max() - g["maxabs"][j, f]) / scale
+        worst = max(e, e_norm, e_sum, e_max)
+        if not worst <= tol:
+            bad[name] = (e, e_norm, e_sum, e_max)
+    assert not bad, f"{what}, step {(j + 1) * int(g['every'])}: {bad}"
+
+
+@pytest.mark.slow
+def test_fp64_128cubed_100_steps_match_stored_oracle_trajectory(torch_cuda):
+    """The plain forward workload at full size: 128^3, 100 steps, all fields and u, v every
+    10 steps, and identical CG iteration counts in every step."""
+    from paper_1810_05370_gb300 import Simulation
+    g = _golden()
+    n, every, dt = int(g["n"]), int(g["every"]), float(g["dt"])
+    P = workload_params(precond_elas=int(g["precond_elas"]))
+    sim = Simulation(n, P, initial_state(n, int(g["seed"])), precision="fp64")
+    assert abs(sim.init_stats["it_elas"] - int(g["it_elas_init"])) <= 1
+    for j in range(int(g["steps"]) // every):
+        for k in range(every):
+            s = sim.step(dt)
+            step = j * every + k
+            assert list(s["it_diff"]) == list(g["it_diff"][step]), (step, s["it_diff"])
+            assert abs(s["it_elas"] - int(g["it_elas"][step])) <= 1, (step, s["it_elas"])
+        _check_snapshot(g, j, sim.numpy(), TOL, "fp64")
+    sim.close()
+
+
+@pytest.mark.slow
+def test_mixed_128cubed_100_steps_match_stored_oracle_trajectory(torch_cuda):
+    """The mixed path on the same 128^3 trajectory, every 10 steps, within the mixed gate."""
+    from paper_1810_05370_gb300 import Simulation
+    g = _golden()
+    n, every, dt = int(g["n"]), int(g["every"]), float(g["dt"])
+    P = workload_params(precond_elas=int(g["precond_elas"]))
+    sim = Simulation(n, P, initial_state(n, int(g["seed"])), precision="mixed")
+    for j in range(int(g["steps"]) // every):
+        stats = sim.step(dt, nsteps=every)
+        assert stats["relres_elas"] <= P["rtol_elas"]
+        _check_snapshot(g, j, sim.numpy(), TOL_MIXED, "mixed")
+    sim.close()
+
+
+@pytest.mark.slow
+def test_mixed_vs_fp64_256cubed_100_steps_scaled_preconditioner(torch_cuda):
+    """The mixed-precision workload as benchmarked (256^3, scaled spectral preconditioner),
+    100 steps: every field within 1e-5 of the FP64 path."""
+    n, steps, dt = 256, 100, 0.01
+    P = workload_params(precond_elas=SCALED)
+    ref, _, _ = gpu_run(n, P, steps, dt, "fp64")
+    got, _, st = gpu_run(n, P, steps, dt, "mixed")
+    errs = {k: rel_l2(got[k], ref[k]) for k in FIELDS}
+    print("mixed vs fp64 at 256^3 x 100:", {k: f"{v:.1e}" for k, v in errs.items()})
+    assert max(errs.values()) <= TOL_MIXED, errs
+    for s in st:
+        assert s["relres_elas"] <= P["rtol_elas"]
+
+
+@pytest.mark.slow
+def test_mixed_256cubed_initial_displacement_solves_oracle_equation(torch_cuda, oracle):
+    """256^3 with the benchmark's kernels (FFT plans of n = 256 on all three axes): the mixed
+    path's u^0 satisfies the oracle's discrete elasticity equation to the CG tolerance, and
+    the scaled spectral preconditioner keeps the refined solve short."""
+    from paper_1810_05370_gb300 import Simulation
+    n = 256
+    P = workload_params(precond_elas=SCALED)
+    st = initial_state(n, seed=0)
+    sim = Simulation(n, P, st, precision="mixed")
+    u0 = np.stack([sim.state[k].cpu().numpy() for k in ("ux", "uy", "uz")])
+    s0 = sim.init_stats
+    sim.close()
+    mu, lam, eta = oracle.lame(n, P, st)
+    b = oracle.force(n, P, st["p"], st["n"])
+    Au = oracle.elasticity_apply(n, mu, lam, eta, u0)
+    res = np.linalg.norm(Au + b) / np.linalg.norm(b)
+    assert res <= 2 * P["rtol_elas"], res
+    assert s0["it_elas"] <= 150, s0   # Jacobi needs several hundred

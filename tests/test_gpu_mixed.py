@@ -87,18 +87,6 @@ def test_mixed_solve_elasticity_matches_oracle(torch_cuda, oracle):
     assert rel_l2(got, ref) <= 1e-8
 
 
-@pytest.mark.slow
-def test_mixed_vs_fp64_256cubed(torch_cuda):
-    """The 256^3 workload: mixed against the FP64 GPU path after 20 steps."""
-    n, steps, dt = 256, 20, 0.01
-    P = workload_params()
-    ref, _, _ = run_gpu(n, P, steps, dt, "fp64")
-    got, _, st = run_gpu(n, P, steps, dt, "mixed")
-    errs = errors(got, ref)
-    print("mixed vs fp64 at 256^3, rel-L2:", {k: f"{v:.1e}" for k, v in errs.items()})
-    assert max(errs.values()) <= TOL_MIXED, errs
-
-
 @pytest.mark.parametrize("precond", [0, 1])
 def test_mixed_double_fp32_residual_reaches_1e10(torch_cuda, oracle, precond):
     """At rtol_elas = 1e-10 the mixed refinement uses the double-FP32 residual; the solve must
