@@ -43,12 +43,79 @@ ELAS_MATVEC_BYTES_PER_VOXEL = {("fp64", "jacobi"): 17 * 8, ("fp64", "spectral"):
                                ("mixed", "jacobi"): 18 * 4, ("mixed", "spectral"): 9 * 4,
                                ("mixed", "scaled"): 9 * 4}
 ELAS_MATVEC_FLOPS_PER_VOXEL = 123
-# DRAM traffic per launch at 256^3 with the scaled spectral preconditioner
-# (dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture, mean of two launches;
-# profiles/elas32_matvec_spec_256.md): the operator kernel 415.7 + 174.9 MB, the fused update
-# + x forward pass 1012.4 + 558.6 MB.  Only for these kernels in this configuration.
-MATVEC_SPEC_DRAM_BYTES_256 = 590.55e6
-UPDATE_XFWD_DRAM_BYTES_256 = 1570.92e6
+
+
+def mixed_kernel_bytes(n, precond):
+    """Algorithmic bytes per voxel of one launch of each kernel of the mixed multispecies step
+    (every array element the kernel must read or write once; neighbour re-reads are free).
+    FP64 arrays 8 B, FP32 arrays 4 B, (hi, lo) FP32 pairs 8 B; W is the half spectrum of the
+    three components, n/2 + 1 complex FP32 modes per row of n voxels."""
+    W = 3 * 8 * (n // 2 + 1) / n
+    s = 12 if precond == "scaled" else 0        # the scaled preconditioner's s (3 comps)
+    return {
+        "k_diff_faces": 80,          # g, w, f in; 3 faces, rho, 3 face pairs out
+        "k_diff_diag": 40,           # 3 faces in; diagonal and its inverse out
+        "k_to_f32": 84,              # FP32 copies: 4 arrays in S0, 10 in S1 (mean per launch)
+        "k_divergence": 32,          # v (3) in, div v out
+        "k_sl32": 88,                # 10 FP32 fields gathered, 6 FP64 fields out
+        "k_df_pack3": 48,            # 3 FP64 in, 3 pairs out
+        "k_cn_ir_residual_df": 76,   # 3 face pairs, D^-1; per field (i, l): x pair, rhs pair, r, e
+        "k_cn32_pupdate": 28,        # D^-1, r and p (2 fields) in, p out
+        "k_cn32_matvec": 28,         # 3 FP32 faces, p (2 fields) in, q out
+        "k_cn32_update": 52,         # D^-1, e, r, p, q (2 fields) in, e, r out
+        "k_cn_ir_correct": 56,       # x (FP64), e in; x, x pair out (2 fields)
+        "k_cn_init": 56,             # oxygen, FP64: 3 faces, D^-1, x in; r, p out
+        "k_cn_matvec": 48,           # 3 faces, diagonal, p in; q out
+        "k_cn_update": 56,           # D^-1, x, r, p, q in; x, r out
+        "k_cn_pupdate": 32,          # D^-1, r, p in; p out
+        "k_react": 128,              # 9 FP64 in, 7 out
+        "k_lame": 80,                # 7 species in; mu, lambda, eta out
+        "k_elas_coef_df": 136,       # mu, lambda pairs, eta, p, n in; F, G, diagonal, b pairs out
+        "k_elas_extrapolate": 96,    # u, v in; u, du out
+        "k_spec_mean": 24,           # mu, lambda, eta in
+        "k_elas_ir_residual_df": 160,  # u, F, G, diagonal, b pairs (3 each), mu, lambda pairs
+        #                                in; r, e (FP32) out
+        "k_spec_x_fwd": 12 + s + W,  # r (and s) in, half spectrum out
+        "k_spec_y_fwd": 2 * W,       # half spectrum in and out
+        "k_spec_y_inv": 2 * W,
+        "k_spec_zr": 2 * W,
+        "k_spec_z": 2 * W,
+        "k_spec_x_inv_p": W + s + 24,  # half spectrum (and s), p_old in; p out
+        "k_elas32_matvec_spec": 36,  # p (3), mu, lambda, eta in; q (3) out
+        "k_spec_update_xfwd": 72 + s + W,  # e, p, r, q in; e, r out (3 each); spectrum out
+        "k_elas_ir_correct": 132,    # u, du, e in; u, du, u pairs out
+        "k_elas_ir_finish": 48,      # du in, v out
+    }
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# of a single kernel, per voxel, with the hash of the source it was measured on: reported
+# only while the kernel's source (its .cu file and the shared headers) is unchanged.
+MEASURED_TRAFFIC = {}
+KERNEL_SOURCE = {"k_spec_update_xfwd": "tg_spectral.cu", "k_spec_y_fwd": "tg_spectral.cu",
+                 "k_spec_y_inv": "tg_spectral.cu", "k_spec_zr": "tg_spectral.cu",
+                 "k_spec_x_inv_p": "tg_spectral.cu", "k_elas32_matvec_spec": "tg_mixed.cu",
+                 "k_cn32_matvec": "tg_cn_mixed.cu", "k_cn32_update": "tg_cn_mixed.cu",
+                 "k_sl32": "tg_mixed.cu"}
+
+
+def kernel_source_sha(kernel):
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1810_05370_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in (KERNEL_SOURCE.get(kernel), "tg_internal.cuh", "tg_tiles.cuh"):
+        if f is None:
+            return None
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, n):
+    m = MEASURED_TRAFFIC.get(kernel)
+    if m is None or m["sha"] != kernel_source_sha(kernel):
+        return None
+    return m["bytes_per_voxel"] * n ** 3
 
 
 def parse():
@@ -75,9 +142,19 @@ def parse():
     ap.add_argument("--no-single", action="store_true",
                     help="skip the single-species model (Eq. e:rd) line")
     ap.add_argument("--batch-sims", type=int, default=64)
-    ap.add_argument("--batch-steps", type=int, default=3)
-    ap.add_argument("--cpu-sample-n", type=int, default=64)
-    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--batch-seq-steps", type=int, default=5,
+                    help="timed steps per simulation of the sequential mixed comparison")
+    ap.add_argument("--batch-seq-steps-fp64", type=int, default=2)
+    ap.add_argument("--cpu-sample-n", type=int, default=256,
+                    help="grid of the all-core oracle timing (init untimed)")
+    ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    ap.add_argument("--cpu-single-n", type=int, default=64,
+                    help="grid of the one-thread oracle timing")
+    ap.add_argument("--ref-n", type=int, default=128,
+                    help="grid of each step of the reference arm (the oracle)")
+    ap.add_argument("--oracle-child", type=int, nargs=4, default=None,
+                    metavar=("N", "STEPS", "WARMUP", "PRECOND"), help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -154,37 +231,58 @@ def dist_setup(args):
     return world, rank, local
 
 
-def oracle_sample(n, steps, warm_steps=0, precond=0):
-    """Time the CPU oracle (all host cores) on `steps` steps of an n^3 synthetic brain, with
-    the given elasticity preconditioner (the GPU line's)."""
-    cores = len(os.sched_getaffinity(0))
-    os.environ["OMP_NUM_THREADS"] = str(cores)
+def oracle_child(a):
+    """--oracle-child: init (untimed) and `steps` timed oracle steps on the n^3 synthetic
+    brain in this process (OMP_NUM_THREADS set by the parent); prints one JSON line."""
     from oracle import Oracle
     from synth import initial_state, workload_params
+    n, steps, warm, precond = a.oracle_child
     O = Oracle()
     P = workload_params(precond_elas=precond)
     st = initial_state(n, seed=0)
+    t0 = time.perf_counter()
     O.init(n, P, st)
-    for _ in range(warm_steps):
+    t_init = time.perf_counter() - t0
+    for _ in range(warm):
         O.step(n, P, 0.01, st)
+    its = []
     t0 = time.perf_counter()
     for _ in range(steps):
-        O.step(n, P, 0.01, st)
-    dt = time.perf_counter() - t0
-    return n ** 3 * steps / dt, cores, dt
+        its.append(O.step(n, P, 0.01, st))
+    secs = time.perf_counter() - t0
+    print(json.dumps({"n": n, "steps": steps, "secs": secs, "init_secs": t_init,
+                      "value": n ** 3 * steps / secs,
+                      "threads": int(os.environ.get("OMP_NUM_THREADS", "0")),
+                      "it_elas": [s["it_elas"] for s in its],
+                      "it_diff": [s["it_diff"] for s in its]}), flush=True)
+
+
+def oracle_sample(n, steps, warm_steps=0, precond=0, threads=None):
+    """Time the CPU oracle on `steps` steps of an n^3 synthetic brain (init and warm-up steps
+    untimed) in a child process with `threads` OpenMP threads (default: every core this
+    process may run on)."""
+    cores = len(os.sched_getaffinity(0))
+    threads = cores if threads is None else threads
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", str(n),
+                        str(steps), str(warm_steps), str(precond)], env=env,
+                       capture_output=True, text=True, check=True)
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle (the paper has no code; the oracle is the plain FP64
+    statement of the same step) on the host cores, rank 0 only."""
     if rank != 0:
         return
-    n = args.cpu_sample_n
-    value, cores, secs = oracle_sample(n, args.steps, warm_steps=args.warmup,
-                                       precond=PRECONDS[args.precond])
-    sample = (f"CPU oracle, {n}^3 synthetic brain (same generator and parameters as the "
-              f"{args.n}^3 workload, {args.precond} elasticity preconditioner), "
-              f"{args.warmup} untimed + {args.steps} timed steps, "
-              f"{cores} OpenMP threads; elasticity CG iterations grow with N, so the "
-              f"per-voxel rate at {args.n}^3 would be lower")
+    n = args.ref_n
+    o = oracle_sample(n, args.steps, warm_steps=args.warmup, precond=PRECONDS[args.precond])
+    value, secs = o["value"], o["secs"]
+    sample = (f"CPU oracle, {n}^3 synthetic brain per step (same generator and parameters as "
+              f"the {args.n}^3 workload, {args.precond} elasticity preconditioner), init and "
+              f"{args.warmup} warm-up steps untimed, {args.steps} timed steps, "
+              f"{o['threads']} OpenMP threads; elasticity and diffusion CG iterations grow with "
+              f"N, so the per-voxel rate at {args.n}^3 is lower")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
@@ -192,8 +290,8 @@ def run_reference(args, world, rank):
         "data": "synthetic",
         "config": {"workload": f"{args.n}^3 synthetic brain, multispecies step, dt {args.dt}",
                    "grid": args.n, "precision": args.precision,
-                   "elasticity_preconditioner": args.precond},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "elasticity_preconditioner": args.precond, "sample_grid": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": o["threads"], "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -202,11 +300,15 @@ def run_reference(args, world, rank):
 
 def run_batch(args, dev):
     """64 simulations of uneven grids (64/96/128^3, rho ~ U[5,15], k_scale ~ U[0.5,2]) stepped
-    as one batch (persistent solvers, replayed step graph, autotuned tiles) against the same
-    simulations run one after another through the single-simulation path, both mixed."""
+    as one batch (persistent solvers, replayed step graph, autotuned tiles) for the workload's
+    steps, against the same simulations run one after another through the single-simulation
+    path with each one's best elasticity preconditioner (the scaled spectral one where the
+    grid allows it), mixed and FP64; the sequential runs are timed on a sample of steps per
+    simulation after one untimed step."""
     import torch
     from paper_1810_05370_gb300 import Simulation
     from paper_1810_05370_gb300.batch import Batch
+    from paper_1810_05370_gb300 import _tg
     from synth import batch_workload, initial_state
     spec = batch_workload(args.batch_sims)
     states = [initial_state(n, seed) for n, _, seed in spec]
@@ -222,29 +324,47 @@ def run_batch(args, dev):
     bt.close()
     del bt
     torch.cuda.empty_cache()
-    t_seq = 0.0
-    for (n, P, _), st in zip(spec, states):
-        sim = Simulation(n, P, st, precision="mixed", device=dev)
-        sim.step(args.dt)                                 # warm-up, as for the batch
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        sim.step(args.dt, args.batch_steps)
-        torch.cuda.synchronize(dev)
-        t_seq += time.perf_counter() - t0
-        sim.close()
+
+    def best_precond(n, P):
+        for pc in (PRECONDS["scaled"], PRECONDS["jacobi"]):
+            if _tg.tg_workspace_bytes(_tg.make_grid(n), _tg.make_params(dict(P, precond_elas=pc)),
+                                      _tg.TG_MIXED) > 0:
+                return pc
+        return PRECONDS["jacobi"]
+
+    seq = {}
+    for prec, k in (("mixed", args.batch_seq_steps), ("fp64", args.batch_seq_steps_fp64)):
+        t_seq, vs = 0.0, 0
+        for (n, P, _), st in zip(spec, states):
+            Pb = dict(P, precond_elas=best_precond(n, P))
+            sim = Simulation(n, Pb, st, precision=prec, device=dev)
+            sim.step(args.dt)                             # untimed first step
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            sim.step(args.dt, k)
+            torch.cuda.synchronize(dev)
+            t_seq += time.perf_counter() - t0
+            vs += n ** 3 * k
+            sim.close()
+        torch.cuda.empty_cache()
+        seq[prec] = {"voxel_steps_per_s": vs / t_seq, "steps_per_sim": k, "seconds": t_seq}
     vs = voxels * args.batch_steps
     return {"sims": len(spec), "voxels": voxels, "steps": args.batch_steps, "precision": "mixed",
-            "voxel_steps_per_s": vs / t_batch, "sequential_voxel_steps_per_s": vs / t_seq,
-            "speedup_over_sequential": t_seq / t_batch, "seconds": t_batch,
-            "sequential_seconds": t_seq, "graph": stats["graph"],
-            "tile_depth": stats["tile_depth"], "coop_blocks": stats["coop_blocks"],
-            "inner_iterations": stats["it_elas_total"], "launches": stats["launches"],
+            "voxel_steps_per_s": vs / t_batch, "seconds": t_batch,
+            "sequential_best_path": seq,
+            "speedup_over_sequential_mixed": (vs / t_batch) / seq["mixed"]["voxel_steps_per_s"],
+            "graph": stats["graph"], "tile_depth": stats["tile_depth"],
+            "coop_blocks": stats["coop_blocks"], "inner_iterations": stats["it_elas_total"],
+            "launches": stats["launches"],
             "autotune": {"best_zc": tune["best_zc"], "best_blocks": tune["best_blocks"],
                          "candidates": tune["candidates"]}}
 
 
 def main():
     args = parse()
+    if args.oracle_child:
+        oracle_child(args)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -301,6 +421,7 @@ def main():
         e1.record(sim.stream)
         barrier()
         agg["clocks"] = clocks.stop() if clocks is not None else None
+        agg["kernels"] = sim.kernel_times()
         sim.set_timing(False)
         ms = e0.elapsed_time(e1)
         if dist is not None:
@@ -321,51 +442,45 @@ def main():
     peaks, peak_src = load_peaks()
 
     def roofline(agg, precision):
-        avg_ms = agg["t_mv"] / max(agg["n_mv"], 1)
-        mv_bytes = ELAS_MATVEC_BYTES_PER_VOXEL[(precision, args.precond)] * V
-        gbs = mv_bytes / (avg_ms * 1e-3) / 1e9
-        share = agg["t_mv"] / agg["ms"] if agg["ms"] > 0 else None
+        """The dominant kernel's roofline and one row per timed kernel (CUDA events on the
+        launching stream, launches that did work only)."""
         if precision == "fp64":
+            avg_ms = agg["t_mv"] / max(agg["n_mv"], 1)
+            gbs = ELAS_MATVEC_BYTES_PER_VOXEL[(precision, args.precond)] * V / (avg_ms * 1e-3) / 1e9
             tfl = ELAS_MATVEC_FLOPS_PER_VOXEL * V / (avg_ms * 1e-3) / 1e12
             r64 = {"kernel": "k_elas_matvec (FP64 19-point Navier-Lame operator + <p, Ap>)",
                    "bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS,
                    "unit": "TFLOP/s", "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
                    "peak_source": "derived FP64 roof (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                    "hbm_gbs": gbs, "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"],
-                   "share_of_step": share}
+                   "share_of_step": agg["t_mv"] / agg["ms"] if agg["ms"] > 0 else None}
             return r64, [r64]
-        kname = "k_elas32_matvec" if args.precond == "jacobi" else "k_elas32_matvec_spec"
-        captured = args.n == 256 and args.precond == "scaled"
-        traffic = MATVEC_SPEC_DRAM_BYTES_256 if kname == "k_elas32_matvec_spec" and captured else None
-        mv = {"kernel": f"{kname} (FP32 19-point Navier-Lame operator, faces on the fly, "
-                        "+ <p, Ap>)",
-              "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-              "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
-              "traffic_per_voxel": traffic / V if traffic else None,
-              "peak_source": f"{peak_src} HBM copy bandwidth",
-              "bytes_per_voxel": ELAS_MATVEC_BYTES_PER_VOXEL[(precision, args.precond)],
-              "avg_launch_ms": avg_ms, "launches_timed": agg["n_mv"], "share_of_step": share}
-        if agg["n_up"] == 0:
-            return mv, [mv]
-        # the spectral CG's update fused with the first FFT pass: e, p, r, q read and e, r
-        # written (3 components each, FP32), the half spectrum written (nx/2 + 1 complex FP32
-        # modes per row and component), and with the scaled preconditioner s read
-        n = args.n
-        up_bpv = 6 * 12 + 3 * 8 * (n // 2 + 1) / n + (12 if args.precond == "scaled" else 0)
-        up_ms = agg["t_up"] / agg["n_up"]
-        up_gbs = up_bpv * V / (up_ms * 1e-3) / 1e9
-        up = {"kernel": "k_spec_update_xfwd (CG update e += alpha p, r -= alpha q, <r, r>, fused "
-                        "with the x forward FFT pass of the preconditioner)",
-              "bound": "hbm", "achieved": up_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-              "frac": up_gbs / peaks["hbm_gbs"],
-              "traffic": UPDATE_XFWD_DRAM_BYTES_256 if captured else None,
-              "traffic_per_voxel": UPDATE_XFWD_DRAM_BYTES_256 / V if captured else None,
-              "peak_source": f"{peak_src} HBM copy bandwidth", "bytes_per_voxel": up_bpv,
-              "avg_launch_ms": up_ms, "launches_timed": agg["n_up"],
-              "share_of_step": agg["t_up"] / agg["ms"] if agg["ms"] > 0 else None}
-        # the dominant kernel is the one with the larger share of the step
-        top = up if agg["t_up"] > agg["t_mv"] else mv
-        return top, [mv, up]
+        table = mixed_kernel_bytes(args.n, args.precond)
+        rows = []
+        for name, (ms, launches) in agg["kernels"].items():
+            bpv = table.get(name)
+            avg = ms / max(launches, 1)
+            row = {"kernel": name, "launches_per_step": launches / args.steps,
+                   "avg_launch_ms": avg, "ms_per_step": ms / args.steps,
+                   "share_of_step": ms / agg["ms"] if agg["ms"] > 0 else None,
+                   "bytes_per_voxel": bpv}
+            if bpv is not None and avg > 0:
+                gbs = bpv * V / (avg * 1e-3) / 1e9
+                traffic = measured_traffic(name, args.n)
+                row.update({"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
+                            "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
+                            "traffic_per_voxel": traffic / V if traffic else None})
+            rows.append(row)
+        rows.sort(key=lambda r: -r["ms_per_step"])
+        top = next(r for r in rows if r["bytes_per_voxel"] is not None)
+        roof = {k: top.get(k) for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+        roof.update({"kernel": top["kernel"], "bytes_per_voxel": top["bytes_per_voxel"],
+                     "traffic_per_voxel": top.get("traffic_per_voxel"),
+                     "peak_source": f"{peak_src} HBM copy bandwidth",
+                     "avg_launch_ms": top["avg_launch_ms"],
+                     "launches_timed": int(round(top["launches_per_step"] * args.steps)),
+                     "share_of_step": top["share_of_step"]})
+        return roof, rows
 
     roof, roof_all = roofline(agg, args.precision)
 
@@ -480,13 +595,19 @@ def main():
     # ---------------------------------------------------------------- CPU baseline (rank 0)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cn = args.cpu_sample_n
-        v_cpu, cores, secs = oracle_sample(cn, args.cpu_sample_steps,
-                                           precond=PRECONDS[args.precond])
-        cpu = {"value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{cn}^3 synthetic brain, {args.precond} elasticity preconditioner, "
-                         f"{args.cpu_sample_steps} steps after init "
-                         f"({secs:.1f} s); per-voxel cost grows with N, so this flatters the oracle"}
+        pc = PRECONDS[args.precond]
+        o_all = oracle_sample(args.cpu_sample_n, args.cpu_sample_steps, precond=pc)
+        o_one = oracle_sample(args.cpu_single_n, 2, precond=pc, threads=1)
+        cpu = {"value": o_all["value"], "unit": UNIT, "cores": o_all["threads"],
+               "kind": "oracle",
+               "sample": f"{args.cpu_sample_n}^3 synthetic brain (the workload), "
+                         f"{args.precond} elasticity preconditioner, init untimed "
+                         f"({o_all['init_secs']:.1f} s), {args.cpu_sample_steps} timed step(s) "
+                         f"({o_all['secs']:.1f} s), {o_all['threads']} OpenMP threads",
+               "solver": {"it_elas": o_all["it_elas"], "it_diff": o_all["it_diff"]},
+               "single_thread": {"value": o_one["value"], "unit": UNIT, "cores": 1,
+                                 "sample": f"{args.cpu_single_n}^3, init untimed, 2 timed steps "
+                                           f"({o_one['secs']:.1f} s), 1 thread"}}
 
     if rank == 0:
         out = {
@@ -511,6 +632,8 @@ def main():
                        "it_diff_per_step": agg["it_diff"]},
             "roofline": roof,
             "roofline_kernels": roof_all,
+            "kernel_ms_per_step": sum(r["ms_per_step"] for r in roof_all)
+            if args.precision == "mixed" else None,
             "compare": other,
             "adjoint": adjoint,
             "single_species": single,

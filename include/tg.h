@@ -220,11 +220,28 @@ tg_status tg_diagnostics(tg_ctx* ctx, const double seed[3], double u_threshold,
  * workspace was sized for either (TG_ERR_WORKSPACE otherwise). */
 tg_status tg_set_params(tg_ctx* ctx, const tg_params* params);
 
-/* Optional kernel timing for profiling: with enable != 0 every launch of the elasticity
- * operator kernel (the innermost loop of S6) is bracketed by CUDA events on the context's
- * stream and stats report the summed device time of the launches that did work.  The events
- * are created on first use (host-side objects, no device allocation). */
+/* Optional kernel timing for profiling.  With enable != 0 every kernel launch of tg_step and
+ * tg_solve_elasticity is bracketed by two CUDA events on the stream it is launched on, and
+ * the elapsed time between them is added to that kernel's total.  A CG solve queues its
+ * iterations ahead of its convergence test, and the iterations queued after convergence
+ * return at once; their launches are left out, so the totals cover the launches that did
+ * work.  The stats of a call report the elasticity operator's and the mixed spectral CG
+ * update's totals (t_elas_matvec_ms, t_spec_update_ms); tg_kernel_times reports every
+ * kernel.  Switching timing on resets the totals.  The events are created on first use
+ * (host-side objects, no device allocation) and reused every step. */
 tg_status tg_set_timing(tg_ctx* ctx, int32_t enable);
+
+/* One kernel's timing totals since timing was last switched on (see tg_set_timing). */
+typedef struct {
+  const char* name;    /* the kernel's name in the library (static string)                 */
+  double ms;           /* summed device time of its launches that did work, in ms           */
+  int64_t launches;    /* how many launches that sum covers                                  */
+} tg_kernel_time;
+
+/* Writes up to capacity entries (kernels with at least one timed launch, in a fixed order)
+ * to out and returns how many such kernels there are; -1 if ctx is NULL, capacity < 0 or out
+ * is NULL with capacity > 0.  Host only; reads no device memory. */
+int32_t tg_kernel_times(const tg_ctx* ctx, tg_kernel_time* out, int32_t capacity);
 
 /* Elasticity solve that allocates nothing and needs no workspace or context.
  *

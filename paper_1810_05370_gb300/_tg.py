@@ -80,6 +80,10 @@ class tg_diag(C.Structure):
                                                 "trace_max", "shear_max", "d_max")]
 
 
+class tg_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("ms", C.c_double), ("launches", C.c_int64)]
+
+
 class TGError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -101,6 +105,7 @@ def _load():
         "tg_solve_elasticity": (C.c_int, [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(tg_stats)]),
         "tg_set_params": (C.c_int, [C.c_void_p, P(tg_params)]),
         "tg_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+        "tg_kernel_times": (C.c_int32, [C.c_void_p, P(tg_kernel_time), C.c_int32]),
         "tg_diagnostics": (C.c_int, [C.c_void_p, P(C.c_double), C.c_double, P(C.c_void_p),
                                      P(tg_diag)]),
         "tg_workspace_bytes_adjoint": (C.c_size_t, [P(tg_grid), P(tg_params), C.c_int]),
@@ -259,6 +264,17 @@ def tg_set_timing(ctx, enable: bool):
     rc = lib.tg_set_timing(ctx, 1 if enable else 0)
     if rc != TG_OK:
         raise TGError(rc, "tg_set_timing")
+
+
+def tg_kernel_times(ctx) -> dict:
+    """{kernel name: (total ms, launches)} since timing was switched on."""
+    count = lib.tg_kernel_times(ctx, None, 0)
+    if count < 0:
+        raise TGError(TG_ERR_ARG, "tg_kernel_times")
+    arr = (tg_kernel_time * max(count, 1))()
+    got = lib.tg_kernel_times(ctx, arr, count)
+    return {arr[k].name.decode(): (float(arr[k].ms), int(arr[k].launches))
+            for k in range(min(got, count))}
 
 
 TG_STATIC_MAX_VOXELS = 32768

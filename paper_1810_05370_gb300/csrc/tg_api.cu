@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -12,6 +13,10 @@
 #include "tg_internal.cuh"
 
 using namespace tg;
+
+namespace tg {
+thread_local const KHook* tg_khook = nullptr;
+}  // namespace tg
 
 namespace {
 
@@ -349,6 +354,42 @@ __global__ void k_cg_reset(CgScal* S, int count, double rtol, int maxit) {
   }
 }
 
+// Per-kernel timing of one context (tg_set_timing).  Each timed launch is bracketed by two
+// events on its stream; launches inside a CG solve carry the iteration they belong to and the
+// solve's slot, and count only if the solve was still running at that iteration (a host-driven
+// solve queues iterations ahead and the ones after convergence return at once).
+struct KRec {
+  int kid, e0, e1, iter, slot;
+};
+
+struct Prof {
+  KHook hook;
+  std::vector<cudaEvent_t> ev;   // pool, reused every step
+  int next;                      // first unused event of the pool
+  std::vector<KRec> recs;        // launches of the current step
+  std::vector<int> did;          // per solve slot: iterations that did work
+  int iter, slot;                // tag of the launches being queued (-1: not in a CG loop)
+  cudaStream_t open_st[4];       // stream -> its pending start event
+  int open_ev[4];
+  double call_ms[K_COUNT];       // this call
+  long long call_n[K_COUNT];
+  double cum_ms[K_COUNT];        // since timing was switched on
+  long long cum_n[K_COUNT];
+};
+
+const char* const kKernelNames[K_COUNT] = {
+    "k_diff_faces", "k_diff_diag", "k_to_f32", "k_divergence", "k_sl", "k_sl32",
+    "k_cn_init", "k_cn_matvec", "k_cn_update", "k_cn_pupdate",
+    "k_cn_ir_residual", "k_cn_ir_residual_df", "k_cn32_pupdate", "k_cn32_matvec",
+    "k_cn32_update", "k_cn_ir_correct", "k_react", "k_lame", "k_elas_coef", "k_elas_coef_df",
+    "k_elas32_coef", "k_df_pack3", "k_elas_extrapolate", "k_spec_mean", "k_spec_scale",
+    "k_elas_ir_residual", "k_elas_ir_residual_df", "k_elas32_scale_r", "k_spec_x_fwd",
+    "k_spec_y_fwd", "k_spec_z", "k_spec_zr", "k_spec_y_inv", "k_spec_x_inv", "k_spec_x_inv_p",
+    "k_elas32_matvec", "k_elas32_update", "k_elas32_matvec_spec", "k_elas32_update_spec",
+    "k_spec_update_xfwd", "k_elas_ir_correct", "k_elas_ir_finish", "k_elas_init",
+    "k_elas_init_spec", "k_elas_matvec", "k_elas_update", "k_elas_pupdate", "k_elas_update_spec",
+    "k_elas_pupdate_spec", "k_elas_finish"};
+
 }  // namespace
 
 struct tg_ctx {
@@ -382,14 +423,10 @@ struct tg_ctx {
   int prev_it_elas;
   int prev_it_inner[2];   // inner FP32 iterations of the first and of later refinement sweeps
   int prev_it_cn_inner[2];  // the same for the mixed precision's diffusion solves
-  // profiling: launches queued, and optional event timing of the elasticity operator kernel
+  // profiling: launches queued, and optional event timing of every kernel (tg_set_timing)
   long long launches;
   int timing;
-  std::vector<cudaEvent_t> ev;   // pairs (start, stop) per operator launch of one solve
-  double t_matvec_ms;
-  long long n_matvec;
-  double t_update_ms;    // the mixed spectral CG's fused update + x forward pass
-  long long n_update;
+  Prof prof;
   bool df_res;           // the mixed precision's residual in double-FP32 (df_residual_ok)
   bool cn_df;            // ... and that of its diffusion solves (cn_df_ok)
   bool in_batch;         // owned by a batch (its persistent solvers read FP64 faces)
@@ -429,6 +466,108 @@ tg_status status_of(const CgScal& s) {
   }
 }
 
+// ---------------------------------------------------------------- per-kernel timing
+int prof_event(tg_ctx* X) {
+  Prof& P = X->prof;
+  if (P.next == (int)P.ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    P.ev.push_back(e);
+  }
+  return P.next++;
+}
+
+int prof_open_index(const Prof& P, cudaStream_t st) {
+  for (int k = 0; k < 4; ++k)
+    if (P.open_ev[k] >= 0 && P.open_st[k] == st) return k;
+  return -1;
+}
+
+void prof_pre(void* self, cudaStream_t st) {
+  tg_ctx* X = static_cast<tg_ctx*>(self);
+  Prof& P = X->prof;
+  int k = prof_open_index(P, st);
+  if (k < 0)
+    for (k = 0; k < 4 && P.open_ev[k] >= 0; ++k) {
+    }
+  if (k >= 4) return;
+  const int e = prof_event(X);
+  if (e < 0 || cudaEventRecord(P.ev[e], st) != cudaSuccess) return;
+  P.open_st[k] = st;
+  P.open_ev[k] = e;
+}
+
+void prof_post(void* self, int kid, cudaStream_t st) {
+  tg_ctx* X = static_cast<tg_ctx*>(self);
+  Prof& P = X->prof;
+  const int k = prof_open_index(P, st);
+  if (k < 0) return;
+  const int e0 = P.open_ev[k];
+  P.open_ev[k] = -1;
+  const int e = prof_event(X);
+  if (e < 0 || cudaEventRecord(P.ev[e], st) != cudaSuccess) return;
+  P.recs.push_back({kid, e0, e, P.iter, P.slot});
+}
+
+void prof_reset_step(Prof& P) {
+  P.next = 0;
+  P.recs.clear();
+  P.did.clear();
+  P.iter = -1;
+  P.slot = -1;
+  for (int k = 0; k < 4; ++k) P.open_ev[k] = -1;
+}
+
+// a CG solve whose iterations are about to be queued: its slot, or -1 with timing off
+int prof_open_solve(tg_ctx* X) {
+  if (!X->timing) return -1;
+  X->prof.did.push_back(INT_MAX);
+  return (int)X->prof.did.size() - 1;
+}
+
+void prof_iter(tg_ctx* X, int slot, int q) {
+  X->prof.slot = slot;
+  X->prof.iter = slot >= 0 ? q : -1;
+}
+
+void prof_close_solve(tg_ctx* X, int slot, const CgScal* host, int nsolves) {
+  X->prof.iter = -1;
+  X->prof.slot = -1;
+  if (slot < 0) return;
+  int did = 0;
+  for (int r = 0; r < nsolves; ++r) did = std::max(did, host[r].it);
+  X->prof.did[slot] = did;
+}
+
+// after a step (its streams synchronised): add the launches that did work, then reuse the pool
+void prof_harvest(tg_ctx* X) {
+  Prof& P = X->prof;
+  for (const KRec& r : P.recs) {
+    if (r.iter >= 0 && r.slot >= 0 && r.slot < (int)P.did.size() && r.iter >= P.did[r.slot])
+      continue;
+    float ms = 0.0f;
+    if (cudaEventSynchronize(P.ev[r.e1]) != cudaSuccess) continue;
+    if (cudaEventElapsedTime(&ms, P.ev[r.e0], P.ev[r.e1]) != cudaSuccess) continue;
+    P.call_ms[r.kid] += ms;
+    P.call_n[r.kid] += 1;
+    P.cum_ms[r.kid] += ms;
+    P.cum_n[r.kid] += 1;
+  }
+  prof_reset_step(P);
+}
+
+// installs the context's timing hook for the calling thread while a call runs
+struct HookScope {
+  const KHook* saved;
+  explicit HookScope(tg_ctx* X) : saved(tg_khook) {
+    if (!X->timing) return;
+    X->prof.hook = {prof_pre, prof_post, X};
+    prof_reset_step(X->prof);
+    tg_khook = &X->prof.hook;
+  }
+  ~HookScope() { tg_khook = saved; }
+};
+
 // Queue iterations in chunks and read the device-side flags back between chunks.  Kernels of
 // a finished solve return at once, so overshooting a chunk only costs empty launches.
 // On stream st; `queued` iterations may already be in flight (then the loop reads the flags
@@ -436,12 +575,15 @@ tg_status status_of(const CgScal& s) {
 int first_chunk(int prev) { return prev > 0 ? std::max(1, prev - prev / 8) : 4; }
 
 template <class IterFn>
-tg_status drive_cg_on(tg_ctx* X, cudaStream_t st, IterFn iter, const CgScal* dev, int nsolves,
-                      int maxit, int prev, CgScal* host, long long queued = 0) {
+tg_status drive_cg_loop(tg_ctx* X, cudaStream_t st, IterFn iter, const CgScal* dev, int nsolves,
+                        int maxit, int prev, CgScal* host, long long queued, int slot) {
   int chunk = queued > 0 ? 0 : first_chunk(prev);
   const long long first = queued > 0 ? queued : chunk;
   for (;;) {
-    for (int c = 0; c < chunk; ++c) CK(iter((int)(queued + c)));
+    for (int c = 0; c < chunk; ++c) {
+      prof_iter(X, slot, (int)(queued + c));
+      CK(iter((int)(queued + c)));
+    }
     queued += chunk;
     CK(cudaMemcpyAsync(host, dev, nsolves * sizeof(CgScal), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -453,21 +595,22 @@ tg_status drive_cg_on(tg_ctx* X, cudaStream_t st, IterFn iter, const CgScal* dev
   }
 }
 
+// slot: the timing slot of a solve whose first iterations the caller queued itself (with
+// prof_iter tags), or INT_MIN to open one here
+template <class IterFn>
+tg_status drive_cg_on(tg_ctx* X, cudaStream_t st, IterFn iter, const CgScal* dev, int nsolves,
+                      int maxit, int prev, CgScal* host, long long queued = 0,
+                      int slot = INT_MIN) {
+  if (slot == INT_MIN) slot = prof_open_solve(X);
+  const tg_status s = drive_cg_loop(X, st, iter, dev, nsolves, maxit, prev, host, queued, slot);
+  prof_close_solve(X, slot, host, nsolves);
+  return s;
+}
+
 template <class IterFn>
 tg_status drive_cg(tg_ctx* X, IterFn iter, const CgScal* dev, int nsolves, int maxit, int prev,
                    CgScal* host) {
   return drive_cg_on(X, X->stream, iter, dev, nsolves, maxit, prev, host);
-}
-
-// grow the event pool to hold the events of `iters` timed iterations (three each: before and
-// after the operator kernel, after the update pass); false if events cannot be created
-bool ensure_events(tg_ctx* X, int iters) {
-  while ((int)X->ev.size() < 3 * iters) {
-    cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) return false;
-    X->ev.push_back(e);
-  }
-  return true;
 }
 
 // the single-species model (Eq. e:rd): c is carried in p, only it diffuses
@@ -684,7 +827,12 @@ tg_status cn_solve_mixed_concurrent(tg_ctx* X, tg_stats* stats) {
   CK(cudaGetLastError());
   CK(launch_cn_init(X->G, C, so, MASK_O));
   const int chunk = first_chunk(X->prev_it_diff);
-  for (int c = 0; c < chunk; ++c) CK(launch_cn_iter(X->G, C, so));
+  const int slot = prof_open_solve(X);
+  for (int c = 0; c < chunk; ++c) {
+    prof_iter(X, slot, c);
+    CK(launch_cn_iter(X->G, C, so));
+  }
+  prof_iter(X, -1, -1);
   X->launches += 2 + 3LL * chunk;
   // i and l on the context's stream meanwhile
   tg_status e = cn_solve3_mixed(X, stats, CN_MIXED_MASK);
@@ -696,7 +844,7 @@ tg_status cn_solve_mixed_concurrent(tg_ctx* X, tg_stats* stats) {
   e = drive_cg_on(X, so, [&](int) {
     X->launches += 3;
     return launch_cn_iter(X->G, C, so);
-  }, C.S, 3, X->prm.maxit_diff, X->prev_it_diff, host, chunk);
+  }, C.S, 3, X->prm.maxit_diff, X->prev_it_diff, host, chunk, slot);
   if (e != TG_OK) {
     cudaStreamSynchronize(so);
     return e;
@@ -733,21 +881,6 @@ Elas32 elas32_view(tg_ctx* X) {
   I.partial = X->partial;
   I.counter = X->counter;
   return I;
-}
-
-// add the event-timed operator launches that did work (the first `did` of `recorded`)
-void harvest_timing(tg_ctx* X, int recorded, int did, bool update = false) {
-  for (int q = 0; q < std::min(recorded, did); ++q) {
-    float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, X->ev[3 * q], X->ev[3 * q + 1]) == cudaSuccess) {
-      X->t_matvec_ms += ms;
-      X->n_matvec += 1;
-    }
-    if (update && cudaEventElapsedTime(&ms, X->ev[3 * q + 1], X->ev[3 * q + 2]) == cudaSuccess) {
-      X->t_update_ms += ms;
-      X->n_update += 1;
-    }
-  }
 }
 
 // TG_MIXED elasticity: iterative refinement with an FP64 residual and FP32 inner PCG.
@@ -809,24 +942,16 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
       X->launches += 5;
     }
     CgScal host[1];
-    int recorded = 0;
     const int slot = sweeps == 0 ? 0 : 1;
-    tg_status s = drive_cg(X, [&](int q) {
+    tg_status s = drive_cg(X, [&](int) {
       X->launches += spec ? 6 : 2;
-      const bool timed = X->timing && ensure_events(X, q + 1);
-      if (timed) {
-        cudaEventRecord(X->ev[3 * q], X->stream);
-        recorded = q + 1;
-      }
       cudaError_t e = spec ? launch_elas32_matvec_spec(X->G, I, X->stream)
                            : launch_elas32_matvec(X->G, I, X->stream);
-      if (timed) cudaEventRecord(X->ev[3 * q + 1], X->stream);
       if (e != cudaSuccess) return e;
       if (!spec) return launch_elas32_update(X->G, I, X->stream);
-      return launch_spectral_update(V, I, X->z32, X->stream, timed ? X->ev[3 * q + 2] : nullptr);
+      return launch_spectral_update(V, I, X->z32, X->stream);
     }, I.S, 1, X->prm.maxit_elas, X->prev_it_inner[slot], host);
     if (s != TG_OK) return s;
-    harvest_timing(X, recorded, host[0].it, spec);
     X->prev_it_inner[slot] = host[0].it;
     inner_total += host[0].it;
     if (host[0].status == CG_NONFINITE) return fail(X, TG_ERR_NONFINITE);
@@ -879,16 +1004,9 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
     X->launches += 2;
   }
   CgScal host[1];
-  int recorded = 0;
-  tg_status s = drive_cg(X, [&](int q) {
+  tg_status s = drive_cg(X, [&](int) {
     X->launches += spec ? 8 : 3;
-    const bool timed = X->timing && ensure_events(X, q + 1);
-    if (timed) {
-      cudaEventRecord(X->ev[3 * q], X->stream);
-      recorded = q + 1;
-    }
     cudaError_t e = launch_elas_matvec(X->G, E, X->stream);
-    if (timed) cudaEventRecord(X->ev[3 * q + 1], X->stream);
     if (e != cudaSuccess) return e;
     if (!spec) return launch_elas_update(X->G, E, X->stream);
     e = launch_elas_update_spec(X->G, E, X->stream);
@@ -898,8 +1016,6 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
   }, E.S, 1, X->prm.maxit_elas, X->prev_it_elas, host);
   if (s != TG_OK) return s;
   X->prev_it_elas = host[0].it;
-  // launches after convergence return at once: only the first `it` did the work
-  harvest_timing(X, recorded, host[0].it);
   if (stats) {
     stats->it_elas = host[0].it;
     stats->it_elas_outer = 1;
@@ -935,19 +1051,22 @@ tg_status build_elas_coef(tg_ctx* X, bool force) {
 
 void reset_profile(tg_ctx* X) {
   X->launches = 0;
-  X->t_matvec_ms = 0.0;
-  X->n_matvec = 0;
-  X->t_update_ms = 0.0;
-  X->n_update = 0;
+  for (int k = 0; k < K_COUNT; ++k) {
+    X->prof.call_ms[k] = 0.0;
+    X->prof.call_n[k] = 0;
+  }
   for (int q = 0; q < 4; ++q) X->t_phase[q] = 0.0;
 }
 
 void fill_profile(tg_ctx* X, tg_stats* stats) {
+  const Prof& P = X->prof;
   stats->launches = X->launches;
-  stats->t_elas_matvec_ms = X->t_matvec_ms;
-  stats->n_elas_matvec = X->n_matvec;
-  stats->t_spec_update_ms = X->t_update_ms;
-  stats->n_spec_update = X->n_update;
+  stats->t_elas_matvec_ms =
+      P.call_ms[K_ELAS_MATVEC] + P.call_ms[K_ELAS32_MATVEC] + P.call_ms[K_ELAS32_MATVEC_SPEC];
+  stats->n_elas_matvec =
+      P.call_n[K_ELAS_MATVEC] + P.call_n[K_ELAS32_MATVEC] + P.call_n[K_ELAS32_MATVEC_SPEC];
+  stats->t_spec_update_ms = P.call_ms[K_SPEC_UPDATE_XFWD];
+  stats->n_spec_update = P.call_n[K_SPEC_UPDATE_XFWD];
   for (int q = 0; q < 4; ++q) stats->t_phase_ms[q] = X->t_phase[q];
 }
 
@@ -1388,6 +1507,7 @@ tg_status tg_step(tg_ctx* X, double dt, int32_t nsteps, void* tape, tg_stats* st
   if (stats) memset(stats, 0, sizeof(*stats));
   reset_profile(X);
   CK(cudaSetDevice(X->device));
+  HookScope hook(X);
   const size_t stride = round_up((size_t)X->G.nvox * sizeof(double));
   for (int q = 0; q < T_COUNT; ++q)
     X->tape[q] = tape ? (double*)((char*)tape + (size_t)q * stride) : nullptr;
@@ -1397,6 +1517,7 @@ tg_status tg_step(tg_ctx* X, double dt, int32_t nsteps, void* tape, tg_stats* st
       X->tape[0] = nullptr;
       return fail(X, e);
     }
+    if (X->timing) prof_harvest(X);
     if (stats) stats->steps += 1;
   }
   X->tape[0] = nullptr;
@@ -1412,10 +1533,12 @@ tg_status tg_solve_elasticity(tg_ctx* X, double* const rhs[3], double* u[3], tg_
   if (stats) memset(stats, 0, sizeof(*stats));
   reset_profile(X);
   CK(cudaSetDevice(X->device));
+  HookScope hook(X);
   tg_status e = build_elas_coef(X, rhs == nullptr);
   if (e != TG_OK) return fail(X, e);
   double* const uu[3] = {u[0], u[1], u[2]};
   e = elas_solve(X, uu, rhs, rhs == nullptr, 0.0, stats);
+  if (e == TG_OK && X->timing) prof_harvest(X);
   if (e == TG_OK && stats) fill_profile(X, stats);
   return e;
 }
@@ -1513,8 +1636,29 @@ tg_status tg_diagnostics(tg_ctx* X, const double seed[3], double u_threshold,
 
 tg_status tg_set_timing(tg_ctx* X, int32_t enable) {
   if (!X) return TG_ERR_ARG;
+  if (enable && !X->timing) {
+    for (int k = 0; k < K_COUNT; ++k) {
+      X->prof.cum_ms[k] = 0.0;
+      X->prof.cum_n[k] = 0;
+    }
+  }
   X->timing = enable != 0;
   return TG_OK;
+}
+
+int32_t tg_kernel_times(const tg_ctx* X, tg_kernel_time* out, int32_t capacity) {
+  if (!X || capacity < 0 || (capacity > 0 && !out)) return -1;
+  int32_t count = 0;
+  for (int k = 0; k < K_COUNT; ++k) {
+    if (X->prof.cum_n[k] == 0) continue;
+    if (count < capacity) {
+      out[count].name = kKernelNames[k];
+      out[count].ms = X->prof.cum_ms[k];
+      out[count].launches = X->prof.cum_n[k];
+    }
+    ++count;
+  }
+  return count;
 }
 
 void tg_free(tg_ctx* X) {
@@ -1525,7 +1669,7 @@ void tg_free(tg_ctx* X) {
   }
   if (X->fork_ev) cudaEventDestroy(X->fork_ev);
   if (X->join_ev) cudaEventDestroy(X->join_ev);
-  for (cudaEvent_t e : X->ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : X->prof.ev) cudaEventDestroy(e);
   if (X->pev_ok)
     for (cudaEvent_t e : X->pev) cudaEventDestroy(e);
   delete X;

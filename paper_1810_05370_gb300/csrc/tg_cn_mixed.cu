@@ -312,26 +312,28 @@ cudaError_t launch_cn_ir_residual(const Geo& G, const Cn3& C, const Cn32& I, CgS
                                   bool init, double tau_min, int max_sweeps, int mask,
                                   cudaStream_t st) {
   if (C.df)
-    k_cn_ir_residual_df<<<G.grid, dim3(BX, BY), 0, st>>>(G, C, I, Sout, init ? 1 : 0, tau_min,
-                                                         max_sweeps, mask);
+    TG_TIMED(K_CN_IR_RESIDUAL_DF, st,
+             k_cn_ir_residual_df<<<G.grid, dim3(BX, BY), 0, st>>>(G, C, I, Sout, init ? 1 : 0, tau_min,
+                                                                  max_sweeps, mask));
   else
-    k_cn_ir_residual<<<G.grid, dim3(BX, BY), 0, st>>>(G, C, I, Sout, init ? 1 : 0, tau_min,
-                                                      max_sweeps, mask);
+    TG_TIMED(K_CN_IR_RESIDUAL, st,
+             k_cn_ir_residual<<<G.grid, dim3(BX, BY), 0, st>>>(G, C, I, Sout, init ? 1 : 0, tau_min,
+                                                               max_sweeps, mask));
   return cudaGetLastError();
 }
 
 // one inner iteration of the three FP32 solves: the first iteration of a sweep forms p from
 // the residual before the operator
 cudaError_t launch_cn32_iter(const Geo& G, const Cn32& I, cudaStream_t st) {
-  k_cn32_pupdate<<<flat_blocks(G), NT, 0, st>>>(G.nvox, I);
-  k_cn32_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, I);
-  k_cn32_update<<<flat_blocks(G), NT, 0, st>>>(G.nvox, I);
+  TG_TIMED(K_CN32_PUPDATE, st, k_cn32_pupdate<<<flat_blocks(G), NT, 0, st>>>(G.nvox, I));
+  TG_TIMED(K_CN32_MATVEC, st, k_cn32_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, I));
+  TG_TIMED(K_CN32_UPDATE, st, k_cn32_update<<<flat_blocks(G), NT, 0, st>>>(G.nvox, I));
   return cudaGetLastError();
 }
 
 cudaError_t launch_cn_ir_correct(const Geo& G, const Cn3& C, const Cn32& I, int mask,
                                  cudaStream_t st) {
-  k_cn_ir_correct<<<flat_blocks(G), NT, 0, st>>>(G.nvox, C, I, mask);
+  TG_TIMED(K_CN_IR_CORRECT, st, k_cn_ir_correct<<<flat_blocks(G), NT, 0, st>>>(G.nvox, C, I, mask));
   return cudaGetLastError();
 }
 

@@ -161,21 +161,23 @@ cudaError_t launch_diff_coef(const Geo& G, const DevParams& P, double dt, const 
   float2* df[3] = {nullptr, nullptr, nullptr};
   if (Kfdf)
     for (int d = 0; d < 3; ++d) df[d] = reinterpret_cast<float2*>(Kfdf[d]);
-  k_diff_faces<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, 0.5 * dt, g, w, f, Kf[0], Kf[1], Kf[2],
-                                                rho, df[0], df[1], df[2]);
-  k_diff_diag<<<G.grid, dim3(BX, BY), 0, st>>>(G, Kf[0], Kf[1], Kf[2], dsum, dinv);
+  TG_TIMED(K_DIFF_FACES, st,
+           k_diff_faces<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, 0.5 * dt, g, w, f, Kf[0], Kf[1], Kf[2],
+                                                         rho, df[0], df[1], df[2]));
+  TG_TIMED(K_DIFF_DIAG, st,
+           k_diff_diag<<<G.grid, dim3(BX, BY), 0, st>>>(G, Kf[0], Kf[1], Kf[2], dsum, dinv));
   return cudaGetLastError();
 }
 
 cudaError_t launch_cn_init(const Geo& G, const Cn3& C, cudaStream_t st, int mask) {
-  k_cn_init<<<G.grid, dim3(BX, BY), 0, st>>>(G, C, mask);
+  TG_TIMED(K_CN_INIT, st, k_cn_init<<<G.grid, dim3(BX, BY), 0, st>>>(G, C, mask));
   return cudaGetLastError();
 }
 
 cudaError_t launch_cn_iter(const Geo& G, const Cn3& C, cudaStream_t st) {
-  k_cn_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, C);
-  k_cn_update<<<G.grid, dim3(BX, BY), 0, st>>>(G, C);
-  k_cn_pupdate<<<G.grid, dim3(BX, BY), 0, st>>>(G, C);
+  TG_TIMED(K_CN_MATVEC, st, k_cn_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, C));
+  TG_TIMED(K_CN_UPDATE, st, k_cn_update<<<G.grid, dim3(BX, BY), 0, st>>>(G, C));
+  TG_TIMED(K_CN_PUPDATE, st, k_cn_pupdate<<<G.grid, dim3(BX, BY), 0, st>>>(G, C));
   return cudaGetLastError();
 }
 

@@ -291,51 +291,56 @@ __global__ void __launch_bounds__(NT) k_elas_finish(Geo G, Elas E, double inv_dt
 cudaError_t launch_elas_coef_df(const Geo& G, const DevParams& P, const Elas& E,
                                 const Elas32& I, const double* p, const double* n, bool force,
                                 cudaStream_t st) {
-  k_elas_coef_df<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, E, I, p, n, force ? 1 : 0);
+  TG_TIMED(K_ELAS_COEF_DF, st,
+           k_elas_coef_df<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, E, I, p, n, force ? 1 : 0));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas_coef(const Geo& G, const DevParams& P, const Elas& E, const double* p,
                              const double* n, bool force, cudaStream_t st) {
-  k_elas_coef<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, E, p, n, force ? 1 : 0);
+  TG_TIMED(K_ELAS_COEF, st,
+           k_elas_coef<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, E, p, n, force ? 1 : 0));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas_init(const Geo& G, const Elas& E, bool minus_b, cudaStream_t st) {
-  k_elas_init<false><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, minus_b ? 1 : 0);
+  TG_TIMED(K_ELAS_INIT, st,
+           k_elas_init<false><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, minus_b ? 1 : 0));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas_init_spec(const Geo& G, const Elas& E, bool minus_b, cudaStream_t st) {
-  k_elas_init<true><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, minus_b ? 1 : 0);
+  TG_TIMED(K_ELAS_INIT_SPEC, st,
+           k_elas_init<true><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, minus_b ? 1 : 0));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas_matvec(const Geo& G, const Elas& E, cudaStream_t st) {
-  k_elas_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
+  TG_TIMED(K_ELAS_MATVEC, st, k_elas_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, E));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas_update(const Geo& G, const Elas& E, cudaStream_t st) {
-  k_elas_update<false><<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
-  k_elas_pupdate<<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
+  TG_TIMED(K_ELAS_UPDATE, st, k_elas_update<false><<<G.grid, dim3(BX, BY), 0, st>>>(G, E));
+  TG_TIMED(K_ELAS_PUPDATE, st, k_elas_pupdate<<<G.grid, dim3(BX, BY), 0, st>>>(G, E));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas_update_spec(const Geo& G, const Elas& E, cudaStream_t st) {
-  k_elas_update<true><<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
+  TG_TIMED(K_ELAS_UPDATE_SPEC, st, k_elas_update<true><<<G.grid, dim3(BX, BY), 0, st>>>(G, E));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas_pupdate_spec(const Geo& G, const Elas& E, cudaStream_t st) {
-  k_elas_pupdate_spec<<<G.grid, dim3(BX, BY), 0, st>>>(G, E);
+  TG_TIMED(K_ELAS_PUPDATE_SPEC, st, k_elas_pupdate_spec<<<G.grid, dim3(BX, BY), 0, st>>>(G, E));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas_finish(const Geo& G, const Elas& E, double inv_dt, bool zero_rhs,
                                bool extrap, cudaStream_t st) {
-  k_elas_finish<<<G.grid, dim3(BX, BY), 0, st>>>(G, E, inv_dt, zero_rhs ? 1 : 0,
-                                                 extrap ? 1 : 0);
+  TG_TIMED(K_ELAS_FINISH, st,
+           k_elas_finish<<<G.grid, dim3(BX, BY), 0, st>>>(G, E, inv_dt, zero_rhs ? 1 : 0,
+                                                          extrap ? 1 : 0));
   return cudaGetLastError();
 }
 

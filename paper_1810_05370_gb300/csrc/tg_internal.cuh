@@ -15,6 +15,40 @@ constexpr int BY = 8;
 constexpr int NT = BX * BY;
 constexpr int NWARP = NT / 32;
 
+// ------------------------------------------------------------------ optional kernel timing
+// Kernels that the timing of tg_set_timing reports one by one.  Every launch site of the step
+// and the solves brackets its kernel with TG_TIMED; when the calling host thread has a hook
+// installed (a context with timing on), the hook records CUDA events before and after the
+// launch on the launch's own stream.  Without a hook the bracket is one thread-local load.
+enum KernelId : int {
+  K_DIFF_FACES, K_DIFF_DIAG, K_TO_F32, K_DIVERGENCE, K_SL, K_SL32,
+  K_CN_INIT, K_CN_MATVEC, K_CN_UPDATE, K_CN_PUPDATE,
+  K_CN_IR_RESIDUAL, K_CN_IR_RESIDUAL_DF, K_CN32_PUPDATE, K_CN32_MATVEC, K_CN32_UPDATE,
+  K_CN_IR_CORRECT, K_REACT, K_LAME, K_ELAS_COEF, K_ELAS_COEF_DF, K_ELAS32_COEF, K_DF_PACK3,
+  K_ELAS_EXTRAPOLATE, K_SPEC_MEAN, K_SPEC_SCALE, K_ELAS_IR_RESIDUAL, K_ELAS_IR_RESIDUAL_DF,
+  K_ELAS32_SCALE_R, K_SPEC_X_FWD, K_SPEC_Y_FWD, K_SPEC_Z, K_SPEC_ZR, K_SPEC_Y_INV,
+  K_SPEC_X_INV, K_SPEC_X_INV_P, K_ELAS32_MATVEC, K_ELAS32_UPDATE, K_ELAS32_MATVEC_SPEC,
+  K_ELAS32_UPDATE_SPEC, K_SPEC_UPDATE_XFWD, K_ELAS_IR_CORRECT, K_ELAS_IR_FINISH,
+  K_ELAS_INIT, K_ELAS_INIT_SPEC, K_ELAS_MATVEC, K_ELAS_UPDATE, K_ELAS_PUPDATE, K_ELAS_UPDATE_SPEC,
+  K_ELAS_PUPDATE_SPEC, K_ELAS_FINISH,
+  K_COUNT
+};
+
+struct KHook {
+  void (*pre)(void* self, cudaStream_t st);
+  void (*post)(void* self, int kid, cudaStream_t st);
+  void* self;
+};
+extern thread_local const KHook* tg_khook;
+
+#define TG_TIMED(kid, st, ...)                          \
+  do {                                                  \
+    const ::tg::KHook* h_ = ::tg::tg_khook;             \
+    if (h_) h_->pre(h_->self, (st));                    \
+    __VA_ARGS__;                                        \
+    if (h_) h_->post(h_->self, (kid), (st));            \
+  } while (0)
+
 struct Geo {
   int nx, ny, nz;
   long long nxy, nvox;
@@ -556,7 +590,7 @@ cudaError_t launch_spectral(const Spec<R>&, const R* const r[3], R* const z[3], 
                             cudaStream_t st, const PUpd<R>* pu = nullptr);
 cudaError_t launch_elas32_matvec_spec(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_spectral_update(const Spec<float>&, const Elas32&, float* const z[3],
-                                   cudaStream_t st, cudaEvent_t after_update = nullptr);
+                                   cudaStream_t st);
 cudaError_t launch_elas32_scale_r(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_elas32_update_spec(const Geo&, const Elas32&, cudaStream_t st);
 

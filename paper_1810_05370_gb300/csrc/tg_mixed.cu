@@ -281,20 +281,22 @@ int stream_blocks(long long n) {
 }  // namespace
 
 cudaError_t launch_to_f32(long long n, const F32Copy& c, cudaStream_t st) {
-  k_to_f32<<<stream_blocks(n), NT, 0, st>>>(n, c);
+  TG_TIMED(K_TO_F32, st, k_to_f32<<<stream_blocks(n), NT, 0, st>>>(n, c));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas32_coef(const Geo& G, const Elas& E, const Elas32& I, cudaStream_t st,
                               int parts) {
-  k_elas32_coef<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, I, parts);
+  TG_TIMED(K_ELAS32_COEF, st,
+           k_elas32_coef<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, I, parts));
   return cudaGetLastError();
 }
 
 cudaError_t launch_df_pack3(const Geo& G, const double* const b[3], double* const out[3],
                             cudaStream_t st) {
-  k_df_pack3<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, b[0], b[1], b[2], out[0], out[1],
-                                                   out[2]);
+  TG_TIMED(K_DF_PACK3, st,
+           k_df_pack3<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, b[0], b[1], b[2], out[0], out[1],
+                                                            out[2]));
   return cudaGetLastError();
 }
 
@@ -303,16 +305,19 @@ cudaError_t launch_df_pack3(const Geo& G, const double* const b[3], double* cons
 cudaError_t launch_elas_ir_residual(const Geo& G, const Elas& E, const Elas32& I, CgScal* Sout,
                                     bool minus_b, double tau_min, cudaStream_t st) {
   if (E.df)
-    k_elas_ir_residual<true><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, I, Sout, minus_b ? 1 : 0,
-                                                              tau_min, 1 << 30);
+    TG_TIMED(K_ELAS_IR_RESIDUAL_DF, st,
+             k_elas_ir_residual<true><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, I, Sout, minus_b ? 1 : 0,
+                                                                       tau_min, 1 << 30));
   else
-    k_elas_ir_residual<false><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, I, Sout, minus_b ? 1 : 0,
-                                                               tau_min, 1 << 30);
+    TG_TIMED(K_ELAS_IR_RESIDUAL, st,
+             k_elas_ir_residual<false><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, I, Sout, minus_b ? 1 : 0,
+                                                                        tau_min, 1 << 30));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas32_matvec(const Geo& G, const Elas32& I, cudaStream_t st) {
-  k_elas32_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, make_consts32(G), I);
+  TG_TIMED(K_ELAS32_MATVEC, st,
+           k_elas32_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, make_consts32(G), I));
   return cudaGetLastError();
 }
 
@@ -325,44 +330,50 @@ static int reduce_blocks(const Geo& G, long long items) {
 }
 
 cudaError_t launch_elas32_update(const Geo& G, const Elas32& I, cudaStream_t st) {
-  k_elas32_update<<<reduce_blocks(G, (G.nvox + 3) / 4), NT, 0, st>>>(G.nvox, I);
+  TG_TIMED(K_ELAS32_UPDATE, st,
+           k_elas32_update<<<reduce_blocks(G, (G.nvox + 3) / 4), NT, 0, st>>>(G.nvox, I));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas32_scale_r(const Geo& G, const Elas32& I, cudaStream_t st) {
-  k_elas32_scale_r<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, I);
+  TG_TIMED(K_ELAS32_SCALE_R, st, k_elas32_scale_r<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, I));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas32_matvec_spec(const Geo& G, const Elas32& I, cudaStream_t st) {
-  k_elas32_matvec_spec<<<G.grid, dim3(BX, BY), 0, st>>>(G, make_consts32(G), I);
+  TG_TIMED(K_ELAS32_MATVEC_SPEC, st,
+           k_elas32_matvec_spec<<<G.grid, dim3(BX, BY), 0, st>>>(G, make_consts32(G), I));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas32_update_spec(const Geo& G, const Elas32& I, cudaStream_t st) {
-  k_elas32_update_spec<<<reduce_blocks(G, (G.nvox + 3) / 4), NT, 0, st>>>(G.nvox, I);
+  TG_TIMED(K_ELAS32_UPDATE_SPEC, st,
+           k_elas32_update_spec<<<reduce_blocks(G, (G.nvox + 3) / 4), NT, 0, st>>>(G.nvox, I));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas_ir_correct(const Geo& G, const Elas& E, const Elas32& I, cudaStream_t st) {
-  k_elas_ir_correct<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, I);
+  TG_TIMED(K_ELAS_IR_CORRECT, st,
+           k_elas_ir_correct<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, I));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas_extrapolate(const Geo& G, const Elas& E, double dt, cudaStream_t st) {
-  k_elas_extrapolate<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, dt);
+  TG_TIMED(K_ELAS_EXTRAPOLATE, st,
+           k_elas_extrapolate<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, dt));
   return cudaGetLastError();
 }
 
 cudaError_t launch_elas_ir_finish(const Geo& G, const Elas& E, double inv_dt, bool zero_rhs,
                                   cudaStream_t st) {
-  k_elas_ir_finish<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, inv_dt, zero_rhs ? 1 : 0);
+  TG_TIMED(K_ELAS_IR_FINISH, st,
+           k_elas_ir_finish<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, inv_dt, zero_rhs ? 1 : 0));
   return cudaGetLastError();
 }
 
 cudaError_t launch_sl32(const Geo& G, double dt, const Sl32& S, cudaStream_t st) {
   const float3 dth = make_float3((float)(dt / G.h[0]), (float)(dt / G.h[1]), (float)(dt / G.h[2]));
-  k_sl32<<<G.grid, dim3(BX, BY), 0, st>>>(G, (float)dt, dth, S);
+  TG_TIMED(K_SL32, st, k_sl32<<<G.grid, dim3(BX, BY), 0, st>>>(G, (float)dt, dth, S));
   return cudaGetLastError();
 }
 

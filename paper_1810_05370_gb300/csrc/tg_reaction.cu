@@ -166,18 +166,21 @@ cudaError_t launch_react(const Geo& G, const DevParams& P, double dt, const doub
                          cudaStream_t st) {
   const int sg = single ? 1 : 0;
   if (fp32_rates)
-    k_react<float><<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, sg, rho, i_dag, p, i, n, g, w, o,
-                                                     l);
+    TG_TIMED(K_REACT, st,
+             k_react<float><<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, sg, rho, i_dag, p, i, n, g, w, o,
+                                                              l));
   else
-    k_react<double><<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, sg, rho, i_dag, p, i, n, g, w, o,
-                                                      l);
+    TG_TIMED(K_REACT, st,
+             k_react<double><<<G.grid, dim3(BX, BY), 0, st>>>(G, P, dt, sg, rho, i_dag, p, i, n, g, w, o,
+                                                               l));
   return cudaGetLastError();
 }
 
 cudaError_t launch_lame(const Geo& G, const DevParams& P, const double* p, const double* i,
                         const double* n, const double* g, const double* w, const double* f,
                         const double* bg, double* mu, double* lam, double* eta, cudaStream_t st) {
-  k_lame<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, p, i, n, g, w, f, bg, mu, lam, eta);
+  TG_TIMED(K_LAME, st,
+           k_lame<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, p, i, n, g, w, f, bg, mu, lam, eta));
   return cudaGetLastError();
 }
 

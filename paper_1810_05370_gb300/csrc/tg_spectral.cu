@@ -988,7 +988,8 @@ template <typename R>
 cudaError_t launch_spec_scale(const Geo& G, const Spec<R>& V, const Elas& E, cudaStream_t st) {
   const long long want = (G.nvox + NT - 1) / NT;
   const int blocks = (int)(want < 4096 ? (want > 0 ? want : 1) : 4096);
-  k_spec_scale<R><<<blocks, NT, 0, st>>>(G.nvox, V, E, G.ih2[0], G.ih2[1], G.ih2[2]);
+  TG_TIMED(K_SPEC_SCALE, st,
+           k_spec_scale<R><<<blocks, NT, 0, st>>>(G.nvox, V, E, G.ih2[0], G.ih2[1], G.ih2[2]));
   return cudaGetLastError();
 }
 
@@ -1004,7 +1005,8 @@ cudaError_t launch_spec_mean(long long n, const double* mu, const double* lam,
                              unsigned int* counter, cudaStream_t st) {
   const long long want = (n + NT - 1) / NT;
   const int blocks = (int)(want < 1024 ? (want > 0 ? want : 1) : 1024);
-  k_spec_mean<<<blocks, NT, 0, st>>>(n, mu, lam, eta, mean, partial, counter);
+  TG_TIMED(K_SPEC_MEAN, st,
+           k_spec_mean<<<blocks, NT, 0, st>>>(n, mu, lam, eta, mean, partial, counter));
   return cudaGetLastError();
 }
 
@@ -1014,16 +1016,16 @@ void launch_spec_z(const Spec<R>& V, CgScal* S, cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
     const dim3 g((V.nxh + ZR_COLS - 1) / ZR_COLS, V.ny);
     if (V.nz == 256) {
-      k_spec_zr<16><<<g, 16 * ZR_COLS, spec_smem_zr<16>(), st>>>(V, S);
+      TG_TIMED(K_SPEC_ZR, st, k_spec_zr<16><<<g, 16 * ZR_COLS, spec_smem_zr<16>(), st>>>(V, S));
       return;
     }
     if (V.nz == 128) {
-      k_spec_zr<8><<<g, 8 * ZR_COLS, spec_smem_zr<8>(), st>>>(V, S);
+      TG_TIMED(K_SPEC_ZR, st, k_spec_zr<8><<<g, 8 * ZR_COLS, spec_smem_zr<8>(), st>>>(V, S));
       return;
     }
   }
   const dim3 gz((V.nxh + V.tz - 1) / V.tz, V.ny);
-  k_spec_z<R><<<gz, V.nt_z, spec_smem_z(V), st>>>(V, S);
+  TG_TIMED(K_SPEC_Z, st, k_spec_z<R><<<gz, V.nt_z, spec_smem_z(V), st>>>(V, S));
 }
 
 template <typename R>
@@ -1031,37 +1033,40 @@ cudaError_t launch_spectral(const Spec<R>& V, const R* const r[3], R* const z[3]
                             cudaStream_t st, const PUpd<R>* pu) {
   const dim3 gx(V.ny / (2 * V.pb), V.nz, 3);
   const dim3 gy((V.nxh + V.tx - 1) / V.tx, V.nz, 3);
-  k_spec_x_fwd<R><<<gx, NT, spec_smem_x(V), st>>>(V, r[0], r[1], r[2], S);
-  k_spec_y<R, -1><<<gy, NT, spec_smem_y(V), st>>>(V, S);
+  TG_TIMED(K_SPEC_X_FWD, st,
+           k_spec_x_fwd<R><<<gx, NT, spec_smem_x(V), st>>>(V, r[0], r[1], r[2], S));
+  TG_TIMED(K_SPEC_Y_FWD, st, k_spec_y<R, -1><<<gy, NT, spec_smem_y(V), st>>>(V, S));
   launch_spec_z(V, S, st);
-  k_spec_y<R, +1><<<gy, NT, spec_smem_y(V), st>>>(V, S);
+  TG_TIMED(K_SPEC_Y_INV, st, k_spec_y<R, +1><<<gy, NT, spec_smem_y(V), st>>>(V, S));
   PUpd<R> P = {};
   if constexpr (sizeof(R) == 4) {
     if (pu) {
       P = *pu;
-      k_spec_x_inv<R, true><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S, P);
+      TG_TIMED(K_SPEC_X_INV_P, st,
+               k_spec_x_inv<R, true><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S, P));
       return cudaGetLastError();
     }
   }
-  k_spec_x_inv<R, false><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S, P);
+  TG_TIMED(K_SPEC_X_INV, st,
+           k_spec_x_inv<R, false><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S, P));
   return cudaGetLastError();
 }
 
 // one preconditioned CG iteration's update and preconditioner (mixed precision): the fused
 // update + x forward pass, then the remaining four passes
 cudaError_t launch_spectral_update(const Spec<float>& V, const Elas32& I, float* const z[3],
-                                   cudaStream_t st, cudaEvent_t after_update) {
+                                   cudaStream_t st) {
   const dim3 gx(V.ny / (2 * V.pb), V.nz, 3);
   const dim3 gy((V.nxh + V.tx - 1) / V.tx, V.nz, 3);
-  k_spec_update_xfwd<<<gx, NT, spec_smem_x(V), st>>>(V, I);
-  if (after_update) cudaEventRecord(after_update, st);
-  k_spec_y<float, -1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S);
+  TG_TIMED(K_SPEC_UPDATE_XFWD, st, k_spec_update_xfwd<<<gx, NT, spec_smem_x(V), st>>>(V, I));
+  TG_TIMED(K_SPEC_Y_FWD, st, k_spec_y<float, -1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S));
   launch_spec_z(V, I.S, st);
-  k_spec_y<float, +1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S);
+  TG_TIMED(K_SPEC_Y_INV, st, k_spec_y<float, +1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S));
   PUpd<float> P;   // p = z + beta p_old straight from the last pass
   for (int b = 0; b < 2; ++b)
     for (int a = 0; a < 3; ++a) P.p[b][a] = I.p[b][a];
-  k_spec_x_inv<float, true><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], I.S, P);
+  TG_TIMED(K_SPEC_X_INV_P, st,
+           k_spec_x_inv<float, true><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], I.S, P));
   return cudaGetLastError();
 }
 

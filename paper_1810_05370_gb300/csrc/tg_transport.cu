@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(NT) k_sl(Geo G, double dt, double3 dt_h,
 }  // namespace
 
 cudaError_t launch_divergence(const Geo& G, const double* const v[3], double* div, cudaStream_t st) {
-  k_divergence<<<G.grid, dim3(BX, BY), 0, st>>>(G, v[0], v[1], v[2], div);
+  TG_TIMED(K_DIVERGENCE, st,
+           k_divergence<<<G.grid, dim3(BX, BY), 0, st>>>(G, v[0], v[1], v[2], div));
   return cudaGetLastError();
 }
 
@@ -131,7 +132,8 @@ cudaError_t launch_sl_advect(const Geo& G, double dt, const double* const v[3], 
     b.a[s] = qout[s];
   }
   const double3 dth = make_double3(dt / G.h[0], dt / G.h[1], dt / G.h[2]);
-  k_sl<<<G.grid, dim3(BX, BY), 0, st>>>(G, dt, dth, v[0], v[1], v[2], div, a, b);
+  TG_TIMED(K_SL, st,
+           k_sl<<<G.grid, dim3(BX, BY), 0, st>>>(G, dt, dth, v[0], v[1], v[2], div, a, b));
   return cudaGetLastError();
 }
 

@@ -102,6 +102,10 @@ class Simulation:
     def set_timing(self, enable: bool = True):
         _tg.tg_set_timing(self.ctx, enable)
 
+    def kernel_times(self) -> dict:
+        """{kernel: (total ms, launches that did work)} since timing was switched on."""
+        return _tg.tg_kernel_times(self.ctx)
+
     def diagnostics(self, seed, u_threshold: float = 0.0, fields: bool = False) -> dict:
         """Mass-effect diagnostics of the current state (tg_diagnostics): summaries, plus the
         per-node tr T, max shear and det(I + grad u) tensors when fields is True."""
