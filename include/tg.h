@@ -14,7 +14,8 @@
  *   S3  reaction of p, i, n, g, w (Eq. e:p - e:w: logistic growth, go-or-grow switching,
  *       hypoxic death);  S4 oxygen reaction (Eq. e:ox);  S5 edema reaction (Eq. e:edema);
  *   S6  screened elasticity (eta I - L_h) u = -b (Eq. e:screening with Eq. e:lame and
- *       e:forcingfunction), CG from the extrapolated u^n + dt v^n, preconditioned by Jacobi
+ *       e:forcingfunction), CG from u extrapolated in time (see tg_reset_history),
+ *       preconditioned by Jacobi
  *       or (Section 3) by the exact inverse of the constant-coefficient operator with the
  *       domain means of mu, lambda, eta;
  *   S7  v = (u^{n+1} - u^n) / dt.
@@ -217,8 +218,19 @@ tg_status tg_diagnostics(tg_ctx* ctx, const double seed[3], double u_threshold,
 
 /* Replace the parameters used by later calls (e.g. a parameter sweep on one context).
  * Switching to TG_PRECOND_SPECTRAL or TG_PRECOND_SPECTRAL_SCALED needs a context whose
- * workspace was sized for either (TG_ERR_WORKSPACE otherwise). */
+ * workspace was sized for either (TG_ERR_WORKSPACE otherwise).  Clears the step history (see
+ * tg_reset_history). */
 tg_status tg_set_params(tg_ctx* ctx, const tg_params* params);
+
+/* The starting guess of a step's elasticity solve (the paper names none) is u extrapolated in
+ * time: linearly, u^n + dt v^n, on a context's first step, and quadratically,
+ * u^n + dt v^n + dt (v^n - v^{n-1}), on later ones, for which the context keeps v^{n-1} in its
+ * workspace.  The solution is the same within rtol_elas either way; the quadratic start needs
+ * fewer iterations.  A caller that overwrites u or v between steps (restoring a checkpoint,
+ * say) calls tg_reset_history so that the next step starts linearly again; without it the
+ * result is still correct to the tolerance, only the iteration count (and so the exact
+ * iterate) differs.  tg_init and tg_set_params clear the history too. */
+tg_status tg_reset_history(tg_ctx* ctx);
 
 /* Optional kernel timing for profiling.  With enable != 0 every kernel launch of tg_step and
  * tg_solve_elasticity is bracketed by two CUDA events on the stream it is launched on, and

@@ -73,7 +73,9 @@ def _make_types(cs):
     P = C.POINTER(R)
 
     class State(C.Structure):
-        _fields_ = [(name, P) for name in SPECIES] + [("u", P * 3), ("v", P * 3)]
+        _fields_ = [(name, P) for name in SPECIES] + [("u", P * 3), ("v", P * 3),
+                                                      ("vprev", P * 3),
+                                                      ("vprev_valid", C.c_int32)]
 
     class Stats(C.Structure):
         _fields_ = [("it_diff", C.c_int32 * 3), ("it_elas", C.c_int32),
@@ -133,13 +135,27 @@ class Oracle:
         return a.ctypes.data_as(C.POINTER(self.R))
 
     def state(self, st):
+        """The state struct over the dict's arrays.  The history of the elasticity start
+        (the previous step's velocity, keys vpx, vpy, vpz, and its flag vp_valid) is kept in
+        the dict itself, created on first use: successive steps on one dict extrapolate u
+        quadratically, like successive steps of one GPU context."""
         s = self.State()
         for name in SPECIES:
             setattr(s, name, self._ptr(st[name]))
+        if "vpx" not in st:
+            for c in "xyz":
+                st["vp" + c] = np.zeros_like(st["v" + c])
+            st["vp_valid"] = np.zeros((), dtype=np.int32)
         for a, c in enumerate("xyz"):
             s.u[a] = self._ptr(st["u" + c])
             s.v[a] = self._ptr(st["v" + c])
+            s.vprev[a] = self._ptr(st["vp" + c])
+        s.vprev_valid = int(np.real(st["vp_valid"]))
         return s
+
+    @staticmethod
+    def _keep_history(st, s):
+        st["vp_valid"] = np.asarray(s.vprev_valid, dtype=np.int32)
 
     @staticmethod
     def _stats_dict(s):
@@ -154,16 +170,20 @@ class Oracle:
     def init(self, n, params, st, L=None):
         """u^0 from the state (v^0 = 0); st is a dict of arrays modified in place."""
         stats = self.Stats()
+        s = self.state(st)
         rc = self.lib.or_init(C.byref(self.grid(n, L)), C.byref(self.params(params)),
-                              C.byref(self.state(st)), C.byref(stats))
+                              C.byref(s), C.byref(stats))
         self._check(rc, "init")
+        self._keep_history(st, s)
         return self._stats_dict(stats)
 
     def step(self, n, params, dt, st, L=None):
         stats = self.Stats()
+        s = self.state(st)
         rc = self.lib.or_step(C.byref(self.grid(n, L)), C.byref(self.params(params)),
-                              C.c_double(dt), C.byref(self.state(st)), C.byref(stats))
+                              C.c_double(dt), C.byref(s), C.byref(stats))
         self._check(rc, "step")
+        self._keep_history(st, s)
         return self._stats_dict(stats)
 
     # ------------------------------------------------------------------ building blocks

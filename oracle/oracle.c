@@ -891,6 +891,7 @@ int or_init(const or_grid* G, const or_params* P, or_state* S, or_stats* stats) 
     memset(S->u[a], 0, (size_t)m * sizeof(real_t));
     memset(S->v[a], 0, (size_t)m * sizeof(real_t));
   }
+  S->vprev_valid = 0;
   int32_t it = 0;
   double rr = 0.0;
   int st = elasticity_substep(G, P, S, &it, &rr);
@@ -910,7 +911,9 @@ int or_init(const or_grid* G, const or_params* P, or_state* S, or_stats* stats) 
  *  S1  semi-Lagrangian advection of p, i, n, g, w (conservative) and f with v^n;
  *  S2  Crank-Nicolson diffusion of i, o and edema l; the increment of i leaves g and w;
  *  S3  reaction of p, i, n, g, w;  S4 oxygen reaction;  S5 edema reaction;
- *  S6  elasticity solve for u^{n+1}, started from u^n + dt v^n;
+ *  S6  elasticity solve for u^{n+1}, started from the extrapolation of u in time: quadratic,
+ *      u^n + dt v^n + dt (v^n - v^{n-1}), when the previous step's velocity is kept
+ *      (S->vprev), else linear, u^n + dt v^n;
  *  S7  v^{n+1} = (u^{n+1} - u^n) / dt. */
 int or_step(const or_grid* G, const or_params* P, double dt, or_state* S, or_stats* stats) {
   if (!valid_grid(G) || !(dt > 0.0)) return OR_ERR_ARG;
@@ -961,12 +964,23 @@ int or_step(const or_grid* G, const or_params* P, double dt, or_state* S, or_sta
     /* S6 - S7 */
     real_t* u_old[3] = {qout[1], qout[2], qout[3]};
     for (int a = 0; a < 3; ++a) memcpy(u_old[a], S->u[a], (size_t)m * sizeof(real_t));
-    /* the solve starts from the linear extrapolation u^n + dt v^n (= 2 u^n - u^{n-1}) */
+    /* the solve starts from the extrapolation of u through u^n, u^{n-1} (and u^{n-2}):
+     * d = dt v^n is the linear increment (u^n + d = 2 u^n - u^{n-1}); with the previous
+     * step's velocity, q = dt (v^n - v^{n-1}) makes it quadratic
+     * (u^n + d + q = 3 u^n - 3 u^{n-1} + u^{n-2}) */
+    const int quad = S->vprev[0] != NULL && S->vprev_valid;
     for (int a = 0; a < 3; ++a)
-      for (int64_t e = 0; e < m; ++e) S->u[a][e] = S->u[a][e] + dt * S->v[a][e];
+      for (int64_t e = 0; e < m; ++e) {
+        real_t s = dt * S->v[a][e];
+        if (quad) s = s + dt * (S->v[a][e] - S->vprev[a][e]);
+        S->u[a][e] = S->u[a][e] + s;
+      }
     st = elasticity_substep(G, P, S, &local.it_elas, &local.relres_elas);
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) {
+      if (S->vprev[0] != NULL) memcpy(S->vprev[a], S->v[a], (size_t)m * sizeof(real_t));
       for (int64_t e = 0; e < m; ++e) S->v[a][e] = (S->u[a][e] - u_old[a][e]) / dt;
+    }
+    if (S->vprev[0] != NULL) S->vprev_valid = 1;
   }
   if (stats) *stats = local;
   free(K); free(Kf[0]); free(Kf[1]); free(Kf[2]); free(rho);

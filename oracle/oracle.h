@@ -45,6 +45,11 @@ typedef struct {
 typedef struct {
   real_t *p, *i, *n, *g, *w, *f, *o, *l, *bg;   /* species and materials               */
   real_t *u[3], *v[3];                           /* displacement, velocity              */
+  /* optional history of the elasticity solve's starting guess: the velocity at the start of
+   * the previous step (vprev[0] == NULL: none kept); vprev_valid says whether it holds one.
+   * or_init clears vprev_valid, or_step uses and then refreshes it. */
+  real_t *vprev[3];
+  int32_t vprev_valid;
 } or_state;
 
 typedef struct {

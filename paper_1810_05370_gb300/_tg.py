@@ -105,6 +105,7 @@ def _load():
         "tg_solve_elasticity": (C.c_int, [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(tg_stats)]),
         "tg_set_params": (C.c_int, [C.c_void_p, P(tg_params)]),
         "tg_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+        "tg_reset_history": (C.c_int, [C.c_void_p]),
         "tg_kernel_times": (C.c_int32, [C.c_void_p, P(tg_kernel_time), C.c_int32]),
         "tg_diagnostics": (C.c_int, [C.c_void_p, P(C.c_double), C.c_double, P(C.c_void_p),
                                      P(tg_diag)]),
@@ -258,6 +259,12 @@ def tg_set_params(ctx, params: tg_params):
     rc = lib.tg_set_params(ctx, C.byref(params))
     if rc != TG_OK:
         raise TGError(rc, "tg_set_params")
+
+
+def tg_reset_history(ctx):
+    rc = lib.tg_reset_history(ctx)
+    if rc != TG_OK:
+        raise TGError(rc, "tg_reset_history")
 
 
 def tg_set_timing(ctx, enable: bool):

@@ -30,6 +30,7 @@ enum Arr {
   A_DSUM_E0, A_DSUM_E1, A_DSUM_E2, A_DINV_E0, A_DINV_E1, A_DINV_E2,
   A_B0, A_B1, A_B2, A_DU0, A_DU1, A_DU2, A_ER0, A_ER1, A_ER2, A_EP0, A_EP1, A_EP2,
   A_EQ0, A_EQ1, A_EQ2,
+  A_VP0, A_VP1, A_VP2,   // velocity at the previous step's start (quadratic extrapolation)
   // (hi, lo) FP32 pairs of u, mu, lambda for the double-FP32 residual (TG_MIXED only), and of
   // the diffusion faces and fields for the diffusion solves' double-FP32 residual
   A_UDF0, A_UDF1, A_UDF2, A_MUDF, A_LAMDF,
@@ -430,6 +431,8 @@ struct tg_ctx {
   bool df_res;           // the mixed precision's residual in double-FP32 (df_residual_ok)
   bool cn_df;            // ... and that of its diffusion solves (cn_df_ok)
   bool in_batch;         // owned by a batch (its persistent solvers read FP64 faces)
+  bool hist_ok;          // the A_VP arrays hold the previous step's starting velocity: the next
+                         // step's elasticity solve starts from the quadratic extrapolation
   cudaEvent_t pev[5];    // phase boundaries of a step (created on first use)
   bool pev_ok;
   double t_phase[4];
@@ -662,6 +665,7 @@ Elas elas_view(tg_ctx* X, double* const u[3], double* const b[3]) {
     E.q[d] = X->a[A_EQ0 + d];
     E.u[d] = u[d];
     E.v[d] = X->st.v[d];
+    E.vp[d] = X->a[A_VP0 + d];
     E.z[d] = X->z64[d];
     E.udf[d] = reinterpret_cast<float2*>(X->a[A_UDF0 + d]);
   }
@@ -896,8 +900,8 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
   const Elas32 I = elas32_view(X);
   CgScal* Sout = X->scal + 3;
   const size_t bytes = (size_t)X->G.nvox * sizeof(double);
-  if (inv_dt > 0.0) {   // a step's solve: start from the extrapolated u^n + dt v^n
-    CK(launch_elas_extrapolate(X->G, E, 1.0 / inv_dt, X->stream));
+  if (inv_dt > 0.0) {   // a step's solve: start from u extrapolated in time
+    CK(launch_elas_extrapolate(X->G, E, 1.0 / inv_dt, X->hist_ok, X->stream));
     X->launches += 1;
   } else {
     for (int d = 0; d < 3; ++d) CK(cudaMemsetAsync(E.du[d], 0, bytes, X->stream));
@@ -982,8 +986,8 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
   k_cg_reset<<<1, 32, 0, X->stream>>>(X->scal + 3, 1, X->prm.rtol_elas, X->prm.maxit_elas);
   CK(cudaGetLastError());
   const double* const r64[3] = {E.r[0], E.r[1], E.r[2]};
-  if (inv_dt > 0.0) {   // a step's solve: start from the extrapolated u^n + dt v^n
-    CK(launch_elas_extrapolate(X->G, E, 1.0 / inv_dt, X->stream));
+  if (inv_dt > 0.0) {   // a step's solve: start from u extrapolated in time
+    CK(launch_elas_extrapolate(X->G, E, 1.0 / inv_dt, X->hist_ok, X->stream));
     X->launches += 1;
   }
   Spec<double> V = X->sp64;   // the scaled preconditioner's view carries s
@@ -1024,7 +1028,8 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
   }
   tg_status e = status_of(host[0]);
   if (e != TG_OK) return fail(X, e);
-  CK(launch_elas_finish(X->G, E, inv_dt, host[0].status == CG_ZERO_RHS, inv_dt > 0.0,
+  CK(launch_elas_finish(X->G, E, inv_dt, host[0].status == CG_ZERO_RHS,
+                        inv_dt > 0.0 ? (X->hist_ok ? 2 : 1) : 0,
                         X->stream));
   X->launches += 1;
   CK(cudaStreamSynchronize(X->stream));
@@ -1203,6 +1208,7 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   if (e != TG_OK) return e;
   e = elas_solve(X, S.u, nullptr, true, 1.0 / dt, stats);
   if (e != TG_OK) return e;
+  X->hist_ok = true;   // the finish kept v^n: the next step may extrapolate quadratically
   phase_mark(X, 4);
   for (int d = 0; d < 3; ++d) REC(T_UP0 + d, S.u[d]);
   phase_harvest(X);
@@ -1594,6 +1600,13 @@ tg_status tg_set_params(tg_ctx* X, const tg_params* params) {
   X->df_res = df_residual_ok(X);
   X->cn_df = cn_df_ok(X);
   X->dp = make_dev_params(params);
+  X->hist_ok = false;
+  return TG_OK;
+}
+
+tg_status tg_reset_history(tg_ctx* X) {
+  if (!X) return TG_ERR_ARG;
+  X->hist_ok = false;
   return TG_OK;
 }
 
@@ -1872,7 +1885,7 @@ tg_status queue_post_diffusion(tg_ctx* X, double dt) {
   double* const u[3] = {S.u[0], S.u[1], S.u[2]};
   const Elas E = elas_view(X, u, nullptr);
   CK(launch_elas32_coef(G, E, elas32_view(X), s));
-  CK(launch_elas_extrapolate(G, E, dt, s));   // u^n + dt v^n; du = dt v^n
+  CK(launch_elas_extrapolate(G, E, dt, false, s));   // u^n + dt v^n; du = dt v^n
   return TG_OK;
 }
 

@@ -263,8 +263,10 @@ __global__ void __launch_bounds__(NT) k_elas_pupdate_spec(Geo G, Elas E) {
   }
 }
 
-// u += du (du = -u when the right-hand side vanished, i.e. u = 0), v = vo + du / dt with
-// vo = v^n when the solve started from the extrapolated u^n + dt v^n (extrap), else 0
+// u += du (du = -u when the right-hand side vanished, i.e. u = 0), v = vo + du / dt with vo
+// the velocity of the starting guess: v^n for the linear extrapolation (extrap == 1),
+// v^n + (v^n - v^{n-1}) for the quadratic one (extrap == 2), 0 without (extrap == 0).  A step
+// keeps v^n in vp before writing v^{n+1}.
 __global__ void __launch_bounds__(NT) k_elas_finish(Geo G, Elas E, double inv_dt, int zero_rhs,
                                                     int extrap) {
   const int i = blockIdx.x * BX + threadIdx.x;
@@ -279,7 +281,9 @@ __global__ void __launch_bounds__(NT) k_elas_finish(Geo G, Elas E, double inv_dt
       const double du = zero_rhs ? -uo : E.du[a][c];
       E.u[a][c] = zero_rhs ? 0.0 : uo + du;
       if (inv_dt > 0.0) {
-        const double vo = extrap ? E.v[a][c] : 0.0;
+        const double vn = E.v[a][c];
+        const double vo = extrap == 0 ? 0.0 : (extrap == 1 ? vn : vn + (vn - E.vp[a][c]));
+        if (E.vp[a]) E.vp[a][c] = vn;
         E.v[a][c] = vo + du * inv_dt;
       }
     }
@@ -337,10 +341,10 @@ cudaError_t launch_elas_pupdate_spec(const Geo& G, const Elas& E, cudaStream_t s
 }
 
 cudaError_t launch_elas_finish(const Geo& G, const Elas& E, double inv_dt, bool zero_rhs,
-                               bool extrap, cudaStream_t st) {
+                               int extrap, cudaStream_t st) {
   TG_TIMED(K_ELAS_FINISH, st,
            k_elas_finish<<<G.grid, dim3(BX, BY), 0, st>>>(G, E, inv_dt, zero_rhs ? 1 : 0,
-                                                          extrap ? 1 : 0));
+                                                          extrap));
   return cudaGetLastError();
 }
 

@@ -455,6 +455,8 @@ struct Elas {
   double* q[3];
   double* u[3];      // displacement (in: u^n, out: u^{n+1})
   double* v[3];      // velocity (written when dt > 0)
+  double* vp[3];     // velocity at the previous step's start (the quadratic extrapolation's
+                     // history; a step's finish stores v^n there before writing v^{n+1})
   double* z[3];      // spectral preconditioner output (null with Jacobi)
   // double-FP32 residual of the mixed precision (df != 0): F, G and dsum then hold (hi, lo)
   // FP32 pairs instead of FP64 values, and udf, mudf, lamdf the pairs of u, mu and lambda
@@ -554,7 +556,7 @@ cudaError_t launch_elas_init_spec(const Geo&, const Elas&, bool rhs_is_minus_b, 
 cudaError_t launch_elas_update_spec(const Geo&, const Elas&, cudaStream_t st);
 cudaError_t launch_elas_pupdate_spec(const Geo&, const Elas&, cudaStream_t st);
 cudaError_t launch_elas_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
-                               bool extrap, cudaStream_t st);
+                               int extrap, cudaStream_t st);
 
 // mixed precision (tg_mixed.cu)
 cudaError_t launch_to_f32(long long n, const F32Copy& c, cudaStream_t st);
@@ -568,7 +570,8 @@ cudaError_t launch_elas_ir_residual(const Geo&, const Elas&, const Elas32&, CgSc
 cudaError_t launch_elas32_matvec(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_elas32_update(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_elas_ir_correct(const Geo&, const Elas&, const Elas32&, cudaStream_t st);
-cudaError_t launch_elas_extrapolate(const Geo&, const Elas&, double dt, cudaStream_t st);
+cudaError_t launch_elas_extrapolate(const Geo&, const Elas&, double dt, bool quadratic,
+                                    cudaStream_t st);
 cudaError_t launch_elas_ir_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
                                   cudaStream_t st);
 cudaError_t launch_sl32(const Geo&, double dt, const Sl32&, cudaStream_t st);

@@ -166,21 +166,27 @@ __global__ void __launch_bounds__(NT) k_elas_ir_correct(long long n, Elas E, Ela
                         1.0 / I.S->scale);
 }
 
-// Starting guess of a step's solve, linear extrapolation in time: u = u^n + dt v^n
-// (= 2 u^n - u^{n-1}), du = dt v^n so that v^{n+1} = du / dt still measures u^{n+1} - u^n
-__global__ void __launch_bounds__(NT) k_elas_extrapolate(long long n, Elas E, double dt) {
+// Starting guess of a step's solve, extrapolation in time.  Linear: the increment
+// s = dt v^n gives u^n + s = 2 u^n - u^{n-1}.  Quadratic (the previous step's velocity kept in
+// vp): s = dt v^n + dt (v^n - v^{n-1}) gives 3 u^n - 3 u^{n-1} + u^{n-2}.  u = u^n + s and
+// du = s, so that v^{n+1} = du / dt still measures u^{n+1} - u^n.  Each operation is rounded
+// on its own (no contraction), in the oracle's order.
+__global__ void __launch_bounds__(NT) k_elas_extrapolate(long long n, Elas E, double dt,
+                                                         int quadratic) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double d = __dmul_rn(dt, E.v[a][c]);   // rounded as u + dt v is, no contraction
-      E.u[a][c] = __dadd_rn(E.u[a][c], d);
-      E.du[a][c] = d;
+      const double v = E.v[a][c];
+      double s = __dmul_rn(dt, v);
+      if (quadratic) s = __dadd_rn(s, __dmul_rn(dt, __dsub_rn(v, E.vp[a][c])));
+      E.u[a][c] = __dadd_rn(E.u[a][c], s);
+      E.du[a][c] = s;
     }
   }
 }
 
-// v = du / dt; a vanishing right-hand side means u = 0
+// v = du / dt (a step: v^n is kept in vp first); a vanishing right-hand side means u = 0
 __global__ void __launch_bounds__(NT) k_elas_ir_finish(long long n, Elas E, double inv_dt,
                                                        int zero_rhs) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -192,7 +198,10 @@ __global__ void __launch_bounds__(NT) k_elas_ir_finish(long long n, Elas E, doub
         du -= E.u[a][c];
         E.u[a][c] = 0.0;
       }
-      if (inv_dt > 0.0) E.v[a][c] = du * inv_dt;
+      if (inv_dt > 0.0) {
+        if (E.vp[a]) E.vp[a][c] = E.v[a][c];
+        E.v[a][c] = du * inv_dt;
+      }
     }
   }
 }
@@ -358,9 +367,11 @@ cudaError_t launch_elas_ir_correct(const Geo& G, const Elas& E, const Elas32& I,
   return cudaGetLastError();
 }
 
-cudaError_t launch_elas_extrapolate(const Geo& G, const Elas& E, double dt, cudaStream_t st) {
+cudaError_t launch_elas_extrapolate(const Geo& G, const Elas& E, double dt, bool quadratic,
+                                    cudaStream_t st) {
   TG_TIMED(K_ELAS_EXTRAPOLATE, st,
-           k_elas_extrapolate<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, dt));
+           k_elas_extrapolate<<<stream_blocks(G.nvox), NT, 0, st>>>(G.nvox, E, dt,
+                                                                    quadratic ? 1 : 0));
   return cudaGetLastError();
 }
 

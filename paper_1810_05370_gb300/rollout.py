@@ -70,6 +70,7 @@ class Rollout:
     def _restore(self, s):
         for k, v in self.checkpoints[s].items():
             self.sim.state[k].copy_(v)
+        self.sim.reset_history()
 
     def _last_segment(self):
         return ((self.steps - 1) // self.every) * self.every

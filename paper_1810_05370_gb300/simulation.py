@@ -99,6 +99,11 @@ class Simulation:
         rp = None if rhs is None else [r.data_ptr() for r in rhs]
         return _tg.tg_solve_elasticity(self.ctx, rp, [x.data_ptr() for x in u])
 
+    def reset_history(self):
+        """Forget the previous step's velocity (after overwriting u or v): the next step's
+        elasticity solve starts from the linear extrapolation again."""
+        _tg.tg_reset_history(self.ctx)
+
     def set_timing(self, enable: bool = True):
         _tg.tg_set_timing(self.ctx, enable)
 

@@ -697,6 +697,36 @@ def test_step_conserves_total_cell_mass_pointwise_without_flow(oracle):
     assert np.max(np.abs(st["vx"])) > 0        # the elasticity solve produced a velocity
 
 
+@pytest.mark.parametrize("history", [False, True])
+def test_elasticity_start_is_the_polynomial_extrapolation_in_time(oracle, history):
+    """The starting guess of a step's elasticity solve: with a tolerance no residual can miss
+    the solve stops at its start, so u^{n+1} shows it.  Without a kept history it must be the
+    line through u^{n-1} = u^n - dt v^n and u^n, extrapolated to t^{n+1} (2 u^n - u^{n-1});
+    with the previous step's velocity it must be the parabola through u^{n-2}, u^{n-1}, u^n
+    (3 u^n - 3 u^{n-1} + u^{n-2}, equal spacing).  The step then keeps v^n as the history."""
+    n = (12, 10, 8)
+    dt = 0.01
+    st = initial_state(n, seed=6)
+    rng = np.random.default_rng(2)
+    X, Y, Z = mesh(n)
+    U, V, VP = ([0.01 * rng.standard_normal() * np.sin(X + a) * np.cos(Y - a) + 0 * Z
+                 for a in range(3)] for _ in range(3))
+    for a, c in enumerate("xyz"):
+        st["u" + c] = U[a].copy()       # the oracle works in place
+        st["v" + c] = V[a].copy()
+        st["vp" + c] = VP[a].copy()
+    st["vp_valid"] = np.asarray(1 if history else 0, dtype=np.int32)
+    s = oracle.step(n, workload_params(rtol_elas=1e30), dt, st)
+    assert s["it_elas"] == 0
+    for a, c in enumerate("xyz"):
+        u1 = U[a] - dt * V[a]              # u^{n-1}
+        u2 = u1 - dt * VP[a]               # u^{n-2}
+        want = 3 * U[a] - 3 * u1 + u2 if history else 2 * U[a] - u1
+        assert np.max(np.abs(st["u" + c] - want)) <= 1e-15 * np.abs(U[a]).max() + 1e-18
+        assert np.array_equal(st["vp" + c], V[a])
+    assert int(st["vp_valid"]) == 1
+
+
 def test_init_displacement_points_away_from_tumor(oracle):
     """Sign reading of Eq. e:screening: the tumor pushes tissue outward."""
     n = (32, 32, 32)
