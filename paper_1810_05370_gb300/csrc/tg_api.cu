@@ -382,7 +382,7 @@ const char* const kKernelNames[K_COUNT] = {
     "k_diff_faces", "k_diff_diag", "k_to_f32", "k_divergence", "k_sl", "k_sl32",
     "k_cn_init", "k_cn_matvec", "k_cn_update", "k_cn_pupdate",
     "k_cn_ir_residual", "k_cn_ir_residual_df", "k_cn32_pupdate", "k_cn32_matvec",
-    "k_cn32_update", "k_cn_ir_correct", "k_react", "k_lame", "k_elas_coef", "k_elas_coef_df",
+    "k_cn32_update", "k_cn_ir_correct", "k_cn32_neumann", "k_react", "k_lame", "k_elas_coef", "k_elas_coef_df",
     "k_elas32_coef", "k_df_pack3", "k_elas_extrapolate", "k_spec_mean", "k_spec_scale",
     "k_elas_ir_residual", "k_elas_ir_residual_df", "k_elas32_scale_r", "k_spec_x_fwd",
     "k_spec_y_fwd", "k_spec_z", "k_spec_zr", "k_spec_y_inv", "k_spec_x_inv", "k_spec_x_inv_p",
@@ -736,6 +736,7 @@ Cn32 cn32_view(tg_ctx* X) {
     I.Kf[r] = X->b32[B_CKF0 + r];
   }
   I.dinv = X->b32[B_CDINV];
+  for (int r = 0; r < 3; ++r) I.z[r] = nullptr;
   I.S = X->scal + 5;
   I.partial = X->partial;
   I.counter = X->counter;
@@ -743,10 +744,22 @@ Cn32 cn32_view(tg_ctx* X) {
 }
 
 // S2 in the mixed precision: FP64 residuals around FP32 inner solves (the FP32 faces and
-// diagonal were written in S0).  Statistics count inner iterations.
+// diagonal were written in S0).  Statistics count inner iterations.  The inner CG of up to two
+// solves is preconditioned by the Neumann-series polynomial (launch_cn32_iter), which needs
+// about a third of Jacobi's iterations at 256^3; z lives in the elasticity's second p buffer,
+// free during S2.
 tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
   const Cn3 C = cn_view(X);
-  const Cn32 I = cn32_view(X);
+  Cn32 I = cn32_view(X);
+  int slot[2] = {-1, -1}, nslot = 0;
+  for (int r = 0; r < 3; ++r)
+    if ((mask >> r) & 1) {
+      if (nslot < 2) slot[nslot] = r;
+      ++nslot;
+    }
+  if (nslot <= 2)
+    for (int q = 0; q < nslot; ++q) I.z[slot[q]] = X->b32[B_PB0 + slot[q]];
+  const long long cap = (long long)X->G.nblocks * MAX_NV;
   k_cg_reset<<<1, 32, 0, X->stream>>>(X->scal, 3, X->prm.rtol_diff, X->prm.maxit_diff);
   CK(cudaGetLastError());
   X->launches += 1;
@@ -773,11 +786,11 @@ tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
     for (int r = 0; r < 3; ++r) any |= out[r].status == CG_RUNNING;
     if (!any) break;
     CgScal host[3];
-    const int slot = sweeps == 0 ? 0 : 1;
+    const int sw = sweeps == 0 ? 0 : 1;
     tg_status st = drive_cg(X, [&](int) {
-      X->launches += 3;
-      return launch_cn32_iter(X->G, I, X->stream);
-    }, I.S, 3, X->prm.maxit_diff, X->prev_it_cn_inner[slot], host);
+      X->launches += nslot <= 2 ? 4 : 3;
+      return launch_cn32_iter(X->G, I, X->stream, slot[0], slot[1], cap);
+    }, I.S, 3, X->prm.maxit_diff, X->prev_it_cn_inner[sw], host);
     if (st != TG_OK) return st;
     int itmax = 0;
     for (int r = 0; r < 3; ++r) {
@@ -785,7 +798,7 @@ tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
       itmax = std::max(itmax, host[r].it);
       if (host[r].status == CG_NONFINITE) return fail(X, TG_ERR_NONFINITE);
     }
-    X->prev_it_cn_inner[slot] = itmax;
+    X->prev_it_cn_inner[sw] = itmax;
     CK(launch_cn_ir_correct(X->G, C, I, mask, X->stream));
     X->launches += 1;
     ++sweeps;

@@ -192,7 +192,9 @@ __global__ void __launch_bounds__(NT) k_cn32_matvec(Geo G, Cn32 I) {
 
 // e += alpha p, r -= alpha q; <r, D^{-1} r>, <r, r>.  float4 groups g = g0, g0 + gs, ... of an
 // n-voxel system plus the scalar tail n - n % 4 .. n (block 0); a group's products are summed
-// in FP32, groups in FP64.
+// in FP32, groups in FP64.  With the polynomial preconditioner (NEU) only <r, r> is formed:
+// the next iteration's preconditioner kernel forms <r, z> and beta.
+template <bool NEU>
 __global__ void __launch_bounds__(NT) k_cn32_update(long long n, Cn32 I) {
   bool act[3];
   if (!active3(I, act)) return;
@@ -202,7 +204,8 @@ __global__ void __launch_bounds__(NT) k_cn32_update(long long n, Cn32 I) {
   double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   const long long gs = (long long)gridDim.x * blockDim.x, ng = n / 4;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < ng; v += gs) {
-    const float4 d = __ldg(reinterpret_cast<const float4*>(I.dinv) + v);
+    const float4 d = NEU ? float4{0.0f, 0.0f, 0.0f, 0.0f}
+                         : __ldg(reinterpret_cast<const float4*>(I.dinv) + v);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       if (!act[r]) continue;
@@ -216,21 +219,22 @@ __global__ void __launch_bounds__(NT) k_cn32_update(long long n, Cn32 I) {
       x.x -= a * q.x; x.y -= a * q.y; x.z -= a * q.z; x.w -= a * q.w;
       *e4 = e;
       *r4 = x;
-      acc[2 * r] += (double)(x.x * (d.x * x.x) + x.y * (d.y * x.y) + x.z * (d.z * x.z) +
-                             x.w * (d.w * x.w));
+      if (!NEU)
+        acc[2 * r] += (double)(x.x * (d.x * x.x) + x.y * (d.y * x.y) + x.z * (d.z * x.z) +
+                               x.w * (d.w * x.w));
       acc[2 * r + 1] += (double)(x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w);
     }
   }
   if (blockIdx.x == 0) {
     for (long long c = 4 * ng + threadIdx.x; c < n; c += blockDim.x) {
-      const float di = I.dinv[c];
+      const float di = NEU ? 0.0f : I.dinv[c];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         if (!act[r]) continue;
         I.e[r][c] += alpha[r] * I.p[r][c];
         const float res = I.r[r][c] - alpha[r] * I.q[r][c];
         I.r[r][c] = res;
-        acc[2 * r] += (double)(res * (di * res));
+        if (!NEU) acc[2 * r] += (double)(res * (di * res));
         acc[2 * r + 1] += (double)(res * res);
       }
     }
@@ -238,12 +242,19 @@ __global__ void __launch_bounds__(NT) k_cn32_update(long long n, Cn32 I) {
   double out[6];
   if (reduce_last_block<6>(acc, I.partial, I.counter, out) && threadIdx.x == 0) {
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-      if (act[r]) cg_after_update(I.S[r], out[2 * r], out[2 * r + 1]);
+    for (int r = 0; r < 3; ++r) {
+      if (!act[r]) continue;
+      if (NEU)
+        cg_after_update_rr(I.S[r], out[2 * r + 1]);
+      else
+        cg_after_update(I.S[r], out[2 * r], out[2 * r + 1]);
+    }
   }
 }
 
-// p = D^{-1} r + beta p (p = D^{-1} r on an inner solve's first iteration), float4 groups
+// p = z + beta p (p = z on an inner solve's first iteration), float4 groups; z = D^{-1} r
+// (Jacobi) or the polynomial preconditioner's output I.z (NEU)
+template <bool NEU>
 __global__ void __launch_bounds__(NT) k_cn32_pupdate(long long n, Cn32 I) {
   bool act[3];
   if (!active3(I, act)) return;
@@ -256,13 +267,19 @@ __global__ void __launch_bounds__(NT) k_cn32_pupdate(long long n, Cn32 I) {
   }
   const long long gs = (long long)gridDim.x * blockDim.x, ng = n / 4;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < ng; v += gs) {
-    const float4 d = __ldg(reinterpret_cast<const float4*>(I.dinv) + v);
+    const float4 d = NEU ? float4{0.0f, 0.0f, 0.0f, 0.0f}
+                         : __ldg(reinterpret_cast<const float4*>(I.dinv) + v);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       if (!act[r]) continue;
-      const float4 x = reinterpret_cast<const float4*>(I.r[r])[v];
       float4* p4 = reinterpret_cast<float4*>(I.p[r]) + v;
-      const float4 z = {d.x * x.x, d.y * x.y, d.z * x.z, d.w * x.w};
+      float4 z;
+      if (NEU) {
+        z = reinterpret_cast<const float4*>(I.z[r])[v];
+      } else {
+        const float4 x = reinterpret_cast<const float4*>(I.r[r])[v];
+        z = float4{d.x * x.x, d.y * x.y, d.z * x.z, d.w * x.w};
+      }
       if (first[r]) {
         *p4 = z;
       } else {
@@ -274,14 +291,210 @@ __global__ void __launch_bounds__(NT) k_cn32_pupdate(long long n, Cn32 I) {
   }
   if (blockIdx.x == 0) {
     for (long long c = 4 * ng + threadIdx.x; c < n; c += blockDim.x) {
-      const float di = I.dinv[c];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         if (!act[r]) continue;
-        const float z = di * I.r[r][c];
+        const float z = NEU ? I.z[r][c] : I.dinv[c] * I.r[r][c];
         I.p[r][c] = first[r] ? z : z + beta[r] * I.p[r][c];
       }
     }
+  }
+}
+
+// ------------------------------------------------------------- polynomial preconditioner
+// M r = (I + N + N^2 + N^3) D^{-1} r with N = D^{-1} (D - A): the first four terms of the
+// Neumann series of A^{-1} = (I - N)^{-1} D^{-1} in the Jacobi splitting A = D - (D - A).
+// (D - A) y at a node is the sum over its six faces of the face coefficient times y at the
+// neighbour across it, so the terms y_0 = D^{-1} r, y_{j+1} = D^{-1} (D - A) y_j are three
+// Jacobi sweeps.  M is symmetric positive definite: it is D^{-1/2} q(B) D^{-1/2} with B the
+// symmetric Jacobi-scaled operator, whose spectrum lies in (0, 2) (Gershgorin), and
+// q(x) = (1 - (1 - x)^4) / x > 0 there.
+//
+// The three sweeps run in one pass over memory (temporal blocking).  A block owns an
+// NM_X x NM_Y tile of (x, y) columns -- the NM_OX x NM_OY output columns and a halo of
+// NM_H = 3 -- and marches up a chunk of z planes: at step t it forms y_0 on plane t over the
+// whole tile, y_1 on plane t - 1 one column in from the edge, y_2 on plane t - 2 two columns
+// in and y_3 on plane t - 3 over the output columns, whose z = y_0 + y_1 + y_2 + y_3 it
+// writes.  A term's x and y neighbours come from the previous step's shared-memory plane of
+// the term below it (two planes per term, alternating), its z neighbours and the column's
+// own faces from registers that shift one plane per step; one barrier per step.  Global
+// memory is read once per plane (r, three faces, D^{-1}) and z written once, plus the halo
+// columns, which neighbouring blocks also read (mostly from L2).  Two solves (slots) share
+// the face reads.  <r, z> of each solve is summed for its CG scalars.
+constexpr int NM_X = 32, NM_Y = 16, NM_H = 3;
+constexpr int NM_OX = NM_X - 2 * NM_H, NM_OY = NM_Y - 2 * NM_H;
+constexpr int NM_CELLS = NM_X * NM_Y;
+
+struct NmTile {
+  float y[3][2][2][NM_CELLS];   // terms 0..2: [term][plane parity][slot][cell]
+  float ax[4][NM_CELLS];        // x and y faces of the last four planes (index plane & 3)
+  float ay[4][NM_CELLS];
+  double red[NM_CELLS / 32][2];
+  bool last;
+};
+
+__global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int r0, int r1,
+                                                              int zc) {
+  const bool run0 = r0 >= 0 && I.S[r0].status == CG_RUNNING;
+  const bool run1 = r1 >= 0 && I.S[r1].status == CG_RUNNING;
+  if (!run0 && !run1) return;
+  __shared__ NmTile T;
+  const int tx = threadIdx.x, ty = threadIdx.y, cell = ty * NM_X + tx;
+  const int xo = blockIdx.x * NM_OX, yo = blockIdx.y * NM_OY;
+  const int gxu = xo - NM_H + tx, gyu = yo - NM_H + ty;   // unwrapped tile coordinates
+  const int gx = ((gxu % G.nx) + G.nx) % G.nx, gy = ((gyu % G.ny) + G.ny) % G.ny;
+  const long long col = (long long)gy * G.nx + gx;
+  auto inside = [&](int j) { return tx >= j && tx < NM_X - j && ty >= j && ty < NM_Y - j; };
+  const bool in1 = inside(1), in2 = inside(2), in3 = inside(3);
+  const bool out = in3 && gxu < G.nx && gyu < G.ny;   // each output column written once
+  const int k0 = blockIdx.z * zc, k1 = min(G.nz, k0 + zc);
+  const bool run[2] = {run0, run1};
+  const int rs[2] = {run0 ? r0 : 0, run1 ? r1 : 0};
+  auto plane = [&](int k) {
+    const int kw = k < 0 ? k + G.nz : (k >= G.nz ? k - G.nz : k);
+    return (long long)kw * G.nxy + col;
+  };
+  // registers: suffix a, b, c, d, e = planes t, t-1, t-2, t-3, t-4 at step t (y1 from t-1,
+  // y2 from t-2)
+  float y0a[2] = {0, 0}, y0b[2] = {0, 0}, y0c[2] = {0, 0}, y0d[2] = {0, 0};
+  float y1a[2] = {0, 0}, y1b[2] = {0, 0}, y1c[2] = {0, 0};
+  float y2a[2] = {0, 0}, y2b[2] = {0, 0}, y2c[2] = {0, 0};
+  float ra[2] = {0, 0}, rb[2] = {0, 0}, rc[2] = {0, 0}, rd[2] = {0, 0};
+  float axa = 0, axb = 0, axc = 0, axd = 0, aya = 0, ayb = 0, ayc = 0, ayd = 0;
+  float aza = 0, azb = 0, azc = 0, azd = 0, aze = 0, dia = 0, dib = 0, dic = 0, did = 0;
+  float acc[2] = {0.0f, 0.0f};
+  // the next plane's loads are issued one step ahead
+  float nr[2], nax, nay, naz, ndi;
+  auto fetch = [&](int k) {
+    const long long g = plane(k);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) nr[s] = run[s] ? __ldg(I.r[rs[s]] + g) : 0.0f;
+    nax = __ldg(I.Kf[0] + g);
+    nay = __ldg(I.Kf[1] + g);
+    naz = __ldg(I.Kf[2] + g);
+    ndi = __ldg(I.dinv + g);
+  };
+  fetch(k0 - NM_H);
+  for (int t = k0 - NM_H; t <= k1 + NM_H - 1; ++t) {
+    // shift the column registers by one plane and take plane t
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      y0d[s] = y0c[s]; y0c[s] = y0b[s]; y0b[s] = y0a[s];
+      y1c[s] = y1b[s]; y1b[s] = y1a[s];
+      y2c[s] = y2b[s]; y2b[s] = y2a[s];
+      rd[s] = rc[s]; rc[s] = rb[s]; rb[s] = ra[s]; ra[s] = nr[s];
+    }
+    axd = axc; axc = axb; axb = axa; axa = nax;
+    ayd = ayc; ayc = ayb; ayb = aya; aya = nay;
+    aze = azd; azd = azc; azc = azb; azb = aza; aza = naz;
+    did = dic; dic = dib; dib = dia; dia = ndi;
+    if (t + 1 <= k1 + NM_H - 1) fetch(t + 1);
+
+    // term 0 on plane t, the whole tile
+    const int pt = (t + 4) & 1, ft = (t + 4) & 3;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      y0a[s] = dia * ra[s];
+      T.y[0][pt][s][cell] = y0a[s];
+    }
+    T.ax[ft][cell] = axa;
+    T.ay[ft][cell] = aya;
+    // term 1 on plane t - 1
+    {
+      const int k = t - 1;
+      if (in1 && k >= k0 - 2 && k <= k1 + 1) {
+        const int pk = (k + 4) & 1, fk = (k + 4) & 3;
+        const float axm = T.ax[fk][cell - 1], aym = T.ay[fk][cell - NM_X];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const float* Y = T.y[0][pk][s];
+          y1a[s] = dib * (axb * Y[cell + 1] + axm * Y[cell - 1] + ayb * Y[cell + NM_X] +
+                          aym * Y[cell - NM_X] + azb * y0a[s] + azc * y0c[s]);
+          T.y[1][pk][s][cell] = y1a[s];
+        }
+      }
+    }
+    // term 2 on plane t - 2
+    {
+      const int k = t - 2;
+      if (in2 && k >= k0 - 1 && k <= k1) {
+        const int pk = (k + 4) & 1, fk = (k + 4) & 3;
+        const float axm = T.ax[fk][cell - 1], aym = T.ay[fk][cell - NM_X];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const float* Y = T.y[1][pk][s];
+          y2a[s] = dic * (axc * Y[cell + 1] + axm * Y[cell - 1] + ayc * Y[cell + NM_X] +
+                          aym * Y[cell - NM_X] + azc * y1a[s] + azd * y1c[s]);
+          T.y[2][pk][s][cell] = y2a[s];
+        }
+      }
+    }
+    // term 3 on plane t - 3, and the output there
+    {
+      const int k = t - 3;
+      if (in3 && k >= k0 && k < k1) {
+        const int pk = (k + 4) & 1, fk = (k + 4) & 3;
+        const float axm = T.ax[fk][cell - 1], aym = T.ay[fk][cell - NM_X];
+        const long long g = plane(k);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const float* Y = T.y[2][pk][s];
+          const float y3 = did * (axd * Y[cell + 1] + axm * Y[cell - 1] + ayd * Y[cell + NM_X] +
+                                  aym * Y[cell - NM_X] + azd * y2a[s] + aze * y2c[s]);
+          const float z = ((y0d[s] + y1c[s]) + y2b[s]) + y3;
+          if (out && run[s]) {
+            I.z[rs[s]][g] = z;
+            acc[s] += rd[s] * z;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // <r, z> per solve: warps, then the block's warps in order, then the blocks in order by the
+  // last block to finish
+  const int lane = cell & 31, warp = cell >> 5, nb = gridDim.x * gridDim.y * gridDim.z;
+  const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const double v = warp_sum((double)acc[s]);
+    if (lane == 0) T.red[warp][s] = v;
+  }
+  __syncthreads();
+  if (cell == 0) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      double v = 0.0;
+      for (int w = 0; w < NM_CELLS / 32; ++w) v += T.red[w][s];
+      I.partial[2 * (size_t)b + s] = v;
+    }
+    __threadfence();
+    T.last = atomicAdd(I.counter, 1u) == (unsigned int)(nb - 1);
+  }
+  __syncthreads();
+  if (!T.last) return;
+  __threadfence();
+  double tot[2] = {0.0, 0.0};
+  for (int k = cell; k < nb; k += NM_CELLS) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) tot[s] += __ldcg(I.partial + 2 * (size_t)k + s);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const double v = warp_sum(tot[s]);
+    if (lane == 0) T.red[warp][s] = v;
+  }
+  __syncthreads();
+  if (cell == 0) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      double v = 0.0;
+      for (int w = 0; w < NM_CELLS / 32; ++w) v += T.red[w][s];
+      if (run[s]) cg_after_precond(I.S[rs[s]], v);
+    }
+    *I.counter = 0u;
   }
 }
 
@@ -322,12 +535,29 @@ cudaError_t launch_cn_ir_residual(const Geo& G, const Cn3& C, const Cn32& I, CgS
   return cudaGetLastError();
 }
 
-// one inner iteration of the three FP32 solves: the first iteration of a sweep forms p from
-// the residual before the operator
-cudaError_t launch_cn32_iter(const Geo& G, const Cn32& I, cudaStream_t st) {
-  TG_TIMED(K_CN32_PUPDATE, st, k_cn32_pupdate<<<flat_blocks(G), NT, 0, st>>>(G.nvox, I));
+// one inner iteration of the FP32 solves: the first iteration of a sweep forms p from the
+// (preconditioned) residual before the operator
+cudaError_t launch_cn32_iter(const Geo& G, const Cn32& I, cudaStream_t st, int r0, int r1,
+                             long long partial_capacity) {
+  if (I.z[0] == nullptr && I.z[1] == nullptr && I.z[2] == nullptr) {
+    TG_TIMED(K_CN32_PUPDATE, st, k_cn32_pupdate<false><<<flat_blocks(G), NT, 0, st>>>(G.nvox, I));
+    TG_TIMED(K_CN32_MATVEC, st, k_cn32_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, I));
+    TG_TIMED(K_CN32_UPDATE, st, k_cn32_update<false><<<flat_blocks(G), NT, 0, st>>>(G.nvox, I));
+    return cudaGetLastError();
+  }
+  // z chunk: 32 planes, more while the blocks' two partial sums would not fit the buffer
+  const long long gx = (G.nx + NM_OX - 1) / NM_OX, gy = (G.ny + NM_OY - 1) / NM_OY;
+  int zc = 32;
+  while (zc < G.nz && gx * gy * ((G.nz + zc - 1) / zc) * 2 > partial_capacity) zc *= 2;
+  zc = zc < G.nz ? zc : G.nz;
+  const long long gz = (G.nz + zc - 1) / zc;
+  if (gx * gy * gz * 2 > partial_capacity || r0 < 0) return cudaErrorInvalidValue;
+  TG_TIMED(K_CN32_NEUMANN, st,
+           k_cn32_neumann<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(NM_X, NM_Y), 0,
+                            st>>>(G, I, r0, r1, zc));
+  TG_TIMED(K_CN32_PUPDATE, st, k_cn32_pupdate<true><<<flat_blocks(G), NT, 0, st>>>(G.nvox, I));
   TG_TIMED(K_CN32_MATVEC, st, k_cn32_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, I));
-  TG_TIMED(K_CN32_UPDATE, st, k_cn32_update<<<flat_blocks(G), NT, 0, st>>>(G.nvox, I));
+  TG_TIMED(K_CN32_UPDATE, st, k_cn32_update<true><<<flat_blocks(G), NT, 0, st>>>(G.nvox, I));
   return cudaGetLastError();
 }
 

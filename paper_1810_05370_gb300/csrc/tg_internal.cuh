@@ -24,7 +24,7 @@ enum KernelId : int {
   K_DIFF_FACES, K_DIFF_DIAG, K_TO_F32, K_DIVERGENCE, K_SL, K_SL32,
   K_CN_INIT, K_CN_MATVEC, K_CN_UPDATE, K_CN_PUPDATE,
   K_CN_IR_RESIDUAL, K_CN_IR_RESIDUAL_DF, K_CN32_PUPDATE, K_CN32_MATVEC, K_CN32_UPDATE,
-  K_CN_IR_CORRECT, K_REACT, K_LAME, K_ELAS_COEF, K_ELAS_COEF_DF, K_ELAS32_COEF, K_DF_PACK3,
+  K_CN_IR_CORRECT, K_CN32_NEUMANN, K_REACT, K_LAME, K_ELAS_COEF, K_ELAS_COEF_DF, K_ELAS32_COEF, K_DF_PACK3,
   K_ELAS_EXTRAPOLATE, K_SPEC_MEAN, K_SPEC_SCALE, K_ELAS_IR_RESIDUAL, K_ELAS_IR_RESIDUAL_DF,
   K_ELAS32_SCALE_R, K_SPEC_X_FWD, K_SPEC_Y_FWD, K_SPEC_Z, K_SPEC_ZR, K_SPEC_Y_INV,
   K_SPEC_X_INV, K_SPEC_X_INV_P, K_ELAS32_MATVEC, K_ELAS32_UPDATE, K_ELAS32_MATVEC_SPEC,
@@ -410,6 +410,7 @@ struct Cn32 {
   float* r[3];
   float* p[3];
   float* q[3];
+  float* z[3];         // preconditioned residual of the polynomial preconditioner (null: Jacobi)
   const float* Kf[3];
   const float* dinv;
   CgScal* S;           // 3 inner solves
@@ -420,7 +421,12 @@ struct Cn32 {
 // FP32 copy, e = 0, and the outer test / inner start per right-hand side (Sout: 3 entries)
 cudaError_t launch_cn_ir_residual(const Geo&, const Cn3&, const Cn32&, CgScal* Sout, bool init,
                                   double tau_min, int max_sweeps, int mask, cudaStream_t st);
-cudaError_t launch_cn32_iter(const Geo&, const Cn32&, cudaStream_t st);
+// One inner iteration.  With I.z set the iteration is preconditioned by the Neumann series of
+// the Jacobi splitting (launch_cn32_neumann, solves r0 and r1, -1 for none) and begins with
+// it: z = M r, <r, z>; p = z + beta p; q = A p; e, r updated (convergence from |r|).
+// partial_capacity: doubles the reduction buffer holds.
+cudaError_t launch_cn32_iter(const Geo&, const Cn32&, cudaStream_t st, int r0 = -1,
+                             int r1 = -1, long long partial_capacity = 0);
 cudaError_t launch_cn_ir_correct(const Geo&, const Cn3&, const Cn32&, int mask, cudaStream_t st);
 
 // SL (S1)
