@@ -389,7 +389,8 @@ const char* const kKernelNames[K_COUNT] = {
     "k_elas32_matvec", "k_elas32_update", "k_elas32_matvec_spec", "k_elas32_update_spec",
     "k_spec_update_xfwd", "k_elas_ir_correct", "k_elas_ir_finish", "k_elas_init",
     "k_elas_init_spec", "k_elas_matvec", "k_elas_update", "k_elas_pupdate", "k_elas_update_spec",
-    "k_elas_pupdate_spec", "k_elas_finish"};
+    "k_elas_pupdate_spec", "k_elas_finish", "k_ox_prep", "k_ox_init", "k_ox_matvec",
+    "k_ox_update", "k_ox_pupdate", "k_ox_finish"};
 
 }  // namespace
 
@@ -767,12 +768,15 @@ tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
   int sweeps = 0;
   CgScal out[3];
   if (C.df) {   // (hi, lo) pairs of the fields for the first double-FP32 residual
-    double* const pk[3] = {reinterpret_cast<double*>(C.xdf[0]), reinterpret_cast<double*>(C.xdf[1]),
-                           reinterpret_cast<double*>(C.xdf[2])};
-    // only the solved fields are read (oxygen may be in its own solve on the side stream)
+    // only the solved fields are read and only their pairs written: oxygen may be in its own
+    // solve on the side stream, whose double-FP32 iterate lives in the oxygen pair array (an
+    // unsolved slot repeats the first solved one, the same value to the same address)
     const int f0 = (mask & 1) ? 0 : ((mask & 4) ? 2 : 1);
-    const double* const src[3] = {C.x[(mask & 1) ? 0 : f0], C.x[(mask & 2) ? 1 : f0],
-                                  C.x[(mask & 4) ? 2 : f0]};
+    auto pick = [&](int r) { return ((mask >> r) & 1) ? r : f0; };
+    double* const pk[3] = {reinterpret_cast<double*>(C.xdf[pick(0)]),
+                           reinterpret_cast<double*>(C.xdf[pick(1)]),
+                           reinterpret_cast<double*>(C.xdf[pick(2)])};
+    const double* const src[3] = {C.x[pick(0)], C.x[pick(1)], C.x[pick(2)]};
     CK(launch_df_pack3(X->G, src, pk, X->stream));
     X->launches += 1;
   }
@@ -820,11 +824,31 @@ tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
   return TG_OK;
 }
 
-// S2 of the mixed multispecies step: the FP64 oxygen solve on the side stream, concurrently with
-// the FP32-refined i and l solves on the context's stream.  The FP64 CG is limited by the FP64
-// units and the refined solves by memory, so the two overlap.  The oxygen solve has its own CG
-// scalars (scal + 8) and reduction buffers; the first chunk of its iterations is queued before
-// the i, l solve starts and the rest is driven after it; events fork and join the streams.
+// the mixed precision's double-FP32 oxygen solve: pairs in the FP64 arrays of the oxygen CG
+// (free then), the diagonal pairs in those of the FP64 diagonal (S0 copied what the FP32 solves
+// need before S2 starts), face pairs from S0; scalars and reductions of the side stream
+OxDf ox_view(tg_ctx* X) {
+  OxDf O;
+  for (int d = 0; d < 3; ++d) O.Kf[d] = reinterpret_cast<const float2*>(X->a[A_KFDF0 + d]);
+  O.dd = reinterpret_cast<float2*>(X->a[A_DSUM_D]);
+  O.di = reinterpret_cast<float2*>(X->a[A_DINV_D]);
+  O.x = reinterpret_cast<float2*>(X->a[A_XDF1]);
+  O.r = reinterpret_cast<float2*>(X->a[A_CR1]);
+  O.p = reinterpret_cast<float2*>(X->a[A_CP1]);
+  O.q = reinterpret_cast<float2*>(X->a[A_CQ1]);
+  O.o = X->st.o;
+  O.S = X->scal + 9;
+  O.partial = X->partial2;
+  O.counter = X->counter2;
+  return O;
+}
+
+// S2 of the mixed multispecies step: the oxygen solve on the side stream, concurrently with the
+// FP32-refined i and l solves on the context's stream.  The oxygen solve follows the FP64 CG's
+// iterates: in double-FP32 arithmetic (tg_cn_ox.cu) when the face pairs exist (cn_df), else in
+// FP64.  It has its own CG scalars (scal + 8 .. 10) and reduction buffers; the first chunk of
+// its iterations is queued before the i, l solve starts and the rest is driven after it;
+// events fork and join the streams.
 tg_status cn_solve_mixed_concurrent(tg_ctx* X, tg_stats* stats) {
   constexpr int MASK_O = 7 & ~CN_MIXED_MASK;
   if (!X->side) {   // default priority (the highest measured no better)
@@ -833,24 +857,32 @@ tg_status cn_solve_mixed_concurrent(tg_ctx* X, tg_stats* stats) {
     CK(cudaEventCreateWithFlags(&X->join_ev, cudaEventDisableTiming));
   }
   cudaStream_t so = X->side;
+  const bool df = X->cn_df;
   Cn3 C = cn_view(X);
   C.S = X->scal + 8;
   C.partial = X->partial2;
   C.counter = X->counter2;
   C.df = 0;
+  const OxDf O = ox_view(X);
+  CgScal* const dev = df ? O.S : C.S;   // the oxygen entry of the device scalars
+  const int ns = df ? 1 : 3;
+  auto iter = [&](int) -> cudaError_t {
+    X->launches += 3;
+    return df ? launch_ox_iter(X->G, O, so) : launch_cn_iter(X->G, C, so);
+  };
   CK(cudaEventRecord(X->fork_ev, X->stream));
   CK(cudaStreamWaitEvent(so, X->fork_ev, 0));
-  k_cg_reset<<<1, 32, 0, so>>>(C.S, 3, X->prm.rtol_diff, X->prm.maxit_diff);
+  k_cg_reset<<<1, 32, 0, so>>>(dev, ns, X->prm.rtol_diff, X->prm.maxit_diff);
   CK(cudaGetLastError());
-  CK(launch_cn_init(X->G, C, so, MASK_O));
+  CK(df ? launch_ox_start(X->G, O, so) : launch_cn_init(X->G, C, so, MASK_O));
   const int chunk = first_chunk(X->prev_it_diff);
   const int slot = prof_open_solve(X);
   for (int c = 0; c < chunk; ++c) {
     prof_iter(X, slot, c);
-    CK(launch_cn_iter(X->G, C, so));
+    CK(iter(c));
   }
   prof_iter(X, -1, -1);
-  X->launches += 2 + 3LL * chunk;
+  X->launches += 2 + (df ? 1 : 0);
   // i and l on the context's stream meanwhile
   tg_status e = cn_solve3_mixed(X, stats, CN_MIXED_MASK);
   if (e != TG_OK) {
@@ -858,25 +890,27 @@ tg_status cn_solve_mixed_concurrent(tg_ctx* X, tg_stats* stats) {
     return e;
   }
   CgScal host[3];
-  e = drive_cg_on(X, so, [&](int) {
-    X->launches += 3;
-    return launch_cn_iter(X->G, C, so);
-  }, C.S, 3, X->prm.maxit_diff, X->prev_it_diff, host, chunk, slot);
+  e = drive_cg_on(X, so, iter, dev, ns, X->prm.maxit_diff, X->prev_it_diff, host, chunk, slot);
   if (e != TG_OK) {
     cudaStreamSynchronize(so);
     return e;
   }
-  if (host[1].status == CG_ZERO_RHS)
+  const CgScal& ho = df ? host[0] : host[1];
+  if (df) {
+    CK(launch_ox_finish(X->G, O, so));
+    X->launches += 1;
+  } else if (ho.status == CG_ZERO_RHS) {
     CK(cudaMemsetAsync(C.x[1], 0, (size_t)X->G.nvox * sizeof(double), so));
+  }
   CK(cudaEventRecord(X->join_ev, so));
   CK(cudaStreamWaitEvent(X->stream, X->join_ev, 0));
-  X->prev_it_diff = host[1].it;
+  X->prev_it_diff = ho.it;
   if (stats) {
-    stats->it_diff[1] = host[1].it;
-    stats->relres_diff[1] = host[1].bb > 0.0 ? sqrt(host[1].rr / host[1].bb) : 0.0;
-    stats->it_diff_total += host[1].it;
+    stats->it_diff[1] = ho.it;
+    stats->relres_diff[1] = ho.bb > 0.0 ? sqrt(ho.rr / ho.bb) : 0.0;
+    stats->it_diff_total += ho.it;
   }
-  e = status_of(host[1]);
+  e = status_of(ho);
   return e == TG_OK ? TG_OK : fail(X, e);
 }
 

@@ -315,20 +315,21 @@ __global__ void __launch_bounds__(NT) k_cn32_pupdate(long long n, Cn32 I) {
 // NM_H = 3 -- and marches up a chunk of z planes: at step t it forms y_0 on plane t over the
 // whole tile, y_1 on plane t - 1 one column in from the edge, y_2 on plane t - 2 two columns
 // in and y_3 on plane t - 3 over the output columns, whose z = y_0 + y_1 + y_2 + y_3 it
-// writes.  A term's x and y neighbours come from the previous step's shared-memory plane of
-// the term below it (two planes per term, alternating), its z neighbours and the column's
-// own faces from registers that shift one plane per step; one barrier per step.  Global
-// memory is read once per plane (r, three faces, D^{-1}) and z written once, plus the halo
-// columns, which neighbouring blocks also read (mostly from L2).  Two solves (slots) share
-// the face reads.  <r, z> of each solve is summed for its CG scalars.
+// writes.  A warp is one row of the tile, so a term's x neighbours come from the neighbouring
+// lanes (shuffles); its y neighbours from the previous step's shared-memory plane of the term
+// below it (two planes per term, alternating); its z neighbours and the column's own faces
+// from registers.  The registers of the last four planes form rings indexed by the plane
+// modulo 4; the march is unrolled by four so that every ring index is a constant.  One
+// barrier per step.  Global memory is read once per plane (r, three faces, D^{-1}) and z
+// written once, plus the halo columns, which neighbouring blocks also read (mostly from L2).
+// Two solves (slots) share the face reads.  <r, z> of each solve is summed for its CG scalars.
 constexpr int NM_X = 32, NM_Y = 16, NM_H = 3;
 constexpr int NM_OX = NM_X - 2 * NM_H, NM_OY = NM_Y - 2 * NM_H;
 constexpr int NM_CELLS = NM_X * NM_Y;
 
 struct NmTile {
   float y[3][2][2][NM_CELLS];   // terms 0..2: [term][plane parity][slot][cell]
-  float ax[4][NM_CELLS];        // x and y faces of the last four planes (index plane & 3)
-  float ay[4][NM_CELLS];
+  float ay[4][NM_CELLS];        // y faces of the last four planes (index plane & 3)
   double red[NM_CELLS / 32][2];
   bool last;
 };
@@ -350,106 +351,129 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
   const int k0 = blockIdx.z * zc, k1 = min(G.nz, k0 + zc);
   const bool run[2] = {run0, run1};
   const int rs[2] = {run0 ? r0 : 0, run1 ? r1 : 0};
-  auto plane = [&](int k) {
-    const int kw = k < 0 ? k + G.nz : (k >= G.nz ? k - G.nz : k);
+  auto plane = [&](int k) {   // k >= k0 - 3 >= -3; up to three padding steps past k1 + 2
+    const int kw = ((k % G.nz) + G.nz) % G.nz;
     return (long long)kw * G.nxy + col;
   };
-  // registers: suffix a, b, c, d, e = planes t, t-1, t-2, t-3, t-4 at step t (y1 from t-1,
-  // y2 from t-2)
-  float y0a[2] = {0, 0}, y0b[2] = {0, 0}, y0c[2] = {0, 0}, y0d[2] = {0, 0};
-  float y1a[2] = {0, 0}, y1b[2] = {0, 0}, y1c[2] = {0, 0};
-  float y2a[2] = {0, 0}, y2b[2] = {0, 0}, y2c[2] = {0, 0};
-  float ra[2] = {0, 0}, rb[2] = {0, 0}, rc[2] = {0, 0}, rd[2] = {0, 0};
-  float axa = 0, axb = 0, axc = 0, axd = 0, aya = 0, ayb = 0, ayc = 0, ayd = 0;
-  float aza = 0, azb = 0, azc = 0, azd = 0, aze = 0, dia = 0, dib = 0, dic = 0, did = 0;
+  // rings over the last four planes, slot = (plane - tb) & 3 with tb = k0 - NM_H
+  float y0[4][2], y1[4][2], y2[4][2], rr[4][2], lz[4][2];   // lz: a_z(k-1) y_2(k-1) of plane k
+  float ax[4], ay[4], az[4], di[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) y0[m][q] = y1[m][q] = y2[m][q] = rr[m][q] = lz[m][q] = 0.0f;
+    ax[m] = ay[m] = az[m] = di[m] = 0.0f;
+  }
   float acc[2] = {0.0f, 0.0f};
-  // the next plane's loads are issued one step ahead
-  float nr[2], nax, nay, naz, ndi;
+  float nr[2], nax, nay, naz, ndi;   // plane t + 1, loaded one step ahead
   auto fetch = [&](int k) {
     const long long g = plane(k);
 #pragma unroll
-    for (int s = 0; s < 2; ++s) nr[s] = run[s] ? __ldg(I.r[rs[s]] + g) : 0.0f;
+    for (int q = 0; q < 2; ++q) nr[q] = run[q] ? __ldg(I.r[rs[q]] + g) : 0.0f;
     nax = __ldg(I.Kf[0] + g);
     nay = __ldg(I.Kf[1] + g);
     naz = __ldg(I.Kf[2] + g);
     ndi = __ldg(I.dinv + g);
   };
-  fetch(k0 - NM_H);
-  for (int t = k0 - NM_H; t <= k1 + NM_H - 1; ++t) {
-    // shift the column registers by one plane and take plane t
+  const int tb = k0 - NM_H;
+  const int te = tb + ((k1 - k0 + 2 * NM_H + 3) & ~3);   // steps tb .. te - 1, a multiple of 4
+  fetch(tb);
+  for (int t0 = tb; t0 < te; t0 += 4) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      y0d[s] = y0c[s]; y0c[s] = y0b[s]; y0b[s] = y0a[s];
-      y1c[s] = y1b[s]; y1b[s] = y1a[s];
-      y2c[s] = y2b[s]; y2b[s] = y2a[s];
-      rd[s] = rc[s]; rc[s] = rb[s]; rb[s] = ra[s]; ra[s] = nr[s];
-    }
-    axd = axc; axc = axb; axb = axa; axa = nax;
-    ayd = ayc; ayc = ayb; ayb = aya; aya = nay;
-    aze = azd; azd = azc; azc = azb; azb = aza; aza = naz;
-    did = dic; dic = dib; dib = dia; dia = ndi;
-    if (t + 1 <= k1 + NM_H - 1) fetch(t + 1);
-
-    // term 0 on plane t, the whole tile
-    const int pt = (t + 4) & 1, ft = (t + 4) & 3;
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + u;
+      constexpr int M = 3;   // slot of plane t - 1 is (u + M) & 3, etc.
+      const int s0 = u, s1 = (u + M) & 3, s2 = (u + 2 * M) & 3, s3 = (u + 3 * M) & 3;
+      // take plane t, prefetch plane t + 1
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      y0a[s] = dia * ra[s];
-      T.y[0][pt][s][cell] = y0a[s];
-    }
-    T.ax[ft][cell] = axa;
-    T.ay[ft][cell] = aya;
-    // term 1 on plane t - 1
-    {
-      const int k = t - 1;
-      if (in1 && k >= k0 - 2 && k <= k1 + 1) {
-        const int pk = (k + 4) & 1, fk = (k + 4) & 3;
-        const float axm = T.ax[fk][cell - 1], aym = T.ay[fk][cell - NM_X];
+      for (int q = 0; q < 2; ++q) rr[s0][q] = nr[q];
+      ax[s0] = nax;
+      ay[s0] = nay;
+      az[s0] = naz;
+      di[s0] = ndi;
+      if (t + 1 < te) fetch(t + 1);
+      // term 0 on plane t, the whole tile
+      const int pt = (t + 4) & 1;
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const float* Y = T.y[0][pk][s];
-          y1a[s] = dib * (axb * Y[cell + 1] + axm * Y[cell - 1] + ayb * Y[cell + NM_X] +
-                          aym * Y[cell - NM_X] + azb * y0a[s] + azc * y0c[s]);
-          T.y[1][pk][s][cell] = y1a[s];
-        }
+      for (int q = 0; q < 2; ++q) {
+        y0[s0][q] = di[s0] * rr[s0][q];
+        T.y[0][pt][q][cell] = y0[s0][q];
       }
-    }
-    // term 2 on plane t - 2
-    {
-      const int k = t - 2;
-      if (in2 && k >= k0 - 1 && k <= k1) {
+      T.ay[(t + 4) & 3][cell] = ay[s0];
+      // term 1 on plane t - 1
+      {
+        const int k = t - 1;
         const int pk = (k + 4) & 1, fk = (k + 4) & 3;
-        const float axm = T.ax[fk][cell - 1], aym = T.ay[fk][cell - NM_X];
+        const float axm = __shfl_up_sync(0xffffffffu, ax[s1], 1);
+        float yp[2], ym[2];   // every lane takes part in the shuffles
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const float* Y = T.y[1][pk][s];
-          y2a[s] = dic * (axc * Y[cell + 1] + axm * Y[cell - 1] + ayc * Y[cell + NM_X] +
-                          aym * Y[cell - NM_X] + azc * y1a[s] + azd * y1c[s]);
-          T.y[2][pk][s][cell] = y2a[s];
+        for (int q = 0; q < 2; ++q) {
+          yp[q] = __shfl_down_sync(0xffffffffu, y0[s1][q], 1);
+          ym[q] = __shfl_up_sync(0xffffffffu, y0[s1][q], 1);
         }
-      }
-    }
-    // term 3 on plane t - 3, and the output there
-    {
-      const int k = t - 3;
-      if (in3 && k >= k0 && k < k1) {
-        const int pk = (k + 4) & 1, fk = (k + 4) & 3;
-        const float axm = T.ax[fk][cell - 1], aym = T.ay[fk][cell - NM_X];
-        const long long g = plane(k);
+        if (in1 && k >= k0 - 2 && k <= k1 + 1) {
+          const float aym = T.ay[fk][cell - NM_X];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const float* Y = T.y[2][pk][s];
-          const float y3 = did * (axd * Y[cell + 1] + axm * Y[cell - 1] + ayd * Y[cell + NM_X] +
-                                  aym * Y[cell - NM_X] + azd * y2a[s] + aze * y2c[s]);
-          const float z = ((y0d[s] + y1c[s]) + y2b[s]) + y3;
-          if (out && run[s]) {
-            I.z[rs[s]][g] = z;
-            acc[s] += rd[s] * z;
+          for (int q = 0; q < 2; ++q) {
+            const float* Y = T.y[0][pk][q];
+            y1[s1][q] = di[s1] * (ax[s1] * yp[q] + axm * ym[q] + ay[s1] * Y[cell + NM_X] +
+                                  aym * Y[cell - NM_X] + az[s1] * y0[s0][q] + az[s2] * y0[s2][q]);
+            T.y[1][pk][q][cell] = y1[s1][q];
           }
         }
       }
+      // term 2 on plane t - 2; the z-lower term a_z(k) y_2(k) of the plane above it
+      {
+        const int k = t - 2;
+        const int pk = (k + 4) & 1, fk = (k + 4) & 3;
+        const float axm = __shfl_up_sync(0xffffffffu, ax[s2], 1);
+        float yp[2], ym[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          yp[q] = __shfl_down_sync(0xffffffffu, y1[s2][q], 1);
+          ym[q] = __shfl_up_sync(0xffffffffu, y1[s2][q], 1);
+        }
+        if (in2 && k >= k0 - 1 && k <= k1) {
+          const float aym = T.ay[fk][cell - NM_X];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const float* Y = T.y[1][pk][q];
+            y2[s2][q] = di[s2] * (ax[s2] * yp[q] + axm * ym[q] + ay[s2] * Y[cell + NM_X] +
+                                  aym * Y[cell - NM_X] + az[s2] * y1[s1][q] + az[s3] * y1[s3][q]);
+            T.y[2][pk][q][cell] = y2[s2][q];
+            lz[s1][q] = az[s2] * y2[s2][q];   // for term 3 on plane t - 1 (two steps on)
+          }
+        }
+      }
+      // term 3 on plane t - 3, and the output there
+      {
+        const int k = t - 3;
+        const int pk = (k + 4) & 1, fk = (k + 4) & 3;
+        const float axm = __shfl_up_sync(0xffffffffu, ax[s3], 1);
+        float yp[2], ym[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          yp[q] = __shfl_down_sync(0xffffffffu, y2[s3][q], 1);
+          ym[q] = __shfl_up_sync(0xffffffffu, y2[s3][q], 1);
+        }
+        if (in3 && k >= k0 && k < k1) {
+          const float aym = T.ay[fk][cell - NM_X];
+          const long long g = plane(k);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const float* Y = T.y[2][pk][q];
+            const float y3 = di[s3] * (ax[s3] * yp[q] + axm * ym[q] + ay[s3] * Y[cell + NM_X] +
+                                       aym * Y[cell - NM_X] + az[s3] * y2[s2][q] + lz[s3][q]);
+            const float z = ((y0[s3][q] + y1[s3][q]) + y2[s3][q]) + y3;
+            if (out && run[q]) {
+              I.z[rs[q]][g] = z;
+              acc[q] += rr[s3][q] * z;
+            }
+          }
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 
   // <r, z> per solve: warps, then the block's warps in order, then the blocks in order by the
@@ -457,17 +481,17 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
   const int lane = cell & 31, warp = cell >> 5, nb = gridDim.x * gridDim.y * gridDim.z;
   const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const double v = warp_sum((double)acc[s]);
-    if (lane == 0) T.red[warp][s] = v;
+  for (int q = 0; q < 2; ++q) {
+    const double v = warp_sum((double)acc[q]);
+    if (lane == 0) T.red[warp][q] = v;
   }
   __syncthreads();
   if (cell == 0) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
+    for (int q = 0; q < 2; ++q) {
       double v = 0.0;
-      for (int w = 0; w < NM_CELLS / 32; ++w) v += T.red[w][s];
-      I.partial[2 * (size_t)b + s] = v;
+      for (int w = 0; w < NM_CELLS / 32; ++w) v += T.red[w][q];
+      I.partial[2 * (size_t)b + q] = v;
     }
     __threadfence();
     T.last = atomicAdd(I.counter, 1u) == (unsigned int)(nb - 1);
@@ -478,21 +502,21 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
   double tot[2] = {0.0, 0.0};
   for (int k = cell; k < nb; k += NM_CELLS) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) tot[s] += __ldcg(I.partial + 2 * (size_t)k + s);
+    for (int q = 0; q < 2; ++q) tot[q] += __ldcg(I.partial + 2 * (size_t)k + q);
   }
   __syncthreads();
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const double v = warp_sum(tot[s]);
-    if (lane == 0) T.red[warp][s] = v;
+  for (int q = 0; q < 2; ++q) {
+    const double v = warp_sum(tot[q]);
+    if (lane == 0) T.red[warp][q] = v;
   }
   __syncthreads();
   if (cell == 0) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
+    for (int q = 0; q < 2; ++q) {
       double v = 0.0;
-      for (int w = 0; w < NM_CELLS / 32; ++w) v += T.red[w][s];
-      if (run[s]) cg_after_precond(I.S[rs[s]], v);
+      for (int w = 0; w < NM_CELLS / 32; ++w) v += T.red[w][q];
+      if (run[q]) cg_after_precond(I.S[rs[q]], v);
     }
     *I.counter = 0u;
   }

@@ -30,7 +30,8 @@ enum KernelId : int {
   K_SPEC_X_INV, K_SPEC_X_INV_P, K_ELAS32_MATVEC, K_ELAS32_UPDATE, K_ELAS32_MATVEC_SPEC,
   K_ELAS32_UPDATE_SPEC, K_SPEC_UPDATE_XFWD, K_ELAS_IR_CORRECT, K_ELAS_IR_FINISH,
   K_ELAS_INIT, K_ELAS_INIT_SPEC, K_ELAS_MATVEC, K_ELAS_UPDATE, K_ELAS_PUPDATE, K_ELAS_UPDATE_SPEC,
-  K_ELAS_PUPDATE_SPEC, K_ELAS_FINISH,
+  K_ELAS_PUPDATE_SPEC, K_ELAS_FINISH, K_OX_PREP, K_OX_INIT, K_OX_MATVEC, K_OX_UPDATE,
+  K_OX_PUPDATE, K_OX_FINISH,
   K_COUNT
 };
 
@@ -428,6 +429,26 @@ cudaError_t launch_cn_ir_residual(const Geo&, const Cn3&, const Cn32&, CgScal* S
 cudaError_t launch_cn32_iter(const Geo&, const Cn32&, cudaStream_t st, int r0 = -1,
                              int r1 = -1, long long partial_capacity = 0);
 cudaError_t launch_cn_ir_correct(const Geo&, const Cn3&, const Cn32&, int mask, cudaStream_t st);
+
+// The oxygen solve of the mixed precision in double-FP32 arithmetic (tg_cn_ox.cu): the FP64
+// path's Jacobi-CG iterates, carried as (hi, lo) FP32 pairs.
+struct OxDf {
+  const float2* Kf[3];   // face pairs a_d,j (written in S0 for the double-FP32 residuals)
+  float2* dd;            // CN diagonal 1 + sum of the six faces
+  float2* di;            // its inverse
+  float2* x;             // CG iterate
+  float2* r;
+  float2* p;
+  float2* q;
+  double* o;             // the oxygen field: start, and the result
+  CgScal* S;             // the solve's scalars
+  double* partial;
+  unsigned int* counter;
+};
+// prep (diagonal pairs, x = o) and the CG start; one iteration; o = x
+cudaError_t launch_ox_start(const Geo&, const OxDf&, cudaStream_t st);
+cudaError_t launch_ox_iter(const Geo&, const OxDf&, cudaStream_t st);
+cudaError_t launch_ox_finish(const Geo&, const OxDf&, cudaStream_t st);
 
 // SL (S1)
 cudaError_t launch_divergence(const Geo&, const double* const v[3], double* div, cudaStream_t st);
