@@ -382,7 +382,8 @@ const char* const kKernelNames[K_COUNT] = {
     "k_diff_faces", "k_diff_diag", "k_to_f32", "k_divergence", "k_sl", "k_sl32",
     "k_cn_init", "k_cn_matvec", "k_cn_update", "k_cn_pupdate",
     "k_cn_ir_residual", "k_cn_ir_residual_df", "k_cn32_pupdate", "k_cn32_matvec",
-    "k_cn32_update", "k_cn_ir_correct", "k_cn32_neumann", "k_react", "k_lame", "k_elas_coef", "k_elas_coef_df",
+    "k_cn32_update", "k_cn_ir_correct", "k_cn32_neumann", "k_diff_node_df", "k_diff_faces_df",
+    "k_react", "k_lame", "k_elas_coef", "k_elas_coef_df",
     "k_elas32_coef", "k_df_pack3", "k_elas_extrapolate", "k_spec_mean", "k_spec_scale",
     "k_elas_ir_residual", "k_elas_ir_residual_df", "k_elas32_scale_r", "k_spec_x_fwd",
     "k_spec_y_fwd", "k_spec_z", "k_spec_zr", "k_spec_y_inv", "k_spec_x_inv", "k_spec_x_inv_p",
@@ -1175,10 +1176,22 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   phase_mark(X, 0);
   double* const Kf[3] = {X->a[A_KF0], X->a[A_KF1], X->a[A_KF2]};
   double* const Kfdf[3] = {X->a[A_KFDF0], X->a[A_KFDF1], X->a[A_KFDF2]};
-  CK(launch_diff_coef(G, X->dp, dt, S.g, S.w, S.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
-                      X->a[A_RHO], s, X->cn_df ? Kfdf : nullptr));
-  X->launches += 1;   // S0 is two kernels (faces, diagonal)
-  if (X->prec == TG_MIXED) {   // FP32 faces and diagonal of the inner diffusion solves
+  if (X->prec == TG_MIXED && X->cn_df) {
+    // the mixed solves read the faces as pairs and as FP32 values only (the oxygen solve in
+    // double-FP32, tg_cn_ox.cu): formed in double-FP32, node K pairs in the FP64 transport
+    // scratch (the mixed transport writes the state directly)
+    float2* const pairs[3] = {reinterpret_cast<float2*>(Kfdf[0]), reinterpret_cast<float2*>(Kfdf[1]),
+                              reinterpret_cast<float2*>(Kfdf[2])};
+    float* const f32[3] = {X->b32[B_CKF0], X->b32[B_CKF1], X->b32[B_CKF2]};
+    CK(launch_diff_coef_df(G, X->dp, dt, S.g, S.w, S.f, reinterpret_cast<float2*>(X->a[A_SL0]),
+                           X->a[A_RHO], pairs, f32, X->b32[B_CDINV], s));
+    X->launches += 2;
+  } else {
+    CK(launch_diff_coef(G, X->dp, dt, S.g, S.w, S.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
+                        X->a[A_RHO], s, X->cn_df ? Kfdf : nullptr));
+    X->launches += 1;   // S0 is two kernels (faces, diagonal)
+  }
+  if (X->prec == TG_MIXED && !X->cn_df) {   // FP32 faces and diagonal of the inner solves
     F32Copy cp;
     const double* src[4] = {Kf[0], Kf[1], Kf[2], X->a[A_DINV_D]};
     for (int q = 0; q < 4; ++q) {

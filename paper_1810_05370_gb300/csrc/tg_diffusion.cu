@@ -56,6 +56,74 @@ __global__ void __launch_bounds__(NT) k_diff_faces(Geo G, DevParams P, double ha
   }
 }
 
+// The same S0 for the mixed precision with double-FP32 residuals, whose solves need the faces
+// only as (hi, lo) pairs (double-FP32 residuals and oxygen solve) and as FP32 values (inner
+// solves), with the FP32 inverse diagonal.  Pass 1 forms each node's K once in FP64 (three
+// products) and keeps it as a pair, with rho; pass 2 forms each node's six faces as harmonic
+// means in double-FP32 arithmetic on the FP32 units (the quotient as a product with the
+// double-FP32 reciprocal), so no FP64 division is left.
+__global__ void __launch_bounds__(NT) k_diff_node_df(Geo G, DevParams P,
+                                                     const double* __restrict__ g,
+                                                     const double* __restrict__ w,
+                                                     const double* __restrict__ f, float2* Kn,
+                                                     double* rho) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const long long c = ((long long)k * G.ny + j) * G.nx + i;
+    const double gc = g[c], wc = w[c];
+    Kn[c] = df_pack(node_K(P, gc, wc, f[c]));
+    rho[c] = P.rho_g * gc + P.rho_w * wc;
+  }
+}
+
+// 2 a b / (a + b), 0 if a + b = 0.  Below 1e-30 (far outside tissue, where K is an FP32
+// subnormal) the face, at most 2 (a + b), is dropped: it is ~1e-30 of the CN diagonal's 1, and
+// the reciprocal of a subnormal sum would overflow.
+__device__ __forceinline__ Df df_harmonic(Df a, Df b) {
+  const Df s = df_add(a, b);
+  if (!(s.hi > 1e-30f)) return Df{0.0f, 0.0f};
+  const Df y = {1.0f / s.hi, 0.0f};   // reciprocal: FP32 start, one Newton step in double-FP32
+  const Df inv = df_add(y, df_mul(y, df_sub(Df{1.0f, 0.0f}, df_mul(s, y))));
+  const Df ab = df_mul(a, b);
+  return df_mul(Df{2.0f * ab.hi, 2.0f * ab.lo}, inv);
+}
+
+__global__ void __launch_bounds__(NT) k_diff_faces_df(Geo G, Df sx, Df sy, Df sz,
+                                                      const float2* __restrict__ Kn,
+                                                      float2* dfx, float2* dfy, float2* dfz,
+                                                      float* f32x, float* f32y, float* f32z,
+                                                      float* dinv32) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const Nbr nb = make_nbr(G, i, j, k);
+    const long long c = nb.at(0, 0, 0);
+    auto K = [&](long long e) { return df_of(__ldg(Kn + e)); };
+    const Df kc = K(c);
+    const Df fxp = df_mul(sx, df_harmonic(kc, K(nb.at(1, 0, 0))));
+    const Df fyp = df_mul(sy, df_harmonic(kc, K(nb.at(0, 1, 0))));
+    const Df fzp = df_mul(sz, df_harmonic(kc, K(nb.at(0, 0, 1))));
+    const Df fxm = df_mul(sx, df_harmonic(K(nb.at(-1, 0, 0)), kc));
+    const Df fym = df_mul(sy, df_harmonic(K(nb.at(0, -1, 0)), kc));
+    const Df fzm = df_mul(sz, df_harmonic(K(nb.at(0, 0, -1)), kc));
+    dfx[c] = make_float2(fxp.hi, fxp.lo);
+    dfy[c] = make_float2(fyp.hi, fyp.lo);
+    dfz[c] = make_float2(fzp.hi, fzp.lo);
+    f32x[c] = fxp.hi;
+    f32y[c] = fyp.hi;
+    f32z[c] = fzp.hi;
+    // 1 + (xp + xm) + (yp + ym) + (zp + zm), as the FP64 diagonal
+    const Df d = df_add(df_add(df_add(Df{1.0f, 0.0f}, df_add(fxp, fxm)), df_add(fyp, fym)),
+                        df_add(fzp, fzm));
+    dinv32[c] = 1.0f / d.hi;
+  }
+}
+
 // CN diagonal 1 + sum of the six faces of each node, and its inverse
 __global__ void __launch_bounds__(NT) k_diff_diag(Geo G, const double* __restrict__ Kfx,
                                                   const double* __restrict__ Kfy,
@@ -166,6 +234,21 @@ cudaError_t launch_diff_coef(const Geo& G, const DevParams& P, double dt, const 
                                                          rho, df[0], df[1], df[2]));
   TG_TIMED(K_DIFF_DIAG, st,
            k_diff_diag<<<G.grid, dim3(BX, BY), 0, st>>>(G, Kf[0], Kf[1], Kf[2], dsum, dinv));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diff_coef_df(const Geo& G, const DevParams& P, double dt, const double* g,
+                                const double* w, const double* f, float2* Kn, double* rho,
+                                float2* const Kfdf[3], float* const Kf32[3], float* dinv32,
+                                cudaStream_t st) {
+  TG_TIMED(K_DIFF_NODE_DF, st,
+           k_diff_node_df<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, g, w, f, Kn, rho));
+  const Df sx = df_split_host(0.5 * dt * G.ih2[0]), sy = df_split_host(0.5 * dt * G.ih2[1]),
+           sz = df_split_host(0.5 * dt * G.ih2[2]);
+  TG_TIMED(K_DIFF_FACES_DF, st,
+           k_diff_faces_df<<<G.grid, dim3(BX, BY), 0, st>>>(G, sx, sy, sz, Kn, Kfdf[0], Kfdf[1],
+                                                            Kfdf[2], Kf32[0], Kf32[1], Kf32[2],
+                                                            dinv32));
   return cudaGetLastError();
 }
 

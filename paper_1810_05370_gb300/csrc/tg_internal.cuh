@@ -24,7 +24,7 @@ enum KernelId : int {
   K_DIFF_FACES, K_DIFF_DIAG, K_TO_F32, K_DIVERGENCE, K_SL, K_SL32,
   K_CN_INIT, K_CN_MATVEC, K_CN_UPDATE, K_CN_PUPDATE,
   K_CN_IR_RESIDUAL, K_CN_IR_RESIDUAL_DF, K_CN32_PUPDATE, K_CN32_MATVEC, K_CN32_UPDATE,
-  K_CN_IR_CORRECT, K_CN32_NEUMANN, K_REACT, K_LAME, K_ELAS_COEF, K_ELAS_COEF_DF, K_ELAS32_COEF, K_DF_PACK3,
+  K_CN_IR_CORRECT, K_CN32_NEUMANN, K_DIFF_NODE_DF, K_DIFF_FACES_DF, K_REACT, K_LAME, K_ELAS_COEF, K_ELAS_COEF_DF, K_ELAS32_COEF, K_DF_PACK3,
   K_ELAS_EXTRAPOLATE, K_SPEC_MEAN, K_SPEC_SCALE, K_ELAS_IR_RESIDUAL, K_ELAS_IR_RESIDUAL_DF,
   K_ELAS32_SCALE_R, K_SPEC_X_FWD, K_SPEC_Y_FWD, K_SPEC_Z, K_SPEC_ZR, K_SPEC_Y_INV,
   K_SPEC_X_INV, K_SPEC_X_INV_P, K_ELAS32_MATVEC, K_ELAS32_UPDATE, K_ELAS32_MATVEC_SPEC,
@@ -509,6 +509,10 @@ __device__ __forceinline__ Df df_split(double x) {
   const float hi = __double2float_rn(x);
   return {hi, __double2float_rn(x - (double)hi)};
 }
+inline Df df_split_host(double x) {   // the same split on the host (round to nearest)
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
 __device__ __forceinline__ Df df_of(float2 v) { return {v.x, v.y}; }
 __device__ __forceinline__ float2 df_pack(double x) {
   const Df d = df_split(x);
@@ -539,6 +543,13 @@ __device__ __forceinline__ Df df_mul(Df x, Df y) {
   return df_fast_two_sum(p, e);
 }
 __device__ __forceinline__ double df_value(Df x) { return (double)x.hi + (double)x.lo; }
+
+// S0 of the mixed precision with double-FP32 residuals: node K pairs (Kn, scratch), rho, the
+// face pairs, the FP32 faces and the FP32 inverse CN diagonal (no FP64 faces)
+cudaError_t launch_diff_coef_df(const Geo&, const DevParams&, double dt, const double* g,
+                                const double* w, const double* f, float2* Kn, double* rho,
+                                float2* const Kfdf[3], float* const Kf32[3], float* dinv32,
+                                cudaStream_t st);
 
 // 4 h_A h_D [ d_D(mu d_A u_D) + d_A(lambda d_D u_D) ] at the centre node (centred differences)
 template <int A, int D>

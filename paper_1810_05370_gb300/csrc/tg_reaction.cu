@@ -76,13 +76,15 @@ __global__ void __launch_bounds__(NT) k_react(Geo G, DevParams P, double dt, int
   const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
   for (int k = k0; k < k1; ++k) {
     const long long c = ((long long)k * G.ny + j) * G.nx + i;
-    // S2 fix-up: the Crank-Nicolson increment of i comes out of g and w, in proportion
+    // S2 fix-up: the Crank-Nicolson increment of i comes out of g and w, in proportion (the
+    // proportions in T: a relative error of ~1e-7 in them moves g and w by ~1e-7 of the small
+    // increment)
     double y[5] = {p[c], ii[c], n[c], g[c], w[c]};
     {
       const double di = y[single ? 0 : 1] - i_dag[c];
-      const double gw = y[3] + y[4];
-      const double fg = gw > 0.0 ? y[3] / gw : 0.0;
-      const double fw = gw > 0.0 ? y[4] / gw : 0.0;
+      const T gw = (T)(y[3] + y[4]);
+      const double fg = gw > (T)0 ? (double)((T)y[3] / gw) : 0.0;
+      const double fw = gw > (T)0 ? (double)((T)y[4] / gw) : 0.0;
       y[3] = y[3] - di * fg;
       y[4] = y[4] - di * fw;
     }
@@ -119,9 +121,11 @@ __global__ void __launch_bounds__(NT) k_react(Geo G, DevParams P, double dt, int
     const double os = oo + dt * ko1;
     const double ko2 = -P.delta_p * y[0] + P.delta_s * (P.o_heal - os) * gwn;
     o[c] = oo + 0.5 * dt * (ko1 + ko2);
-    // S5: edema, d_t l = delta_e i / (i + delta_half) (1 - i) - delta_l l   (Eq. e:edema)
+    // S5: edema, d_t l = delta_e i / (i + delta_half) (1 - i) - delta_l l   (Eq. e:edema);
+    // the source, a rate like those of S3, in T
     const double l0 = l[c];
-    const double src = P.delta_e * y[1] / (y[1] + P.delta_half) * (1.0 - y[1]);
+    const T it = (T)y[1];
+    const double src = (double)((T)P.delta_e * it / (it + (T)P.delta_half) * ((T)1 - it));
     const double kl1 = src - P.delta_l * l0;
     const double ls = l0 + dt * kl1;
     const double kl2 = src - P.delta_l * ls;
