@@ -64,6 +64,15 @@ def mixed_kernel_bytes(n, precond):
         "k_cn32_matvec": 28,         # 3 FP32 faces, p (2 fields) in, q out
         "k_cn32_update": 52,         # D^-1, e, r, p, q (2 fields) in, e, r out
         "k_cn_ir_correct": 56,       # x (FP64), e in; x, x pair out (2 fields)
+        "k_cn32_neumann": 32,        # r (2 fields), 3 FP32 faces, D^-1 in; z (2 fields) out
+        "k_diff_node_df": 40,        # g, w, f in; K pair, rho out
+        "k_diff_faces_df": 48,       # K pairs in; 3 face pairs, 3 FP32 faces, D^-1 out
+        "k_ox_prep": 56,             # oxygen, double-FP32: 3 face pairs, o in; d, D^-1, x pairs out
+        "k_ox_init": 56,             # 3 face pairs, x, D^-1 in; r, p out
+        "k_ox_matvec": 48,           # 3 face pairs, d, p in; q out
+        "k_ox_update": 56,           # x, p, r, q, D^-1 in; x, r out
+        "k_ox_pupdate": 32,          # D^-1, r, p in; p out
+        "k_ox_finish": 16,           # x pair in, o out
         "k_cn_init": 56,             # oxygen, FP64: 3 faces, D^-1, x in; r, p out
         "k_cn_matvec": 48,           # 3 faces, diagonal, p in; q out
         "k_cn_update": 56,           # D^-1, x, r, p, q in; x, r out
