@@ -80,7 +80,7 @@ def mixed_kernel_bytes(n, precond):
         "k_react": 128,              # 9 FP64 in, 7 out
         "k_lame": 80,                # 7 species in; mu, lambda, eta out
         "k_elas_coef_df": 136,       # mu, lambda pairs, eta, p, n in; F, G, diagonal, b pairs out
-        "k_elas_extrapolate": 96,    # u, v in; u, du out
+        "k_elas_extrapolate": 120,   # u, v, v^{n-1} in; u, du out
         "k_spec_mean": 24,           # mu, lambda, eta in
         "k_elas_ir_residual_df": 160,  # u, F, G, diagonal, b pairs (3 each), mu, lambda pairs
         #                                in; r, e (FP32) out
@@ -93,7 +93,7 @@ def mixed_kernel_bytes(n, precond):
         "k_elas32_matvec_spec": 36,  # p (3), mu, lambda, eta in; q (3) out
         "k_spec_update_xfwd": 72 + s + W,  # e, p, r, q in; e, r out (3 each); spectrum out
         "k_elas_ir_correct": 132,    # u, du, e in; u, du, u pairs out
-        "k_elas_ir_finish": 48,      # du in, v out
+        "k_elas_ir_finish": 96,      # du, v in; v, v^{n-1} out
     }
 
 

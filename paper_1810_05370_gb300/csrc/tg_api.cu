@@ -283,6 +283,7 @@ Spec<R> spec_view(const Geo& G, const Layout& L, char* ws, size_t tab_off) {
   V.partial = (double*)(ws + L.sp_partial);
   V.counter = (unsigned int*)(ws + L.sp_counter);
   V.nb_partial = spec_partial_count(G);
+  V.zmap = nullptr;
   return V;
 }
 
@@ -440,6 +441,7 @@ struct tg_ctx {
   double t_phase[4];
   // spectral elasticity preconditioner (workspace sized for it when L.spectral)
   Spec<float> sp32;      // FP32 form: mixed precision, adjoint refined solves
+  alignas(64) unsigned char zmap32[128];   // TMA tensor map of sp32.W for its z pass
   Spec<double> sp64;     // FP64 form: FP64 solves
   float* z32[3];
   double* z64[3];
@@ -467,6 +469,7 @@ tg_status status_of(const CgScal& s) {
     case CG_ZERO_RHS: return TG_OK;
     case CG_NONFINITE: return TG_ERR_NONFINITE;
     case CG_MAXIT: return TG_ERR_NOCONV;
+    case CG_TIMEOUT: return TG_ERR_TIMEOUT;
     default: return TG_ERR_CUDA;
   }
 }
@@ -1444,6 +1447,7 @@ tg_status spectral_setup(tg_ctx* X) {
     }
     if (spec_prepare(X->sp32) != cudaSuccess) return TG_ERR_CUDA;
     if (launch_spec_tables(X->sp32, X->G.h, X->stream) != cudaSuccess) return TG_ERR_CUDA;
+    X->sp32.zmap = spec_make_zmap(X->sp32, X->zmap32) ? X->zmap32 : nullptr;
   }
   if (need64) {
     X->sp64 = spec_view<double>(X->G, L, X->ws, L.sp_tab64);

@@ -68,7 +68,8 @@ enum CgStatus : int {
   CG_CONVERGED = 1,
   CG_NONFINITE = 2,
   CG_MAXIT = 3,
-  CG_ZERO_RHS = 4
+  CG_ZERO_RHS = 4,
+  CG_TIMEOUT = 5     // a bounded device-side wait gave up (the solve's kernels return at once)
 };
 
 struct CgScal {
@@ -353,6 +354,7 @@ struct Spec {
   double* partial;            // per-block partial sums (x inverse pass, means)
   unsigned int* counter;
   int nb_partial;             // capacity of partial, in doubles
+  const void* zmap;           // host: TMA tensor map of W for the FP32 z pass (null: none)
 };
 
 // The CG p-update fused into the x inverse pass (mixed precision): the pass writes the new
@@ -632,6 +634,9 @@ cudaError_t launch_spectral(const Spec<R>&, const R* const r[3], R* const z[3], 
 cudaError_t launch_elas32_matvec_spec(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_spectral_update(const Spec<float>&, const Elas32&, float* const z[3],
                                    cudaStream_t st);
+// the TMA tensor map (a CUtensorMap, 128 bytes, 64-byte aligned storage) of the FP32 W for the
+// z pass with nz = 128 or 256; false if the grid has no such pass or the driver refuses
+bool spec_make_zmap(const Spec<float>& V, void* map);
 cudaError_t launch_elas32_scale_r(const Geo&, const Elas32&, cudaStream_t st);
 cudaError_t launch_elas32_update_spec(const Geo&, const Elas32&, cudaStream_t st);
 

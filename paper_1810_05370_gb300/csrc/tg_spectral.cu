@@ -27,6 +27,9 @@
 // registers (one radix-2, 4 or 8 stage takes the remainder of log2 n), ping-ponging between
 // two shared-memory buffers with one barrier per stage; each block keeps its line length's
 // twiddles in shared memory and issues its global loads in batches of eight per thread.
+#include <cuda.h>           // CUtensorMap (types only; the encoder comes from the driver)
+#include <cudaTypedefs.h>
+
 #include "tg_tiles.cuh"
 
 namespace tg {
@@ -792,6 +795,221 @@ __global__ void __launch_bounds__(ZR_COLS * P, 512 / (ZR_COLS * P))
     cg_after_precond(*S, out);
 }
 
+// ------------------------------------------------- z pass, tiles staged by TMA (FP32)
+// The register z pass above with its global traffic moved to the tensor-memory accelerator:
+// one thread issues three bulk tensor copies (the block's ZR_COLS mode columns at one ky, all
+// nz planes, one component each) that land in shared memory and complete on an mbarrier; the
+// threads transform from and back into that tile, a thread's elements staying in its own slots
+// of the tile between the forward transform, the 3x3 inverse and the inverse transform (the
+// forward transform leaves the modes of a column thread on the planes it loaded); three bulk
+// tensor stores write the tile back.  No global load or store is issued by the threads, and
+// nothing of the tile is held in registers across the copies.  Waits on the mbarrier are
+// bounded in time; a wait that gives up marks the solve CG_TIMEOUT and returns.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// true once the phase completed; false after limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns) {
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 63 && globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, int c0, int c1, int c2,
+                                             int c3, const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+      ::"l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit_and_wait() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+constexpr uint64_t ZR_WAIT_NS = 2000000000ull;   // 2 s for a tile that takes microseconds
+
+template <int P>
+constexpr size_t spec_smem_zr_tma() {   // tile (3 components), exchange buffer, twiddles, barrier
+  return (size_t)(3 * 16 * P * ZR_COLS + 16 * zr_row<P>() + 16 * P) * sizeof(float2) + 16;
+}
+
+template <int P>
+__global__ void __launch_bounds__(ZR_COLS * P)
+    k_spec_zr_tma(const __grid_constant__ CUtensorMap map, Spec<float> V, CgScal* S) {
+  using C = float2;
+  constexpr int N = 16 * P, J = 16 / P, LP = P == 16 ? 4 : (P == 8 ? 3 : 2);
+  constexpr int TILE = N * ZR_COLS;            // elements of one component
+  static_assert(P == 8 || P == 16, "nz = 128 or 256");
+  if (spec_skip<float>(S)) return;
+  extern __shared__ __align__(1024) unsigned char zr_smem[];
+  C* tile = reinterpret_cast<C*>(zr_smem);     // [component][plane][column]
+  C* xb = tile + 3 * TILE;                     // exchange buffer
+  C* tw = xb + 16 * zr_row<P>();
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tw + N);
+  const int c = threadIdx.x % ZR_COLS, t = threadIdx.x / ZR_COLS;
+  const int kx0 = blockIdx.x * ZR_COLS, ky = blockIdx.y;
+  const bool valid = kx0 + c < V.nxh;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, 3u * TILE * (uint32_t)sizeof(C));
+#pragma unroll
+    for (int q = 0; q < 3; ++q) tma_load_4d(tile + q * TILE, &map, kx0, ky, 0, q, bar);
+  }
+  load_roots(tw, V.tw[2], N);
+  __syncthreads();                             // barrier initialised, twiddles visible
+  if (!mbar_wait_bounded(bar, 0, ZR_WAIT_NS)) {
+    if (threadIdx.x == 0) S->status = CG_TIMEOUT;
+    mbar_wait_bounded(bar, 0, ZR_WAIT_NS);     // the copies in flight target this tile
+    return;
+  }
+  auto el = [&](int q, int z) -> C& { return tile[q * TILE + z * ZR_COLS + c]; };
+  auto slot = [&](int k2, int tt) { return k2 * zr_row<P>() + tt * ZR_COLS + c; };
+  C v[16];
+
+  // forward transform of component q (four-step, nz = 16 x P, as in k_spec_zr): the modes
+  // kz = t + P j + 16 k1 land in v[j P + k1] and are kept on the planes kz of the tile
+  auto forward = [&](int q) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = el(q, t + P * m);
+    dft<4, -1>(v);
+#pragma unroll
+    for (int k2 = 1; k2 < 16; ++k2) v[k2] = cmul(v[k2], tw[t * k2]);
+    if (q > 0) __syncthreads();                // the previous exchange has been read
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) xb[slot(k2, t)] = v[k2];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int u = 0; u < P; ++u) v[j * P + u] = xb[slot(t + P * j, u)];
+#pragma unroll
+    for (int j = 0; j < J; ++j) dft<LP, -1>(*reinterpret_cast<C(*)[P]>(&v[j * P]));
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) el(q, t + P * j + 16 * k1) = v[j * P + k1];
+  };
+  auto inverse = [&](int q) {
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) v[j * P + k1] = el(q, t + P * j + 16 * k1);
+#pragma unroll
+    for (int j = 0; j < J; ++j) dft<LP, +1>(*reinterpret_cast<C(*)[P]>(&v[j * P]));
+    __syncthreads();                           // the previous exchange has been read
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int u = 0; u < P; ++u) xb[slot(t + P * j, u)] = v[j * P + u];
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) v[k2] = xb[slot(k2, t)];
+#pragma unroll
+    for (int k2 = 1; k2 < 16; ++k2) v[k2] = cmul(v[k2], root<+1>(tw, t * k2));
+    dft<4, +1>(v);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) el(q, t + P * m) = v[m];
+  };
+
+#pragma unroll 1
+  for (int q = 0; q < 3; ++q) forward(q);
+
+  // the 3x3 inverse per mode (as in k_spec_zr) and the Parseval term of <r, z>; columns past
+  // nx/2 (row padding, whatever they hold) take no part in the sum
+  const int kx = valid ? kx0 + c : 0;
+  const float mu0 = (float)V.mean[0], lam0 = (float)V.mean[1], eta0 = (float)V.mean[2];
+  const float cc = lam0 + mu0;
+  const float inv_vol = (float)(1.0 / ((double)V.nx * V.ny * V.nz));
+  const float Sx = V.S[0][kx], Tx = V.T[0][kx];
+  const float Sy = V.S[1][ky], Ty = V.T[1][ky];
+  const float wgt = (kx == 0 || kx == V.nx / 2) ? 1.0f : 2.0f;
+  float rz_part = 0.0f;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      const int kz = t + P * j + 16 * k1;
+      const float Sv[3] = {Sx, Sy, __ldg(V.S[2] + kz)};
+      const float Tv[3] = {Tx, Ty, __ldg(V.T[2] + kz)};
+      const float base = eta0 + mu0 * (Sv[0] + Sv[1] + Sv[2]);
+      const C rv[3] = {el(0, kz), el(1, kz), el(2, kz)};
+      float tdt = 0.0f, dinv[3];
+      C y[3], s = {0.0f, 0.0f};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float D = base + cc * (Sv[q] - Tv[q] * Tv[q]);
+        dinv[q] = D > 0.0f ? __fdividef(1.0f, D) : 0.0f;
+        y[q] = C{rv[q].x * dinv[q], rv[q].y * dinv[q]};
+        tdt += Tv[q] * Tv[q] * dinv[q];
+        s.x += Tv[q] * y[q].x;
+        s.y += Tv[q] * y[q].y;
+      }
+      const float f = __fdividef(cc, 1.0f + cc * tdt);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float g = f * Tv[q] * dinv[q];
+        const C zq = C{(y[q].x - g * s.x) * inv_vol, (y[q].y - g * s.y) * inv_vol};
+        if (valid) rz_part += wgt * (rv[q].x * zq.x + rv[q].y * zq.y);
+        el(q, kz) = zq;
+      }
+    }
+  }
+
+#pragma unroll 1
+  for (int q = 0; q < 3; ++q) inverse(q);
+  fence_proxy_async_smem();                    // the tile's writes, visible to the copies
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) tma_store_4d(&map, kx0, ky, 0, q, tile + q * TILE);
+    bulk_commit_and_wait();
+  }
+  double out;
+  if (block_sum_last((double)rz_part, V.partial, V.counter, blockIdx.y * gridDim.x + blockIdx.x,
+                     gridDim.x * gridDim.y, out))
+    cg_after_precond(*S, out);
+}
+
 // ---------------------------------------------------------------------------- x inverse
 // block (pair tile, z, component): the half spectra of rows y0 + 2l, y0 + 2l + 1 form
 // C[k] = A[k] + i B[k] over all k (Hermitian extension); the inverse transform is
@@ -980,8 +1198,35 @@ cudaError_t spec_prepare(const Spec<R>& V) {
   if constexpr (sizeof(R) == 4) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_zr<16>, A, optin);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_zr<8>, A, optin);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_zr_tma<16>, A, optin);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_zr_tma<8>, A, optin);
   }
   return e;
+}
+
+// W as a 4-D tensor of 8-byte elements (x modes with the row pitch nxp, y, z, component); box:
+// ZR_COLS modes x 1 row x all nz planes x 1 component.  The base is 256-byte aligned, the
+// strides multiples of 16 bytes (nxp is a multiple of 16 modes), the box's inner extent
+// ZR_COLS * 8 = 64 bytes, and the kernel's x coordinates multiples of ZR_COLS (64 bytes).
+bool spec_make_zmap(const Spec<float>& V, void* map) {
+  if (V.nz != 128 && V.nz != 256) return false;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr)
+    return false;
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const cuuint64_t dims[4] = {(cuuint64_t)V.nxp, (cuuint64_t)V.ny, (cuuint64_t)V.nz, 3};
+  const cuuint64_t row = (cuuint64_t)V.nxp * sizeof(float2);
+  const cuuint64_t strides[3] = {row, row * V.ny, row * V.ny * V.nz};
+  const cuuint32_t box[4] = {(cuuint32_t)ZR_COLS, 1, (cuuint32_t)V.nz, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if ((reinterpret_cast<uintptr_t>(V.W) & 15) != 0 || (row & 15) != 0) return false;
+  return encode(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, V.W, dims,
+                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <typename R>
@@ -1010,11 +1255,23 @@ cudaError_t launch_spec_mean(long long n, const double* mu, const double* lam,
   return cudaGetLastError();
 }
 
-// the z pass: in registers for FP32 and nz = 128 or 256, staged through shared memory otherwise
+// the z pass: for FP32 and nz = 128 or 256 in registers, from tiles staged by TMA when the
+// context made the tensor map (and the pass updates a solve's scalars), else from global
+// memory; staged through shared memory otherwise
 template <typename R>
 void launch_spec_z(const Spec<R>& V, CgScal* S, cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
     const dim3 g((V.nxh + ZR_COLS - 1) / ZR_COLS, V.ny);
+    if (V.zmap != nullptr && S != nullptr && (V.nz == 256 || V.nz == 128)) {
+      const CUtensorMap& map = *static_cast<const CUtensorMap*>(V.zmap);
+      if (V.nz == 256)
+        TG_TIMED(K_SPEC_ZR, st,
+                 k_spec_zr_tma<16><<<g, 16 * ZR_COLS, spec_smem_zr_tma<16>(), st>>>(map, V, S));
+      else
+        TG_TIMED(K_SPEC_ZR, st,
+                 k_spec_zr_tma<8><<<g, 8 * ZR_COLS, spec_smem_zr_tma<8>(), st>>>(map, V, S));
+      return;
+    }
     if (V.nz == 256) {
       TG_TIMED(K_SPEC_ZR, st, k_spec_zr<16><<<g, 16 * ZR_COLS, spec_smem_zr<16>(), st>>>(V, S));
       return;
