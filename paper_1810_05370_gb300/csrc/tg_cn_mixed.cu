@@ -351,11 +351,14 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
   const int k0 = blockIdx.z * zc, k1 = min(G.nz, k0 + zc);
   const bool run[2] = {run0, run1};
   const int rs[2] = {run0 ? r0 : 0, run1 ? r1 : 0};
-  auto plane = [&](int k) {   // k >= k0 - 3 >= -3; up to three padding steps past k1 + 2
-    const int kw = ((k % G.nz) + G.nz) % G.nz;
-    return (long long)kw * G.nxy + col;
-  };
-  // rings over the last four planes, slot = (plane - tb) & 3 with tb = k0 - NM_H
+  const float* const rsrc[2] = {I.r[run0 ? r0 : 0] + col, I.r[run1 ? r1 : 0] + col};
+  float* const zdst[2] = {I.z[run0 ? r0 : 0] + col, I.z[run1 ? r1 : 0] + col};
+  const float* const kfx = I.Kf[0] + col;
+  const float* const kfy = I.Kf[1] + col;
+  const float* const kfz = I.Kf[2] + col;
+  const float* const dsrc = I.dinv + col;
+  // rings over the last four planes, slot = (plane - tb) & 3 with tb = k0 - NM_H; the shared
+  // planes of the terms alternate with (plane - tb) & 1, the y faces with (plane - tb) & 3
   float y0[4][2], y1[4][2], y2[4][2], rr[4][2], lz[4][2];   // lz: a_z(k-1) y_2(k-1) of plane k
   float ax[4], ay[4], az[4], di[4];
 #pragma unroll
@@ -365,45 +368,52 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
     ax[m] = ay[m] = az[m] = di[m] = 0.0f;
   }
   float acc[2] = {0.0f, 0.0f};
-  float nr[2], nax, nay, naz, ndi;   // plane t + 1, loaded one step ahead
-  auto fetch = [&](int k) {
-    const long long g = plane(k);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) nr[q] = run[q] ? __ldg(I.r[rs[q]] + g) : 0.0f;
-    nax = __ldg(I.Kf[0] + g);
-    nay = __ldg(I.Kf[1] + g);
-    naz = __ldg(I.Kf[2] + g);
-    ndi = __ldg(I.dinv + g);
-  };
+  // planes t + 1 and t + 2 in flight: the loads of plane t + 2 are issued at step t into the
+  // set that plane t came from (set = (plane - tb) & 1)
+  float pr[2][2], pax[2], pay[2], paz[2], pdi[2];
   const int tb = k0 - NM_H;
-  const int te = tb + ((k1 - k0 + 2 * NM_H + 3) & ~3);   // steps tb .. te - 1, a multiple of 4
-  fetch(tb);
-  for (int t0 = tb; t0 < te; t0 += 4) {
+  const int nsteps = (k1 - k0 + 2 * NM_H + 3) & ~3;     // a multiple of 4
+  // wrapped plane indices of the next fetch and of the output (t - 3), advanced per step
+  int kf = ((tb % G.nz) + G.nz) % G.nz;
+  int ko = k0;   // the first output plane (k0 < nz), written at rel = 2 NM_H
+  auto fetch = [&](int set) {
+    const long long g = (long long)kf * G.nxy;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) pr[set][q] = run[q] ? __ldg(rsrc[q] + g) : 0.0f;
+    pax[set] = __ldg(kfx + g);
+    pay[set] = __ldg(kfy + g);
+    paz[set] = __ldg(kfz + g);
+    pdi[set] = __ldg(dsrc + g);
+    kf = kf + 1 == G.nz ? 0 : kf + 1;
+  };
+  fetch(0);
+  fetch(1);
+  // term j is formed on plane t - j while t - j lies in [k0 - 3 + j, k1 + 2 - j], i.e. while
+  // the step's offset rel = t - tb lies in [2 j, k1 - k0 + 5]; the output needs rel >= 6
+  const int rel_end = k1 - k0 + 2 * NM_H - 1;
+  for (int m4 = 0; m4 < nsteps; m4 += 4) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int t = t0 + u;
-      constexpr int M = 3;   // slot of plane t - 1 is (u + M) & 3, etc.
-      const int s0 = u, s1 = (u + M) & 3, s2 = (u + 2 * M) & 3, s3 = (u + 3 * M) & 3;
-      // take plane t, prefetch plane t + 1
+      const int rel = m4 + u;
+      const int s0 = u, s1 = (u + 3) & 3, s2 = (u + 2) & 3, s3 = (u + 1) & 3;
+      const int p0 = u & 1, p1 = (u + 1) & 1;   // parities of planes t, t - 1 (t - 2: p0, ...)
+      const int ps = u & 1;
 #pragma unroll
-      for (int q = 0; q < 2; ++q) rr[s0][q] = nr[q];
-      ax[s0] = nax;
-      ay[s0] = nay;
-      az[s0] = naz;
-      di[s0] = ndi;
-      if (t + 1 < te) fetch(t + 1);
+      for (int q = 0; q < 2; ++q) rr[s0][q] = pr[ps][q];
+      ax[s0] = pax[ps];
+      ay[s0] = pay[ps];
+      az[s0] = paz[ps];
+      di[s0] = pdi[ps];
+      if (rel + 2 < nsteps) fetch(ps);
       // term 0 on plane t, the whole tile
-      const int pt = (t + 4) & 1;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         y0[s0][q] = di[s0] * rr[s0][q];
-        T.y[0][pt][q][cell] = y0[s0][q];
+        T.y[0][p0][q][cell] = y0[s0][q];
       }
-      T.ay[(t + 4) & 3][cell] = ay[s0];
+      T.ay[s0][cell] = ay[s0];
       // term 1 on plane t - 1
       {
-        const int k = t - 1;
-        const int pk = (k + 4) & 1, fk = (k + 4) & 3;
         const float axm = __shfl_up_sync(0xffffffffu, ax[s1], 1);
         float yp[2], ym[2];   // every lane takes part in the shuffles
 #pragma unroll
@@ -411,21 +421,20 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
           yp[q] = __shfl_down_sync(0xffffffffu, y0[s1][q], 1);
           ym[q] = __shfl_up_sync(0xffffffffu, y0[s1][q], 1);
         }
-        if (in1 && k >= k0 - 2 && k <= k1 + 1) {
-          const float aym = T.ay[fk][cell - NM_X];
+        if (in1 && rel >= 2 && rel <= rel_end) {
+          const float aym = T.ay[s1][cell - NM_X];
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
-            const float* Y = T.y[0][pk][q];
-            y1[s1][q] = di[s1] * (ax[s1] * yp[q] + axm * ym[q] + ay[s1] * Y[cell + NM_X] +
-                                  aym * Y[cell - NM_X] + az[s1] * y0[s0][q] + az[s2] * y0[s2][q]);
-            T.y[1][pk][q][cell] = y1[s1][q];
+            const float* Y = T.y[0][p1][q];
+            const float ha = ax[s1] * yp[q] + axm * ym[q] + az[s1] * y0[s0][q];
+            const float hb = ay[s1] * Y[cell + NM_X] + aym * Y[cell - NM_X] + az[s2] * y0[s2][q];
+            y1[s1][q] = di[s1] * (ha + hb);
+            T.y[1][p1][q][cell] = y1[s1][q];
           }
         }
       }
       // term 2 on plane t - 2; the z-lower term a_z(k) y_2(k) of the plane above it
       {
-        const int k = t - 2;
-        const int pk = (k + 4) & 1, fk = (k + 4) & 3;
         const float axm = __shfl_up_sync(0xffffffffu, ax[s2], 1);
         float yp[2], ym[2];
 #pragma unroll
@@ -433,22 +442,21 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
           yp[q] = __shfl_down_sync(0xffffffffu, y1[s2][q], 1);
           ym[q] = __shfl_up_sync(0xffffffffu, y1[s2][q], 1);
         }
-        if (in2 && k >= k0 - 1 && k <= k1) {
-          const float aym = T.ay[fk][cell - NM_X];
+        if (in2 && rel >= 4 && rel <= rel_end) {
+          const float aym = T.ay[s2][cell - NM_X];
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
-            const float* Y = T.y[1][pk][q];
-            y2[s2][q] = di[s2] * (ax[s2] * yp[q] + axm * ym[q] + ay[s2] * Y[cell + NM_X] +
-                                  aym * Y[cell - NM_X] + az[s2] * y1[s1][q] + az[s3] * y1[s3][q]);
-            T.y[2][pk][q][cell] = y2[s2][q];
+            const float* Y = T.y[1][p0][q];
+            const float ha = ax[s2] * yp[q] + axm * ym[q] + az[s2] * y1[s1][q];
+            const float hb = ay[s2] * Y[cell + NM_X] + aym * Y[cell - NM_X] + az[s3] * y1[s3][q];
+            y2[s2][q] = di[s2] * (ha + hb);
+            T.y[2][p0][q][cell] = y2[s2][q];
             lz[s1][q] = az[s2] * y2[s2][q];   // for term 3 on plane t - 1 (two steps on)
           }
         }
       }
       // term 3 on plane t - 3, and the output there
       {
-        const int k = t - 3;
-        const int pk = (k + 4) & 1, fk = (k + 4) & 3;
         const float axm = __shfl_up_sync(0xffffffffu, ax[s3], 1);
         float yp[2], ym[2];
 #pragma unroll
@@ -456,20 +464,24 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
           yp[q] = __shfl_down_sync(0xffffffffu, y2[s3][q], 1);
           ym[q] = __shfl_up_sync(0xffffffffu, y2[s3][q], 1);
         }
-        if (in3 && k >= k0 && k < k1) {
-          const float aym = T.ay[fk][cell - NM_X];
-          const long long g = plane(k);
+        if (rel >= 2 * NM_H) {
+          if (in3 && rel <= rel_end) {
+            const float aym = T.ay[s3][cell - NM_X];
+            const long long g = (long long)ko * G.nxy;
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const float* Y = T.y[2][pk][q];
-            const float y3 = di[s3] * (ax[s3] * yp[q] + axm * ym[q] + ay[s3] * Y[cell + NM_X] +
-                                       aym * Y[cell - NM_X] + az[s3] * y2[s2][q] + lz[s3][q]);
-            const float z = ((y0[s3][q] + y1[s3][q]) + y2[s3][q]) + y3;
-            if (out && run[q]) {
-              I.z[rs[q]][g] = z;
-              acc[q] += rr[s3][q] * z;
+            for (int q = 0; q < 2; ++q) {
+              const float* Y = T.y[2][p1][q];
+              const float ha = ax[s3] * yp[q] + axm * ym[q] + az[s3] * y2[s2][q];
+              const float hb = ay[s3] * Y[cell + NM_X] + aym * Y[cell - NM_X] + lz[s3][q];
+              const float y3 = di[s3] * (ha + hb);
+              const float z = ((y0[s3][q] + y1[s3][q]) + y2[s3][q]) + y3;
+              if (out && run[q]) {
+                zdst[q][g] = z;
+                acc[q] += rr[s3][q] * z;
+              }
             }
           }
+          ko = ko + 1 == G.nz ? 0 : ko + 1;
         }
       }
       __syncthreads();
