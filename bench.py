@@ -55,7 +55,7 @@ def mixed_kernel_bytes(n, precond):
     return {
         "k_diff_faces": 80,          # g, w, f in; 3 faces, rho, 3 face pairs out
         "k_diff_diag": 40,           # 3 faces in; diagonal and its inverse out
-        "k_to_f32": 84,              # FP32 copies: 4 arrays in S0, 10 in S1 (mean per launch)
+        "k_to_f32": 120,             # FP32 copies of the 10 fields the transport gathers
         "k_divergence": 32,          # v (3) in, div v out
         "k_sl32": 88,                # 10 FP32 fields gathered, 6 FP64 fields out
         "k_df_pack3": 48,            # 3 FP64 in, 3 pairs out
