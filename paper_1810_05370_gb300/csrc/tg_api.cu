@@ -42,7 +42,7 @@ enum Arr {
 enum Arr32 {
   B_MU, B_LAM, B_ETA, B_DINV0, B_DINV1, B_DINV2,
   B_E0, B_E1, B_E2, B_R0, B_R1, B_R2, B_P0, B_P1, B_P2, B_PB0, B_PB1, B_PB2, B_Q0, B_Q1, B_Q2,
-  B_V0, B_V1, B_V2, B_DIV, B_SQ0, B_SQ1, B_SQ2, B_SQ3, B_SQ4, B_SQ5,
+  B_SL0, B_SL1, B_SL2, B_SL3, B_SL4, B_SL5, B_SL6, B_SL7, B_SL8, B_SL9, B_SL10, B_SL11,
   B_CKF0, B_CKF1, B_CKF2, B_CDINV,   // FP32 CN faces and Jacobi inverse diagonal
   B_COUNT
 };
@@ -392,7 +392,7 @@ const char* const kKernelNames[K_COUNT] = {
     "k_spec_update_xfwd", "k_elas_ir_correct", "k_elas_ir_finish", "k_elas_init",
     "k_elas_init_spec", "k_elas_matvec", "k_elas_update", "k_elas_pupdate", "k_elas_update_spec",
     "k_elas_pupdate_spec", "k_elas_finish", "k_ox_prep", "k_ox_init", "k_ox_matvec",
-    "k_ox_update", "k_ox_pupdate", "k_ox_finish"};
+    "k_ox_update", "k_ox_pupdate", "k_ox_finish", "k_sl32_pack", "k_lame_df"};
 
 }  // namespace
 
@@ -918,6 +918,19 @@ tg_status cn_solve_mixed_concurrent(tg_ctx* X, tg_stats* stats) {
   return e == TG_OK ? TG_OK : fail(X, e);
 }
 
+// The interleaved inputs of the FP32 transport.  The FP32 arrays are consecutive, each at
+// least nvox * 4 bytes and 256-byte aligned, so four of them hold one float4 per voxel.
+Sl32 sl32_view(tg_ctx* X) {
+  tg_state& S = X->st;
+  Sl32 T;
+  T.v4 = reinterpret_cast<float4*>(X->b32[B_SL0]);
+  T.qa = reinterpret_cast<float4*>(X->b32[B_SL4]);
+  T.qb = reinterpret_cast<float4*>(X->b32[B_SL8]);
+  double* const outs[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
+  for (int q = 0; q < 6; ++q) T.out[q] = outs[q];
+  return T;
+}
+
 Elas32 elas32_view(tg_ctx* X) {
   Elas32 I;
   I.mu = X->b32[B_MU];
@@ -1089,17 +1102,19 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
 
 tg_status build_elas_coef(tg_ctx* X, bool force) {
   const tg_state& S = X->st;
-  CK(launch_lame(X->G, X->dp, S.p, S.i, S.n, S.g, S.w, S.f, S.bg, X->a[A_MU], X->a[A_LAM],
-                 X->a[A_ETA], X->stream));
   double* const u[3] = {S.u[0], S.u[1], S.u[2]};
   const Elas E = elas_view(X, u, nullptr);
-  if (X->df_res) {   // FP32 nodes and node pairs first, then the faces in double-FP32
+  if (X->df_res) {   // node values and pairs (and s = p + n) first, then faces and force
     const Elas32 I = elas32_view(X);
-    CK(launch_elas32_coef(X->G, E, I, X->stream, ELAS32_NODES));
-    CK(launch_elas_coef_df(X->G, X->dp, E, I, S.p, S.n, force, X->stream));
-    X->launches += 3;
+    float2* const sdf = reinterpret_cast<float2*>(X->a[A_DIV]);   // free in the mixed step
+    CK(launch_lame_df(X->G, X->dp, S.p, S.i, S.n, S.g, S.w, S.f, S.bg, X->a[A_MU], X->a[A_LAM],
+                      X->a[A_ETA], I.mu, I.lam, I.eta, E.mudf, E.lamdf, sdf, X->stream));
+    CK(launch_elas_coef_df(X->G, X->dp, E, I, sdf, force, X->stream));
+    X->launches += 2;
     return TG_OK;
   }
+  CK(launch_lame(X->G, X->dp, S.p, S.i, S.n, S.g, S.w, S.f, S.bg, X->a[A_MU], X->a[A_LAM],
+                 X->a[A_ETA], X->stream));
   CK(launch_elas_coef(X->G, X->dp, E, S.p, S.n, force, X->stream));
   X->launches += 2;
   return TG_OK;
@@ -1207,30 +1222,16 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   }
   // S1: semi-Lagrangian transport with v^n
   const double* const v[3] = {S.v[0], S.v[1], S.v[2]};
-  CK(launch_divergence(G, v, X->a[A_DIV], s));
   const double* const qin[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
   if (X->prec == TG_MIXED) {
-    // FP32 copies of everything the interpolation gathers, then FP32 transport into the state
-    F32Copy cp;
-    const double* src[10] = {S.v[0], S.v[1], S.v[2], X->a[A_DIV], S.p, S.i, S.n, S.g, S.w, S.f};
-    const int dst[10] = {B_V0, B_V1, B_V2, B_DIV, B_SQ0, B_SQ1, B_SQ2, B_SQ3, B_SQ4, B_SQ5};
-    for (int q = 0; q < 10; ++q) {
-      cp.src[q] = src[q];
-      cp.dst[q] = X->b32[dst[q]];
-    }
-    cp.count = 10;
-    CK(launch_to_f32(G.nvox, cp, s));
-    Sl32 T;
-    for (int d = 0; d < 3; ++d) T.v[d] = X->b32[B_V0 + d];
-    T.div = X->b32[B_DIV];
-    double* const outs[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
-    for (int q = 0; q < 6; ++q) {
-      T.q[q] = X->b32[B_SQ0 + q];
-      T.out[q] = outs[q];
-    }
+    // interleaved FP32 copies of everything the interpolation gathers, then FP32 transport
+    // into the state
+    const Sl32 T = sl32_view(X);
+    CK(launch_sl32_pack(G, v, qin, T, s));
     CK(launch_sl32(G, dt, T, s));
-    X->launches += 3;
+    X->launches += 2;
   } else {
+    CK(launch_divergence(G, v, X->a[A_DIV], s));
     double* const qout[6] = {X->a[A_SL0], X->a[A_SL1], X->a[A_SL2],
                              X->a[A_SL3], X->a[A_SL4], X->a[A_SL5]};
     CK(launch_sl_advect(G, dt, v, X->a[A_DIV], qin, qout, s));
@@ -1914,24 +1915,9 @@ tg_status queue_pre_diffusion(tg_ctx* X, double dt) {
   CK(launch_diff_coef(G, X->dp, dt, S.g, S.w, S.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
                       X->a[A_RHO], s));
   const double* const v[3] = {S.v[0], S.v[1], S.v[2]};
-  CK(launch_divergence(G, v, X->a[A_DIV], s));
-  F32Copy cp;
-  const double* src[10] = {S.v[0], S.v[1], S.v[2], X->a[A_DIV], S.p, S.i, S.n, S.g, S.w, S.f};
-  const int dst[10] = {B_V0, B_V1, B_V2, B_DIV, B_SQ0, B_SQ1, B_SQ2, B_SQ3, B_SQ4, B_SQ5};
-  for (int q = 0; q < 10; ++q) {
-    cp.src[q] = src[q];
-    cp.dst[q] = X->b32[dst[q]];
-  }
-  cp.count = 10;
-  CK(launch_to_f32(G.nvox, cp, s));
-  Sl32 T;
-  for (int d = 0; d < 3; ++d) T.v[d] = X->b32[B_V0 + d];
-  T.div = X->b32[B_DIV];
-  double* const outs[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
-  for (int q = 0; q < 6; ++q) {
-    T.q[q] = X->b32[B_SQ0 + q];
-    T.out[q] = outs[q];
-  }
+  const double* const qin[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
+  const Sl32 T = sl32_view(X);
+  CK(launch_sl32_pack(G, v, qin, T, s));
   CK(launch_sl32(G, dt, T, s));
   CK(cudaMemcpyAsync(X->a[A_IDAG], S.i, bytes, cudaMemcpyDeviceToDevice, s));
   return TG_OK;

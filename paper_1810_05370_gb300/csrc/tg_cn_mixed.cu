@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(NT) k_cn_ir_correct(long long n, Cn3 C, Cn32 I
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       if (!((mask >> r) & 1)) continue;
-      const double x = C.x[r][c] + (double)I.e[r][c];
+      const double x = C.x[r][c] + f64_of(I.e[r][c]);
       C.x[r][c] = x;
       if (C.df) C.xdf[r][c] = df_pack(x);   // the next residual's pairs
     }

@@ -58,10 +58,11 @@ __global__ void __launch_bounds__(NT) k_diff_faces(Geo G, DevParams P, double ha
 
 // The same S0 for the mixed precision with double-FP32 residuals, whose solves need the faces
 // only as (hi, lo) pairs (double-FP32 residuals and oxygen solve) and as FP32 values (inner
-// solves), with the FP32 inverse diagonal.  Pass 1 forms each node's K once in FP64 (three
-// products) and keeps it as a pair, with rho; pass 2 forms each node's six faces as harmonic
-// means in double-FP32 arithmetic on the FP32 units (the quotient as a product with the
-// double-FP32 reciprocal), so no FP64 division is left.
+// solves), with the FP32 inverse diagonal.  Pass 1 forms each node's K once in double-FP32
+// from the split FP64 fields and keeps it as a pair, with rho (one FP64 addition, for its
+// FP64 output); pass 2 forms each node's six faces as harmonic means in double-FP32
+// arithmetic on the FP32 units (the quotient as a product with the double-FP32 reciprocal),
+// so no FP64 division is left.
 __global__ void __launch_bounds__(NT) k_diff_node_df(Geo G, DevParams P,
                                                      const double* __restrict__ g,
                                                      const double* __restrict__ w,
@@ -70,12 +71,17 @@ __global__ void __launch_bounds__(NT) k_diff_node_df(Geo G, DevParams P,
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= G.nx || j >= G.ny) return;
+  const Df kg = df_split(P.k_g), kw = df_split(P.k_w), kf = df_split(P.k_f);
+  const Df ks = df_split(P.k_scale), rg = df_split(P.rho_g), rw = df_split(P.rho_w);
   const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
   for (int k = k0; k < k1; ++k) {
     const long long c = ((long long)k * G.ny + j) * G.nx + i;
-    const double gc = g[c], wc = w[c];
-    Kn[c] = df_pack(node_K(P, gc, wc, f[c]));
-    rho[c] = P.rho_g * gc + P.rho_w * wc;
+    const Df gc = df_split(g[c]), wc = df_split(w[c]);
+    // node_K's order: k_scale ((k_g g + k_w w) + k_f f), clamped at 0
+    Df K = df_mul(ks, df_add(df_add(df_mul(kg, gc), df_mul(kw, wc)), df_mul(kf, df_split(f[c]))));
+    if (!(K.hi > 0.0f)) K = Df{0.0f, 0.0f};
+    Kn[c] = make_float2(K.hi, K.lo);
+    rho[c] = df_value(df_add(df_mul(rg, gc), df_mul(rw, wc)));
   }
 }
 

@@ -76,19 +76,23 @@ __global__ void __launch_bounds__(NT) k_elas_coef(Geo G, DevParams P, Elas E,
 }
 
 // The coefficient build of the double-FP32 residual (mixed precision): faces, diagonal and
-// force as (hi, lo) pairs.  The faces are formed from the pairs of the node mu and lambda
-// (written first by the FP32 node pass) in double-FP32 arithmetic on the FP32 units; only
-// the force (tanh) is evaluated in FP64.  With Jacobi preconditioning this also writes the
-// inner solves' FP32 inverse diagonal.
-__global__ void __launch_bounds__(NT) k_elas_coef_df(Geo G, DevParams P, Elas E, Elas32 I,
-                                                     const double* __restrict__ p,
-                                                     const double* __restrict__ n, int force) {
+// force as (hi, lo) pairs, all in double-FP32 arithmetic on the FP32 units (no FP64
+// operation).  The faces are formed from the pairs of the node mu and lambda, the force
+// b = zeta tanh(s) grad_h s from the pairs of s = p + n (both written first by k_lame_df),
+// with the double-FP32 tanh.  With Jacobi preconditioning this also writes the inner solves'
+// FP32 inverse diagonal.
+__global__ void __launch_bounds__(NT, 4) k_elas_coef_df(Geo G, DevParams P, Elas E, Elas32 I,
+                                                     const float2* __restrict__ sdf, int force) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= G.nx || j >= G.ny) return;
-  Df ih2[3];
+  Df ih2[3], i2h[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) ih2[d] = df_split(G.ih2[d]);
+  for (int d = 0; d < 3; ++d) {
+    ih2[d] = df_split(G.ih2[d]);
+    i2h[d] = df_split(G.inv2h[d]);
+  }
+  const Df zeta = df_split(P.zeta);
   auto half = [](Df x) { return Df{0.5f * x.hi, 0.5f * x.lo}; };    // exact
   auto twice = [](Df x) { return Df{2.0f * x.hi, 2.0f * x.lo}; };   // exact
   const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
@@ -101,14 +105,14 @@ __global__ void __launch_bounds__(NT) k_elas_coef_df(Geo G, DevParams P, Elas E,
     Df Fp[3], Fm[3], Gp[3], Gm[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const Df mp = half(df_add(muc, df_of(E.mudf[np[d]])));
-      const Df mm = half(df_add(df_of(E.mudf[nm[d]]), muc));
-      const Df lp = half(df_add(lac, df_of(E.lamdf[np[d]])));
-      const Df lm = half(df_add(df_of(E.lamdf[nm[d]]), lac));
+      const Df mp = half(df_add_pos(muc, df_of(E.mudf[np[d]])));
+      const Df mm = half(df_add_pos(df_of(E.mudf[nm[d]]), muc));
+      const Df lp = half(df_add_pos(lac, df_of(E.lamdf[np[d]])));
+      const Df lm = half(df_add_pos(df_of(E.lamdf[nm[d]]), lac));
       Gp[d] = df_mul(mp, ih2[d]);
       Gm[d] = df_mul(mm, ih2[d]);
-      Fp[d] = df_mul(df_add(lp, twice(mp)), ih2[d]);
-      Fm[d] = df_mul(df_add(lm, twice(mm)), ih2[d]);
+      Fp[d] = df_mul(df_add_pos(lp, twice(mp)), ih2[d]);
+      Fm[d] = df_mul(df_add_pos(lm, twice(mm)), ih2[d]);
       reinterpret_cast<float2*>(E.F[d])[c] = make_float2(Fp[d].hi, Fp[d].lo);
       reinterpret_cast<float2*>(E.G[d])[c] = make_float2(Gp[d].hi, Gp[d].lo);
     }
@@ -118,17 +122,16 @@ __global__ void __launch_bounds__(NT) k_elas_coef_df(Geo G, DevParams P, Elas E,
       Df s = et;
 #pragma unroll
       for (int d = 0; d < 3; ++d)
-        s = df_add(s, d == a ? df_add(Fp[d], Fm[d]) : df_add(Gp[d], Gm[d]));
+        s = df_add_pos(s, d == a ? df_add_pos(Fp[d], Fm[d]) : df_add_pos(Gp[d], Gm[d]));
       reinterpret_cast<float2*>(E.dsum[a])[c] = make_float2(s.hi, s.lo);
       if (E.jacobi) I.dinv[a][c] = 1.0f / __fadd_rn(s.hi, s.lo);
     }
-    if (force) {
-      const double sc = p[c] + n[c];
-      const double th = P.zeta * tanh(sc);
+    if (force) {   // the FP64 path's order: zeta tanh(s), then th ((s+ - s-) / (2 h))
+      const Df th = df_mul(zeta, df_tanh(df_of(sdf[c])));
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const double bv = th * (((p[np[d]] + n[np[d]]) - (p[nm[d]] + n[nm[d]])) * G.inv2h[d]);
-        reinterpret_cast<float2*>(E.b[d])[c] = df_pack(bv);
+        const Df bv = df_mul(th, df_mul(df_sub(df_of(sdf[np[d]]), df_of(sdf[nm[d]])), i2h[d]));
+        reinterpret_cast<float2*>(E.b[d])[c] = make_float2(bv.hi, bv.lo);
       }
     }
   }
@@ -293,10 +296,9 @@ __global__ void __launch_bounds__(NT) k_elas_finish(Geo G, Elas E, double inv_dt
 }  // namespace
 
 cudaError_t launch_elas_coef_df(const Geo& G, const DevParams& P, const Elas& E,
-                                const Elas32& I, const double* p, const double* n, bool force,
-                                cudaStream_t st) {
+                                const Elas32& I, const float2* sdf, bool force, cudaStream_t st) {
   TG_TIMED(K_ELAS_COEF_DF, st,
-           k_elas_coef_df<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, E, I, p, n, force ? 1 : 0));
+           k_elas_coef_df<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, E, I, sdf, force ? 1 : 0));
   return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "tg.h"
+#include "tg_fpconv.cuh"
 
 namespace tg {
 
@@ -31,7 +32,7 @@ enum KernelId : int {
   K_ELAS32_UPDATE_SPEC, K_SPEC_UPDATE_XFWD, K_ELAS_IR_CORRECT, K_ELAS_IR_FINISH,
   K_ELAS_INIT, K_ELAS_INIT_SPEC, K_ELAS_MATVEC, K_ELAS_UPDATE, K_ELAS_PUPDATE, K_ELAS_UPDATE_SPEC,
   K_ELAS_PUPDATE_SPEC, K_ELAS_FINISH, K_OX_PREP, K_OX_INIT, K_OX_MATVEC, K_OX_UPDATE,
-  K_OX_PUPDATE, K_OX_FINISH,
+  K_OX_PUPDATE, K_OX_FINISH, K_SL32_PACK, K_LAME_DF,
   K_COUNT
 };
 
@@ -305,10 +306,13 @@ struct Elas32 {    // inner FP32 elasticity solve of the mixed precision
   unsigned int* counter;
 };
 
-struct Sl32 {      // FP32 transport: inputs as FP32 copies, outputs to the FP64 state
-  const float* v[3];
-  const float* div;
-  const float* q[6];
+// FP32 transport.  Its inputs are FP32 copies interleaved per voxel, so that one 16-byte load
+// brings four of the values a stencil tap needs: v4 = (v_x, v_y, v_z, 0),
+// qa = (p, i, n, div_h v), qb = (g, w, f, 0).  The outputs go to the FP64 state.
+struct Sl32 {
+  float4* v4;
+  float4* qa;
+  float4* qb;
   double* out[6];
 };
 
@@ -468,6 +472,13 @@ cudaError_t launch_react(const Geo&, const DevParams&, double dt, const double* 
 cudaError_t launch_lame(const Geo&, const DevParams&, const double* p, const double* i,
                         const double* n, const double* g, const double* w, const double* f,
                         const double* bg, double* mu, double* lam, double* eta, cudaStream_t st);
+// the same in double-FP32 for the double-FP32 residual: FP64 mu, lambda, eta, their FP32
+// copies, the (hi, lo) pairs of mu and lambda, and the pairs of s = p + n for the force
+cudaError_t launch_lame_df(const Geo&, const DevParams&, const double* p, const double* i,
+                           const double* n, const double* g, const double* w, const double* f,
+                           const double* bg, double* mu, double* lam, double* eta, float* mu32,
+                           float* lam32, float* eta32, float2* mudf, float2* lamdf, float2* sdf,
+                           cudaStream_t st);
 
 struct Elas {
   const double* mu;
@@ -499,52 +510,13 @@ struct Elas {
   unsigned int* counter;
 };
 
-// A double-FP32 ("double-float") number hi + lo, |lo| <= ulp(hi) / 2: about 48 bits of
-// significand from FP32 arithmetic, which GB300 executes 64 times faster than FP64.  The
-// operations are the classical error-free transformations: Knuth's two-sum for a + b, and
-// the fused multiply-add remainder a * b - fl(a * b) for products; __fadd_rn / __fmul_rn keep
-// the compiler from contracting them.
-struct Df {
-  float hi, lo;
-};
-__device__ __forceinline__ Df df_split(double x) {
-  const float hi = __double2float_rn(x);
-  return {hi, __double2float_rn(x - (double)hi)};
-}
-inline Df df_split_host(double x) {   // the same split on the host (round to nearest)
-  const float hi = (float)x;
-  return {hi, (float)(x - (double)hi)};
-}
+// Double-FP32 numbers (Df) and the FP64 <-> FP32 conversions on the integer pipes come from
+// tg_fpconv.cuh; the storage forms here.
 __device__ __forceinline__ Df df_of(float2 v) { return {v.x, v.y}; }
 __device__ __forceinline__ float2 df_pack(double x) {
   const Df d = df_split(x);
   return make_float2(d.hi, d.lo);
 }
-__device__ __forceinline__ Df df_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ Df df_fast_two_sum(float a, float b) {   // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ Df df_add(Df x, Df y) {
-  Df s = df_two_sum(x.hi, y.hi);
-  const Df t = df_two_sum(x.lo, y.lo);
-  s = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
-}
-__device__ __forceinline__ Df df_sub(Df x, Df y) { return df_add(x, Df{-y.hi, -y.lo}); }
-__device__ __forceinline__ Df df_mul(Df x, Df y) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = __fmaf_rn(x.hi, y.hi, -p);
-  e = __fmaf_rn(x.hi, y.lo, e);
-  e = __fmaf_rn(x.lo, y.hi, e);
-  return df_fast_two_sum(p, e);
-}
-__device__ __forceinline__ double df_value(Df x) { return (double)x.hi + (double)x.lo; }
 
 // S0 of the mixed precision with double-FP32 residuals: node K pairs (Kn, scratch), rho, the
 // face pairs, the FP32 faces and the FP32 inverse CN diagonal (no FP64 faces)
@@ -586,9 +558,10 @@ __device__ __forceinline__ double elas_row64(const Geo& G, const Nbr& nb, long l
 
 cudaError_t launch_elas_coef(const Geo&, const DevParams&, const Elas&, const double* p,
                              const double* n, bool force, cudaStream_t st);
-// the same as (hi, lo) pairs from the node pairs E.mudf, E.lamdf (E.df); I.dinv if E.jacobi
+// the same as (hi, lo) pairs from the node pairs E.mudf, E.lamdf (E.df) and the pairs sdf of
+// s = p + n, all written by launch_lame_df; I.dinv if E.jacobi
 cudaError_t launch_elas_coef_df(const Geo&, const DevParams&, const Elas&, const Elas32& I,
-                                const double* p, const double* n, bool force, cudaStream_t st);
+                                const float2* sdf, bool force, cudaStream_t st);
 cudaError_t launch_elas_init(const Geo&, const Elas&, bool rhs_is_minus_b, cudaStream_t st);
 cudaError_t launch_elas_matvec(const Geo&, const Elas&, cudaStream_t st);
 cudaError_t launch_elas_update(const Geo&, const Elas&, cudaStream_t st);   // update + p-update
@@ -614,6 +587,10 @@ cudaError_t launch_elas_extrapolate(const Geo&, const Elas&, double dt, bool qua
                                     cudaStream_t st);
 cudaError_t launch_elas_ir_finish(const Geo&, const Elas&, double inv_dt, bool zero_rhs,
                                   cudaStream_t st);
+// S1 of the mixed precision: the interleaved FP32 inputs (div_h v formed in FP64 and rounded),
+// then the transport.  Both need nvox < 2^31 (32-bit voxel offsets).
+cudaError_t launch_sl32_pack(const Geo&, const double* const v[3], const double* const q[6],
+                             const Sl32&, cudaStream_t st);
 cudaError_t launch_sl32(const Geo&, double dt, const Sl32&, cudaStream_t st);
 
 // spectral preconditioner: one-time tables, per-solve means, z = A0^{-1} r with <r, z>

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(NT) k_to_f32(long long n, F32Copy c) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
 #pragma unroll 1
-    for (int a = 0; a < c.count; ++a) c.dst[a][e] = (float)c.src[a][e];
+    for (int a = 0; a < c.count; ++a) c.dst[a][e] = f32_of(c.src[a][e]);
   }
 }
 
@@ -35,19 +35,19 @@ __global__ void __launch_bounds__(NT) k_elas32_coef(long long n, Elas E, Elas32 
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
     if (parts & ELAS32_NODES) {
-      const double mu = E.mu[e], lam = E.lam[e];
-      I.mu[e] = (float)mu;
-      I.lam[e] = (float)lam;
-      I.eta[e] = (float)E.eta[e];
+      const Df mu = df_split(E.mu[e]), lam = df_split(E.lam[e]);   // hi = fl32(value)
+      I.mu[e] = mu.hi;
+      I.lam[e] = lam.hi;
+      I.eta[e] = f32_of(E.eta[e]);
       if (E.df) {
-        E.mudf[e] = df_pack(mu);
-        E.lamdf[e] = df_pack(lam);
+        E.mudf[e] = make_float2(mu.hi, mu.lo);
+        E.lamdf[e] = make_float2(lam.hi, lam.lo);
       }
     }
     if ((parts & ELAS32_DINV) && E.jacobi) {
-      I.dinv[0][e] = (float)E.dinv[0][e];
-      I.dinv[1][e] = (float)E.dinv[1][e];
-      I.dinv[2][e] = (float)E.dinv[2][e];
+      I.dinv[0][e] = f32_of(E.dinv[0][e]);
+      I.dinv[1][e] = f32_of(E.dinv[1][e]);
+      I.dinv[2][e] = f32_of(E.dinv[2][e]);
     }
     if ((parts & ELAS32_U) && E.df) {
 #pragma unroll
@@ -174,6 +174,20 @@ __global__ void __launch_bounds__(NT) k_elas_ir_correct(long long n, Elas E, Ela
 __global__ void __launch_bounds__(NT) k_elas_extrapolate(long long n, Elas E, double dt,
                                                          int quadratic) {
   const long long stride = (long long)gridDim.x * blockDim.x;
+  if (E.df) {   // mixed precision: s in double-FP32, two FP64 additions per component
+    const Df dtd = df_split(dt);
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const Df v = df_split(E.v[a][c]);
+        const Df w = quadratic ? df_add(v, df_sub(v, df_split(E.vp[a][c]))) : v;
+        const double s = df_value(df_mul(dtd, w));
+        E.u[a][c] = E.u[a][c] + s;
+        E.du[a][c] = s;
+      }
+    }
+    return;
+  }
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -208,8 +222,14 @@ __global__ void __launch_bounds__(NT) k_elas_ir_finish(long long n, Elas E, doub
 
 // ------------------------------------------------------------------------------ FP32 transport
 
+struct Species6 {   // p, i, n, g, w, f
+  const double* a[6];
+};
+
+// Taps of one tricubic interpolation: 32-bit voxel offsets of the four x, y, z nodes and
+// their Lagrange weights.
 struct Cubic32 {
-  long long xo[4], yo[4], zo[4];
+  int xo[4], yo[4], zo[4];
   float wx[4], wy[4], wz[4];
 };
 
@@ -221,12 +241,16 @@ __device__ __forceinline__ void lagrange4f(float t, float w[4]) {
   w[3] = tp1 * t * tm1 * (1.0f / 6.0f);
 }
 
-// node j plus sub-cell offset d (FP32): base node j + floor(d), fraction d - floor(d)
-__device__ __forceinline__ void axis32(int j, float d, int n, long long stride, long long o[4],
-                                       float w[4]) {
+// node j plus sub-cell offset d (FP32): base node j + floor(d), fraction d - floor(d); the
+// periodic wrap takes a division only when the first node leaves [0, n)
+__device__ __forceinline__ void axis32(int j, float d, int n, int stride, int o[4], float w[4]) {
   const float fl = floorf(d);
-  long long m = ((long long)j + (long long)fl - 1) % n;
-  if (m < 0) m += n;
+  int m = (int)((unsigned)j + (unsigned)(int)fl - 1u);
+  if ((unsigned)m >= (unsigned)n) {
+    long long mm = ((long long)j + (long long)fl - 1) % n;
+    if (mm < 0) mm += n;
+    m = (int)mm;
+  }
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     o[a] = m * stride;
@@ -235,50 +259,113 @@ __device__ __forceinline__ void axis32(int j, float d, int n, long long stride, 
   lagrange4f(d - fl, w);
 }
 
-__device__ __forceinline__ float eval32(const Cubic32& T, const float* __restrict__ q) {
-  float s = 0.0f;
+// the interpolant of the four interleaved fields of q: x first, then y, then z
+__device__ __forceinline__ float4 eval32x4(const Cubic32& T, const float4* __restrict__ q) {
+  float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    float sy = 0.0f;
+    float4 sy = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const float* row = q + T.zo[c] + T.yo[b];
-      const float sx = T.wx[0] * __ldg(row + T.xo[0]) + T.wx[1] * __ldg(row + T.xo[1]) +
-                       T.wx[2] * __ldg(row + T.xo[2]) + T.wx[3] * __ldg(row + T.xo[3]);
-      sy += T.wy[b] * sx;
+      const float4* row = q + (T.zo[c] + T.yo[b]);
+      const float4 a0 = __ldg(row + T.xo[0]), a1 = __ldg(row + T.xo[1]);
+      const float4 a2 = __ldg(row + T.xo[2]), a3 = __ldg(row + T.xo[3]);
+      sy.x += T.wy[b] * (T.wx[0] * a0.x + T.wx[1] * a1.x + T.wx[2] * a2.x + T.wx[3] * a3.x);
+      sy.y += T.wy[b] * (T.wx[0] * a0.y + T.wx[1] * a1.y + T.wx[2] * a2.y + T.wx[3] * a3.y);
+      sy.z += T.wy[b] * (T.wx[0] * a0.z + T.wx[1] * a1.z + T.wx[2] * a2.z + T.wx[3] * a3.z);
+      sy.w += T.wy[b] * (T.wx[0] * a0.w + T.wx[1] * a1.w + T.wx[2] * a2.w + T.wx[3] * a3.w);
     }
-    s += T.wz[c] * sy;
+    s.x += T.wz[c] * sy.x;
+    s.y += T.wz[c] * sy.y;
+    s.z += T.wz[c] * sy.z;
+    s.w += T.wz[c] * sy.w;
   }
   return s;
 }
 
-__global__ void __launch_bounds__(NT) k_sl32(Geo G, float dt, float3 dt_h, Sl32 S) {
+// the velocity interpolant: the first three components only
+__device__ __forceinline__ float3 eval32x3(const Cubic32& T, const float4* __restrict__ q) {
+  float3 s = make_float3(0.0f, 0.0f, 0.0f);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float3 sy = make_float3(0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float4* row = q + (T.zo[c] + T.yo[b]);
+      const float4 a0 = __ldg(row + T.xo[0]), a1 = __ldg(row + T.xo[1]);
+      const float4 a2 = __ldg(row + T.xo[2]), a3 = __ldg(row + T.xo[3]);
+      sy.x += T.wy[b] * (T.wx[0] * a0.x + T.wx[1] * a1.x + T.wx[2] * a2.x + T.wx[3] * a3.x);
+      sy.y += T.wy[b] * (T.wx[0] * a0.y + T.wx[1] * a1.y + T.wx[2] * a2.y + T.wx[3] * a3.y);
+      sy.z += T.wy[b] * (T.wx[0] * a0.z + T.wx[1] * a1.z + T.wx[2] * a2.z + T.wx[3] * a3.z);
+    }
+    s.x += T.wz[c] * sy.x;
+    s.y += T.wz[c] * sy.y;
+    s.z += T.wz[c] * sy.z;
+  }
+  return s;
+}
+
+// The interleaved FP32 inputs of S1: the velocity, div_h v by central differences and the six
+// transported species.  Each difference v(+) - v(-) is taken from the split FP64 values,
+// (hi+ - hi-) + (lo+ - lo-) in FP32, so that it keeps FP32's relative precision where the
+// neighbours nearly cancel, without FP64 arithmetic.
+__global__ void __launch_bounds__(NT) k_sl32_pack(Geo G, const double* __restrict__ vx,
+                                                  const double* __restrict__ vy,
+                                                  const double* __restrict__ vz, Species6 q, Sl32 S) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= G.nx || j >= G.ny) return;
+  const float i2h[3] = {f32_of(G.inv2h[0]), f32_of(G.inv2h[1]), f32_of(G.inv2h[2])};
+  auto diff = [](double a, double b) {
+    const Df x = df_split(a), y = df_split(b);
+    return (x.hi - y.hi) + (x.lo - y.lo);
+  };
   const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
   for (int k = k0; k < k1; ++k) {
-    const long long c = ((long long)k * G.ny + j) * G.nx + i;
-    const float v0x = S.v[0][c], v0y = S.v[1][c], v0z = S.v[2][c];
+    const Nbr nb = make_nbr(G, i, j, k);
+    const long long c = nb.at(0, 0, 0);
+    const float div = diff(vx[nb.at(1, 0, 0)], vx[nb.at(-1, 0, 0)]) * i2h[0] +
+                      diff(vy[nb.at(0, 1, 0)], vy[nb.at(0, -1, 0)]) * i2h[1] +
+                      diff(vz[nb.at(0, 0, 1)], vz[nb.at(0, 0, -1)]) * i2h[2];
+    S.v4[c] = make_float4(f32_of(vx[c]), f32_of(vy[c]), f32_of(vz[c]), 0.0f);
+    S.qa[c] = make_float4(f32_of(q.a[0][c]), f32_of(q.a[1][c]), f32_of(q.a[2][c]), div);
+    S.qb[c] = make_float4(f32_of(q.a[3][c]), f32_of(q.a[4][c]), f32_of(q.a[5][c]), 0.0f);
+  }
+}
+
+// Semi-Lagrangian step S1 in FP32 arithmetic (FP64 state): the departure point by the
+// two-stage rule of the FP64 path, tricubic interpolation of the species and div_h v there,
+// and the compression source -q div v by Heun's rule along the characteristic.
+__global__ void __launch_bounds__(NT, 3) k_sl32(Geo G, float dt, float3 dt_h, Sl32 S) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= G.nx || j >= G.ny) return;
+  const int nxy = G.nx * G.ny;
+  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  for (int k = k0; k < k1; ++k) {
+    const int c = (k * G.ny + j) * G.nx + i;
+    const float4 v0 = __ldg(S.v4 + c);
     Cubic32 T;
-    axis32(i, -v0x * dt_h.x, G.nx, 1, T.xo, T.wx);
-    axis32(j, -v0y * dt_h.y, G.ny, G.nx, T.yo, T.wy);
-    axis32(k, -v0z * dt_h.z, G.nz, G.nxy, T.zo, T.wz);
-    const float vsx = eval32(T, S.v[0]), vsy = eval32(T, S.v[1]), vsz = eval32(T, S.v[2]);
-    axis32(i, -0.5f * (v0x + vsx) * dt_h.x, G.nx, 1, T.xo, T.wx);
-    axis32(j, -0.5f * (v0y + vsy) * dt_h.y, G.ny, G.nx, T.yo, T.wy);
-    axis32(k, -0.5f * (v0z + vsz) * dt_h.z, G.nz, G.nxy, T.zo, T.wz);
-    const float dX = eval32(T, S.div);
-    const float dx = S.div[c];
+    axis32(i, -v0.x * dt_h.x, G.nx, 1, T.xo, T.wx);
+    axis32(j, -v0.y * dt_h.y, G.ny, G.nx, T.yo, T.wy);
+    axis32(k, -v0.z * dt_h.z, G.nz, nxy, T.zo, T.wz);
+    const float3 vs = eval32x3(T, S.v4);
+    axis32(i, -0.5f * (v0.x + vs.x) * dt_h.x, G.nx, 1, T.xo, T.wx);
+    axis32(j, -0.5f * (v0.y + vs.y) * dt_h.y, G.ny, G.nx, T.yo, T.wy);
+    axis32(k, -0.5f * (v0.z + vs.z) * dt_h.z, G.nz, nxy, T.zo, T.wz);
+    const float4 a = eval32x4(T, S.qa);   // p, i, n, div v at the departure point
+    const float4 b = eval32x4(T, S.qb);   // g, w, f
+    const float dX = a.w;
+    const float dx = __ldg(S.qa + c).w;
+    const float qX[5] = {a.x, a.y, a.z, b.x, b.y};
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
-      const float qX = eval32(T, S.q[s]);
-      const float gX = -qX * dX;
-      const float qs = qX + dt * gX;
+      const float gX = -qX[s] * dX;
+      const float qs = qX[s] + dt * gX;
       const float gs = -qs * dx;
-      S.out[s][c] = (double)(qX + 0.5f * dt * (gX + gs));
+      S.out[s][c] = f64_of(qX[s] + 0.5f * dt * (gX + gs));
     }
-    S.out[5][c] = (double)eval32(T, S.q[5]);
+    S.out[5][c] = f64_of(b.z);
   }
 }
 
@@ -382,7 +469,18 @@ cudaError_t launch_elas_ir_finish(const Geo& G, const Elas& E, double inv_dt, bo
   return cudaGetLastError();
 }
 
+cudaError_t launch_sl32_pack(const Geo& G, const double* const v[3], const double* const q[6],
+                             const Sl32& S, cudaStream_t st) {
+  if (G.nvox >= (1LL << 31)) return cudaErrorInvalidValue;
+  Species6 qs;
+  for (int s = 0; s < 6; ++s) qs.a[s] = q[s];
+  TG_TIMED(K_SL32_PACK, st,
+           k_sl32_pack<<<G.grid, dim3(BX, BY), 0, st>>>(G, v[0], v[1], v[2], qs, S));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sl32(const Geo& G, double dt, const Sl32& S, cudaStream_t st) {
+  if (G.nvox >= (1LL << 31)) return cudaErrorInvalidValue;
   const float3 dth = make_float3((float)(dt / G.h[0]), (float)(dt / G.h[1]), (float)(dt / G.h[2]));
   TG_TIMED(K_SL32, st, k_sl32<<<G.grid, dim3(BX, BY), 0, st>>>(G, (float)dt, dth, S));
   return cudaGetLastError();

@@ -497,7 +497,7 @@ __device__ __forceinline__ void elas_ir_correct_range(const Elas& E, const Elas3
   for (long long c = c0; c < c1; c += cs) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double e = (double)I.e[a][c] * inv_scale;
+      const double e = f64_of_scaled(I.e[a][c], inv_scale);   // exact; no FP64 operation
       const double un = E.u[a][c] + e;
       E.u[a][c] = un;
       E.du[a][c] += e;
