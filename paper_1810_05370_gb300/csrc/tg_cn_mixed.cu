@@ -93,18 +93,22 @@ __global__ void __launch_bounds__(NT) k_cn_ir_residual_df(Geo G, Cn3 C, Cn32 I, 
         if (!((mask >> r) & 1)) continue;
         const float2* x = C.xdf[r];
         const Df xc = df_of(x[c]);
-        Df s = df_mul(f[0], df_sub(df_of(x[nbr[0]]), xc));
+        // s = sum over faces of a (x_n - x_c), one compensated sum of double-FP32 products
+        CSum acc = {0.0f, 0.0f};
 #pragma unroll
-        for (int q = 1; q < 6; ++q) s = df_add(s, df_mul(f[q], df_sub(df_of(x[nbr[q]]), xc)));
+        for (int q = 0; q < 6; ++q) cs_fma(acc, f[q], df_sub_near(df_of(x[nbr[q]]), xc));
         float2* rhs2 = reinterpret_cast<float2*>(C.p[r]);
-        Df rhs;
+        Df rhs, res;
         if (init) {
+          const Df s = cs_value(acc);
           rhs = df_add(xc, s);
           rhs2[c] = make_float2(rhs.hi, rhs.lo);
+          res = df_add(df_sub(rhs, xc), s);
         } else {
           rhs = df_of(rhs2[c]);
+          cs_add(acc, df_sub(rhs, xc));   // res = (rhs - x) + s
+          res = cs_value(acc);
         }
-        const Df res = df_add(df_sub(rhs, xc), s);
         const float r32 = __fadd_rn(res.hi, res.lo);
         I.r[r][c] = r32;
         I.e[r][c] = 0.0f;

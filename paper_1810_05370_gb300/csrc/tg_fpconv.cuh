@@ -251,6 +251,35 @@ TG_HD Df df_mul(Df x, Df y) {
   e = fpc::fma(x.lo, y.hi, e);
   return df_fast_two_sum(p, e);
 }
+// A compensated sum s + c.  Each addend's leading part enters s through an error-free
+// two-sum; that error, the addend's tail and the products' rounding errors (fused
+// multiply-add remainders) collect in the FP32 compensation c.  This is the summation and dot
+// product of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26,
+// 2005) with double-FP32 operands: about 11 FP32 operations per product term against 26 for a
+// double-FP32 product and addition, with an error of order 2^-48 of the terms' magnitudes.
+struct CSum {
+  float s, c;
+};
+TG_HD void cs_add(CSum& a, Df t) {   // a += t
+  const Df q = df_two_sum(a.s, t.hi);
+  a.s = q.hi;
+  a.c = fpc::add(a.c, fpc::add(q.lo, t.lo));
+}
+TG_HD void cs_fma(CSum& a, Df x, Df y) {   // a += x y
+  const float p = fpc::mul(x.hi, y.hi);
+  const float e = fpc::fma(x.hi, y.hi, -p);
+  const Df q = df_two_sum(a.s, p);
+  a.s = q.hi;
+  a.c = fpc::fma(x.hi, y.lo, fpc::fma(x.lo, y.hi, fpc::add(a.c, fpc::add(q.lo, e))));
+}
+TG_HD Df cs_value(CSum a) { return df_two_sum(a.s, a.c); }
+// x - y for values whose difference matters only to 2^-48 of their own size (neighbouring
+// nodes of a smooth field): one two-sum of the leading parts, the tails' difference added
+TG_HD Df df_sub_near(Df x, Df y) {
+  const Df q = df_two_sum(x.hi, -y.hi);
+  return df_two_sum(q.hi, fpc::add(q.lo, fpc::sub(x.lo, y.lo)));
+}
+
 // x / y: the FP32 quotient, then one correction from the double-FP32 remainder x - q y
 TG_HD Df df_div(Df x, Df y) {
   const float q = fpc::div(x.hi, y.hi);

@@ -134,12 +134,12 @@ __global__ void __launch_bounds__(NT) k_elas32_update_spec(long long n, Elas32 I
 
 // FP64 residual of the current iterate, outer stopping test and start of the inner solve
 template <bool DF>
-__global__ void __launch_bounds__(NT) k_elas_ir_residual(Geo G, Elas E, Elas32 I, CgScal* Sout,
-                                                         int minus_b, double tau_min,
-                                                         int max_sweeps) {
+__global__ void __launch_bounds__(NT, DF ? 3 : 1) k_elas_ir_residual(Geo G, Elas E, Elas32 I, CgScal* Sout,
+                                                            int minus_b, double tau_min,
+                                                            int max_sweeps, ScDf scd) {
   double acc[3] = {0.0, 0.0, 0.0};
   if (DF)
-    elas_ir_residual_tile_df(G, E, I, minus_b, blockIdx.x, blockIdx.y, blockIdx.z, acc);
+    elas_ir_residual_tile_df(G, E, I, minus_b, blockIdx.x, blockIdx.y, blockIdx.z, scd, acc);
   else
     elas_ir_residual_tile(G, E, I, minus_b, blockIdx.x, blockIdx.y, blockIdx.z, acc);
   double out[3];
@@ -403,11 +403,13 @@ cudaError_t launch_elas_ir_residual(const Geo& G, const Elas& E, const Elas32& I
   if (E.df)
     TG_TIMED(K_ELAS_IR_RESIDUAL_DF, st,
              k_elas_ir_residual<true><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, I, Sout, minus_b ? 1 : 0,
-                                                                       tau_min, 1 << 30));
+                                                                       tau_min, 1 << 30,
+                                                                       sc_df_host(G)));
   else
     TG_TIMED(K_ELAS_IR_RESIDUAL, st,
              k_elas_ir_residual<false><<<G.grid, dim3(BX, BY), 0, st>>>(G, E, I, Sout, minus_b ? 1 : 0,
-                                                                        tau_min, 1 << 30));
+                                                                        tau_min, 1 << 30,
+                                                                        ScDf{}));
   return cudaGetLastError();
 }
 

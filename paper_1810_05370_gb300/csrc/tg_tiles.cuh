@@ -368,54 +368,70 @@ __device__ __forceinline__ void elas_ir_residual_tile(const Geo& G, const Elas& 
 }
 
 // The same residual in double-FP32 arithmetic (Elas::df): the operator's faces, diagonal, u,
-// mu, lambda and b are (hi, lo) FP32 pairs and every product and sum is an error-free
-// double-FP32 operation, so the FP64 units only convert the per-thread sums.  Sums of squares
-// are formed in FP32 per thread (a few dozen terms of one sign) and in FP64 across threads.
+// mu, lambda and b are (hi, lo) FP32 pairs, and each component's residual b - A u is one
+// compensated sum (CSum) started at b, into which every product of the operator enters with
+// its rounding error, so the FP64 units only convert the per-thread sums.  The differences of
+// neighbouring u in the mixed derivatives are double-FP32 differences.  Sums of squares are
+// formed in FP32 per thread (a few dozen terms of one sign) and in FP64 across threads.
+__device__ __forceinline__ Df ndf(float2 v) { return Df{-v.x, -v.y}; }
+
 template <int A, int D>
-__device__ __forceinline__ Df elas_mixed_df(const Nbr& nb, const float2* __restrict__ xd,
+__device__ __forceinline__ Df elas_mixed_cs(const Nbr& nb, const float2* __restrict__ xd,
                                             const float2* __restrict__ mu,
                                             const float2* __restrict__ lam) {
   const Df epp = df_of(xd[at2<A, D>(nb, +1, +1)]);
   const Df epm = df_of(xd[at2<A, D>(nb, -1, +1)]);
   const Df emp = df_of(xd[at2<A, D>(nb, +1, -1)]);
   const Df emm = df_of(xd[at2<A, D>(nb, -1, -1)]);
-  const Df t1 = df_mul(df_of(mu[at1<D>(nb, +1)]), df_sub(epp, epm));
-  const Df t2 = df_mul(df_of(mu[at1<D>(nb, -1)]), df_sub(emp, emm));
-  const Df t3 = df_mul(df_of(lam[at1<A>(nb, +1)]), df_sub(epp, emp));
-  const Df t4 = df_mul(df_of(lam[at1<A>(nb, -1)]), df_sub(epm, emm));
-  return df_sub(df_add(df_sub(t1, t2), t3), t4);
+  CSum m = {0.0f, 0.0f};
+  cs_fma(m, df_of(mu[at1<D>(nb, +1)]), df_sub_near(epp, epm));
+  cs_fma(m, ndf(mu[at1<D>(nb, -1)]), df_sub_near(emp, emm));
+  cs_fma(m, df_of(lam[at1<A>(nb, +1)]), df_sub_near(epp, emp));
+  cs_fma(m, ndf(lam[at1<A>(nb, -1)]), df_sub_near(epm, emm));
+  return cs_value(m);
 }
 
+// component A of rhs - (eta I - L_h) u at node c
 template <int A>
-__device__ __forceinline__ Df elas_row_df(const Nbr& nb, long long c, const Elas& E,
-                                          const Df (&sc)[3][3]) {
+__device__ __forceinline__ Df elas_res_row_cs(const Nbr& nb, long long c, const Elas& E,
+                                              const Df (&sc)[3][3], Df rhs) {
   constexpr int D1 = (A + 1) % 3, D2 = (A + 2) % 3;
   const float2* __restrict__ xa = E.udf[A];
   const float2* __restrict__ CA = reinterpret_cast<const float2*>(E.F[A]);
   const float2* __restrict__ C1 = reinterpret_cast<const float2*>(E.G[D1]);
   const float2* __restrict__ C2 = reinterpret_cast<const float2*>(E.G[D2]);
   const float2* __restrict__ DS = reinterpret_cast<const float2*>(E.dsum[A]);
-  Df v = df_mul(df_of(DS[c]), df_of(xa[c]));
-  v = df_sub(v, df_mul(df_of(CA[c]), df_of(xa[at1<A>(nb, 1)])));
-  v = df_sub(v, df_mul(df_of(CA[at1<A>(nb, -1)]), df_of(xa[at1<A>(nb, -1)])));
-  v = df_sub(v, df_mul(df_of(C1[c]), df_of(xa[at1<D1>(nb, 1)])));
-  v = df_sub(v, df_mul(df_of(C1[at1<D1>(nb, -1)]), df_of(xa[at1<D1>(nb, -1)])));
-  v = df_sub(v, df_mul(df_of(C2[c]), df_of(xa[at1<D2>(nb, 1)])));
-  v = df_sub(v, df_mul(df_of(C2[at1<D2>(nb, -1)]), df_of(xa[at1<D2>(nb, -1)])));
-  v = df_sub(v, df_mul(sc[A][D1], elas_mixed_df<A, D1>(nb, E.udf[D1], E.mudf, E.lamdf)));
-  v = df_sub(v, df_mul(sc[A][D2], elas_mixed_df<A, D2>(nb, E.udf[D2], E.mudf, E.lamdf)));
-  return v;
+  CSum v = {rhs.hi, rhs.lo};
+  cs_fma(v, ndf(DS[c]), df_of(xa[c]));
+  cs_fma(v, df_of(CA[c]), df_of(xa[at1<A>(nb, 1)]));
+  cs_fma(v, df_of(CA[at1<A>(nb, -1)]), df_of(xa[at1<A>(nb, -1)]));
+  cs_fma(v, df_of(C1[c]), df_of(xa[at1<D1>(nb, 1)]));
+  cs_fma(v, df_of(C1[at1<D1>(nb, -1)]), df_of(xa[at1<D1>(nb, -1)]));
+  cs_fma(v, df_of(C2[c]), df_of(xa[at1<D2>(nb, 1)]));
+  cs_fma(v, df_of(C2[at1<D2>(nb, -1)]), df_of(xa[at1<D2>(nb, -1)]));
+  cs_fma(v, sc[A][D1], elas_mixed_cs<A, D1>(nb, E.udf[D1], E.mudf, E.lamdf));
+  cs_fma(v, sc[A][D2], elas_mixed_cs<A, D2>(nb, E.udf[D2], E.mudf, E.lamdf));
+  return cs_value(v);
+}
+
+// The mixed-derivative weights 1 / (4 h_a h_d) as (hi, lo) pairs, passed as a kernel argument
+// (read from the constant bank where used, so they take no registers).
+struct ScDf {
+  Df v[3][3];
+};
+inline ScDf sc_df_host(const Geo& G) {
+  ScDf s;
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) s.v[a][d] = df_split_host(G.s_cross[a][d]);
+  return s;
 }
 
 // b holds (hi, lo) pairs as well: E.b[a] reinterpreted
 __device__ __forceinline__ void elas_ir_residual_tile_df(const Geo& G, const Elas& E,
                                                          const Elas32& I, int minus_b, int bx,
-                                                         int by, int bz, double (&acc)[3]) {
-  Df sc[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) sc[a][d] = df_split(G.s_cross[a][d]);
+                                                         int by, int bz, const ScDf& scd,
+                                                         double (&acc)[3]) {
+  const Df(&sc)[3][3] = scd.v;
   float sbb = 0.0f, srr = 0.0f, srz = 0.0f;
   const int i = bx * BX + threadIdx.x;
   const int j = by * BY + threadIdx.y;
@@ -424,20 +440,22 @@ __device__ __forceinline__ void elas_ir_residual_tile_df(const Geo& G, const Ela
     for (int k = k0; k < k1; ++k) {
       const Nbr nb = make_nbr(G, i, j, k);
       const long long c = nb.at(0, 0, 0);
-      Df Au[3];
-      Au[0] = elas_row_df<0>(nb, c, E, sc);
-      Au[1] = elas_row_df<1>(nb, c, E, sc);
-      Au[2] = elas_row_df<2>(nb, c, E, sc);
+      Df rhs[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const float2 bv = reinterpret_cast<const float2*>(E.b[a])[c];
-        const Df rhs = minus_b ? Df{-bv.x, -bv.y} : Df{bv.x, bv.y};
-        const Df res = df_sub(rhs, Au[a]);
-        const float r32 = __fadd_rn(res.hi, res.lo);
+        rhs[a] = minus_b ? Df{-bv.x, -bv.y} : Df{bv.x, bv.y};
+      }
+      const Df res[3] = {elas_res_row_cs<0>(nb, c, E, sc, rhs[0]),
+                         elas_res_row_cs<1>(nb, c, E, sc, rhs[1]),
+                         elas_res_row_cs<2>(nb, c, E, sc, rhs[2])};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float r32 = __fadd_rn(res[a].hi, res[a].lo);
         const float z32 = E.jacobi ? I.dinv[a][c] * r32 : 0.0f;
         I.r[a][c] = r32;
         I.e[a][c] = 0.0f;
-        sbb += rhs.hi * rhs.hi;
+        sbb += rhs[a].hi * rhs[a].hi;
         srr += r32 * r32;
         srz += r32 * z32;
       }

@@ -46,4 +46,17 @@ void tgc_df_div_mul(const double* x, const double* y, double* quo, double* prod,
   }
 }
 
+// sum_q x[q] y[q] over rows of m terms as one compensated sum started at b (a residual
+// b - sum of products when the products are passed negated), returned as hi + lo in FP64
+void tgc_cs_dot(const double* b, const double* x, const double* y, double* out, long rows, long m) {
+  for (long r = 0; r < rows; ++r) {
+    const tg::Df b0 = tg::df_split(b[r]);
+    tg::CSum a = {b0.hi, b0.lo};
+    for (long q = 0; q < m; ++q) tg::cs_fma(a, tg::df_split(x[r * m + q]), tg::df_split(y[r * m + q]));
+    const tg::Df v = tg::cs_value(a);
+    out[r] = (double)v.hi + (double)v.lo;
+  }
 }
+
+}
+
