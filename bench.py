@@ -151,6 +151,8 @@ def parse():
     ap.add_argument("--no-single", action="store_true",
                     help="skip the single-species model (Eq. e:rd) line")
     ap.add_argument("--batch-sims", type=int, default=64)
+    ap.add_argument("--batch-threads", type=int, default=0,
+                    help="host threads of the concurrent batch (0: up to 8)")
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--batch-seq-steps", type=int, default=5,
                     help="timed steps per simulation of the sequential mixed comparison")
@@ -309,11 +311,12 @@ def run_reference(args, world, rank):
 
 def run_batch(args, dev):
     """64 simulations of uneven grids (64/96/128^3, rho ~ U[5,15], k_scale ~ U[0.5,2]) stepped
-    as one batch (persistent solvers, replayed step graph, autotuned tiles) for the workload's
-    steps, against the same simulations run one after another through the single-simulation
-    path with each one's best elasticity preconditioner (the scaled spectral one where the
-    grid allows it), mixed and FP64; the sequential runs are timed on a sample of steps per
-    simulation after one untimed step."""
+    as one batch for the workload's steps, in both batch forms: persistent (cooperative
+    solvers, replayed step graph, autotuned tiles) and concurrent (each member on the
+    single-simulation path with its best elasticity preconditioner -- the scaled spectral one
+    where the grid allows it -- on its own stream, host threads driving them); against the
+    same simulations run one after another through the single-simulation path, mixed and
+    FP64, timed on a sample of steps per simulation after one untimed step."""
     import torch
     from paper_1810_05370_gb300 import Simulation
     from paper_1810_05370_gb300.batch import Batch
@@ -341,6 +344,21 @@ def run_batch(args, dev):
                 return pc
         return PRECONDS["jacobi"]
 
+    # the concurrent batch: every member on the single-simulation path with its best
+    # preconditioner, on its own stream, host threads driving them
+    cb = Batch([(n, dict(P, precond_elas=best_precond(n, P)), st)
+                for (n, P, _), st in zip(spec, states)], device=dev, concurrent=True,
+               threads=args.batch_threads)
+    cb.step(args.dt, 1)                                   # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    cstats = cb.step(args.dt, args.batch_steps)
+    torch.cuda.synchronize(dev)
+    t_conc = time.perf_counter() - t0
+    cb.close()
+    del cb
+    torch.cuda.empty_cache()
+
     seq = {}
     for prec, k in (("mixed", args.batch_seq_steps), ("fp64", args.batch_seq_steps_fp64)):
         t_seq, vs = 0.0, 0
@@ -359,6 +377,12 @@ def run_batch(args, dev):
         seq[prec] = {"voxel_steps_per_s": vs / t_seq, "steps_per_sim": k, "seconds": t_seq}
     vs = voxels * args.batch_steps
     return {"sims": len(spec), "voxels": voxels, "steps": args.batch_steps, "precision": "mixed",
+            "concurrent": {"voxel_steps_per_s": vs / t_conc, "seconds": t_conc,
+                           "threads": args.batch_threads or min(len(spec), 8),
+                           "speedup_over_sequential_mixed":
+                               (vs / t_conc) / seq["mixed"]["voxel_steps_per_s"],
+                           "inner_iterations": cstats["it_elas_total"],
+                           "launches": cstats["launches"]},
             "voxel_steps_per_s": vs / t_batch, "seconds": t_batch,
             "sequential_best_path": seq,
             "speedup_over_sequential_mixed": (vs / t_batch) / seq["mixed"]["voxel_steps_per_s"],

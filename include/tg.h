@@ -328,6 +328,28 @@ tg_status tg_batch_init(int32_t nsims, const tg_grid* grids, const tg_params* pa
  * NULL. */
 tg_status tg_batch_autotune(tg_batch* batch, double dt, tg_batch_tune* result);
 
+/* Concurrent batches.  The same simulations, each stepped by the single-simulation path --
+ * its own elasticity preconditioner as its params give it (the scaled spectral one where the
+ * grid allows it), the double-FP32 refinements, the Neumann inner CN solves, the extrapolated
+ * elasticity starts -- on a CUDA stream of its own.  A pool of nthreads host threads (0: up to
+ * 8) drives them: each thread takes the largest simulation not yet stepped and advances it by
+ * all nsteps of a tg_batch_step call, so several simulations' kernels share the GPU.  Members
+ * may mix grids, preconditioners, models and precisions' solvers (prec applies to all).  The
+ * workspace holds one tg_workspace_bytes(grid, params, prec) region per member, each rounded
+ * up to 256 bytes: tg_batch_concurrent_workspace_bytes gives the total, 0 if any member is
+ * invalid.  The states are read after the work already queued on cuda_stream; each
+ * tg_batch_step returns with every member's step complete.  tg_batch_autotune has nothing to
+ * tune (result zeroed) and tg_batch_set_timeout nothing to limit; tg_batch_stats report the
+ * summed iteration counts and launches (graph, tile_depth, coop_blocks are 0).  The first
+ * member that fails stops the others at their next simulation and its status is returned;
+ * the batch then refuses further steps (TG_ERR_STATE). */
+size_t tg_batch_concurrent_workspace_bytes(int32_t nsims, const tg_grid* grids,
+                                           const tg_params* params, tg_precision prec);
+tg_status tg_batch_concurrent_init(int32_t nsims, const tg_grid* grids, const tg_params* params,
+                                   const tg_state* states, tg_precision prec, void* workspace,
+                                   size_t workspace_bytes, int32_t nthreads, void* cuda_stream,
+                                   tg_batch** out);
+
 /* Advance every simulation by nsteps steps of dt (the split of tg_step). */
 tg_status tg_batch_step(tg_batch* batch, double dt, int32_t nsteps, tg_batch_stats* stats);
 

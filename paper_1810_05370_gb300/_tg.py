@@ -120,6 +120,11 @@ def _load():
         "tg_batch_workspace_bytes": (C.c_size_t, [C.c_int32, P(tg_grid), C.c_int]),
         "tg_batch_init": (C.c_int, [C.c_int32, P(tg_grid), P(tg_params), P(tg_state), C.c_int,
                                     C.c_void_p, C.c_size_t, C.c_void_p, P(C.c_void_p)]),
+        "tg_batch_concurrent_workspace_bytes": (C.c_size_t, [C.c_int32, P(tg_grid), P(tg_params),
+                                                             C.c_int]),
+        "tg_batch_concurrent_init": (C.c_int, [C.c_int32, P(tg_grid), P(tg_params), P(tg_state),
+                                               C.c_int, C.c_void_p, C.c_size_t, C.c_int32,
+                                               C.c_void_p, P(C.c_void_p)]),
         "tg_batch_autotune": (C.c_int, [C.c_void_p, C.c_double, P(tg_batch_tune)]),
         "tg_batch_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, P(tg_batch_stats)]),
         "tg_batch_set_timeout": (C.c_int, [C.c_void_p, C.c_uint64]),
@@ -318,6 +323,25 @@ def tg_batch_init(grids, params, states, prec, workspace_ptr, workspace_bytes, s
                            C.c_size_t(workspace_bytes), C.c_void_p(stream_ptr), C.byref(out))
     if rc != TG_OK:
         raise TGError(rc, "tg_batch_init")
+    return out
+
+
+def tg_batch_concurrent_workspace_bytes(grids, params, prec) -> int:
+    n = len(grids)
+    return int(lib.tg_batch_concurrent_workspace_bytes(n, (tg_grid * n)(*grids),
+                                                       (tg_params * n)(*params), int(prec)))
+
+
+def tg_batch_concurrent_init(grids, params, states, prec, workspace_ptr, workspace_bytes,
+                             nthreads, stream_ptr):
+    n = len(grids)
+    ga, pa, sa = (tg_grid * n)(*grids), (tg_params * n)(*params), (tg_state * n)(*states)
+    out = C.c_void_p()
+    rc = lib.tg_batch_concurrent_init(n, ga, pa, sa, int(prec), C.c_void_p(workspace_ptr),
+                                      C.c_size_t(workspace_bytes), C.c_int32(nthreads),
+                                      C.c_void_p(stream_ptr), C.byref(out))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_batch_concurrent_init")
     return out
 
 

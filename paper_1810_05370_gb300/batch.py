@@ -8,9 +8,15 @@ from .simulation import STATE_KEYS, _torch
 
 
 class Batch:
-    """sims: list of (n, params, state) with n an int or (nx, ny, nz); mixed precision only."""
+    """sims: list of (n, params, state) with n an int or (nx, ny, nz).
 
-    def __init__(self, sims, device=None, stream=None):
+    concurrent=False: the persistent batch solvers (mixed precision, Jacobi-PCG, one captured
+    step graph).  concurrent=True: every simulation steps through the single-simulation path
+    (its params' preconditioner) on its own stream, `threads` host threads (0: up to 8)
+    driving them; `precision` is "mixed" or "fp64" there."""
+
+    def __init__(self, sims, device=None, stream=None, concurrent=False, threads=0,
+                 precision="mixed"):
         torch = _torch()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         # the step is captured as a CUDA graph, which needs a stream of its own
@@ -36,13 +42,25 @@ class Batch:
             self.cstates.append(s)
             self.states.append(st)
             self.shapes.append(shape)
-        nbytes = _tg.tg_batch_workspace_bytes(self.grids, _tg.TG_MIXED)
+        prec = {"mixed": _tg.TG_MIXED, "fp64": _tg.TG_FP64}[precision]
+        if concurrent:
+            nbytes = _tg.tg_batch_concurrent_workspace_bytes(self.grids, self.cparams, prec)
+        else:
+            if precision != "mixed":
+                raise ValueError("the persistent batch runs the mixed precision only")
+            nbytes = _tg.tg_batch_workspace_bytes(self.grids, prec)
         if nbytes == 0:
             raise ValueError("invalid batch")
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         torch.cuda.synchronize(self.device)
-        self.handle = _tg.tg_batch_init(self.grids, self.cparams, self.cstates, _tg.TG_MIXED,
-                                        self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        if concurrent:
+            self.handle = _tg.tg_batch_concurrent_init(self.grids, self.cparams, self.cstates, prec,
+                                                       self.workspace.data_ptr(), nbytes, threads,
+                                                       self.stream.cuda_stream)
+        else:
+            self.handle = _tg.tg_batch_init(self.grids, self.cparams, self.cstates, prec,
+                                            self.workspace.data_ptr(), nbytes,
+                                            self.stream.cuda_stream)
         self.voxels = int(sum(np.prod(s) for s in self.shapes))
 
     def autotune(self, dt: float) -> dict:

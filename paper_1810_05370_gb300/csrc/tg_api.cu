@@ -6,8 +6,10 @@
 
 #include <algorithm>
 #include <climits>
+#include <atomic>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "tg_internal.cuh"
@@ -1967,6 +1969,11 @@ struct tg_batch {
   bool use_graph;
   int broken;
   long long launches;
+  // concurrent batches: every member steps through the single-simulation path on its own
+  // stream, driven by a pool of host threads
+  bool concurrent;
+  int nthreads;
+  std::vector<cudaStream_t> streams;
 };
 
 namespace {
@@ -2256,12 +2263,134 @@ tg_status tg_batch_init(int32_t nsims, const tg_grid* grids, const tg_params* pa
   return TG_OK;
 }
 
+size_t tg_batch_concurrent_workspace_bytes(int32_t nsims, const tg_grid* grids,
+                                           const tg_params* params, tg_precision prec) {
+  if (nsims <= 0 || !grids || !params || (prec != TG_MIXED && prec != TG_FP64)) return 0;
+  size_t total = 0;
+  for (int s = 0; s < nsims; ++s) {
+    const size_t b = tg_workspace_bytes(&grids[s], &params[s], prec);
+    if (b == 0) return 0;
+    total += round_up(b);
+  }
+  return total;
+}
+
+tg_status tg_batch_concurrent_init(int32_t nsims, const tg_grid* grids, const tg_params* params,
+                                   const tg_state* states, tg_precision prec, void* workspace,
+                                   size_t workspace_bytes, int32_t nthreads, void* cuda_stream,
+                                   tg_batch** out) {
+  if (out) *out = nullptr;
+  if (!out || nsims <= 0 || !grids || !params || !states || nthreads < 0) return TG_ERR_ARG;
+  const size_t need = tg_batch_concurrent_workspace_bytes(nsims, grids, params, prec);
+  if (need == 0) return TG_ERR_ARG;
+  if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < need)
+    return TG_ERR_WORKSPACE;
+  tg_batch* B = new (std::nothrow) tg_batch();
+  if (!B) return TG_ERR_CUDA;
+  B->nsims = nsims;
+  B->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&B->device);
+  B->concurrent = true;
+  B->nthreads = nthreads > 0 ? std::min<int>(nthreads, nsims) : std::min<int>(nsims, 8);
+  // the callers' work on cuda_stream (the states' upload) comes first
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess) {
+    delete B;
+    return TG_ERR_CUDA;
+  }
+  char* base = (char*)workspace;
+  size_t off = 0;
+  for (int s = 0; s < nsims; ++s) {
+    cudaStream_t st = nullptr;
+    tg_status e = TG_OK;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) e = TG_ERR_CUDA;
+    tg_ctx* X = nullptr;
+    const size_t b = tg_workspace_bytes(&grids[s], &params[s], prec);
+    if (e == TG_OK)
+      e = tg_init(&grids[s], &params[s], prec, &states[s], base + off, b, st, 0, &X, nullptr);
+    if (e == TG_OK && cudaStreamSynchronize(st) != cudaSuccess) e = TG_ERR_CUDA;
+    if (e != TG_OK) {
+      if (X) tg_free(X);
+      if (st) cudaStreamDestroy(st);
+      tg_batch_free(B);
+      return e;
+    }
+    B->streams.push_back(st);
+    B->ctx.push_back(X);
+    off += round_up(b);
+  }
+  *out = B;
+  return TG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Step the members of a concurrent batch: the host threads take members off one list, largest
+// first (a longest-processing-time schedule), and step each through all nsteps before taking
+// the next; members share nothing, so the only synchronisation is the list counter.  The
+// first failure stops the other threads at their next member.
+tg_status batch_concurrent_step(tg_batch* B, double dt, int32_t nsteps, tg_batch_stats* stats) {
+  const int n = B->nsims;
+  std::vector<int> order(n);
+  for (int s = 0; s < n; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return B->ctx[a]->G.nvox > B->ctx[b]->G.nvox; });
+  std::atomic<int> next{0};
+  std::atomic<int> err{TG_OK};
+  std::mutex mu;
+  tg_batch_stats acc;
+  memset(&acc, 0, sizeof(acc));
+  auto worker = [&]() {
+    if (cudaSetDevice(B->device) != cudaSuccess) {
+      err.store(TG_ERR_CUDA);
+      return;
+    }
+    for (;;) {
+      const int q = next.fetch_add(1);
+      if (q >= n || err.load() != TG_OK) return;
+      const int s = order[q];
+      tg_stats st;
+      const tg_status e = tg_step(B->ctx[s], dt, nsteps, nullptr, &st);
+      if (e != TG_OK) {
+        int expect = TG_OK;
+        err.compare_exchange_strong(expect, (int)e);
+        return;
+      }
+      std::lock_guard<std::mutex> lock(mu);
+      acc.it_elas_total += st.it_elas_total;
+      acc.it_elas_max = std::max<int64_t>(acc.it_elas_max, st.it_elas);
+      acc.it_diff_total += st.it_diff_total;
+      acc.relres_elas_max = std::max(acc.relres_elas_max, st.relres_elas);
+      acc.launches += st.launches;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < B->nthreads; ++t) pool.emplace_back(worker);
+  worker();   // the calling thread is one of the pool
+  for (std::thread& t : pool) t.join();
+  if (err.load() != TG_OK) return (tg_status)err.load();
+  if (stats) {
+    *stats = acc;
+    stats->steps = nsteps;
+  }
+  return TG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 tg_status tg_batch_step(tg_batch* B, double dt, int32_t nsteps, tg_batch_stats* stats) {
   if (!B) return TG_ERR_ARG;
   if (B->broken) return TG_ERR_STATE;
   if (!(dt > 0.0) || !isfinite(dt) || nsteps < 0) return TG_ERR_ARG;
   if (stats) memset(stats, 0, sizeof(*stats));
   BCK(cudaSetDevice(B->device));
+  if (B->concurrent) {
+    const tg_status e = batch_concurrent_step(B, dt, nsteps, stats);
+    return e == TG_OK ? e : bfail(B, e);
+  }
   B->launches = 0;
   for (int32_t s = 0; s < nsteps; ++s) {
     tg_status e = batch_one_step(B, dt, stats);
@@ -2282,6 +2411,10 @@ tg_status tg_batch_autotune(tg_batch* B, double dt, tg_batch_tune* result) {
   if (!B) return TG_ERR_ARG;
   if (B->broken) return TG_ERR_STATE;
   if (!(dt > 0.0)) return TG_ERR_ARG;
+  if (B->concurrent) {   // nothing to tune: the members run the single-simulation kernels
+    if (result) memset(result, 0, sizeof(*result));
+    return TG_OK;
+  }
   BCK(cudaSetDevice(B->device));
   for (tg_ctx* X : B->ctx) {
     tg_status e = build_elas_coef(X, true);
@@ -2359,6 +2492,10 @@ void tg_batch_free(tg_batch* B) {
   if (!B) return;
   if (B->graph_ready) cudaGraphExecDestroy(B->graph);
   for (tg_ctx* X : B->ctx) tg_free(X);
+  for (cudaStream_t st : B->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
   delete B;
 }
 

@@ -1,5 +1,7 @@
-"""Batched simulations (persistent cooperative solvers, captured step graph) against the oracle
-and the single-simulation path; bounded grid-wide waits; the autotuner."""
+"""Batched simulations against the oracle and the single-simulation path: the persistent
+batch (cooperative solvers, captured step graph; bounded grid-wide waits; the autotuner) and
+the concurrent batch (each member on the single-simulation path on its own stream, host
+threads driving them)."""
 import numpy as np
 import pytest
 
@@ -85,6 +87,68 @@ def test_batch_wait_limit_reports_timeout(torch_cuda):
     with pytest.raises(_tg.TGError) as e:
         batch.step(0.01)
     assert e.value.status == _tg.TG_ERR_TIMEOUT
+    with pytest.raises(_tg.TGError) as e:
+        batch.step(0.01)
+    assert e.value.status == _tg.TG_ERR_STATE
+    batch.close()
+
+
+def _spectral_or_jacobi(n, P):
+    """The scaled spectral preconditioner where the grid allows it, else Jacobi."""
+    from paper_1810_05370_gb300 import _tg
+    for pc in (2, 0):
+        if _tg.tg_workspace_bytes(_tg.make_grid(n), _tg.make_params(dict(P, precond_elas=pc)),
+                                  _tg.TG_MIXED) > 0:
+            return dict(P, precond_elas=pc)
+    return dict(P, precond_elas=0)
+
+
+def test_concurrent_batch_equals_single_runs(torch_cuda, oracle):
+    """The concurrent batch steps each member through the single-simulation path on its own
+    stream: results are bit-identical to single runs, whatever the thread count, and match
+    the oracle to the mixed precision's tolerance."""
+    from paper_1810_05370_gb300 import Simulation
+    from paper_1810_05370_gb300.batch import Batch
+    steps, dt = 3, 0.01
+    spec = small_batch() + [((32, 32, 32), workload_params(rho_g=8.0, rho_w=8.0), 1004)]
+    spec = [(n, _spectral_or_jacobi(n, P), seed) for n, P, seed in spec]
+    assert any(P["precond_elas"] == 2 for _, P, _ in spec)
+    for threads in (1, 3):
+        batch = Batch([(n, P, initial_state(n, seed)) for n, P, seed in spec], concurrent=True,
+                      threads=threads)
+        stats = batch.step(dt, nsteps=steps)
+        assert stats["steps"] == steps and stats["it_elas_total"] > 0
+        for s, (n, P, seed) in enumerate(spec):
+            got = batch.numpy(s)
+            sim = Simulation(n, P, initial_state(n, seed), precision="mixed")
+            sim.step(dt, nsteps=steps)
+            single = sim.numpy()
+            sim.close()
+            for k in FIELDS:
+                assert np.array_equal(got[k], single[k]), (threads, s, k)
+            if threads == 1:
+                ref = initial_state(n, seed)
+                oracle.init(n, P, ref)
+                for _ in range(steps):
+                    oracle.step(n, P, dt, ref)
+                errs = {k: rel_l2(got[k], ref[k]) for k in FIELDS}
+                assert max(errs.values()) <= 1e-5, (s, errs)
+        batch.close()
+
+
+def test_concurrent_batch_member_failure_stops_the_batch(torch_cuda):
+    """A member that cannot converge fails its step (made on the host: its diffusion solves
+    get one CG iteration); the batch returns that member's status and then refuses further
+    steps."""
+    from paper_1810_05370_gb300 import _tg
+    from paper_1810_05370_gb300.batch import Batch
+    spec = small_batch()
+    spec[1] = (spec[1][0], dict(spec[1][1], maxit_diff=1), spec[1][2])
+    batch = Batch([(n, P, initial_state(n, seed)) for n, P, seed in spec], concurrent=True,
+                  threads=2)
+    with pytest.raises(_tg.TGError) as e:
+        batch.step(0.01, nsteps=2)
+    assert e.value.status == _tg.TG_ERR_NOCONV
     with pytest.raises(_tg.TGError) as e:
         batch.step(0.01)
     assert e.value.status == _tg.TG_ERR_STATE
