@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(NT) k_elas32_update(long long n, Elas32 I) {
 __global__ void __launch_bounds__(NT) k_elas32_matvec_spec(Geo G, Consts32 K, Elas32 I) {
   if (!running(I.S)) return;
   __shared__ Tile32 T;
-  const float part = elas32_matvec_tile<false, true>(G, K, I, I.S->it, I.S->beta, blockIdx.x,
-                                                     blockIdx.y, blockIdx.z, T);
+  const float part = elas32_matvec_tile_spec(G, K, I, I.S->it, blockIdx.x, blockIdx.y,
+                                             blockIdx.z, T);
   double acc[1] = {(double)part};
   double out[1];
   if (reduce_last_block<1>(acc, I.partial, I.counter, out) && threadIdx.x == 0 && threadIdx.y == 0) {

@@ -3,6 +3,8 @@
 // (tg_diffusion.cu, tg_mixed.cu) and the batched persistent solvers (tg_batch.cu).
 #pragma once
 
+#include <type_traits>
+
 #include "tg_internal.cuh"
 
 namespace tg {
@@ -284,6 +286,145 @@ __device__ __forceinline__ float elas32_matvec_tile(const Geo& G, const Consts32
     s3 = sf;
   }
   __syncthreads();                      // the tile may be restaged by the caller's next item
+  return part;
+}
+
+// The FP32 operator on the spectral path (p_new already written by the preconditioner), with
+// the tile layout of elas32_matvec_tile and its arithmetic.  The z loop is unrolled by the
+// four plane slots, so the slots of planes k-1, k, k+1 and of the plane being staged are
+// compile-time constants and every shared address is the thread's base plus a constant (the
+// rotating slots of elas32_matvec_tile cost ~40 integer instructions per node).
+template <int S0, int S1, int S2>
+__device__ __forceinline__ Cell cell_of(Tile32& T, int ci) {
+  Cell t;
+  constexpr int sl[3] = {S0, S1, S2};
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t.p[o][a] = &T.p[sl[o]][a][ci];
+    t.mu[o] = &T.mu[sl[o]][ci];
+    t.la[o] = &T.la[sl[o]][ci];
+  }
+  return t;
+}
+
+struct SpecTileCtx {
+  const float* __restrict__ pn[3];
+  long long ho0, ho1, col;
+  int tid, hs1, ci, k1;
+  bool two, on;
+};
+
+struct StagedNode {
+  float p[3], mu, la;
+};
+
+__device__ __forceinline__ long long spec_plane_offset(const Geo& G, int kk) {
+  const int kw = kk < 0 ? kk + G.nz : (kk >= G.nz ? kk - G.nz : kk);
+  return (long long)kw * G.nxy;
+}
+
+__device__ __forceinline__ void spec_fetch(const SpecTileCtx& X, const Elas32& I, long long g,
+                                           StagedNode& v) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) v.p[a] = __ldg(X.pn[a] + g);
+  v.mu = __ldg(I.mu + g);
+  v.la = __ldg(I.lam + g);
+}
+
+template <int S>
+__device__ __forceinline__ void spec_put(Tile32& T, const StagedNode& v, int s) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) T.p[S][a][s] = v.p[a];
+  T.mu[S][s] = v.mu;
+  T.la[S][s] = v.la;
+}
+
+// plane k from slots (S0, S1, S2); plane k + 2 is staged into slot S3
+template <int S0, int S1, int S2, int S3>
+__device__ __forceinline__ void spec_step(const Geo& G, const Consts32& K, const Elas32& I,
+                                          const SpecTileCtx& X, Tile32& T, int k, float& eta_next,
+                                          StagedNode& r0, StagedNode& r1, float& part) {
+  const float eta_k = eta_next;
+  const bool more = k + 1 < X.k1;
+  if (X.on && more) eta_next = __ldg(I.eta + (long long)(k + 1) * G.nxy + X.col);
+  if (more) {
+    const long long zo = spec_plane_offset(G, k + 2);
+    spec_fetch(X, I, zo + X.ho0, r0);
+    if (X.two) spec_fetch(X, I, zo + X.ho1, r1);
+  }
+  __syncthreads();   // plane k + 1 (staged by the previous step) is visible
+  if (X.on) {
+    const Cell t = cell_of<S0, S1, S2>(T, X.ci);
+    const long long c = (long long)k * G.nxy + X.col;
+    Fac32 f;
+    tile_fac(T, t, K.ih2, eta_k, f);
+    const float q0 = row_tile<0>(T, t, f, K.sc);
+    const float q1 = row_tile<1>(T, t, f, K.sc);
+    const float q2 = row_tile<2>(T, t, f, K.sc);
+    I.q[0][c] = q0;
+    I.q[1][c] = q1;
+    I.q[2][c] = q2;
+    part += tp(T, t, 0, 0, 0, 0) * q0 + tp(T, t, 1, 0, 0, 0) * q1 + tp(T, t, 2, 0, 0, 0) * q2;
+  }
+  if (more) {
+    spec_put<S3>(T, r0, X.tid);
+    if (X.two) spec_put<S3>(T, r1, X.hs1);
+  }
+}
+
+__device__ __forceinline__ float elas32_matvec_tile_spec(const Geo& G, const Consts32& K,
+                                                         const Elas32& I, int it, int bx, int by,
+                                                         int bz, Tile32& T) {
+  SpecTileCtx X;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) X.pn[a] = I.p[(it & 1) ^ 1][a];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  X.tid = ty * BX + tx;
+  const int i0 = bx * BX, j0 = by * BY;
+  const int i = i0 + tx, j = j0 + ty;
+  X.on = (i < G.nx) && (j < G.ny);
+  const int k0 = bz * G.zc;
+  X.k1 = min(G.nz, k0 + G.zc);
+  auto wrapped = [&](int s) {   // full modulo: a tile may be wider than the grid
+    int gi = (i0 - 1 + s % HX) % G.nx, gj = (j0 - 1 + s / HX) % G.ny;
+    gi = gi < 0 ? gi + G.nx : gi;
+    gj = gj < 0 ? gj + G.ny : gj;
+    return (long long)gj * G.nx + gi;
+  };
+  X.hs1 = X.tid + NT;
+  X.two = X.hs1 < HXY;
+  X.ho0 = wrapped(X.tid);
+  X.ho1 = X.two ? wrapped(X.hs1) : 0;
+  X.ci = (ty + 1) * HX + (tx + 1);
+  X.col = (long long)j * G.nx + i;
+  StagedNode r0, r1;
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    const long long zo = spec_plane_offset(G, k0 - 1 + o);
+    spec_fetch(X, I, zo + X.ho0, r0);
+    if (X.two) spec_fetch(X, I, zo + X.ho1, r1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T.p[o][a][X.tid] = r0.p[a];
+      if (X.two) T.p[o][a][X.hs1] = r1.p[a];
+    }
+    T.mu[o][X.tid] = r0.mu;
+    T.la[o][X.tid] = r0.la;
+    if (X.two) {
+      T.mu[o][X.hs1] = r1.mu;
+      T.la[o][X.hs1] = r1.la;
+    }
+  }
+  float part = 0.0f;
+  float eta_next = (X.on && k0 < X.k1) ? __ldg(I.eta + (long long)k0 * G.nxy + X.col) : 0.0f;
+  for (int k = k0; k < X.k1; k += 4) {
+    spec_step<0, 1, 2, 3>(G, K, I, X, T, k, eta_next, r0, r1, part);
+    if (k + 1 < X.k1) spec_step<1, 2, 3, 0>(G, K, I, X, T, k + 1, eta_next, r0, r1, part);
+    if (k + 2 < X.k1) spec_step<2, 3, 0, 1>(G, K, I, X, T, k + 2, eta_next, r0, r1, part);
+    if (k + 3 < X.k1) spec_step<3, 0, 1, 2>(G, K, I, X, T, k + 3, eta_next, r0, r1, part);
+  }
+  __syncthreads();
   return part;
 }
 
