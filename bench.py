@@ -57,11 +57,14 @@ def mixed_kernel_bytes(n, precond):
         "k_diff_diag": 40,           # 3 faces in; diagonal and its inverse out
         "k_to_f32": 120,             # FP32 copies of the 10 fields the transport gathers
         "k_divergence": 32,          # v (3) in, div v out
-        "k_sl32": 88,                # 10 FP32 fields gathered, 6 FP64 fields out
+        "k_sl32": 96,                # 3 interleaved float4 inputs gathered, 6 FP64 fields out
+        "k_sl32_pack": 120,          # v (3), 6 species in (FP64); 3 interleaved float4 out
+        "k_lame_df": 116,            # p, i, n, g, w, f, bg in; mu, lam, eta (FP64 and FP32),
+                                     # mu, lam and p + n pairs out
         "k_df_pack3": 48,            # 3 FP64 in, 3 pairs out
         "k_cn_ir_residual_df": 76,   # 3 face pairs, D^-1; per field (i, l): x pair, rhs pair, r, e
         "k_cn32_pupdate": 28,        # D^-1, r and p (2 fields) in, p out
-        "k_cn32_matvec": 28,         # 3 FP32 faces, p (2 fields) in, q out
+        "k_cn32_matvec": 44,         # 3 FP32 faces, z, previous p (2 fields) in; p, q out
         "k_cn32_update": 52,         # D^-1, e, r, p, q (2 fields) in, e, r out
         "k_cn_ir_correct": 56,       # x (FP64), e in; x, x pair out (2 fields)
         "k_cn32_neumann": 32,        # r (2 fields), 3 FP32 faces, D^-1 in; z (2 fields) out
@@ -79,7 +82,8 @@ def mixed_kernel_bytes(n, precond):
         "k_cn_pupdate": 32,          # D^-1, r, p in; p out
         "k_react": 128,              # 9 FP64 in, 7 out
         "k_lame": 80,                # 7 species in; mu, lambda, eta out
-        "k_elas_coef_df": 136,       # mu, lambda pairs, eta, p, n in; F, G, diagonal, b pairs out
+        "k_elas_coef_df": 128,       # mu, lambda, p + n pairs, eta in; F, G, diagonal, b pairs out
+        "k_elas32_coef": 48,         # u (3) in; u pairs out
         "k_elas_extrapolate": 120,   # u, v, v^{n-1} in; u, du out
         "k_spec_mean": 24,           # mu, lambda, eta in
         "k_elas_ir_residual_df": 160,  # u, F, G, diagonal, b pairs (3 each), mu, lambda pairs

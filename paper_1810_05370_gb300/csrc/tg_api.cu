@@ -743,7 +743,10 @@ Cn32 cn32_view(tg_ctx* X) {
     I.Kf[r] = X->b32[B_CKF0 + r];
   }
   I.dinv = X->b32[B_CDINV];
-  for (int r = 0; r < 3; ++r) I.z[r] = nullptr;
+  for (int r = 0; r < 3; ++r) {
+    I.z[r] = nullptr;
+    I.palt[r] = X->b32[B_SL0 + r];   // the transport's inputs are free after S1
+  }
   I.S = X->scal + 5;
   I.partial = X->partial;
   I.counter = X->counter;
@@ -798,7 +801,7 @@ tg_status cn_solve3_mixed(tg_ctx* X, tg_stats* stats, int mask) {
     CgScal host[3];
     const int sw = sweeps == 0 ? 0 : 1;
     tg_status st = drive_cg(X, [&](int) {
-      X->launches += nslot <= 2 ? 4 : 3;
+      X->launches += 3;
       return launch_cn32_iter(X->G, I, X->stream, slot[0], slot[1], cap);
     }, I.S, 3, X->prm.maxit_diff, X->prev_it_cn_inner[sw], host);
     if (st != TG_OK) return st;

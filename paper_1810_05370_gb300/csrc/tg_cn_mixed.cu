@@ -194,6 +194,87 @@ __global__ void __launch_bounds__(NT) k_cn32_matvec(Geo G, Cn32 I) {
   }
 }
 
+// The operator of an inner iteration preconditioned by the polynomial, with the p-update
+// fused: at iteration k, p = z + beta p_old (p = z at a solve's first iteration) is formed at
+// the stencil's nodes from z and the previous direction (buffer (k & 1) ? palt : p), written
+// at the thread's node into the other buffer, and q = A p, <p, q> follow (A p as in
+// k_cn32_matvec).  Each thread marches its (i, j) column through the block's z range with p of
+// planes k-1, k and the z-face below in registers; offsets are 32-bit (nvox < 2^31).
+__global__ void __launch_bounds__(NT) k_cn32_matvec_neu(Geo G, Cn32 I) {
+  bool act[3];
+  if (!active3(I, act)) return;
+  float beta[3];
+  bool first[3];
+  const float* zin[3];
+  const float* pin[3];
+  float* pout[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    first[r] = I.S[r].it == 0;
+    beta[r] = first[r] ? 0.0f : (float)I.S[r].beta;
+    const bool odd = I.S[r].it & 1;
+    zin[r] = I.z[r];
+    pin[r] = odd ? I.palt[r] : I.p[r];
+    pout[r] = odd ? I.p[r] : I.palt[r];
+  }
+  float part[3] = {0.0f, 0.0f, 0.0f};
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i < G.nx && j < G.ny) {
+    const int nx = G.nx, nxy = G.nx * G.ny, nz = G.nz;
+    const int ixp = i + 1 == nx ? 0 : i + 1, ixm = i == 0 ? nx - 1 : i - 1;
+    const int jyp = j + 1 == G.ny ? 0 : j + 1, jym = j == 0 ? G.ny - 1 : j - 1;
+    const int oc = j * nx + i, oxp = j * nx + ixp, oxm = j * nx + ixm;
+    const int oyp = jyp * nx + i, oym = jym * nx + i;
+    const int k0 = blockIdx.z * G.zc, k1 = min(nz, k0 + G.zc);
+    auto plane = [&](int k) { return (k < 0 ? k + nz : (k >= nz ? k - nz : k)) * nxy; };
+    auto pn = [&](int r, int idx) {
+      const float z = __ldg(zin[r] + idx);
+      return first[r] ? z : z + beta[r] * __ldg(pin[r] + idx);
+    };
+    float pm[3], pc[3];
+    const int bm = plane(k0 - 1), b0 = plane(k0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      pm[r] = act[r] ? pn(r, bm + oc) : 0.0f;
+      pc[r] = act[r] ? pn(r, b0 + oc) : 0.0f;
+    }
+    float fzm = __ldg(I.Kf[2] + bm + oc);
+    for (int k = k0; k < k1; ++k) {
+      const int b = plane(k), bn = plane(k + 1);
+      const float fxp = __ldg(I.Kf[0] + b + oc), fxm = __ldg(I.Kf[0] + b + oxm);
+      const float fyp = __ldg(I.Kf[1] + b + oc), fym = __ldg(I.Kf[1] + b + oym);
+      const float fzp = __ldg(I.Kf[2] + b + oc);
+      const float d = 1.0f + ((fxp + fxm) + (fyp + fym) + (fzp + fzm));
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        if (!act[r]) continue;
+        const float pp = pn(r, bn + oc);
+        const float q = d * pc[r] - (fxp * pn(r, b + oxp) + fxm * pn(r, b + oxm) +
+                                     fyp * pn(r, b + oyp) + fym * pn(r, b + oym) + fzp * pp +
+                                     fzm * pm[r]);
+        pout[r][b + oc] = pc[r];
+        I.q[r][b + oc] = q;
+        part[r] += pc[r] * q;
+        pm[r] = pc[r];
+        pc[r] = pp;
+      }
+      fzm = fzp;
+    }
+  }
+  double acc[3] = {(double)part[0], (double)part[1], (double)part[2]};
+  double out[3];
+  if (reduce_last_block<3>(acc, I.partial, I.counter, out) && threadIdx.x == 0 &&
+      threadIdx.y == 0) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      if (act[r]) {
+        I.S[r].pq = out[r];
+        I.S[r].alpha = I.S[r].rz / out[r];
+      }
+  }
+}
+
 // e += alpha p, r -= alpha q; <r, D^{-1} r>, <r, r>.  float4 groups g = g0, g0 + gs, ... of an
 // n-voxel system plus the scalar tail n - n % 4 .. n (block 0); a group's products are summed
 // in FP32, groups in FP64.  With the polynomial preconditioner (NEU) only <r, r> is formed:
@@ -203,8 +284,12 @@ __global__ void __launch_bounds__(NT) k_cn32_update(long long n, Cn32 I) {
   bool act[3];
   if (!active3(I, act)) return;
   float alpha[3];
+  const float* pcur[3];   // the search direction this iteration's operator kernel used
 #pragma unroll
-  for (int r = 0; r < 3; ++r) alpha[r] = (float)I.S[r].alpha;
+  for (int r = 0; r < 3; ++r) {
+    alpha[r] = (float)I.S[r].alpha;
+    pcur[r] = (NEU && !(I.S[r].it & 1)) ? I.palt[r] : I.p[r];
+  }
   double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   const long long gs = (long long)gridDim.x * blockDim.x, ng = n / 4;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < ng; v += gs) {
@@ -215,7 +300,7 @@ __global__ void __launch_bounds__(NT) k_cn32_update(long long n, Cn32 I) {
       if (!act[r]) continue;
       float4* e4 = reinterpret_cast<float4*>(I.e[r]) + v;
       float4* r4 = reinterpret_cast<float4*>(I.r[r]) + v;
-      const float4 p = reinterpret_cast<const float4*>(I.p[r])[v];
+      const float4 p = reinterpret_cast<const float4*>(pcur[r])[v];
       const float4 q = reinterpret_cast<const float4*>(I.q[r])[v];
       float4 e = *e4, x = *r4;
       const float a = alpha[r];
@@ -235,7 +320,7 @@ __global__ void __launch_bounds__(NT) k_cn32_update(long long n, Cn32 I) {
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         if (!act[r]) continue;
-        I.e[r][c] += alpha[r] * I.p[r][c];
+        I.e[r][c] += alpha[r] * pcur[r][c];
         const float res = I.r[r][c] - alpha[r] * I.q[r][c];
         I.r[r][c] = res;
         if (!NEU) acc[2 * r] += (double)(res * (di * res));
@@ -592,11 +677,11 @@ cudaError_t launch_cn32_iter(const Geo& G, const Cn32& I, cudaStream_t st, int r
   zc = zc < G.nz ? zc : G.nz;
   const long long gz = (G.nz + zc - 1) / zc;
   if (gx * gy * gz * 2 > partial_capacity || r0 < 0) return cudaErrorInvalidValue;
+  if (G.nvox >= (1LL << 31)) return cudaErrorInvalidValue;   // 32-bit offsets below
   TG_TIMED(K_CN32_NEUMANN, st,
            k_cn32_neumann<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(NM_X, NM_Y), 0,
                             st>>>(G, I, r0, r1, zc));
-  TG_TIMED(K_CN32_PUPDATE, st, k_cn32_pupdate<true><<<flat_blocks(G), NT, 0, st>>>(G.nvox, I));
-  TG_TIMED(K_CN32_MATVEC, st, k_cn32_matvec<<<G.grid, dim3(BX, BY), 0, st>>>(G, I));
+  TG_TIMED(K_CN32_MATVEC, st, k_cn32_matvec_neu<<<G.grid, dim3(BX, BY), 0, st>>>(G, I));
   TG_TIMED(K_CN32_UPDATE, st, k_cn32_update<true><<<flat_blocks(G), NT, 0, st>>>(G.nvox, I));
   return cudaGetLastError();
 }

@@ -418,6 +418,8 @@ struct Cn32 {
   float* p[3];
   float* q[3];
   float* z[3];         // preconditioned residual of the polynomial preconditioner (null: Jacobi)
+  float* palt[3];      // with z: the second search-direction buffer (iteration k writes
+                       // p[k & 1 ? p : palt], reading the other)
   const float* Kf[3];
   const float* dinv;
   CgScal* S;           // 3 inner solves
