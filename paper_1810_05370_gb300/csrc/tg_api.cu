@@ -424,6 +424,10 @@ struct tg_ctx {
   unsigned int* counter2;
   cudaStream_t side;
   cudaEvent_t fork_ev, join_ev;
+  // the oxygen solve of the mixed step, running on the side stream from S0 on: its first
+  // chunk of iterations and profiler slot (ox_begin) until ox_end drives the rest and joins
+  bool ox_running;
+  int ox_chunk, ox_slot;
   int broken;
   int prev_it_diff;
   int prev_it_elas;
@@ -858,7 +862,34 @@ OxDf ox_view(tg_ctx* X) {
 // FP64.  It has its own CG scalars (scal + 8 .. 10) and reduction buffers; the first chunk of
 // its iterations is queued before the i, l solve starts and the rest is driven after it;
 // events fork and join the streams.
-tg_status cn_solve_mixed_concurrent(tg_ctx* X, tg_stats* stats) {
+// The oxygen solve of the mixed step runs on a side stream.  It needs only the S0 faces and
+// o, which the transport does not touch, so it is forked right after S0 (ox_begin): its start
+// and first chunk of iterations overlap the transport (L1-bound) and then the i, l solves on
+// the context's stream; ox_end drives its remaining iterations, finishes and joins.  OxGuard
+// keeps no side-stream work alive past an early return.
+struct OxParts {
+  Cn3 C;
+  OxDf O;
+  CgScal* dev;
+  int ns;
+  bool df;
+};
+
+OxParts ox_parts(tg_ctx* X) {
+  OxParts P;
+  P.df = X->cn_df;
+  P.C = cn_view(X);
+  P.C.S = X->scal + 8;
+  P.C.partial = X->partial2;
+  P.C.counter = X->counter2;
+  P.C.df = 0;
+  P.O = ox_view(X);
+  P.dev = P.df ? P.O.S : P.C.S;   // the oxygen entry of the device scalars
+  P.ns = P.df ? 1 : 3;
+  return P;
+}
+
+tg_status ox_begin(tg_ctx* X) {
   constexpr int MASK_O = 7 & ~CN_MIXED_MASK;
   if (!X->side) {   // default priority (the highest measured no better)
     CK(cudaStreamCreateWithFlags(&X->side, cudaStreamNonBlocking));
@@ -866,53 +897,46 @@ tg_status cn_solve_mixed_concurrent(tg_ctx* X, tg_stats* stats) {
     CK(cudaEventCreateWithFlags(&X->join_ev, cudaEventDisableTiming));
   }
   cudaStream_t so = X->side;
-  const bool df = X->cn_df;
-  Cn3 C = cn_view(X);
-  C.S = X->scal + 8;
-  C.partial = X->partial2;
-  C.counter = X->counter2;
-  C.df = 0;
-  const OxDf O = ox_view(X);
-  CgScal* const dev = df ? O.S : C.S;   // the oxygen entry of the device scalars
-  const int ns = df ? 1 : 3;
-  auto iter = [&](int) -> cudaError_t {
-    X->launches += 3;
-    return df ? launch_ox_iter(X->G, O, so) : launch_cn_iter(X->G, C, so);
-  };
+  const OxParts P = ox_parts(X);
   CK(cudaEventRecord(X->fork_ev, X->stream));
   CK(cudaStreamWaitEvent(so, X->fork_ev, 0));
-  k_cg_reset<<<1, 32, 0, so>>>(dev, ns, X->prm.rtol_diff, X->prm.maxit_diff);
+  X->ox_running = true;
+  k_cg_reset<<<1, 32, 0, so>>>(P.dev, P.ns, X->prm.rtol_diff, X->prm.maxit_diff);
   CK(cudaGetLastError());
-  CK(df ? launch_ox_start(X->G, O, so) : launch_cn_init(X->G, C, so, MASK_O));
-  const int chunk = first_chunk(X->prev_it_diff);
-  const int slot = prof_open_solve(X);
-  for (int c = 0; c < chunk; ++c) {
-    prof_iter(X, slot, c);
-    CK(iter(c));
+  CK(P.df ? launch_ox_start(X->G, P.O, so) : launch_cn_init(X->G, P.C, so, MASK_O));
+  X->ox_chunk = first_chunk(X->prev_it_diff);
+  X->ox_slot = prof_open_solve(X);
+  for (int c = 0; c < X->ox_chunk; ++c) {
+    prof_iter(X, X->ox_slot, c);
+    X->launches += 3;
+    CK(P.df ? launch_ox_iter(X->G, P.O, so) : launch_cn_iter(X->G, P.C, so));
   }
   prof_iter(X, -1, -1);
-  X->launches += 2 + (df ? 1 : 0);
-  // i and l on the context's stream meanwhile
-  tg_status e = cn_solve3_mixed(X, stats, CN_MIXED_MASK);
-  if (e != TG_OK) {
-    cudaStreamSynchronize(so);   // nothing of the side stream outlives the call
-    return e;
-  }
+  X->launches += 2 + (P.df ? 1 : 0);
+  return TG_OK;
+}
+
+tg_status ox_end(tg_ctx* X, tg_stats* stats) {
+  cudaStream_t so = X->side;
+  const OxParts P = ox_parts(X);
+  auto iter = [&](int) -> cudaError_t {
+    X->launches += 3;
+    return P.df ? launch_ox_iter(X->G, P.O, so) : launch_cn_iter(X->G, P.C, so);
+  };
   CgScal host[3];
-  e = drive_cg_on(X, so, iter, dev, ns, X->prm.maxit_diff, X->prev_it_diff, host, chunk, slot);
-  if (e != TG_OK) {
-    cudaStreamSynchronize(so);
-    return e;
-  }
-  const CgScal& ho = df ? host[0] : host[1];
-  if (df) {
-    CK(launch_ox_finish(X->G, O, so));
+  tg_status e = drive_cg_on(X, so, iter, P.dev, P.ns, X->prm.maxit_diff, X->prev_it_diff, host,
+                            X->ox_chunk, X->ox_slot);
+  if (e != TG_OK) return e;
+  const CgScal& ho = P.df ? host[0] : host[1];
+  if (P.df) {
+    CK(launch_ox_finish(X->G, P.O, so));
     X->launches += 1;
   } else if (ho.status == CG_ZERO_RHS) {
-    CK(cudaMemsetAsync(C.x[1], 0, (size_t)X->G.nvox * sizeof(double), so));
+    CK(cudaMemsetAsync(P.C.x[1], 0, (size_t)X->G.nvox * sizeof(double), so));
   }
   CK(cudaEventRecord(X->join_ev, so));
   CK(cudaStreamWaitEvent(X->stream, X->join_ev, 0));
+  X->ox_running = false;
   X->prev_it_diff = ho.it;
   if (stats) {
     stats->it_diff[1] = ho.it;
@@ -922,6 +946,17 @@ tg_status cn_solve_mixed_concurrent(tg_ctx* X, tg_stats* stats) {
   e = status_of(ho);
   return e == TG_OK ? TG_OK : fail(X, e);
 }
+
+// on an early return between ox_begin and ox_end: wait for the side stream's work
+struct OxGuard {
+  tg_ctx* X;
+  ~OxGuard() {
+    if (X->ox_running) {
+      cudaStreamSynchronize(X->side);
+      X->ox_running = false;
+    }
+  }
+};
 
 // The interleaved inputs of the FP32 transport.  The FP32 arrays are consecutive, each at
 // least nvox * 4 bytes and 256-byte aligned, so four of them hold one float4 per voxel.
@@ -1225,6 +1260,13 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
     CK(launch_to_f32(G.nvox, cp, s));
     X->launches += 1;
   }
+  // the mixed oxygen solve needs only the faces and o: it starts now, beside S1 and S2
+  OxGuard ox_guard{X};
+  const bool ox_side = X->prec == TG_MIXED && !single_species(X);
+  if (ox_side) {
+    const tg_status e0 = ox_begin(X);
+    if (e0 != TG_OK) return e0;
+  }
   // S1: semi-Lagrangian transport with v^n
   const double* const v[3] = {S.v[0], S.v[1], S.v[2]};
   const double* const qin[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
@@ -1258,7 +1300,8 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   if (single) {
     e = X->prec == TG_MIXED ? cn_solve3_mixed(X, stats, 1) : cn_solve3(X, stats, 1);
   } else if (X->prec == TG_MIXED) {
-    e = cn_solve_mixed_concurrent(X, stats);
+    e = cn_solve3_mixed(X, stats, CN_MIXED_MASK);   // i and l; the oxygen runs on the side
+    if (e == TG_OK) e = ox_end(X, stats);
   } else {
     e = cn_solve3(X, stats);
   }
