@@ -84,7 +84,7 @@ def mixed_kernel_bytes(n, precond):
         "k_lame": 80,                # 7 species in; mu, lambda, eta out
         "k_elas_coef_df": 128,       # mu, lambda, p + n pairs, eta in; F, G, diagonal, b pairs out
         "k_elas32_coef": 48,         # u (3) in; u pairs out
-        "k_elas_extrapolate": 120,   # u, v, v^{n-1} in; u, du out
+        "k_elas_extrapolate": 144,   # u, v, v^{n-1} in; u, du, u pairs out
         "k_spec_mean": 24,           # mu, lambda, eta in
         "k_elas_ir_residual_df": 160,  # u, F, G, diagonal, b pairs (3 each), mu, lambda pairs
         #                                in; r, e (FP32) out

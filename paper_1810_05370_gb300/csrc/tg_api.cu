@@ -1012,16 +1012,19 @@ tg_status elas_solve_mixed(tg_ctx* X, double* const u[3], double* const b_ext[3]
   }
   k_cg_reset<<<1, 32, 0, X->stream>>>(Sout, 1, X->prm.rtol_elas, X->prm.maxit_elas);
   CK(cudaGetLastError());
-  // with the double-FP32 residual the node coefficients came with the faces; only the
-  // (extrapolated) starting u is packed here
-  CK(launch_elas32_coef(X->G, E, I, X->stream,
-                        X->df_res ? ELAS32_U : ELAS32_NODES | ELAS32_DINV | ELAS32_U));
-  X->launches += 2;
+  // with the double-FP32 residual the node coefficients came with the faces, and the
+  // extrapolation wrote the pairs of a step's starting u; otherwise u is packed here
+  if (!(X->df_res && inv_dt > 0.0)) {
+    CK(launch_elas32_coef(X->G, E, I, X->stream,
+                          X->df_res ? ELAS32_U : ELAS32_NODES | ELAS32_DINV | ELAS32_U));
+    X->launches += 1;
+  }
+  X->launches += 1;
   const bool spec = spectral_on(X);
   Spec<float> V = X->sp32;   // the scaled preconditioner's view carries s
   if (spec) {
     CK(launch_spec_mean(X->G.nvox, E.mu, E.lam, E.eta, V.mean, V.partial, V.counter,
-                        X->stream));
+                        X->stream, true));
     X->launches += 1;
     if (X->prm.precond_elas == TG_PRECOND_SPECTRAL_SCALED) {
       for (int d = 0; d < 3; ++d) V.s[d] = X->s32[d];
@@ -1097,7 +1100,7 @@ tg_status elas_solve(tg_ctx* X, double* const u[3], double* const b_ext[3], bool
   Spec<double> V = X->sp64;   // the scaled preconditioner's view carries s
   if (spec) {
     CK(launch_spec_mean(X->G.nvox, E.mu, E.lam, E.eta, V.mean, V.partial, V.counter,
-                        X->stream));
+                        X->stream, false));
     if (X->prm.precond_elas == TG_PRECOND_SPECTRAL_SCALED) {
       for (int d = 0; d < 3; ++d) V.s[d] = X->s64[d];
       CK(launch_spec_scale(X->G, V, E, X->stream));

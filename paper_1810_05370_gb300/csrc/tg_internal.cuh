@@ -604,9 +604,11 @@ cudaError_t spec_prepare(const Spec<R>&);   // shared-memory limits of the pass 
 // V.s = (D0 / D)^{1/2} from E.dsum and the means (TG_PRECOND_SPECTRAL_SCALED)
 template <typename R>
 cudaError_t launch_spec_scale(const Geo&, const Spec<R>& V, const Elas& E, cudaStream_t st);
+// the domain means of mu, lambda, eta; fp32_terms: each thread's terms summed in FP32 (the
+// mixed precision), else every term in FP64
 cudaError_t launch_spec_mean(long long n, const double* mu, const double* lam,
                              const double* eta, double* mean, double* partial,
-                             unsigned int* counter, cudaStream_t st);
+                             unsigned int* counter, cudaStream_t st, bool fp32_terms);
 template <typename R>
 cudaError_t launch_spectral(const Spec<R>&, const R* const r[3], R* const z[3], CgScal* S,
                             cudaStream_t st, const PUpd<R>* pu = nullptr);

@@ -182,8 +182,10 @@ __global__ void __launch_bounds__(NT) k_elas_extrapolate(long long n, Elas E, do
         const Df v = df_split(E.v[a][c]);
         const Df w = quadratic ? df_add(v, df_sub(v, df_split(E.vp[a][c]))) : v;
         const double s = df_value(df_mul(dtd, w));
-        E.u[a][c] = E.u[a][c] + s;
+        const double un = E.u[a][c] + s;
+        E.u[a][c] = un;
         E.du[a][c] = s;
+        E.udf[a][c] = df_pack(un);   // the pairs the double-FP32 residual reads
       }
     }
     return;

@@ -1118,16 +1118,32 @@ __global__ void k_spec_tables(Spec<R> V, double h0, double h1, double h2) {
   }
 }
 
+template <bool F32>
 __global__ void __launch_bounds__(NT) k_spec_mean(long long n, const double* __restrict__ mu,
                                                   const double* __restrict__ lam,
                                                   const double* __restrict__ eta, double* mean,
                                                   double* partial, unsigned int* counter) {
+  // F32 (the mixed precision): a thread's terms summed in FP32 from FP32 values converted on
+  // the integer pipes (the means only shape the preconditioner), threads and blocks in FP64;
+  // otherwise every term in FP64, as the oracle forms the means
   double acc[3] = {0.0, 0.0, 0.0};
+  float fa[3] = {0.0f, 0.0f, 0.0f};
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-    acc[0] += mu[e];
-    acc[1] += lam[e];
-    acc[2] += eta[e];
+    if (F32) {
+      fa[0] += f32_of(mu[e]);
+      fa[1] += f32_of(lam[e]);
+      fa[2] += f32_of(eta[e]);
+    } else {
+      acc[0] += mu[e];
+      acc[1] += lam[e];
+      acc[2] += eta[e];
+    }
+  }
+  if (F32) {
+    acc[0] = (double)fa[0];
+    acc[1] = (double)fa[1];
+    acc[2] = (double)fa[2];
   }
   double out[3];
   if (reduce_indexed<3>(acc, partial, counter, blockIdx.x, gridDim.x, out) && threadIdx.x == 0) {
@@ -1247,11 +1263,15 @@ cudaError_t launch_spec_tables(const Spec<R>& V, const double h[3], cudaStream_t
 
 cudaError_t launch_spec_mean(long long n, const double* mu, const double* lam,
                              const double* eta, double* mean, double* partial,
-                             unsigned int* counter, cudaStream_t st) {
+                             unsigned int* counter, cudaStream_t st, bool fp32_terms) {
   const long long want = (n + NT - 1) / NT;
   const int blocks = (int)(want < 1024 ? (want > 0 ? want : 1) : 1024);
-  TG_TIMED(K_SPEC_MEAN, st,
-           k_spec_mean<<<blocks, NT, 0, st>>>(n, mu, lam, eta, mean, partial, counter));
+  if (fp32_terms)
+    TG_TIMED(K_SPEC_MEAN, st,
+             k_spec_mean<true><<<blocks, NT, 0, st>>>(n, mu, lam, eta, mean, partial, counter));
+  else
+    TG_TIMED(K_SPEC_MEAN, st,
+             k_spec_mean<false><<<blocks, NT, 0, st>>>(n, mu, lam, eta, mean, partial, counter));
   return cudaGetLastError();
 }
 
