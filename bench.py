@@ -531,14 +531,9 @@ def main():
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                for k in FIELDS:
-                    sim.state[k].copy_(host[k], non_blocking=True)
-            sim.step(args.dt)
-            with torch.cuda.stream(stream):
-                for k in FIELDS:
-                    host[k].copy_(sim.state[k], non_blocking=True)
-            stream.synchronize()
+            # the state up from pinned host memory, one step, the new state down: the
+            # library overlaps the copies with the step's phases (tg_step_host)
+            sim.step_host(host, host, args.dt)
         barrier()
         secs = time.perf_counter() - t0
         if dist is not None:

@@ -175,6 +175,18 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
  * that receives the step's forward values for tg_adjoint_step.  stats may be NULL. */
 tg_status tg_step(tg_ctx* ctx, double dt, int32_t nsteps, void* tape, tg_stats* stats);
 
+/* One step of dt for a caller whose state lives in host memory.  in and out hold HOST
+ * pointers (page-locked for asynchronous copies; pageable memory works but copies
+ * synchronously), one array of nvox doubles per field in the layout of tg_state; they may be
+ * the same.  The state is copied from in into the context's device state, the step runs
+ * (tg_step, no tape), and the new state is copied to out, bg included (unchanged).  The
+ * copies overlap the step where the split allows: u goes up on a copy stream while S0-S5
+ * run (only S6 reads it) and p, i, n, g, w, f, o, l, bg come down while S6-S7 run (nothing
+ * after S5 changes them); the other fields go up before S0, and u, v come down after S7.
+ * Returns once out holds the new state.  Errors as tg_step. */
+tg_status tg_step_host(tg_ctx* ctx, const tg_state* in, tg_state* out, double dt,
+                       tg_stats* stats);
+
 /* Discrete adjoint of one step (the paper's stated next goal, adjoint-based parameter
  * estimation, Section 5).  tape holds what tg_step recorded for this step.  lam holds the
  * adjoint of every state field after the step (device arrays, bg ignored) and is

@@ -102,6 +102,7 @@ def _load():
         "tg_init": (C.c_int, [P(tg_grid), P(tg_params), C.c_int, P(tg_state), C.c_void_p,
                               C.c_size_t, C.c_void_p, C.c_uint32, P(C.c_void_p), P(tg_stats)]),
         "tg_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, P(tg_stats)]),
+        "tg_step_host": (C.c_int, [C.c_void_p, P(tg_state), P(tg_state), C.c_double, P(tg_stats)]),
         "tg_solve_elasticity": (C.c_int, [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(tg_stats)]),
         "tg_set_params": (C.c_int, [C.c_void_p, P(tg_params)]),
         "tg_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -239,6 +240,15 @@ def tg_adjoint_init(ctx, lam_u_ptrs, grad):
     rc = lib.tg_adjoint_init(ctx, u, grad)
     if rc != TG_OK:
         raise TGError(rc, "tg_adjoint_init")
+
+
+def tg_step_host(ctx, state_in, state_out, dt):
+    st = tg_stats()
+    rc = lib.tg_step_host(ctx, C.byref(state_in), C.byref(state_out), C.c_double(dt),
+                          C.byref(st))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_step_host")
+    return stats_dict(st)
 
 
 def tg_step(ctx, dt, nsteps=1, tape_ptr=None):

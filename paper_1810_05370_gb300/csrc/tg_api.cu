@@ -428,6 +428,12 @@ struct tg_ctx {
   // chunk of iterations and profiler slot (ox_begin) until ox_end drives the rest and joins
   bool ox_running;
   int ox_chunk, ox_slot;
+  // tg_step_host: the caller's host copies of the state and the copy stream that moves u up
+  // during S0-S5 and the species down during S6-S7
+  const tg_state* host_in;
+  tg_state* host_out;
+  cudaStream_t copy;
+  cudaEvent_t entry_ev, up_ev[4], s5_ev;
   int broken;
   int prev_it_diff;
   int prev_it_elas;
@@ -900,6 +906,7 @@ tg_status ox_begin(tg_ctx* X) {
   const OxParts P = ox_parts(X);
   CK(cudaEventRecord(X->fork_ev, X->stream));
   CK(cudaStreamWaitEvent(so, X->fork_ev, 0));
+  if (X->host_in) CK(cudaStreamWaitEvent(so, X->up_ev[2], 0));   // o is up (tg_step_host)
   X->ox_running = true;
   k_cg_reset<<<1, 32, 0, so>>>(P.dev, P.ns, X->prm.rtol_diff, X->prm.maxit_diff);
   CK(cudaGetLastError());
@@ -1234,6 +1241,7 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
     for (int q = 0; q < 14; ++q) REC(T_P + q, start[q]);
   }
   // S0: K faces, CN diagonal and rho from the step's start
+  if (X->host_in) CK(cudaStreamWaitEvent(s, X->up_ev[0], 0));   // g, w, f are up
   phase_mark(X, 0);
   double* const Kf[3] = {X->a[A_KF0], X->a[A_KF1], X->a[A_KF2]};
   double* const Kfdf[3] = {X->a[A_KFDF0], X->a[A_KFDF1], X->a[A_KFDF2]};
@@ -1271,6 +1279,7 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
     if (e0 != TG_OK) return e0;
   }
   // S1: semi-Lagrangian transport with v^n
+  if (X->host_in) CK(cudaStreamWaitEvent(s, X->up_ev[1], 0));   // v, p, i, n are up
   const double* const v[3] = {S.v[0], S.v[1], S.v[2]};
   const double* const qin[6] = {S.p, S.i, S.n, S.g, S.w, S.f};
   if (X->prec == TG_MIXED) {
@@ -1296,6 +1305,7 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   }
   // S2: Crank-Nicolson diffusion of i, o, l (i after transport kept for the g, w fix-up);
   // single species: of c alone
+  if (X->host_in) CK(cudaStreamWaitEvent(s, X->up_ev[2], 0));   // o, l are up
   phase_mark(X, 1);
   const bool single = single_species(X);
   CK(cudaMemcpyAsync(X->a[A_IDAG], single ? S.p : S.i, bytes, cudaMemcpyDeviceToDevice, s));
@@ -1317,6 +1327,17 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
   CK(launch_react(G, X->dp, dt, X->a[A_RHO], X->a[A_IDAG], S.p, S.i, S.n, S.g, S.w, S.o, S.l,
                   X->prec == TG_MIXED, single_species(X), s));
   X->launches += 1;
+  if (X->host_out) {   // nothing after S5 changes the species: down during S6-S7
+    CK(cudaEventRecord(X->s5_ev, s));
+    CK(cudaStreamWaitEvent(X->copy, X->s5_ev, 0));
+    double* const dst[9] = {X->host_out->p, X->host_out->i, X->host_out->n, X->host_out->g,
+                            X->host_out->w, X->host_out->f, X->host_out->o, X->host_out->l,
+                            X->host_out->bg};
+    const double* const src[9] = {S.p, S.i, S.n, S.g, S.w, S.f, S.o, S.l, S.bg};
+    for (int q = 0; q < 9; ++q)
+      CK(cudaMemcpyAsync(dst[q], src[q], bytes, cudaMemcpyDeviceToHost, X->copy));
+  }
+  if (X->host_in) CK(cudaStreamWaitEvent(s, X->up_ev[3], 0));   // bg and u are up
   // S6-S7: elasticity from the post-reaction state, then v = du / dt
   phase_mark(X, 3);
   e = build_elas_coef(X, true);
@@ -1620,6 +1641,56 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
   return TG_OK;
 }
 
+// One step with the state in host memory, the copies overlapped with the step (tg.h).
+tg_status tg_step_host(tg_ctx* X, const tg_state* in, tg_state* out, double dt,
+                       tg_stats* stats) {
+  if (!X || !in || !out) return TG_ERR_ARG;
+  if (X->broken) return TG_ERR_STATE;
+  if (!(dt > 0.0) || !isfinite(dt)) return TG_ERR_ARG;
+  CK(cudaSetDevice(X->device));
+  if (!X->copy) {
+    CK(cudaStreamCreateWithFlags(&X->copy, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&X->entry_ev, cudaEventDisableTiming));
+    for (int g = 0; g < 4; ++g) CK(cudaEventCreateWithFlags(&X->up_ev[g], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&X->s5_ev, cudaEventDisableTiming));
+  }
+  tg_state& S = X->st;
+  cudaStream_t s = X->stream;
+  const size_t bytes = (size_t)X->G.nvox * sizeof(double);
+  // up on the copy stream, after everything already queued on the context's stream, in the
+  // order the split reads the fields: S0 (g, w, f), S1 (v, p, i, n), S2 (o, l), S6 (bg, u);
+  // the step waits for each group where it first reads it
+  CK(cudaEventRecord(X->entry_ev, s));
+  CK(cudaStreamWaitEvent(X->copy, X->entry_ev, 0));
+  const double* const src[15] = {in->g, in->w, in->f, in->v[0], in->v[1], in->v[2], in->p,
+                                 in->i, in->n, in->o, in->l, in->bg, in->u[0], in->u[1],
+                                 in->u[2]};
+  double* const dst[15] = {S.g, S.w, S.f, S.v[0], S.v[1], S.v[2], S.p, S.i, S.n, S.o, S.l,
+                           S.bg, S.u[0], S.u[1], S.u[2]};
+  const int group_end[4] = {3, 9, 11, 15};
+  for (int g = 0, q = 0; g < 4; ++g) {
+    for (; q < group_end[g]; ++q)
+      CK(cudaMemcpyAsync(dst[q], src[q], bytes, cudaMemcpyHostToDevice, X->copy));
+    CK(cudaEventRecord(X->up_ev[g], X->copy));
+  }
+  X->host_in = in;
+  X->host_out = out;
+  tg_status e = tg_step(X, dt, 1, nullptr, stats);
+  X->host_in = nullptr;
+  X->host_out = nullptr;
+  if (e != TG_OK) {
+    cudaStreamSynchronize(X->copy);
+    return e;
+  }
+  for (int a = 0; a < 3; ++a) {
+    CK(cudaMemcpyAsync(out->u[a], S.u[a], bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(out->v[a], S.v[a], bytes, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(X->copy));
+  CK(cudaStreamSynchronize(s));
+  return TG_OK;
+}
+
 tg_status tg_step(tg_ctx* X, double dt, int32_t nsteps, void* tape, tg_stats* stats) {
   if (!X) return TG_ERR_ARG;
   if (X->broken) return TG_ERR_STATE;
@@ -1798,6 +1869,13 @@ void tg_free(tg_ctx* X) {
   }
   if (X->fork_ev) cudaEventDestroy(X->fork_ev);
   if (X->join_ev) cudaEventDestroy(X->join_ev);
+  if (X->copy) {
+    cudaStreamSynchronize(X->copy);
+    cudaStreamDestroy(X->copy);
+    cudaEventDestroy(X->entry_ev);
+    for (int g = 0; g < 4; ++g) cudaEventDestroy(X->up_ev[g]);
+    cudaEventDestroy(X->s5_ev);
+  }
   for (cudaEvent_t e : X->prof.ev) cudaEventDestroy(e);
   if (X->pev_ok)
     for (cudaEvent_t e : X->pev) cudaEventDestroy(e);

@@ -69,6 +69,26 @@ class Simulation:
         """nsteps steps; with a tape (uint8 CUDA tensor of tape_bytes()), record one step."""
         return _tg.tg_step(self.ctx, dt, nsteps, None if tape is None else tape.data_ptr())
 
+    def step_host(self, host_in: dict, host_out: dict, dt: float) -> dict:
+        """One step with the state in host memory: host_in / host_out map the state's keys to
+        CPU tensors (float64, contiguous, pinned for asynchronous copies; they may be the same
+        tensors).  The copies overlap the step (tg_step_host)."""
+        def cstate(h):
+            s = _tg.tg_state()
+            for k in ("p", "i", "n", "g", "w", "f", "o", "l", "bg"):
+                setattr(s, k, h[k].data_ptr())
+            for a, c in enumerate("xyz"):
+                s.u[a] = h["u" + c].data_ptr()
+                s.v[a] = h["v" + c].data_ptr()
+            return s
+        for h in (host_in, host_out):
+            for k in STATE_KEYS:
+                t = h[k]
+                if t.device.type != "cpu" or not t.is_contiguous() or t.dtype != _torch().float64 \
+                        or tuple(t.shape) != tuple(self.state[k].shape):
+                    raise ValueError(f"host state {k}: a contiguous float64 CPU tensor of the grid's shape")
+        return _tg.tg_step_host(self.ctx, cstate(host_in), cstate(host_out), dt)
+
     def tape_bytes(self) -> int:
         return _tg.tg_tape_bytes(self.grid)
 
