@@ -109,14 +109,16 @@ KERNEL_SOURCE = {"k_spec_update_xfwd": "tg_spectral.cu", "k_spec_y_fwd": "tg_spe
                  "k_spec_y_inv": "tg_spectral.cu", "k_spec_zr": "tg_spectral.cu",
                  "k_spec_x_inv_p": "tg_spectral.cu", "k_elas32_matvec_spec": "tg_mixed.cu",
                  "k_cn32_matvec": "tg_cn_mixed.cu", "k_cn32_update": "tg_cn_mixed.cu",
-                 "k_sl32": "tg_mixed.cu"}
+                 "k_cn32_neumann": "tg_cn_mixed.cu", "k_sl32": "tg_mixed.cu",
+                 "k_ox_matvec": "tg_cn_ox.cu", "k_ox_update": "tg_cn_ox.cu",
+                 "k_elas_ir_residual_df": "tg_mixed.cu"}
 
 
 def kernel_source_sha(kernel):
     import hashlib
     csrc = os.path.join(ROOT, "paper_1810_05370_gb300", "csrc")
     h = hashlib.sha256()
-    for f in (KERNEL_SOURCE.get(kernel), "tg_internal.cuh", "tg_tiles.cuh"):
+    for f in (KERNEL_SOURCE.get(kernel), "tg_internal.cuh", "tg_tiles.cuh", "tg_fpconv.cuh"):
         if f is None:
             return None
         with open(os.path.join(csrc, f), "rb") as fh:
