@@ -862,17 +862,14 @@ OxDf ox_view(tg_ctx* X) {
   return O;
 }
 
-// S2 of the mixed multispecies step: the oxygen solve on the side stream, concurrently with the
-// FP32-refined i and l solves on the context's stream.  The oxygen solve follows the FP64 CG's
-// iterates: in double-FP32 arithmetic (tg_cn_ox.cu) when the face pairs exist (cn_df), else in
-// FP64.  It has its own CG scalars (scal + 8 .. 10) and reduction buffers; the first chunk of
-// its iterations is queued before the i, l solve starts and the rest is driven after it;
-// events fork and join the streams.
-// The oxygen solve of the mixed step runs on a side stream.  It needs only the S0 faces and
+// The oxygen solve of the mixed multispecies step runs on a side stream, concurrently with the
+// FP32-refined i and l solves on the context's stream.  It follows the FP64 CG's iterates: in
+// double-FP32 arithmetic (tg_cn_ox.cu) when the face pairs exist (cn_df), else in FP64, with
+// its own CG scalars (scal + 8 .. 10) and reduction buffers.  It needs only the S0 faces and
 // o, which the transport does not touch, so it is forked right after S0 (ox_begin): its start
-// and first chunk of iterations overlap the transport (L1-bound) and then the i, l solves on
-// the context's stream; ox_end drives its remaining iterations, finishes and joins.  OxGuard
-// keeps no side-stream work alive past an early return.
+// and first chunk of iterations overlap the transport (L1-bound) and then the i, l solves;
+// ox_end drives its remaining iterations, finishes and joins.  OxGuard keeps no side-stream
+// work alive past an early return.
 struct OxParts {
   Cn3 C;
   OxDf O;
