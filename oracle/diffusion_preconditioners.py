@@ -11,7 +11,9 @@ how many PCG iterations the i solve of a step needs to reach |r| <= 1e-8 |rhs| w
   * the Neumann series of the Jacobi splitting, 2 to 4 terms (1 to 3 Jacobi sweeps; the mixed
     path's inner preconditioner uses 4 terms in one pass over memory),
   * the Chebyshev polynomial of the Jacobi-scaled operator on its Gershgorin interval
-    [1/d_max, 2 - 1/d_max] (d the CN diagonal), 1 to 3 extra sweeps.
+    [1/d_max, 2 - 1/d_max] (d the CN diagonal), 1 to 3 extra sweeps, and the same cubic
+    written on the Neumann terms y_j = N^j D^-1 r: w (y_0 + y_1) + (y_2 + y_3) with
+    w = (2 d_max - 1) / d_max^2 (the mixed path's inner preconditioner).
 The spectral inverse costs five FFT passes over the field per application; a sweep of the
 Neumann or Chebyshev polynomial costs one stencil application (all three fused into one pass
 on the GPU).
@@ -108,6 +110,13 @@ def study(n, dt=0.01, rtol=1e-8, seed=0):
             return x
         return M
 
+    def cheb_terms(r):
+        w = (2 * diag.max() - 1) / diag.max() ** 2
+        y = [r / diag]
+        for _ in range(3):
+            y.append(y[-1] - A(y[-1]) / diag)
+        return w * (y[0] + y[1]) + (y[2] + y[3])
+
     out = {"jacobi": pcg(lambda r: r / diag)}
     Kbox, Ktis = K.mean(), K[K > 0].mean()
     out["spectral, box-mean K"] = pcg(spectral(Kbox, False))
@@ -117,6 +126,7 @@ def study(n, dt=0.01, rtol=1e-8, seed=0):
         out[f"neumann, {t} terms ({t - 1} sweeps)"] = pcg(neumann(t))
     for sw in (1, 2, 3):
         out[f"chebyshev, {sw} extra sweeps"] = pcg(chebyshev(sw))
+    out["chebyshev cubic on the Neumann terms"] = pcg(cheb_terms)
     return out
 
 

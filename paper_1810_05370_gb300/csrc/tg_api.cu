@@ -183,6 +183,7 @@ struct Layout {
   size_t adj[C_COUNT];
   size_t partial, counter, scal, grad;
   size_t partial2, counter2;   // reductions of the oxygen solve running on the side stream
+  size_t dmax;                 // the CN diagonal's maximum (mixed S0), one float
   bool spectral;
   size_t sp_w, sp_z32[3], sp_z64[3], sp_s32[3], sp_s64[3], sp_tab32, sp_tab64, sp_mean,
       sp_partial, sp_counter;
@@ -219,6 +220,8 @@ Layout layout(const Geo& G, tg_precision prec, bool adjoint = false, bool spectr
   if (prec == TG_MIXED) off += round_up((size_t)G.nblocks * MAX_NV * sizeof(double));
   L.counter2 = off;
   if (prec == TG_MIXED) off += ALIGN;
+  L.dmax = off;
+  off += ALIGN;
   // spectral preconditioner: the FP32 form serves the mixed precision and the adjoint's
   // refined solves, the FP64 form the FP64 solves; one half-spectrum buffer serves both
   L.spectral = spectral;
@@ -422,6 +425,7 @@ struct tg_ctx {
   // forked from and joined to the context's stream by events, with its own reductions
   double* partial2;
   unsigned int* counter2;
+  float* dmax;   // max over nodes of the CN diagonal 1 + sum of faces, from S0 (mixed)
   cudaStream_t side;
   cudaEvent_t fork_ev, join_ev;
   // the oxygen solve of the mixed step, running on the side stream from S0 on: its first
@@ -753,6 +757,7 @@ Cn32 cn32_view(tg_ctx* X) {
     I.Kf[r] = X->b32[B_CKF0 + r];
   }
   I.dinv = X->b32[B_CDINV];
+  I.dmax = X->cn_df ? X->dmax : nullptr;
   for (int r = 0; r < 3; ++r) {
     I.z[r] = nullptr;
     I.palt[r] = X->b32[B_SL0 + r];   // the transport's inputs are free after S1
@@ -1249,8 +1254,9 @@ tg_status do_step(tg_ctx* X, double dt, tg_stats* stats) {
     float2* const pairs[3] = {reinterpret_cast<float2*>(Kfdf[0]), reinterpret_cast<float2*>(Kfdf[1]),
                               reinterpret_cast<float2*>(Kfdf[2])};
     float* const f32[3] = {X->b32[B_CKF0], X->b32[B_CKF1], X->b32[B_CKF2]};
+    CK(cudaMemsetAsync(X->dmax, 0, sizeof(float), s));
     CK(launch_diff_coef_df(G, X->dp, dt, S.g, S.w, S.f, reinterpret_cast<float2*>(X->a[A_SL0]),
-                           X->a[A_RHO], pairs, f32, X->b32[B_CDINV], s));
+                           X->a[A_RHO], pairs, f32, X->b32[B_CDINV], X->dmax, s));
     X->launches += 2;
   } else {
     CK(launch_diff_coef(G, X->dp, dt, S.g, S.w, S.f, Kf, X->a[A_DSUM_D], X->a[A_DINV_D],
@@ -1604,6 +1610,7 @@ tg_status tg_init(const tg_grid* grid, const tg_params* params, tg_precision pre
   X->scal = (CgScal*)(X->ws + L.scal);
   X->partial2 = (double*)(X->ws + L.partial2);
   X->counter2 = (unsigned int*)(X->ws + L.counter2);
+  X->dmax = (float*)(X->ws + L.dmax);
   if (cudaMemsetAsync(X->counter, 0, ALIGN, X->stream) != cudaSuccess ||
       (prec == TG_MIXED && cudaMemsetAsync(X->counter2, 0, ALIGN, X->stream) != cudaSuccess)) {
     tg_free(X);

@@ -391,13 +391,21 @@ __global__ void __launch_bounds__(NT) k_cn32_pupdate(long long n, Cn32 I) {
 }
 
 // ------------------------------------------------------------- polynomial preconditioner
-// M r = (I + N + N^2 + N^3) D^{-1} r with N = D^{-1} (D - A): the first four terms of the
-// Neumann series of A^{-1} = (I - N)^{-1} D^{-1} in the Jacobi splitting A = D - (D - A).
+// M r = q(N) D^{-1} r, a cubic in N = D^{-1} (D - A) (the Jacobi splitting A = D - (D - A)).
 // (D - A) y at a node is the sum over its six faces of the face coefficient times y at the
 // neighbour across it, so the terms y_0 = D^{-1} r, y_{j+1} = D^{-1} (D - A) y_j are three
-// Jacobi sweeps.  M is symmetric positive definite: it is D^{-1/2} q(B) D^{-1/2} with B the
-// symmetric Jacobi-scaled operator, whose spectrum lies in (0, 2) (Gershgorin), and
-// q(x) = (1 - (1 - x)^4) / x > 0 there.
+// Jacobi sweeps, and M r = w (y_0 + y_1) + (y_2 + y_3).
+//   * w = 1 is the Neumann series I + N + N^2 + N^3 of A^{-1} = (I - N)^{-1} D^{-1}.
+//   * The Chebyshev choice: with B = D^{-1/2} A D^{-1/2}, whose spectrum lies in
+//     [1/d_max, 2 - 1/d_max] (Gershgorin, the CN operator being I plus a positive
+//     semidefinite part), the cubic q minimising max |1 - x q(x)| there satisfies
+//     1 - x q(x) = T_4((1 - x)/delta) / T_4(1/delta), delta = 1 - 1/d_max; written in
+//     n = 1 - x it is q = K (1 + n)(1 - delta^2 + n^2), i.e. (scale aside, which CG ignores)
+//     w = 1 - delta^2 = (2 d_max - 1) / d_max^2.  It reduces x q(x)'s condition number about
+//     16-fold where the Neumann series reduces it 4-fold (the first orders of T_4 and of
+//     1 - (1 - x)^4 at the interval's end): 7 instead of 10 inner iterations per solve at
+//     256^3 on the oracle's operator of the synthetic brain.
+// Both are symmetric positive definite: M = D^{-1/2} q(B) D^{-1/2} with q > 0 on B's spectrum.
 //
 // The three sweeps run in one pass over memory (temporal blocking).  A block owns an
 // NM_X x NM_Y tile of (x, y) columns -- the NM_OX x NM_OY output columns and a halo of
@@ -428,6 +436,14 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
   const bool run0 = r0 >= 0 && I.S[r0].status == CG_RUNNING;
   const bool run1 = r1 >= 0 && I.S[r1].status == CG_RUNNING;
   if (!run0 && !run1) return;
+  // the weight of the first two terms (the last two weigh 1): the degree-3 Chebyshev
+  // polynomial on the Jacobi-scaled operator's Gershgorin interval when S0 measured the
+  // largest diagonal, else 1 (the Neumann series)
+  float wch = 1.0f;
+  if (I.dmax) {
+    const float dm = *I.dmax;
+    if (dm > 1.0f) wch = (2.0f * dm - 1.0f) / (dm * dm);
+  }
   __shared__ NmTile T;
   const int tx = threadIdx.x, ty = threadIdx.y, cell = ty * NM_X + tx;
   const int xo = blockIdx.x * NM_OX, yo = blockIdx.y * NM_OY;
@@ -563,7 +579,7 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
               const float ha = ax[s3] * yp[q] + axm * ym[q] + az[s3] * y2[s2][q];
               const float hb = ay[s3] * Y[cell + NM_X] + aym * Y[cell - NM_X] + lz[s3][q];
               const float y3 = di[s3] * (ha + hb);
-              const float z = ((y0[s3][q] + y1[s3][q]) + y2[s3][q]) + y3;
+              const float z = wch * (y0[s3][q] + y1[s3][q]) + (y2[s3][q] + y3);
               if (out && run[q]) {
                 zdst[q][g] = z;
                 acc[q] += rr[s3][q] * z;

@@ -101,11 +101,12 @@ __global__ void __launch_bounds__(NT) k_diff_faces_df(Geo G, Df sx, Df sy, Df sz
                                                       const float2* __restrict__ Kn,
                                                       float2* dfx, float2* dfy, float2* dfz,
                                                       float* f32x, float* f32y, float* f32z,
-                                                      float* dinv32) {
+                                                      float* dinv32, float* dmax) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
-  if (i >= G.nx || j >= G.ny) return;
-  const int k0 = blockIdx.z * G.zc, k1 = min(G.nz, k0 + G.zc);
+  float dm = 0.0f;   // the largest diagonal this thread formed
+  const bool on = i < G.nx && j < G.ny;
+  const int k0 = blockIdx.z * G.zc, k1 = on ? min(G.nz, k0 + G.zc) : k0;
   for (int k = k0; k < k1; ++k) {
     const Nbr nb = make_nbr(G, i, j, k);
     const long long c = nb.at(0, 0, 0);
@@ -127,6 +128,18 @@ __global__ void __launch_bounds__(NT) k_diff_faces_df(Geo G, Df sx, Df sy, Df sz
     const Df d = df_add(df_add(df_add(Df{1.0f, 0.0f}, df_add(fxp, fxm)), df_add(fyp, fym)),
                         df_add(fzp, fzm));
     dinv32[c] = 1.0f / d.hi;
+    dm = fmaxf(dm, d.hi);
+  }
+  // the block's maximum into *dmax (positive floats order as their bit patterns)
+  for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+  __shared__ float wmax[NT / 32];
+  const int lane = (threadIdx.y * BX + threadIdx.x) & 31, warp = (threadIdx.y * BX + threadIdx.x) >> 5;
+  if (lane == 0) wmax[warp] = dm;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    float b = 0.0f;
+    for (int q = 0; q < NT / 32; ++q) b = fmaxf(b, wmax[q]);
+    atomicMax(reinterpret_cast<unsigned int*>(dmax), __float_as_uint(b));
   }
 }
 
@@ -246,7 +259,7 @@ cudaError_t launch_diff_coef(const Geo& G, const DevParams& P, double dt, const 
 cudaError_t launch_diff_coef_df(const Geo& G, const DevParams& P, double dt, const double* g,
                                 const double* w, const double* f, float2* Kn, double* rho,
                                 float2* const Kfdf[3], float* const Kf32[3], float* dinv32,
-                                cudaStream_t st) {
+                                float* dmax, cudaStream_t st) {
   TG_TIMED(K_DIFF_NODE_DF, st,
            k_diff_node_df<<<G.grid, dim3(BX, BY), 0, st>>>(G, P, g, w, f, Kn, rho));
   const Df sx = df_split_host(0.5 * dt * G.ih2[0]), sy = df_split_host(0.5 * dt * G.ih2[1]),
@@ -254,7 +267,7 @@ cudaError_t launch_diff_coef_df(const Geo& G, const DevParams& P, double dt, con
   TG_TIMED(K_DIFF_FACES_DF, st,
            k_diff_faces_df<<<G.grid, dim3(BX, BY), 0, st>>>(G, sx, sy, sz, Kn, Kfdf[0], Kfdf[1],
                                                             Kfdf[2], Kf32[0], Kf32[1], Kf32[2],
-                                                            dinv32));
+                                                            dinv32, dmax));
   return cudaGetLastError();
 }
 

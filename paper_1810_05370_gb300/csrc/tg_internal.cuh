@@ -422,6 +422,7 @@ struct Cn32 {
                        // p[k & 1 ? p : palt], reading the other)
   const float* Kf[3];
   const float* dinv;
+  const float* dmax;   // the CN diagonal's maximum (for the polynomial's weights), or null
   CgScal* S;           // 3 inner solves
   double* partial;
   unsigned int* counter;
@@ -525,7 +526,7 @@ __device__ __forceinline__ float2 df_pack(double x) {
 cudaError_t launch_diff_coef_df(const Geo&, const DevParams&, double dt, const double* g,
                                 const double* w, const double* f, float2* Kn, double* rho,
                                 float2* const Kfdf[3], float* const Kf32[3], float* dinv32,
-                                cudaStream_t st);
+                                float* dmax, cudaStream_t st);
 
 // 4 h_A h_D [ d_D(mu d_A u_D) + d_A(lambda d_D u_D) ] at the centre node (centred differences)
 template <int A, int D>
