@@ -105,19 +105,19 @@ def mixed_kernel_bytes(n, precond):
 # of a single kernel, per voxel, with the hash of the source it was measured on: reported
 # only while the kernel's source (its .cu file and the shared headers) is unchanged.
 MEASURED_TRAFFIC = {   # 256^3 mixed step, profiles/launches_mixed_spectral_256.md
-    "k_cn32_neumann": {"bytes_per_voxel": 31.8, "sha": "bccd5caea75ab20c"},
-    "k_cn32_matvec": {"bytes_per_voxel": 40.2, "sha": "bccd5caea75ab20c"},
-    "k_cn32_update": {"bytes_per_voxel": 43.1, "sha": "bccd5caea75ab20c"},
-    "k_spec_update_xfwd": {"bytes_per_voxel": 85.8, "sha": "b9cdf1b534fcc624"},
-    "k_elas32_matvec_spec": {"bytes_per_voxel": 32.3, "sha": "6acdadc44a1c6c74"},
-    "k_spec_x_inv_p": {"bytes_per_voxel": 42.3, "sha": "b9cdf1b534fcc624"},
-    "k_spec_y_fwd": {"bytes_per_voxel": 19.9, "sha": "b9cdf1b534fcc624"},
-    "k_spec_y_inv": {"bytes_per_voxel": 19.9, "sha": "b9cdf1b534fcc624"},
-    "k_spec_zr": {"bytes_per_voxel": 20.4, "sha": "b9cdf1b534fcc624"},
-    "k_elas_ir_residual_df": {"bytes_per_voxel": 166.7, "sha": "6acdadc44a1c6c74"},
-    "k_ox_matvec": {"bytes_per_voxel": 48.0, "sha": "982c941edc623918"},
-    "k_ox_update": {"bytes_per_voxel": 53.7, "sha": "982c941edc623918"},
-    "k_sl32": {"bytes_per_voxel": 97.5, "sha": "6acdadc44a1c6c74"},
+    "k_spec_update_xfwd": {"bytes_per_voxel": 93.6, "sha": "5267b4e010f82a4f"},
+    "k_elas32_matvec_spec": {"bytes_per_voxel": 35.2, "sha": "2ab33a9920771825"},
+    "k_spec_x_inv_p": {"bytes_per_voxel": 47.2, "sha": "5267b4e010f82a4f"},
+    "k_spec_y_fwd": {"bytes_per_voxel": 22.3, "sha": "5267b4e010f82a4f"},
+    "k_spec_y_inv": {"bytes_per_voxel": 22.3, "sha": "5267b4e010f82a4f"},
+    "k_spec_zr": {"bytes_per_voxel": 22.9, "sha": "5267b4e010f82a4f"},
+    "k_cn32_neumann": {"bytes_per_voxel": 32.6, "sha": "5595ba70ae2bca9e"},
+    "k_cn32_matvec": {"bytes_per_voxel": 40.6, "sha": "5595ba70ae2bca9e"},
+    "k_cn32_update": {"bytes_per_voxel": 45.2, "sha": "5595ba70ae2bca9e"},
+    "k_elas_ir_residual_df": {"bytes_per_voxel": 166.8, "sha": "2ab33a9920771825"},
+    "k_ox_matvec": {"bytes_per_voxel": 48.0, "sha": "7e0b44dea056458d"},
+    "k_ox_update": {"bytes_per_voxel": 53.7, "sha": "7e0b44dea056458d"},
+    "k_sl32": {"bytes_per_voxel": 97.5, "sha": "2ab33a9920771825"},
 }
 KERNEL_SOURCE = {"k_spec_update_xfwd": "tg_spectral.cu", "k_spec_y_fwd": "tg_spectral.cu",
                  "k_spec_y_inv": "tg_spectral.cu", "k_spec_zr": "tg_spectral.cu",
