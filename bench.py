@@ -255,6 +255,18 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_rate(ms_local, units_per_rank, world, dist=None, device=None):
+    """Whole-job throughput of `world` replicas (one per GPU, no data-path collective): every
+    rank's units over the slowest rank's time.  Returns (max ms, units per second)."""
+    ms = ms_local
+    if dist is not None:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -476,13 +488,7 @@ def main():
         agg["clocks"] = clocks.stop() if clocks is not None else None
         agg["kernels"] = sim.kernel_times()
         sim.set_timing(False)
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        agg["ms"] = ms
-        agg["value"] = world * V * args.steps / (ms * 1e-3)
+        agg["ms"], agg["value"] = job_rate(e0.elapsed_time(e1), V * args.steps, world, dist, dev)
         return agg
 
     clocks = Clocks(local)
@@ -551,12 +557,8 @@ def main():
             # library overlaps the copies with the step's phases (tg_step_host)
             sim.step_host(host, host, args.dt)
         barrier()
-        secs = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([secs], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            secs = float(t.item())
-        e2e = {"value": world * V * args.steps / secs, "unit": UNIT,
+        _, e2e_rate = job_rate(1e3 * (time.perf_counter() - t0), V * args.steps, world, dist, dev)
+        e2e = {"value": e2e_rate, "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     # ---------------------------------------------------------------- the other precision

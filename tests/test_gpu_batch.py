@@ -153,3 +153,30 @@ def test_concurrent_batch_member_failure_stops_the_batch(torch_cuda):
         batch.step(0.01)
     assert e.value.status == _tg.TG_ERR_STATE
     batch.close()
+
+
+def test_concurrent_batch_workload_sizes(torch_cuda):
+    """Members drawn from the batched workload's own generator (64^3, 96^3, 128^3 grids, rho and
+    k_scale varying), the spectral preconditioner where the grid allows it: bit-identical to
+    the same simulations run alone for two steps."""
+    from paper_1810_05370_gb300 import Simulation
+    from paper_1810_05370_gb300.batch import Batch
+    from synth import batch_workload
+    spec = batch_workload(12)
+    picked = {}
+    for n, P, seed in spec:
+        picked.setdefault(n, (n, P, seed))
+    members = [picked[n] for n in sorted(picked)]
+    assert [m[0] for m in members] == [64, 96, 128]
+    members = [(n, _spectral_or_jacobi(n, P), seed) for n, P, seed in members]
+    batch = Batch([(n, P, initial_state(n, seed)) for n, P, seed in members], concurrent=True)
+    batch.step(0.01, nsteps=2)
+    for s, (n, P, seed) in enumerate(members):
+        sim = Simulation(n, P, initial_state(n, seed), precision="mixed")
+        sim.step(0.01, nsteps=2)
+        single = sim.numpy()
+        sim.close()
+        got = batch.numpy(s)
+        for k in FIELDS:
+            assert np.array_equal(got[k], single[k]), (n, k)
+    batch.close()
