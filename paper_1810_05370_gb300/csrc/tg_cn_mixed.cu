@@ -425,7 +425,7 @@ constexpr int NM_OX = NM_X - 2 * NM_H, NM_OY = NM_Y - 2 * NM_H;
 constexpr int NM_CELLS = NM_X * NM_Y;
 
 struct NmTile {
-  float y[3][2][2][NM_CELLS];   // terms 0..2: [term][plane parity][slot][cell]
+  float2 y[3][2][NM_CELLS];     // terms 0..2 of the two solves: [term][plane parity][cell]
   float ay[4][NM_CELLS];        // y faces of the last four planes (index plane & 3)
   double red[NM_CELLS / 32][2];
   bool last;
@@ -449,19 +449,29 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
   const int xo = blockIdx.x * NM_OX, yo = blockIdx.y * NM_OY;
   const int gxu = xo - NM_H + tx, gyu = yo - NM_H + ty;   // unwrapped tile coordinates
   const int gx = ((gxu % G.nx) + G.nx) % G.nx, gy = ((gyu % G.ny) + G.ny) % G.ny;
-  const long long col = (long long)gy * G.nx + gx;
-  auto inside = [&](int j) { return tx >= j && tx < NM_X - j && ty >= j && ty < NM_Y - j; };
-  const bool in1 = inside(1), in2 = inside(2), in3 = inside(3);
-  const bool out = in3 && gxu < G.nx && gyu < G.ny;   // each output column written once
+  // 32-bit offsets (the launch checks nvox < 2^31)
+  const unsigned nxy = (unsigned)(G.nx * G.ny), nvox = nxy * (unsigned)G.nz;
+  const unsigned col = (unsigned)(gy * G.nx + gx);
+  // Term j is formed on the rows j .. NM_Y - 1 - j (a warp is a row, so the test is uniform
+  // over a warp and the shuffles inside it see every lane).  Its lanes tx < j and
+  // tx >= NM_X - j form values from wrapped shuffles that only the same outer lanes of the
+  // next term read, never an output column; likewise the terms formed in the first and last
+  // steps of the march, from planes whose lower terms do not exist yet, feed only terms of
+  // planes outside the output range.
+  const bool row1 = ty >= 1 && ty < NM_Y - 1, row2 = ty >= 2 && ty < NM_Y - 2;
+  const bool row3 = ty >= 3 && ty < NM_Y - 3;
+  const bool out = row3 && tx >= NM_H && tx < NM_X - NM_H && gxu < G.nx && gyu < G.ny;
   const int k0 = blockIdx.z * zc, k1 = min(G.nz, k0 + zc);
   const bool run[2] = {run0, run1};
-  const int rs[2] = {run0 ? r0 : 0, run1 ? r1 : 0};
-  const float* const rsrc[2] = {I.r[run0 ? r0 : 0] + col, I.r[run1 ? r1 : 0] + col};
-  float* const zdst[2] = {I.z[run0 ? r0 : 0] + col, I.z[run1 ? r1 : 0] + col};
-  const float* const kfx = I.Kf[0] + col;
-  const float* const kfy = I.Kf[1] + col;
-  const float* const kfz = I.Kf[2] + col;
-  const float* const dsrc = I.dinv + col;
+  // a solve that does not run reads the other one's residual (its z is neither stored nor
+  // summed), so the loads need no test
+  const int ld[2] = {run0 ? r0 : r1, run1 ? r1 : r0};
+  const float* const rsrc[2] = {I.r[ld[0]], I.r[ld[1]]};
+  float* const zdst[2] = {I.z[ld[0]], I.z[ld[1]]};
+  const float* const kfx = I.Kf[0];
+  const float* const kfy = I.Kf[1];
+  const float* const kfz = I.Kf[2];
+  const float* const dsrc = I.dinv;
   // rings over the last four planes, slot = (plane - tb) & 3 with tb = k0 - NM_H; the shared
   // planes of the terms alternate with (plane - tb) & 1, the y faces with (plane - tb) & 3
   float y0[4][2], y1[4][2], y2[4][2], rr[4][2], lz[4][2];   // lz: a_z(k-1) y_2(k-1) of plane k
@@ -478,23 +488,24 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
   float pr[2][2], pax[2], pay[2], paz[2], pdi[2];
   const int tb = k0 - NM_H;
   const int nsteps = (k1 - k0 + 2 * NM_H + 3) & ~3;     // a multiple of 4
-  // wrapped plane indices of the next fetch and of the output (t - 3), advanced per step
-  int kf = ((tb % G.nz) + G.nz) % G.nz;
-  int ko = k0;   // the first output plane (k0 < nz), written at rel = 2 NM_H
+  // offsets of the next fetched plane and of the output plane (t - 3), advanced per step
+  unsigned fo = (unsigned)(((tb % G.nz) + G.nz) % G.nz) * nxy;
+  unsigned zo = (unsigned)k0 * nxy;   // the first output plane (k0 < nz), written at rel = 2 NM_H
   auto fetch = [&](int set) {
-    const long long g = (long long)kf * G.nxy;
+    const unsigned o = fo + col;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) pr[set][q] = run[q] ? __ldg(rsrc[q] + g) : 0.0f;
-    pax[set] = __ldg(kfx + g);
-    pay[set] = __ldg(kfy + g);
-    paz[set] = __ldg(kfz + g);
-    pdi[set] = __ldg(dsrc + g);
-    kf = kf + 1 == G.nz ? 0 : kf + 1;
+    for (int q = 0; q < 2; ++q) pr[set][q] = __ldg(rsrc[q] + o);
+    pax[set] = __ldg(kfx + o);
+    pay[set] = __ldg(kfy + o);
+    paz[set] = __ldg(kfz + o);
+    pdi[set] = __ldg(dsrc + o);
+    fo += nxy;
+    if (fo == nvox) fo = 0u;
   };
   fetch(0);
   fetch(1);
-  // term j is formed on plane t - j while t - j lies in [k0 - 3 + j, k1 + 2 - j], i.e. while
-  // the step's offset rel = t - tb lies in [2 j, k1 - k0 + 5]; the output needs rel >= 6
+  // the output of plane t - 3 is kept for the steps whose offset rel = t - tb lies in
+  // [2 NM_H, k1 - k0 + 2 NM_H - 1]
   const int rel_end = k1 - k0 + 2 * NM_H - 1;
   for (int m4 = 0; m4 < nsteps; m4 += 4) {
 #pragma unroll
@@ -512,34 +523,31 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
       if (rel + 2 < nsteps) fetch(ps);
       // term 0 on plane t, the whole tile
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        y0[s0][q] = di[s0] * rr[s0][q];
-        T.y[0][p0][q][cell] = y0[s0][q];
-      }
+      for (int q = 0; q < 2; ++q) y0[s0][q] = di[s0] * rr[s0][q];
+      T.y[0][p0][cell] = make_float2(y0[s0][0], y0[s0][1]);
       T.ay[s0][cell] = ay[s0];
       // term 1 on plane t - 1
-      {
+      if (row1) {
         const float axm = __shfl_up_sync(0xffffffffu, ax[s1], 1);
-        float yp[2], ym[2];   // every lane takes part in the shuffles
+        float yp[2], ym[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           yp[q] = __shfl_down_sync(0xffffffffu, y0[s1][q], 1);
           ym[q] = __shfl_up_sync(0xffffffffu, y0[s1][q], 1);
         }
-        if (in1 && rel >= 2 && rel <= rel_end) {
-          const float aym = T.ay[s1][cell - NM_X];
+        const float aym = T.ay[s1][cell - NM_X];
+        const float2 Yp = T.y[0][p1][cell + NM_X], Ym = T.y[0][p1][cell - NM_X];
+        const float yn[2] = {Yp.x, Yp.y}, ys[2] = {Ym.x, Ym.y};
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const float* Y = T.y[0][p1][q];
-            const float ha = ax[s1] * yp[q] + axm * ym[q] + az[s1] * y0[s0][q];
-            const float hb = ay[s1] * Y[cell + NM_X] + aym * Y[cell - NM_X] + az[s2] * y0[s2][q];
-            y1[s1][q] = di[s1] * (ha + hb);
-            T.y[1][p1][q][cell] = y1[s1][q];
-          }
+        for (int q = 0; q < 2; ++q) {
+          const float ha = ax[s1] * yp[q] + axm * ym[q] + az[s1] * y0[s0][q];
+          const float hb = ay[s1] * yn[q] + aym * ys[q] + az[s2] * y0[s2][q];
+          y1[s1][q] = di[s1] * (ha + hb);
         }
+        T.y[1][p1][cell] = make_float2(y1[s1][0], y1[s1][1]);
       }
       // term 2 on plane t - 2; the z-lower term a_z(k) y_2(k) of the plane above it
-      {
+      if (row2) {
         const float axm = __shfl_up_sync(0xffffffffu, ax[s2], 1);
         float yp[2], ym[2];
 #pragma unroll
@@ -547,21 +555,20 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
           yp[q] = __shfl_down_sync(0xffffffffu, y1[s2][q], 1);
           ym[q] = __shfl_up_sync(0xffffffffu, y1[s2][q], 1);
         }
-        if (in2 && rel >= 4 && rel <= rel_end) {
-          const float aym = T.ay[s2][cell - NM_X];
+        const float aym = T.ay[s2][cell - NM_X];
+        const float2 Yp = T.y[1][p0][cell + NM_X], Ym = T.y[1][p0][cell - NM_X];
+        const float yn[2] = {Yp.x, Yp.y}, ys[2] = {Ym.x, Ym.y};
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const float* Y = T.y[1][p0][q];
-            const float ha = ax[s2] * yp[q] + axm * ym[q] + az[s2] * y1[s1][q];
-            const float hb = ay[s2] * Y[cell + NM_X] + aym * Y[cell - NM_X] + az[s3] * y1[s3][q];
-            y2[s2][q] = di[s2] * (ha + hb);
-            T.y[2][p0][q][cell] = y2[s2][q];
-            lz[s1][q] = az[s2] * y2[s2][q];   // for term 3 on plane t - 1 (two steps on)
-          }
+        for (int q = 0; q < 2; ++q) {
+          const float ha = ax[s2] * yp[q] + axm * ym[q] + az[s2] * y1[s1][q];
+          const float hb = ay[s2] * yn[q] + aym * ys[q] + az[s3] * y1[s3][q];
+          y2[s2][q] = di[s2] * (ha + hb);
+          lz[s1][q] = az[s2] * y2[s2][q];   // for term 3 on plane t - 1 (two steps on)
         }
+        T.y[2][p0][cell] = make_float2(y2[s2][0], y2[s2][1]);
       }
       // term 3 on plane t - 3, and the output there
-      {
+      if (row3) {
         const float axm = __shfl_up_sync(0xffffffffu, ax[s3], 1);
         float yp[2], ym[2];
 #pragma unroll
@@ -569,25 +576,26 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
           yp[q] = __shfl_down_sync(0xffffffffu, y2[s3][q], 1);
           ym[q] = __shfl_up_sync(0xffffffffu, y2[s3][q], 1);
         }
-        if (rel >= 2 * NM_H) {
-          if (in3 && rel <= rel_end) {
-            const float aym = T.ay[s3][cell - NM_X];
-            const long long g = (long long)ko * G.nxy;
+        const float aym = T.ay[s3][cell - NM_X];
+        const float2 Yp = T.y[2][p1][cell + NM_X], Ym = T.y[2][p1][cell - NM_X];
+        const float yn[2] = {Yp.x, Yp.y}, ys[2] = {Ym.x, Ym.y};
+        if (out && rel >= 2 * NM_H && rel <= rel_end) {
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              const float* Y = T.y[2][p1][q];
-              const float ha = ax[s3] * yp[q] + axm * ym[q] + az[s3] * y2[s2][q];
-              const float hb = ay[s3] * Y[cell + NM_X] + aym * Y[cell - NM_X] + lz[s3][q];
-              const float y3 = di[s3] * (ha + hb);
-              const float z = wch * (y0[s3][q] + y1[s3][q]) + (y2[s3][q] + y3);
-              if (out && run[q]) {
-                zdst[q][g] = z;
-                acc[q] += rr[s3][q] * z;
-              }
+          for (int q = 0; q < 2; ++q) {
+            const float ha = ax[s3] * yp[q] + axm * ym[q] + az[s3] * y2[s2][q];
+            const float hb = ay[s3] * yn[q] + aym * ys[q] + lz[s3][q];
+            const float y3 = di[s3] * (ha + hb);
+            const float z = wch * (y0[s3][q] + y1[s3][q]) + (y2[s3][q] + y3);
+            if (run[q]) {
+              zdst[q][zo + col] = z;
+              acc[q] += rr[s3][q] * z;
             }
           }
-          ko = ko + 1 == G.nz ? 0 : ko + 1;
         }
+      }
+      if (rel >= 2 * NM_H) {
+        zo += nxy;
+        if (zo == nvox) zo = 0u;
       }
       __syncthreads();
     }
@@ -633,7 +641,7 @@ __global__ void __launch_bounds__(NM_CELLS, 1) k_cn32_neumann(Geo G, Cn32 I, int
     for (int q = 0; q < 2; ++q) {
       double v = 0.0;
       for (int w = 0; w < NM_CELLS / 32; ++w) v += T.red[w][q];
-      if (run[q]) cg_after_precond(I.S[rs[q]], v);
+      if (run[q]) cg_after_precond(I.S[ld[q]], v);
     }
     *I.counter = 0u;
   }

@@ -869,8 +869,9 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 constexpr uint64_t ZR_WAIT_NS = 2000000000ull;   // 2 s for a tile that takes microseconds
 
 template <int P>
-constexpr size_t spec_smem_zr_tma() {   // tile (3 components), twiddles, barrier
-  return (size_t)(3 * 16 * P * ZR_COLS + 16 * P) * sizeof(float2) + 16;
+constexpr size_t spec_smem_zr_tma() {   // tile (3 components), twiddles, S_z and T_z, barrier
+  return (size_t)(3 * 16 * P * ZR_COLS + 16 * P) * sizeof(float2) + 2 * 16 * P * sizeof(float) +
+         16;
 }
 
 template <int P>
@@ -884,7 +885,9 @@ __global__ void __launch_bounds__(ZR_COLS * P)
   extern __shared__ __align__(1024) unsigned char zr_smem[];
   C* tile = reinterpret_cast<C*>(zr_smem);     // [component][plane][column]
   C* tw = tile + 3 * TILE;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(tw + N);
+  float* Sz = reinterpret_cast<float*>(tw + N);   // the z symbols S_z, T_z of the N modes
+  float* Tz = Sz + N;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Tz + N);
   const int c = threadIdx.x % ZR_COLS, t = threadIdx.x / ZR_COLS;
   const int kx0 = blockIdx.x * ZR_COLS, ky = blockIdx.y;
   const bool valid = kx0 + c < V.nxh;
@@ -895,7 +898,11 @@ __global__ void __launch_bounds__(ZR_COLS * P)
     for (int q = 0; q < 3; ++q) tma_load_4d(tile + q * TILE, &map, kx0, ky, 0, q, bar);
   }
   load_roots(tw, V.tw[2], N);
-  __syncthreads();                             // barrier initialised, twiddles visible
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    Sz[k] = V.S[2][k];
+    Tz[k] = V.T[2][k];
+  }
+  __syncthreads();                             // barrier initialised, tables visible
   if (!mbar_wait_bounded(bar, 0, ZR_WAIT_NS)) {
     if (threadIdx.x == 0) S->status = CG_TIMEOUT;
     mbar_wait_bounded(bar, 0, ZR_WAIT_NS);     // the copies in flight target this tile
@@ -968,7 +975,7 @@ __global__ void __launch_bounds__(ZR_COLS * P)
   const int kx = valid ? kx0 + c : 0;
   const float mu0 = (float)V.mean[0], lam0 = (float)V.mean[1], eta0 = (float)V.mean[2];
   const float cc = lam0 + mu0;
-  const float inv_vol = (float)(1.0 / ((double)V.nx * V.ny * V.nz));
+  const float inv_vol = 1.0f / ((float)V.nx * (float)V.ny * (float)V.nz);
   const float Sx = V.S[0][kx], Tx = V.T[0][kx];
   const float Sy = V.S[1][ky], Ty = V.T[1][ky];
   const float wgt = (kx == 0 || kx == V.nx / 2) ? 1.0f : 2.0f;
@@ -978,8 +985,8 @@ __global__ void __launch_bounds__(ZR_COLS * P)
 #pragma unroll
     for (int k1 = 0; k1 < P; ++k1) {
       const int kz = t + P * j + 16 * k1;
-      const float Sv[3] = {Sx, Sy, __ldg(V.S[2] + kz)};
-      const float Tv[3] = {Tx, Ty, __ldg(V.T[2] + kz)};
+      const float Sv[3] = {Sx, Sy, Sz[kz]};
+      const float Tv[3] = {Tx, Ty, Tz[kz]};
       const float base = eta0 + mu0 * (Sv[0] + Sv[1] + Sv[2]);
       const C rv[3] = {el(0, kz), el(1, kz), el(2, kz)};
       float tdt = 0.0f, dinv[3];
