@@ -195,83 +195,176 @@ __global__ void __launch_bounds__(NT) k_cn32_matvec(Geo G, Cn32 I) {
 }
 
 // The operator of an inner iteration preconditioned by the polynomial, with the p-update
-// fused: at iteration k, p = z + beta p_old (p = z at a solve's first iteration) is formed at
-// the stencil's nodes from z and the previous direction (buffer (k & 1) ? palt : p), written
-// at the thread's node into the other buffer, and q = A p, <p, q> follow (A p as in
-// k_cn32_matvec).  Each thread marches its (i, j) column through the block's z range with p of
-// planes k-1, k and the z-face below in registers; offsets are 32-bit (nvox < 2^31).
-__global__ void __launch_bounds__(NT) k_cn32_matvec_neu(Geo G, Cn32 I) {
-  bool act[3];
-  if (!active3(I, act)) return;
-  float beta[3];
-  bool first[3];
-  const float* zin[3];
-  const float* pin[3];
-  float* pout[3];
+// fused: at iteration k, p = z + beta p_old (p = z at a solve's first iteration) is formed
+// from z and the previous direction (buffer (k & 1) ? palt : p), written at the node into the
+// other buffer, and q = A p, <p, q> follow (A p as in k_cn32_matvec), for the solves r0, r1
+// (-1: none).  A block is MV_X x MV_Y columns marching up a chunk of zc planes: lanes
+// 1 .. MV_X - 2 of rows 1 .. MV_Y - 2 are its output columns and the outer lanes and rows
+// hold the neighbouring columns (periodically wrapped), so each thread forms p of its own
+// column only, one plane ahead from loads issued a step earlier, and takes the x neighbours'
+// p and x face from the neighbouring lanes (shuffles), the y neighbours' p and y face from the
+// rows above and below through shared memory (two planes, alternating; one barrier per
+// plane), and the z neighbours' from its registers.  Offsets are 32-bit (nvox < 2^31).
+constexpr int MV_X = 32, MV_Y = 16, MV_OX = MV_X - 2, MV_OY = MV_Y - 2;
+constexpr int MV_CELLS = MV_X * MV_Y;
+
+__global__ void __launch_bounds__(MV_CELLS, 2) k_cn32_matvec_neu(Geo G, Cn32 I, int r0, int r1,
+                                                                 int zc) {
+  const bool run0 = r0 >= 0 && I.S[r0].status == CG_RUNNING;
+  const bool run1 = r1 >= 0 && I.S[r1].status == CG_RUNNING;
+  if (!run0 && !run1) return;
+  const bool run[2] = {run0, run1};
+  // a solve that does not run reads the other one's vectors (nothing of it is stored)
+  const int ld[2] = {run0 ? r0 : r1, run1 ? r1 : r0};
+  float beta[2];
+  bool first[2];
+  const float* zin[2];
+  const float* pin[2];
+  float* pout[2];
+  float* qout[2];
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    first[r] = I.S[r].it == 0;
-    beta[r] = first[r] ? 0.0f : (float)I.S[r].beta;
-    const bool odd = I.S[r].it & 1;
-    zin[r] = I.z[r];
-    pin[r] = odd ? I.palt[r] : I.p[r];
-    pout[r] = odd ? I.p[r] : I.palt[r];
+  for (int q = 0; q < 2; ++q) {
+    const int it = I.S[ld[q]].it;
+    first[q] = it == 0;
+    beta[q] = first[q] ? 0.0f : (float)I.S[ld[q]].beta;
+    zin[q] = I.z[ld[q]];
+    pin[q] = (it & 1) ? I.palt[ld[q]] : I.p[ld[q]];
+    pout[q] = (it & 1) ? I.p[ld[q]] : I.palt[ld[q]];
+    qout[q] = I.q[ld[q]];
   }
-  float part[3] = {0.0f, 0.0f, 0.0f};
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  if (i < G.nx && j < G.ny) {
-    const int nx = G.nx, nxy = G.nx * G.ny, nz = G.nz;
-    const int ixp = i + 1 == nx ? 0 : i + 1, ixm = i == 0 ? nx - 1 : i - 1;
-    const int jyp = j + 1 == G.ny ? 0 : j + 1, jym = j == 0 ? G.ny - 1 : j - 1;
-    const int oc = j * nx + i, oxp = j * nx + ixp, oxm = j * nx + ixm;
-    const int oyp = jyp * nx + i, oym = jym * nx + i;
-    const int k0 = blockIdx.z * G.zc, k1 = min(nz, k0 + G.zc);
-    auto plane = [&](int k) { return (k < 0 ? k + nz : (k >= nz ? k - nz : k)) * nxy; };
-    auto pn = [&](int r, int idx) {
-      const float z = __ldg(zin[r] + idx);
-      return first[r] ? z : z + beta[r] * __ldg(pin[r] + idx);
-    };
-    float pm[3], pc[3];
-    const int bm = plane(k0 - 1), b0 = plane(k0);
+  __shared__ float sp[2][2][MV_CELLS];   // p of the step's plane: [step parity][solve][cell]
+  __shared__ float sfy[2][MV_CELLS];     // the y face above each cell, same planes
+  __shared__ double red[MV_CELLS / 32][2];
+  __shared__ bool last;
+  const int tx = threadIdx.x, ty = threadIdx.y, cell = ty * MV_X + tx;
+  const int iu = blockIdx.x * MV_OX - 1 + tx, ju = blockIdx.y * MV_OY - 1 + ty;   // unwrapped
+  const int gx = ((iu % G.nx) + G.nx) % G.nx, gy = ((ju % G.ny) + G.ny) % G.ny;
+  const unsigned nxy = (unsigned)(G.nx * G.ny), nvox = nxy * (unsigned)G.nz;
+  const unsigned col = (unsigned)(gy * G.nx + gx);
+  const bool out = tx >= 1 && tx < MV_X - 1 && ty >= 1 && ty < MV_Y - 1 && iu < G.nx && ju < G.ny;
+  const int cn = ty < MV_Y - 1 ? cell + MV_X : cell, cs = ty > 0 ? cell - MV_X : cell;
+  const int k0 = blockIdx.z * zc, k1 = min(G.nz, k0 + zc);
+  auto poff = [&](int k) {
+    return (unsigned)(k < 0 ? k + G.nz : (k >= G.nz ? k - G.nz : k)) * nxy;
+  };
+  const float* const kfx = I.Kf[0];
+  const float* const kfy = I.Kf[1];
+  const float* const kfz = I.Kf[2];
+  // p of the planes k0 - 1 and k0, z and p_old of plane k0 + 1, the faces of plane k0 and the
+  // z face below it
+  float pm[2], pc[2], nzv[2], npv[2];
+  {
+    const unsigned om = poff(k0 - 1) + col, o0 = poff(k0) + col, o1 = poff(k0 + 1) + col;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      pm[r] = act[r] ? pn(r, bm + oc) : 0.0f;
-      pc[r] = act[r] ? pn(r, b0 + oc) : 0.0f;
-    }
-    float fzm = __ldg(I.Kf[2] + bm + oc);
-    for (int k = k0; k < k1; ++k) {
-      const int b = plane(k), bn = plane(k + 1);
-      const float fxp = __ldg(I.Kf[0] + b + oc), fxm = __ldg(I.Kf[0] + b + oxm);
-      const float fyp = __ldg(I.Kf[1] + b + oc), fym = __ldg(I.Kf[1] + b + oym);
-      const float fzp = __ldg(I.Kf[2] + b + oc);
-      const float d = 1.0f + ((fxp + fxm) + (fyp + fym) + (fzp + fzm));
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        if (!act[r]) continue;
-        const float pp = pn(r, bn + oc);
-        const float q = d * pc[r] - (fxp * pn(r, b + oxp) + fxm * pn(r, b + oxm) +
-                                     fyp * pn(r, b + oyp) + fym * pn(r, b + oym) + fzp * pp +
-                                     fzm * pm[r]);
-        pout[r][b + oc] = pc[r];
-        I.q[r][b + oc] = q;
-        part[r] += pc[r] * q;
-        pm[r] = pc[r];
-        pc[r] = pp;
-      }
-      fzm = fzp;
+    for (int q = 0; q < 2; ++q) {
+      const float zm = __ldg(zin[q] + om), z0 = __ldg(zin[q] + o0);
+      pm[q] = first[q] ? zm : zm + beta[q] * __ldg(pin[q] + om);
+      pc[q] = first[q] ? z0 : z0 + beta[q] * __ldg(pin[q] + o0);
+      nzv[q] = __ldg(zin[q] + o1);
+      npv[q] = first[q] ? 0.0f : __ldg(pin[q] + o1);
     }
   }
-  double acc[3] = {(double)part[0], (double)part[1], (double)part[2]};
-  double out[3];
-  if (reduce_last_block<3>(acc, I.partial, I.counter, out) && threadIdx.x == 0 &&
-      threadIdx.y == 0) {
+  float fzm = __ldg(kfz + poff(k0 - 1) + col);
+  float fx = __ldg(kfx + poff(k0) + col), fy = __ldg(kfy + poff(k0) + col);
+  float fz = __ldg(kfz + poff(k0) + col);
+  float part[2] = {0.0f, 0.0f};
+  unsigned ob = poff(k0), o1p = poff(k0 + 1), o2p = poff(k0 + 2);   // planes k, k + 1, k + 2
+  int buf = 0;
+  for (int k = k0; k < k1; ++k) {
+    float pp[2];   // p of plane k + 1
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-      if (act[r]) {
-        I.S[r].pq = out[r];
-        I.S[r].alpha = I.S[r].rz / out[r];
+    for (int q = 0; q < 2; ++q) pp[q] = first[q] ? nzv[q] : nzv[q] + beta[q] * npv[q];
+    float nfx = 0.0f, nfy = 0.0f, nfz = 0.0f;
+    if (k + 1 < k1) {   // the next step's loads: z, p_old of plane k + 2, faces of plane k + 1
+      const unsigned o2 = o2p + col, o1 = o1p + col;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        nzv[q] = __ldg(zin[q] + o2);
+        npv[q] = first[q] ? 0.0f : __ldg(pin[q] + o2);
       }
+      nfx = __ldg(kfx + o1);
+      nfy = __ldg(kfy + o1);
+      nfz = __ldg(kfz + o1);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) sp[buf][q][cell] = pc[q];
+    sfy[buf][cell] = fy;
+    __syncthreads();
+    const float fxm = __shfl_up_sync(0xffffffffu, fx, 1);
+    const float fym = sfy[buf][cs];
+    const float d = 1.0f + ((fx + fxm) + (fy + fym) + (fz + fzm));
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float pxp = __shfl_down_sync(0xffffffffu, pc[q], 1);
+      const float pxm = __shfl_up_sync(0xffffffffu, pc[q], 1);
+      const float pyp = sp[buf][q][cn], pym = sp[buf][q][cs];
+      const float qv = d * pc[q] - (fx * pxp + fxm * pxm + fy * pyp + fym * pym + fz * pp[q] +
+                                    fzm * pm[q]);
+      if (out && run[q]) {
+        pout[q][ob + col] = pc[q];
+        qout[q][ob + col] = qv;
+        part[q] += pc[q] * qv;
+      }
+      pm[q] = pc[q];
+      pc[q] = pp[q];
+    }
+    fzm = fz;
+    fx = nfx;
+    fy = nfy;
+    fz = nfz;
+    ob = o1p;
+    o1p = o2p;
+    o2p += nxy;
+    if (o2p == nvox) o2p = 0u;
+    buf ^= 1;
+  }
+
+  // <p, q> per solve: warps, then the block's warps in order, then the blocks in order by the
+  // last block to finish
+  const int lane = cell & 31, warp = cell >> 5, nb = gridDim.x * gridDim.y * gridDim.z;
+  const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const double v = warp_sum((double)part[q]);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (cell == 0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      double v = 0.0;
+      for (int w = 0; w < MV_CELLS / 32; ++w) v += red[w][q];
+      I.partial[2 * (size_t)b + q] = v;
+    }
+    __threadfence();
+    last = atomicAdd(I.counter, 1u) == (unsigned int)(nb - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double tot[2] = {0.0, 0.0};
+  for (int k = cell; k < nb; k += MV_CELLS) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) tot[q] += __ldcg(I.partial + 2 * (size_t)k + q);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const double v = warp_sum(tot[q]);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (cell == 0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      double v = 0.0;
+      for (int w = 0; w < MV_CELLS / 32; ++w) v += red[w][q];
+      if (run[q]) {
+        I.S[ld[q]].pq = v;
+        I.S[ld[q]].alpha = I.S[ld[q]].rz / v;
+      }
+    }
+    *I.counter = 0u;
   }
 }
 
@@ -705,7 +798,19 @@ cudaError_t launch_cn32_iter(const Geo& G, const Cn32& I, cudaStream_t st, int r
   TG_TIMED(K_CN32_NEUMANN, st,
            k_cn32_neumann<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(NM_X, NM_Y), 0,
                             st>>>(G, I, r0, r1, zc));
-  TG_TIMED(K_CN32_MATVEC, st, k_cn32_matvec_neu<<<G.grid, dim3(BX, BY), 0, st>>>(G, I));
+  // the operator's grid: about as many blocks as the standard one, each block's two sums in
+  // the partial buffer
+  const long long mgx = (G.nx + MV_OX - 1) / MV_OX, mgy = (G.ny + MV_OY - 1) / MV_OY;
+  long long mgz = (G.nblocks + mgx * mgy - 1) / (mgx * mgy);
+  mgz = std::max(1LL, std::min(mgz, (long long)G.nz));
+  int mzc = (int)((G.nz + mgz - 1) / mgz);
+  while (mzc < G.nz && mgx * mgy * ((G.nz + mzc - 1) / mzc) * 2 > partial_capacity) mzc *= 2;
+  mzc = mzc < G.nz ? mzc : G.nz;
+  mgz = (G.nz + mzc - 1) / mzc;
+  if (mgx * mgy * mgz * 2 > partial_capacity) return cudaErrorInvalidValue;
+  TG_TIMED(K_CN32_MATVEC, st,
+           k_cn32_matvec_neu<<<dim3((unsigned)mgx, (unsigned)mgy, (unsigned)mgz),
+                               dim3(MV_X, MV_Y), 0, st>>>(G, I, r0, r1, mzc));
   TG_TIMED(K_CN32_UPDATE, st, k_cn32_update<true><<<flat_blocks(G), NT, 0, st>>>(G.nvox, I));
   return cudaGetLastError();
 }
