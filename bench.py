@@ -105,15 +105,15 @@ def mixed_kernel_bytes(n, precond):
 # of a single kernel, per voxel, with the hash of the source it was measured on: reported
 # only while the kernel's source (its .cu file and the shared headers) is unchanged.
 MEASURED_TRAFFIC = {   # 256^3 mixed step, profiles/launches_mixed_spectral_256.md
-    "k_spec_update_xfwd": {"bytes_per_voxel": 93.6, "sha": "5267b4e010f82a4f"},
+    "k_spec_update_xfwd": {"bytes_per_voxel": 85.1, "sha": "30ae096378a9dcaa"},
     "k_elas32_matvec_spec": {"bytes_per_voxel": 35.2, "sha": "2ab33a9920771825"},
-    "k_spec_x_inv_p": {"bytes_per_voxel": 47.2, "sha": "5267b4e010f82a4f"},
-    "k_spec_y_fwd": {"bytes_per_voxel": 22.3, "sha": "5267b4e010f82a4f"},
-    "k_spec_y_inv": {"bytes_per_voxel": 22.3, "sha": "5267b4e010f82a4f"},
-    "k_spec_zr": {"bytes_per_voxel": 22.9, "sha": "5267b4e010f82a4f"},
-    "k_cn32_neumann": {"bytes_per_voxel": 32.6, "sha": "5595ba70ae2bca9e"},
-    "k_cn32_matvec": {"bytes_per_voxel": 40.6, "sha": "5595ba70ae2bca9e"},
-    "k_cn32_update": {"bytes_per_voxel": 45.2, "sha": "5595ba70ae2bca9e"},
+    "k_spec_x_inv_p": {"bytes_per_voxel": 42.0, "sha": "30ae096378a9dcaa"},
+    "k_spec_y_fwd": {"bytes_per_voxel": 19.1, "sha": "30ae096378a9dcaa"},
+    "k_spec_y_inv": {"bytes_per_voxel": 19.1, "sha": "30ae096378a9dcaa"},
+    "k_spec_zr": {"bytes_per_voxel": 19.6, "sha": "30ae096378a9dcaa"},
+    "k_cn32_neumann": {"bytes_per_voxel": 32.6, "sha": "ee268c5807b26d8b"},
+    "k_cn32_matvec": {"bytes_per_voxel": 40.9, "sha": "ee268c5807b26d8b"},
+    "k_cn32_update": {"bytes_per_voxel": 45.3, "sha": "ee268c5807b26d8b"},
     "k_elas_ir_residual_df": {"bytes_per_voxel": 166.8, "sha": "2ab33a9920771825"},
     "k_ox_matvec": {"bytes_per_voxel": 48.0, "sha": "7e0b44dea056458d"},
     "k_ox_update": {"bytes_per_voxel": 53.7, "sha": "7e0b44dea056458d"},
