@@ -153,6 +153,15 @@ void spec_shape(const Geo& G, Spec<R>& V) {
   V.pb = std::max(1, std::min(std::min(G.ny / 2, 16), floor_pow2(65536 / (2 * G.nx * cs))));
   V.tx = std::max(1, std::min(16, floor_pow2(65536 / (2 * G.ny * cs))));
   V.tz = std::max(1, std::min(16, floor_pow2(65536 / (6 * G.nz * cs))));
+  // in place when each x-pass stage (a radix 2/4/8 stage for ln mod 4, then radix 16) has at
+  // most one butterfly per thread of a block
+  {
+    int ln = 0;
+    while ((1 << ln) < G.nx) ++ln;
+    const long long first = (long long)V.pb * G.nx >> ((ln & 3) ? (ln & 3) : 4);
+    const long long r16 = (long long)V.pb * G.nx >> 4;
+    V.x_inpl = std::max(first, r16) <= NT ? 1 : 0;
+  }
   const int items = 3 * V.tz * std::max(1, G.nz / 16);
   V.nt_z = std::max(64, std::min(NT, (items + 31) / 32 * 32));
 }

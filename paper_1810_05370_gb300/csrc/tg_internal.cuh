@@ -348,6 +348,9 @@ struct Spec {
   int nx, ny, nz, nxh, nxp;   // grid; x modes kept (nx/2 + 1); row pitch of W in modes
   int pb, tx, tz;             // row pairs per x-pass block; mode columns per y / z block
   int nt_z;                   // threads of a z-pass block
+  int x_inpl;                 // the x passes other than the fused update pass transform in
+                              // place in one line buffer (every stage's butterflies at most
+                              // one per thread of a block)
   C* W;                       // 3 components x nz x ny x nxp
   C* tw[3];                   // exp(-2 pi i k / n_d), k < n_d
   R* S[3];                    // 4 sin^2(theta_k / 2) / h_d^2, theta_k = 2 pi k / n_d
@@ -371,6 +374,9 @@ struct PUpd {
 
 // shared memory of each pass (bytes): the line length's twiddles and two line buffers
 template <typename R> size_t spec_smem_x(const Spec<R>& V) {   // lines padded to pb + 1
+  return (1 + (V.x_inpl ? 1 : 2) * ((size_t)V.pb + 1)) * V.nx * sizeof(typename CxOf<R>::T);
+}
+template <typename R> size_t spec_smem_x2(const Spec<R>& V) {   // always two line buffers
   return (1 + 2 * ((size_t)V.pb + 1)) * V.nx * sizeof(typename CxOf<R>::T);
 }
 template <typename R> size_t spec_smem_y(const Spec<R>& V) {

@@ -187,7 +187,69 @@ __device__ C* fft_lines(C* a, C* b, int ln, int llo, int hi, int ls, int es, con
   return a;
 }
 
+// The same transforms in place in one buffer, for plans whose every stage has at most one
+// butterfly per thread (the launch's shape guarantees it): a thread reads its butterfly's
+// inputs, the block synchronises, the thread writes the outputs where the ping-pong stage
+// would have written them in the other buffer, so the values are those of fft_lines bit for
+// bit.  Two barriers per stage, half the shared memory.
+template <int LR, int SGN, typename C>
+__device__ __forceinline__ void fft_stage_inplace(C* a, int ln, int lNs, int llo, int hi, int ls,
+                                                  int es, const C* tw) {
+  constexpr int R = 1 << LR;
+  const int lnb = ln - LR, nb = 1 << lnb, Ns = 1 << lNs, lts = ln - lNs - LR;
+  const int lo_mask = (1 << llo) - 1;
+  const int total = hi << (llo + lnb);
+  const int it = threadIdx.x;
+  const bool act = it < total;
+  C v[R];
+  int base = 0, d = 0;
+  if (act) {
+    const int ll = it & lo_mask;
+    const int rest = it >> llo;
+    const int j = rest & (nb - 1);
+    const int l = ((rest >> lnb) << llo) + ll;
+    const int k = j & (Ns - 1);
+    d = ((j >> lNs) << (lNs + LR)) + k;
+    base = l * ls;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = a[base + (j + r * nb) * es];
+    if (k > 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], root<SGN>(tw, (r * k) << lts));
+    }
+    dft<LR, SGN>(v);
+  }
+  __syncthreads();   // every input of the stage is read
+  if (act) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[base + (d + r * Ns) * es] = v[r];
+  }
+}
+
+template <int SGN, typename C>
+__device__ C* fft_lines_inplace(C* a, int ln, int llo, int hi, int ls, int es, const C* tw) {
+  int lNs = ln & 3;
+  if (lNs == 1) fft_stage_inplace<1, SGN>(a, ln, 0, llo, hi, ls, es, tw);
+  if (lNs == 2) fft_stage_inplace<2, SGN>(a, ln, 0, llo, hi, ls, es, tw);
+  if (lNs == 3) fft_stage_inplace<3, SGN>(a, ln, 0, llo, hi, ls, es, tw);
+  if (lNs != 0) __syncthreads();
+  for (; lNs < ln; lNs += 4) {
+    fft_stage_inplace<4, SGN>(a, ln, lNs, llo, hi, ls, es, tw);
+    __syncthreads();
+  }
+  return a;
+}
+
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
+// The x passes' transform of pb interleaved lines: FORM 0 in two buffers, 1 in place, 2 as the
+// shape's x_inpl says (the hot kernels are instantiated per form, so each holds one path)
+template <int SGN, int FORM, typename C>
+__device__ __forceinline__ const C* fft_x(bool inpl, C* a, C* b, int ln, int llo, int es,
+                                          const C* tw) {
+  if (FORM == 1 || (FORM == 2 && inpl)) return fft_lines_inplace<SGN>(a, ln, llo, 1, 1, es, tw);
+  return fft_lines<SGN>(a, b, ln, llo, 1, 1, es, tw);
+}
 
 // --------------------------------------------------- stages that read or write global memory
 // The y and z passes keep their lines interleaved both in global memory (consecutive mode
@@ -432,13 +494,13 @@ __device__ __forceinline__ XTile<R> x_tile(const Spec<R>& V) {
 }
 
 // transform the staged rows (in a) and write both half spectra to W
-template <typename R>
+template <typename R, int FORM>
 __device__ __forceinline__ void x_fwd_finish(const Spec<R>& V, const XTile<R>& t,
                                              typename CxOf<R>::T* a, typename CxOf<R>::T* b,
                                              const typename CxOf<R>::T* tw) {
   using C = typename CxOf<R>::T;
   const int n = t.n, es = t.es;
-  const C* F = fft_lines<-1>(a, b, t.ln, ilog2(t.pb), 1, 1, es, tw);
+  const C* F = fft_x<-1, FORM>(V.x_inpl != 0, a, b, t.ln, ilog2(t.pb), es, tw);
   C* W = V.W + (((size_t)t.comp * V.nz + t.z) * V.ny + t.y0) * V.nxp;
   for (int idx = threadIdx.x; idx < t.pb * V.nxh; idx += blockDim.x) {
     const int l = idx / V.nxh, k = idx - l * V.nxh;
@@ -486,7 +548,7 @@ __global__ void __launch_bounds__(NT) k_spec_x_fwd(Spec<R> V, const R* __restric
     }
   }
   __syncthreads();
-  x_fwd_finish(V, t, a, b, tw);
+  x_fwd_finish<R, 2>(V, t, a, b, tw);
 }
 
 // The mixed precision's CG update fused into the x forward pass: for the block's rows
@@ -553,7 +615,7 @@ __global__ void __launch_bounds__(NT, 4) k_spec_update_xfwd(Spec<float> V, Elas3
   if (reduce_indexed<1>(acc, V.partial, V.counter, bl, nb, out) && threadIdx.x == 0)
     cg_after_update_rr(*I.S, out[0]);   // reduce_indexed's barriers also publish the staging
   __syncthreads();
-  x_fwd_finish(V, t, a, b, tw);
+  x_fwd_finish<float, 0>(V, t, a, b, tw);   // two buffers (in place it ran slower)
 }
 
 // ---------------------------------------------------------------------------- y pass
@@ -1031,7 +1093,7 @@ __global__ void __launch_bounds__(ZR_COLS * P)
 // C[k] = A[k] + i B[k] over all k (Hermitian extension); the inverse transform is
 // a + i b.  Writes z = s (inverse transform) (s = 1 unscaled), or with PU the new search
 // direction p = z + beta p_old (beta = 0 on a solve's first iteration).
-template <typename R, bool PUP>
+template <typename R, bool PUP, int FORM>
 __global__ void __launch_bounds__(NT, PUP ? 4 : 2) k_spec_x_inv(Spec<R> V, R* z0, R* z1, R* z2,
                                                                 const CgScal* S, PUpd<R> PU) {
   using C = typename CxOf<R>::T;
@@ -1074,7 +1136,7 @@ __global__ void __launch_bounds__(NT, PUP ? 4 : 2) k_spec_x_inv(Spec<R> V, R* z0
     }
   }
   __syncthreads();
-  const C* F = fft_lines<+1>(a, b, ln, ilog2(pb), 1, 1, es, tw);
+  const C* F = fft_x<+1, FORM>(V.x_inpl != 0, a, b, ln, ilog2(pb), es, tw);
   R* out = comp == 0 ? z0 : (comp == 1 ? z1 : z2);
   const R* pold = nullptr;
   R beta = (R)0;
@@ -1214,15 +1276,16 @@ cudaError_t spec_prepare(const Spec<R>& V) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   optin -= 1024;
-  if (spec_smem_x(V) > (size_t)optin || spec_smem_y(V) > (size_t)optin ||
+  if (spec_smem_x2(V) > (size_t)optin || spec_smem_y(V) > (size_t)optin ||
       spec_smem_z(V) > (size_t)optin)
     return cudaErrorInvalidValue;
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   e = cudaFuncSetAttribute(k_spec_x_fwd<R>, A, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_update_xfwd, A, optin);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_x_inv<R, false>, A, optin);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_x_inv<R, false, 2>, A, optin);
   if constexpr (sizeof(R) == 4) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_x_inv<R, true>, A, optin);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_x_inv<R, true, 0>, A, optin);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_x_inv<R, true, 1>, A, optin);
   }
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_y<R, -1>, A, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_y<R, +1>, A, optin);
@@ -1335,13 +1398,17 @@ cudaError_t launch_spectral(const Spec<R>& V, const R* const r[3], R* const z[3]
   if constexpr (sizeof(R) == 4) {
     if (pu) {
       P = *pu;
-      TG_TIMED(K_SPEC_X_INV_P, st,
-               k_spec_x_inv<R, true><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S, P));
+      if (V.x_inpl)
+        TG_TIMED(K_SPEC_X_INV_P, st,
+                 k_spec_x_inv<R, true, 1><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S, P));
+      else
+        TG_TIMED(K_SPEC_X_INV_P, st,
+                 k_spec_x_inv<R, true, 0><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S, P));
       return cudaGetLastError();
     }
   }
   TG_TIMED(K_SPEC_X_INV, st,
-           k_spec_x_inv<R, false><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S, P));
+           k_spec_x_inv<R, false, 2><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], S, P));
   return cudaGetLastError();
 }
 
@@ -1351,15 +1418,19 @@ cudaError_t launch_spectral_update(const Spec<float>& V, const Elas32& I, float*
                                    cudaStream_t st) {
   const dim3 gx(V.ny / (2 * V.pb), V.nz, 3);
   const dim3 gy((V.nxh + V.tx - 1) / V.tx, V.nz, 3);
-  TG_TIMED(K_SPEC_UPDATE_XFWD, st, k_spec_update_xfwd<<<gx, NT, spec_smem_x(V), st>>>(V, I));
+  TG_TIMED(K_SPEC_UPDATE_XFWD, st, k_spec_update_xfwd<<<gx, NT, spec_smem_x2(V), st>>>(V, I));
   TG_TIMED(K_SPEC_Y_FWD, st, k_spec_y<float, -1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S));
   launch_spec_z(V, I.S, st);
   TG_TIMED(K_SPEC_Y_INV, st, k_spec_y<float, +1><<<gy, NT, spec_smem_y(V), st>>>(V, I.S));
   PUpd<float> P;   // p = z + beta p_old straight from the last pass
   for (int b = 0; b < 2; ++b)
     for (int a = 0; a < 3; ++a) P.p[b][a] = I.p[b][a];
-  TG_TIMED(K_SPEC_X_INV_P, st,
-           k_spec_x_inv<float, true><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], I.S, P));
+  if (V.x_inpl)
+    TG_TIMED(K_SPEC_X_INV_P, st,
+             k_spec_x_inv<float, true, 1><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], I.S, P));
+  else
+    TG_TIMED(K_SPEC_X_INV_P, st,
+             k_spec_x_inv<float, true, 0><<<gx, NT, spec_smem_x(V), st>>>(V, z[0], z[1], z[2], I.S, P));
   return cudaGetLastError();
 }
 
