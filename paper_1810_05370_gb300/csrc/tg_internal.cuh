@@ -379,8 +379,14 @@ template <typename R> size_t spec_smem_x(const Spec<R>& V) {   // lines padded t
 template <typename R> size_t spec_smem_x2(const Spec<R>& V) {   // always two line buffers
   return (1 + 2 * ((size_t)V.pb + 1)) * V.nx * sizeof(typename CxOf<R>::T);
 }
+// a y transform of at most two stages (n <= 256) stages through one buffer only
+__host__ __device__ inline int spec_y_buffers(int ny) {
+  int ln = 0;
+  while ((1 << ln) < ny) ++ln;
+  return ((ln & 3) ? 1 : 0) + (ln >> 2) <= 2 ? 1 : 2;
+}
 template <typename R> size_t spec_smem_y(const Spec<R>& V) {
-  return (1 + 2 * (size_t)V.tx) * V.ny * sizeof(typename CxOf<R>::T);
+  return (1 + (size_t)spec_y_buffers(V.ny) * V.tx) * V.ny * sizeof(typename CxOf<R>::T);
 }
 template <typename R> size_t spec_smem_z(const Spec<R>& V) {
   return (1 + 2 * (size_t)3 * V.tz) * V.nz * sizeof(typename CxOf<R>::T);

@@ -619,15 +619,15 @@ __global__ void __launch_bounds__(NT, 4) k_spec_update_xfwd(Spec<float> V, Elas3
 }
 
 // ---------------------------------------------------------------------------- y pass
-// block (mode-column tile, z, component), in place
+// block (mode-column tile, z, component), in place; the FP32 pass at four blocks per SM
 template <typename R, int SGN>
-__global__ void __launch_bounds__(NT) k_spec_y(Spec<R> V, const CgScal* S) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 0) k_spec_y(Spec<R> V, const CgScal* S) {
   using C = typename CxOf<R>::T;
   if (spec_skip<R>(S)) return;
   const int tx = V.tx, ltx = ilog2(tx);
   C* tw = smem_cx<C>();
   C* a = tw + V.ny;
-  C* b = a + (size_t)tx * V.ny;
+  C* b = spec_y_buffers(V.ny) == 1 ? a : a + (size_t)tx * V.ny;   // one or two stages: b only
   load_roots(tw, V.tw[1], V.ny);
   const int kx0 = blockIdx.x * tx, z = blockIdx.y, comp = blockIdx.z;
   const ColIO<C> io{V.W + ((size_t)comp * V.nz + z) * V.ny * V.nxp + kx0, V.nxp,
