@@ -105,27 +105,36 @@ def mixed_kernel_bytes(n, precond):
 # of a single kernel, per voxel, with the hash of the source it was measured on: reported
 # only while the kernel's source (its .cu file and the shared headers) is unchanged.
 MEASURED_TRAFFIC = {   # 256^3 mixed step, profiles/launches_mixed_spectral_256.md
-    "k_spec_update_xfwd": {"bytes_per_voxel": 85.1, "sha": "30ae096378a9dcaa"},
-    "k_elas32_matvec_spec": {"bytes_per_voxel": 35.2, "sha": "2ab33a9920771825"},
-    "k_spec_x_inv_p": {"bytes_per_voxel": 42.0, "sha": "30ae096378a9dcaa"},
-    "k_spec_y_fwd": {"bytes_per_voxel": 19.1, "sha": "30ae096378a9dcaa"},
-    "k_spec_y_inv": {"bytes_per_voxel": 19.1, "sha": "30ae096378a9dcaa"},
-    "k_spec_zr": {"bytes_per_voxel": 19.6, "sha": "30ae096378a9dcaa"},
-    "k_cn32_neumann": {"bytes_per_voxel": 32.6, "sha": "ee268c5807b26d8b"},
-    "k_cn32_matvec": {"bytes_per_voxel": 40.9, "sha": "ee268c5807b26d8b"},
-    "k_cn32_update": {"bytes_per_voxel": 45.3, "sha": "ee268c5807b26d8b"},
-    "k_elas_ir_residual_df": {"bytes_per_voxel": 166.8, "sha": "2ab33a9920771825"},
-    "k_ox_matvec": {"bytes_per_voxel": 48.0, "sha": "7e0b44dea056458d"},
-    "k_ox_update": {"bytes_per_voxel": 53.7, "sha": "7e0b44dea056458d"},
-    "k_sl32": {"bytes_per_voxel": 97.5, "sha": "2ab33a9920771825"},
+    "k_spec_update_xfwd": {"bytes_per_voxel": 85.6, "sha": "d59493db2c07f8d9"},
+    "k_elas32_matvec_spec": {"bytes_per_voxel": 32.2, "sha": "7ec7d47f12615f35"},
+    "k_spec_x_inv_p": {"bytes_per_voxel": 42.6, "sha": "d59493db2c07f8d9"},
+    "k_spec_y_fwd": {"bytes_per_voxel": 19.9, "sha": "d59493db2c07f8d9"},
+    "k_spec_y_inv": {"bytes_per_voxel": 19.4, "sha": "d59493db2c07f8d9"},
+    "k_spec_zr": {"bytes_per_voxel": 20.4, "sha": "d59493db2c07f8d9"},
+    "k_cn32_neumann": {"bytes_per_voxel": 32.6, "sha": "7336241f68141960"},
+    "k_cn32_matvec": {"bytes_per_voxel": 40.4, "sha": "7336241f68141960"},
+    "k_cn32_update": {"bytes_per_voxel": 45.3, "sha": "7336241f68141960"},
+    "k_cn_ir_residual_df": {"bytes_per_voxel": 75.9, "sha": "7336241f68141960"},
+    "k_elas_ir_residual_df": {"bytes_per_voxel": 166.7, "sha": "7ec7d47f12615f35"},
+    "k_ox_matvec": {"bytes_per_voxel": 48.0, "sha": "63e5600d8107b556"},
+    "k_ox_update": {"bytes_per_voxel": 53.7, "sha": "63e5600d8107b556"},
+    "k_ox_pupdate": {"bytes_per_voxel": 28.8, "sha": "63e5600d8107b556"},
+    "k_sl32": {"bytes_per_voxel": 97.5, "sha": "7ec7d47f12615f35"},
+    "k_sl32_pack": {"bytes_per_voxel": 118.4, "sha": "7ec7d47f12615f35"},
+    "k_elas_coef_df": {"bytes_per_voxel": 126.4, "sha": "eb3281616b3713f0"},
+    "k_react": {"bytes_per_voxel": 125.2, "sha": "8ca213d5b6f3fcea"},
+    "k_lame_df": {"bytes_per_voxel": 113.0, "sha": "8ca213d5b6f3fcea"},
 }
-KERNEL_SOURCE = {"k_spec_update_xfwd": "tg_spectral.cu", "k_spec_y_fwd": "tg_spectral.cu",
-                 "k_spec_y_inv": "tg_spectral.cu", "k_spec_zr": "tg_spectral.cu",
-                 "k_spec_x_inv_p": "tg_spectral.cu", "k_elas32_matvec_spec": "tg_mixed.cu",
-                 "k_cn32_matvec": "tg_cn_mixed.cu", "k_cn32_update": "tg_cn_mixed.cu",
-                 "k_cn32_neumann": "tg_cn_mixed.cu", "k_sl32": "tg_mixed.cu",
-                 "k_ox_matvec": "tg_cn_ox.cu", "k_ox_update": "tg_cn_ox.cu",
-                 "k_elas_ir_residual_df": "tg_mixed.cu"}
+KERNEL_SOURCE = {
+    "k_spec_update_xfwd": "tg_spectral.cu", "k_elas32_matvec_spec": "tg_mixed.cu",
+    "k_spec_x_inv_p": "tg_spectral.cu", "k_spec_y_fwd": "tg_spectral.cu",
+    "k_spec_y_inv": "tg_spectral.cu", "k_spec_zr": "tg_spectral.cu",
+    "k_cn32_neumann": "tg_cn_mixed.cu", "k_cn32_matvec": "tg_cn_mixed.cu",
+    "k_cn32_update": "tg_cn_mixed.cu", "k_cn_ir_residual_df": "tg_cn_mixed.cu",
+    "k_elas_ir_residual_df": "tg_mixed.cu", "k_ox_matvec": "tg_cn_ox.cu",
+    "k_ox_update": "tg_cn_ox.cu", "k_ox_pupdate": "tg_cn_ox.cu", "k_sl32": "tg_mixed.cu",
+    "k_sl32_pack": "tg_mixed.cu", "k_elas_coef_df": "tg_elasticity.cu",
+    "k_react": "tg_reaction.cu", "k_lame_df": "tg_reaction.cu"}
 
 
 def kernel_source_sha(kernel):
