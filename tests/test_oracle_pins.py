@@ -1023,3 +1023,71 @@ def test_displacement_extent_brute_force(oracle):
     got = oracle.displacement_extent(n, u, seed, 0.1)
     assert abs(got - r[r < 1.3].max()) < 1e-12
     assert oracle.displacement_extent(n, u, seed, 1.0) == 0.0
+
+
+def test_chebyshev_weight_of_the_neumann_terms():
+    """The inner CN preconditioner of the mixed path is w (y0 + y1) + (y2 + y3) on the Neumann
+    terms y_j = N^j D^-1 r, N = I - D^-1 A, with w = (2 d_max - 1) / d_max^2.  In n = 1 - x
+    (x an eigenvalue of the Jacobi-scaled operator, in [1/d_max, 2 - 1/d_max] by Gershgorin)
+    the polynomial is q = w (1 + n) + n^2 + n^3; up to the scale CG ignores, 1 - x q(x) must be
+    the shifted Chebyshev polynomial T_4((1 - x)/delta) / T_4(1/delta), delta = 1 - 1/d_max,
+    the minimax residual polynomial of degree 4 on that interval.  A wrong weight (the plain
+    Neumann series w = 1, or delta in place of delta^2) fails the identity."""
+    n = sym.symbols("n")
+    T4 = lambda s: 8 * s ** 4 - 8 * s ** 2 + 1  # noqa: E731
+    for d in (sym.Rational(3, 2), sym.Integer(4), sym.Integer(37), sym.Integer(10000)):
+        delta = 1 - 1 / d
+        w = (2 * d - 1) / d ** 2
+        x = 1 - n
+        K = 8 / (delta ** 4 * T4(1 / delta))
+        target = T4(n / delta) / T4(1 / delta)
+        q = w * (1 + n) + n ** 2 + n ** 3
+        assert sym.expand(1 - x * K * q - target) == 0   # exact, rational coefficients
+        for wrong in (sym.Integer(1), 1 - delta):
+            qw = wrong * (1 + n) + n ** 2 + n ** 3
+            assert sym.expand(1 - x * K * qw - target) != 0
+    # q > 0 on the interval (the preconditioner is SPD) for diagonals from 1 to 1e4
+    for dm in (1.5, 4.0, 37.0, 1e4):
+        xs = np.linspace(1 / dm, 2 - 1 / dm, 2001)
+        ns = 1 - xs
+        wv = (2 * dm - 1) / dm ** 2
+        qv = wv * (1 + ns) + ns ** 2 + ns ** 3
+        assert qv.min() > 0
+        # and it narrows the spread of x q(x) against the plain Neumann series (w = 1)
+        qn = 1 + ns + ns ** 2 + ns ** 3
+        kc = (xs * qv).max() / (xs * qv).min()
+        kn = (xs * qn).max() / (xs * qn).min()
+        assert kc < kn
+
+
+def test_chebyshev_neumann_preconditioner_is_symmetric_positive_on_the_cn_operator(oracle):
+    """The same cubic applied with the oracle's CN operator of a synthetic brain (16^3): M is
+    symmetric (<u, M v> = <M u, v>) and positive (<v, M v> > 0), as CG needs."""
+    n, dt = 16, 0.01
+    P = workload_params()
+    st = initial_state(n, 0)
+    K = oracle.diffusion_node_K(n, P, st["g"], st["w"], st["f"])
+    Kf = oracle.diffusion_faces(n, K)
+    h = TWO_PI / n
+    a = 0.5 * dt / h ** 2
+    A = lambda v: v - 0.5 * dt * oracle.diffusion_apply(n, Kf, np.ascontiguousarray(v))  # noqa: E731
+    diag = 1 + a * sum(Kf[q] + np.roll(Kf[q], 1, axis=2 - q) for q in range(3))
+    # the diagonal is A's: A applied to a unit vector at one node returns it there
+    e = np.zeros((n, n, n))
+    e[3, 5, 7] = 1.0
+    assert abs(A(e)[3, 5, 7] - diag[3, 5, 7]) < 1e-13
+    dm = diag.max()
+    w = (2 * dm - 1) / dm ** 2
+
+    def M(r):
+        y = [r / diag]
+        for _ in range(3):
+            y.append(y[-1] - A(y[-1]) / diag)
+        return w * (y[0] + y[1]) + (y[2] + y[3])
+
+    rng = np.random.default_rng(5)
+    u, v = rng.standard_normal((2, n, n, n))
+    assert abs(np.vdot(u, M(v)) - np.vdot(M(u), v)) < 1e-12 * np.linalg.norm(u) * np.linalg.norm(v)
+    for _ in range(3):
+        v = rng.standard_normal((n, n, n))
+        assert np.vdot(v, M(v)) > 0
